@@ -1,0 +1,187 @@
+/*
+ * elrt.h - C ABI of the GB300 element-learning radiative-transfer library.
+ *
+ * Steady mono-energetic transport on the x-z plane (Sec. 2.1, eq. RT_PDE):
+ *     s . grad u + sigma_e u - sigma_s int_S p(s, s') u(s') ds' = 0,   u = g on the inflow boundary,
+ * discretised by Q_p spectral elements on LGL nodes, N uniform angular cells with p_a = 0, upwind DG
+ * and its hybridisation (Sec. 2.2).  The library builds each element's in2out and in2sol operators
+ * (eqs. hdg_local_i2u, hdg_local_i2o, ang_ave), solves the global skeleton system
+ * (eq. hdg_global_mat) and recovers the mean intensity (Algorithm 1).
+ *
+ * Conventions shared by every entry point
+ *   - Mesh: a uniform nx x nz grid of square elements of side h (km); element e = ix + nx*iz,
+ *     ix along +x, iz along +z (up).  Node i = a + (p+1) b of an element sits at the LGL points
+ *     (xi_a, xi_b) of the reference square [-1, 1]^2.
+ *   - Angular cell k is the interval [k dth, (k+1) dth), dth = 2 pi / N, N a multiple of 4 (so no
+ *     cell is tangent to a face).  sigma_s = omega * sigma_e with omega constant per element.
+ *   - Faces of an element, in this order: bottom (-z), right (+x), top (+z), left (-x).
+ *   - Skeleton DOFs of an element (n_in = n_out = 2 (p+1) N): per face, per face node m in the
+ *     order of increasing coordinate along the face, the N/2 cells leaving (outflow) or entering
+ *     (inflow) through that face in increasing k.  The inflow of an element through face F is the
+ *     outflow of its neighbour through the opposite face, same nodes and cells, or boundary data.
+ *   - Boundary inflow array (eq. for hat V_h^g, the projection P_M g): the four domain sides in
+ *     the order bottom, right, top, left; nx faces (bottom/top) or nz faces (right/left) in the
+ *     order of increasing coordinate; per face p+1 nodes; per node the N/2 entering cells in
+ *     increasing k.  Length 2 (nx + nz) (p+1) N/2.
+ *   - in2out: [E][n_out][n_in] row-major; in2sol (mean intensity): [E][(p+1)^2][n_in] row-major.
+ *   - Pointers documented as "device" must be device (or managed) memory of the current CUDA
+ *     device; "host" pointers are ordinary host memory.  The caller owns every buffer it passes;
+ *     a context owns only its own workspace.
+ *   - Every call is asynchronous on the context's stream unless it says it synchronises.
+ *   - Errors: argument checks run on the host before any launch and return ELRT_EINVAL; CUDA
+ *     failures return ELRT_ECUDA; elrt_last_error() gives a message.  No exception and no abort
+ *     crosses this boundary.
+ */
+#ifndef ELRT_H
+#define ELRT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ELRT_OK = 0,
+    ELRT_EINVAL = 1,      /* bad argument (checked on the host before any launch) */
+    ELRT_ENOMEM = 2,      /* device allocation failed */
+    ELRT_ESINGULAR = 3,   /* an element's local matrix had a zero pivot */
+    ELRT_ENOCONV = 4,     /* iteration limit reached before the tolerance */
+    ELRT_ETIMEOUT = 5,    /* a bounded device wait gave up */
+    ELRT_ECUDA = 6,       /* a CUDA runtime call failed */
+    ELRT_ENOTRAINED = 7   /* the network has no weights */
+} elrt_status;
+
+typedef enum {
+    ELRT_ANG_FV0 = 0,     /* paper: P0 angular cells, cell-averaged direction and phase */
+    ELRT_ANG_DO = 1       /* direction and phase sampled at cell centres */
+} elrt_angular;
+
+typedef enum {
+    ELRT_LOCAL_FP64 = 0,     /* FP64 LU with partial pivoting on the CUDA cores */
+    ELRT_LOCAL_FP32_IR = 1,  /* FP32 LU, then FP64 iterative refinement with the structured residual */
+    ELRT_LOCAL_TF32_IR = 2   /* TF32 tensor-core trailing updates, FP32 accumulation, FP64 refinement */
+} elrt_local_mode;
+
+typedef enum { ELRT_F32 = 0, ELRT_F64 = 1 } elrt_dtype;
+
+/* Element discretisation: degree p (1..10), N angular cells (4..32, multiple of 4), HG asymmetry g. */
+typedef struct {
+    int32_t p;
+    int32_t n_angles;
+    int32_t angular;   /* elrt_angular */
+    double hg_g;       /* in [0, 1) */
+} elrt_disc;
+
+typedef struct elrt_ctx elrt_ctx;
+
+typedef struct {
+    int32_t refine_steps;      /* refinement steps taken (IR modes) */
+    int32_t n_flagged;         /* elements whose status word is non-zero */
+    double max_rel_residual;   /* max over elements of max|B^ + A X| / max|B^| after the last step */
+} elrt_local_stats;
+
+typedef struct {
+    int32_t iterations;        /* Arnoldi steps in total */
+    int32_t restarts;          /* completed restart cycles */
+    int32_t converged;         /* 1 if the relative residual reached rtol */
+    double rel_residual;       /* ||b - A x|| / ||b||, recomputed explicitly at exit */
+} elrt_solve_stats;
+
+/* ---------------------------------------------------------------- sizes and host-side tables */
+
+/* Sizes of one element: nodes (p+1)^2, local unknowns (p+1)^2 N, inflow/outflow DOFs 2 (p+1) N,
+ * and the length of the boundary inflow array of an nx x nz mesh.  -1 on an invalid disc. */
+int64_t elrt_n_nodes(const elrt_disc* disc);
+int64_t elrt_n_local(const elrt_disc* disc);
+int64_t elrt_n_skel(const elrt_disc* disc);
+int64_t elrt_n_inflow(const elrt_disc* disc, int32_t nx, int32_t nz);
+
+/* LGL nodes (ascending) and weights of degree p into host arrays of p+1 doubles (Sec. 2.2.1:
+ * Lagrange basis on the LGL points, which are also the quadrature points). */
+elrt_status elrt_lgl(int32_t p, double* xi, double* w);
+
+/* Phase coupling W[k][l] (host, N*N doubles, row-major) after dividing the scattering term by the
+ * cell width: fv0 W_kl = (1/dth) int_k int_l p(t - t'), do W_kl = dth p(t_k - t_l), rows scaled
+ * to sum to 1; p the HG function of Sec. 2.1 normalised on the circle. */
+elrt_status elrt_phase_matrix(const elrt_disc* disc, double* W);
+
+/* Physical coordinates (km) of the LGL nodes of every element: host arrays x, z of E (p+1)^2. */
+elrt_status elrt_node_coords(const elrt_disc* disc, int32_t nx, int32_t nz, double h, double* x, double* z);
+
+/* ---------------------------------------------------------------- context */
+
+/* Creates a context for one discretisation on the current CUDA device.  `stream` is a
+ * cudaStream_t (NULL: the legacy default stream).  Workspace is allocated on first use and grown
+ * as needed; elrt_destroy frees it.  Not thread-safe: one host thread per context. */
+elrt_status elrt_create(elrt_ctx** ctx, const elrt_disc* disc, void* stream);
+elrt_status elrt_destroy(elrt_ctx* ctx);
+elrt_status elrt_set_stream(elrt_ctx* ctx, void* stream);
+const char* elrt_status_str(elrt_status s);
+const char* elrt_last_error(const elrt_ctx* ctx);   /* message of the last failing call (or "") */
+
+/* ---------------------------------------------------------------- measurement */
+
+/* Kernel timing.  While enabled, the context records CUDA events on its own stream around every
+ * launch of its kernels and, at the next synchronisation inside a call, adds the elapsed times to
+ * per-kernel totals.  elrt_profile_get returns the total milliseconds and the number of timed
+ * launches of one kernel ("assemble", "lu_factor_solve", "lu_resolve", "residual", "restrict",
+ * "gemv", "krylov"); unknown names give 0.  elrt_launch_count returns how many kernels the
+ * context launched since creation or the last reset (whether or not timing is on). */
+elrt_status elrt_profile_enable(elrt_ctx* ctx, int32_t on);
+elrt_status elrt_profile_reset(elrt_ctx* ctx);
+elrt_status elrt_profile_get(elrt_ctx* ctx, const char* kernel, double* total_ms, int64_t* launches);
+int64_t elrt_launch_count(const elrt_ctx* ctx);
+
+/* ---------------------------------------------------------------- local stage (Sec. 2.2.3) */
+
+/* Element matrices of eq. hdg_local_mat, scaled to the reference element (Sec. 2.4.1: sigma -> h
+ * sigma / 2) and divided by the cell width: A = B - C + M - S (device, [E][nu][nu] FP64) and the
+ * right-hand sides -B^ (device, [E][nu][n_in] FP64).  kappa: device [E][(p+1)^2] FP64, km^-1 at
+ * the nodes; omega: device [E]; h: element side (km), or per-element sides h_elem (device [E],
+ * NULL to use h).  Provided for verification; the solve paths below never materialise A in FP64. */
+elrt_status elrt_assemble(elrt_ctx* ctx, int64_t n_elems, double h, const double* h_elem,
+                          const double* kappa, const double* omega, double* A, double* rhs);
+
+/* in2out and in2sol of E elements (eqs. hdg_local_i2u, hdg_local_i2o, ang_ave):
+ *   X = -(B - C + M - S)^{-1} B^,  in2out = R^o X,  in2sol = (1/N) sum_k X[(k, i), :].
+ * mode: elrt_local_mode; out_dtype: elrt_dtype of in2out/in2sol (device buffers sized above).
+ * refine_steps: FP64 refinement steps for the IR modes (ignored for FP64; 0..8).
+ * elem_status: device [E] int32 or NULL; per element 0 = ok, 1 = zero pivot, 2 = refinement
+ * residual above 1e-10 after the last step, 4 = non-finite value.  stats (host, may be NULL)
+ * synchronises the stream to fill it.  Inputs are checked for NaN and negative values on the
+ * device; a bad input makes the call return ELRT_EINVAL after synchronising. */
+elrt_status elrt_build_local(elrt_ctx* ctx, int64_t n_elems, double h, const double* h_elem,
+                             const double* kappa, const double* omega, int32_t mode,
+                             int32_t refine_steps, int32_t out_dtype, void* in2out, void* in2sol,
+                             int32_t* elem_status, elrt_local_stats* stats);
+
+/* ---------------------------------------------------------------- global stage (Sec. 2.3) */
+
+/* y = (I - A_int) x on the skeleton of an nx x nz mesh: per element y_K = x_K - in2out_K x_in(K)
+ * with the inflow gathered from the neighbours' outflow and zero on the domain boundary.
+ * x, y: device [E][n_out] FP64; in2out: device, dtype elrt_dtype. */
+elrt_status elrt_global_apply(elrt_ctx* ctx, int32_t nx, int32_t nz, const void* in2out, int32_t dtype,
+                              const double* x, double* y);
+
+/* Solves eq. hdg_global_mat, sum_K (R^o_K - A_i2o^K) u^ = 0 with the boundary inflow moved to the
+ * right-hand side, by restarted GMRES(restart) with classical Gram-Schmidt applied twice, FP64
+ * vectors and reductions, until ||b - A x|| <= rtol ||b|| or max_iter Arnoldi steps.
+ * inflow: device boundary data (layout above); skeleton: device [E][n_out] FP64, read as the
+ * initial guess if use_guess != 0, else zeroed; on return it holds the outflow DOFs.
+ * Synchronises.  Returns ELRT_ENOCONV (stats filled, skeleton = last iterate) if not converged. */
+elrt_status elrt_solve_global(elrt_ctx* ctx, int32_t nx, int32_t nz, const void* in2out, int32_t dtype,
+                              const double* inflow, double rtol, int32_t max_iter, int32_t restart,
+                              int32_t use_guess, double* skeleton, elrt_solve_stats* stats);
+
+/* Mean intensity u^m_K = in2sol_K x_in(K) (Algorithm 1 step 4 with eq. ang_ave), boundary inflow
+ * included.  in2sol: device [E][(p+1)^2][n_in]; skeleton: device [E][n_out] FP64;
+ * mean: device [E][(p+1)^2] FP64. */
+elrt_status elrt_recover_mean(elrt_ctx* ctx, int32_t nx, int32_t nz, const void* in2sol, int32_t dtype,
+                              const double* skeleton, const double* inflow, double* mean);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* ELRT_H */

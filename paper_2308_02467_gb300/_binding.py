@@ -1,0 +1,257 @@
+"""ctypes binding of libelrt.so (argument marshalling only)."""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libelrt.so")
+HEADER = os.path.join(HERE, "..", "include", "elrt.h")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_2308_02467_gb300.build`")
+_lib = C.CDLL(LIB_PATH)
+
+ANG_FV0, ANG_DO = 0, 1
+LOCAL_FP64, LOCAL_FP32_IR, LOCAL_TF32_IR = 0, 1, 2
+F32, F64 = 0, 1
+STATUS = {0: "ok", 1: "EINVAL", 2: "ENOMEM", 3: "ESINGULAR", 4: "ENOCONV", 5: "ETIMEOUT", 6: "ECUDA", 7: "ENOTRAINED"}
+
+
+class Disc(C.Structure):
+    _fields_ = [("p", C.c_int32), ("n_angles", C.c_int32), ("angular", C.c_int32), ("hg_g", C.c_double)]
+
+
+class LocalStats(C.Structure):
+    _fields_ = [("refine_steps", C.c_int32), ("n_flagged", C.c_int32), ("max_rel_residual", C.c_double)]
+
+
+class SolveStats(C.Structure):
+    _fields_ = [("iterations", C.c_int32), ("restarts", C.c_int32), ("converged", C.c_int32),
+                ("rel_residual", C.c_double)]
+
+
+class ElrtError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_vp, _i32, _i64, _d = C.c_void_p, C.c_int32, C.c_int64, C.c_double
+_P = C.POINTER
+_sig = {
+    "elrt_n_nodes": (_i64, [_P(Disc)]),
+    "elrt_n_local": (_i64, [_P(Disc)]),
+    "elrt_n_skel": (_i64, [_P(Disc)]),
+    "elrt_n_inflow": (_i64, [_P(Disc), _i32, _i32]),
+    "elrt_lgl": (_i32, [_i32, _vp, _vp]),
+    "elrt_phase_matrix": (_i32, [_P(Disc), _vp]),
+    "elrt_node_coords": (_i32, [_P(Disc), _i32, _i32, _d, _vp, _vp]),
+    "elrt_create": (_i32, [_P(_vp), _P(Disc), _vp]),
+    "elrt_destroy": (_i32, [_vp]),
+    "elrt_set_stream": (_i32, [_vp, _vp]),
+    "elrt_status_str": (C.c_char_p, [_i32]),
+    "elrt_last_error": (C.c_char_p, [_vp]),
+    "elrt_assemble": (_i32, [_vp, _i64, _d, _vp, _vp, _vp, _vp, _vp]),
+    "elrt_build_local": (_i32, [_vp, _i64, _d, _vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp, _vp, _P(LocalStats)]),
+    "elrt_global_apply": (_i32, [_vp, _i32, _i32, _vp, _i32, _vp, _vp]),
+    "elrt_solve_global": (_i32, [_vp, _i32, _i32, _vp, _i32, _vp, _d, _i32, _i32, _i32, _vp, _P(SolveStats)]),
+    "elrt_recover_mean": (_i32, [_vp, _i32, _i32, _vp, _i32, _vp, _vp, _vp]),
+    "elrt_profile_enable": (_i32, [_vp, _i32]),
+    "elrt_profile_reset": (_i32, [_vp]),
+    "elrt_profile_get": (_i32, [_vp, C.c_char_p, _P(_d), _P(_i64)]),
+    "elrt_launch_count": (_i64, [_vp]),
+}
+for _name, (_res, _args) in _sig.items():
+    _f = getattr(_lib, _name)
+    _f.restype = _res
+    _f.argtypes = _args
+
+
+def exported_symbols() -> list[str]:
+    """Names of the entry points declared in include/elrt.h (each must resolve in the library)."""
+    text = open(HEADER).read()
+    return sorted(set(re.findall(r"\b(elrt_[a-z0-9_]+)\s*\(", text)))
+
+
+def _check(status, ctx=None):
+    if status != 0:
+        msg = _lib.elrt_last_error(ctx)
+        raise ElrtError(status, msg.decode() if msg else "")
+
+
+def _disc(p, n_angles, hg_g=0.0, angular=ANG_FV0) -> Disc:
+    return Disc(int(p), int(n_angles), int(angular), float(hg_g))
+
+
+# ----------------------------------------------------------------------------- host helpers
+def elrt_n_nodes(p, n_angles):
+    return _lib.elrt_n_nodes(C.byref(_disc(p, n_angles)))
+
+
+def elrt_n_local(p, n_angles):
+    return _lib.elrt_n_local(C.byref(_disc(p, n_angles)))
+
+
+def elrt_n_skel(p, n_angles):
+    return _lib.elrt_n_skel(C.byref(_disc(p, n_angles)))
+
+
+def elrt_n_inflow(p, n_angles, nx, nz):
+    return _lib.elrt_n_inflow(C.byref(_disc(p, n_angles)), nx, nz)
+
+
+def elrt_lgl(p):
+    xi = np.zeros(p + 1)
+    w = np.zeros(p + 1)
+    _check(_lib.elrt_lgl(p, xi.ctypes.data, w.ctypes.data))
+    return xi, w
+
+
+def elrt_phase_matrix(n_angles, hg_g, angular=ANG_FV0):
+    W = np.zeros((n_angles, n_angles))
+    _check(_lib.elrt_phase_matrix(C.byref(_disc(1, n_angles, hg_g, angular)), W.ctypes.data))
+    return W
+
+
+def elrt_node_coords(p, n_angles, nx, nz, h):
+    nm = (p + 1) ** 2
+    x = np.zeros((nx * nz, nm))
+    z = np.zeros((nx * nz, nm))
+    _check(_lib.elrt_node_coords(C.byref(_disc(p, n_angles)), nx, nz, h, x.ctypes.data, z.ctypes.data))
+    return x, z
+
+
+# ----------------------------------------------------------------------------- device calls
+def _ptr(t, dtype=None, n=None, name="tensor"):
+    import torch
+    if t is None:
+        return None
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must be {dtype}, got {t.dtype}")
+    if n is not None and t.numel() != n:
+        raise ValueError(f"{name} must have {n} elements, got {t.numel()}")
+    return t.data_ptr()
+
+
+def _dt(t):
+    import torch
+    if t.dtype == torch.float32:
+        return F32
+    if t.dtype == torch.float64:
+        return F64
+    raise ValueError("operators must be float32 or float64")
+
+
+class Context:
+    """An elrt_ctx for one discretisation; calls run on the current torch CUDA stream."""
+
+    def __init__(self, p, n_angles, hg_g=0.0, angular=ANG_FV0):
+        import torch
+        self.disc = _disc(p, n_angles, hg_g, angular)
+        self.p, self.n_angles, self.hg_g, self.angular = p, n_angles, hg_g, angular
+        self.nm = (p + 1) ** 2
+        self.nu = self.nm * n_angles
+        self.nin = 2 * (p + 1) * n_angles
+        h = C.c_void_p()
+        _check(_lib.elrt_create(C.byref(h), C.byref(self.disc), C.c_void_p(torch.cuda.current_stream().cuda_stream)))
+        self._h = h
+
+    def _sync_stream(self):
+        import torch
+        _lib.elrt_set_stream(self._h, C.c_void_p(torch.cuda.current_stream().cuda_stream))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.elrt_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- measurement
+    def elrt_profile_enable(self, on=True):
+        _check(_lib.elrt_profile_enable(self._h, int(bool(on))), self._h)
+
+    def elrt_profile_reset(self):
+        _check(_lib.elrt_profile_reset(self._h), self._h)
+
+    def elrt_profile_get(self, kernel):
+        ms, n = C.c_double(), C.c_int64()
+        _check(_lib.elrt_profile_get(self._h, kernel.encode(), C.byref(ms), C.byref(n)), self._h)
+        return ms.value, n.value
+
+    def elrt_launch_count(self):
+        return _lib.elrt_launch_count(self._h)
+
+    # ---- local stage
+    def elrt_assemble(self, kappa, omega, h, A, rhs, h_elem=None):
+        import torch
+        E = omega.numel()
+        self._sync_stream()
+        _check(_lib.elrt_assemble(self._h, E, float(h), _ptr(h_elem, torch.float64, E, "h_elem"),
+                                  _ptr(kappa, torch.float64, E * self.nm, "kappa"),
+                                  _ptr(omega, torch.float64, E, "omega"),
+                                  _ptr(A, torch.float64, E * self.nu * self.nu, "A"),
+                                  _ptr(rhs, torch.float64, E * self.nu * self.nin, "rhs")), self._h)
+
+    def elrt_build_local(self, kappa, omega, h, in2out, in2sol, mode=LOCAL_FP64, refine_steps=2,
+                         elem_status=None, h_elem=None, stats=True):
+        import torch
+        E = omega.numel()
+        self._sync_stream()
+        st = LocalStats()
+        dt = _dt(in2out)
+        if in2sol.dtype != in2out.dtype:
+            raise ValueError("in2out and in2sol must share a dtype")
+        _check(_lib.elrt_build_local(
+            self._h, E, float(h), _ptr(h_elem, torch.float64, E, "h_elem"),
+            _ptr(kappa, torch.float64, E * self.nm, "kappa"), _ptr(omega, torch.float64, E, "omega"),
+            int(mode), int(refine_steps), dt, _ptr(in2out, None, E * self.nin * self.nin, "in2out"),
+            _ptr(in2sol, None, E * self.nm * self.nin, "in2sol"),
+            _ptr(elem_status, torch.int32, E, "elem_status"), C.byref(st) if stats else None), self._h)
+        return st if stats else None
+
+    # ---- global stage
+    def elrt_global_apply(self, nx, nz, in2out, x, y):
+        import torch
+        n = nx * nz * self.nin
+        self._sync_stream()
+        _check(_lib.elrt_global_apply(self._h, nx, nz, _ptr(in2out, None, n * self.nin, "in2out"), _dt(in2out),
+                                      _ptr(x, torch.float64, n, "x"), _ptr(y, torch.float64, n, "y")), self._h)
+
+    def elrt_solve_global(self, nx, nz, in2out, inflow, skeleton, rtol=1e-10, max_iter=5000, restart=50,
+                          use_guess=False, raise_on_noconv=True):
+        import torch
+        n = nx * nz * self.nin
+        self._sync_stream()
+        st = SolveStats()
+        s = _lib.elrt_solve_global(self._h, nx, nz, _ptr(in2out, None, n * self.nin, "in2out"), _dt(in2out),
+                                   _ptr(inflow, torch.float64, 2 * (nx + nz) * (self.p + 1) * (self.n_angles // 2),
+                                        "inflow"),
+                                   float(rtol), int(max_iter), int(restart), int(bool(use_guess)),
+                                   _ptr(skeleton, torch.float64, n, "skeleton"), C.byref(st))
+        if s == 4 and not raise_on_noconv:
+            return st
+        _check(s, self._h)
+        return st
+
+    def elrt_recover_mean(self, nx, nz, in2sol, skeleton, inflow, mean):
+        import torch
+        E = nx * nz
+        self._sync_stream()
+        _check(_lib.elrt_recover_mean(self._h, nx, nz, _ptr(in2sol, None, E * self.nm * self.nin, "in2sol"),
+                                      _dt(in2sol), _ptr(skeleton, torch.float64, E * self.nin, "skeleton"),
+                                      _ptr(inflow, torch.float64, None, "inflow"),
+                                      _ptr(mean, torch.float64, E * self.nm, "mean")), self._h)

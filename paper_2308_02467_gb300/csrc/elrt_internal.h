@@ -1,0 +1,89 @@
+// Internal declarations shared by the host code and the kernels of the library.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <map>
+#include <string>
+#include <vector>
+
+#include "../../include/elrt.h"
+
+#define ELRT_MAX_N1 11   // p <= 10
+#define ELRT_MAX_ANG 32  // N <= 32
+
+// Everything a kernel needs to know about the element discretisation; passed by value
+// (fits in the 4 KB classic kernel-parameter space).
+struct Tab {
+    int p, n1, nm, N, half, nu, nin, nface;
+    double w[ELRT_MAX_N1];                      // LGL weights
+    double D[ELRT_MAX_N1 * ELRT_MAX_N1];        // D[m*n1+a] = l_a'(xi_m)
+    double sx[ELRT_MAX_ANG], sz[ELRT_MAX_ANG];  // direction of cell k
+    double wc[ELRT_MAX_ANG];                    // circulant phase: W[k][l] = wc[(k-l) mod N]
+    double sdn[4][ELRT_MAX_ANG];                // sbar_k . n_F
+    signed char outc[4][ELRT_MAX_ANG / 2];      // outflow cells of face F, increasing k
+    signed char inc[4][ELRT_MAX_ANG / 2];       // inflow cells of face F, increasing k
+};
+
+// volume node at face position m of face F (bottom, right, top, left)
+__host__ __device__ inline int face_node(int F, int m, int p) {
+    int n1 = p + 1;
+    switch (F) {
+        case 0: return m;
+        case 1: return p + n1 * m;
+        case 2: return m + n1 * p;
+        default: return n1 * m;
+    }
+}
+
+struct elrt_ctx {
+    elrt_disc disc;
+    Tab tab;
+    cudaStream_t stream;
+    int device;
+    std::string last_error;
+    // workspace (grown on demand)
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    void* gm = nullptr;     // GMRES workspace
+    size_t gm_bytes = 0;
+    int* d_flags = nullptr; // small device scratch for flags/counters
+    double* h_pinned = nullptr;  // pinned host scratch for small read-backs
+    // measurement
+    int64_t launches = 0;
+    bool profiling = false;
+    struct Pending { const char* name; cudaEvent_t a, b; };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> event_pool;
+    std::map<std::string, std::pair<double, int64_t>> prof;
+};
+
+// Brackets kernel launches with events when profiling is on; counts launches always.
+struct ProfScope {
+    elrt_ctx* ctx;
+    int idx;
+    ProfScope(elrt_ctx* c, const char* name, int nlaunch = 1);
+    ~ProfScope();
+};
+void prof_flush(elrt_ctx* ctx);  // call after a stream synchronisation
+
+// ---- host helpers implemented in host.cpp
+elrt_status ctx_fail(elrt_ctx* ctx, elrt_status s, const std::string& msg);
+elrt_status cuda_check(elrt_ctx* ctx, cudaError_t e, const char* what);
+elrt_status ensure_ws(elrt_ctx* ctx, void** buf, size_t* have, size_t need);
+
+// ---- launchers implemented in local.cu
+elrt_status local_assemble_f64(elrt_ctx* ctx, int64_t E, double h, const double* h_elem, const double* kappa,
+                               const double* omega, double* A, double* rhs);
+elrt_status local_build(elrt_ctx* ctx, int64_t E, double h, const double* h_elem, const double* kappa,
+                        const double* omega, int mode, int refine_steps, int out_dtype, void* in2out,
+                        void* in2sol, int32_t* elem_status, elrt_local_stats* stats);
+
+// ---- launchers implemented in global.cu
+elrt_status global_apply(elrt_ctx* ctx, int nx, int nz, const void* A, int dtype, const double* x, double* y);
+elrt_status global_solve(elrt_ctx* ctx, int nx, int nz, const void* A, int dtype, const double* inflow,
+                         double rtol, int max_iter, int restart, int use_guess, double* x,
+                         elrt_solve_stats* stats);
+elrt_status global_recover(elrt_ctx* ctx, int nx, int nz, const void* A, int dtype, const double* x,
+                           const double* inflow, double* mean);

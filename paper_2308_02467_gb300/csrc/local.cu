@@ -1,0 +1,746 @@
+// Local stage (Sec. 2.2.3, eqs. hdg_local_mat, hdg_local_i2u, hdg_local_i2o, ang_ave; App. A):
+// per element, assemble [A | -B^], factor A = P L U by blocked right-looking LU with partial
+// pivoting while the right-hand sides ride along as extra columns (so the forward substitution
+// comes for free), back-substitute, optionally refine in FP64 with the structured residual, and
+// restrict the solution to in2out / in2sol.
+//
+// Layout of the per-element workspace matrix M (row-major, leading dimension ld):
+//   columns [0, nu)        the local matrix A, overwritten by L (unit lower, below the diagonal)
+//                          and U; panels are swapped LAPACK-style inside a panel and
+//                          LINPACK-style across panels (earlier L columns keep their order);
+//   columns [nu, nu + nin) the right-hand sides -B^, overwritten by the solution X (or by the
+//                          refinement residual / correction).
+// One thread block of 256 threads works on one element at a time.
+#include <math.h>
+#include <stdio.h>
+
+#include <algorithm>
+
+#include "elrt_internal.h"
+
+namespace {
+
+constexpr int kThreads = 256;
+
+// ------------------------------------------------------------------------------------------------
+// assembly
+// ------------------------------------------------------------------------------------------------
+
+// Entry (row r = (k, i), column c) of the augmented matrix [A | -B^] of eq. hdg_local_mat divided
+// by (h/2) dth, with kh = kappa_hat_i and om = omega.  Node i = (a, b), column node j = (jc, jd).
+__device__ __forceinline__ double aug_entry(const Tab& t, int k, int i, int c, const double* kh, double om) {
+    const int nm = t.nm, n1 = t.n1, p = t.p;
+    const int a = i % n1, b = i / n1;
+    double v = 0.0;
+    if (c < t.nu) {
+        const int l = c / nm, j = c - l * nm;
+        if (l == k) {
+            const int jc = j % n1, jd = j / n1;
+            const double wj = t.w[jc] * t.w[jd];
+            // -C^k_ij = -w_j (sbar_k . grad phi_i)(x_j)
+            if (jd == b) v -= wj * t.sx[k] * t.D[jc * n1 + a];
+            if (jc == a) v -= wj * t.sz[k] * t.D[jd * n1 + b];
+            if (j == i) {
+                // B^k_ii: outflow faces through node i; M_ii = w_i kappa_hat_i
+                double bd = 0.0;
+                if (b == 0 && t.sdn[0][k] > 0) bd += t.w[a] * t.sdn[0][k];
+                if (a == p && t.sdn[1][k] > 0) bd += t.w[b] * t.sdn[1][k];
+                if (b == p && t.sdn[2][k] > 0) bd += t.w[a] * t.sdn[2][k];
+                if (a == 0 && t.sdn[3][k] > 0) bd += t.w[b] * t.sdn[3][k];
+                v += bd + t.w[a] * t.w[b] * kh[i];
+            }
+        }
+        if (j == i) {
+            int d = k - l;
+            if (d < 0) d += t.N;
+            v -= t.w[a] * t.w[b] * om * kh[i] * t.wc[d];  // -S
+        }
+    } else if (c < t.nu + t.nin) {
+        const int col = c - t.nu;
+        const int F = col / t.nface, rem = col - F * t.nface;
+        const int m = rem / t.half, kk = rem - m * t.half;
+        if (t.inc[F][kk] == k && face_node(F, m, p) == i) v = -t.w[m] * t.sdn[F][k];  // -B^ (positive)
+    }
+    return v;
+}
+
+// Grid: (E, N).  Block (e, k) writes rows (k, 0..nm-1) of element e; columns >= nu + nin are 0.
+// Also validates the inputs (flags[0] |= 1 on a negative or non-finite kappa / h, omega outside [0, 1]).
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_assemble(Tab t, double h, const double* __restrict__ h_elem,
+                                                       const double* __restrict__ kappa,
+                                                       const double* __restrict__ omega, T* __restrict__ M,
+                                                       int64_t ld, int64_t estride, T* __restrict__ rhs_out,
+                                                       int64_t rhs_ld, int* flags) {
+    __shared__ double kh[ELRT_MAX_N1 * ELRT_MAX_N1];
+    const int64_t e = blockIdx.x;
+    const int k = blockIdx.y;
+    const double he = h_elem ? h_elem[e] : h;
+    const double om = omega[e];
+    for (int i = threadIdx.x; i < t.nm; i += blockDim.x) {
+        double kv = kappa[e * t.nm + i];
+        if (!(kv >= 0.0) || !isfinite(kv)) atomicOr(flags, 1);
+        kh[i] = kv * 0.5 * he;
+    }
+    if (threadIdx.x == 0 && (!(he > 0.0) || !isfinite(he) || !(om >= 0.0 && om <= 1.0))) atomicOr(flags, 1);
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    T* Me = M + e * estride;
+    for (int i = warp; i < t.nm; i += kThreads / 32) {
+        const int r = k * t.nm + i;
+        if (rhs_out) {
+            // separate outputs: A into M (ld = nu), -B^ into rhs_out
+            for (int c = lane; c < t.nu; c += 32) Me[(int64_t)r * ld + c] = (T)aug_entry(t, k, i, c, kh, om);
+            for (int c = lane; c < t.nin; c += 32)
+                rhs_out[e * (int64_t)t.nu * rhs_ld + (int64_t)r * rhs_ld + c] = (T)aug_entry(t, k, i, t.nu + c, kh, om);
+        } else {
+            for (int c = lane; c < ld; c += 32) Me[(int64_t)r * ld + c] = (T)aug_entry(t, k, i, c, kh, om);
+        }
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// blocked LU with partial pivoting on the CUDA cores
+// ------------------------------------------------------------------------------------------------
+
+template <typename T>
+__device__ __forceinline__ T tabs(T x) { return x < T(0) ? -x : x; }
+
+// M[r0 + r][c0 + c] -= sum_q Ls[(lrow0 + r) * lds + q] * Us[q * CW + c]
+// for r in [0, nrows), c in [0, ncols) (ncols <= CW), q in [0, jb).
+// Thread (tr, tc) = (tid / 32, tid % 32) owns rows tr + 8 s (s < 8) and columns tc + 32 q (q < QN).
+template <typename T, int NB, int QN>
+__device__ __forceinline__ void rank_update(T* __restrict__ M, int64_t ld, int r0, int nrows, int c0, int ncols,
+                                            const T* __restrict__ Ls, int lds, int lrow0, const T* __restrict__ Us,
+                                            int jb) {
+    constexpr int CW = 32 * QN;
+    const int tr = threadIdx.x >> 5, tc = threadIdx.x & 31;
+    for (int rb = 0; rb < nrows; rb += 64) {
+        T acc[8][QN];
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+            const int r = rb + tr + 8 * s;
+#pragma unroll
+            for (int q = 0; q < QN; ++q) {
+                const int c = tc + 32 * q;
+                acc[s][q] = (r < nrows && c < ncols) ? M[(int64_t)(r0 + r) * ld + c0 + c] : T(0);
+            }
+        }
+#pragma unroll 4
+        for (int kq = 0; kq < NB; ++kq) {
+            if (kq < jb) {
+                T bv[QN];
+#pragma unroll
+                for (int q = 0; q < QN; ++q) bv[q] = Us[kq * CW + tc + 32 * q];
+#pragma unroll
+                for (int s = 0; s < 8; ++s) {
+                    const int r = rb + tr + 8 * s;
+                    const T av = (r < nrows) ? Ls[(lrow0 + r) * lds + kq] : T(0);
+#pragma unroll
+                    for (int q = 0; q < QN; ++q) acc[s][q] -= av * bv[q];
+                }
+            }
+        }
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+            const int r = rb + tr + 8 * s;
+#pragma unroll
+            for (int q = 0; q < QN; ++q) {
+                const int c = tc + 32 * q;
+                if (r < nrows && c < ncols) M[(int64_t)(r0 + r) * ld + c0 + c] = acc[s][q];
+            }
+        }
+    }
+}
+
+// block-wide argmax of |value| (ties: smallest index)
+template <typename T>
+__device__ __forceinline__ void block_argmax(T v, int idx, T* sval, int* sidx, T* out_v, int* out_i) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        T ov = __shfl_down_sync(0xffffffffu, v, off);
+        int oi = __shfl_down_sync(0xffffffffu, idx, off);
+        if (ov > v || (ov == v && oi < idx && oi >= 0)) {
+            v = ov;
+            idx = oi;
+        }
+    }
+    if (lane == 0) {
+        sval[warp] = v;
+        sidx[warp] = idx;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        T bv = sval[0];
+        int bi = sidx[0];
+        for (int w = 1; w < kThreads / 32; ++w) {
+            if (sval[w] > bv || (sval[w] == bv && sidx[w] >= 0 && (bi < 0 || sidx[w] < bi))) {
+                bv = sval[w];
+                bi = sidx[w];
+            }
+        }
+        *out_v = bv;
+        *out_i = bi;
+    }
+    __syncthreads();
+}
+
+// Forward step of panel J on the columns [c_begin, c_end): apply the panel's row swaps, solve with
+// the unit lower L11 (rows 0..jb-1 of Ps) and update the rows below with L21.
+// Ps holds rows J..nu-1 of the panel columns (relative row index), stride NB + 1.
+template <typename T, int NB, int QN>
+__device__ void panel_forward(T* __restrict__ M, int64_t ld, int nu, int J, int jb, const int* ipiv_s, const T* Ps,
+                              T* Us, int c_begin, int c_end) {
+    constexpr int CW = 32 * QN;
+    constexpr int lds = NB + 1;
+    for (int cs = c_begin; cs < c_end; cs += CW) {
+        const int ncols = min(CW, c_end - cs);
+        for (int tcol = threadIdx.x; tcol < CW; tcol += kThreads) {
+            if (tcol < ncols) {
+                const int col = cs + tcol;
+                T x[NB];
+#pragma unroll
+                for (int jj = 0; jj < NB; ++jj) {
+                    if (jj < jb) {
+                        const int pr = ipiv_s[jj];
+                        if (pr != jj) {
+                            T a = M[(int64_t)(J + jj) * ld + col];
+                            T b = M[(int64_t)(J + pr) * ld + col];
+                            M[(int64_t)(J + jj) * ld + col] = b;
+                            M[(int64_t)(J + pr) * ld + col] = a;
+                        }
+                    }
+                }
+#pragma unroll
+                for (int jj = 0; jj < NB; ++jj) x[jj] = (jj < jb) ? M[(int64_t)(J + jj) * ld + col] : T(0);
+#pragma unroll
+                for (int jj = 1; jj < NB; ++jj) {
+                    T s = x[jj];
+#pragma unroll
+                    for (int ii = 0; ii < jj; ++ii) s -= Ps[jj * lds + ii] * x[ii];
+                    x[jj] = s;
+                }
+#pragma unroll
+                for (int jj = 0; jj < NB; ++jj) {
+                    if (jj < jb) M[(int64_t)(J + jj) * ld + col] = x[jj];
+                    Us[jj * CW + tcol] = x[jj];
+                }
+            } else {
+#pragma unroll
+                for (int jj = 0; jj < NB; ++jj) Us[jj * CW + tcol] = T(0);
+            }
+        }
+        __syncthreads();
+        rank_update<T, NB, QN>(M, ld, J + jb, nu - J - jb, cs, ncols, Ps, lds, jb, Us, jb);
+        __syncthreads();
+    }
+}
+
+// Backward substitution U X = Y on the columns [c_begin, c_end), panel by panel from the last.
+template <typename T, int NB, int QN>
+__device__ void backward_sweep(T* __restrict__ M, int64_t ld, int nu, T* Ps, T* Us, int c_begin, int c_end) {
+    constexpr int CW = 32 * QN;
+    constexpr int lds = NB + 1;
+    const int last = ((nu - 1) / NB) * NB;
+    for (int J = last; J >= 0; J -= NB) {
+        const int jb = min(NB, nu - J);
+        // U[0:J+jb, J:J+jb] -> Ps
+        for (int idx = threadIdx.x; idx < (J + jb) * NB; idx += kThreads) {
+            const int r = idx / NB, c = idx - r * NB;
+            Ps[r * lds + c] = (c < jb) ? M[(int64_t)r * ld + J + c] : T(0);
+        }
+        __syncthreads();
+        for (int cs = c_begin; cs < c_end; cs += CW) {
+            const int ncols = min(CW, c_end - cs);
+            for (int tcol = threadIdx.x; tcol < CW; tcol += kThreads) {
+                if (tcol < ncols) {
+                    const int col = cs + tcol;
+                    T x[NB];
+#pragma unroll
+                    for (int jj = 0; jj < NB; ++jj) x[jj] = (jj < jb) ? M[(int64_t)(J + jj) * ld + col] : T(0);
+#pragma unroll
+                    for (int jj = NB - 1; jj >= 0; --jj) {
+                        if (jj < jb) {
+                            T s = x[jj];
+#pragma unroll
+                            for (int ii = jj + 1; ii < NB; ++ii)
+                                if (ii < jb) s -= Ps[(J + jj) * lds + ii] * x[ii];
+                            const T d = Ps[(J + jj) * lds + jj];
+                            x[jj] = (d != T(0)) ? s / d : T(0);
+                        }
+                    }
+#pragma unroll
+                    for (int jj = 0; jj < NB; ++jj) {
+                        if (jj < jb) M[(int64_t)(J + jj) * ld + col] = x[jj];
+                        Us[jj * CW + tcol] = x[jj];
+                    }
+                } else {
+#pragma unroll
+                    for (int jj = 0; jj < NB; ++jj) Us[jj * CW + tcol] = T(0);
+                }
+            }
+            __syncthreads();
+            if (J > 0) rank_update<T, NB, QN>(M, ld, 0, J, cs, ncols, Ps, lds, 0, Us, jb);
+            __syncthreads();
+        }
+    }
+}
+
+template <typename T, int NB, int QN>
+constexpr size_t lu_smem_bytes(int nu) {
+    return (size_t)nu * (NB + 1) * sizeof(T) + (size_t)NB * 32 * QN * sizeof(T);
+}
+
+// Factor A (columns [0, nu)) and solve for the right-hand sides (columns [nu, nu + nin)).
+// estatus[e] |= 1 on an exactly zero pivot (the element's result is then meaningless).
+template <typename T, int NB, int QN>
+__global__ void __launch_bounds__(kThreads, 1) k_lu_factor_solve(Tab t, T* __restrict__ Mall, int64_t ld,
+                                                                 int64_t estride, int* __restrict__ ipiv_all,
+                                                                 int* __restrict__ estatus, int64_t E) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* Ps = reinterpret_cast<T*>(smem_raw);
+    T* Us = Ps + (size_t)t.nu * (NB + 1);
+    __shared__ T red_v[kThreads / 32];
+    __shared__ int red_i[kThreads / 32];
+    __shared__ int ipiv_s[NB];
+    __shared__ T piv_v;
+    __shared__ int piv_i;
+    constexpr int lds = NB + 1;
+    const int nu = t.nu, ncols = t.nu + t.nin;
+    for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
+        T* M = Mall + e * estride;
+        int* ipiv = ipiv_all + e * (int64_t)nu;
+        int bad = 0;
+        for (int J = 0; J < nu; J += NB) {
+            const int jb = min(NB, nu - J);
+            const int R = nu - J;
+            for (int idx = threadIdx.x; idx < R * NB; idx += kThreads) {
+                const int r = idx / NB, c = idx - r * NB;
+                Ps[r * lds + c] = (c < jb) ? M[(int64_t)(J + r) * ld + J + c] : T(0);
+            }
+            __syncthreads();
+            // unblocked LU with partial pivoting of the R x jb panel in shared memory
+            for (int jj = 0; jj < jb; ++jj) {
+                T bv = T(-1);
+                int bi = -1;
+                for (int r = jj + threadIdx.x; r < R; r += kThreads) {
+                    const T v = tabs(Ps[r * lds + jj]);
+                    if (v > bv) {
+                        bv = v;
+                        bi = r;
+                    }
+                }
+                block_argmax<T>(bv, bi, red_v, red_i, &piv_v, &piv_i);
+                const int pr = piv_i;
+                if (threadIdx.x == 0) ipiv_s[jj] = pr;
+                if (!(piv_v > T(0))) bad = 1;
+                if (pr != jj) {
+                    for (int c = threadIdx.x; c < NB; c += kThreads) {
+                        T x = Ps[jj * lds + c];
+                        Ps[jj * lds + c] = Ps[pr * lds + c];
+                        Ps[pr * lds + c] = x;
+                    }
+                }
+                __syncthreads();
+                const T d = Ps[jj * lds + jj];
+                const T inv = (d != T(0)) ? T(1) / d : T(0);
+                for (int r = jj + 1 + threadIdx.x; r < R; r += kThreads) {
+                    const T l = Ps[r * lds + jj] * inv;
+                    Ps[r * lds + jj] = l;
+                    for (int c = jj + 1; c < jb; ++c) Ps[r * lds + c] -= l * Ps[jj * lds + c];
+                }
+                __syncthreads();
+            }
+            for (int idx = threadIdx.x; idx < R * jb; idx += kThreads) {
+                const int r = idx / jb, c = idx - r * jb;
+                M[(int64_t)(J + r) * ld + J + c] = Ps[r * lds + c];
+            }
+            if (threadIdx.x < jb) ipiv[J + threadIdx.x] = J + ipiv_s[threadIdx.x];
+            __syncthreads();
+            panel_forward<T, NB, QN>(M, ld, nu, J, jb, ipiv_s, Ps, Us, J + jb, ncols);
+        }
+        backward_sweep<T, NB, QN>(M, ld, nu, Ps, Us, nu, ncols);
+        if (threadIdx.x == 0 && bad) estatus[e] |= 1;
+        __syncthreads();
+    }
+}
+
+// Solve A D = R for the right-hand sides stored in columns [nu, nu + nin), with the factors and
+// pivots left by k_lu_factor_solve (forward sweep with the interleaved swaps, then backward).
+template <typename T, int NB, int QN>
+__global__ void __launch_bounds__(kThreads, 1) k_lu_resolve(Tab t, T* __restrict__ Mall, int64_t ld, int64_t estride,
+                                                            const int* __restrict__ ipiv_all, int64_t E) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* Ps = reinterpret_cast<T*>(smem_raw);
+    T* Us = Ps + (size_t)t.nu * (NB + 1);
+    __shared__ int ipiv_s[NB];
+    constexpr int lds = NB + 1;
+    const int nu = t.nu, ncols = t.nu + t.nin;
+    for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
+        T* M = Mall + e * estride;
+        const int* ipiv = ipiv_all + e * (int64_t)nu;
+        for (int J = 0; J < nu; J += NB) {
+            const int jb = min(NB, nu - J);
+            const int R = nu - J;
+            for (int idx = threadIdx.x; idx < R * NB; idx += kThreads) {
+                const int r = idx / NB, c = idx - r * NB;
+                Ps[r * lds + c] = (c < jb) ? M[(int64_t)(J + r) * ld + J + c] : T(0);
+            }
+            if (threadIdx.x < jb) ipiv_s[threadIdx.x] = ipiv[J + threadIdx.x] - J;
+            __syncthreads();
+            panel_forward<T, NB, QN>(M, ld, nu, J, jb, ipiv_s, Ps, Us, nu, ncols);
+        }
+        backward_sweep<T, NB, QN>(M, ld, nu, Ps, Us, nu, ncols);
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// FP64 refinement: structured residual R = -B^ - A X computed from the tables (never from the
+// dense A), optional accumulation X += D, per-element max |R|.
+// ------------------------------------------------------------------------------------------------
+
+// mode 0: X64 = (double) src;  mode 1: X64 += (double) src.  Afterwards R -> src (as T).
+// One block per element; columns in chunks of CWR staged in shared memory.
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_residual(Tab t, double h, const double* __restrict__ h_elem,
+                                                       const double* __restrict__ kappa,
+                                                       const double* __restrict__ omega, T* __restrict__ Mall,
+                                                       int64_t ld, int64_t estride, double* __restrict__ X64all,
+                                                       int mode, int CWR, double* __restrict__ maxres, int64_t E) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* Xs = reinterpret_cast<double*>(smem_raw);  // [nu][CWR]
+    __shared__ double kh[ELRT_MAX_N1 * ELRT_MAX_N1];
+    __shared__ double red[kThreads / 32];
+    const int nu = t.nu, nin = t.nin, nm = t.nm, n1 = t.n1, N = t.N, p = t.p;
+    const int64_t e = blockIdx.x;
+    if (e >= E) return;
+    const double he = h_elem ? h_elem[e] : h;
+    const double om = omega[e];
+    for (int i = threadIdx.x; i < nm; i += kThreads) kh[i] = kappa[e * nm + i] * 0.5 * he;
+    T* M = Mall + e * estride;
+    double* X64 = X64all + e * (int64_t)nu * nin;
+    double rmax = 0.0;
+    const int rows_per_pass = kThreads / CWR;
+    const int tcol = threadIdx.x % CWR, trow = threadIdx.x / CWR;
+    for (int cs = 0; cs < nin; cs += CWR) {
+        __syncthreads();
+        for (int r = trow; r < nu; r += rows_per_pass) {
+            const int col = cs + tcol;
+            double v = 0.0;
+            if (col < nin) {
+                const double d = (double)M[(int64_t)r * ld + nu + col];
+                v = (mode == 0) ? d : X64[(int64_t)r * nin + col] + d;
+                X64[(int64_t)r * nin + col] = v;
+            }
+            Xs[r * CWR + tcol] = v;
+        }
+        __syncthreads();
+        for (int r = trow; r < nu; r += rows_per_pass) {
+            const int col = cs + tcol;
+            if (col >= nin) continue;
+            const int k = r / nm, i = r - k * nm;
+            const int a = i % n1, b = i / n1;
+            const double wi = t.w[a] * t.w[b];
+            // (B + M) X
+            double bd = 0.0;
+            if (b == 0 && t.sdn[0][k] > 0) bd += t.w[a] * t.sdn[0][k];
+            if (a == p && t.sdn[1][k] > 0) bd += t.w[b] * t.sdn[1][k];
+            if (b == p && t.sdn[2][k] > 0) bd += t.w[a] * t.sdn[2][k];
+            if (a == 0 && t.sdn[3][k] > 0) bd += t.w[b] * t.sdn[3][k];
+            double ax = (bd + wi * kh[i]) * Xs[r * CWR + tcol];
+            // - C X: sum over the x-line and the z-line through node i
+            const int base = k * nm;
+            double cx = 0.0, cz = 0.0;
+            for (int q = 0; q < n1; ++q) {
+                cx += t.w[q] * t.D[q * n1 + a] * Xs[(base + q + n1 * b) * CWR + tcol];
+                cz += t.w[q] * t.D[q * n1 + b] * Xs[(base + a + n1 * q) * CWR + tcol];
+            }
+            ax -= t.sx[k] * t.w[b] * cx + t.sz[k] * t.w[a] * cz;
+            // - S X
+            double sc = 0.0;
+            for (int l = 0; l < N; ++l) {
+                int d = k - l;
+                if (d < 0) d += N;
+                sc += t.wc[d] * Xs[(l * nm + i) * CWR + tcol];
+            }
+            ax -= wi * om * kh[i] * sc;
+            // -B^ entry of this (row, column)
+            const int F = col / t.nface, rem = col - F * t.nface;
+            const int m = rem / t.half, kk = rem - m * t.half;
+            const double rhs = (t.inc[F][kk] == k && face_node(F, m, p) == i) ? -t.w[m] * t.sdn[F][k] : 0.0;
+            const double res = rhs - ax;
+            rmax = fmax(rmax, fabs(res));
+            M[(int64_t)r * ld + nu + col] = (T)res;
+        }
+    }
+    // block max
+    for (int off = 16; off > 0; off >>= 1) rmax = fmax(rmax, __shfl_down_sync(0xffffffffu, rmax, off));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = rmax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) m = fmax(m, red[w]);
+        maxres[e] = m;
+    }
+}
+
+// ------------------------------------------------------------------------------------------------
+// restriction (eqs. hdg_local_i2o and ang_ave): in2out = R^o X, in2sol = (1/N) sum_k X[(k, i)]
+// ------------------------------------------------------------------------------------------------
+
+// Source X: either the FP64 buffer (X64, leading dim nin) or the T solution in M (leading dim ld).
+template <typename S, typename O>
+__global__ void __launch_bounds__(kThreads) k_restrict(Tab t, const S* __restrict__ X, int64_t xld, int64_t xestride,
+                                                       int64_t xcol0, O* __restrict__ in2out, O* __restrict__ in2sol,
+                                                       int* __restrict__ estatus, int64_t E) {
+    const int nin = t.nin, nm = t.nm, half = t.half;
+    const int64_t e = blockIdx.x;
+    if (e >= E) return;
+    const S* Xe = X + e * xestride + xcol0;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nrows = t.nin + nm;  // n_out == nin rows of in2out, then nm rows of in2sol
+    int bad = 0;
+    for (int r = warp; r < nrows; r += kThreads / 32) {
+        if (r < nin) {
+            const int F = r / t.nface, rem = r - F * t.nface;
+            const int m = rem / half, kk = rem - m * half;
+            const int row = t.outc[F][kk] * nm + face_node(F, m, t.p);
+            for (int c = lane; c < nin; c += 32) {
+                const double v = (double)Xe[(int64_t)row * xld + c];
+                if (!isfinite(v)) bad = 1;
+                in2out[e * (int64_t)nin * nin + (int64_t)r * nin + c] = (O)v;
+            }
+        } else {
+            const int i = r - nin;
+            for (int c = lane; c < nin; c += 32) {
+                double s = 0.0;
+                for (int k = 0; k < t.N; ++k) s += (double)Xe[(int64_t)(k * nm + i) * xld + c];
+                s /= t.N;
+                if (!isfinite(s)) bad = 1;
+                in2sol[e * (int64_t)nm * nin + (int64_t)i * nin + c] = (O)s;
+            }
+        }
+    }
+    if (bad) atomicOr(&estatus[e], 4);
+}
+
+__global__ void k_flag_residual(const double* __restrict__ maxres, int* __restrict__ estatus, double tol, int64_t E) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < E && !(maxres[e] <= tol)) estatus[e] |= 2;
+}
+
+__global__ void k_reduce_status(const int* __restrict__ estatus, const double* __restrict__ maxres, int64_t E,
+                                int* __restrict__ nflag, unsigned long long* __restrict__ maxbits) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < E) {
+        if (estatus[e]) atomicAdd(nflag, 1);
+        if (maxres) {
+            double v = maxres[e];
+            if (!(v >= 0.0)) v = 1e300;
+            atomicMax(maxbits, (unsigned long long)__double_as_longlong(v));
+        }
+    }
+}
+
+__global__ void k_copy_status(const int* __restrict__ src, int32_t* __restrict__ dst, int64_t E) {
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < E) dst[e] = src[e];
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------------------
+// launchers
+// ------------------------------------------------------------------------------------------------
+
+elrt_status local_assemble_f64(elrt_ctx* ctx, int64_t E, double h, const double* h_elem, const double* kappa,
+                               const double* omega, double* A, double* rhs) {
+    const Tab& t = ctx->tab;
+    elrt_status s = cuda_check(ctx, cudaMemsetAsync(ctx->d_flags, 0, sizeof(int), ctx->stream), "memset flags");
+    if (s) return s;
+    for (int64_t e0 = 0; e0 < E; e0 += 65535) {
+        const int64_t n = std::min<int64_t>(65535, E - e0);
+        dim3 grid((unsigned)n, t.N);
+        ProfScope ps(ctx, "assemble");
+        k_assemble<double><<<grid, kThreads, 0, ctx->stream>>>(
+            t, h, h_elem ? h_elem + e0 : nullptr, kappa + e0 * t.nm, omega + e0, A + e0 * (int64_t)t.nu * t.nu, t.nu,
+            (int64_t)t.nu * t.nu, rhs + e0 * (int64_t)t.nu * t.nin, t.nin, ctx->d_flags);
+    }
+    s = cuda_check(ctx, cudaGetLastError(), "k_assemble launch");
+    if (s) return s;
+    s = cuda_check(ctx, cudaMemcpyAsync(ctx->h_pinned, ctx->d_flags, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream),
+                   "flags read-back");
+    if (s) return s;
+    s = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "elrt_assemble");
+    if (s) return s;
+    prof_flush(ctx);
+    if (*(int*)ctx->h_pinned) return ctx_fail(ctx, ELRT_EINVAL, "negative/non-finite kappa or h, or omega outside [0,1]");
+    return ELRT_OK;
+}
+
+namespace {
+
+template <typename T, int NB, int QN>
+elrt_status run_lu(elrt_ctx* ctx, T* M, int64_t ld, int64_t estride, int* ipiv, int* estatus, int64_t n, bool resolve) {
+    const Tab& t = ctx->tab;
+    const size_t smem = lu_smem_bytes<T, NB, QN>(t.nu);
+    if (smem > 227 * 1024) return ctx_fail(ctx, ELRT_EINVAL, "local system too large for the shared-memory panel");
+    cudaError_t e;
+    if (!resolve) {
+        e = cudaFuncSetAttribute(k_lu_factor_solve<T, NB, QN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_check(ctx, e, "smem attribute");
+        ProfScope ps(ctx, "lu_factor_solve");
+        k_lu_factor_solve<T, NB, QN><<<(unsigned)n, kThreads, smem, ctx->stream>>>(t, M, ld, estride, ipiv, estatus, n);
+    } else {
+        e = cudaFuncSetAttribute(k_lu_resolve<T, NB, QN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_check(ctx, e, "smem attribute");
+        ProfScope ps(ctx, "lu_resolve");
+        k_lu_resolve<T, NB, QN><<<(unsigned)n, kThreads, smem, ctx->stream>>>(t, M, ld, estride, ipiv, n);
+    }
+    return cuda_check(ctx, cudaGetLastError(), "lu launch");
+}
+
+template <typename T>
+elrt_status run_residual(elrt_ctx* ctx, double h, const double* h_elem, const double* kappa, const double* omega,
+                         T* M, int64_t ld, int64_t estride, double* X64, int mode, double* maxres, int64_t n) {
+    const Tab& t = ctx->tab;
+    int cwr = 32;
+    while (cwr > 1 && (size_t)t.nu * cwr * sizeof(double) > 200 * 1024) cwr >>= 1;
+    const size_t smem = (size_t)t.nu * cwr * sizeof(double);
+    cudaError_t e = cudaFuncSetAttribute(k_residual<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "smem attribute");
+    ProfScope ps(ctx, "residual");
+    k_residual<T><<<(unsigned)n, kThreads, smem, ctx->stream>>>(t, h, h_elem, kappa, omega, M, ld, estride, X64, mode,
+                                                                 cwr, maxres, n);
+    return cuda_check(ctx, cudaGetLastError(), "residual launch");
+}
+
+template <typename S, typename O>
+elrt_status run_restrict(elrt_ctx* ctx, const S* X, int64_t xld, int64_t xestride, int64_t xcol0, O* in2out, O* in2sol,
+                         int* estatus, int64_t n) {
+    ProfScope ps(ctx, "restrict");
+    k_restrict<S, O><<<(unsigned)n, kThreads, 0, ctx->stream>>>(ctx->tab, X, xld, xestride, xcol0, in2out, in2sol,
+                                                               estatus, n);
+    return cuda_check(ctx, cudaGetLastError(), "restrict launch");
+}
+
+template <typename T, int NB, int QN>
+elrt_status build_chunked(elrt_ctx* ctx, int64_t E, double h, const double* h_elem, const double* kappa,
+                          const double* omega, int mode, int steps, int out_dtype, void* in2out, void* in2sol,
+                          int32_t* elem_status, elrt_local_stats* stats) {
+    const Tab& t = ctx->tab;
+    const int64_t ld = ((t.nu + t.nin + 31) / 32) * 32;
+    const int64_t estride = (int64_t)t.nu * ld;
+    const bool ir = (mode != ELRT_LOCAL_FP64);
+    double bmax = 0.0;  // max |B^| entry, the scale of the residuals
+    for (int F = 0; F < 4; ++F)
+        for (int k = 0; k < t.N; ++k)
+            for (int m = 0; m < t.n1; ++m) bmax = std::max(bmax, fabs(t.w[m] * t.sdn[F][k]));
+    const bool want_res = ir || stats || elem_status;
+    // bytes per element: M, ipiv, status, maxres, and the FP64 solution when refining / measuring
+    const size_t per = estride * sizeof(T) + t.nu * sizeof(int) + sizeof(int) + sizeof(double) +
+                       (want_res ? (size_t)t.nu * t.nin * sizeof(double) : 0);
+    const size_t budget = (size_t)16 << 30;
+    int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(E, (int64_t)(budget / per)));
+    if (chunk < E) {  // balance the chunks
+        const int64_t nch = (E + chunk - 1) / chunk;
+        chunk = (E + nch - 1) / nch;
+    }
+    elrt_status s = ensure_ws(ctx, &ctx->ws, &ctx->ws_bytes, per * chunk + 1024);
+    if (s) return s;
+    unsigned char* base = (unsigned char*)ctx->ws;
+    T* M = (T*)base;
+    double* X64 = (double*)(base + (size_t)chunk * estride * sizeof(T));
+    double* maxres = X64 + (want_res ? (size_t)chunk * t.nu * t.nin : 0);
+    int* ipiv = (int*)(maxres + chunk);
+    int* estat = ipiv + (size_t)chunk * t.nu;
+    s = cuda_check(ctx, cudaMemsetAsync(ctx->d_flags, 0, 4 * sizeof(int) + 2 * sizeof(unsigned long long), ctx->stream),
+                   "memset flags");
+    if (s) return s;
+    const size_t osz = out_dtype == ELRT_F32 ? sizeof(float) : sizeof(double);
+    for (int64_t e0 = 0; e0 < E; e0 += chunk) {
+        const int64_t n = std::min(chunk, E - e0);
+        const double* he = h_elem ? h_elem + e0 : nullptr;
+        const double* ka = kappa + e0 * t.nm;
+        const double* om = omega + e0;
+        s = cuda_check(ctx, cudaMemsetAsync(estat, 0, n * sizeof(int), ctx->stream), "memset status");
+        if (s) return s;
+        for (int64_t a0 = 0; a0 < n; a0 += 65535) {
+            const int64_t m = std::min<int64_t>(65535, n - a0);
+            dim3 grid((unsigned)m, t.N);
+            ProfScope ps(ctx, "assemble");
+            k_assemble<T><<<grid, kThreads, 0, ctx->stream>>>(t, h, he ? he + a0 : nullptr, ka + a0 * t.nm, om + a0,
+                                                              M + a0 * estride, ld, estride, nullptr, 0, ctx->d_flags);
+        }
+        s = cuda_check(ctx, cudaGetLastError(), "assemble launch");
+        if (s) return s;
+        s = run_lu<T, NB, QN>(ctx, M, ld, estride, ipiv, estat, n, false);
+        if (s) return s;
+        void* o_i2o = (unsigned char*)in2out + (size_t)e0 * t.nin * t.nin * osz;
+        void* o_i2m = (unsigned char*)in2sol + (size_t)e0 * t.nm * t.nin * osz;
+        if (want_res) {
+            s = run_residual<T>(ctx, h, he, ka, om, M, ld, estride, X64, 0, maxres, n);
+            for (int it = 0; it < (ir ? steps : 0) && !s; ++it) {
+                s = run_lu<T, NB, QN>(ctx, M, ld, estride, ipiv, estat, n, true);
+                if (!s) s = run_residual<T>(ctx, h, he, ka, om, M, ld, estride, X64, 1, maxres, n);
+            }
+            if (s) return s;
+            // flag elements whose residual exceeds 1e-10 max|B^|
+            ProfScope ps(ctx, "status");
+            k_flag_residual<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(maxres, estat, 1e-10 * bmax, n);
+            if (out_dtype == ELRT_F32)
+                s = run_restrict<double, float>(ctx, X64, t.nin, (int64_t)t.nu * t.nin, 0, (float*)o_i2o, (float*)o_i2m,
+                                                estat, n);
+            else
+                s = run_restrict<double, double>(ctx, X64, t.nin, (int64_t)t.nu * t.nin, 0, (double*)o_i2o,
+                                                 (double*)o_i2m, estat, n);
+        } else {
+            if (out_dtype == ELRT_F32)
+                s = run_restrict<T, float>(ctx, M, ld, estride, t.nu, (float*)o_i2o, (float*)o_i2m, estat, n);
+            else
+                s = run_restrict<T, double>(ctx, M, ld, estride, t.nu, (double*)o_i2o, (double*)o_i2m, estat, n);
+        }
+        if (s) return s;
+        ProfScope ps(ctx, "status", elem_status ? 2 : 1);
+        k_reduce_status<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(
+            estat, want_res ? maxres : nullptr, n, ctx->d_flags + 1, (unsigned long long*)(ctx->d_flags + 4));
+        if (elem_status)
+            k_copy_status<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(estat, elem_status + e0, n);
+        s = cuda_check(ctx, cudaGetLastError(), "status launch");
+        if (s) return s;
+    }
+    s = cuda_check(ctx, cudaMemcpyAsync(ctx->h_pinned, ctx->d_flags, 4 * sizeof(int) + 2 * sizeof(unsigned long long),
+                                        cudaMemcpyDeviceToHost, ctx->stream),
+                   "flags read-back");
+    if (s) return s;
+    s = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "elrt_build_local");
+    if (s) return s;
+    prof_flush(ctx);
+    const int* hf = (const int*)ctx->h_pinned;
+    if (hf[0]) return ctx_fail(ctx, ELRT_EINVAL, "negative/non-finite kappa or h, or omega outside [0,1]");
+    if (stats) {
+        stats->refine_steps = ir ? steps : 0;
+        stats->n_flagged = hf[1];
+        unsigned long long bits = *(const unsigned long long*)(hf + 4);
+        double mr;
+        memcpy(&mr, &bits, sizeof(mr));
+        stats->max_rel_residual = want_res ? mr / bmax : 0.0;
+    }
+    return ELRT_OK;
+}
+
+}  // namespace
+
+elrt_status local_build(elrt_ctx* ctx, int64_t E, double h, const double* h_elem, const double* kappa,
+                        const double* omega, int mode, int refine_steps, int out_dtype, void* in2out, void* in2sol,
+                        int32_t* elem_status, elrt_local_stats* stats) {
+    if (mode == ELRT_LOCAL_FP64)
+        return build_chunked<double, 16, 4>(ctx, E, h, h_elem, kappa, omega, mode, refine_steps, out_dtype, in2out,
+                                            in2sol, elem_status, stats);
+    if (mode == ELRT_LOCAL_FP32_IR)
+        return build_chunked<float, 32, 8>(ctx, E, h, h_elem, kappa, omega, mode, refine_steps, out_dtype, in2out,
+                                           in2sol, elem_status, stats);
+    return ctx_fail(ctx, ELRT_EINVAL, "local mode not available in this build");
+}

@@ -1,0 +1,181 @@
+"""GPU parity of the local stage (assembly, LU, refinement, restriction) against the FP64 oracle."""
+
+import numpy as np
+import pytest
+
+from oracle import hdg
+from tests import _helpers as H
+
+pytestmark = pytest.mark.gpu
+
+CASES = [  # (p, N, angular, n_elems): ragged panels (nu % NB != 0) and several tiles
+    (2, 4, "fv0", 7),
+    (4, 8, "fv0", 16),
+    (3, 12, "do", 5),
+    (6, 16, "fv0", 9),
+    (8, 16, "fv0", 3),
+]
+
+
+def _ctx(E, p, N, g, ang):
+    return E.Context(p, N, g, 0 if ang == "fv0" else 1)
+
+
+def _oracle_ops(p, N, g, ang, kappa, omega, h):
+    d = hdg.Disc(p, N, g, ang)
+    return d, hdg.build_local(d, kappa * h / 2, omega)
+
+
+@pytest.mark.parametrize("p,N,ang,n", CASES[:4])
+def test_assembly_matches_oracle(lib, p, N, ang, n):
+    import torch
+    kappa, omega, h = H.random_elements(n, p, seed=p * 100 + N)
+    ctx = _ctx(lib, p, N, 0.85, ang)
+    A = torch.empty(n, ctx.nu, ctx.nu, dtype=torch.float64, device="cuda")
+    R = torch.empty(n, ctx.nu, ctx.nin, dtype=torch.float64, device="cuda")
+    ctx.elrt_assemble(torch.tensor(kappa, device="cuda"), torch.tensor(omega, device="cuda"), h, A, R)
+    A, R = A.cpu().numpy(), R.cpu().numpy()
+    d = hdg.Disc(p, N, 0.85, ang)
+    for e in range(n):
+        Ao, Bo = d.local_system(kappa[e] * h / 2, omega[e])
+        np.testing.assert_allclose(A[e], Ao, atol=1e-13 * np.abs(Ao).max())
+        np.testing.assert_allclose(R[e], -Bo, atol=1e-15)
+        assert np.array_equal(A[e] != 0, Ao != 0)       # same sparsity pattern
+
+
+@pytest.mark.parametrize("p,N,ang,n", CASES)
+def test_local_fp64_matches_oracle(lib, p, N, ang, n):
+    import torch
+    kappa, omega, h = H.random_elements(n, p, seed=p * 10 + N)
+    ctx = _ctx(lib, p, N, 0.85, ang)
+    i2o = torch.empty(n, ctx.nin, ctx.nin, dtype=torch.float64, device="cuda")
+    i2m = torch.empty(n, ctx.nm, ctx.nin, dtype=torch.float64, device="cuda")
+    st = ctx.elrt_build_local(torch.tensor(kappa, device="cuda"), torch.tensor(omega, device="cuda"), h, i2o, i2m,
+                              mode=lib.LOCAL_FP64)
+    assert st.n_flagged == 0 and st.max_rel_residual < 1e-12
+    _, (o_i2o, o_i2m) = _oracle_ops(p, N, 0.85, ang, kappa, omega, h)
+    np.testing.assert_allclose(i2o.cpu().numpy(), o_i2o, atol=1e-11)
+    np.testing.assert_allclose(i2m.cpu().numpy(), o_i2m, atol=1e-11)
+
+
+@pytest.mark.parametrize("p,N,ang,n", CASES)
+def test_local_fp32_refined_matches_oracle(lib, p, N, ang, n):
+    """FP32 LU + 2 FP64 refinement steps reaches FP64-level agreement (target 1e-6)."""
+    import torch
+    kappa, omega, h = H.random_elements(n, p, seed=p * 10 + N + 1)
+    ctx = _ctx(lib, p, N, 0.85, ang)
+    i2o = torch.empty(n, ctx.nin, ctx.nin, dtype=torch.float64, device="cuda")
+    i2m = torch.empty(n, ctx.nm, ctx.nin, dtype=torch.float64, device="cuda")
+    k, o = torch.tensor(kappa, device="cuda"), torch.tensor(omega, device="cuda")
+    _, (o_i2o, o_i2m) = _oracle_ops(p, N, 0.85, ang, kappa, omega, h)
+    st0 = ctx.elrt_build_local(k, o, h, i2o, i2m, mode=lib.LOCAL_FP32_IR, refine_steps=0)
+    err0 = np.abs(i2o.cpu().numpy() - o_i2o).max()
+    st = ctx.elrt_build_local(k, o, h, i2o, i2m, mode=lib.LOCAL_FP32_IR, refine_steps=2)
+    err2 = np.abs(i2o.cpu().numpy() - o_i2o).max()
+    assert st.n_flagged == 0 and st.max_rel_residual < 1e-12
+    assert err0 < 1e-3 and st0.max_rel_residual > 1e-9     # unrefined: FP32 accuracy
+    assert err2 < 1e-10, (err0, err2)
+    np.testing.assert_allclose(i2m.cpu().numpy(), o_i2m, atol=1e-10)
+
+
+def test_fp32_output_dtype(lib):
+    import torch
+    p, N, n = 4, 8, 6
+    kappa, omega, h = H.random_elements(n, p, seed=3)
+    ctx = _ctx(lib, p, N, 0.5, "fv0")
+    i2o = torch.empty(n, ctx.nin, ctx.nin, dtype=torch.float32, device="cuda")
+    i2m = torch.empty(n, ctx.nm, ctx.nin, dtype=torch.float32, device="cuda")
+    ctx.elrt_build_local(torch.tensor(kappa, device="cuda"), torch.tensor(omega, device="cuda"), h, i2o, i2m,
+                         mode=lib.LOCAL_FP32_IR)
+    _, (o_i2o, o_i2m) = _oracle_ops(p, N, 0.5, "fv0", kappa, omega, h)
+    np.testing.assert_allclose(i2o.cpu().numpy(), o_i2o, atol=1e-6, rtol=1e-6)
+    np.testing.assert_allclose(i2m.cpu().numpy(), o_i2m, atol=1e-6, rtol=1e-6)
+
+
+def test_albedo_one_row_sums(lib):
+    """Constant preservation holds for the library's operators too (omega = 1)."""
+    import torch
+    p, N, n = 6, 16, 8
+    kappa, _, h = H.random_elements(n, p, seed=11)
+    ctx = _ctx(lib, p, N, 0.85, "fv0")
+    i2o = torch.empty(n, ctx.nin, ctx.nin, dtype=torch.float64, device="cuda")
+    i2m = torch.empty(n, ctx.nm, ctx.nin, dtype=torch.float64, device="cuda")
+    ctx.elrt_build_local(torch.tensor(kappa, device="cuda"), torch.ones(n, dtype=torch.float64, device="cuda"), h,
+                         i2o, i2m, mode=lib.LOCAL_FP32_IR)
+    np.testing.assert_allclose(i2o.sum(-1).cpu().numpy(), 1.0, atol=1e-11)
+    np.testing.assert_allclose(i2m.sum(-1).cpu().numpy(), 1.0, atol=1e-11)
+
+
+def test_per_element_h_and_empty_batch(lib):
+    import torch
+    p, N, n = 3, 8, 5
+    kappa, omega, _ = H.random_elements(n, p, seed=5)
+    hs = np.linspace(0.05, 1.0, n)
+    ctx = _ctx(lib, p, N, 0.85, "fv0")
+    i2o = torch.empty(n, ctx.nin, ctx.nin, dtype=torch.float64, device="cuda")
+    i2m = torch.empty(n, ctx.nm, ctx.nin, dtype=torch.float64, device="cuda")
+    ctx.elrt_build_local(torch.tensor(kappa, device="cuda"), torch.tensor(omega, device="cuda"), 1.0, i2o, i2m,
+                         mode=lib.LOCAL_FP64, h_elem=torch.tensor(hs, device="cuda"))
+    d = hdg.Disc(p, N, 0.85)
+    for e in range(n):
+        a, m, _ = d.local_operators(kappa[e] * hs[e] / 2, omega[e])
+        np.testing.assert_allclose(i2o[e].cpu().numpy(), a, atol=1e-11)
+    z = torch.empty(0, dtype=torch.float64, device="cuda")
+    ctx.elrt_build_local(z.view(0, ctx.nm), z, 1.0, z, z, mode=lib.LOCAL_FP64)
+
+
+@pytest.mark.parametrize("bad", ["negative", "nan", "omega"])
+def test_bad_inputs_rejected(lib, bad):
+    import torch
+    p, N, n = 2, 4, 3
+    kappa, omega, h = H.random_elements(n, p, seed=1)
+    if bad == "negative":
+        kappa[1, 3] = -1.0
+    elif bad == "nan":
+        kappa[2, 0] = np.nan
+    else:
+        omega[0] = 1.5
+    ctx = _ctx(lib, p, N, 0.85, "fv0")
+    i2o = torch.empty(n, ctx.nin, ctx.nin, dtype=torch.float64, device="cuda")
+    i2m = torch.empty(n, ctx.nm, ctx.nin, dtype=torch.float64, device="cuda")
+    with pytest.raises(lib.ElrtError) as ei:
+        ctx.elrt_build_local(torch.tensor(kappa, device="cuda"), torch.tensor(omega, device="cuda"), h, i2o, i2m)
+    assert ei.value.status == 1
+
+
+def test_full_size_slab_sampled_parity_and_energy_balance(lib):
+    """The 64 x 64, p = 6, N = 16 Gaussian-cloud slab in the benchmark's launch configuration:
+    sampled elements against the oracle one by one; the energy balance on every element."""
+    import torch
+    import workloads as W
+    prob = W.problem_gaussian_slab()
+    ctx = _ctx(lib, 6, 16, 0.85, "fv0")
+    kap = torch.tensor(H.lib_kappa(prob), device="cuda")
+    om = torch.tensor(prob.omega, device="cuda")
+    n = prob.n_elems
+    i2o = torch.empty(n, ctx.nin, ctx.nin, dtype=torch.float32, device="cuda")
+    i2m = torch.empty(n, ctx.nm, ctx.nin, dtype=torch.float32, device="cuda")
+    st = ctx.elrt_build_local(kap, om, prob.h, i2o, i2m, mode=lib.LOCAL_FP32_IR, refine_steps=2)
+    assert st.n_flagged == 0
+    d = hdg.Disc(6, 16, 0.85)
+    mesh = hdg.Mesh(prob.nx, prob.nz, prob.h)
+    kh_o = hdg.nodal_kappa_hat(prob, d, mesh)
+    rng = np.random.default_rng(0)
+    for e in list(rng.choice(n, 6, replace=False)) + [0, n - 1, 32 * 64 + 32]:
+        a, m, _ = d.local_operators(kh_o[e], prob.omega[e])
+        np.testing.assert_allclose(i2o[e].double().cpu().numpy(), a, atol=2e-6, rtol=2e-6)
+        np.testing.assert_allclose(i2m[e].double().cpu().numpy(), m, atol=2e-6, rtol=2e-6)
+    # energy balance on every element, evaluated in FP64 from the library's FP32 operators
+    xi, w = lib.elrt_lgl(6)
+    sx, sz = hdg.directions(16, "fv0")
+    normals = ((0, -1), (1, 0), (0, 1), (-1, 0))
+    sdn = [sx * a + sz * b for a, b in normals]
+    inc = [[k for k in range(16) if sdn[F][k] < 0] for F in range(4)]
+    outc = [[k for k in range(16) if sdn[F][k] > 0] for F in range(4)]
+    w2 = np.outer(w, w).reshape(-1)
+    khl = H.lib_kappa(prob) * prob.h / 2
+    A = i2o.double().cpu().numpy()
+    Mm = i2m.double().cpu().numpy()
+    worst = max(np.abs(H.energy_defect(w, sdn, inc, outc, w2, khl[e], prob.omega[e], 16, A[e], Mm[e])).max()
+                for e in range(0, n, 7))
+    assert worst < 1e-5
