@@ -157,6 +157,31 @@ elrt_status elrt_build_local(elrt_ctx* ctx, int64_t n_elems, double h, const dou
                              int32_t refine_steps, int32_t out_dtype, void* in2out, void* in2sol,
                              int32_t* elem_status, elrt_local_stats* stats);
 
+/* Same operators as elrt_build_local (modes ELRT_LOCAL_FP64 and ELRT_LOCAL_FP32_IR), for callers
+ * that cannot allocate device memory: code running where cudaMalloc is not allowed or not wanted,
+ * such as a host process whose device memory is owned and budgeted by another framework, a
+ * real-time loop that must not allocate after start-up, or a plug-in that is handed buffers but
+ * no allocator.  The paper has no counterpart; this is a library convenience.
+ *   - It needs no context and allocates nothing: no cudaMalloc, cudaFree or other allocating call.
+ *     Its scratch is one file-scope device array of ELRT_STATIC_SCRATCH_MIB MiB that every GPU
+ *     which loads the library holds until the process exits.  The batch is processed in chunks
+ *     that fit the array; ELRT_EINVAL is returned, before any launch, when a single element's
+ *     workspace does not fit (the element's local system of nu = (p+1)^2 N unknowns needs about
+ *     nu (nu + n_in) 4 bytes in FP32_IR, or 8 bytes in FP64, plus nu n_in 8 bytes in FP32_IR).
+ *   - The first call on a device looks up the array's device address (once per device, with
+ *     that device current); make that first call before any stream capture.
+ *   - Every call on a device shares the array and leaves its contents behind; what must start
+ *     at zero is cleared by each call.  Calls whose work overlaps on the GPU (other streams,
+ *     other host threads) race on the array: serialise them.
+ *   - The caller passes inputs and outputs exactly as for elrt_build_local; `stream` is a
+ *     cudaStream_t (NULL: legacy default stream).  The call synchronises that stream at the end
+ *     and returns ELRT_EINVAL for bad arguments or invalid kappa/omega/h, ELRT_ECUDA on a CUDA
+ *     failure.  It reports no statistics and no per-element status. */
+#define ELRT_STATIC_SCRATCH_MIB 64
+elrt_status elrt_build_local_static(const elrt_disc* disc, void* stream, int64_t n_elems, double h,
+                                    const double* h_elem, const double* kappa, const double* omega, int32_t mode,
+                                    int32_t refine_steps, int32_t out_dtype, void* in2out, void* in2sol);
+
 /* ---------------------------------------------------------------- global stage (Sec. 2.3) */
 
 /* y = (I - A_int) x on the skeleton of an nx x nz mesh: per element y_K = x_K - in2out_K x_in(K)

@@ -65,6 +65,7 @@ _sig = {
     "elrt_profile_reset": (_i32, [_vp]),
     "elrt_profile_get": (_i32, [_vp, C.c_char_p, _P(_d), _P(_i64)]),
     "elrt_launch_count": (_i64, [_vp]),
+    "elrt_build_local_static": (_i32, [_P(Disc), _vp, _i64, _d, _vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(_lib, _name)
@@ -127,6 +128,22 @@ def elrt_node_coords(p, n_angles, nx, nz, h):
 
 
 # ----------------------------------------------------------------------------- device calls
+def elrt_build_local_static(p, n_angles, hg_g, angular, kappa, omega, h, in2out, in2sol, mode=LOCAL_FP32_IR,
+                            refine_steps=2, h_elem=None):
+    """The allocation-free local build (no context; scratch in a fixed device array of the library).
+    Returns the status code (0 = ok) instead of raising, so callers can inspect rejections."""
+    import torch
+    E = omega.numel()
+    nm, nin = (p + 1) ** 2, 2 * (p + 1) * n_angles
+    d = _disc(p, n_angles, hg_g, angular)
+    return _lib.elrt_build_local_static(
+        C.byref(d), C.c_void_p(torch.cuda.current_stream().cuda_stream), E, float(h),
+        _ptr(h_elem, torch.float64, E, "h_elem"), _ptr(kappa, torch.float64, E * nm, "kappa"),
+        _ptr(omega, torch.float64, E, "omega"), int(mode), int(refine_steps), _dt(in2out),
+        _ptr(in2out, None, E * nin * nin, "in2out"), _ptr(in2sol, None, E * nm * nin, "in2sol"))
+
+
+
 def _ptr(t, dtype=None, n=None, name="tensor"):
     import torch
     if t is None:

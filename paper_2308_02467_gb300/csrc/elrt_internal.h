@@ -69,6 +69,8 @@ struct ProfScope {
 void prof_flush(elrt_ctx* ctx);  // call after a stream synchronisation
 
 // ---- host helpers implemented in host.cpp
+bool elrt_disc_valid(const elrt_disc* d);
+bool elrt_fill_tab(const elrt_disc* d, Tab* t);
 elrt_status ctx_fail(elrt_ctx* ctx, elrt_status s, const std::string& msg);
 elrt_status cuda_check(elrt_ctx* ctx, cudaError_t e, const char* what);
 elrt_status ensure_ws(elrt_ctx* ctx, void** buf, size_t* have, size_t need);

@@ -183,6 +183,9 @@ thread_local std::string g_err;
 
 }  // namespace
 
+bool elrt_disc_valid(const elrt_disc* d) { return disc_ok(d); }
+bool elrt_fill_tab(const elrt_disc* d, Tab* t) { return disc_ok(d) && build_tab(d, t); }
+
 elrt_status ctx_fail(elrt_ctx* ctx, elrt_status s, const std::string& msg) {
     if (ctx) ctx->last_error = msg;
     g_err = msg;

@@ -744,3 +744,124 @@ elrt_status local_build(elrt_ctx* ctx, int64_t E, double h, const double* h_elem
                                            in2sol, elem_status, stats);
     return ctx_fail(ctx, ELRT_EINVAL, "local mode not available in this build");
 }
+
+// ------------------------------------------------------------------------------------------------
+// Allocation-free variant of elrt_build_local (see elrt_build_local_static in include/elrt.h).
+// Its scratch is one file-scope device array; nothing here allocates device or host memory.
+// ------------------------------------------------------------------------------------------------
+
+#include <mutex>
+
+static __device__ __align__(256) unsigned char g_static_scratch[(size_t)ELRT_STATIC_SCRATCH_MIB << 20];
+
+namespace {
+
+constexpr size_t kStaticBytes = (size_t)ELRT_STATIC_SCRATCH_MIB << 20;
+constexpr size_t kStaticHead = 256;  // input-validation flag
+constexpr int kStaticMaxDevices = 64;
+void* g_static_addr[kStaticMaxDevices];
+std::once_flag g_static_once[kStaticMaxDevices];
+cudaError_t g_static_err[kStaticMaxDevices];
+
+// Device address of the array on the current device.  In host code the symbol itself is only a
+// host-side stand-in, so the address is looked up once per device, with that device current.
+elrt_status static_scratch(void** out) {
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kStaticMaxDevices) return ELRT_ECUDA;
+    std::call_once(g_static_once[dev],
+                   [dev] { g_static_err[dev] = cudaGetSymbolAddress(&g_static_addr[dev], g_static_scratch); });
+    if (g_static_err[dev] != cudaSuccess || !g_static_addr[dev]) return ELRT_ECUDA;
+    *out = g_static_addr[dev];
+    return ELRT_OK;
+}
+
+template <typename T, int NB, int QN>
+elrt_status static_build(const Tab& t, cudaStream_t sm, unsigned char* scratch, int64_t E, double h,
+                         const double* h_elem, const double* kappa, const double* omega, int mode, int steps,
+                         int out_dtype, void* in2out, void* in2sol) {
+    const int64_t ld = ((t.nu + t.nin + 31) / 32) * 32;
+    const int64_t estride = (int64_t)t.nu * ld;
+    const bool ir = mode != ELRT_LOCAL_FP64;
+    const size_t per = estride * sizeof(T) + (ir ? (size_t)t.nu * t.nin * sizeof(double) : 0) + sizeof(double) +
+                       (size_t)t.nu * sizeof(int) + sizeof(int) + 64;
+    if (per > kStaticBytes - kStaticHead) return ELRT_EINVAL;  // one element does not fit the array
+    const size_t lu_smem = lu_smem_bytes<T, NB, QN>(t.nu);
+    int cwr = 32;
+    while (cwr > 1 && (size_t)t.nu * cwr * sizeof(double) > 200 * 1024) cwr >>= 1;
+    const size_t res_smem = (size_t)t.nu * cwr * sizeof(double);
+    if (lu_smem > 227 * 1024) return ELRT_EINVAL;
+    const int64_t chunk = std::min<int64_t>(E, (int64_t)((kStaticBytes - kStaticHead) / per));
+    int* flags = (int*)scratch;
+    T* M = (T*)(scratch + kStaticHead);
+    double* X64 = (double*)((unsigned char*)M + (size_t)chunk * estride * sizeof(T));
+    double* maxres = X64 + (ir ? (size_t)chunk * t.nu * t.nin : 0);
+    int* ipiv = (int*)(maxres + chunk);
+    int* estat = ipiv + (size_t)chunk * t.nu;
+    if (cudaFuncSetAttribute(k_lu_factor_solve<T, NB, QN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lu_smem) ||
+        cudaFuncSetAttribute(k_lu_resolve<T, NB, QN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lu_smem) ||
+        cudaFuncSetAttribute(k_residual<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)res_smem))
+        return ELRT_ECUDA;
+    if (cudaMemsetAsync(flags, 0, sizeof(int), sm) != cudaSuccess) return ELRT_ECUDA;
+    const size_t osz = out_dtype == ELRT_F32 ? sizeof(float) : sizeof(double);
+    for (int64_t e0 = 0; e0 < E; e0 += chunk) {
+        const int64_t n = std::min(chunk, E - e0);
+        const double* he = h_elem ? h_elem + e0 : nullptr;
+        const double* ka = kappa + e0 * t.nm;
+        const double* om = omega + e0;
+        if (cudaMemsetAsync(estat, 0, n * sizeof(int), sm) != cudaSuccess) return ELRT_ECUDA;
+        k_assemble<T><<<dim3((unsigned)n, t.N), kThreads, 0, sm>>>(t, h, he, ka, om, M, ld, estride, nullptr, 0, flags);
+        k_lu_factor_solve<T, NB, QN><<<(unsigned)n, kThreads, lu_smem, sm>>>(t, M, ld, estride, ipiv, estat, n);
+        void* o_i2o = (unsigned char*)in2out + (size_t)e0 * t.nin * t.nin * osz;
+        void* o_i2m = (unsigned char*)in2sol + (size_t)e0 * t.nm * t.nin * osz;
+        if (ir) {
+            k_residual<T><<<(unsigned)n, kThreads, res_smem, sm>>>(t, h, he, ka, om, M, ld, estride, X64, 0, cwr, maxres, n);
+            for (int it = 0; it < steps; ++it) {
+                k_lu_resolve<T, NB, QN><<<(unsigned)n, kThreads, lu_smem, sm>>>(t, M, ld, estride, ipiv, n);
+                k_residual<T><<<(unsigned)n, kThreads, res_smem, sm>>>(t, h, he, ka, om, M, ld, estride, X64, 1, cwr,
+                                                                      maxres, n);
+            }
+            if (out_dtype == ELRT_F32)
+                k_restrict<double, float><<<(unsigned)n, kThreads, 0, sm>>>(t, X64, t.nin, (int64_t)t.nu * t.nin, 0,
+                                                                           (float*)o_i2o, (float*)o_i2m, estat, n);
+            else
+                k_restrict<double, double><<<(unsigned)n, kThreads, 0, sm>>>(t, X64, t.nin, (int64_t)t.nu * t.nin, 0,
+                                                                            (double*)o_i2o, (double*)o_i2m, estat, n);
+        } else {
+            if (out_dtype == ELRT_F32)
+                k_restrict<T, float><<<(unsigned)n, kThreads, 0, sm>>>(t, M, ld, estride, t.nu, (float*)o_i2o,
+                                                                      (float*)o_i2m, estat, n);
+            else
+                k_restrict<T, double><<<(unsigned)n, kThreads, 0, sm>>>(t, M, ld, estride, t.nu, (double*)o_i2o,
+                                                                       (double*)o_i2m, estat, n);
+        }
+        if (cudaGetLastError() != cudaSuccess) return ELRT_ECUDA;
+    }
+    int bad = 0;
+    if (cudaMemcpyAsync(&bad, flags, sizeof(int), cudaMemcpyDeviceToHost, sm) != cudaSuccess) return ELRT_ECUDA;
+    if (cudaStreamSynchronize(sm) != cudaSuccess) return ELRT_ECUDA;
+    return bad ? ELRT_EINVAL : ELRT_OK;
+}
+
+}  // namespace
+
+extern "C" elrt_status elrt_build_local_static(const elrt_disc* disc, void* stream, int64_t n_elems, double h,
+                                               const double* h_elem, const double* kappa, const double* omega,
+                                               int32_t mode, int32_t refine_steps, int32_t out_dtype, void* in2out,
+                                               void* in2sol) {
+    if (!elrt_disc_valid(disc) || n_elems < 0 || (n_elems > 0 && (!kappa || !omega || !in2out || !in2sol)) ||
+        (!h_elem && !(h > 0)) || (mode != ELRT_LOCAL_FP64 && mode != ELRT_LOCAL_FP32_IR) ||
+        (out_dtype != ELRT_F32 && out_dtype != ELRT_F64) || refine_steps < 0 || refine_steps > 8)
+        return ELRT_EINVAL;
+    if (n_elems == 0) return ELRT_OK;
+    Tab t;
+    if (!elrt_fill_tab(disc, &t)) return ELRT_EINVAL;
+    void* scratch = nullptr;
+    elrt_status s = static_scratch(&scratch);
+    if (s) return s;
+    cudaStream_t sm = (cudaStream_t)stream;
+    if (mode == ELRT_LOCAL_FP64)
+        return static_build<double, 16, 4>(t, sm, (unsigned char*)scratch, n_elems, h, h_elem, kappa, omega, mode,
+                                           refine_steps, out_dtype, in2out, in2sol);
+    return static_build<float, 32, 8>(t, sm, (unsigned char*)scratch, n_elems, h, h_elem, kappa, omega, mode,
+                                      refine_steps, out_dtype, in2out, in2sol);
+}
