@@ -23,7 +23,11 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-WORKLOAD = "gaussian-cloud slab 64x64 elements, p=6, N=16, g=0.85, albedo 0.99, beam 300 deg"
+def workload_name(nx):
+    return f"gaussian-cloud slab {nx}x{nx} elements, p=6, N=16, g=0.85, albedo 0.99, beam 300 deg"
+
+
+WORKLOAD = workload_name(64)
 
 
 def parse():
@@ -36,6 +40,7 @@ def parse():
     ap.add_argument("--refine", type=int, default=1)
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--nx", type=int, default=64, help="elements per side of the slab (64: the benchmark workload)")
     return ap.parse_args()
 
 
@@ -161,7 +166,7 @@ def run_ours(args, rank, world, local_rank):
     if dist:
         import torch.distributed as td
 
-    prob = W.problem_gaussian_slab()
+    prob = W.problem_gaussian_slab(n=args.nx)
     mode = E.LOCAL_FP32_IR if args.mode == "fp32ir" else E.LOCAL_FP64
     ctx = E.Context(prob.p, prob.n_angles, prob.hg_g, E.ANG_FV0)
     nx, nz, n = prob.nx, prob.nz, prob.n_elems
@@ -259,7 +264,7 @@ def run_ours(args, rank, world, local_rank):
         "value": val, "unit": "elements/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64" if args.mode == "fp32ir" else "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "elements": n, "p": prob.p, "n_angles": prob.n_angles,
+        "config": {"workload": workload_name(args.nx), "elements": n, "p": prob.p, "n_angles": prob.n_angles,
                    "local_mode": args.mode, "refine_steps": args.refine, "gmres_rtol": args.rtol, "gmres_restart": 50,
                    "operator_dtype": "f32", "parallelism": f"replicas x{world}",
                    "l2": "working set larger than L2 (in2out 822 MB, local workspace > 10 GB) on every step"},

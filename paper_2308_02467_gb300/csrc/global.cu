@@ -29,17 +29,34 @@ struct GmState {
     double tol;    // rtol * ||b||
 };
 
-__device__ __forceinline__ double dotp(float4 a, const double* x) {
-    return (double)a.x * x[0] + (double)a.y * x[1] + (double)a.z * x[2] + (double)a.w * x[3];
-}
-__device__ __forceinline__ double dotp(double2 a, const double* x) { return a.x * x[0] + a.y * x[1]; }
+// Float-float accumulation: GB300 issues FP32 at ~64x its FP64 rate, so the FP32 operator entries
+// are multiplied by x = xh + xl (two floats) with exact products (FMA gives the rounding error of
+// a * xh) and summed with Knuth's TwoSum; the pair (s, c) carries ~44 significant bits.
+struct FF {
+    float s, c;
+};
 
-template <typename A> struct Vec;
-template <> struct Vec<float> { typedef float4 T; static constexpr int W = 4; };
-template <> struct Vec<double> { typedef double2 T; static constexpr int W = 2; };
+__device__ __forceinline__ void ff_add_prod(FF& acc, float a, float xh, float xl) {
+    // explicit _rn operations: no contraction into FMAs may touch the error-free steps
+    const float p = __fmul_rn(a, xh);
+    const float e = fmaf(a, xh, -p);       // a * xh - p exactly
+    const float t = __fadd_rn(acc.s, p);
+    const float bp = __fsub_rn(t, acc.s);
+    const float err = __fadd_rn(__fsub_rn(acc.s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+    acc.s = t;
+    acc.c += err + e + a * xl;
+}
+
+__device__ __forceinline__ void ff_row(FF& acc, float4 a, const float* xh, const float* xl) {
+    ff_add_prod(acc, a.x, xh[0], xl[0]);
+    ff_add_prod(acc, a.y, xh[1], xl[1]);
+    ff_add_prod(acc, a.z, xh[2], xl[2]);
+    ff_add_prod(acc, a.w, xh[3], xl[3]);
+}
 
 // y_K = alpha * xself_K + beta * (Aop_K x_in(K)),  Aop_K: rows x nin (row-major),
 // x_in(K) gathered from x (neighbours' outflow, NULL: zero) and g (boundary data, NULL: zero).
+// FP32 operators: float-float accumulation; FP64 operators: FP64 accumulation.
 template <typename A>
 __global__ void __launch_bounds__(kThreads) k_elem_gemv(int nx, int nz, int nin, int nface, int rows,
                                                         const A* __restrict__ Aop, const double* __restrict__ x,
@@ -47,7 +64,9 @@ __global__ void __launch_bounds__(kThreads) k_elem_gemv(int nx, int nz, int nin,
                                                         double alpha, double beta, double* __restrict__ y,
                                                         const GmState* __restrict__ st) {
     if (st && st->done) return;
-    __shared__ __align__(16) double xin[4 * ELRT_MAX_N1 * (ELRT_MAX_ANG / 2)];
+    constexpr int kMaxIn = 4 * ELRT_MAX_N1 * (ELRT_MAX_ANG / 2);
+    __shared__ __align__(16) double xin[kMaxIn];
+    __shared__ __align__(16) float xinh[kMaxIn], xinl[kMaxIn];
     const int64_t e = blockIdx.x;
     const int ix = (int)(e % nx), iz = (int)(e / nx);
     for (int c = threadIdx.x; c < nin; c += kThreads) {
@@ -71,22 +90,40 @@ __global__ void __launch_bounds__(kThreads) k_elem_gemv(int nx, int nz, int nin,
             v = g[side0 + (int64_t)face * nface + off];
         }
         xin[c] = v;
+        const float vh = (float)v;
+        xinh[c] = vh;
+        xinl[c] = (float)(v - (double)vh);
     }
     __syncthreads();
-    typedef typename Vec<A>::T VT;
-    constexpr int W = Vec<A>::W;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nv = nin / W;
-    const VT* Ae = reinterpret_cast<const VT*>(Aop + e * (int64_t)rows * nin);
+    const A* Ae = Aop + e * (int64_t)rows * nin;
     for (int r = warp; r < rows; r += 2 * (kThreads / 32)) {
         const int r2 = r + kThreads / 32;
         double s1 = 0.0, s2 = 0.0;
-        for (int q = lane; q < nv; q += 32) {
-            const VT a1 = __ldcs(Ae + (int64_t)r * nv + q);
-            s1 += dotp(a1, xin + q * W);
-            if (r2 < rows) {
-                const VT a2 = __ldcs(Ae + (int64_t)r2 * nv + q);
-                s2 += dotp(a2, xin + q * W);
+        if constexpr (sizeof(A) == 4) {
+            const int nv = nin / 4;
+            const float4* A4 = reinterpret_cast<const float4*>(Ae);
+            FF a1{0.f, 0.f}, a2{0.f, 0.f};
+            for (int q = lane; q < nv; q += 32) {
+                const float4 v1 = __ldcs(A4 + (int64_t)r * nv + q);
+                ff_row(a1, v1, xinh + 4 * q, xinl + 4 * q);
+                if (r2 < rows) {
+                    const float4 v2 = __ldcs(A4 + (int64_t)r2 * nv + q);
+                    ff_row(a2, v2, xinh + 4 * q, xinl + 4 * q);
+                }
+            }
+            s1 = (double)a1.s + (double)a1.c;
+            s2 = (double)a2.s + (double)a2.c;
+        } else {
+            const int nv = nin / 2;
+            const double2* A2 = reinterpret_cast<const double2*>(Ae);
+            for (int q = lane; q < nv; q += 32) {
+                const double2 v1 = __ldcs(A2 + (int64_t)r * nv + q);
+                s1 += v1.x * xin[2 * q] + v1.y * xin[2 * q + 1];
+                if (r2 < rows) {
+                    const double2 v2 = __ldcs(A2 + (int64_t)r2 * nv + q);
+                    s2 += v2.x * xin[2 * q] + v2.y * xin[2 * q + 1];
+                }
             }
         }
 #pragma unroll
