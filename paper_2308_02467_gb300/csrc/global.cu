@@ -13,6 +13,7 @@
 #include <vector>
 
 #include "elrt_internal.h"
+#include "ff.h"
 
 namespace {
 
@@ -29,31 +30,6 @@ struct GmState {
     double tol;    // rtol * ||b||
 };
 
-// Float-float accumulation: GB300 issues FP32 at ~64x its FP64 rate, so the FP32 operator entries
-// are multiplied by x = xh + xl (two floats) with exact products (FMA gives the rounding error of
-// a * xh) and summed with Knuth's TwoSum; the pair (s, c) carries ~44 significant bits.
-struct FF {
-    float s, c;
-};
-
-__device__ __forceinline__ void ff_add_prod(FF& acc, float a, float xh, float xl) {
-    // explicit _rn operations: no contraction into FMAs may touch the error-free steps
-    const float p = __fmul_rn(a, xh);
-    const float e = fmaf(a, xh, -p);       // a * xh - p exactly
-    const float t = __fadd_rn(acc.s, p);
-    const float bp = __fsub_rn(t, acc.s);
-    const float err = __fadd_rn(__fsub_rn(acc.s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
-    acc.s = t;
-    acc.c += err + e + a * xl;
-}
-
-__device__ __forceinline__ void ff_row(FF& acc, float4 a, const float* xh, const float* xl) {
-    ff_add_prod(acc, a.x, xh[0], xl[0]);
-    ff_add_prod(acc, a.y, xh[1], xl[1]);
-    ff_add_prod(acc, a.z, xh[2], xl[2]);
-    ff_add_prod(acc, a.w, xh[3], xl[3]);
-}
-
 // y_K = alpha * xself_K + beta * (Aop_K x_in(K)),  Aop_K: rows x nin (row-major),
 // x_in(K) gathered from x (neighbours' outflow, NULL: zero) and g (boundary data, NULL: zero).
 // FP32 operators: float-float accumulation; FP64 operators: FP64 accumulation.
@@ -66,7 +42,7 @@ __global__ void __launch_bounds__(kThreads) k_elem_gemv(int nx, int nz, int nin,
     if (st && st->done) return;
     constexpr int kMaxIn = 4 * ELRT_MAX_N1 * (ELRT_MAX_ANG / 2);
     __shared__ __align__(16) double xin[kMaxIn];
-    __shared__ __align__(16) float xinh[kMaxIn], xinl[kMaxIn];
+    __shared__ __align__(16) ff xff[kMaxIn];
     const int64_t e = blockIdx.x;
     const int ix = (int)(e % nx), iz = (int)(e / nx);
     for (int c = threadIdx.x; c < nin; c += kThreads) {
@@ -90,9 +66,7 @@ __global__ void __launch_bounds__(kThreads) k_elem_gemv(int nx, int nz, int nin,
             v = g[side0 + (int64_t)face * nface + off];
         }
         xin[c] = v;
-        const float vh = (float)v;
-        xinh[c] = vh;
-        xinl[c] = (float)(v - (double)vh);
+        xff[c] = ff_from_double(v);
     }
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -101,19 +75,28 @@ __global__ void __launch_bounds__(kThreads) k_elem_gemv(int nx, int nz, int nin,
         const int r2 = r + kThreads / 32;
         double s1 = 0.0, s2 = 0.0;
         if constexpr (sizeof(A) == 4) {
+            // float-float: exact products of the FP32 entries with x = xh + xl, TwoSum accumulation
             const int nv = nin / 4;
             const float4* A4 = reinterpret_cast<const float4*>(Ae);
-            FF a1{0.f, 0.f}, a2{0.f, 0.f};
+            ff a1{0.f, 0.f}, a2{0.f, 0.f};
             for (int q = lane; q < nv; q += 32) {
                 const float4 v1 = __ldcs(A4 + (int64_t)r * nv + q);
-                ff_row(a1, v1, xinh + 4 * q, xinl + 4 * q);
+                ff_fma_f(a1, v1.x, xff[4 * q]);
+                ff_fma_f(a1, v1.y, xff[4 * q + 1]);
+                ff_fma_f(a1, v1.z, xff[4 * q + 2]);
+                ff_fma_f(a1, v1.w, xff[4 * q + 3]);
                 if (r2 < rows) {
                     const float4 v2 = __ldcs(A4 + (int64_t)r2 * nv + q);
-                    ff_row(a2, v2, xinh + 4 * q, xinl + 4 * q);
+                    ff_fma_f(a2, v2.x, xff[4 * q]);
+                    ff_fma_f(a2, v2.y, xff[4 * q + 1]);
+                    ff_fma_f(a2, v2.z, xff[4 * q + 2]);
+                    ff_fma_f(a2, v2.w, xff[4 * q + 3]);
                 }
             }
-            s1 = (double)a1.s + (double)a1.c;
-            s2 = (double)a2.s + (double)a2.c;
+            a1 = ff_warp_sum(ff_norm(a1.h, a1.l));
+            a2 = ff_warp_sum(ff_norm(a2.h, a2.l));
+            s1 = ff_to_double(a1);
+            s2 = ff_to_double(a2);
         } else {
             const int nv = nin / 2;
             const double2* A2 = reinterpret_cast<const double2*>(Ae);
@@ -125,11 +108,11 @@ __global__ void __launch_bounds__(kThreads) k_elem_gemv(int nx, int nz, int nin,
                     s2 += v2.x * xin[2 * q] + v2.y * xin[2 * q + 1];
                 }
             }
-        }
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            s1 += __shfl_down_sync(0xffffffffu, s1, off);
-            s2 += __shfl_down_sync(0xffffffffu, s2, off);
+            for (int off = 16; off > 0; off >>= 1) {
+                s1 += __shfl_down_sync(0xffffffffu, s1, off);
+                s2 += __shfl_down_sync(0xffffffffu, s2, off);
+            }
         }
         if (lane == 0) {
             const int64_t o1 = e * rows + r;

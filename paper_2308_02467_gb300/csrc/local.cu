@@ -17,6 +17,7 @@
 #include <algorithm>
 
 #include "elrt_internal.h"
+#include "ff.h"
 
 namespace {
 
@@ -402,7 +403,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_lu_resolve(Tab t, T* __restrict
 // ------------------------------------------------------------------------------------------------
 
 // mode 0: X64 = (double) src;  mode 1: X64 += (double) src.  Afterwards R -> src (as T).
-// One block per element; columns in chunks of CWR staged in shared memory.
+// One block per element; columns in chunks of CWR staged in shared memory as float-float pairs,
+// every product and sum in float-float (about 44 bits, at FP32 issue rate).
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_residual(Tab t, double h, const double* __restrict__ h_elem,
                                                        const double* __restrict__ kappa,
@@ -410,15 +412,38 @@ __global__ void __launch_bounds__(kThreads) k_residual(Tab t, double h, const do
                                                        int64_t ld, int64_t estride, double* __restrict__ X64all,
                                                        int mode, int CWR, double* __restrict__ maxres, int64_t E) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    double* Xs = reinterpret_cast<double*>(smem_raw);  // [nu][CWR]
-    __shared__ double kh[ELRT_MAX_N1 * ELRT_MAX_N1];
-    __shared__ double red[kThreads / 32];
     const int nu = t.nu, nin = t.nin, nm = t.nm, n1 = t.n1, N = t.N, p = t.p;
+    ff* Xs = reinterpret_cast<ff*>(smem_raw);  // [nu][CWR]
+    ff* dcoef = Xs + (size_t)nu * CWR;         // [nu]: B^k_ii + w_i kappa_hat_i
+    __shared__ ff wd[ELRT_MAX_N1 * ELRT_MAX_N1];      // w_q D[q][a]
+    __shared__ ff sxw[ELRT_MAX_ANG * ELRT_MAX_N1];    // sx_k w_b
+    __shared__ ff szw[ELRT_MAX_ANG * ELRT_MAX_N1];    // sz_k w_a
+    __shared__ ff wcf[ELRT_MAX_ANG];                  // circulant phase
+    __shared__ ff scoef[ELRT_MAX_N1 * ELRT_MAX_N1];   // w_i omega kappa_hat_i
+    __shared__ double red[kThreads / 32];
     const int64_t e = blockIdx.x;
     if (e >= E) return;
     const double he = h_elem ? h_elem[e] : h;
     const double om = omega[e];
-    for (int i = threadIdx.x; i < nm; i += kThreads) kh[i] = kappa[e * nm + i] * 0.5 * he;
+    for (int q = threadIdx.x; q < n1 * n1; q += kThreads) wd[q] = ff_from_double(t.w[q / n1] * t.D[q]);
+    for (int q = threadIdx.x; q < N * n1; q += kThreads) {
+        const int k = q / n1, b = q - k * n1;
+        sxw[q] = ff_from_double(t.sx[k] * t.w[b]);
+        szw[q] = ff_from_double(t.sz[k] * t.w[b]);
+    }
+    for (int q = threadIdx.x; q < N; q += kThreads) wcf[q] = ff_from_double(t.wc[q]);
+    for (int i = threadIdx.x; i < nm; i += kThreads)
+        scoef[i] = ff_from_double(t.w[i % n1] * t.w[i / n1] * om * kappa[e * nm + i] * 0.5 * he);
+    for (int r = threadIdx.x; r < nu; r += kThreads) {
+        const int k = r / nm, i = r - k * nm;
+        const int a = i % n1, b = i / n1;
+        double bd = 0.0;
+        if (b == 0 && t.sdn[0][k] > 0) bd += t.w[a] * t.sdn[0][k];
+        if (a == p && t.sdn[1][k] > 0) bd += t.w[b] * t.sdn[1][k];
+        if (b == p && t.sdn[2][k] > 0) bd += t.w[a] * t.sdn[2][k];
+        if (a == 0 && t.sdn[3][k] > 0) bd += t.w[b] * t.sdn[3][k];
+        dcoef[r] = ff_from_double(bd + t.w[a] * t.w[b] * kappa[e * nm + i] * 0.5 * he);
+    }
     T* M = Mall + e * estride;
     double* X64 = X64all + e * (int64_t)nu * nin;
     double rmax = 0.0;
@@ -434,7 +459,7 @@ __global__ void __launch_bounds__(kThreads) k_residual(Tab t, double h, const do
                 v = (mode == 0) ? d : X64[(int64_t)r * nin + col] + d;
                 X64[(int64_t)r * nin + col] = v;
             }
-            Xs[r * CWR + tcol] = v;
+            Xs[r * CWR + tcol] = ff_from_double(v);
         }
         __syncthreads();
         for (int r = trow; r < nu; r += rows_per_pass) {
@@ -442,35 +467,34 @@ __global__ void __launch_bounds__(kThreads) k_residual(Tab t, double h, const do
             if (col >= nin) continue;
             const int k = r / nm, i = r - k * nm;
             const int a = i % n1, b = i / n1;
-            const double wi = t.w[a] * t.w[b];
-            // (B + M) X
-            double bd = 0.0;
-            if (b == 0 && t.sdn[0][k] > 0) bd += t.w[a] * t.sdn[0][k];
-            if (a == p && t.sdn[1][k] > 0) bd += t.w[b] * t.sdn[1][k];
-            if (b == p && t.sdn[2][k] > 0) bd += t.w[a] * t.sdn[2][k];
-            if (a == 0 && t.sdn[3][k] > 0) bd += t.w[b] * t.sdn[3][k];
-            double ax = (bd + wi * kh[i]) * Xs[r * CWR + tcol];
-            // - C X: sum over the x-line and the z-line through node i
             const int base = k * nm;
-            double cx = 0.0, cz = 0.0;
+            // (B + M) X
+            ff acc = ff_mul(dcoef[r], Xs[r * CWR + tcol]);
+            // - C X along the x-line and the z-line through node i
+            ff tx{0.f, 0.f}, tz{0.f, 0.f};
             for (int q = 0; q < n1; ++q) {
-                cx += t.w[q] * t.D[q * n1 + a] * Xs[(base + q + n1 * b) * CWR + tcol];
-                cz += t.w[q] * t.D[q * n1 + b] * Xs[(base + a + n1 * q) * CWR + tcol];
+                ff_fma(tx, wd[q * n1 + a], Xs[(base + q + n1 * b) * CWR + tcol]);
+                ff_fma(tz, wd[q * n1 + b], Xs[(base + a + n1 * q) * CWR + tcol]);
             }
-            ax -= t.sx[k] * t.w[b] * cx + t.sz[k] * t.w[a] * cz;
+            tx = ff_norm(tx.h, tx.l);
+            tz = ff_norm(tz.h, tz.l);
+            ff cxz = ff_add(ff_mul(sxw[k * n1 + b], tx), ff_mul(szw[k * n1 + a], tz));
             // - S X
-            double sc = 0.0;
+            ff sc{0.f, 0.f};
             for (int l = 0; l < N; ++l) {
                 int d = k - l;
                 if (d < 0) d += N;
-                sc += t.wc[d] * Xs[(l * nm + i) * CWR + tcol];
+                ff_fma(sc, wcf[d], Xs[(l * nm + i) * CWR + tcol]);
             }
-            ax -= wi * om * kh[i] * sc;
+            sc = ff_norm(sc.h, sc.l);
+            ff s_term = ff_mul(scoef[i], sc);
+            acc = ff_add(acc, ff{-cxz.h, -cxz.l});
+            acc = ff_add(acc, ff{-s_term.h, -s_term.l});
             // -B^ entry of this (row, column)
             const int F = col / t.nface, rem = col - F * t.nface;
             const int m = rem / t.half, kk = rem - m * t.half;
             const double rhs = (t.inc[F][kk] == k && face_node(F, m, p) == i) ? -t.w[m] * t.sdn[F][k] : 0.0;
-            const double res = rhs - ax;
+            const double res = rhs - ff_to_double(acc);
             rmax = fmax(rmax, fabs(res));
             M[(int64_t)r * ld + nu + col] = (T)res;
         }
@@ -607,8 +631,8 @@ elrt_status run_residual(elrt_ctx* ctx, double h, const double* h_elem, const do
                          T* M, int64_t ld, int64_t estride, double* X64, int mode, double* maxres, int64_t n) {
     const Tab& t = ctx->tab;
     int cwr = 32;
-    while (cwr > 1 && (size_t)t.nu * cwr * sizeof(double) > 200 * 1024) cwr >>= 1;
-    const size_t smem = (size_t)t.nu * cwr * sizeof(double);
+    while (cwr > 1 && (size_t)t.nu * (cwr + 1) * sizeof(double) > 212 * 1024) cwr >>= 1;
+    const size_t smem = (size_t)t.nu * (cwr + 1) * sizeof(double);
     cudaError_t e = cudaFuncSetAttribute(k_residual<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_check(ctx, e, "smem attribute");
     ProfScope ps(ctx, "residual");
@@ -787,8 +811,8 @@ elrt_status static_build(const Tab& t, cudaStream_t sm, unsigned char* scratch, 
     if (per > kStaticBytes - kStaticHead) return ELRT_EINVAL;  // one element does not fit the array
     const size_t lu_smem = lu_smem_bytes<T, NB, QN>(t.nu);
     int cwr = 32;
-    while (cwr > 1 && (size_t)t.nu * cwr * sizeof(double) > 200 * 1024) cwr >>= 1;
-    const size_t res_smem = (size_t)t.nu * cwr * sizeof(double);
+    while (cwr > 1 && (size_t)t.nu * (cwr + 1) * sizeof(double) > 212 * 1024) cwr >>= 1;
+    const size_t res_smem = (size_t)t.nu * (cwr + 1) * sizeof(double);
     if (lu_smem > 227 * 1024) return ELRT_EINVAL;
     const int64_t chunk = std::min<int64_t>(E, (int64_t)((kStaticBytes - kStaticHead) / per));
     int* flags = (int*)scratch;
