@@ -29,6 +29,10 @@ def workload_name(nx):
 
 WORKLOAD = workload_name(64)
 
+# DRAM bytes (read + write) per element of k_lu_factor_solve<float> from one ncu capture
+# (profiles/k_lu_factor_solve_slab16.md); valid while that kernel is unchanged.
+LU_DRAM_BYTES_PER_ELEMENT = (8.189778e9 + 8.537462e9) / 256
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -272,7 +276,10 @@ def run_ours(args, rank, world, local_rank):
         "gmres_iterations": gst.iterations, "gmres_rel_residual": gst.rel_residual,
         "local_max_rel_residual": lst.max_rel_residual, "local_flagged": lst.n_flagged,
         "roofline": {"kernel": "lu_factor_solve", "bound": "alu", "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None, "traffic": None,
+                     "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
+                     "traffic": (LU_DRAM_BYTES_PER_ELEMENT * per_launch) if args.mode == "fp32ir" else None,
+                     "traffic_source": "ncu dram bytes of k_lu_factor_solve on the 16x16 slab (65.3 MB per element, "
+                                       "profiles/k_lu_factor_solve_slab16.md) x elements per launch",
                      "peak_source": peak_note, "flop_per_element": flop_el, "elements_per_launch": per_launch,
                      "avg_launch_ms": lu_ms / lu_n if lu_n else None, "share_of_timed_kernels": lu_ms / total_prof},
         "gpu_launches": launches,
