@@ -206,6 +206,86 @@ elrt_status elrt_solve_global(elrt_ctx* ctx, int32_t nx, int32_t nz, const void*
 elrt_status elrt_recover_mean(elrt_ctx* ctx, int32_t nx, int32_t nz, const void* in2sol, int32_t dtype,
                               const double* skeleton, const double* inflow, double* mean);
 
+/* ---------------------------------------------------------------- element network (Sec. 2.4) */
+
+/* The learned local solver of eq. param2sol: a fully connected network (Sec. 2.4.1)
+ *     x_0 -> x_i = f(A_i x_{i-1} + b_i), i = 1..n_hidden (width units, f = GELU or ELU),
+ *     output = A_out x_{n_hidden} + b_out  (linear),
+ * mapping an element's coefficients to its (in2out, in2sol) = (A_i2o, A_i2m).  Input x_0: the
+ * standardised log kappa_hat at the (p+1)^2 nodes and the standardised albedo (Sec. 2.4.1 with
+ * sigma_s = omega sigma_e: one coefficient field plus the albedo), zero-padded to a multiple of
+ * 64.  Output: the 2(p+1)N x 2(p+1)N in2out entries then the (p+1)^2 x 2(p+1)N in2sol entries,
+ * each standardised by its training-set mean and standard deviation.  Weights are FP32 masters
+ * with BF16 copies; every GEMM runs on tcgen05 (BF16 in, FP32 accumulate); training minimises the
+ * mean absolute error with Adam (Sec. 3.1).  All calls are asynchronous on the network's stream
+ * unless stated. */
+typedef struct elrt_net elrt_net;
+
+typedef struct {
+    int32_t p;            /* element discretisation the network is built for */
+    int32_t n_angles;
+    int32_t n_hidden;     /* hidden layers (0 = linear regression), <= 8 */
+    int32_t width;        /* hidden width, a multiple of 64 */
+    int32_t activation;   /* 0 GELU, 1 ELU */
+    uint64_t seed;        /* initial weights: uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) from this seed */
+} elrt_net_desc;
+
+typedef struct {
+    int32_t epochs;
+    int32_t batch;        /* a multiple of 64 */
+    float lr;             /* Adam step size; divided by 10 after each third of the epochs */
+    float beta1, beta2, eps;
+    uint64_t seed;        /* sample order */
+} elrt_train_opts;
+
+elrt_status elrt_net_create(elrt_net** net, const elrt_net_desc* desc, void* stream);
+elrt_status elrt_net_destroy(elrt_net* net);
+elrt_status elrt_net_set_stream(elrt_net* net, void* stream);
+const char* elrt_net_last_error(const elrt_net* net);
+/* sizes: number of inputs before padding, padded input width, outputs, layers (hidden + 1), parameters */
+elrt_status elrt_net_sizes(const elrt_net* net, int64_t* n_feat, int64_t* n_feat_pad, int64_t* n_out,
+                           int32_t* n_layers, int64_t* n_params);
+
+/* Host copies of layer l's parameters (l = 0 .. n_hidden; W is [out][in_pad] row-major):
+ * what = 0 W, 1 b, 2 dW (last gradient), 3 db; dir = 0 read into host buf, 1 write from it (W, b).
+ * Synchronises. */
+elrt_status elrt_net_params(elrt_net* net, int32_t layer, int32_t what, int32_t dir, float* host_buf);
+
+/* Raw network on standardised features: x device [n][n_feat_pad] FP32 (rounded to BF16 on the
+ * way in), y device [n][n_out] FP32 standardised outputs. */
+elrt_status elrt_net_forward(elrt_net* net, int64_t n, const float* x, float* y);
+
+/* One training step on a batch of n (a multiple of 64) standardised samples: forward, mean
+ * absolute error against t (device [n][n_out] FP32), backward into the gradient buffers, and,
+ * if lr > 0, an Adam update (step counter advanced).  loss (host, may be NULL) gets the batch
+ * MAE; synchronises when loss is given. */
+elrt_status elrt_net_train_step(elrt_net* net, int64_t n, const float* x, const float* t, float lr, float* loss);
+
+/* Training from physical data: kappa device [n][(p+1)^2] (km^-1 at the LGL nodes), omega [n],
+ * h_elem [n] (element sides, km), labels in2out [n][n_in][n_in] and in2sol [n][(p+1)^2][n_in]
+ * (FP32, e.g. from elrt_build_local).  Computes the input and output standardisation from this
+ * set, then runs opts->epochs epochs of shuffled mini-batches.  epoch_loss (host, may be NULL)
+ * receives the mean batch MAE of every epoch.  Synchronises. */
+elrt_status elrt_net_fit(elrt_net* net, int64_t n, const double* kappa, const double* omega, const double* h_elem,
+                         const float* in2out, const float* in2sol, const elrt_train_opts* opts, float* epoch_loss);
+
+/* Learned in2out / in2sol (FP32, layouts as elrt_build_local) of n elements with side h (or
+ * per-element h_elem).  ELRT_ENOTRAINED if the network has no standardisation yet. */
+elrt_status elrt_net_infer(elrt_net* net, int64_t n, double h, const double* h_elem, const double* kappa,
+                           const double* omega, float* in2out, float* in2sol);
+
+/* Learned local stage with classical fallback (Sec. 2.4 with the error indicator of the survey
+ * reading A10): network inference, then the per-element energy-balance defect
+ *     max_j | w_j |s.n|_j - sum_r w_r (s.n)_r A_i2o[r, j] - N sum_i w_i kappa_hat_i (1 - omega) A_i2m[i, j] |
+ *           / (w_j |s.n|_j)
+ * (exactly 0 for the classical operators), and the classical FP32-IR solve for every element whose
+ * defect exceeds tol.  estimate (device [n] FP32, may be NULL) receives the defects; n_fallback
+ * (host, may be NULL) the number of re-solved elements.  ctx and net must share (p, N).
+ * Synchronises. */
+elrt_status elrt_build_local_learned(elrt_ctx* ctx, elrt_net* net, int64_t n, double h, const double* h_elem,
+                                     const double* kappa, const double* omega, double tol, float* in2out,
+                                     float* in2sol, float* estimate, int64_t* n_fallback);
+
 #ifdef __cplusplus
 }
 #endif

@@ -35,6 +35,16 @@ class SolveStats(C.Structure):
                 ("rel_residual", C.c_double)]
 
 
+class NetDesc(C.Structure):
+    _fields_ = [("p", C.c_int32), ("n_angles", C.c_int32), ("n_hidden", C.c_int32), ("width", C.c_int32),
+                ("activation", C.c_int32), ("seed", C.c_uint64)]
+
+
+class TrainOpts(C.Structure):
+    _fields_ = [("epochs", C.c_int32), ("batch", C.c_int32), ("lr", C.c_float), ("beta1", C.c_float),
+                ("beta2", C.c_float), ("eps", C.c_float), ("seed", C.c_uint64)]
+
+
 class ElrtError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -66,6 +76,17 @@ _sig = {
     "elrt_profile_get": (_i32, [_vp, C.c_char_p, _P(_d), _P(_i64)]),
     "elrt_launch_count": (_i64, [_vp]),
     "elrt_build_local_static": (_i32, [_P(Disc), _vp, _i64, _d, _vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp]),
+    "elrt_net_create": (_i32, [_P(_vp), _P(NetDesc), _vp]),
+    "elrt_net_destroy": (_i32, [_vp]),
+    "elrt_net_set_stream": (_i32, [_vp, _vp]),
+    "elrt_net_last_error": (C.c_char_p, [_vp]),
+    "elrt_net_sizes": (_i32, [_vp, _P(_i64), _P(_i64), _P(_i64), _P(_i32), _P(_i64)]),
+    "elrt_net_params": (_i32, [_vp, _i32, _i32, _i32, _vp]),
+    "elrt_net_forward": (_i32, [_vp, _i64, _vp, _vp]),
+    "elrt_net_train_step": (_i32, [_vp, _i64, _vp, _vp, C.c_float, _P(C.c_float)]),
+    "elrt_net_fit": (_i32, [_vp, _i64, _vp, _vp, _vp, _vp, _vp, _P(TrainOpts), _vp]),
+    "elrt_net_infer": (_i32, [_vp, _i64, _d, _vp, _vp, _vp, _vp, _vp]),
+    "elrt_build_local_learned": (_i32, [_vp, _vp, _i64, _d, _vp, _vp, _vp, _d, _vp, _vp, _vp, _P(_i64)]),
 }
 for _name, (_res, _args) in _sig.items():
     _f = getattr(_lib, _name)
@@ -272,3 +293,115 @@ class Context:
                                       _dt(in2sol), _ptr(skeleton, torch.float64, E * self.nin, "skeleton"),
                                       _ptr(inflow, torch.float64, None, "inflow"),
                                       _ptr(mean, torch.float64, E * self.nm, "mean")), self._h)
+
+
+def _net_check(status, h):
+    if status != 0:
+        msg = _lib.elrt_net_last_error(h)
+        raise ElrtError(status, msg.decode() if msg else "")
+
+
+class Net:
+    """An elrt_net: the element network of Sec. 2.4.1 (calls run on the current torch stream)."""
+
+    def __init__(self, p, n_angles, n_hidden=4, width=1024, activation="gelu", seed=0):
+        import torch
+        d = NetDesc(p, n_angles, n_hidden, width, 0 if activation == "gelu" else 1, seed)
+        h = C.c_void_p()
+        _check(_lib.elrt_net_create(C.byref(h), C.byref(d), C.c_void_p(torch.cuda.current_stream().cuda_stream)))
+        self._h = h
+        a, b, c, nl, npar = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int32(), C.c_int64()
+        _lib.elrt_net_sizes(h, C.byref(a), C.byref(b), C.byref(c), C.byref(nl), C.byref(npar))
+        self.n_feat, self.n_feat_pad, self.n_out, self.n_layers, self.n_params = a.value, b.value, c.value, nl.value, npar.value
+        self.p, self.n_angles, self.width = p, n_angles, width
+        self.nm = (p + 1) ** 2
+        self.nin = 2 * (p + 1) * n_angles
+
+    def _s(self):
+        import torch
+        _lib.elrt_net_set_stream(self._h, C.c_void_p(torch.cuda.current_stream().cuda_stream))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.elrt_net_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def layer_shape(self, l):
+        out = self.n_out if l == self.n_layers - 1 else self.width
+        inp = self.n_feat_pad if l == 0 else self.width
+        return out, inp
+
+    def elrt_net_params(self, layer, what, value=None):
+        """what: 'W', 'b', 'dW', 'db'.  Returns a host array, or writes `value` (W, b)."""
+        code = {"W": 0, "b": 1, "dW": 2, "db": 3}[what]
+        out, inp = self.layer_shape(layer)
+        shape = (out, inp) if code in (0, 2) else (out,)
+        if value is None:
+            buf = np.zeros(shape, dtype=np.float32)
+            _net_check(_lib.elrt_net_params(self._h, layer, code, 0, buf.ctypes.data), self._h)
+            return buf
+        buf = np.ascontiguousarray(np.asarray(value, dtype=np.float32).reshape(shape))
+        _net_check(_lib.elrt_net_params(self._h, layer, code, 1, buf.ctypes.data), self._h)
+
+    def elrt_net_forward(self, x, y):
+        import torch
+        self._s()
+        n = x.shape[0]
+        _net_check(_lib.elrt_net_forward(self._h, n, _ptr(x, torch.float32, n * self.n_feat_pad, "x"),
+                                         _ptr(y, torch.float32, n * self.n_out, "y")), self._h)
+
+    def elrt_net_train_step(self, x, t, lr=0.0):
+        import torch
+        self._s()
+        n = x.shape[0]
+        loss = C.c_float()
+        _net_check(_lib.elrt_net_train_step(self._h, n, _ptr(x, torch.float32, n * self.n_feat_pad, "x"),
+                                            _ptr(t, torch.float32, n * self.n_out, "t"), float(lr), C.byref(loss)),
+                   self._h)
+        return loss.value
+
+    def elrt_net_fit(self, kappa, omega, h_elem, in2out, in2sol, epochs, batch, lr=1e-3, seed=0):
+        import torch
+        self._s()
+        n = omega.numel()
+        o = TrainOpts(epochs, batch, lr, 0.9, 0.999, 1e-8, seed)
+        losses = np.zeros(epochs, dtype=np.float32)
+        _net_check(_lib.elrt_net_fit(self._h, n, _ptr(kappa, torch.float64, n * self.nm, "kappa"),
+                                     _ptr(omega, torch.float64, n, "omega"), _ptr(h_elem, torch.float64, n, "h_elem"),
+                                     _ptr(in2out, torch.float32, n * self.nin * self.nin, "in2out"),
+                                     _ptr(in2sol, torch.float32, n * self.nm * self.nin, "in2sol"), C.byref(o),
+                                     losses.ctypes.data), self._h)
+        return losses
+
+    def elrt_net_infer(self, kappa, omega, h, in2out, in2sol, h_elem=None):
+        import torch
+        self._s()
+        n = omega.numel()
+        _net_check(_lib.elrt_net_infer(self._h, n, float(h), _ptr(h_elem, torch.float64, n, "h_elem"),
+                                       _ptr(kappa, torch.float64, n * self.nm, "kappa"),
+                                       _ptr(omega, torch.float64, n, "omega"),
+                                       _ptr(in2out, torch.float32, n * self.nin * self.nin, "in2out"),
+                                       _ptr(in2sol, torch.float32, n * self.nm * self.nin, "in2sol")), self._h)
+
+
+def elrt_build_local_learned(ctx, net, kappa, omega, h, in2out, in2sol, tol=1e-3, h_elem=None, estimate=None):
+    """Learned operators with the energy-balance estimate and classical fallback; returns the
+    number of elements re-solved classically."""
+    import torch
+    ctx._sync_stream()
+    net._s()
+    n = omega.numel()
+    nf = C.c_int64()
+    _check(_lib.elrt_build_local_learned(
+        ctx._h, net._h, n, float(h), _ptr(h_elem, torch.float64, n, "h_elem"),
+        _ptr(kappa, torch.float64, n * ctx.nm, "kappa"), _ptr(omega, torch.float64, n, "omega"), float(tol),
+        _ptr(in2out, torch.float32, n * ctx.nin * ctx.nin, "in2out"),
+        _ptr(in2sol, torch.float32, n * ctx.nm * ctx.nin, "in2sol"),
+        _ptr(estimate, torch.float32, n, "estimate"), C.byref(nf)), ctx._h)
+    return nf.value

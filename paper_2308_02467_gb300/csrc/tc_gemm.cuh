@@ -1,0 +1,329 @@
+// tcgen05 / TMEM / TMA building blocks and a BF16 GEMM with fused epilogues for sm_103a.
+//
+//   D[M][N] = A[M][K] . B[N][K]^T      (A, B bf16, K contiguous; FP32 accumulation in TMEM)
+//
+// One CTA computes one BM x BN tile: warp 0 issues TMA loads of A and B k-blocks (BK = 64 bf16 =
+// 128 bytes per row, 128-byte swizzle) into a STAGES-deep ring guarded by mbarriers; warp 1
+// allocates BN TMEM columns and, from one elected lane, issues tcgen05.mma (M = 128, N = BN,
+// K = 16 per instruction) and tcgen05.commit to free each stage; warps 2-5 wait for the final
+// commit, read the accumulator with tcgen05.ld (warp w owns TMEM lanes 32 (w % 4) .. + 31) and
+// run the epilogue.  Every wait is bounded (about 2 s of clock64); on timeout the kernel records
+// an error code, stops issuing work, waits (bounded) for its own copies in flight, frees its TMEM
+// and returns.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tc {
+
+constexpr int BM = 128;
+constexpr int BK = 64;
+constexpr int kGemmThreads = 192;
+constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait for phase `parity`; false on timeout or when *abort is set.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*abort) return false;
+        if (clock64() - t0 > kWaitCycles) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(const CUtensorMap* map, uint64_t* bar, void* dst, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst_smem, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst_smem)),
+                 "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of 128 bytes,
+// 8-row groups 1024 bytes apart (tile base 1024-byte aligned).
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);  // start address
+    d |= (uint64_t)1 << 16;                    // leading byte offset (unused with this swizzle)
+    d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset between 8-row groups
+    d |= (uint64_t)1 << 46;                    // descriptor version
+    d |= (uint64_t)2 << 61;                    // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor, kind::f16: BF16 A and B (K-major), FP32 D, shape M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+// ------------------------------------------------------------------------------------------------
+// GEMM with fused epilogues
+// ------------------------------------------------------------------------------------------------
+
+enum Epi : int {
+    EPI_F32 = 0,        // out_f[m][n] = acc                                  (weight gradients)
+    EPI_BIAS_ACT = 1,   // z = acc + bias; h = act(z): out_bf (h), z_out (z), out_bf_t (h^T)
+    EPI_OUTPUT = 2,     // y = (acc + bias) * col_std + col_mean -> out_f (n < split) / out_f2 (n >= split)
+    EPI_LOSS = 3,       // y = acc + bias; d = sign(y - t) * scale -> out_bf, out_bf_t; loss += |y - t|
+    EPI_DACT = 4,       // d = acc * act'(z_in): out_bf, out_bf_t
+};
+
+struct EpiArgs {
+    const float* bias = nullptr;           // [N]
+    __nv_bfloat16* out_bf = nullptr;       // [M][ld_out]
+    __nv_bfloat16* out_bf_t = nullptr;     // [N][ld_t]
+    __nv_bfloat16* z_out = nullptr;        // [M][ld_out]
+    const __nv_bfloat16* z_in = nullptr;   // [M][ld_out]
+    float* out_f = nullptr;                // [M][ld_out] (EPI_F32, EPI_OUTPUT n < split)
+    float* out_f2 = nullptr;               // [M][ld_out2] (EPI_OUTPUT n >= split)
+    const float* col_mean = nullptr;
+    const float* col_std = nullptr;
+    const float* target = nullptr;         // [M][ld_out] standardised targets
+    float* loss_acc = nullptr;             // one float
+    float loss_scale = 0.f;
+    int split = 0;
+    int ld_out = 0, ld_out2 = 0, ld_t = 0;
+    int act = 0;                           // 0 GELU (exact, erf), 1 ELU
+    int* err = nullptr;
+};
+
+__device__ __forceinline__ float act_f(float z, int act) {
+    if (act == 0) return 0.5f * z * (1.f + erff(z * 0.70710678118654752f));
+    return z > 0.f ? z : expm1f(z);
+}
+__device__ __forceinline__ float act_df(float z, int act) {
+    if (act == 0) return 0.5f * (1.f + erff(z * 0.70710678118654752f)) + z * 0.39894228040143268f * expf(-0.5f * z * z);
+    return z > 0.f ? 1.f : expf(z);
+}
+
+template <int BN>
+struct GemmSmem {
+    static constexpr int STAGES = BN == 256 ? 4 : 6;
+    static constexpr int A_BYTES = BM * BK * 2;
+    static constexpr int B_BYTES = BN * BK * 2;
+    static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+    static constexpr int TOTAL = STAGES * STAGE_BYTES + 1024 /*alignment*/ + 256 /*barriers*/;
+};
+
+template <int BN>
+__global__ void __launch_bounds__(kGemmThreads, 1)
+    k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N, int K,
+                int mode, EpiArgs ep) {
+    using S = GemmSmem<BN>;
+    extern __shared__ __align__(1024) unsigned char gsm_raw[];
+    unsigned char* base = (unsigned char*)(((uintptr_t)gsm_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char* As = base;
+    unsigned char* Bs = base + S::STAGES * S::A_BYTES;
+    uint64_t* full = (uint64_t*)(base + S::STAGES * S::STAGE_BYTES);
+    uint64_t* empty = full + S::STAGES;
+    uint64_t* accb = empty + S::STAGES;
+    uint32_t* tmem_slot = (uint32_t*)(accb + 1);
+    volatile int* abort = (volatile int*)(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const int nk = (K + BK - 1) / BK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < S::STAGES; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(accb, 1);
+        *abort = 0;
+        fence_barrier_init();
+    }
+    if (warp == 1) {
+        tmem_alloc(tmem_slot, BN);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem_d = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // TMA producer
+        int issued = 0;
+        for (int kb = 0; kb < nk; ++kb) {
+            const int s = kb % S::STAGES;
+            const uint32_t ph = (kb / S::STAGES) & 1;
+            if (!mbar_wait(&empty[s], ph ^ 1, abort)) {
+                if (ep.err) atomicOr(ep.err, 1);
+                *abort = 1;
+                break;
+            }
+            mbar_expect_tx(&full[s], S::STAGE_BYTES);
+            tma_load_2d(&tmA, &full[s], As + s * S::A_BYTES, kb * BK, m0);
+            tma_load_2d(&tmB, &full[s], Bs + s * S::B_BYTES, kb * BK, n0);
+            ++issued;
+        }
+        // on abort: let every copy this thread issued land before the CTA exits
+        if (*abort) {
+            for (int kb = 0; kb < issued; ++kb) {
+                const int s = kb % S::STAGES;
+                const long long t0 = clock64();
+                while (!mbar_try_wait(&full[s], (kb / S::STAGES) & 1) && clock64() - t0 < kWaitCycles / 4) {
+                }
+            }
+        }
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        constexpr uint32_t idesc = idesc_bf16(BM, BN);
+        for (int kb = 0; kb < nk; ++kb) {
+            const int s = kb % S::STAGES;
+            const uint32_t ph = (kb / S::STAGES) & 1;
+            if (!mbar_wait(&full[s], ph, abort)) {
+                if (ep.err) atomicOr(ep.err, 2);
+                *abort = 1;
+                break;
+            }
+            tc_fence_after();
+            const uint64_t ad = sw128_desc(smem_u32(As + s * S::A_BYTES));
+            const uint64_t bd = sw128_desc(smem_u32(Bs + s * S::B_BYTES));
+#pragma unroll
+            for (int k = 0; k < BK / 16; ++k)
+                mma_bf16(tmem_d, ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2), idesc, (kb | k) != 0 ? 1u : 0u);
+            mma_commit(&empty[s]);
+        }
+        mma_commit(accb);
+    } else if (warp >= 2) {
+        // epilogue: warp w owns TMEM lanes 32 (w % 4) .. + 31, i.e. tile rows
+        const int q = warp & 3;
+        const int row = q * 32 + lane;
+        const int m = m0 + row;
+        // tcgen05.ld is .sync.aligned: the whole warp must take the same branch
+        const bool ok = __all_sync(0xffffffffu, mbar_wait(accb, 0, abort) && !*abort);
+        if (!ok && ep.err) atomicOr(ep.err, 4);
+        tc_fence_after();
+        float lsum = 0.f;
+        if (ok) {
+            for (int c0 = 0; c0 < BN; c0 += 16) {
+                if (n0 + c0 >= N) break;
+                float v[16];
+                tmem_ld16(tmem_d + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
+                if (m >= M) continue;
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int n = n0 + c0 + j;
+                    if (n >= N) break;
+                    float a = v[j];
+                    if (mode == EPI_F32) {
+                        ep.out_f[(size_t)m * ep.ld_out + n] = a;
+                    } else if (mode == EPI_BIAS_ACT) {
+                        const float z = a + ep.bias[n];
+                        const __nv_bfloat16 hb = __float2bfloat16_rn(act_f(z, ep.act));
+                        ep.out_bf[(size_t)m * ep.ld_out + n] = hb;
+                        if (ep.z_out) ep.z_out[(size_t)m * ep.ld_out + n] = __float2bfloat16_rn(z);
+                        if (ep.out_bf_t) ep.out_bf_t[(size_t)n * ep.ld_t + m] = hb;
+                    } else if (mode == EPI_OUTPUT) {
+                        const float y = (a + ep.bias[n]) * ep.col_std[n] + ep.col_mean[n];
+                        if (n < ep.split) ep.out_f[(size_t)m * ep.ld_out + n] = y;
+                        else ep.out_f2[(size_t)m * ep.ld_out2 + (n - ep.split)] = y;
+                    } else if (mode == EPI_LOSS) {
+                        const float y = a + ep.bias[n];
+                        const float d = y - ep.target[(size_t)m * ep.ld_out + n];
+                        lsum += fabsf(d);
+                        const float gsgn = d > 0.f ? ep.loss_scale : (d < 0.f ? -ep.loss_scale : 0.f);
+                        const __nv_bfloat16 gb = __float2bfloat16_rn(gsgn);
+                        ep.out_bf[(size_t)m * ep.ld_out + n] = gb;
+                        if (ep.out_bf_t) ep.out_bf_t[(size_t)n * ep.ld_t + m] = gb;
+                    } else {  // EPI_DACT
+                        const float z = __bfloat162float(ep.z_in[(size_t)m * ep.ld_out + n]);
+                        const __nv_bfloat16 gb = __float2bfloat16_rn(a * act_df(z, ep.act));
+                        ep.out_bf[(size_t)m * ep.ld_out + n] = gb;
+                        if (ep.out_bf_t) ep.out_bf_t[(size_t)n * ep.ld_t + m] = gb;
+                    }
+                }
+            }
+        }
+        if (mode == EPI_LOSS && ep.loss_acc) {
+            for (int off = 16; off > 0; off >>= 1) lsum += __shfl_down_sync(0xffffffffu, lsum, off);
+            if (lane == 0) atomicAdd(ep.loss_acc, lsum);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        // the final commit tracks every MMA this CTA issued: never free TMEM under one in flight
+        if (lane == 0) {
+            const long long t0 = clock64();
+            while (!mbar_try_wait(accb, 0) && clock64() - t0 < kWaitCycles) {
+            }
+        }
+        __syncwarp();
+        tc_fence_after();
+        tmem_dealloc(tmem_d, BN);
+    }
+}
+
+}  // namespace tc
