@@ -45,6 +45,10 @@ def parse():
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nx", type=int, default=64, help="elements per side of the slab (64: the benchmark workload)")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-path section")
+    ap.add_argument("--train-elements", type=int, default=32768)
+    ap.add_argument("--train-epochs", type=int, default=30)
+    ap.add_argument("--learned-tol", type=float, default=1e-3)
     return ap.parse_args()
 
 
@@ -157,6 +161,92 @@ def run_reference(args, rank, world):
 # ------------------------------------------------------------------------------------------------
 # our arm (GPU)
 # ------------------------------------------------------------------------------------------------
+
+def learned_section(args, E, W, ctx, prob, kap, om, g, um_classical, peaks):
+    """Train the element network on seeded elements with classical labels (untimed), then time the
+    learned local stage alone and the whole learned pipeline on the benchmark slab."""
+    import numpy as np
+    import torch
+    out = {}
+    p, N = prob.p, prob.n_angles
+    xi, wq = E.elrt_lgl(p)
+    xx, zz = np.meshgrid(xi, xi)
+    n_tr = args.train_elements
+    t0 = time.perf_counter()
+    eb = W.element_batch(n_tr)
+    k_tr = torch.tensor(eb.kappa_at(xx.reshape(-1), zz.reshape(-1)), device="cuda")
+    o_tr = torch.tensor(eb.omega, device="cuda")
+    h_tr = torch.tensor(eb.h, device="cuda")
+    a_tr = torch.empty(n_tr, ctx.nin, ctx.nin, device="cuda", dtype=torch.float32)
+    m_tr = torch.empty(n_tr, ctx.nm, ctx.nin, device="cuda", dtype=torch.float32)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    ctx.elrt_build_local(k_tr, o_tr, 1.0, a_tr, m_tr, mode=E.LOCAL_FP32_IR, refine_steps=1, h_elem=h_tr)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    net = E.Net(p, N, n_hidden=4, width=1024, activation="gelu", seed=2308)
+    batch = 1024
+    losses = net.elrt_net_fit(k_tr, o_tr, h_tr, a_tr, m_tr, epochs=args.train_epochs, batch=batch, lr=1e-3, seed=7)
+    torch.cuda.synchronize()
+    t3 = time.perf_counter()
+    del a_tr, m_tr
+    samples = (n_tr // batch) * batch * args.train_epochs
+    flop_sample = 2.0 * net.n_params
+    out["training"] = {"elements": n_tr, "epochs": args.train_epochs, "batch": batch, "label_s": t2 - t1,
+                       "input_gen_s": t1 - t0, "train_s": t3 - t2, "samples_per_s": samples / (t3 - t2),
+                       "tflops": 3 * flop_sample * samples / (t3 - t2) / 1e12,
+                       "loss_first": float(losses[0]), "loss_last": float(losses[-1]), "params": net.n_params,
+                       "recipe": "element_batch (h~U[0.05,1] km, lognormal GRF kappa, albedo U[0.9,1]), labels from "
+                                 "elrt_build_local FP32_IR; 4x1024 GELU; MAE; Adam lr 1e-3 /10 per third"}
+    n = prob.n_elems
+    i2o = torch.empty(n, ctx.nin, ctx.nin, device="cuda", dtype=torch.float32)
+    i2m = torch.empty(n, ctx.nm, ctx.nin, device="cuda", dtype=torch.float32)
+    sk = torch.empty(n * ctx.nin, device="cuda", dtype=torch.float64)
+    um = torch.empty(n, ctx.nm, device="cuda", dtype=torch.float64)
+    stream = torch.cuda.current_stream()
+    # the learned local stage alone (network inference): tensor roofline
+    for _ in range(3):
+        net.elrt_net_infer(kap, om, prob.h, i2o, i2m)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 10
+    e0.record(stream)
+    for _ in range(reps):
+        net.elrt_net_infer(kap, om, prob.h, i2o, i2m)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    inf_ms = e0.elapsed_time(e1) / reps
+    inf_tflops = flop_sample * n / (inf_ms / 1000) / 1e12
+    out["inference"] = {"ms": inf_ms, "elements_per_s": n / (inf_ms / 1000), "tflops": inf_tflops,
+                        "roofline": {"bound": "tensor", "achieved": inf_tflops, "peak": peaks["bf16_tflops"],
+                                     "unit": "TFLOP/s", "frac": inf_tflops / peaks["bf16_tflops"],
+                                     "flop_per_element": flop_sample}}
+    # the whole learned pipeline with fallback
+    stats = {}
+
+    def lstep():
+        stats["nf"] = E.elrt_build_local_learned(ctx, net, kap, om, prob.h, i2o, i2m, tol=args.learned_tol)
+        stats["g"] = ctx.elrt_solve_global(prob.nx, prob.nz, i2o, g, sk, rtol=args.rtol, max_iter=20000, restart=50)
+        ctx.elrt_recover_mean(prob.nx, prob.nz, i2m, sk, g, um)
+
+    lstep()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        lstep()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    l_ms = e0.elapsed_time(e1) / args.steps
+    w2 = np.outer(wq, wq).reshape(-1)
+    ref = um_classical.cpu().numpy()
+    got = um.cpu().numpy()
+    rel = float(np.sqrt(np.sum(w2 * (got - ref) ** 2) / np.sum(w2 * ref ** 2)))
+    out["pipeline"] = {"ms_per_step": l_ms, "elements_per_s": n / (l_ms / 1000), "fallback_elements": stats["nf"],
+                       "fallback_fraction": stats["nf"] / n, "tol": args.learned_tol,
+                       "gmres_iterations": stats["g"].iterations, "rel_l2_vs_classical": rel}
+    net.close()
+    return out
+
 
 def run_ours(args, rank, world, local_rank):
     import numpy as np
@@ -311,6 +401,12 @@ def run_ours(args, rank, world, local_rank):
                                          f"same field at {nsamp}x{nsamp} elements ({nsamp * nsamp} elements), {t_cpu:.1f} s"}
         out["rel_l2_vs_oracle_sample"] = err
         sctx.close()
+    if not args.no_learned:
+        um_classical = um.clone()
+        out["learned"] = learned_section(args, E, W, ctx, prob, kap, om, g, um_classical, peaks)
+        lp = out["learned"]["pipeline"]
+        out["learned_vs_classical"] = {"classical_ms": ms, "learned_ms": lp["ms_per_step"],
+                                       "speedup": ms / lp["ms_per_step"], "rel_l2": lp["rel_l2_vs_classical"]}
     print(json.dumps(out), flush=True)
     ctx.close()
 

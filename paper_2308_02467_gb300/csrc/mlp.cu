@@ -260,7 +260,8 @@ elrt_status gemm(elrt_net* net, const bf16* A, const bf16* Bm, int M, int N, int
     const bool wide = N >= 2048;
     if (!make_map(&ta, A, M, K, tc::BM) || !make_map(&tb, Bm, N, K, wide ? 256 : 128))
         return net_fail(net, ELRT_EINVAL, "tensor map encoding failed (alignment or stride)");
-    dim3 grid((M + tc::BM - 1) / tc::BM, wide ? (N + 255) / 256 : (N + 127) / 128);
+    const int tiles = ((M + tc::BM - 1) / tc::BM) * (wide ? (N + 255) / 256 : (N + 127) / 128);
+    dim3 grid(std::min(tiles, 152));
     if (wide) {
         const int smem = tc::GemmSmem<256>::TOTAL;
         cudaFuncSetAttribute(tc::k_gemm_bf16<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

@@ -172,8 +172,111 @@ struct GemmSmem {
     static constexpr int B_BYTES = BN * BK * 2;
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
     static constexpr int TOTAL = STAGES * STAGE_BYTES + 1024 /*alignment*/ + 256 /*barriers*/;
+    static constexpr int TMEM_COLS = 2 * BN;  // two accumulators: epilogue of one tile overlaps the next
 };
 
+__device__ __forceinline__ void st_f32x16(float* dst, const float (&v)[16]) {
+    float4* d = reinterpret_cast<float4*>(dst);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) d[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+}
+
+__device__ __forceinline__ void st_bf16x16(__nv_bfloat16* dst, const float (&v)[16]) {
+    uint32_t w[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        __nv_bfloat162 h2 = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+        w[q] = *reinterpret_cast<uint32_t*>(&h2);
+    }
+    uint4* d = reinterpret_cast<uint4*>(dst);
+    d[0] = make_uint4(w[0], w[1], w[2], w[3]);
+    d[1] = make_uint4(w[4], w[5], w[6], w[7]);
+}
+
+// Epilogue of 16 consecutive columns n0c .. n0c+15 of row m (v holds the accumulator values).
+__device__ __forceinline__ void epilogue16(int mode, const EpiArgs& ep, int m, int n0c, int N, float (&v)[16],
+                                           float& lsum) {
+    const bool full = n0c + 16 <= N;
+    if (mode == EPI_F32) {
+        if (full) {
+            st_f32x16(ep.out_f + (size_t)m * ep.ld_out + n0c, v);
+        } else {
+            _Pragma("unroll") for (int j = 0; j < 16; ++j) if (n0c + j < N)
+ep.out_f[(size_t)m * ep.ld_out + n0c + j] = v[j];
+        }
+    } else if (mode == EPI_BIAS_ACT) {
+        float z[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int n = n0c + j;
+            z[j] = v[j] + (n < N ? ep.bias[n] : 0.f);
+            v[j] = act_f(z[j], ep.act);
+        }
+        if (full) {
+            st_bf16x16(ep.out_bf + (size_t)m * ep.ld_out + n0c, v);
+            if (ep.z_out) st_bf16x16(ep.z_out + (size_t)m * ep.ld_out + n0c, z);
+        } else {
+            _Pragma("unroll") for (int j = 0; j < 16; ++j) if (n0c + j < N) {
+                ep.out_bf[(size_t)m * ep.ld_out + n0c + j] = __float2bfloat16_rn(v[j]);
+                if (ep.z_out) ep.z_out[(size_t)m * ep.ld_out + n0c + j] = __float2bfloat16_rn(z[j]);
+            }
+        }
+        if (ep.out_bf_t)
+            _Pragma("unroll") for (int j = 0; j < 16; ++j) if (n0c + j < N)
+ep.out_bf_t[(size_t)(n0c + j) * ep.ld_t + m] = __float2bfloat16_rn(v[j]);
+    } else if (mode == EPI_OUTPUT) {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int n = n0c + j < N ? n0c + j : N - 1;
+            v[j] = (v[j] + ep.bias[n]) * ep.col_std[n] + ep.col_mean[n];
+        }
+        // the split (a multiple of 16) never falls inside a 16-column group
+        float* dst = n0c < ep.split ? ep.out_f + (size_t)m * ep.ld_out + n0c
+                                    : ep.out_f2 + (size_t)m * ep.ld_out2 + (n0c - ep.split);
+        if (full) {
+            st_f32x16(dst, v);
+        } else {
+            _Pragma("unroll") for (int j = 0; j < 16; ++j) if (n0c + j < N)
+dst[j] = v[j];
+        }
+    } else if (mode == EPI_LOSS) {
+        _Pragma("unroll") for (int j = 0; j < 16; ++j) if (n0c + j < N) {
+            const int n = n0c + j;
+            const float y = v[j] + ep.bias[n];
+            const float d = y - ep.target[(size_t)m * ep.ld_out + n];
+            lsum += fabsf(d);
+            v[j] = d > 0.f ? ep.loss_scale : (d < 0.f ? -ep.loss_scale : 0.f);
+        }
+        if (full) {
+            st_bf16x16(ep.out_bf + (size_t)m * ep.ld_out + n0c, v);
+        } else {
+            _Pragma("unroll") for (int j = 0; j < 16; ++j) if (n0c + j < N)
+ep.out_bf[(size_t)m * ep.ld_out + n0c + j] = __float2bfloat16_rn(v[j]);
+        }
+        if (ep.out_bf_t)
+            _Pragma("unroll") for (int j = 0; j < 16; ++j) if (n0c + j < N)
+ep.out_bf_t[(size_t)(n0c + j) * ep.ld_t + m] = __float2bfloat16_rn(v[j]);
+    } else {  // EPI_DACT
+        _Pragma("unroll") for (int j = 0; j < 16; ++j) if (n0c + j < N) {
+            const float z = __bfloat162float(ep.z_in[(size_t)m * ep.ld_out + n0c + j]);
+            v[j] = v[j] * act_df(z, ep.act);
+        }
+        if (full) {
+            st_bf16x16(ep.out_bf + (size_t)m * ep.ld_out + n0c, v);
+        } else {
+            _Pragma("unroll") for (int j = 0; j < 16; ++j) if (n0c + j < N)
+ep.out_bf[(size_t)m * ep.ld_out + n0c + j] = __float2bfloat16_rn(v[j]);
+        }
+        if (ep.out_bf_t)
+            _Pragma("unroll") for (int j = 0; j < 16; ++j) if (n0c + j < N)
+ep.out_bf_t[(size_t)(n0c + j) * ep.ld_t + m] = __float2bfloat16_rn(v[j]);
+    }
+}
+
+// Persistent: each CTA walks tiles blockIdx.x, blockIdx.x + gridDim.x, ... (M tiles fastest, so
+// concurrently running CTAs share the B tile in L2).  The TMA producer streams k-blocks of
+// consecutive tiles through the ring without a break; the MMA issuer alternates between two TMEM
+// accumulators so the epilogue of one tile overlaps the MMAs of the next.
 template <int BN>
 __global__ void __launch_bounds__(kGemmThreads, 1)
     k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N, int K,
@@ -185,126 +288,125 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     unsigned char* Bs = base + S::STAGES * S::A_BYTES;
     uint64_t* full = (uint64_t*)(base + S::STAGES * S::STAGE_BYTES);
     uint64_t* empty = full + S::STAGES;
-    uint64_t* accb = empty + S::STAGES;
-    uint32_t* tmem_slot = (uint32_t*)(accb + 1);
+    uint64_t* acc_full = empty + S::STAGES;  // [2]
+    uint64_t* acc_empty = acc_full + 2;      // [2]
+    uint32_t* tmem_slot = (uint32_t*)(acc_empty + 2);
     volatile int* abort = (volatile int*)(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
     const int nk = (K + BK - 1) / BK;
+    const int mt = (M + BM - 1) / BM, ntl = (N + BN - 1) / BN;
+    const int ntiles = mt * ntl;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S::STAGES; ++s) {
             mbar_init(&full[s], 1);
             mbar_init(&empty[s], 1);
         }
-        mbar_init(accb, 1);
+        for (int a = 0; a < 2; ++a) {
+            mbar_init(&acc_full[a], 1);
+            mbar_init(&acc_empty[a], 4);  // one arrival per epilogue warp
+        }
         *abort = 0;
         fence_barrier_init();
     }
     if (warp == 1) {
-        tmem_alloc(tmem_slot, BN);
+        tmem_alloc(tmem_slot, S::TMEM_COLS);
         tmem_relinquish();
     }
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    const uint32_t tmem_d = *tmem_slot;
+    const uint32_t tmem_base = *tmem_slot;
+    int committed = 0;  // accumulator commits issued by this CTA (MMA thread)
 
     if (warp == 0 && lane == 0) {
         // TMA producer
-        int issued = 0;
-        for (int kb = 0; kb < nk; ++kb) {
-            const int s = kb % S::STAGES;
-            const uint32_t ph = (kb / S::STAGES) & 1;
-            if (!mbar_wait(&empty[s], ph ^ 1, abort)) {
-                if (ep.err) atomicOr(ep.err, 1);
-                *abort = 1;
-                break;
+        int kbg = 0, issued = 0;
+        for (int tile = blockIdx.x; tile < ntiles && !*abort; tile += gridDim.x) {
+            const int m0 = (tile % mt) * BM, n0 = (tile / mt) * BN;
+            for (int kb = 0; kb < nk; ++kb, ++kbg) {
+                const int s = kbg % S::STAGES;
+                const uint32_t ph = (kbg / S::STAGES) & 1;
+                if (!mbar_wait(&empty[s], ph ^ 1, abort)) {
+                    if (ep.err) atomicOr(ep.err, 1);
+                    *abort = 1;
+                    break;
+                }
+                mbar_expect_tx(&full[s], S::STAGE_BYTES);
+                tma_load_2d(&tmA, &full[s], As + s * S::A_BYTES, kb * BK, m0);
+                tma_load_2d(&tmB, &full[s], Bs + s * S::B_BYTES, kb * BK, n0);
+                ++issued;
             }
-            mbar_expect_tx(&full[s], S::STAGE_BYTES);
-            tma_load_2d(&tmA, &full[s], As + s * S::A_BYTES, kb * BK, m0);
-            tma_load_2d(&tmB, &full[s], Bs + s * S::B_BYTES, kb * BK, n0);
-            ++issued;
         }
-        // on abort: let every copy this thread issued land before the CTA exits
-        if (*abort) {
-            for (int kb = 0; kb < issued; ++kb) {
-                const int s = kb % S::STAGES;
+        if (*abort) {  // let every copy this thread issued land before the CTA exits
+            for (int q = (issued > S::STAGES ? issued - S::STAGES : 0); q < issued; ++q) {
                 const long long t0 = clock64();
-                while (!mbar_try_wait(&full[s], (kb / S::STAGES) & 1) && clock64() - t0 < kWaitCycles / 4) {
+                while (!mbar_try_wait(&full[q % S::STAGES], (q / S::STAGES) & 1) && clock64() - t0 < kWaitCycles / 4) {
                 }
             }
         }
     } else if (warp == 1 && lane == 0) {
         // MMA issuer
         constexpr uint32_t idesc = idesc_bf16(BM, BN);
-        for (int kb = 0; kb < nk; ++kb) {
-            const int s = kb % S::STAGES;
-            const uint32_t ph = (kb / S::STAGES) & 1;
-            if (!mbar_wait(&full[s], ph, abort)) {
-                if (ep.err) atomicOr(ep.err, 2);
+        int kbg = 0, t = 0;
+        for (int tile = blockIdx.x; tile < ntiles && !*abort; tile += gridDim.x, ++t) {
+            const int a = t & 1;
+            if (!mbar_wait(&acc_empty[a], ((t >> 1) & 1) ^ 1, abort)) {
+                if (ep.err) atomicOr(ep.err, 8);
                 *abort = 1;
                 break;
             }
             tc_fence_after();
-            const uint64_t ad = sw128_desc(smem_u32(As + s * S::A_BYTES));
-            const uint64_t bd = sw128_desc(smem_u32(Bs + s * S::B_BYTES));
+            const uint32_t dt = tmem_base + (uint32_t)(a * BN);
+            bool ok = true;
+            for (int kb = 0; kb < nk; ++kb, ++kbg) {
+                const int s = kbg % S::STAGES;
+                const uint32_t ph = (kbg / S::STAGES) & 1;
+                if (!mbar_wait(&full[s], ph, abort)) {
+                    if (ep.err) atomicOr(ep.err, 2);
+                    *abort = 1;
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                const uint64_t ad = sw128_desc(smem_u32(As + s * S::A_BYTES));
+                const uint64_t bd = sw128_desc(smem_u32(Bs + s * S::B_BYTES));
 #pragma unroll
-            for (int k = 0; k < BK / 16; ++k)
-                mma_bf16(tmem_d, ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2), idesc, (kb | k) != 0 ? 1u : 0u);
-            mma_commit(&empty[s]);
+                for (int k = 0; k < BK / 16; ++k)
+                    mma_bf16(dt, ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2), idesc, (kb | k) != 0 ? 1u : 0u);
+                mma_commit(&empty[s]);
+            }
+            mma_commit(&acc_full[a]);
+            ++committed;
+            if (!ok) break;
         }
-        mma_commit(accb);
     } else if (warp >= 2) {
         // epilogue: warp w owns TMEM lanes 32 (w % 4) .. + 31, i.e. tile rows
         const int q = warp & 3;
-        const int row = q * 32 + lane;
-        const int m = m0 + row;
-        // tcgen05.ld is .sync.aligned: the whole warp must take the same branch
-        const bool ok = __all_sync(0xffffffffu, mbar_wait(accb, 0, abort) && !*abort);
-        if (!ok && ep.err) atomicOr(ep.err, 4);
-        tc_fence_after();
         float lsum = 0.f;
-        if (ok) {
+        int t = 0;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++t) {
+            const int a = t & 1;
+            const int m0 = (tile % mt) * BM, n0 = (tile / mt) * BN;
+            // tcgen05.ld is .sync.aligned: the whole warp must take the same branch
+            const bool ok = __all_sync(0xffffffffu, mbar_wait(&acc_full[a], (t >> 1) & 1, abort) && !*abort);
+            if (!ok) {
+                if (ep.err && lane == 0) atomicOr(ep.err, 4);
+                break;
+            }
+            tc_fence_after();
+            const int m = m0 + q * 32 + lane;
+            const uint32_t tb = tmem_base + (uint32_t)(a * BN) + ((uint32_t)(q * 32) << 16);
             for (int c0 = 0; c0 < BN; c0 += 16) {
                 if (n0 + c0 >= N) break;
                 float v[16];
-                tmem_ld16(tmem_d + ((uint32_t)(q * 32) << 16) + (uint32_t)c0, v);
-                if (m >= M) continue;
-#pragma unroll
-                for (int j = 0; j < 16; ++j) {
-                    const int n = n0 + c0 + j;
-                    if (n >= N) break;
-                    float a = v[j];
-                    if (mode == EPI_F32) {
-                        ep.out_f[(size_t)m * ep.ld_out + n] = a;
-                    } else if (mode == EPI_BIAS_ACT) {
-                        const float z = a + ep.bias[n];
-                        const __nv_bfloat16 hb = __float2bfloat16_rn(act_f(z, ep.act));
-                        ep.out_bf[(size_t)m * ep.ld_out + n] = hb;
-                        if (ep.z_out) ep.z_out[(size_t)m * ep.ld_out + n] = __float2bfloat16_rn(z);
-                        if (ep.out_bf_t) ep.out_bf_t[(size_t)n * ep.ld_t + m] = hb;
-                    } else if (mode == EPI_OUTPUT) {
-                        const float y = (a + ep.bias[n]) * ep.col_std[n] + ep.col_mean[n];
-                        if (n < ep.split) ep.out_f[(size_t)m * ep.ld_out + n] = y;
-                        else ep.out_f2[(size_t)m * ep.ld_out2 + (n - ep.split)] = y;
-                    } else if (mode == EPI_LOSS) {
-                        const float y = a + ep.bias[n];
-                        const float d = y - ep.target[(size_t)m * ep.ld_out + n];
-                        lsum += fabsf(d);
-                        const float gsgn = d > 0.f ? ep.loss_scale : (d < 0.f ? -ep.loss_scale : 0.f);
-                        const __nv_bfloat16 gb = __float2bfloat16_rn(gsgn);
-                        ep.out_bf[(size_t)m * ep.ld_out + n] = gb;
-                        if (ep.out_bf_t) ep.out_bf_t[(size_t)n * ep.ld_t + m] = gb;
-                    } else {  // EPI_DACT
-                        const float z = __bfloat162float(ep.z_in[(size_t)m * ep.ld_out + n]);
-                        const __nv_bfloat16 gb = __float2bfloat16_rn(a * act_df(z, ep.act));
-                        ep.out_bf[(size_t)m * ep.ld_out + n] = gb;
-                        if (ep.out_bf_t) ep.out_bf_t[(size_t)n * ep.ld_t + m] = gb;
-                    }
-                }
+                tmem_ld16(tb + (uint32_t)c0, v);
+                if (m < M) epilogue16(mode, ep, m, n0 + c0, N, v, lsum);
             }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&acc_empty[a])) : "memory");
         }
         if (mode == EPI_LOSS && ep.loss_acc) {
             for (int off = 16; off > 0; off >>= 1) lsum += __shfl_down_sync(0xffffffffu, lsum, off);
@@ -314,15 +416,16 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     tc_fence_before();
     __syncthreads();
     if (warp == 1) {
-        // the final commit tracks every MMA this CTA issued: never free TMEM under one in flight
-        if (lane == 0) {
+        // the last commit tracks every MMA this CTA issued: never free TMEM under one in flight
+        if (lane == 0 && committed > 0) {
+            const int last = committed - 1;
             const long long t0 = clock64();
-            while (!mbar_try_wait(accb, 0) && clock64() - t0 < kWaitCycles) {
+            while (!mbar_try_wait(&acc_full[last & 1], (last >> 1) & 1) && clock64() - t0 < kWaitCycles) {
             }
         }
         __syncwarp();
         tc_fence_after();
-        tmem_dealloc(tmem_d, BN);
+        tmem_dealloc(tmem_base, S::TMEM_COLS);
     }
 }
 
