@@ -40,7 +40,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="fp32ir", choices=["fp32ir", "fp64"])
+    ap.add_argument("--mode", default="fp32ir", choices=["tf32ir", "fp32ir", "fp64"])
     ap.add_argument("--refine", type=int, default=1)
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -241,6 +241,19 @@ def learned_section(args, E, W, ctx, prob, kap, om, g, um_classical, peaks):
     ref = um_classical.cpu().numpy()
     got = um.cpu().numpy()
     rel = float(np.sqrt(np.sum(w2 * (got - ref) ** 2) / np.sum(w2 * ref ** 2)))
+    # the plain FP64 classical GPU path on the same slab, one step (the comparison of the method)
+    i2o64 = torch.empty(n, ctx.nin, ctx.nin, device="cuda", dtype=torch.float64)
+    i2m64 = torch.empty(n, ctx.nm, ctx.nin, device="cuda", dtype=torch.float64)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    ctx.elrt_build_local(kap, om, prob.h, i2o64, i2m64, mode=E.LOCAL_FP64, stats=False)
+    g64 = ctx.elrt_solve_global(prob.nx, prob.nz, i2o64, g, sk, rtol=args.rtol, max_iter=20000, restart=50)
+    ctx.elrt_recover_mean(prob.nx, prob.nz, i2m64, sk, g, um)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    out["classical_fp64"] = {"ms_per_step": e0.elapsed_time(e1), "gmres_iterations": g64.iterations,
+                             "operator_dtype": "f64"}
+    del i2o64, i2m64
     out["pipeline"] = {"ms_per_step": l_ms, "elements_per_s": n / (l_ms / 1000), "fallback_elements": stats["nf"],
                        "fallback_fraction": stats["nf"] / n, "tol": args.learned_tol,
                        "gmres_iterations": stats["g"].iterations, "rel_l2_vs_classical": rel}
@@ -261,7 +274,7 @@ def run_ours(args, rank, world, local_rank):
         import torch.distributed as td
 
     prob = W.problem_gaussian_slab(n=args.nx)
-    mode = E.LOCAL_FP32_IR if args.mode == "fp32ir" else E.LOCAL_FP64
+    mode = {"tf32ir": E.LOCAL_TF32_IR, "fp32ir": E.LOCAL_FP32_IR, "fp64": E.LOCAL_FP64}[args.mode]
     ctx = E.Context(prob.p, prob.n_angles, prob.hg_g, E.ANG_FV0)
     nx, nz, n = prob.nx, prob.nz, prob.n_elems
     xs, zs = E.elrt_node_coords(prob.p, prob.n_angles, nx, nz, prob.h)
@@ -306,8 +319,8 @@ def run_ours(args, rank, world, local_rank):
     barrier()
     ms = ev0.elapsed_time(ev1) / args.steps
     launches = ctx.elrt_launch_count()
-    prof = {k: ctx.elrt_profile_get(k) for k in ("assemble", "lu_factor_solve", "lu_resolve", "residual", "restrict",
-                                                  "status", "gemv", "krylov")}
+    prof = {k: ctx.elrt_profile_get(k) for k in ("assemble", "lu_factor_solve", "lu_resolve", "lu_tc_panel",
+                                                  "lu_tc_update", "residual", "restrict", "status", "gemv", "krylov")}
     ctx.elrt_profile_enable(False)
     if dist:
         t = torch.tensor([ms], device="cuda")
@@ -357,7 +370,7 @@ def run_ours(args, rank, world, local_rank):
         "metric": "elements/s (classical element pipeline: local operators + skeleton GMRES + mean recovery)",
         "value": val, "unit": "elements/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32+f64" if args.mode == "fp32ir" else "f64", "data": "synthetic",
+        "dtype": {"tf32ir": "tf32x3+f32+ff", "fp32ir": "f32+ff", "fp64": "f64"}[args.mode], "data": "synthetic",
         "config": {"workload": workload_name(args.nx), "elements": n, "p": prob.p, "n_angles": prob.n_angles,
                    "local_mode": args.mode, "refine_steps": args.refine, "gmres_rtol": args.rtol, "gmres_restart": 50,
                    "operator_dtype": "f32", "parallelism": f"replicas x{world}",
@@ -405,8 +418,11 @@ def run_ours(args, rank, world, local_rank):
         um_classical = um.clone()
         out["learned"] = learned_section(args, E, W, ctx, prob, kap, om, g, um_classical, peaks)
         lp = out["learned"]["pipeline"]
-        out["learned_vs_classical"] = {"classical_ms": ms, "learned_ms": lp["ms_per_step"],
-                                       "speedup": ms / lp["ms_per_step"], "rel_l2": lp["rel_l2_vs_classical"]}
+        f64 = out["learned"]["classical_fp64"]["ms_per_step"]
+        out["learned_vs_classical"] = {"classical_fp32ir_ms": ms, "classical_fp64_ms": f64,
+                                       "learned_ms": lp["ms_per_step"],
+                                       "speedup_vs_fp32ir": ms / lp["ms_per_step"],
+                                       "speedup_vs_fp64": f64 / lp["ms_per_step"], "rel_l2": lp["rel_l2_vs_classical"]}
     print(json.dumps(out), flush=True)
     ctx.close()
 

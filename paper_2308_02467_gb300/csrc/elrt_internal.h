@@ -82,6 +82,12 @@ elrt_status local_build(elrt_ctx* ctx, int64_t E, double h, const double* h_elem
                         const double* omega, int mode, int refine_steps, int out_dtype, void* in2out,
                         void* in2sol, int32_t* elem_status, elrt_local_stats* stats);
 
+// ---- tensor-core LU (lu_tc.cu)
+elrt_status tc_lu_factor_solve(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, int64_t E, int* estat, float* side,
+                               int* err);
+elrt_status tc_lu_resolve(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, int64_t E, float* side, int* err);
+size_t tc_lu_side_floats(const Tab& t, int64_t ld);
+
 // ---- launchers implemented in global.cu
 elrt_status global_apply(elrt_ctx* ctx, int nx, int nz, const void* A, int dtype, const double* x, double* y);
 elrt_status global_solve(elrt_ctx* ctx, int nx, int nz, const void* A, int dtype, const double* inflow,

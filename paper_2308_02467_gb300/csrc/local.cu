@@ -15,6 +15,7 @@
 #include <stdio.h>
 
 #include <algorithm>
+#include <string>
 
 #include "elrt_internal.h"
 #include "ff.h"
@@ -663,16 +664,19 @@ elrt_status build_chunked(elrt_ctx* ctx, int64_t E, double h, const double* h_el
         for (int k = 0; k < t.N; ++k)
             for (int m = 0; m < t.n1; ++m) bmax = std::max(bmax, fabs(t.w[m] * t.sdn[F][k]));
     const bool want_res = ir || stats || elem_status;
-    // bytes per element: M, ipiv, status, maxres, and the FP64 solution when refining / measuring
+    const bool tc = (mode == ELRT_LOCAL_TF32_IR);
+    const size_t side_per = tc ? tc_lu_side_floats(t, ld) * sizeof(float) : 0;
+    // bytes per element: M, ipiv, status, maxres, the FP64 solution when refining / measuring,
+    // and the split operand buffers of the tensor-core LU
     const size_t per = estride * sizeof(T) + t.nu * sizeof(int) + sizeof(int) + sizeof(double) +
-                       (want_res ? (size_t)t.nu * t.nin * sizeof(double) : 0);
+                       (want_res ? (size_t)t.nu * t.nin * sizeof(double) : 0) + side_per;
     const size_t budget = (size_t)16 << 30;
     int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(E, (int64_t)(budget / per)));
     if (chunk < E) {  // balance the chunks
         const int64_t nch = (E + chunk - 1) / chunk;
         chunk = (E + nch - 1) / nch;
     }
-    elrt_status s = ensure_ws(ctx, &ctx->ws, &ctx->ws_bytes, per * chunk + 1024);
+    elrt_status s = ensure_ws(ctx, &ctx->ws, &ctx->ws_bytes, per * chunk + 2048);
     if (s) return s;
     unsigned char* base = (unsigned char*)ctx->ws;
     T* M = (T*)base;
@@ -680,6 +684,7 @@ elrt_status build_chunked(elrt_ctx* ctx, int64_t E, double h, const double* h_el
     double* maxres = X64 + (want_res ? (size_t)chunk * t.nu * t.nin : 0);
     int* ipiv = (int*)(maxres + chunk);
     int* estat = ipiv + (size_t)chunk * t.nu;
+    float* side = tc ? (float*)(((uintptr_t)(estat + chunk) + 255) & ~(uintptr_t)255) : nullptr;
     s = cuda_check(ctx, cudaMemsetAsync(ctx->d_flags, 0, 4 * sizeof(int) + 2 * sizeof(unsigned long long), ctx->stream),
                    "memset flags");
     if (s) return s;
@@ -700,14 +705,25 @@ elrt_status build_chunked(elrt_ctx* ctx, int64_t E, double h, const double* h_el
         }
         s = cuda_check(ctx, cudaGetLastError(), "assemble launch");
         if (s) return s;
-        s = run_lu<T, NB, QN>(ctx, M, ld, estride, ipiv, estat, n, false);
+        if constexpr (sizeof(T) == 4) {
+            if (tc) s = tc_lu_factor_solve(ctx, M, ld, estride, n, estat, side, ctx->d_flags + 2);
+            else s = run_lu<T, NB, QN>(ctx, M, ld, estride, ipiv, estat, n, false);
+        } else {
+            s = run_lu<T, NB, QN>(ctx, M, ld, estride, ipiv, estat, n, false);
+        }
         if (s) return s;
         void* o_i2o = (unsigned char*)in2out + (size_t)e0 * t.nin * t.nin * osz;
         void* o_i2m = (unsigned char*)in2sol + (size_t)e0 * t.nm * t.nin * osz;
         if (want_res) {
             s = run_residual<T>(ctx, h, he, ka, om, M, ld, estride, X64, 0, maxres, n);
             for (int it = 0; it < (ir ? steps : 0) && !s; ++it) {
-                s = run_lu<T, NB, QN>(ctx, M, ld, estride, ipiv, estat, n, true);
+                if constexpr (sizeof(T) == 4) {
+                    if (tc) s = tc_lu_resolve(ctx, M, ld, estride, n, side, ctx->d_flags + 2);
+                    else s = run_lu<T, NB, QN>(ctx, M, ld, estride, ipiv, estat, n, true);
+                } else {
+                    s = run_lu<T, NB, QN>(ctx, M, ld, estride, ipiv, estat, n, true);
+                }
+                if (s) break;
                 if (!s) s = run_residual<T>(ctx, h, he, ka, om, M, ld, estride, X64, 1, maxres, n);
             }
             if (s) return s;
@@ -744,6 +760,7 @@ elrt_status build_chunked(elrt_ctx* ctx, int64_t E, double h, const double* h_el
     prof_flush(ctx);
     const int* hf = (const int*)ctx->h_pinned;
     if (hf[0]) return ctx_fail(ctx, ELRT_EINVAL, "negative/non-finite kappa or h, or omega outside [0,1]");
+    if (hf[2]) return ctx_fail(ctx, ELRT_ETIMEOUT, "a tensor-core LU wait timed out (code " + std::to_string(hf[2]) + ")");
     if (stats) {
         stats->refine_steps = ir ? steps : 0;
         stats->n_flagged = hf[1];
@@ -763,7 +780,7 @@ elrt_status local_build(elrt_ctx* ctx, int64_t E, double h, const double* h_elem
     if (mode == ELRT_LOCAL_FP64)
         return build_chunked<double, 16, 4>(ctx, E, h, h_elem, kappa, omega, mode, refine_steps, out_dtype, in2out,
                                             in2sol, elem_status, stats);
-    if (mode == ELRT_LOCAL_FP32_IR)
+    if (mode == ELRT_LOCAL_FP32_IR || mode == ELRT_LOCAL_TF32_IR)
         return build_chunked<float, 32, 8>(ctx, E, h, h_elem, kappa, omega, mode, refine_steps, out_dtype, in2out,
                                            in2sol, elem_status, stats);
     return ctx_fail(ctx, ELRT_EINVAL, "local mode not available in this build");

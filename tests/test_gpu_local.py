@@ -179,3 +179,23 @@ def test_full_size_slab_sampled_parity_and_energy_balance(lib):
     worst = max(np.abs(H.energy_defect(w, sdn, inc, outc, w2, khl[e], prob.omega[e], 16, A[e], Mm[e])).max()
                 for e in range(0, n, 7))
     assert worst < 1e-5
+
+
+@pytest.mark.parametrize("p,N,ang,n", CASES)
+def test_local_tensor_core_lu_matches_oracle(lib, p, N, ang, n):
+    """No-pivot LU with 3xTF32 tcgen05 trailing updates, then FP64-class refinement."""
+    import torch
+    kappa, omega, h = H.random_elements(n, p, seed=p * 10 + N + 2)
+    ctx = _ctx(lib, p, N, 0.85, ang)
+    i2o = torch.empty(n, ctx.nin, ctx.nin, dtype=torch.float64, device="cuda")
+    i2m = torch.empty(n, ctx.nm, ctx.nin, dtype=torch.float64, device="cuda")
+    k, o = torch.tensor(kappa, device="cuda"), torch.tensor(omega, device="cuda")
+    _, (o_i2o, o_i2m) = _oracle_ops(p, N, 0.85, ang, kappa, omega, h)
+    st0 = ctx.elrt_build_local(k, o, h, i2o, i2m, mode=lib.LOCAL_TF32_IR, refine_steps=0)
+    err0 = np.abs(i2o.cpu().numpy() - o_i2o).max()
+    st = ctx.elrt_build_local(k, o, h, i2o, i2m, mode=lib.LOCAL_TF32_IR, refine_steps=2)
+    err2 = np.abs(i2o.cpu().numpy() - o_i2o).max()
+    assert st.n_flagged == 0                  # (unrefined results are flagged by the residual check)
+    assert err0 < 1e-4 and st0.max_rel_residual > 1e-10, err0   # 3xTF32: FP32-level before refinement
+    assert err2 < 1e-10 and st.max_rel_residual < 1e-12, (err0, err2, st.max_rel_residual)
+    np.testing.assert_allclose(i2m.cpu().numpy(), o_i2m, atol=1e-10)
