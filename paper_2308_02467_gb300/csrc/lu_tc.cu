@@ -42,118 +42,32 @@ __device__ __forceinline__ void put_split(float* hi, float* lo, int64_t idx, flo
 }
 
 // ------------------------------------------------------------------------------------------------
-// panel kernels (CUDA cores), one block of 256 threads per element.  Row- and column-wise solves
-// run one thread per row / column on data staged in shared memory (stride 65: conflict-free), so
-// every global load and store is coalesced.
+// panel kernels (CUDA cores)
+//   k_diag:   one small block per element factors the 64 x 64 diagonal block and stores the
+//             explicit inverses L11^{-1} (unit lower) and U11^{-1} of every panel;
+//   k_rowcol: many blocks per element; a row tile forms L21 rows x = a U11^{-1}, a column tile
+//             forms U12 columns y = L11^{-1} a (or, in the sweeps of a re-solve, applies L^{-1} or
+//             U^{-1} to right-hand-side columns).  Both are 64 x 64 triangular matvecs with 64
+//             independent accumulators per thread; rows and columns are staged through shared
+//             memory (stride 65) so every global access is coalesced.
 // ------------------------------------------------------------------------------------------------
 
 constexpr int TS = NBP + 1;
-constexpr int PTILE = 256;                                    // rows or columns per staged tile
-constexpr int PANEL_SMEM = PTILE * TS * (int)sizeof(float);   // dynamic shared memory of a panel kernel
+constexpr int PTILE = 256;                                         // rows or columns per tile
+constexpr int RC_SMEM = (PTILE * TS + NBP * TS) * (int)sizeof(float);  // staging + one inverse
 
-__device__ __forceinline__ void load_diag(const float* M, int64_t ld, int J, int jb, float (*D)[TS], bool unit_pad) {
-    for (int idx = threadIdx.x; idx < NBP * NBP; idx += blockDim.x) {
-        const int r = idx / NBP, c = idx % NBP;
-        D[r][c] = (r < jb && c < jb) ? M[(int64_t)(J + r) * ld + J + c] : (unit_pad && r == c ? 1.f : 0.f);
-    }
-}
-
-// rows [r0, r0 + nr) x columns [J, J + jb) of M -> S (one warp per row)
-__device__ __forceinline__ void stage_rows(const float* M, int64_t ld, int r0, int nr, int J, int jb, float* S) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int rr = warp; rr < nr; rr += blockDim.x >> 5) {
-        const float* src = M + (int64_t)(r0 + rr) * ld + J;
-        for (int j = lane; j < NBP; j += 32) S[rr * TS + j] = j < jb ? src[j] : 0.f;
-    }
-}
-
-// S rows -> split buffers rows [r0, r0 + nr) (and back into M when to_M)
-__device__ __forceinline__ void unstage_rows(float* M, int64_t ld, int r0, int nr, int J, int jb, const float* S,
-                                             float* hi, float* lo, bool to_M) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int rr = warp; rr < nr; rr += blockDim.x >> 5) {
-        for (int j = lane; j < NBP; j += 32) {
-            const float v = S[rr * TS + j];
-            if (to_M && j < jb) M[(int64_t)(r0 + rr) * ld + J + j] = v;
-            put_split(hi, lo, (int64_t)(r0 + rr) * NBP + j, v);
-        }
-    }
-}
-
-// rows [r0, r_end) x columns [J, J + jb) of M copied straight into the split buffers
-__device__ __forceinline__ void split_rows(const float* M, int64_t ld, int r0, int r_end, int J, int jb, float* hi,
-                                           float* lo) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int r = r0 + warp; r < r_end; r += blockDim.x >> 5) {
-        const float* src = M + (int64_t)r * ld + J;
-        for (int j = lane; j < NBP; j += 32) put_split(hi, lo, (int64_t)r * NBP + j, j < jb ? src[j] : 0.f);
-    }
-}
-
-// Column solves on columns [c_begin, c_end) of rows J..J+jb: mode 0 forward with the unit lower
-// triangle of D, mode 1 backward with the upper triangle.  Results go back to M and, transposed
-// through S, to the split buffers (row c = column c).
-__device__ __forceinline__ void column_solves(float* M, int64_t ld, int J, int jb, int c_begin, int c_end,
-                                              const float (*D)[TS], float* S, float* hi, float* lo, int mode) {
-    for (int c0 = c_begin; c0 < c_end; c0 += PTILE) {
-        const int nc = min(PTILE, c_end - c0);
-        const int t = threadIdx.x;
-        if (t < nc) {
-            const int c = c0 + t;
-            float y[NBP];
-#pragma unroll
-            for (int i = 0; i < NBP; ++i) y[i] = i < jb ? M[(int64_t)(J + i) * ld + c] : 0.f;
-            if (mode == 0) {
-#pragma unroll
-                for (int i = 1; i < NBP; ++i) {
-                    if (i < jb) {
-                        float s = y[i];
-#pragma unroll
-                        for (int k = 0; k < i; ++k) s -= D[i][k] * y[k];
-                        y[i] = s;
-                    }
-                }
-            } else {
-#pragma unroll
-                for (int ii = 0; ii < NBP; ++ii) {
-                    const int i = NBP - 1 - ii;
-                    if (i < jb) {
-                        float s = y[i];
-#pragma unroll
-                        for (int k = i + 1; k < NBP; ++k)
-                            if (k < jb) s -= D[i][k] * y[k];
-                        y[i] = s / D[i][i];
-                    }
-                }
-            }
-#pragma unroll
-            for (int i = 0; i < NBP; ++i) {
-                if (i < jb) M[(int64_t)(J + i) * ld + c] = y[i];
-                S[t * TS + i] = y[i];
-            }
-        }
-        __syncthreads();
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-        for (int cc = warp; cc < nc; cc += blockDim.x >> 5)
-            for (int i = lane; i < NBP; i += 32) put_split(hi, lo, (int64_t)(c0 + cc) * NBP + i, S[cc * TS + i]);
-        __syncthreads();
-    }
-}
-
-// Factor the diagonal block and form L21 (rows J+jb..nu) and U12 (columns J+jb..ncols).
-__global__ void __launch_bounds__(256) k_panel(int nu, int ncols, int64_t ld, int64_t estride, float* __restrict__ Mall,
-                                               int J, int jb, float* __restrict__ Lh, float* __restrict__ Ll,
-                                               float* __restrict__ Uh, float* __restrict__ Ul, int* __restrict__ estat,
-                                               float piv_tol) {
+// Tinv layout per element: [panel][2][64][64]: [0] = L11^{-1} (unit lower), [1] = U11^{-1} (upper)
+__global__ void __launch_bounds__(64) k_diag(int nu, int64_t ld, int64_t estride, float* __restrict__ Mall, int J,
+                                             int jb, float* __restrict__ Tinv, int npanels, int* __restrict__ estat,
+                                             float piv_tol) {
     __shared__ float D[NBP][TS];
-    extern __shared__ float S[];
     const int64_t e = blockIdx.x;
     float* M = Mall + e * estride;
-    float* lh = Lh + e * (int64_t)nu * NBP;
-    float* ll = Ll + e * (int64_t)nu * NBP;
-    float* uh = Uh + e * ld * NBP;
-    float* ul = Ul + e * ld * NBP;
-    load_diag(M, ld, J, jb, D, true);
+    const int t = threadIdx.x;
+    for (int idx = t; idx < NBP * NBP; idx += 64) {
+        const int r = idx / NBP, c = idx % NBP;
+        D[r][c] = (r < jb && c < jb) ? M[(int64_t)(J + r) * ld + J + c] : (r == c ? 1.f : 0.f);
+    }
     __syncthreads();
     int bad = 0;
     for (int j = 0; j < jb; ++j) {
@@ -162,79 +76,155 @@ __global__ void __launch_bounds__(256) k_panel(int nu, int ncols, int64_t ld, in
             bad = 1;
             piv = piv < 0.f ? -piv_tol : piv_tol;
         }
-        const float inv = 1.f / piv;
         __syncthreads();
-        if (threadIdx.x == 0) D[j][j] = piv;
-        for (int i = j + 1 + threadIdx.x; i < jb; i += blockDim.x) {
-            const float l = D[i][j] * inv;
-            D[i][j] = l;
-            for (int c = j + 1; c < jb; ++c) D[i][c] -= l * D[j][c];
+        if (t == j) D[j][j] = piv;
+        if (t > j && t < jb) {  // thread t eliminates row t
+            const float l = D[t][j] / piv;
+            D[t][j] = l;
+            for (int c = j + 1; c < jb; ++c) D[t][c] -= l * D[j][c];
         }
         __syncthreads();
     }
-    if (bad && threadIdx.x == 0) atomicOr(&estat[e], 1);
-    for (int idx = threadIdx.x; idx < jb * jb; idx += blockDim.x) {
+    if (bad && t == 0) atomicOr(&estat[e], 1);
+    for (int idx = t; idx < jb * jb; idx += 64) {
         const int r = idx / jb, c = idx % jb;
         M[(int64_t)(J + r) * ld + J + c] = D[r][c];
     }
-    // L21 = A21 U11^{-1}: x_j = (a_j - sum_{i<j} x_i U_ij) / U_jj
-    for (int r0 = J + jb; r0 < nu; r0 += PTILE) {
-        const int nr = min(PTILE, nu - r0);
-        stage_rows(M, ld, r0, nr, J, jb, S);
+    float* Li = Tinv + ((int64_t)e * npanels + J / NBP) * 2 * NBP * NBP;
+    float* Ui = Li + NBP * NBP;
+    // column t of L^{-1}: x_t = 1, x_i = -sum_{k=t..i-1} L_ik x_k (i > t)
+    {
+        float x[NBP];
+#pragma unroll
+        for (int i = 0; i < NBP; ++i) {
+            float v = i == t ? 1.f : 0.f;
+            if (i > t) {
+#pragma unroll
+                for (int k = 0; k < i; ++k)
+                    if (k >= t) v -= D[i][k] * x[k];
+            }
+            x[i] = v;
+        }
+#pragma unroll
+        for (int i = 0; i < NBP; ++i) Li[i * NBP + t] = x[i];
+    }
+    // column t of U^{-1}: x_i = 0 (i > t), x_t = 1 / U_tt, x_i = -(sum_{k=i+1..t} U_ik x_k) / U_ii
+    {
+        float x[NBP];
+#pragma unroll
+        for (int ii = 0; ii < NBP; ++ii) {
+            const int i = NBP - 1 - ii;
+            float v = 0.f;
+            if (i == t) {
+                v = 1.f / D[i][i];
+            } else if (i < t) {
+                float s = 0.f;
+#pragma unroll
+                for (int k = i + 1; k < NBP; ++k)
+                    if (k <= t) s += D[i][k] * x[k];
+                v = -s / D[i][i];
+            }
+            x[i] = v;
+        }
+#pragma unroll
+        for (int i = 0; i < NBP; ++i) Ui[i * NBP + t] = x[i];
+    }
+}
+
+// Row/column work of one panel.  Tiles 0 .. nrt-1 are row tiles over rows [r_begin, r_end), the
+// remaining ones column tiles over columns [c_begin, c_end).
+//   row_mode 0: x = a U11^{-1} written to M and to the L split buffers (factorisation);
+//   row_mode 1: rows copied into the L split buffers (sweeps).
+//   col_mode 0: y = L11^{-1} a (factorisation and forward sweep); 1: y = U11^{-1} a (backward sweep);
+//   y goes back to M and, transposed, to the U split buffers.
+__global__ void __launch_bounds__(256, 2) k_rowcol(int nu, int64_t ld, int64_t estride, float* __restrict__ Mall, int J,
+                                                   int jb, const float* __restrict__ Tinv, int npanels, int r_begin,
+                                                   int r_end, int row_mode, int nrt, int c_begin, int c_end,
+                                                   int col_mode, float* __restrict__ Lh, float* __restrict__ Ll,
+                                                   float* __restrict__ Uh, float* __restrict__ Ul) {
+    extern __shared__ float sm[];
+    float* S = sm;                 // PTILE x TS staging
+    float* T = sm + PTILE * TS;    // 64 x TS inverse
+    const int64_t e = blockIdx.x;
+    float* M = Mall + e * estride;
+    const int tile = blockIdx.y;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, t = threadIdx.x;
+    const float* Li = Tinv + ((int64_t)e * npanels + J / NBP) * 2 * NBP * NBP;
+    if (tile < nrt) {
+        const int r0 = r_begin + tile * PTILE;
+        const int nr = min(PTILE, r_end - r0);
+        float* lh = Lh + e * (int64_t)nu * NBP;
+        float* ll = Ll + e * (int64_t)nu * NBP;
+        if (row_mode == 1) {
+            for (int r = r0 + warp; r < r0 + nr; r += 8) {
+                const float* src = M + (int64_t)r * ld + J;
+                for (int j = lane; j < NBP; j += 32) put_split(lh, ll, (int64_t)r * NBP + j, j < jb ? src[j] : 0.f);
+            }
+            return;
+        }
+        const float* Ui = Li + NBP * NBP;
+        for (int idx = t; idx < NBP * NBP; idx += 256) T[(idx / NBP) * TS + idx % NBP] = Ui[idx];
+        for (int rr = warp; rr < nr; rr += 8) {
+            const float* src = M + (int64_t)(r0 + rr) * ld + J;
+            for (int j = lane; j < NBP; j += 32) S[rr * TS + j] = j < jb ? src[j] : 0.f;
+        }
         __syncthreads();
-        const int t = threadIdx.x;
         if (t < nr) {
             float x[NBP];
 #pragma unroll
-            for (int j = 0; j < NBP; ++j) x[j] = S[t * TS + j];
+            for (int j = 0; j < NBP; ++j) x[j] = 0.f;
+            for (int i = 0; i < NBP; ++i) {  // x_j += a_i Uinv[i][j], j >= i
+                const float ai = S[t * TS + i];
 #pragma unroll
-            for (int j = 0; j < NBP; ++j) {
-                if (j < jb) {
-                    float s = x[j];
-#pragma unroll
-                    for (int i = 0; i < j; ++i) s -= x[i] * D[i][j];
-                    x[j] = s / D[j][j];
-                }
+                for (int j = 0; j < NBP; ++j)
+                    if (j >= i) x[j] = fmaf(ai, T[i * TS + j], x[j]);
             }
 #pragma unroll
             for (int j = 0; j < NBP; ++j) S[t * TS + j] = x[j];
         }
         __syncthreads();
-        unstage_rows(M, ld, r0, nr, J, jb, S, lh, ll, true);
-        __syncthreads();
+        for (int rr = warp; rr < nr; rr += 8) {
+            for (int j = lane; j < NBP; j += 32) {
+                const float v = S[rr * TS + j];
+                if (j < jb) M[(int64_t)(r0 + rr) * ld + J + j] = v;
+                put_split(lh, ll, (int64_t)(r0 + rr) * NBP + j, v);
+            }
+        }
+        return;
     }
-    // U12 = L11^{-1} A12 (unit lower): also the forward substitution of the right-hand sides
-    column_solves(M, ld, J, jb, J + jb, ncols, D, S, uh, ul, 0);
-}
-
-// Forward-sweep panel of a re-solve: y_J = L_JJ^{-1} y_J on the right-hand-side columns and the
-// split copies of L21 (rows J+jb..nu) and of y_J^T.
-__global__ void __launch_bounds__(256) k_fwd_panel(int nu, int nin, int64_t ld, int64_t estride, float* __restrict__ Mall,
-                                                   int J, int jb, float* __restrict__ Lh, float* __restrict__ Ll,
-                                                   float* __restrict__ Uh, float* __restrict__ Ul) {
-    __shared__ float D[NBP][TS];
-    extern __shared__ float S[];
-    const int64_t e = blockIdx.x;
-    float* M = Mall + e * estride;
-    load_diag(M, ld, J, jb, D, false);
-    split_rows(M, ld, J + jb, nu, J, jb, Lh + e * (int64_t)nu * NBP, Ll + e * (int64_t)nu * NBP);
+    const int c0 = c_begin + (tile - nrt) * PTILE;
+    const int nc = min(PTILE, c_end - c0);
+    const float* Ti = col_mode == 0 ? Li : Li + NBP * NBP;
+    for (int idx = t; idx < NBP * NBP; idx += 256) T[(idx / NBP) * TS + idx % NBP] = Ti[idx];
     __syncthreads();
-    column_solves(M, ld, J, jb, nu, nu + nin, D, S, Uh + e * ld * NBP, Ul + e * ld * NBP, 0);
-}
-
-// Backward-sweep panel: x_J = U_JJ^{-1} y_J on the right-hand-side columns, split copies of the
-// U column block above the panel (rows 0..J) and of x_J^T.
-__global__ void __launch_bounds__(256) k_back_panel(int nu, int nin, int64_t ld, int64_t estride, float* __restrict__ Mall,
-                                                    int J, int jb, float* __restrict__ Lh, float* __restrict__ Ll,
-                                                    float* __restrict__ Uh, float* __restrict__ Ul) {
-    __shared__ float D[NBP][TS];
-    extern __shared__ float S[];
-    const int64_t e = blockIdx.x;
-    float* M = Mall + e * estride;
-    load_diag(M, ld, J, jb, D, true);
-    split_rows(M, ld, 0, J, J, jb, Lh + e * (int64_t)nu * NBP, Ll + e * (int64_t)nu * NBP);
+    if (t < nc) {
+        const int c = c0 + t;
+        float y[NBP];
+#pragma unroll
+        for (int i = 0; i < NBP; ++i) y[i] = 0.f;
+        for (int k = 0; k < NBP; ++k) {  // y_i += Tinv[i][k] a_k
+            const float ak = k < jb ? M[(int64_t)(J + k) * ld + c] : 0.f;
+            if (col_mode == 0) {
+#pragma unroll
+                for (int i = 0; i < NBP; ++i)
+                    if (i >= k) y[i] = fmaf(T[i * TS + k], ak, y[i]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < NBP; ++i)
+                    if (i <= k) y[i] = fmaf(T[i * TS + k], ak, y[i]);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < NBP; ++i) {
+            if (i < jb) M[(int64_t)(J + i) * ld + c] = y[i];
+            S[t * TS + i] = y[i];
+        }
+    }
     __syncthreads();
-    column_solves(M, ld, J, jb, nu, nu + nin, D, S, Uh + e * ld * NBP, Ul + e * ld * NBP, 1);
+    float* uh = Uh + e * ld * NBP;
+    float* ul = Ul + e * ld * NBP;
+    for (int cc = warp; cc < nc; cc += 8)
+        for (int i = lane; i < NBP; i += 32) put_split(uh, ul, (int64_t)(c0 + cc) * NBP + i, S[cc * TS + i]);
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -458,77 +448,95 @@ elrt_status prepare(elrt_ctx* ctx, const float* Lh, const float* Ll, const float
     static bool attr_done = false;
     if (!attr_done) {
         cudaError_t e = cudaFuncSetAttribute(k_tc_update, cudaFuncAttributeMaxDynamicSharedMemorySize, UpdSmem::TOTAL);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, PANEL_SMEM);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_fwd_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, PANEL_SMEM);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_back_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, PANEL_SMEM);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rowcol, cudaFuncAttributeMaxDynamicSharedMemorySize, RC_SMEM);
         if (e != cudaSuccess) return cuda_check(ctx, e, "smem attribute");
         attr_done = true;
     }
     return ELRT_OK;
 }
 
+int panels_of(int nu) { return (nu + NBP - 1) / NBP; }
+
+elrt_status rowcol(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, int64_t E, int J, int jb, const float* Tinv,
+                   int r_begin, int r_end, int row_mode, int c_begin, int c_end, int col_mode, float* Lh, float* Ll,
+                   float* Uh, float* Ul) {
+    const int nrt = r_end > r_begin ? (r_end - r_begin + PTILE - 1) / PTILE : 0;
+    const int nct = c_end > c_begin ? (c_end - c_begin + PTILE - 1) / PTILE : 0;
+    if (nrt + nct == 0) return ELRT_OK;
+    ProfScope ps(ctx, "lu_tc_panel");
+    k_rowcol<<<dim3((unsigned)E, nrt + nct), 256, RC_SMEM, ctx->stream>>>(
+        ctx->tab.nu, ld, estride, M, J, jb, Tinv, panels_of(ctx->tab.nu), r_begin, r_end, row_mode, nrt, c_begin, c_end,
+        col_mode, Lh, Ll, Uh, Ul);
+    return cuda_check(ctx, cudaGetLastError(), "rowcol launch");
+}
+
 elrt_status backward_sweep_tc(elrt_ctx* ctx, const TcMaps& mp, float* M, int64_t ld, int64_t estride, int64_t E,
-                              float* Lh, float* Ll, float* Uh, float* Ul, int* err) {
+                              const float* Tinv, float* Lh, float* Ll, float* Uh, float* Ul, int* err) {
     const int nu = ctx->tab.nu, nin = ctx->tab.nin;
     const int last = ((nu - 1) / NBP) * NBP;
     for (int J = last; J >= 0; J -= NBP) {
         const int jb = std::min(NBP, nu - J);
-        {
-            ProfScope ps(ctx, "lu_tc_panel");
-            k_back_panel<<<(unsigned)E, 256, PANEL_SMEM, ctx->stream>>>(nu, nin, ld, estride, M, J, jb, Lh, Ll, Uh, Ul);
-        }
-        elrt_status s = update(ctx, mp, M, ld, estride, E, 0, J, nu, nu + nin, err);
+        elrt_status s = rowcol(ctx, M, ld, estride, E, J, jb, Tinv, 0, J, 1, nu, nu + nin, 1, Lh, Ll, Uh, Ul);
+        if (!s) s = update(ctx, mp, M, ld, estride, E, 0, J, nu, nu + nin, err);
         if (s) return s;
     }
-    return cuda_check(ctx, cudaGetLastError(), "backward sweep");
+    return ELRT_OK;
+}
+
+struct Side {
+    float *Lh, *Ll, *Uh, *Ul, *Tinv;
+};
+
+Side carve(float* side, int64_t E, int nu, int64_t ld) {
+    Side sd;
+    sd.Lh = side;
+    sd.Ll = sd.Lh + (size_t)E * nu * NBP;
+    sd.Uh = sd.Ll + (size_t)E * nu * NBP;
+    sd.Ul = sd.Uh + (size_t)E * ld * NBP;
+    sd.Tinv = sd.Ul + (size_t)E * ld * NBP;
+    return sd;
 }
 
 }  // namespace
 
 // Factor every element's matrix without pivoting and solve for its right-hand sides (columns
-// [nu, nu + nin)).  side: 4 buffers of E x max(nu, ld) x 64 floats.  estat[e] |= 1 on a tiny pivot.
+// [nu, nu + nin)).  side: tc_lu_side_floats() floats per element.  estat[e] |= 1 on a tiny pivot.
 elrt_status tc_lu_factor_solve(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, int64_t E, int* estat, float* side,
                                int* err) {
     const int nu = ctx->tab.nu, nin = ctx->tab.nin, ncols = nu + nin;
-    float* Lh = side;
-    float* Ll = Lh + (size_t)E * nu * NBP;
-    float* Uh = Ll + (size_t)E * nu * NBP;
-    float* Ul = Uh + (size_t)E * ld * NBP;
+    const Side sd = carve(side, E, nu, ld);
     TcMaps mp;
-    elrt_status s = prepare(ctx, Lh, Ll, Uh, Ul, ld, E, &mp);
+    elrt_status s = prepare(ctx, sd.Lh, sd.Ll, sd.Uh, sd.Ul, ld, E, &mp);
     if (s) return s;
     for (int J = 0; J < nu; J += NBP) {
         const int jb = std::min(NBP, nu - J);
         {
             ProfScope ps(ctx, "lu_tc_panel");
-            k_panel<<<(unsigned)E, 256, PANEL_SMEM, ctx->stream>>>(nu, ncols, ld, estride, M, J, jb, Lh, Ll, Uh, Ul, estat, 1e-6f);
+            k_diag<<<(unsigned)E, 64, 0, ctx->stream>>>(nu, ld, estride, M, J, jb, sd.Tinv, panels_of(nu), estat, 1e-6f);
         }
-        s = update(ctx, mp, M, ld, estride, E, J + jb, nu, J + jb, ncols, err);
+        s = rowcol(ctx, M, ld, estride, E, J, jb, sd.Tinv, J + jb, nu, 0, J + jb, ncols, 0, sd.Lh, sd.Ll, sd.Uh, sd.Ul);
+        if (!s) s = update(ctx, mp, M, ld, estride, E, J + jb, nu, J + jb, ncols, err);
         if (s) return s;
     }
-    return backward_sweep_tc(ctx, mp, M, ld, estride, E, Lh, Ll, Uh, Ul, err);
+    return backward_sweep_tc(ctx, mp, M, ld, estride, E, sd.Tinv, sd.Lh, sd.Ll, sd.Uh, sd.Ul, err);
 }
 
 // Re-solve A D = R for the right-hand sides in columns [nu, nu + nin) with the stored factors.
 elrt_status tc_lu_resolve(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, int64_t E, float* side, int* err) {
     const int nu = ctx->tab.nu, nin = ctx->tab.nin;
-    float* Lh = side;
-    float* Ll = Lh + (size_t)E * nu * NBP;
-    float* Uh = Ll + (size_t)E * nu * NBP;
-    float* Ul = Uh + (size_t)E * ld * NBP;
+    const Side sd = carve(side, E, nu, ld);
     TcMaps mp;
-    elrt_status s = prepare(ctx, Lh, Ll, Uh, Ul, ld, E, &mp);
+    elrt_status s = prepare(ctx, sd.Lh, sd.Ll, sd.Uh, sd.Ul, ld, E, &mp);
     if (s) return s;
     for (int J = 0; J < nu; J += NBP) {
         const int jb = std::min(NBP, nu - J);
-        {
-            ProfScope ps(ctx, "lu_tc_panel");
-            k_fwd_panel<<<(unsigned)E, 256, PANEL_SMEM, ctx->stream>>>(nu, nin, ld, estride, M, J, jb, Lh, Ll, Uh, Ul);
-        }
-        s = update(ctx, mp, M, ld, estride, E, J + jb, nu, nu, nu + nin, err);
+        s = rowcol(ctx, M, ld, estride, E, J, jb, sd.Tinv, J + jb, nu, 1, nu, nu + nin, 0, sd.Lh, sd.Ll, sd.Uh, sd.Ul);
+        if (!s) s = update(ctx, mp, M, ld, estride, E, J + jb, nu, nu, nu + nin, err);
         if (s) return s;
     }
-    return backward_sweep_tc(ctx, mp, M, ld, estride, E, Lh, Ll, Uh, Ul, err);
+    return backward_sweep_tc(ctx, mp, M, ld, estride, E, sd.Tinv, sd.Lh, sd.Ll, sd.Uh, sd.Ul, err);
 }
 
-size_t tc_lu_side_floats(const Tab& t, int64_t ld) { return (size_t)2 * NBP * (t.nu + ld); }
+size_t tc_lu_side_floats(const Tab& t, int64_t ld) {
+    return (size_t)2 * NBP * (t.nu + ld) + (size_t)panels_of(t.nu) * 2 * NBP * NBP;
+}

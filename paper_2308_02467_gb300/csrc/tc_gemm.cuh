@@ -240,22 +240,38 @@ ep.out_bf_t[(size_t)(n0c + j) * ep.ld_t + m] = __float2bfloat16_rn(v[j]);
 dst[j] = v[j];
         }
     } else if (mode == EPI_LOSS) {
-        _Pragma("unroll") for (int j = 0; j < 16; ++j) if (n0c + j < N) {
-            const int n = n0c + j;
-            const float y = v[j] + ep.bias[n];
-            const float d = y - ep.target[(size_t)m * ep.ld_out + n];
-            lsum += fabsf(d);
-            v[j] = d > 0.f ? ep.loss_scale : (d < 0.f ? -ep.loss_scale : 0.f);
+        float tg[16];
+        if (full) {
+            const float4* src = reinterpret_cast<const float4*>(ep.target + (size_t)m * ep.ld_out + n0c);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float4 v4 = src[q];
+                tg[4 * q] = v4.x;
+                tg[4 * q + 1] = v4.y;
+                tg[4 * q + 2] = v4.z;
+                tg[4 * q + 3] = v4.w;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) tg[j] = n0c + j < N ? ep.target[(size_t)m * ep.ld_out + n0c + j] : 0.f;
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            if (n0c + j < N) {
+                const float y = v[j] + ep.bias[n0c + j];
+                const float d = y - tg[j];
+                lsum += fabsf(d);
+                v[j] = d > 0.f ? ep.loss_scale : (d < 0.f ? -ep.loss_scale : 0.f);
+            }
         }
         if (full) {
             st_bf16x16(ep.out_bf + (size_t)m * ep.ld_out + n0c, v);
         } else {
-            _Pragma("unroll") for (int j = 0; j < 16; ++j) if (n0c + j < N)
-ep.out_bf[(size_t)m * ep.ld_out + n0c + j] = __float2bfloat16_rn(v[j]);
+            _Pragma("unroll") for (int j = 0; j < 16; ++j) if (n0c + j < N) ep.out_bf[(size_t)m * ep.ld_out + n0c + j] = __float2bfloat16_rn(v[j]);
         }
         if (ep.out_bf_t)
             _Pragma("unroll") for (int j = 0; j < 16; ++j) if (n0c + j < N)
-ep.out_bf_t[(size_t)(n0c + j) * ep.ld_t + m] = __float2bfloat16_rn(v[j]);
+                ep.out_bf_t[(size_t)(n0c + j) * ep.ld_t + m] = __float2bfloat16_rn(v[j]);
     } else {  // EPI_DACT
         _Pragma("unroll") for (int j = 0; j < 16; ++j) if (n0c + j < N) {
             const float z = __bfloat162float(ep.z_in[(size_t)m * ep.ld_out + n0c + j]);
