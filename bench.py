@@ -289,8 +289,8 @@ def run_ours(args, rank, world, local_rank):
     um_h = torch.empty(n, ctx.nm, dtype=torch.float64).pin_memory()
     info = {}
 
-    def step(k_, o_, g_):
-        lst = ctx.elrt_build_local(k_, o_, prob.h, i2o, i2m, mode=mode, refine_steps=args.refine)
+    def step(k_, o_, g_, with_stats=False):
+        lst = ctx.elrt_build_local(k_, o_, prob.h, i2o, i2m, mode=mode, refine_steps=args.refine, stats=with_stats)
         gst = ctx.elrt_solve_global(nx, nz, i2o, g_, sk, rtol=args.rtol, max_iter=20000, restart=50)
         ctx.elrt_recover_mean(nx, nz, i2m, sk, g_, um)
         info["local"], info["global"] = lst, gst
@@ -300,6 +300,8 @@ def run_ours(args, rank, world, local_rank):
             td.barrier()
 
     stream = torch.cuda.current_stream()
+    step(kap, om, g, with_stats=True)          # untimed: statistics of the local stage
+    local_stats = info["local"]
     for _ in range(args.warmup):
         step(kap, om, g)
     torch.cuda.synchronize()
@@ -364,7 +366,7 @@ def run_ours(args, rank, world, local_rank):
         peak = 152 * 4 * clk_max * 1e6 / 1e12           # FP64: 2 FMA/clk/SM (1.26 TFLOP/s)
         peak_note = f"FP64 peak derived: 152 SMs x 2 FMA x 2 flop x {clk_max:g} MHz"
     total_prof = sum(v[0] for v in prof.values())
-    gst, lst = info["global"], info["local"]
+    gst, lst = info["global"], local_stats
     val = world * n / (ms / 1000.0)
     out = {
         "metric": "elements/s (classical element pipeline: local operators + skeleton GMRES + mean recovery)",

@@ -206,6 +206,56 @@ elrt_status elrt_solve_global(elrt_ctx* ctx, int32_t nx, int32_t nz, const void*
 elrt_status elrt_recover_mean(elrt_ctx* ctx, int32_t nx, int32_t nz, const void* in2sol, int32_t dtype,
                               const double* skeleton, const double* inflow, double* mean);
 
+/* ---------------------------------------------------------------- whole pipeline (Algorithm 1) */
+
+/* One field: an nx x nz mesh of square elements of side h (km) with its coefficients and
+ * boundary data (all device pointers, layouts as above). */
+typedef struct {
+    int32_t nx, nz;
+    double h;
+    const double* kappa;    /* [nx nz][(p+1)^2] km^-1 at the LGL nodes */
+    const double* omega;    /* [nx nz] */
+    const double* inflow;   /* boundary inflow, length elrt_n_inflow */
+} elrt_field;
+
+typedef struct elrt_net elrt_net;
+
+typedef struct {
+    int32_t mode;           /* elrt_local_mode of the classical local stage */
+    int32_t refine_steps;   /* FP64-class refinement steps (IR modes) */
+    double rtol;            /* GMRES relative residual */
+    int32_t max_iter;
+    int32_t restart;
+    elrt_net* net;          /* non-NULL: learned local stage (elrt_build_local_learned) */
+    double learned_tol;     /* its energy-balance fallback threshold */
+} elrt_solve_opts;
+
+typedef struct {
+    elrt_local_stats local;
+    elrt_solve_stats global;
+    int64_t n_fallback;     /* learned stage: elements re-solved classically */
+    double local_ms, global_ms;
+} elrt_field_stats;
+
+/* Algorithm 1 on one field: local operators (FP32 in2out / in2sol in the context's workspace),
+ * skeleton GMRES, mean intensity.  mean: device [nx nz][(p+1)^2] FP64; skeleton: device
+ * [nx nz][n_out] FP64 or NULL.  Synchronises; ELRT_ENOCONV if GMRES stopped at max_iter (the mean
+ * of the last iterate is still written). */
+elrt_status elrt_solve_field(elrt_ctx* ctx, const elrt_field* field, const elrt_solve_opts* opts, double* mean,
+                             double* skeleton, elrt_field_stats* stats);
+
+/* Many independent fields of uneven sizes and degrees in one call.  ctxs[k] (k < n_ctx) are
+ * contexts of distinct discretisations; field f uses ctxs[field_ctx[f]].  Fields are processed in
+ * waves whose operators fit in wave_bytes of device memory (0: 64 GiB): within a wave the local
+ * stages of all fields that share a discretisation run as one batched build (one launch sequence),
+ * then the skeleton solves run concurrently on up to `workers` streams (0: 8), each with its own
+ * workspace.  means[f]: device [nx nz][(p+1)^2]; stats (host, may be NULL) [n_fields].
+ * Synchronises; returns the first non-OK status (a wave in which a local stage fails is the last
+ * one attempted; a field whose GMRES stops at max_iter still gets its mean). */
+elrt_status elrt_solve_batch(elrt_ctx* const* ctxs, int32_t n_ctx, const elrt_field* fields, const int32_t* field_ctx,
+                             int32_t n_fields, const elrt_solve_opts* opts, size_t wave_bytes, int32_t workers,
+                             double* const* means, elrt_field_stats* stats);
+
 /* ---------------------------------------------------------------- element network (Sec. 2.4) */
 
 /* The learned local solver of eq. param2sol: a fully connected network (Sec. 2.4.1)
@@ -219,8 +269,6 @@ elrt_status elrt_recover_mean(elrt_ctx* ctx, int32_t nx, int32_t nz, const void*
  * with BF16 copies; every GEMM runs on tcgen05 (BF16 in, FP32 accumulate); training minimises the
  * mean absolute error with Adam (Sec. 3.1).  All calls are asynchronous on the network's stream
  * unless stated. */
-typedef struct elrt_net elrt_net;
-
 typedef struct {
     int32_t p;            /* element discretisation the network is built for */
     int32_t n_angles;

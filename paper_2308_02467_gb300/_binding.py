@@ -45,6 +45,21 @@ class TrainOpts(C.Structure):
                 ("beta2", C.c_float), ("eps", C.c_float), ("seed", C.c_uint64)]
 
 
+class Field(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("nz", C.c_int32), ("h", C.c_double), ("kappa", C.c_void_p),
+                ("omega", C.c_void_p), ("inflow", C.c_void_p)]
+
+
+class SolveOpts(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("refine_steps", C.c_int32), ("rtol", C.c_double), ("max_iter", C.c_int32),
+                ("restart", C.c_int32), ("net", C.c_void_p), ("learned_tol", C.c_double)]
+
+
+class FieldStats(C.Structure):
+    _fields_ = [("local", LocalStats), ("glob", SolveStats), ("n_fallback", C.c_int64), ("local_ms", C.c_double),
+                ("global_ms", C.c_double)]
+
+
 class ElrtError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -76,6 +91,9 @@ _sig = {
     "elrt_profile_get": (_i32, [_vp, C.c_char_p, _P(_d), _P(_i64)]),
     "elrt_launch_count": (_i64, [_vp]),
     "elrt_build_local_static": (_i32, [_P(Disc), _vp, _i64, _d, _vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp]),
+    "elrt_solve_field": (_i32, [_vp, _P(Field), _P(SolveOpts), _vp, _vp, _P(FieldStats)]),
+    "elrt_solve_batch": (_i32, [_P(_vp), _i32, _P(Field), _P(_i32), _i32, _P(SolveOpts), C.c_size_t, _i32, _P(_vp),
+                                 _P(FieldStats)]),
     "elrt_net_create": (_i32, [_P(_vp), _P(NetDesc), _vp]),
     "elrt_net_destroy": (_i32, [_vp]),
     "elrt_net_set_stream": (_i32, [_vp, _vp]),
@@ -285,6 +303,21 @@ class Context:
         _check(s, self._h)
         return st
 
+    def elrt_solve_field(self, nx, nz, h, kappa, omega, inflow, mean, skeleton=None, mode=LOCAL_FP32_IR,
+                         refine_steps=1, rtol=1e-8, max_iter=20000, restart=50, net=None, learned_tol=1e-3,
+                         raise_on_noconv=True):
+        import torch
+        E = nx * nz
+        self._sync_stream()
+        f = _field(self, nx, nz, h, kappa, omega, inflow)
+        o = _opts(mode, refine_steps, rtol, max_iter, restart, net, learned_tol)
+        st = FieldStats()
+        s = _lib.elrt_solve_field(self._h, C.byref(f), C.byref(o), _ptr(mean, torch.float64, E * self.nm, "mean"),
+                                  _ptr(skeleton, torch.float64, E * self.nin, "skeleton"), C.byref(st))
+        if not (s == 4 and not raise_on_noconv):
+            _check(s, self._h)
+        return st
+
     def elrt_recover_mean(self, nx, nz, in2sol, skeleton, inflow, mean):
         import torch
         E = nx * nz
@@ -405,3 +438,34 @@ def elrt_build_local_learned(ctx, net, kappa, omega, h, in2out, in2sol, tol=1e-3
         _ptr(in2sol, torch.float32, n * ctx.nm * ctx.nin, "in2sol"),
         _ptr(estimate, torch.float32, n, "estimate"), C.byref(nf)), ctx._h)
     return nf.value
+
+
+def _field(ctx, nx, nz, h, kappa, omega, inflow):
+    import torch
+    E = nx * nz
+    return Field(int(nx), int(nz), float(h), _ptr(kappa, torch.float64, E * ctx.nm, "kappa"),
+                 _ptr(omega, torch.float64, E, "omega"),
+                 _ptr(inflow, torch.float64, 2 * (nx + nz) * (ctx.p + 1) * (ctx.n_angles // 2), "inflow"))
+
+
+def _opts(mode, refine_steps, rtol, max_iter, restart, net, learned_tol):
+    return SolveOpts(int(mode), int(refine_steps), float(rtol), int(max_iter), int(restart),
+                     net._h if net is not None else None, float(learned_tol))
+
+
+def elrt_solve_batch(ctxs, fields, field_ctx, means, mode=LOCAL_FP32_IR, refine_steps=1, rtol=1e-8, max_iter=20000,
+                     restart=50, net=None, learned_tol=1e-3, wave_bytes=0, workers=0):
+    """Many uneven fields: fields[f] = (nx, nz, h, kappa, omega, inflow) tensors; field_ctx[f] indexes ctxs.
+    Returns the per-field FieldStats."""
+    import torch
+    for c in ctxs:
+        c._sync_stream()
+    n = len(fields)
+    F = (Field * max(n, 1))(*[_field(ctxs[field_ctx[i]], *fields[i]) for i in range(n)])
+    fc = (C.c_int32 * max(n, 1))(*field_ctx)
+    hs = (C.c_void_p * len(ctxs))(*[c._h.value for c in ctxs])
+    ms = (C.c_void_p * max(n, 1))(*[_ptr(means[i], torch.float64, None, "mean") for i in range(n)])
+    st = (FieldStats * max(n, 1))()
+    o = _opts(mode, refine_steps, rtol, max_iter, restart, net, learned_tol)
+    _check(_lib.elrt_solve_batch(hs, len(ctxs), F, fc, n, C.byref(o), int(wave_bytes), int(workers), ms, st))
+    return list(st)[:n]

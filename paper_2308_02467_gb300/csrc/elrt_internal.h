@@ -48,6 +48,10 @@ struct elrt_ctx {
     size_t ws_bytes = 0;
     void* gm = nullptr;     // GMRES workspace
     size_t gm_bytes = 0;
+    void* ops = nullptr;    // in2out / in2sol of elrt_solve_field
+    size_t ops_bytes = 0;
+    void* vec = nullptr;    // skeleton of elrt_solve_field when the caller passes none
+    size_t vec_bytes = 0;
     int* d_flags = nullptr; // small device scratch for flags/counters
     double* h_pinned = nullptr;  // pinned host scratch for small read-backs
     // measurement
@@ -95,3 +99,9 @@ elrt_status global_solve(elrt_ctx* ctx, int nx, int nz, const void* A, int dtype
                          elrt_solve_stats* stats);
 elrt_status global_recover(elrt_ctx* ctx, int nx, int nz, const void* A, int dtype, const double* x,
                            const double* inflow, double* mean);
+
+// ---- learned local stage (mlp.cu)
+extern "C" elrt_status elrt_build_local_learned(elrt_ctx* ctx, elrt_net* net, int64_t n, double h, const double* h_elem,
+                                                const double* kappa, const double* omega, double tol, float* in2out,
+                                                float* in2sol, float* estimate, int64_t* n_fallback);
+bool elrt_net_matches(const elrt_net* net, const elrt_disc* disc);

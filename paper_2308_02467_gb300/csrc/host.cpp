@@ -360,6 +360,8 @@ elrt_status elrt_destroy(elrt_ctx* ctx) {
     for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->gm) cudaFree(ctx->gm);
+    if (ctx->ops) cudaFree(ctx->ops);
+    if (ctx->vec) cudaFree(ctx->vec);
     if (ctx->d_flags) cudaFree(ctx->d_flags);
     if (ctx->h_pinned) cudaFreeHost(ctx->h_pinned);
     delete ctx;

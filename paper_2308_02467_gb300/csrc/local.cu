@@ -404,6 +404,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_lu_resolve(Tab t, T* __restrict
 // ------------------------------------------------------------------------------------------------
 
 // mode 0: X64 = (double) src;  mode 1: X64 += (double) src.  Afterwards R -> src (as T).
+// mode 2: X64 += (double) src only (the final correction when no residual is wanted).
 // One block per element; columns in chunks of CWR staged in shared memory as float-float pairs,
 // every product and sum in float-float (about 44 bits, at FP32 issue rate).
 template <typename T>
@@ -460,8 +461,9 @@ __global__ void __launch_bounds__(kThreads) k_residual(Tab t, double h, const do
                 v = (mode == 0) ? d : X64[(int64_t)r * nin + col] + d;
                 X64[(int64_t)r * nin + col] = v;
             }
-            Xs[r * CWR + tcol] = ff_from_double(v);
+            if (mode != 2) Xs[r * CWR + tcol] = ff_from_double(v);
         }
+        if (mode == 2) continue;
         __syncthreads();
         for (int r = trow; r < nu; r += rows_per_pass) {
             const int col = cs + tcol;
@@ -504,7 +506,7 @@ __global__ void __launch_bounds__(kThreads) k_residual(Tab t, double h, const do
     for (int off = 16; off > 0; off >>= 1) rmax = fmax(rmax, __shfl_down_sync(0xffffffffu, rmax, off));
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = rmax;
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x == 0 && mode != 2) {
         double m = 0.0;
         for (int w = 0; w < kThreads / 32; ++w) m = fmax(m, red[w]);
         maxres[e] = m;
@@ -716,6 +718,8 @@ elrt_status build_chunked(elrt_ctx* ctx, int64_t E, double h, const double* h_el
         void* o_i2m = (unsigned char*)in2sol + (size_t)e0 * t.nm * t.nin * osz;
         if (want_res) {
             s = run_residual<T>(ctx, h, he, ka, om, M, ld, estride, X64, 0, maxres, n);
+            // the last correction needs no residual unless statistics or status words are wanted
+            const bool last_residual = stats || elem_status;
             for (int it = 0; it < (ir ? steps : 0) && !s; ++it) {
                 if constexpr (sizeof(T) == 4) {
                     if (tc) s = tc_lu_resolve(ctx, M, ld, estride, n, side, ctx->d_flags + 2);
@@ -724,12 +728,15 @@ elrt_status build_chunked(elrt_ctx* ctx, int64_t E, double h, const double* h_el
                     s = run_lu<T, NB, QN>(ctx, M, ld, estride, ipiv, estat, n, true);
                 }
                 if (s) break;
-                if (!s) s = run_residual<T>(ctx, h, he, ka, om, M, ld, estride, X64, 1, maxres, n);
+                s = run_residual<T>(ctx, h, he, ka, om, M, ld, estride, X64,
+                                    (it + 1 == steps && !last_residual) ? 2 : 1, maxres, n);
             }
             if (s) return s;
-            // flag elements whose residual exceeds 1e-10 max|B^|
-            ProfScope ps(ctx, "status");
-            k_flag_residual<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(maxres, estat, 1e-10 * bmax, n);
+            // flag elements whose residual exceeds 1e-10 max|B^| (when the last residual was computed)
+            if (!(ir && steps > 0 && !last_residual)) {
+                ProfScope ps(ctx, "status");
+                k_flag_residual<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(maxres, estat, 1e-10 * bmax, n);
+            }
             if (out_dtype == ELRT_F32)
                 s = run_restrict<double, float>(ctx, X64, t.nin, (int64_t)t.nu * t.nin, 0, (float*)o_i2o, (float*)o_i2m,
                                                 estat, n);

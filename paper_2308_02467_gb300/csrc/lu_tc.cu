@@ -53,8 +53,9 @@ __device__ __forceinline__ void put_split(float* hi, float* lo, int64_t idx, flo
 // ------------------------------------------------------------------------------------------------
 
 constexpr int TS = NBP + 1;
+constexpr int TI = NBP + 4;                                        // inverse row stride: 16-byte aligned rows
 constexpr int PTILE = 256;                                         // rows or columns per tile
-constexpr int RC_SMEM = (PTILE * TS + NBP * TS) * (int)sizeof(float);  // staging + one inverse
+constexpr int RC_SMEM = (PTILE * TS + NBP * TI) * (int)sizeof(float);  // staging + one inverse
 
 // Tinv layout per element: [panel][2][64][64]: [0] = L11^{-1} (unit lower), [1] = U11^{-1} (upper)
 __global__ void __launch_bounds__(64) k_diag(int nu, int64_t ld, int64_t estride, float* __restrict__ Mall, int J,
@@ -163,7 +164,7 @@ __global__ void __launch_bounds__(256, 2) k_rowcol(int nu, int64_t ld, int64_t e
             return;
         }
         const float* Ui = Li + NBP * NBP;
-        for (int idx = t; idx < NBP * NBP; idx += 256) T[(idx / NBP) * TS + idx % NBP] = Ui[idx];
+        for (int idx = t; idx < NBP * NBP; idx += 256) T[(idx / NBP) * TI + idx % NBP] = Ui[idx];
         for (int rr = warp; rr < nr; rr += 8) {
             const float* src = M + (int64_t)(r0 + rr) * ld + J;
             for (int j = lane; j < NBP; j += 32) S[rr * TS + j] = j < jb ? src[j] : 0.f;
@@ -173,11 +174,17 @@ __global__ void __launch_bounds__(256, 2) k_rowcol(int nu, int64_t ld, int64_t e
             float x[NBP];
 #pragma unroll
             for (int j = 0; j < NBP; ++j) x[j] = 0.f;
-            for (int i = 0; i < NBP; ++i) {  // x_j += a_i Uinv[i][j], j >= i
+            for (int i = 0; i < NBP; ++i) {  // x_j += a_i Uinv[i][j] (Uinv[i][j] = 0 for j < i)
                 const float ai = S[t * TS + i];
+                const float4* Tr = reinterpret_cast<const float4*>(T + i * TI);
 #pragma unroll
-                for (int j = 0; j < NBP; ++j)
-                    if (j >= i) x[j] = fmaf(ai, T[i * TS + j], x[j]);
+                for (int j4 = 0; j4 < NBP / 4; ++j4) {
+                    const float4 u = Tr[j4];
+                    x[4 * j4] = fmaf(ai, u.x, x[4 * j4]);
+                    x[4 * j4 + 1] = fmaf(ai, u.y, x[4 * j4 + 1]);
+                    x[4 * j4 + 2] = fmaf(ai, u.z, x[4 * j4 + 2]);
+                    x[4 * j4 + 3] = fmaf(ai, u.w, x[4 * j4 + 3]);
+                }
             }
 #pragma unroll
             for (int j = 0; j < NBP; ++j) S[t * TS + j] = x[j];
@@ -195,23 +202,23 @@ __global__ void __launch_bounds__(256, 2) k_rowcol(int nu, int64_t ld, int64_t e
     const int c0 = c_begin + (tile - nrt) * PTILE;
     const int nc = min(PTILE, c_end - c0);
     const float* Ti = col_mode == 0 ? Li : Li + NBP * NBP;
-    for (int idx = t; idx < NBP * NBP; idx += 256) T[(idx / NBP) * TS + idx % NBP] = Ti[idx];
+    for (int idx = t; idx < NBP * NBP; idx += 256) T[(idx % NBP) * TI + idx / NBP] = Ti[idx];  // transposed
     __syncthreads();
     if (t < nc) {
         const int c = c0 + t;
         float y[NBP];
 #pragma unroll
         for (int i = 0; i < NBP; ++i) y[i] = 0.f;
-        for (int k = 0; k < NBP; ++k) {  // y_i += Tinv[i][k] a_k
+        for (int k = 0; k < NBP; ++k) {  // y_i += Tinv[i][k] a_k (the inverse is triangular: zeros elsewhere)
             const float ak = k < jb ? M[(int64_t)(J + k) * ld + c] : 0.f;
-            if (col_mode == 0) {
+            const float4* Tc = reinterpret_cast<const float4*>(T + k * TI);
 #pragma unroll
-                for (int i = 0; i < NBP; ++i)
-                    if (i >= k) y[i] = fmaf(T[i * TS + k], ak, y[i]);
-            } else {
-#pragma unroll
-                for (int i = 0; i < NBP; ++i)
-                    if (i <= k) y[i] = fmaf(T[i * TS + k], ak, y[i]);
+            for (int i4 = 0; i4 < NBP / 4; ++i4) {
+                const float4 u = Tc[i4];
+                y[4 * i4] = fmaf(u.x, ak, y[4 * i4]);
+                y[4 * i4 + 1] = fmaf(u.y, ak, y[4 * i4 + 1]);
+                y[4 * i4 + 2] = fmaf(u.z, ak, y[4 * i4 + 2]);
+                y[4 * i4 + 3] = fmaf(u.w, ak, y[4 * i4 + 3]);
             }
         }
 #pragma unroll
@@ -393,11 +400,206 @@ __global__ void __launch_bounds__(UTHREADS, 2)
     }
 }
 
+// Row-strip variant: one block per (128-row block, element) keeps its L21 tile resident and walks
+// the column tiles of [c0, c_end) through a two-stage ring: warp 0 loads the next U12 tile (hi/lo)
+// and the C tile (fp32, 128-byte swizzle, two 32-column boxes) by TMA, warp 1 issues the 3xTF32
+// MMAs into one of two TMEM accumulators, warps 2-5 read the accumulator and the staged C tile,
+// subtract and store.  Stage s is free again after the MMA commit and the four epilogue warps
+// have arrived (count 5).
+struct StripSmem {
+    static constexpr int A_KB = 128 * 32 * 4;
+    static constexpr int B_KB = UBN * 32 * 4;
+    static constexpr int C_HALF = 128 * 32 * 4;               // one 32-column box of the C tile
+    static constexpr int A_BYTES = 4 * A_KB;                  // {hi, lo} x 2 k-blocks
+    static constexpr int STAGE = 4 * B_KB + 2 * C_HALF;       // B {hi, lo} x 2 k-blocks + C tile
+    static constexpr int BYTES = A_BYTES + 2 * STAGE;
+    static constexpr int TOTAL = BYTES + 1024 + 128;
+};
+
+__global__ void __launch_bounds__(192, 1)
+    k_tc_update_strip(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUtensorMap tAl,
+                      const __grid_constant__ CUtensorMap tBh, const __grid_constant__ CUtensorMap tBl,
+                      const __grid_constant__ CUtensorMap tC, float* __restrict__ Mall, int64_t ld, int64_t estride,
+                      int r0, int r_end, int c0, int c_end, int* __restrict__ err) {
+    extern __shared__ __align__(1024) unsigned char ssm_raw[];
+    unsigned char* base = (unsigned char*)(((uintptr_t)ssm_raw + 1023) & ~(uintptr_t)1023);
+    unsigned char* Ah = base;
+    unsigned char* Al = Ah + 2 * StripSmem::A_KB;
+    unsigned char* stage0 = base + StripSmem::A_BYTES;
+    uint64_t* a_full = (uint64_t*)(base + StripSmem::BYTES);
+    uint64_t* full = a_full + 1;       // [2]
+    uint64_t* empty = full + 2;        // [2]
+    uint64_t* acc_full = empty + 2;    // [2]
+    uint64_t* acc_empty = acc_full + 2;  // [2]
+    uint32_t* tmem_slot = (uint32_t*)(acc_empty + 2);
+    volatile int* abort = (volatile int*)(tmem_slot + 1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int e = blockIdx.y;
+    const int m0 = r0 + blockIdx.x * 128;
+    const int ntile = (c_end - c0 + UBN - 1) / UBN;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(a_full, 1);
+        for (int i = 0; i < 2; ++i) {
+            tc::mbar_init(&full[i], 1);
+            tc::mbar_init(&empty[i], 5);
+            tc::mbar_init(&acc_full[i], 1);
+            tc::mbar_init(&acc_empty[i], 4);
+        }
+        *abort = 0;
+        tc::fence_barrier_init();
+    }
+    if (warp == 1) {
+        tc::tmem_alloc(tmem_slot, 2 * UBN);
+        tc::tmem_relinquish();
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    int committed = 0;
+    if (warp == 0 && lane == 0) {
+        tc::mbar_expect_tx(a_full, StripSmem::A_BYTES);
+        for (int kb = 0; kb < 2; ++kb) {
+            tma_load_3d(&tAh, a_full, Ah + kb * StripSmem::A_KB, kb * 32, m0, e);
+            tma_load_3d(&tAl, a_full, Al + kb * StripSmem::A_KB, kb * 32, m0, e);
+        }
+        for (int t = 0; t < ntile; ++t) {
+            const int s = t & 1;
+            if (!tc::mbar_wait(&empty[s], ((t >> 1) & 1) ^ 1, abort)) {
+                if (err) atomicOr(err, 64);
+                *abort = 1;
+                break;
+            }
+            unsigned char* st = stage0 + s * StripSmem::STAGE;
+            const int n0 = c0 + t * UBN;
+            tc::mbar_expect_tx(&full[s], StripSmem::STAGE);
+            for (int kb = 0; kb < 2; ++kb) {
+                tma_load_3d(&tBh, &full[s], st + kb * StripSmem::B_KB, kb * 32, n0, e);
+                tma_load_3d(&tBl, &full[s], st + (2 + kb) * StripSmem::B_KB, kb * 32, n0, e);
+            }
+            tma_load_3d(&tC, &full[s], st + 4 * StripSmem::B_KB, n0, m0, e);
+            tma_load_3d(&tC, &full[s], st + 4 * StripSmem::B_KB + StripSmem::C_HALF, n0 + 32, m0, e);
+        }
+    } else if (warp == 1 && lane == 0) {
+        constexpr uint32_t idesc = idesc_tf32(128, UBN);
+        bool ok = tc::mbar_wait(a_full, 0, abort);
+        for (int t = 0; t < ntile && ok; ++t) {
+            const int s = t & 1, a = t & 1;
+            if (!tc::mbar_wait(&acc_empty[a], ((t >> 1) & 1) ^ 1, abort) || !tc::mbar_wait(&full[s], (t >> 1) & 1, abort)) {
+                ok = false;
+                break;
+            }
+            tc::tc_fence_after();
+            unsigned char* st = stage0 + s * StripSmem::STAGE;
+            const uint32_t d = tmem + (uint32_t)(a * UBN);
+            uint32_t acc = 0;
+            for (int kb = 0; kb < 2; ++kb) {
+                const uint64_t ah = tc::sw128_desc(tc::smem_u32(Ah + kb * StripSmem::A_KB));
+                const uint64_t al = tc::sw128_desc(tc::smem_u32(Al + kb * StripSmem::A_KB));
+                const uint64_t bh = tc::sw128_desc(tc::smem_u32(st + kb * StripSmem::B_KB));
+                const uint64_t bl = tc::sw128_desc(tc::smem_u32(st + (2 + kb) * StripSmem::B_KB));
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    mma_tf32(d, ah + 2 * k, bh + 2 * k, idesc, acc);
+                    acc = 1;
+                    mma_tf32(d, ah + 2 * k, bl + 2 * k, idesc, 1);
+                    mma_tf32(d, al + 2 * k, bh + 2 * k, idesc, 1);
+                }
+            }
+            tc::mma_commit(&empty[s]);
+            tc::mma_commit(&acc_full[a]);
+            ++committed;
+        }
+        if (!ok) {
+            if (err) atomicOr(err, 128);
+            *abort = 1;
+        }
+    } else if (warp >= 2) {
+        const int q = warp & 3;
+        const int row = q * 32 + lane;
+        const int m = m0 + row;
+        float* M = Mall + (int64_t)e * estride;
+        for (int t = 0; t < ntile; ++t) {
+            const int s = t & 1, a = t & 1;
+            const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(&acc_full[a], (t >> 1) & 1, abort) &&
+                                                        tc::mbar_wait(&full[s], (t >> 1) & 1, abort) && !*abort);
+            if (!ok) {
+                if (err && lane == 0) atomicOr(err, 256);
+                break;
+            }
+            tc::tc_fence_after();
+            const unsigned char* cst = stage0 + s * StripSmem::STAGE + 4 * StripSmem::B_KB;
+            const int n0 = c0 + t * UBN;
+            float d[UBN];
+#pragma unroll
+            for (int c = 0; c < UBN; c += 16) {
+                float v[16];
+                tc::tmem_ld16(tmem + (uint32_t)(a * UBN) + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
+#pragma unroll
+                for (int j = 0; j < 16; ++j) d[c + j] = v[j];
+            }
+            // C tile in shared memory: box half hb holds columns n0 + 32 hb .. + 31 of rows m0 .. m0 + 127,
+            // 128-byte rows with the 16-byte chunk index XOR-ed by (row % 8)
+            float out[UBN];
+#pragma unroll
+            for (int hb = 0; hb < 2; ++hb) {
+#pragma unroll
+                for (int ch = 0; ch < 8; ++ch) {
+                    const float4 cv = *reinterpret_cast<const float4*>(cst + hb * StripSmem::C_HALF + row * 128 +
+                                                                       ((ch ^ (row & 7)) << 4));
+                    const int c = hb * 32 + ch * 4;
+                    out[c] = cv.x - d[c];
+                    out[c + 1] = cv.y - d[c + 1];
+                    out[c + 2] = cv.z - d[c + 2];
+                    out[c + 3] = cv.w - d[c + 3];
+                }
+            }
+            tc::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) {
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&acc_empty[a])) : "memory");
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&empty[s])) : "memory");
+            }
+            if (m < r_end) {
+                float* dst = M + (int64_t)m * ld + n0;
+                if (n0 + UBN <= c_end) {
+#pragma unroll
+                    for (int c = 0; c < UBN; c += 4)
+                        *reinterpret_cast<float4*>(dst + c) = make_float4(out[c], out[c + 1], out[c + 2], out[c + 3]);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < UBN; ++c)
+                        if (n0 + c < c_end) dst[c] = out[c];
+                }
+            }
+        }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        if (lane == 0) {
+            if (committed > 0) {
+                const int last = committed - 1;
+                const long long t0 = clock64();
+                while (!tc::mbar_try_wait(&acc_full[last & 1], (last >> 1) & 1) && clock64() - t0 < tc::kWaitCycles) {
+                }
+            }
+            const long long t1 = clock64();  // the resident tile's copy
+            while (!tc::mbar_try_wait(a_full, 0) && clock64() - t1 < tc::kWaitCycles / 4) {
+            }
+        }
+        __syncwarp();
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tmem, 2 * UBN);
+    }
+}
+
 // ------------------------------------------------------------------------------------------------
 // host orchestration
 // ------------------------------------------------------------------------------------------------
 
 PFN_cuTensorMapEncodeTiled_v12000 g_enc = nullptr;
+bool g_strip = false;  // row-strip pipelined trailing update (else one block per tile)
 std::once_flag g_enc_once;
 
 bool enc_ready() {
@@ -424,31 +626,49 @@ bool map3(CUtensorMap* m, const float* p, int64_t rows, int64_t E, int box_rows)
 }
 
 struct TcMaps {
-    CUtensorMap ah, al, bh, bl;
+    CUtensorMap ah, al, bh, bl, c;
 };
 
 elrt_status update(elrt_ctx* ctx, const TcMaps& mp, float* M, int64_t ld, int64_t estride, int64_t E, int r0, int r_end,
                    int c0, int c_end, int* err) {
     if (r_end <= r0 || c_end <= c0) return ELRT_OK;
-    dim3 grid((r_end - r0 + 127) / 128, (c_end - c0 + UBN - 1) / UBN, (unsigned)E);
     ProfScope ps(ctx, "lu_tc_update");
-    k_tc_update<<<grid, UTHREADS, UpdSmem::TOTAL, ctx->stream>>>(mp.ah, mp.al, mp.bh, mp.bl, M, ld, estride, r0, r_end,
-                                                                 c0, c_end, err);
+    if (g_strip) {
+        dim3 grid((r_end - r0 + 127) / 128, (unsigned)E);
+        k_tc_update_strip<<<grid, 192, StripSmem::TOTAL, ctx->stream>>>(mp.ah, mp.al, mp.bh, mp.bl, mp.c, M, ld, estride,
+                                                                          r0, r_end, c0, c_end, err);
+    } else {
+        dim3 grid((r_end - r0 + 127) / 128, (c_end - c0 + UBN - 1) / UBN, (unsigned)E);
+        k_tc_update<<<grid, UTHREADS, UpdSmem::TOTAL, ctx->stream>>>(mp.ah, mp.al, mp.bh, mp.bl, M, ld, estride, r0,
+                                                                     r_end, c0, c_end, err);
+    }
     return cuda_check(ctx, cudaGetLastError(), "tc update launch");
 }
 
+bool mapC(CUtensorMap* m, const float* M, int64_t nu, int64_t ld, int64_t estride, int64_t E) {
+    cuuint64_t dims[3] = {(cuuint64_t)ld, (cuuint64_t)nu, (cuuint64_t)E};
+    cuuint64_t strides[2] = {(cuuint64_t)ld * 4, (cuuint64_t)estride * 4};
+    cuuint32_t box[3] = {32, 128, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    return g_enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)M, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                 CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 elrt_status prepare(elrt_ctx* ctx, const float* Lh, const float* Ll, const float* Uh, const float* Ul, int64_t ld,
-                    int64_t E, TcMaps* mp) {
+                    int64_t E, TcMaps* mp, const float* M = nullptr, int64_t estride = 0) {
     if (!enc_ready()) return ctx_fail(ctx, ELRT_ECUDA, "cuTensorMapEncodeTiled unavailable");
     if (E > 65535) return ctx_fail(ctx, ELRT_EINVAL, "tensor-core LU chunk above 65535 elements");
     const int nu = ctx->tab.nu;
     if (!map3(&mp->ah, Lh, nu, E, 128) || !map3(&mp->al, Ll, nu, E, 128) || !map3(&mp->bh, Uh, ld, E, UBN) ||
-        !map3(&mp->bl, Ul, ld, E, UBN))
+        !map3(&mp->bl, Ul, ld, E, UBN) || (M && !mapC(&mp->c, M, nu, ld, estride, E)))
         return ctx_fail(ctx, ELRT_EINVAL, "tensor map encoding failed");
     static bool attr_done = false;
     if (!attr_done) {
         cudaError_t e = cudaFuncSetAttribute(k_tc_update, cudaFuncAttributeMaxDynamicSharedMemorySize, UpdSmem::TOTAL);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rowcol, cudaFuncAttributeMaxDynamicSharedMemorySize, RC_SMEM);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_tc_update_strip, cudaFuncAttributeMaxDynamicSharedMemorySize, StripSmem::TOTAL);
         if (e != cudaSuccess) return cuda_check(ctx, e, "smem attribute");
         attr_done = true;
     }
@@ -506,7 +726,7 @@ elrt_status tc_lu_factor_solve(elrt_ctx* ctx, float* M, int64_t ld, int64_t estr
     const int nu = ctx->tab.nu, nin = ctx->tab.nin, ncols = nu + nin;
     const Side sd = carve(side, E, nu, ld);
     TcMaps mp;
-    elrt_status s = prepare(ctx, sd.Lh, sd.Ll, sd.Uh, sd.Ul, ld, E, &mp);
+    elrt_status s = prepare(ctx, sd.Lh, sd.Ll, sd.Uh, sd.Ul, ld, E, &mp, M, estride);
     if (s) return s;
     for (int J = 0; J < nu; J += NBP) {
         const int jb = std::min(NBP, nu - J);
@@ -526,7 +746,7 @@ elrt_status tc_lu_resolve(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, 
     const int nu = ctx->tab.nu, nin = ctx->tab.nin;
     const Side sd = carve(side, E, nu, ld);
     TcMaps mp;
-    elrt_status s = prepare(ctx, sd.Lh, sd.Ll, sd.Uh, sd.Ul, ld, E, &mp);
+    elrt_status s = prepare(ctx, sd.Lh, sd.Ll, sd.Uh, sd.Ul, ld, E, &mp, M, estride);
     if (s) return s;
     for (int J = 0; J < nu; J += NBP) {
         const int jb = std::min(NBP, nu - J);

@@ -909,3 +909,7 @@ extern "C" elrt_status elrt_build_local_learned(elrt_ctx* ctx, elrt_net* net, in
     cudaFreeAsync(scratch, sm);
     return cuda_check(ctx, cudaStreamSynchronize(sm), "elrt_build_local_learned");
 }
+
+bool elrt_net_matches(const elrt_net* net, const elrt_disc* disc) {
+    return net && disc && net->desc.p == disc->p && net->desc.n_angles == disc->n_angles;
+}
