@@ -29,9 +29,32 @@ def workload_name(nx):
 
 WORKLOAD = workload_name(64)
 
-# DRAM bytes (read + write) per element of k_lu_factor_solve<float> from one ncu capture
-# (profiles/k_lu_factor_solve_slab16.md); valid while that kernel is unchanged.
-LU_DRAM_BYTES_PER_ELEMENT = (8.189778e9 + 8.537462e9) / 256
+# Kernel groups the library times (elrt_profile_get / elrt_profile_work) and the resource that
+# bounds each: "hbm" (algorithmic bytes / time against the measured copy bandwidth) or "alu" with
+# the pipe whose issue rate limits it.  The float-float residual counts one useful flop per
+# multiply or add of the structured operator; one float-float multiply-add takes 12 FP32 issue
+# slots (1 MUL, 3 FMA, 6 in TwoSum, 2 ADD), so its ALU peak is the FP32 rate x 2 / 12.
+KERNEL_BOUND = {
+    "assemble": ("hbm", None), "lu_factor_solve": ("alu", "fp32"), "lu_resolve": ("hbm", None),
+    "lu_tc_diag": ("alu", "fp32"), "lu_tc_rowcol": ("hbm", None), "lu_tc_update": ("hbm", None),
+    "residual": ("alu", "ff"), "restrict": ("hbm", None), "gemv": ("hbm", None), "krylov": ("hbm", None),
+}
+# DRAM bytes (read + write) per element and step of each kernel group, from one ncu capture of
+# the 16 x 16 slab (its summary is kept under profiles/); groups missing here have no capture of
+# their current kernel (or, like the matvec, fit in L2 at 16 x 16).  Scaled to a launch of the
+# benchmark by elements / launches.
+DRAM_BYTES_PER_ELEMENT_STEP = {
+    "lu_tc_update": 6.478e7, "lu_tc_diag": 2.109e5, "assemble": 2.963e6, "restrict": 1.987e6,
+}
+
+
+def alu_peak_tflops(kind, mode, clk_mhz):
+    fp32 = 152 * 128 * 2 * clk_mhz * 1e6 / 1e12
+    if kind == "fp32":
+        return (152 * 4 * clk_mhz * 1e6 / 1e12) if mode == "fp64" else fp32
+    if kind == "ff":
+        return fp32 * 2 / 12 / 2   # 2 useful flops per 12 FP32 issue slots; fp32 counts 2 flops per slot
+    return None
 
 
 def parse():
@@ -40,7 +63,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--mode", default="fp32ir", choices=["tf32ir", "fp32ir", "fp64"])
+    ap.add_argument("--mode", default="tf32ir", choices=["tf32ir", "fp32ir", "fp64"])
     ap.add_argument("--refine", type=int, default=1)
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -321,8 +344,10 @@ def run_ours(args, rank, world, local_rank):
     barrier()
     ms = ev0.elapsed_time(ev1) / args.steps
     launches = ctx.elrt_launch_count()
-    prof = {k: ctx.elrt_profile_get(k) for k in ("assemble", "lu_factor_solve", "lu_resolve", "lu_tc_panel",
-                                                  "lu_tc_update", "residual", "restrict", "status", "gemv", "krylov")}
+    names = ("assemble", "lu_factor_solve", "lu_resolve", "lu_tc_diag", "lu_tc_rowcol", "lu_tc_update", "residual",
+             "restrict", "status", "gemv", "krylov")
+    prof = {k: ctx.elrt_profile_get(k) for k in names}
+    work = {k: ctx.elrt_profile_work(k) for k in names}
     ctx.elrt_profile_enable(False)
     if dist:
         t = torch.tensor([ms], device="cuda")
@@ -352,20 +377,43 @@ def run_ours(args, rank, world, local_rank):
     if rank != 0:
         return
     peaks, peak_src = load_peaks()
-    nu, nin = ctx.nu, ctx.nin
-    flop_el = 2.0 / 3.0 * nu ** 3 + 2.0 * nu * nu * nin     # LU + forward + backward on nin columns
-    lu_ms, lu_n = prof["lu_factor_solve"]
-    # elements per launch: the library chunks the batch evenly
-    per_launch = n / max(1, lu_n / args.steps)
-    achieved = flop_el * per_launch / (lu_ms / lu_n / 1000.0) / 1e12 if lu_n else None
     clk_max = peaks.get("sm_max_mhz", 2070.0)
-    if args.mode == "fp32ir":
-        peak = 152 * 128 * 2 * clk_max * 1e6 / 1e12     # FP32 FMA lanes x 2 flops x clock
-        peak_note = f"FP32 CUDA-core peak derived: 152 SMs x 128 lanes x 2 flop x {clk_max:g} MHz"
-    else:
-        peak = 152 * 4 * clk_max * 1e6 / 1e12           # FP64: 2 FMA/clk/SM (1.26 TFLOP/s)
-        peak_note = f"FP64 peak derived: 152 SMs x 2 FMA x 2 flop x {clk_max:g} MHz"
+    hbm = peaks["hbm_gbs"]
     total_prof = sum(v[0] for v in prof.values())
+    kernels = {}
+    for name, (ms_k, nl) in prof.items():
+        b, f = work.get(name, (0.0, 0.0))
+        if nl == 0 or name not in KERNEL_BOUND:
+            continue
+        bound, pipe = KERNEL_BOUND[name]
+        t_s = ms_k / 1000.0
+        row = {"ms_per_step": ms_k / args.steps, "launches_per_step": nl / args.steps, "share": ms_k / total_prof,
+               "bytes_per_launch": b / nl, "achieved_gbs": b / t_s / 1e9, "frac_hbm": b / t_s / 1e9 / hbm}
+        if f > 0:
+            row["tflops"] = f / t_s / 1e12
+            pk = alu_peak_tflops(pipe, args.mode, clk_max) if pipe else None
+            if pk:
+                row["frac_alu"] = row["tflops"] / pk
+        row["bound"] = bound
+        kernels[name] = row
+    top = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
+    tk = kernels[top]
+    bound, pipe = KERNEL_BOUND[top]
+    dram = DRAM_BYTES_PER_ELEMENT_STEP.get(top)
+    traffic = dram * n / tk["launches_per_step"] if dram else None
+    if bound == "hbm":
+        roof = {"kernel": top, "bound": "hbm", "achieved": tk["achieved_gbs"], "peak": hbm, "unit": "GB/s",
+                "frac": tk["frac_hbm"], "traffic": traffic,
+                "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})",
+                "algorithmic_bytes_per_launch": tk["bytes_per_launch"]}
+    else:
+        pk = alu_peak_tflops(pipe, args.mode, clk_max)
+        roof = {"kernel": top, "bound": "alu", "achieved": tk["tflops"], "peak": pk, "unit": "TFLOP/s",
+                "frac": tk["tflops"] / pk, "traffic": traffic,
+                "peak_source": f"{pipe} issue rate derived: 152 SMs x 128 FP32 lanes x {clk_max:g} MHz",
+                "algorithmic_bytes_per_launch": tk["bytes_per_launch"]}
+    roof.update({"avg_launch_ms": tk["ms_per_step"] / tk["launches_per_step"], "share_of_timed_kernels": tk["share"],
+                 "elements_per_step": n})
     gst, lst = info["global"], local_stats
     val = world * n / (ms / 1000.0)
     out = {
@@ -377,16 +425,11 @@ def run_ours(args, rank, world, local_rank):
                    "local_mode": args.mode, "refine_steps": args.refine, "gmres_rtol": args.rtol, "gmres_restart": 50,
                    "operator_dtype": "f32", "parallelism": f"replicas x{world}",
                    "l2": "working set larger than L2 (in2out 822 MB, local workspace > 10 GB) on every step"},
-        "breakdown_ms": {k: v[0] / args.steps for k, v in prof.items()},
+        "breakdown_ms": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
         "gmres_iterations": gst.iterations, "gmres_rel_residual": gst.rel_residual,
         "local_max_rel_residual": lst.max_rel_residual, "local_flagged": lst.n_flagged,
-        "roofline": {"kernel": "lu_factor_solve", "bound": "alu", "achieved": achieved, "peak": peak,
-                     "unit": "TFLOP/s", "frac": (achieved / peak) if achieved else None,
-                     "traffic": (LU_DRAM_BYTES_PER_ELEMENT * per_launch) if args.mode == "fp32ir" else None,
-                     "traffic_source": "ncu dram bytes of k_lu_factor_solve on the 16x16 slab (65.3 MB per element, "
-                                       "profiles/k_lu_factor_solve_slab16.md) x elements per launch",
-                     "peak_source": peak_note, "flop_per_element": flop_el, "elements_per_launch": per_launch,
-                     "avg_launch_ms": lu_ms / lu_n if lu_n else None, "share_of_timed_kernels": lu_ms / total_prof},
+        "roofline": roof,
+        "kernels": kernels,
         "gpu_launches": launches,
         "e2e": {"value": world * n / (ms_e2e / 1000.0), "unit": "elements/s",
                 "h2d_bytes_per_step": kap_h.numel() * 8 + om_h.numel() * 8 + g_h.numel() * 8,
@@ -421,9 +464,9 @@ def run_ours(args, rank, world, local_rank):
         out["learned"] = learned_section(args, E, W, ctx, prob, kap, om, g, um_classical, peaks)
         lp = out["learned"]["pipeline"]
         f64 = out["learned"]["classical_fp64"]["ms_per_step"]
-        out["learned_vs_classical"] = {"classical_fp32ir_ms": ms, "classical_fp64_ms": f64,
+        out["learned_vs_classical"] = {"classical_ms": ms, "classical_mode": args.mode, "classical_fp64_ms": f64,
                                        "learned_ms": lp["ms_per_step"],
-                                       "speedup_vs_fp32ir": ms / lp["ms_per_step"],
+                                       "speedup_vs_classical": ms / lp["ms_per_step"],
                                        "speedup_vs_fp64": f64 / lp["ms_per_step"], "rel_l2": lp["rel_l2_vs_classical"]}
     print(json.dumps(out), flush=True)
     ctx.close()

@@ -126,12 +126,18 @@ const char* elrt_last_error(const elrt_ctx* ctx);   /* message of the last faili
 /* Kernel timing.  While enabled, the context records CUDA events on its own stream around every
  * launch of its kernels and, at the next synchronisation inside a call, adds the elapsed times to
  * per-kernel totals.  elrt_profile_get returns the total milliseconds and the number of timed
- * launches of one kernel ("assemble", "lu_factor_solve", "lu_resolve", "residual", "restrict",
- * "gemv", "krylov"); unknown names give 0.  elrt_launch_count returns how many kernels the
- * context launched since creation or the last reset (whether or not timing is on). */
+ * launches of one kernel group ("assemble", "lu_factor_solve", "lu_resolve", "lu_tc_diag",
+ * "lu_tc_rowcol", "lu_tc_update", "residual", "restrict", "status", "gemv", "krylov",
+ * "estimate"); unknown names give 0.  elrt_profile_work returns, for the same timed launches, the
+ * algorithmic bytes (every operand read once and every result written once, at the width the
+ * kernel stores it) and the useful flops the library counts for them (0 where a group has no
+ * arithmetic worth counting); achieved bandwidth = bytes / time.  elrt_launch_count returns how
+ * many kernels the context launched since creation or the last reset (whether or not timing is
+ * on). */
 elrt_status elrt_profile_enable(elrt_ctx* ctx, int32_t on);
 elrt_status elrt_profile_reset(elrt_ctx* ctx);
 elrt_status elrt_profile_get(elrt_ctx* ctx, const char* kernel, double* total_ms, int64_t* launches);
+elrt_status elrt_profile_work(elrt_ctx* ctx, const char* kernel, double* bytes, double* flops);
 int64_t elrt_launch_count(const elrt_ctx* ctx);
 
 /* ---------------------------------------------------------------- local stage (Sec. 2.2.3) */
@@ -322,12 +328,12 @@ elrt_status elrt_net_fit(elrt_net* net, int64_t n, const double* kappa, const do
 elrt_status elrt_net_infer(elrt_net* net, int64_t n, double h, const double* h_elem, const double* kappa,
                            const double* omega, float* in2out, float* in2sol);
 
-/* Learned local stage with classical fallback (Sec. 2.4 with the error indicator of the survey
- * reading A10): network inference, then the per-element energy-balance defect
+/* Learned local stage with classical fallback (Sec. 2.4; the error indicator is an energy balance
+ * that the exact local operators satisfy): network inference, then the per-element defect
  *     max_j | w_j |s.n|_j - sum_r w_r (s.n)_r A_i2o[r, j] - N sum_i w_i kappa_hat_i (1 - omega) A_i2m[i, j] |
  *           / (w_j |s.n|_j)
- * (exactly 0 for the classical operators), and the classical FP32-IR solve for every element whose
- * defect exceeds tol.  estimate (device [n] FP32, may be NULL) receives the defects; n_fallback
+ * (exactly 0 for the classical operators), and the classical TF32-IR solve (one refinement sweep)
+ * for every element whose defect exceeds tol.  estimate (device [n] FP32, may be NULL) receives the defects; n_fallback
  * (host, may be NULL) the number of re-solved elements.  ctx and net must share (p, N).
  * Synchronises. */
 elrt_status elrt_build_local_learned(elrt_ctx* ctx, elrt_net* net, int64_t n, double h, const double* h_elem,

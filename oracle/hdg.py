@@ -14,7 +14,7 @@ Plain, slow, dense numpy code that follows the paper's formulation:
   (Sec. 2.3) or densely on tiny meshes.
 * Algorithm 1, step 4: mean-intensity recovery u^m = A_i2m u^_in.
 
-Readings where the paper is silent (each one listed in the design doc):
+Readings where the paper is silent:
 * every integral uses the (p+1)-point LGL rule per direction (diagonal mass);
 * every equation of element K is divided by (h/2) * dtheta, so only
   kappa_hat = kappa * h / 2 enters (Sec. 2.4.1, second paragraph);

@@ -89,6 +89,7 @@ _sig = {
     "elrt_profile_enable": (_i32, [_vp, _i32]),
     "elrt_profile_reset": (_i32, [_vp]),
     "elrt_profile_get": (_i32, [_vp, C.c_char_p, _P(_d), _P(_i64)]),
+    "elrt_profile_work": (_i32, [_vp, C.c_char_p, _P(_d), _P(_d)]),
     "elrt_launch_count": (_i64, [_vp]),
     "elrt_build_local_static": (_i32, [_P(Disc), _vp, _i64, _d, _vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp]),
     "elrt_solve_field": (_i32, [_vp, _P(Field), _P(SolveOpts), _vp, _vp, _P(FieldStats)]),
@@ -247,6 +248,12 @@ class Context:
         ms, n = C.c_double(), C.c_int64()
         _check(_lib.elrt_profile_get(self._h, kernel.encode(), C.byref(ms), C.byref(n)), self._h)
         return ms.value, n.value
+
+    def elrt_profile_work(self, kernel):
+        """(algorithmic bytes, useful flops) of the timed launches of one kernel group."""
+        b, f = C.c_double(), C.c_double()
+        _check(_lib.elrt_profile_work(self._h, kernel.encode(), C.byref(b), C.byref(f)), self._h)
+        return b.value, f.value
 
     def elrt_launch_count(self):
         return _lib.elrt_launch_count(self._h)

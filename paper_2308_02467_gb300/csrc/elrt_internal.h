@@ -61,13 +61,16 @@ struct elrt_ctx {
     std::vector<Pending> pending;
     std::vector<cudaEvent_t> event_pool;
     std::map<std::string, std::pair<double, int64_t>> prof;
+    std::map<std::string, std::pair<double, double>> work;  // algorithmic bytes, flops of timed launches
 };
 
-// Brackets kernel launches with events when profiling is on; counts launches always.
+// Brackets kernel launches with events when profiling is on; counts launches always.  bytes and
+// flops are the algorithmic work of the bracketed launches (every operand read once, every result
+// written once; useful arithmetic only), summed per name while profiling is on.
 struct ProfScope {
     elrt_ctx* ctx;
     int idx;
-    ProfScope(elrt_ctx* c, const char* name, int nlaunch = 1);
+    ProfScope(elrt_ctx* c, const char* name, int nlaunch = 1, double bytes = 0.0, double flops = 0.0);
     ~ProfScope();
 };
 void prof_flush(elrt_ctx* ctx);  // call after a stream synchronisation

@@ -19,6 +19,12 @@ __device__ __forceinline__ ff ff_from_double(double v) {
     return ff{h, __double2float_rn(v - (double)h)};
 }
 
+// the same split on the host (kernel arguments)
+inline ff ff_from_double_host(double v) {
+    const float h = (float)v;
+    return ff{h, (float)(v - (double)h)};
+}
+
 __device__ __forceinline__ double ff_to_double(ff a) { return (double)a.h + (double)a.l; }
 
 // exact: a + b = s + e

@@ -6,9 +6,10 @@
 //     is enqueued at once and turns into a no-op once the device-side convergence flag is set, so
 //     the host synchronises once per cycle;
 //   * mean-intensity recovery u^m_K = in2sol_K x_in(K) with the boundary data included.
-// Vectors: with FP32 operators the Krylov vectors are float-float pairs (about 44 bits) and every
-// product and sum runs on the FP32 pipes (GB300 issues FP64 at ~1/64 of FP32, and even a one-lane
-// FP64 instruction occupies its FP64 pipe for a warp); with FP64 operators they are FP64.  The
+// Vectors: with FP32 operators the Krylov basis is FP32 while the iterate, the right-hand side and
+// the restart residual are float-float pairs (about 44 bits); every product and sum accumulates in
+// float-float on the FP32 pipes (GB300 issues FP64 at ~1/64 of FP32, and even a one-lane FP64
+// instruction occupies its FP64 pipe for a warp).  With FP64 operators everything is FP64.  The
 // Hessenberg matrix, the Givens rotations and the reduction results are FP64 (a few hundred values).
 #include <math.h>
 #include <string.h>
@@ -19,6 +20,7 @@
 
 #include "elrt_internal.h"
 #include "ff.h"
+#include "tc_gemm.cuh"
 
 namespace {
 
@@ -37,36 +39,63 @@ struct GmState {
 };
 
 // ------------------------------------------------------------------------------------------------
-// vector arithmetic in FP64 or float-float
+// vector arithmetic: FP64 vectors accumulate in FP64; float-float and FP32 vectors accumulate in
+// float-float (an FP32 x FP32 product is exact as a float-float pair, TwoProduct by FMA)
 // ------------------------------------------------------------------------------------------------
 
-template <typename V> struct VA;
-template <> struct VA<double> {
-    static __device__ __forceinline__ double zero() { return 0.0; }
-    static __device__ __forceinline__ double from_d(double x) { return x; }
-    static __device__ __forceinline__ double to_d(double x) { return x; }
-    static __device__ __forceinline__ void fma(double& acc, double a, double b) { acc = ::fma(a, b, acc); }
-    static __device__ __forceinline__ double add(double a, double b) { return a + b; }
-    static __device__ __forceinline__ double neg(double a) { return -a; }
-    static __device__ __forceinline__ double mul(double a, double b) { return a * b; }
-    static __device__ __forceinline__ double norm(double a) { return a; }
-    static __device__ __forceinline__ double shfl_sum(double a) {
+template <typename V> struct KV;
+template <> struct KV<double> {
+    using acc = double;
+    static __device__ __forceinline__ acc zero() { return 0.0; }
+    static __device__ __forceinline__ acc load(double v) { return v; }
+    static __device__ __forceinline__ acc coef(double c) { return c; }
+    static __device__ __forceinline__ void fma_vv(acc& s, double a, double b) { s = ::fma(a, b, s); }
+    static __device__ __forceinline__ void fma_cv(acc& s, acc c, double v) { s = ::fma(c, v, s); }
+    static __device__ __forceinline__ double store(acc s) { return s; }
+    static __device__ __forceinline__ double to_d(acc s) { return s; }
+    static __device__ __forceinline__ acc add(acc a, acc b) { return a + b; }
+    static __device__ __forceinline__ acc neg(acc a) { return -a; }
+    static __device__ __forceinline__ acc mul(acc a, acc b) { return a * b; }
+    static __device__ __forceinline__ acc shfl_sum(acc a) {
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) a += __shfl_down_sync(0xffffffffu, a, off);
         return a;
     }
 };
-template <> struct VA<ff> {
-    static __device__ __forceinline__ ff zero() { return ff{0.f, 0.f}; }
-    static __device__ __forceinline__ ff from_d(double x) { return ff_from_double(x); }
-    static __device__ __forceinline__ double to_d(ff x) { return ff_to_double(x); }
-    static __device__ __forceinline__ void fma(ff& acc, ff a, ff b) { ff_fma(acc, a, b); }
-    static __device__ __forceinline__ ff add(ff a, ff b) { return ff_add(a, b); }
-    static __device__ __forceinline__ ff neg(ff a) { return ff{-a.h, -a.l}; }
-    static __device__ __forceinline__ ff mul(ff a, ff b) { return ff_mul(a, b); }
-    static __device__ __forceinline__ ff norm(ff a) { return ff_norm(a.h, a.l); }
-    static __device__ __forceinline__ ff shfl_sum(ff a) { return ff_warp_sum(ff_norm(a.h, a.l)); }
+struct KVff {  // shared by the float-float and FP32 vector types
+    using acc = ff;
+    static __device__ __forceinline__ acc zero() { return ff{0.f, 0.f}; }
+    static __device__ __forceinline__ acc coef(double c) { return ff_from_double(c); }
+    static __device__ __forceinline__ double to_d(acc s) { return ff_to_double(s); }
+    static __device__ __forceinline__ acc add(acc a, acc b) { return ff_add(a, b); }
+    static __device__ __forceinline__ acc neg(acc a) { return ff{-a.h, -a.l}; }
+    static __device__ __forceinline__ acc mul(acc a, acc b) { return ff_mul(a, b); }
+    static __device__ __forceinline__ acc shfl_sum(acc a) { return ff_warp_sum(ff_norm(a.h, a.l)); }
 };
+template <> struct KV<ff> : KVff {
+    static __device__ __forceinline__ acc load(ff v) { return v; }
+    static __device__ __forceinline__ void fma_vv(acc& s, ff a, ff b) { ff_fma(s, a, b); }
+    static __device__ __forceinline__ void fma_cv(acc& s, acc c, ff v) { ff_fma(s, c, v); }
+    static __device__ __forceinline__ ff store(acc s) { return ff_norm(s.h, s.l); }
+};
+template <> struct KV<float> : KVff {
+    static __device__ __forceinline__ acc load(float v) { return ff{v, 0.f}; }
+    static __device__ __forceinline__ void fma_vv(acc& s, float a, float b) {
+        const float p = __fmul_rn(a, b);
+        const float e = fmaf(a, b, -p);
+        float h, t;
+        two_sum(s.h, p, h, t);
+        s.h = h;
+        s.l = __fadd_rn(s.l, __fadd_rn(t, e));
+    }
+    static __device__ __forceinline__ void fma_cv(acc& s, acc c, float v) { ff_fma_f(s, v, c); }
+    static __device__ __forceinline__ float store(acc s) { return __fadd_rn(s.h, s.l); }
+};
+
+// staging of a gathered inflow value for the FP32-operator matvec
+__device__ __forceinline__ ff to_ff(double v) { return ff_from_double(v); }
+__device__ __forceinline__ ff to_ff(ff v) { return v; }
+__device__ __forceinline__ ff to_ff(float v) { return ff{v, 0.f}; }
 
 // ------------------------------------------------------------------------------------------------
 // block-sparse matvec
@@ -74,7 +103,8 @@ template <> struct VA<ff> {
 
 // y_K = alpha * xself_K + beta * (Aop_K x_in(K)) with alpha, beta in {-1, 0, 1}; Aop_K: rows x nin
 // (row-major); x_in(K) gathered from x (neighbours' outflow, NULL: zero) and g (boundary data, NULL:
-// zero).  FP32 operators: float-float accumulation; FP64 operators: FP64 accumulation.
+// zero).  FP32 operators: float-float accumulation; FP64 operators: FP64 accumulation.  The sum
+// with the self term is formed in the accumulator type and rounded once to V.
 template <typename A, typename V>
 __global__ void __launch_bounds__(kThreads) k_elem_gemv(int nx, int nz, int nin, int nface, int rows,
                                                         const A* __restrict__ Aop, const V* __restrict__ x,
@@ -82,6 +112,8 @@ __global__ void __launch_bounds__(kThreads) k_elem_gemv(int nx, int nz, int nin,
                                                         int alpha, int beta, V* __restrict__ y,
                                                         const GmState* __restrict__ st) {
     if (st && st->done) return;
+    using K = KV<V>;
+    using Acc = typename K::acc;
     constexpr int kMaxIn = 4 * ELRT_MAX_N1 * (ELRT_MAX_ANG / 2);
     __shared__ __align__(16) double xin[sizeof(A) == 8 ? kMaxIn : 1];
     __shared__ __align__(16) ff xff[sizeof(A) == 4 ? kMaxIn : 1];
@@ -90,11 +122,14 @@ __global__ void __launch_bounds__(kThreads) k_elem_gemv(int nx, int nz, int nin,
     for (int c = threadIdx.x; c < nin; c += kThreads) {
         const int F = c / nface, off = c - F * nface;
         const int jx = ix + (F == 1) - (F == 3), jz = iz + (F == 2) - (F == 0);
-        V v = VA<V>::zero();
+        int src = 0;  // 0: zero, 1: neighbour outflow, 2: boundary data
+        V xv{};
+        double gv = 0.0;
         if (jx >= 0 && jx < nx && jz >= 0 && jz < nz) {
             if (x) {
                 const int G = (F + 2) & 3;  // opposite face
-                v = x[((int64_t)jz * nx + jx) * nin + G * nface + off];
+                xv = x[((int64_t)jz * nx + jx) * nin + G * nface + off];
+                src = 1;
             }
         } else if (g) {
             int64_t side0;
@@ -105,14 +140,13 @@ __global__ void __launch_bounds__(kThreads) k_elem_gemv(int nx, int nz, int nin,
                 case 2: side0 = (int64_t)(nx + nz) * nface; face = ix; break;
                 default: side0 = (int64_t)(2 * nx + nz) * nface; face = iz; break;
             }
-            v = VA<V>::from_d(g[side0 + (int64_t)face * nface + off]);
+            gv = g[side0 + (int64_t)face * nface + off];
+            src = 2;
         }
         if constexpr (sizeof(A) == 8) {
-            xin[c] = VA<V>::to_d(v);
-        } else if constexpr (std::is_same<V, double>::value) {
-            xff[c] = ff_from_double(v);
+            xin[c] = src == 1 ? K::to_d(K::load(xv)) : gv;
         } else {
-            xff[c] = v;
+            xff[c] = src == 1 ? to_ff(xv) : (src == 2 ? ff_from_double(gv) : ff{0.f, 0.f});
         }
     }
     __syncthreads();
@@ -120,7 +154,7 @@ __global__ void __launch_bounds__(kThreads) k_elem_gemv(int nx, int nz, int nin,
     const A* Ae = Aop + e * (int64_t)rows * nin;
     for (int r = warp; r < rows; r += 2 * (kThreads / 32)) {
         const int r2 = r + kThreads / 32;
-        V s1, s2;
+        Acc s1, s2;
         if constexpr (sizeof(A) == 4) {
             const int nv = nin / 4;
             const float4* A4 = reinterpret_cast<const float4*>(Ae);
@@ -141,12 +175,12 @@ __global__ void __launch_bounds__(kThreads) k_elem_gemv(int nx, int nz, int nin,
             }
             a1 = ff_warp_sum(ff_norm(a1.h, a1.l));
             a2 = ff_warp_sum(ff_norm(a2.h, a2.l));
-            if constexpr (std::is_same<V, ff>::value) {
-                s1 = a1;
-                s2 = a2;
-            } else {
+            if constexpr (std::is_same<Acc, double>::value) {
                 s1 = ff_to_double(a1);
                 s2 = ff_to_double(a2);
+            } else {
+                s1 = a1;
+                s2 = a2;
             }
         } else {
             const int nv = nin / 2;
@@ -165,19 +199,192 @@ __global__ void __launch_bounds__(kThreads) k_elem_gemv(int nx, int nz, int nin,
                 d1 += __shfl_down_sync(0xffffffffu, d1, off);
                 d2 += __shfl_down_sync(0xffffffffu, d2, off);
             }
-            s1 = VA<V>::from_d(d1);
-            s2 = VA<V>::from_d(d2);
+            s1 = K::coef(d1);
+            s2 = K::coef(d2);
         }
         if (lane == 0) {
             const int64_t o1 = e * rows + r;
-            V t1 = beta > 0 ? s1 : (beta < 0 ? VA<V>::neg(s1) : VA<V>::zero());
-            if (alpha) t1 = VA<V>::add(alpha > 0 ? xself[o1] : VA<V>::neg(xself[o1]), t1);
-            y[o1] = t1;
+            Acc t1 = beta > 0 ? s1 : (beta < 0 ? K::neg(s1) : K::zero());
+            if (alpha) t1 = K::add(alpha > 0 ? K::load(xself[o1]) : K::neg(K::load(xself[o1])), t1);
+            y[o1] = K::store(t1);
             if (r2 < rows) {
                 const int64_t o2 = e * rows + r2;
-                V t2 = beta > 0 ? s2 : (beta < 0 ? VA<V>::neg(s2) : VA<V>::zero());
-                if (alpha) t2 = VA<V>::add(alpha > 0 ? xself[o2] : VA<V>::neg(xself[o2]), t2);
-                y[o2] = t2;
+                Acc t2 = beta > 0 ? s2 : (beta < 0 ? K::neg(s2) : K::zero());
+                if (alpha) t2 = K::add(alpha > 0 ? K::load(xself[o2]) : K::neg(K::load(xself[o2])), t2);
+                y[o2] = K::store(t2);
+            }
+        }
+    }
+}
+
+// Streaming variant for FP32 operators (the same y_K): a persistent grid walks the elements; per
+// block one producer warp copies each element's operator in chunks of 8 RPW rows (contiguous in
+// memory) into a ring of shared-memory stages with bulk asynchronous copies, and eight consumer
+// warps, RPW rows each, form the float-float row sums from shared memory against the gathered
+// inflow (double-buffered per element) and combine them with the self term.
+constexpr int kGvWarps = 8;           // consumer warps
+constexpr int kGemvFlag = 16;         // d_flags slot: a copy wait of the streaming matvec timed out
+constexpr int kGvStages = 3;
+constexpr int kGvStageBytes = 32768;
+constexpr int kGvThreads = 32 * (kGvWarps + 1);
+
+__device__ __forceinline__ ff ff_shfl_xor(ff a, int m) {
+    return ff{__shfl_xor_sync(0xffffffffu, a.h, m), __shfl_xor_sync(0xffffffffu, a.l, m)};
+}
+
+// Reduce RPW per-lane partial sums (rows q = 0..RPW-1) over the warp.  Afterwards lane L with
+// L % (32 / RPW) == 0 holds the sum of row L / (32 / RPW).
+template <int RPW>
+__device__ __forceinline__ ff warp_rows_reduce(ff (&acc)[RPW], int lane) {
+    ff v;
+    if constexpr (RPW == 4) {
+        const bool P = (lane >> 4) & 1;  // keep rows 2P, 2P + 1
+        ff t[2];
+#pragma unroll
+        for (int i = 0; i < 2; ++i) {
+            const ff mine = P ? acc[2 + i] : acc[i];
+            const ff other = P ? acc[i] : acc[2 + i];
+            t[i] = ff_add(mine, ff_shfl_xor(other, 16));
+        }
+        const bool Q = (lane >> 3) & 1;  // keep row 2P + Q
+        const ff mine = Q ? t[1] : t[0];
+        const ff other = Q ? t[0] : t[1];
+        v = ff_add(mine, ff_shfl_xor(other, 8));
+#pragma unroll
+        for (int off = 4; off > 0; off >>= 1) v = ff_add(v, ff_shfl_xor(v, off));
+    } else if constexpr (RPW == 2) {
+        const bool P = (lane >> 4) & 1;
+        const ff mine = P ? acc[1] : acc[0];
+        const ff other = P ? acc[0] : acc[1];
+        v = ff_add(mine, ff_shfl_xor(other, 16));
+#pragma unroll
+        for (int off = 8; off > 0; off >>= 1) v = ff_add(v, ff_shfl_xor(v, off));
+    } else {
+        v = acc[0];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v = ff_add(v, ff_shfl_xor(v, off));
+    }
+    return v;
+}
+
+template <typename V, int RPW>
+__global__ void __launch_bounds__(kGvThreads, 2)
+    k_gemv_stream(int nx, int nz, int nin, int nface, int rows, const float* __restrict__ Aop,
+                  const V* __restrict__ x, const double* __restrict__ g, const V* __restrict__ xself, int alpha,
+                  int beta, V* __restrict__ y, const GmState* __restrict__ st, int* __restrict__ err) {
+    if (st && st->done) return;
+    using K = KV<V>;
+    using Acc = typename K::acc;
+    constexpr int CR = kGvWarps * RPW;  // rows per chunk
+    extern __shared__ __align__(128) unsigned char gsm[];
+    float* stages = reinterpret_cast<float*>(gsm);
+    ff* xs = reinterpret_cast<ff*>(gsm + kGvStages * kGvStageBytes);  // [2][nin]
+    __shared__ uint64_t full[kGvStages], empty[kGvStages];
+    __shared__ int abort_flag;
+    volatile int* abort = &abort_flag;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t E = (int64_t)nx * nz;
+    const int nch = (rows + CR - 1) / CR;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kGvStages; ++i) {
+            tc::mbar_init(&full[i], 1);
+            tc::mbar_init(&empty[i], kGvWarps);
+        }
+        *abort = 0;
+        tc::fence_barrier_init();
+    }
+    __syncthreads();
+    if (warp == kGvWarps) {  // producer
+        if (lane == 0) {
+            int it = 0;
+            for (int64_t e = blockIdx.x; e < E && !*abort; e += gridDim.x) {
+                for (int c = 0; c < nch; ++c, ++it) {
+                    const int s = it % kGvStages;
+                    if (!tc::mbar_wait(&empty[s], ((it / kGvStages) & 1) ^ 1, abort)) {
+                        if (err) atomicOr(err, 1);
+                        *abort = 1;
+                        break;
+                    }
+                    const int nr = min(CR, rows - c * CR);
+                    const uint32_t bytes = (uint32_t)nr * nin * 4u;
+                    tc::mbar_expect_tx(&full[s], bytes);
+                    tc::bulk_load(stages + (size_t)s * (kGvStageBytes / 4), Aop + (e * rows + c * CR) * (int64_t)nin,
+                                  bytes, &full[s]);
+                }
+            }
+            // let the copies in flight land before the block can exit
+            for (int q = (it > kGvStages ? it - kGvStages : 0); q < it; ++q) {
+                const long long t0 = clock64();
+                while (!tc::mbar_try_wait(&full[q % kGvStages], (q / kGvStages) & 1) && clock64() - t0 < tc::kWaitCycles / 4) {
+                }
+            }
+        }
+        return;
+    }
+    // consumers
+    const int ctid = threadIdx.x;  // 0 .. 32 kGvWarps - 1
+    int it = 0, buf = 0;
+    for (int64_t e = blockIdx.x; e < E; e += gridDim.x, buf ^= 1) {
+        ff* xe = xs + buf * nin;
+        const int ix = (int)(e % nx), iz = (int)(e / nx);
+        for (int c = ctid; c < nin; c += 32 * kGvWarps) {
+            const int F = c / nface, off = c - F * nface;
+            const int jx = ix + (F == 1) - (F == 3), jz = iz + (F == 2) - (F == 0);
+            ff v{0.f, 0.f};
+            if (jx >= 0 && jx < nx && jz >= 0 && jz < nz) {
+                if (x) v = to_ff(x[((int64_t)jz * nx + jx) * nin + ((F + 2) & 3) * nface + off]);
+            } else if (g) {
+                int64_t side0;
+                int face;
+                switch (F) {
+                    case 0: side0 = 0; face = ix; break;
+                    case 1: side0 = (int64_t)nx * nface; face = iz; break;
+                    case 2: side0 = (int64_t)(nx + nz) * nface; face = ix; break;
+                    default: side0 = (int64_t)(2 * nx + nz) * nface; face = iz; break;
+                }
+                v = ff_from_double(g[side0 + (int64_t)face * nface + off]);
+            }
+            xe[c] = v;
+        }
+        asm volatile("bar.sync 1, %0;" ::"r"(32 * kGvWarps) : "memory");  // consumers only
+        for (int c = 0; c < nch; ++c, ++it) {
+            const int s = it % kGvStages;
+            if (!__all_sync(0xffffffffu, tc::mbar_wait(&full[s], (it / kGvStages) & 1, abort))) {
+                // keep walking the loops (every later wait returns at once) so that all consumer
+                // warps still meet at the per-element barrier
+                if (lane == 0 && err) atomicOr(err, 2);
+                *abort = 1;
+                continue;
+            }
+            const float* Ac = stages + (size_t)s * (kGvStageBytes / 4) + (size_t)warp * RPW * nin;
+            const int rbase = c * CR + warp * RPW;
+            ff acc[RPW];
+#pragma unroll
+            for (int q = 0; q < RPW; ++q) acc[q] = ff{0.f, 0.f};
+            for (int col = lane; col < nin; col += 32) {
+                const ff xv = xe[col];
+#pragma unroll
+                for (int q = 0; q < RPW; ++q)
+                    if (rbase + q < rows) ff_fma_f(acc[q], Ac[q * nin + col], xv);
+            }
+            // the stage was read through the generic proxy; the next bulk copy into it writes
+            // through the async proxy
+            tc::fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&empty[s])) : "memory");
+#pragma unroll
+            for (int q = 0; q < RPW; ++q) acc[q] = ff_norm(acc[q].h, acc[q].l);
+            const ff sum = warp_rows_reduce<RPW>(acc, lane);
+            constexpr int span = 32 / RPW;
+            const int r = rbase + lane / span;
+            if (lane % span == 0 && r < rows) {
+                Acc sv;
+                if constexpr (std::is_same<Acc, double>::value) sv = ff_to_double(sum);
+                else sv = sum;
+                const int64_t o = e * rows + r;
+                Acc t = beta > 0 ? sv : (beta < 0 ? K::neg(sv) : K::zero());
+                if (alpha) t = K::add(alpha > 0 ? K::load(xself[o]) : K::neg(K::load(xself[o])), t);
+                y[o] = K::store(t);
             }
         }
     }
@@ -187,14 +394,14 @@ __global__ void __launch_bounds__(kThreads) k_elem_gemv(int nx, int nz, int nin,
 // Krylov kernels
 // ------------------------------------------------------------------------------------------------
 
-template <typename V>
-__device__ __forceinline__ double block_sum_to_double(V v, V* red) {
-    v = VA<V>::shfl_sum(v);
+template <typename Acc, typename K>
+__device__ __forceinline__ double block_sum_to_double(Acc v, Acc* red) {
+    v = K::shfl_sum(v);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
     __syncthreads();
     double s = 0.0;
     if (threadIdx.x == 0)
-        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += VA<V>::to_d(red[w]);
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += K::to_d(red[w]);
     return s;
 }
 
@@ -214,13 +421,15 @@ template <typename V>
 __global__ void __launch_bounds__(kThreads) k_dots(const V* __restrict__ Vb, int64_t n, const V* __restrict__ w,
                                                    double* __restrict__ partial, const GmState* __restrict__ st) {
     if (st && st->done) return;
-    __shared__ V red[kThreads / 32];
+    using K = KV<V>;
+    using Acc = typename K::acc;
+    __shared__ Acc red[kThreads / 32];
     const int i = blockIdx.y;
     const V* v = Vb + (int64_t)i * n;
-    V s = VA<V>::zero();
+    Acc s = K::zero();
     for (int64_t k = blockIdx.x * (int64_t)kThreads + threadIdx.x; k < n; k += (int64_t)gridDim.x * kThreads)
-        VA<V>::fma(s, v[k], w[k]);
-    const double tot = block_sum_to_double(VA<V>::norm(s), red);
+        K::fma_vv(s, v[k], w[k]);
+    const double tot = block_sum_to_double<Acc, K>(s, red);
     if (threadIdx.x == 0) partial[(int64_t)i * gridDim.x + blockIdx.x] = tot;
 }
 
@@ -246,32 +455,38 @@ __global__ void __launch_bounds__(kThreads) k_axpy_multi(const V* __restrict__ V
                                                          const double* __restrict__ h, V* __restrict__ w, int sign,
                                                          const GmState* __restrict__ st) {
     if (st && st->done) return;
-    __shared__ V hs[kMaxRestart + 1];
-    for (int i = threadIdx.x; i < nvec; i += blockDim.x) hs[i] = VA<V>::from_d(sign < 0 ? -h[i] : h[i]);
+    using K = KV<V>;
+    using Acc = typename K::acc;
+    __shared__ Acc hs[kMaxRestart + 1];
+    for (int i = threadIdx.x; i < nvec; i += blockDim.x) hs[i] = K::coef(sign < 0 ? -h[i] : h[i]);
     __syncthreads();
     for (int64_t k = blockIdx.x * (int64_t)kThreads + threadIdx.x; k < n; k += (int64_t)gridDim.x * kThreads) {
-        V s = w[k];
-        for (int i = 0; i < nvec; ++i) VA<V>::fma(s, hs[i], Vb[(int64_t)i * n + k]);
-        w[k] = VA<V>::norm(s);
+        Acc s = K::load(w[k]);
+        for (int i = 0; i < nvec; ++i) K::fma_cv(s, hs[i], Vb[(int64_t)i * n + k]);
+        w[k] = K::store(s);
     }
 }
 
-// w /= *d (skipped when *d == 0: lucky breakdown)
-template <typename V>
-__global__ void k_scale(V* __restrict__ w, int64_t n, const double* __restrict__ d, const GmState* __restrict__ st) {
+// out = in / *d (skipped when *d == 0: lucky breakdown); in and out may be the same vector or of
+// two types with one accumulator type (the float-float residual scaled into the FP32 basis)
+template <typename VI, typename VO>
+__global__ void k_scale(const VI* in, VO* out, int64_t n, const double* __restrict__ d,
+                        const GmState* __restrict__ st) {
+    static_assert(std::is_same<typename KV<VI>::acc, typename KV<VO>::acc>::value, "one accumulator type");
     if (st && st->done) return;
     const double dv = *d;
     if (dv == 0.0) return;
-    const V inv = VA<V>::from_d(1.0 / dv);
+    const auto inv = KV<VI>::coef(1.0 / dv);
     for (int64_t k = blockIdx.x * (int64_t)kThreads + threadIdx.x; k < n; k += (int64_t)gridDim.x * kThreads)
-        w[k] = VA<V>::mul(w[k], inv);
+        out[k] = KV<VO>::store(KV<VI>::mul(KV<VI>::load(in[k]), inv));
 }
 
 // r = b - r
 template <typename V>
 __global__ void k_bminus(const V* __restrict__ b, V* __restrict__ r, int64_t n) {
+    using K = KV<V>;
     for (int64_t k = blockIdx.x * (int64_t)kThreads + threadIdx.x; k < n; k += (int64_t)gridDim.x * kThreads)
-        r[k] = VA<V>::add(b[k], VA<V>::neg(r[k]));
+        r[k] = K::store(K::add(K::load(b[k]), K::neg(K::load(r[k]))));
 }
 
 __global__ void k_d2ff(const double* __restrict__ a, ff* __restrict__ b, int64_t n) {
@@ -321,19 +536,21 @@ __global__ void k_solve_upper(const double* __restrict__ H, int ldh, const doubl
     }
 }
 
-// x += sum_{i < j_done} y_i V_i
-template <typename V>
+// x += sum_{i < j_done} y_i V_i (x of type X, basis of type V, one accumulator type)
+template <typename V, typename X>
 __global__ void __launch_bounds__(kThreads) k_update_x(const V* __restrict__ Vb, int64_t n,
-                                                       const double* __restrict__ y, V* __restrict__ x,
+                                                       const double* __restrict__ y, X* __restrict__ x,
                                                        const GmState* __restrict__ st) {
-    __shared__ V ys[kMaxRestart + 1];
+    using Acc = typename KV<X>::acc;
+    static_assert(std::is_same<Acc, typename KV<V>::acc>::value, "one accumulator type");
+    __shared__ Acc ys[kMaxRestart + 1];
     const int nj = st->j_done;
-    for (int i = threadIdx.x; i < nj; i += blockDim.x) ys[i] = VA<V>::from_d(y[i]);
+    for (int i = threadIdx.x; i < nj; i += blockDim.x) ys[i] = KV<X>::coef(y[i]);
     __syncthreads();
     for (int64_t k = blockIdx.x * (int64_t)kThreads + threadIdx.x; k < n; k += (int64_t)gridDim.x * kThreads) {
-        V s = x[k];
-        for (int i = 0; i < nj; ++i) VA<V>::fma(s, ys[i], Vb[(int64_t)i * n + k]);
-        x[k] = VA<V>::norm(s);
+        Acc s = KV<X>::load(x[k]);
+        for (int i = 0; i < nj; ++i) KV<V>::fma_cv(s, ys[i], Vb[(int64_t)i * n + k]);
+        x[k] = KV<X>::store(s);
     }
 }
 
@@ -352,7 +569,41 @@ elrt_status launch_gemv(elrt_ctx* ctx, int nx, int nz, int rows, const void* Aop
     const Tab& t = ctx->tab;
     const int64_t E = (int64_t)nx * nz;
     if (E > 0x7fffffffLL) return ctx_fail(ctx, ELRT_EINVAL, "too many elements");
-    ProfScope ps(ctx, "gemv");
+    // algorithmic bytes: the operators once, the gathered inflow (x or g), the self term, the result
+    const double bytes = (double)E * ((double)rows * t.nin * sizeof(A) + (x ? (double)t.nin * sizeof(V) : 0.0) +
+                                      (g ? 8.0 * t.nin : 0.0) + (xself && beta ? (double)rows * sizeof(V) : 0.0) +
+                                      (double)rows * sizeof(V));
+    ProfScope ps(ctx, "gemv", 1, bytes, 2.0 * (double)E * rows * t.nin);
+    if constexpr (sizeof(A) == 4) {
+        // streaming kernel: 16-byte aligned row chunks (nin % 4 == 0 holds for every valid disc)
+        const int rpw = t.nin * 4 * 32 <= kGvStageBytes ? 4 : (t.nin * 4 * 16 <= kGvStageBytes ? 2 : 1);
+        if (((uintptr_t)Aop & 15) == 0 && t.nin % 4 == 0 && t.nin * 4 * 8 <= kGvStageBytes) {
+            const size_t smem = (size_t)kGvStages * kGvStageBytes + 2 * (size_t)t.nin * sizeof(ff);
+            const unsigned grid = (unsigned)std::min<int64_t>(E, 2 * 152);
+            cudaError_t ce = cudaSuccess;
+            if (rpw == 4) {
+                ce = cudaFuncSetAttribute(k_gemv_stream<V, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                if (ce == cudaSuccess)
+                    k_gemv_stream<V, 4><<<grid, kGvThreads, smem, ctx->stream>>>(nx, nz, t.nin, t.nface, rows,
+                                                                             (const float*)Aop, x, g, xself, alpha,
+                                                                             beta, y, st, ctx->d_flags + kGemvFlag);
+            } else if (rpw == 2) {
+                ce = cudaFuncSetAttribute(k_gemv_stream<V, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                if (ce == cudaSuccess)
+                    k_gemv_stream<V, 2><<<grid, kGvThreads, smem, ctx->stream>>>(nx, nz, t.nin, t.nface, rows,
+                                                                             (const float*)Aop, x, g, xself, alpha,
+                                                                             beta, y, st, ctx->d_flags + kGemvFlag);
+            } else {
+                ce = cudaFuncSetAttribute(k_gemv_stream<V, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                if (ce == cudaSuccess)
+                    k_gemv_stream<V, 1><<<grid, kGvThreads, smem, ctx->stream>>>(nx, nz, t.nin, t.nface, rows,
+                                                                             (const float*)Aop, x, g, xself, alpha,
+                                                                             beta, y, st, ctx->d_flags + kGemvFlag);
+            }
+            if (ce != cudaSuccess) return cuda_check(ctx, ce, "smem attribute");
+            return cuda_check(ctx, cudaGetLastError(), "gemv launch");
+        }
+    }
     k_elem_gemv<A, V><<<(unsigned)E, kThreads, 0, ctx->stream>>>(nx, nz, t.nin, t.nface, rows, (const A*)Aop, x, g,
                                                                  xself, alpha, beta, y, st);
     return cuda_check(ctx, cudaGetLastError(), "gemv launch");
@@ -360,24 +611,32 @@ elrt_status launch_gemv(elrt_ctx* ctx, int nx, int nz, int rows, const void* Aop
 
 unsigned grid_for(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>(4 * 152, (n + kThreads - 1) / kThreads)); }
 
-// GMRES with Krylov vectors of type V (operators of type A).
-template <typename A, typename V>
+// GMRES with operators of type A, Krylov basis of type V and iterate / right-hand side / restart
+// residual of type X.  FP64 operators: V = X = double.  FP32 operators: V = float, X = float-float:
+// the basis only has to span the Krylov space to FP32 accuracy, while every restart recomputes the
+// true residual b - (I - A_int) x in float-float, so the restarts refine the solution to the
+// float-float level (all inner products and norms accumulate in float-float, reduced in FP64).
+template <typename A, typename V, typename X>
 elrt_status gmres(elrt_ctx* ctx, int nx, int nz, const void* Aop, const double* inflow, double rtol, int max_iter,
                   int restart, int use_guess, double* xout, elrt_solve_stats* stats) {
     const Tab& t = ctx->tab;
     const int64_t n = (int64_t)nx * nz * t.nin;
-    const int m = restart;
+    const int m = std::max(1, std::min(restart, kMaxRestart));
     const int nblk = kDotBlocks;
-    const bool own_x = !std::is_same<V, double>::value;  // float-float iterate kept apart from the FP64 output
-    // workspace: V[(m+1) n], b[n], x[n] (float-float only), then the FP64 small arrays and the state
-    const size_t vbytes = ((size_t)(m + 2) * n + (own_x ? n : 0)) * sizeof(V);
+    constexpr bool own_x = !std::is_same<X, double>::value;  // float-float iterate kept apart from the output
+    constexpr bool own_r = !std::is_same<X, V>::value;       // restart residual in X, basis in V
+    // workspace: basis V[(m+1) n], then b[n], x[n] (float-float only), r[n] (when V != X) of type X,
+    // then the FP64 small arrays and the state
+    const size_t vb_bytes = ((size_t)(m + 1) * n * sizeof(V) + 255) & ~(size_t)255;
+    const size_t xbytes = (size_t)n * sizeof(X) * (1 + (own_x ? 1 : 0) + (own_r ? 1 : 0));
     const size_t small = ((size_t)(m + 1) * m + 4 * (size_t)(m + 1) + (size_t)(m + 1) * nblk + 64) * sizeof(double);
-    elrt_status s = ensure_ws(ctx, &ctx->gm, &ctx->gm_bytes, vbytes + small + sizeof(GmState) + 512);
+    elrt_status s = ensure_ws(ctx, &ctx->gm, &ctx->gm_bytes, vb_bytes + xbytes + 256 + small + sizeof(GmState) + 512);
     if (s) return s;
     V* Vb = (V*)ctx->gm;
-    V* b = Vb + (size_t)(m + 1) * n;
-    V* x = own_x ? b + n : (V*)xout;
-    double* H = (double*)((unsigned char*)ctx->gm + ((vbytes + 255) & ~(size_t)255));
+    X* b = (X*)((unsigned char*)ctx->gm + vb_bytes);
+    X* x = own_x ? b + n : (X*)xout;
+    X* r = own_r ? (own_x ? b + 2 * n : b + n) : (X*)Vb;
+    double* H = (double*)((unsigned char*)ctx->gm + ((vb_bytes + xbytes + 255) & ~(size_t)255));
     double* cs = H + (size_t)(m + 1) * m;
     double* sn = cs + (m + 1);
     double* gv = sn + (m + 1);
@@ -387,19 +646,23 @@ elrt_status gmres(elrt_ctx* ctx, int nx, int nz, const void* Aop, const double* 
     GmState* st = (GmState*)(scal + 64);
     cudaStream_t sm = ctx->stream;
     const unsigned gb = grid_for(n);
+    // algorithmic bytes of a pass that touches nvec vectors of type T once each
+    auto kv = [](int nvec, int64_t len, size_t tsize) { return (double)nvec * len * tsize; };
     GmState* hst = (GmState*)ctx->h_pinned;
     const int rows = t.nin;
 
-    // b = A g_bnd
-    s = launch_gemv<A, V>(ctx, nx, nz, rows, Aop, nullptr, inflow, nullptr, 0, 1, b, nullptr);
+    s = cuda_check(ctx, cudaMemsetAsync(ctx->d_flags + kGemvFlag, 0, sizeof(int), sm), "clear flag");
     if (s) return s;
-    { ProfScope ps(ctx, "krylov"); k_dots<V><<<dim3(nblk, 1), kThreads, 0, sm>>>(b, n, b, partial, nullptr); }
+    // b = A g_bnd
+    s = launch_gemv<A, X>(ctx, nx, nz, rows, Aop, nullptr, inflow, nullptr, 0, 1, b, nullptr);
+    if (s) return s;
+    { ProfScope ps(ctx, "krylov", 1, kv(1, n, sizeof(X))); k_dots<X><<<dim3(nblk, 1), kThreads, 0, sm>>>(b, n, b, partial, nullptr); }
     { ProfScope ps(ctx, "krylov"); k_dots_finish<<<1, kThreads, 0, sm>>>(partial, nblk, scal, 2, nullptr); }
     if (!use_guess) {
-        s = cuda_check(ctx, cudaMemsetAsync(x, 0, n * sizeof(V), sm), "zero x");
+        s = cuda_check(ctx, cudaMemsetAsync(x, 0, n * sizeof(X), sm), "zero x");
         if (s) return s;
-    } else if constexpr (std::is_same<V, ff>::value) {
-        ProfScope ps(ctx, "krylov");
+    } else if constexpr (own_x) {
+        ProfScope ps(ctx, "krylov", 1, 16.0 * n);
         k_d2ff<<<gb, kThreads, 0, sm>>>(xout, x, n);
     }
     s = cuda_check(ctx, cudaMemcpyAsync(ctx->h_pinned, scal, sizeof(double), cudaMemcpyDeviceToHost, sm), "read ||b||");
@@ -426,10 +689,10 @@ elrt_status gmres(elrt_ctx* ctx, int nx, int nz, const void* Aop, const double* 
     bool converged = false;
     for (;;) {
         // r = b - (I - A_int) x, beta = ||r||
-        s = launch_gemv<A, V>(ctx, nx, nz, rows, Aop, x, nullptr, x, 1, -1, Vb, nullptr);
+        s = launch_gemv<A, X>(ctx, nx, nz, rows, Aop, x, nullptr, x, 1, -1, r, nullptr);
         if (s) return s;
-        { ProfScope ps(ctx, "krylov"); k_bminus<V><<<gb, kThreads, 0, sm>>>(b, Vb, n); }
-        { ProfScope ps(ctx, "krylov"); k_dots<V><<<dim3(nblk, 1), kThreads, 0, sm>>>(Vb, n, Vb, partial, nullptr); }
+        { ProfScope ps(ctx, "krylov", 1, kv(3, n, sizeof(X))); k_bminus<X><<<gb, kThreads, 0, sm>>>(b, r, n); }
+        { ProfScope ps(ctx, "krylov", 1, kv(1, n, sizeof(X))); k_dots<X><<<dim3(nblk, 1), kThreads, 0, sm>>>(r, n, r, partial, nullptr); }
         { ProfScope ps(ctx, "krylov"); k_dots_finish<<<1, kThreads, 0, sm>>>(partial, nblk, scal + 1, 2, nullptr); }
         s = cuda_check(ctx, cudaMemcpyAsync(ctx->h_pinned, scal + 1, sizeof(double), cudaMemcpyDeviceToHost, sm), "read beta");
         if (!s) s = cuda_check(ctx, cudaStreamSynchronize(sm), "sync beta");
@@ -442,7 +705,10 @@ elrt_status gmres(elrt_ctx* ctx, int nx, int nz, const void* Aop, const double* 
             break;
         }
         if (its >= max_iter) break;
-        { ProfScope ps(ctx, "krylov"); k_scale<V><<<gb, kThreads, 0, sm>>>(Vb, n, scal + 1, nullptr); }
+        {
+            ProfScope ps(ctx, "krylov", 1, kv(1, n, sizeof(X)) + kv(1, n, sizeof(V)));
+            k_scale<X, V><<<gb, kThreads, 0, sm>>>(r, Vb, n, scal + 1, nullptr);
+        }
         { ProfScope ps(ctx, "krylov"); k_cycle_start<<<1, 1, 0, sm>>>(st, gv, m, scal + 1); }
         const int mj = std::min(m, max_iter - its);
         for (int j = 0; j < mj; ++j) {
@@ -452,33 +718,42 @@ elrt_status gmres(elrt_ctx* ctx, int nx, int nz, const void* Aop, const double* 
             s = launch_gemv<A, V>(ctx, nx, nz, rows, Aop, vj, nullptr, vj, 1, -1, w, st);
             if (s) return s;
             // classical Gram-Schmidt, twice
-            { ProfScope ps(ctx, "krylov"); k_dots<V><<<dim3(nblk, j + 1), kThreads, 0, sm>>>(Vb, n, w, partial, st); }
+            const size_t sv = sizeof(V);
+            { ProfScope ps(ctx, "krylov", 1, kv(j + 2, n, sv)); k_dots<V><<<dim3(nblk, j + 1), kThreads, 0, sm>>>(Vb, n, w, partial, st); }
             { ProfScope ps(ctx, "krylov"); k_dots_finish<<<j + 1, kThreads, 0, sm>>>(partial, nblk, hc, 0, st); }
-            { ProfScope ps(ctx, "krylov"); k_axpy_multi<V><<<gb, kThreads, 0, sm>>>(Vb, n, j + 1, hc, w, -1, st); }
-            { ProfScope ps(ctx, "krylov"); k_dots<V><<<dim3(nblk, j + 1), kThreads, 0, sm>>>(Vb, n, w, partial, st); }
+            { ProfScope ps(ctx, "krylov", 1, kv(j + 3, n, sv)); k_axpy_multi<V><<<gb, kThreads, 0, sm>>>(Vb, n, j + 1, hc, w, -1, st); }
+            { ProfScope ps(ctx, "krylov", 1, kv(j + 2, n, sv)); k_dots<V><<<dim3(nblk, j + 1), kThreads, 0, sm>>>(Vb, n, w, partial, st); }
             { ProfScope ps(ctx, "krylov"); k_dots_finish<<<j + 1, kThreads, 0, sm>>>(partial, nblk, yv, 0, st); }
             { ProfScope ps(ctx, "krylov"); k_dots_finish<<<j + 1, kThreads, 0, sm>>>(partial, nblk, hc, 1, st); }  // h += second pass
-            { ProfScope ps(ctx, "krylov"); k_axpy_multi<V><<<gb, kThreads, 0, sm>>>(Vb, n, j + 1, yv, w, -1, st); }
+            { ProfScope ps(ctx, "krylov", 1, kv(j + 3, n, sv)); k_axpy_multi<V><<<gb, kThreads, 0, sm>>>(Vb, n, j + 1, yv, w, -1, st); }
             // h_{j+1,j} = ||w||, v_{j+1} = w / h_{j+1,j}
-            { ProfScope ps(ctx, "krylov"); k_dots<V><<<dim3(nblk, 1), kThreads, 0, sm>>>(w, n, w, partial, st); }
+            { ProfScope ps(ctx, "krylov", 1, kv(1, n, sv)); k_dots<V><<<dim3(nblk, 1), kThreads, 0, sm>>>(w, n, w, partial, st); }
             { ProfScope ps(ctx, "krylov"); k_dots_finish<<<1, kThreads, 0, sm>>>(partial, nblk, hc + j + 1, 2, st); }
-            { ProfScope ps(ctx, "krylov"); k_scale<V><<<gb, kThreads, 0, sm>>>(w, n, hc + j + 1, st); }
+            { ProfScope ps(ctx, "krylov", 1, kv(2, n, sv)); k_scale<V, V><<<gb, kThreads, 0, sm>>>(w, w, n, hc + j + 1, st); }
             { ProfScope ps(ctx, "krylov"); k_givens<<<1, 1, 0, sm>>>(H, m + 1, cs, sn, gv, j, st); }
         }
         { ProfScope ps(ctx, "krylov"); k_solve_upper<<<1, 1, 0, sm>>>(H, m + 1, gv, yv, st); }
-        { ProfScope ps(ctx, "krylov"); k_update_x<V><<<gb, kThreads, 0, sm>>>(Vb, n, yv, x, st); }
+        {
+            ProfScope ps(ctx, "krylov", 1, kv(m, n, sizeof(V)) + kv(2, n, sizeof(X)));
+            k_update_x<V, X><<<gb, kThreads, 0, sm>>>(Vb, n, yv, x, st);
+        }
         s = cuda_check(ctx, cudaGetLastError(), "gmres launches");
         if (s) return s;
+        int* hflag = (int*)((unsigned char*)ctx->h_pinned + 2048);
         s = cuda_check(ctx, cudaMemcpyAsync(hst, st, sizeof(GmState), cudaMemcpyDeviceToHost, sm), "read state");
+        if (!s)
+            s = cuda_check(ctx, cudaMemcpyAsync(hflag, ctx->d_flags + kGemvFlag, sizeof(int), cudaMemcpyDeviceToHost, sm),
+                           "read flag");
         if (!s) s = cuda_check(ctx, cudaStreamSynchronize(sm), "sync cycle");
         if (s) return s;
         prof_flush(ctx);
+        if (*hflag) return ctx_fail(ctx, ELRT_ETIMEOUT, "a copy wait of the streaming matvec timed out");
         its += hst->j_done;
         ++cycles;
         if (hst->j_done == 0) break;  // no progress possible
     }
-    if constexpr (std::is_same<V, ff>::value) {
-        ProfScope ps(ctx, "krylov");
+    if constexpr (own_x) {
+        ProfScope ps(ctx, "krylov", 1, 16.0 * n);
         k_ff2d<<<gb, kThreads, 0, sm>>>(x, xout, n);
         s = cuda_check(ctx, cudaStreamSynchronize(sm), "output");
         if (s) return s;
@@ -510,6 +785,7 @@ elrt_status global_recover(elrt_ctx* ctx, int nx, int nz, const void* A, int dty
 elrt_status global_solve(elrt_ctx* ctx, int nx, int nz, const void* A, int dtype, const double* inflow, double rtol,
                          int max_iter, int restart, int use_guess, double* x, elrt_solve_stats* stats) {
     if (restart > kMaxRestart) return ctx_fail(ctx, ELRT_EINVAL, "restart above 200");
-    if (dtype == ELRT_F32) return gmres<float, ff>(ctx, nx, nz, A, inflow, rtol, max_iter, restart, use_guess, x, stats);
-    return gmres<double, double>(ctx, nx, nz, A, inflow, rtol, max_iter, restart, use_guess, x, stats);
+    if (dtype == ELRT_F32)
+        return gmres<float, float, ff>(ctx, nx, nz, A, inflow, rtol, max_iter, restart, use_guess, x, stats);
+    return gmres<double, double, double>(ctx, nx, nz, A, inflow, rtol, max_iter, restart, use_guess, x, stats);
 }

@@ -227,9 +227,12 @@ static cudaEvent_t pool_get(elrt_ctx* ctx) {
     return e;
 }
 
-ProfScope::ProfScope(elrt_ctx* c, const char* name, int nlaunch) : ctx(c), idx(-1) {
+ProfScope::ProfScope(elrt_ctx* c, const char* name, int nlaunch, double bytes, double flops) : ctx(c), idx(-1) {
     ctx->launches += nlaunch;
     if (!ctx->profiling) return;
+    auto& w = ctx->work[name];
+    w.first += bytes;
+    w.second += flops;
     cudaEvent_t a = pool_get(ctx), b = pool_get(ctx);
     if (!a || !b) return;
     cudaEventRecord(a, ctx->stream);
@@ -268,6 +271,7 @@ elrt_status elrt_profile_reset(elrt_ctx* ctx) {
     cudaStreamSynchronize(ctx->stream);
     prof_flush(ctx);
     ctx->prof.clear();
+    ctx->work.clear();
     ctx->launches = 0;
     return ELRT_OK;
 }
@@ -280,6 +284,14 @@ elrt_status elrt_profile_get(elrt_ctx* ctx, const char* kernel, double* total_ms
     auto it = ctx->prof.find(kernel);
     *total_ms = it == ctx->prof.end() ? 0.0 : it->second.first;
     *launches = it == ctx->prof.end() ? 0 : it->second.second;
+    return ELRT_OK;
+}
+
+elrt_status elrt_profile_work(elrt_ctx* ctx, const char* kernel, double* bytes, double* flops) {
+    if (!ctx || !kernel || !bytes || !flops) return ctx_fail(ctx, ELRT_EINVAL, "elrt_profile_work: bad arguments");
+    auto it = ctx->work.find(kernel);
+    *bytes = it == ctx->work.end() ? 0.0 : it->second.first;
+    *flops = it == ctx->work.end() ? 0.0 : it->second.second;
     return ELRT_OK;
 }
 

@@ -514,6 +514,187 @@ __global__ void __launch_bounds__(kThreads) k_residual(Tab t, double h, const do
 }
 
 // ------------------------------------------------------------------------------------------------
+// Float-float refinement residual of the FP32 / TF32 local solves.  The running solution X is kept
+// as float-float pairs (no FP64 instruction in the element loop); the structured operator is the
+// same as above: (B + M) X on the diagonal, the x- and z-line derivative sums of -C X, and the
+// circulant angular sum of -S X (eq. hdg_local_mat).
+//   mode 0: X = D;  mode 1: X += D;  mode 2: X += D and no residual.
+// In modes 0 and 1, R = -B^ - A X is written over D (FP32) and maxres[e] = max |R|.
+// N1T / NAT fix n1 = p + 1 and N at compile time (0: read from the table).
+// ------------------------------------------------------------------------------------------------
+constexpr int kResThreads = 512;
+
+__device__ __forceinline__ ff ff_neg(ff a) { return ff{-a.h, -a.l}; }
+
+template <int N1T, int NAT>
+__global__ void __launch_bounds__(kResThreads, 2) k_residual_ff(Tab t, double h, const double* __restrict__ h_elem,
+                                                             const double* __restrict__ kappa,
+                                                             const double* __restrict__ omega, float* __restrict__ Mall,
+                                                             int64_t ld, int64_t estride, ff* __restrict__ Xall, int mode,
+                                                             int CWR, double* __restrict__ maxres, int64_t E) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int n1 = N1T > 0 ? N1T : t.n1;
+    const int N = NAT > 0 ? NAT : t.N;
+    const int nm = n1 * n1, nu = nm * N, nin = t.nin, p = n1 - 1;
+    // shared memory (residual_ff_smem): X chunk, then the per-element tables at their exact sizes
+    ff* Xs = reinterpret_cast<ff*>(smem_raw);  // [nu][CWR]
+    ff* dcoef = Xs + (size_t)nu * CWR;         // [nu]: B^k_ii + w_i kappa_hat_i
+    ff* wd = dcoef + nu;                       // [n1][n1]: w_q D[q][a]
+    ff* sxw = wd + nm;                         // [N][n1]: sx_k w_b
+    ff* szw = sxw + N * n1;                    // [N][n1]: sz_k w_a
+    ff* wcf = szw + N * n1;                    // [N]: circulant phase
+    ff* scoef = wcf + N;                       // [nm]: w_i omega kappa_hat_i
+    int* abv = reinterpret_cast<int*>(scoef + nm);  // [nm]: a | b << 8 of node i
+    __shared__ float red[kResThreads / 32];
+    const int64_t e = blockIdx.x;
+    if (e >= E) return;
+    const double he = h_elem ? h_elem[e] : h;
+    const double om = omega[e];
+    for (int q = threadIdx.x; q < nm; q += kResThreads) {
+        wd[q] = ff_from_double(t.w[q / n1] * t.D[q]);
+        abv[q] = (q % n1) | ((q / n1) << 8);
+        scoef[q] = ff_from_double(t.w[q % n1] * t.w[q / n1] * om * kappa[e * nm + q] * 0.5 * he);
+    }
+    for (int q = threadIdx.x; q < N * n1; q += kResThreads) {
+        const int k = q / n1, b = q - k * n1;
+        sxw[q] = ff_from_double(t.sx[k] * t.w[b]);
+        szw[q] = ff_from_double(t.sz[k] * t.w[b]);
+    }
+    for (int q = threadIdx.x; q < N; q += kResThreads) wcf[q] = ff_from_double(t.wc[q]);
+    for (int r = threadIdx.x; r < nu; r += kResThreads) {
+        const int k = r / nm, i = r - k * nm;
+        const int a = i % n1, b = i / n1;
+        double bd = 0.0;
+        if (b == 0 && t.sdn[0][k] > 0) bd += t.w[a] * t.sdn[0][k];
+        if (a == p && t.sdn[1][k] > 0) bd += t.w[b] * t.sdn[1][k];
+        if (b == p && t.sdn[2][k] > 0) bd += t.w[a] * t.sdn[2][k];
+        if (a == 0 && t.sdn[3][k] > 0) bd += t.w[b] * t.sdn[3][k];
+        dcoef[r] = ff_from_double(bd + t.w[a] * t.w[b] * kappa[e * nm + i] * 0.5 * he);
+    }
+    float* M = Mall + e * estride;
+    ff* X = Xall + e * (int64_t)nu * nin;
+    float rmax = 0.f;
+    const int rpp = kResThreads / CWR;
+    const int tcol = threadIdx.x % CWR, trow = threadIdx.x / CWR;
+    for (int cs = 0; cs < nin; cs += CWR) {
+        const int col = cs + tcol;
+        const bool colok = col < nin;
+        __syncthreads();
+        for (int r = trow; r < nu; r += rpp) {
+            ff v{0.f, 0.f};
+            if (colok) {
+                const float d = M[(int64_t)r * ld + nu + col];
+                ff* xp = X + (int64_t)r * nin + col;
+                v = (mode == 0) ? ff{d, 0.f} : ff_add(*xp, ff{d, 0.f});
+                *xp = v;
+            }
+            if (mode != 2) Xs[r * CWR + tcol] = v;
+        }
+        if (mode == 2) continue;
+        __syncthreads();
+        // the one nonzero of this column of B^: row tr, value tv
+        int tr = -1;
+        ff tv{0.f, 0.f};
+        if (colok) {
+            const int F = col / t.nface, rem = col - F * t.nface;
+            const int m = rem / t.half, kk = rem - m * t.half;
+            const int kin = t.inc[F][kk];
+            tr = kin * nm + face_node(F, m, p);
+            tv = ff_from_double(-t.w[m] * t.sdn[F][kin]);
+        }
+        int k = trow / nm, i = trow - k * nm;
+        for (int r = trow; r < nu; r += rpp) {
+            if (colok) {
+                const int ab = abv[i];
+                const int a = ab & 0xff, b = ab >> 8;
+                const ff* xk = Xs + (size_t)k * nm * CWR + tcol;  // angle block k, this column
+                ff acc = ff_mul(dcoef[r], xk[i * CWR]);
+                ff tx{0.f, 0.f}, tz{0.f, 0.f};
+                const ff* xrow = xk + n1 * b * CWR;  // x-line through node i
+                const ff* xcol = xk + a * CWR;       // z-line through node i
+#pragma unroll
+                for (int q = 0; q < n1; ++q) {
+                    ff_fma(tx, wd[q * n1 + a], xrow[q * CWR]);
+                    ff_fma(tz, wd[q * n1 + b], xcol[q * n1 * CWR]);
+                }
+                tx = ff_norm(tx.h, tx.l);
+                tz = ff_norm(tz.h, tz.l);
+                const ff cxz = ff_add(ff_mul(sxw[k * n1 + b], tx), ff_mul(szw[k * n1 + a], tz));
+                const ff* xi = Xs + (size_t)i * CWR + tcol;  // node i across angles
+                ff sc{0.f, 0.f};
+#pragma unroll
+                for (int l = 0; l < N; ++l) {
+                    int d = k - l;
+                    d += d < 0 ? N : 0;
+                    ff_fma(sc, wcf[d], xi[(size_t)l * nm * CWR]);
+                }
+                sc = ff_norm(sc.h, sc.l);
+                acc = ff_add(acc, ff_neg(cxz));
+                acc = ff_add(acc, ff_neg(ff_mul(scoef[i], sc)));
+                const ff res = (r == tr) ? ff_add(tv, ff_neg(acc)) : ff_neg(acc);
+                const float rf = __fadd_rn(res.h, res.l);
+                rmax = fmaxf(rmax, fabsf(rf));
+                M[(int64_t)r * ld + nu + col] = rf;
+            }
+            i += rpp;
+            while (i >= nm) {
+                i -= nm;
+                ++k;
+            }
+        }
+    }
+    if (mode == 2) return;
+    for (int off = 16; off > 0; off >>= 1) rmax = fmaxf(rmax, __shfl_down_sync(0xffffffffu, rmax, off));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = rmax;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        float m = 0.f;
+        for (int w = 0; w < kResThreads / 32; ++w) m = fmaxf(m, red[w]);
+        maxres[e] = (double)m;
+    }
+}
+
+// Restriction from the float-float solution: in2out = R^o X, in2sol = (1/N) sum_k X (eqs.
+// hdg_local_i2o and ang_ave), sums in float-float, rounded once to the output type.
+__device__ __forceinline__ void ff_store(float* dst, ff v) { *dst = __fadd_rn(v.h, v.l); }
+__device__ __forceinline__ void ff_store(double* dst, ff v) { *dst = (double)v.h + (double)v.l; }
+
+template <typename O>
+__global__ void __launch_bounds__(kThreads) k_restrict_ff(Tab t, const ff* __restrict__ X, ff inv_n,
+                                                          O* __restrict__ in2out, O* __restrict__ in2sol,
+                                                          int* __restrict__ estatus, int64_t E) {
+    const int nin = t.nin, nm = t.nm, half = t.half;
+    const int64_t e = blockIdx.x;
+    if (e >= E) return;
+    const ff* Xe = X + e * (int64_t)t.nu * nin;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nrows = nin + nm;
+    int bad = 0;
+    for (int r = warp; r < nrows; r += kThreads / 32) {
+        if (r < nin) {
+            const int F = r / t.nface, rem = r - F * t.nface;
+            const int m = rem / half, kk = rem - m * half;
+            const int row = t.outc[F][kk] * nm + face_node(F, m, t.p);
+            for (int c = lane; c < nin; c += 32) {
+                const ff v = Xe[(int64_t)row * nin + c];
+                if (!isfinite(v.h) || !isfinite(v.l)) bad = 1;
+                ff_store(in2out + e * (int64_t)nin * nin + (int64_t)r * nin + c, v);
+            }
+        } else {
+            const int i = r - nin;
+            for (int c = lane; c < nin; c += 32) {
+                ff s{0.f, 0.f};
+                for (int k = 0; k < t.N; ++k) s = ff_add(s, Xe[(int64_t)(k * nm + i) * nin + c]);
+                s = ff_mul(s, inv_n);
+                if (!isfinite(s.h) || !isfinite(s.l)) bad = 1;
+                ff_store(in2sol + e * (int64_t)nm * nin + (int64_t)i * nin + c, s);
+            }
+        }
+    }
+    if (bad) atomicOr(&estatus[e], 4);
+}
+
+// ------------------------------------------------------------------------------------------------
 // restriction (eqs. hdg_local_i2o and ang_ave): in2out = R^o X, in2sol = (1/N) sum_k X[(k, i)]
 // ------------------------------------------------------------------------------------------------
 
@@ -590,7 +771,7 @@ elrt_status local_assemble_f64(elrt_ctx* ctx, int64_t E, double h, const double*
     for (int64_t e0 = 0; e0 < E; e0 += 65535) {
         const int64_t n = std::min<int64_t>(65535, E - e0);
         dim3 grid((unsigned)n, t.N);
-        ProfScope ps(ctx, "assemble");
+        ProfScope ps(ctx, "assemble", 1, (double)n * (8.0 * t.nu * (t.nu + t.nin) + 8.0 * (t.nm + 2)));
         k_assemble<double><<<grid, kThreads, 0, ctx->stream>>>(
             t, h, h_elem ? h_elem + e0 : nullptr, kappa + e0 * t.nm, omega + e0, A + e0 * (int64_t)t.nu * t.nu, t.nu,
             (int64_t)t.nu * t.nu, rhs + e0 * (int64_t)t.nu * t.nin, t.nin, ctx->d_flags);
@@ -609,6 +790,21 @@ elrt_status local_assemble_f64(elrt_ctx* ctx, int64_t E, double h, const double*
 
 namespace {
 
+// algorithmic bytes / flops of the refinement residual: per entry of X (nu x nin) the correction D is
+// read, X read (modes 1, 2) and written (8 bytes), R written (modes 0, 1); one multiply-add per
+// nonzero of the structured row of A (diagonal, 2 (p + 1) line terms, N angular terms)
+double residual_bytes(const Tab& t, size_t st, int mode, int64_t n) {
+    const double per = (double)st + 8.0 + (mode != 0 ? 8.0 : 0.0) + (mode != 2 ? (double)st : 0.0);
+    return per * t.nu * t.nin * (double)n;
+}
+double residual_flops(const Tab& t, int mode, int64_t n) {
+    return mode == 2 ? (double)t.nu * t.nin * n : 2.0 * (1 + 2 * t.n1 + t.N) * (double)t.nu * t.nin * n;
+}
+// restriction: reads the nin outgoing rows and all nu rows of X, writes in2out and in2sol
+double restrict_bytes(const Tab& t, size_t ss, size_t so, int64_t n) {
+    return ((double)(t.nin + t.nu) * t.nin * ss + (double)(t.nin + t.nm) * t.nin * so) * (double)n;
+}
+
 template <typename T, int NB, int QN>
 elrt_status run_lu(elrt_ctx* ctx, T* M, int64_t ld, int64_t estride, int* ipiv, int* estatus, int64_t n, bool resolve) {
     const Tab& t = ctx->tab;
@@ -618,12 +814,16 @@ elrt_status run_lu(elrt_ctx* ctx, T* M, int64_t ld, int64_t estride, int* ipiv, 
     if (!resolve) {
         e = cudaFuncSetAttribute(k_lu_factor_solve<T, NB, QN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return cuda_check(ctx, e, "smem attribute");
-        ProfScope ps(ctx, "lu_factor_solve");
+        const double nu = t.nu, nin = t.nin;
+        ProfScope ps(ctx, "lu_factor_solve", 1, (double)n * (2.0 * sizeof(T) * nu * (nu + nin) + 4.0 * nu),
+                     (double)n * (2.0 / 3.0 * nu * nu * nu + 2.0 * nu * nu * nin));
         k_lu_factor_solve<T, NB, QN><<<(unsigned)n, kThreads, smem, ctx->stream>>>(t, M, ld, estride, ipiv, estatus, n);
     } else {
         e = cudaFuncSetAttribute(k_lu_resolve<T, NB, QN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return cuda_check(ctx, e, "smem attribute");
-        ProfScope ps(ctx, "lu_resolve");
+        const double nu = t.nu, nin = t.nin;
+        ProfScope ps(ctx, "lu_resolve", 1, (double)n * (sizeof(T) * (nu * nu + 2.0 * nu * nin) + 4.0 * nu),
+                     (double)n * 2.0 * nu * nu * nin);
         k_lu_resolve<T, NB, QN><<<(unsigned)n, kThreads, smem, ctx->stream>>>(t, M, ld, estride, ipiv, n);
     }
     return cuda_check(ctx, cudaGetLastError(), "lu launch");
@@ -638,16 +838,62 @@ elrt_status run_residual(elrt_ctx* ctx, double h, const double* h_elem, const do
     const size_t smem = (size_t)t.nu * (cwr + 1) * sizeof(double);
     cudaError_t e = cudaFuncSetAttribute(k_residual<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_check(ctx, e, "smem attribute");
-    ProfScope ps(ctx, "residual");
+    ProfScope ps(ctx, "residual", 1, residual_bytes(t, sizeof(T), mode, n), residual_flops(t, mode, n));
     k_residual<T><<<(unsigned)n, kThreads, smem, ctx->stream>>>(t, h, h_elem, kappa, omega, M, ld, estride, X64, mode,
                                                                  cwr, maxres, n);
     return cuda_check(ctx, cudaGetLastError(), "residual launch");
 }
 
+// shared memory of the float-float residual for cwr staged columns
+size_t residual_ff_smem(const Tab& t, int cwr) {
+    return ((size_t)t.nu * (cwr + 1) + t.nm + 2 * (size_t)t.N * t.n1 + t.N + t.nm) * sizeof(ff) + t.nm * sizeof(int);
+}
+// columns staged per pass: as many as leave room for two blocks per SM (one stages its next
+// chunk from HBM while the other computes)
+int residual_ff_cwr(const Tab& t) {
+    int cwr = 32;
+    while (cwr > 1 && residual_ff_smem(t, cwr) > 110 * 1024) cwr >>= 1;
+    return cwr;
+}
+
+template <int N1T, int NAT>
+elrt_status launch_residual_ff(elrt_ctx* ctx, double h, const double* h_elem, const double* kappa, const double* omega,
+                               float* M, int64_t ld, int64_t estride, ff* X, int mode, double* maxres, int64_t n) {
+    const Tab& t = ctx->tab;
+    const int cwr = residual_ff_cwr(t);
+    const size_t smem = residual_ff_smem(t, cwr);
+    cudaError_t e =
+        cudaFuncSetAttribute(k_residual_ff<N1T, NAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_check(ctx, e, "smem attribute");
+    ProfScope ps(ctx, "residual", 1, residual_bytes(t, sizeof(float), mode, n), residual_flops(t, mode, n));
+    k_residual_ff<N1T, NAT><<<(unsigned)n, kResThreads, smem, ctx->stream>>>(t, h, h_elem, kappa, omega, M, ld, estride,
+                                                                             X, mode, cwr, maxres, n);
+    return cuda_check(ctx, cudaGetLastError(), "residual launch");
+}
+
+// unrolled shapes for Q6 elements with 16 or 28 angular cells; any other shape reads the table
+elrt_status run_residual_ff(elrt_ctx* ctx, double h, const double* h_elem, const double* kappa, const double* omega,
+                            float* M, int64_t ld, int64_t estride, ff* X, int mode, double* maxres, int64_t n) {
+    const Tab& t = ctx->tab;
+    if (t.n1 == 7 && t.N == 16)
+        return launch_residual_ff<7, 16>(ctx, h, h_elem, kappa, omega, M, ld, estride, X, mode, maxres, n);
+    if (t.n1 == 7 && t.N == 28)
+        return launch_residual_ff<7, 28>(ctx, h, h_elem, kappa, omega, M, ld, estride, X, mode, maxres, n);
+    return launch_residual_ff<0, 0>(ctx, h, h_elem, kappa, omega, M, ld, estride, X, mode, maxres, n);
+}
+
+template <typename O>
+elrt_status run_restrict_ff(elrt_ctx* ctx, const ff* X, O* in2out, O* in2sol, int* estatus, int64_t n) {
+    const ff inv_n = ff_from_double_host(1.0 / ctx->tab.N);
+    ProfScope ps(ctx, "restrict", 1, restrict_bytes(ctx->tab, sizeof(ff), sizeof(O), n));
+    k_restrict_ff<O><<<(unsigned)n, kThreads, 0, ctx->stream>>>(ctx->tab, X, inv_n, in2out, in2sol, estatus, n);
+    return cuda_check(ctx, cudaGetLastError(), "restrict launch");
+}
+
 template <typename S, typename O>
 elrt_status run_restrict(elrt_ctx* ctx, const S* X, int64_t xld, int64_t xestride, int64_t xcol0, O* in2out, O* in2sol,
                          int* estatus, int64_t n) {
-    ProfScope ps(ctx, "restrict");
+    ProfScope ps(ctx, "restrict", 1, restrict_bytes(ctx->tab, sizeof(S), sizeof(O), n));
     k_restrict<S, O><<<(unsigned)n, kThreads, 0, ctx->stream>>>(ctx->tab, X, xld, xestride, xcol0, in2out, in2sol,
                                                                estatus, n);
     return cuda_check(ctx, cudaGetLastError(), "restrict launch");
@@ -701,7 +947,7 @@ elrt_status build_chunked(elrt_ctx* ctx, int64_t E, double h, const double* h_el
         for (int64_t a0 = 0; a0 < n; a0 += 65535) {
             const int64_t m = std::min<int64_t>(65535, n - a0);
             dim3 grid((unsigned)m, t.N);
-            ProfScope ps(ctx, "assemble");
+            ProfScope ps(ctx, "assemble", 1, (double)m * (sizeof(T) * (double)t.nu * (t.nu + t.nin) + 8.0 * (t.nm + 2)));
             k_assemble<T><<<grid, kThreads, 0, ctx->stream>>>(t, h, he ? he + a0 : nullptr, ka + a0 * t.nm, om + a0,
                                                               M + a0 * estride, ld, estride, nullptr, 0, ctx->d_flags);
         }
@@ -717,7 +963,10 @@ elrt_status build_chunked(elrt_ctx* ctx, int64_t E, double h, const double* h_el
         void* o_i2o = (unsigned char*)in2out + (size_t)e0 * t.nin * t.nin * osz;
         void* o_i2m = (unsigned char*)in2sol + (size_t)e0 * t.nm * t.nin * osz;
         if (want_res) {
-            s = run_residual<T>(ctx, h, he, ka, om, M, ld, estride, X64, 0, maxres, n);
+            if constexpr (sizeof(T) == 4)
+                s = run_residual_ff(ctx, h, he, ka, om, M, ld, estride, (ff*)X64, 0, maxres, n);
+            else
+                s = run_residual<T>(ctx, h, he, ka, om, M, ld, estride, X64, 0, maxres, n);
             // the last correction needs no residual unless statistics or status words are wanted
             const bool last_residual = stats || elem_status;
             for (int it = 0; it < (ir ? steps : 0) && !s; ++it) {
@@ -728,8 +977,11 @@ elrt_status build_chunked(elrt_ctx* ctx, int64_t E, double h, const double* h_el
                     s = run_lu<T, NB, QN>(ctx, M, ld, estride, ipiv, estat, n, true);
                 }
                 if (s) break;
-                s = run_residual<T>(ctx, h, he, ka, om, M, ld, estride, X64,
-                                    (it + 1 == steps && !last_residual) ? 2 : 1, maxres, n);
+                const int rmode = (it + 1 == steps && !last_residual) ? 2 : 1;
+                if constexpr (sizeof(T) == 4)
+                    s = run_residual_ff(ctx, h, he, ka, om, M, ld, estride, (ff*)X64, rmode, maxres, n);
+                else
+                    s = run_residual<T>(ctx, h, he, ka, om, M, ld, estride, X64, rmode, maxres, n);
             }
             if (s) return s;
             // flag elements whose residual exceeds 1e-10 max|B^| (when the last residual was computed)
@@ -737,12 +989,19 @@ elrt_status build_chunked(elrt_ctx* ctx, int64_t E, double h, const double* h_el
                 ProfScope ps(ctx, "status");
                 k_flag_residual<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(maxres, estat, 1e-10 * bmax, n);
             }
-            if (out_dtype == ELRT_F32)
-                s = run_restrict<double, float>(ctx, X64, t.nin, (int64_t)t.nu * t.nin, 0, (float*)o_i2o, (float*)o_i2m,
-                                                estat, n);
-            else
-                s = run_restrict<double, double>(ctx, X64, t.nin, (int64_t)t.nu * t.nin, 0, (double*)o_i2o,
-                                                 (double*)o_i2m, estat, n);
+            if constexpr (sizeof(T) == 4) {
+                if (out_dtype == ELRT_F32)
+                    s = run_restrict_ff<float>(ctx, (const ff*)X64, (float*)o_i2o, (float*)o_i2m, estat, n);
+                else
+                    s = run_restrict_ff<double>(ctx, (const ff*)X64, (double*)o_i2o, (double*)o_i2m, estat, n);
+            } else {
+                if (out_dtype == ELRT_F32)
+                    s = run_restrict<double, float>(ctx, X64, t.nin, (int64_t)t.nu * t.nin, 0, (float*)o_i2o,
+                                                    (float*)o_i2m, estat, n);
+                else
+                    s = run_restrict<double, double>(ctx, X64, t.nin, (int64_t)t.nu * t.nin, 0, (double*)o_i2o,
+                                                     (double*)o_i2m, estat, n);
+            }
         } else {
             if (out_dtype == ELRT_F32)
                 s = run_restrict<T, float>(ctx, M, ld, estride, t.nu, (float*)o_i2o, (float*)o_i2m, estat, n);

@@ -56,6 +56,7 @@ constexpr int TS = NBP + 1;
 constexpr int TI = NBP + 4;                                        // inverse row stride: 16-byte aligned rows
 constexpr int PTILE = 256;                                         // rows or columns per tile
 constexpr int RC_SMEM = (PTILE * TS + NBP * TI) * (int)sizeof(float);  // staging + one inverse
+static_assert(PTILE * TS >= NBP * PTILE, "the staging area holds a 64 x PTILE column block");
 
 // Tinv layout per element: [panel][2][64][64]: [0] = L11^{-1} (unit lower), [1] = U11^{-1} (upper)
 __global__ void __launch_bounds__(64) k_diag(int nu, int64_t ld, int64_t estride, float* __restrict__ Mall, int J,
@@ -203,14 +204,17 @@ __global__ void __launch_bounds__(256, 2) k_rowcol(int nu, int64_t ld, int64_t e
     const int nc = min(PTILE, c_end - c0);
     const float* Ti = col_mode == 0 ? Li : Li + NBP * NBP;
     for (int idx = t; idx < NBP * NBP; idx += 256) T[(idx % NBP) * TI + idx / NBP] = Ti[idx];  // transposed
+    // stage the jb x nc block A12 (row k of the panel in S[k][*]) with independent coalesced loads
+    for (int k = warp; k < NBP; k += 8)
+        for (int cc = lane; cc < PTILE; cc += 32)
+            S[k * PTILE + cc] = (k < jb && cc < nc) ? M[(int64_t)(J + k) * ld + c0 + cc] : 0.f;
     __syncthreads();
+    float y[NBP];
     if (t < nc) {
-        const int c = c0 + t;
-        float y[NBP];
 #pragma unroll
         for (int i = 0; i < NBP; ++i) y[i] = 0.f;
         for (int k = 0; k < NBP; ++k) {  // y_i += Tinv[i][k] a_k (the inverse is triangular: zeros elsewhere)
-            const float ak = k < jb ? M[(int64_t)(J + k) * ld + c] : 0.f;
+            const float ak = S[k * PTILE + t];
             const float4* Tc = reinterpret_cast<const float4*>(T + k * TI);
 #pragma unroll
             for (int i4 = 0; i4 < NBP / 4; ++i4) {
@@ -221,6 +225,10 @@ __global__ void __launch_bounds__(256, 2) k_rowcol(int nu, int64_t ld, int64_t e
                 y[4 * i4 + 3] = fmaf(u.w, ak, y[4 * i4 + 3]);
             }
         }
+    }
+    __syncthreads();  // S is reused: from [k][column] staging to [column][i] results
+    if (t < nc) {
+        const int c = c0 + t;
 #pragma unroll
         for (int i = 0; i < NBP; ++i) {
             if (i < jb) M[(int64_t)(J + i) * ld + c] = y[i];
@@ -554,7 +562,10 @@ __global__ void __launch_bounds__(192, 1)
                     out[c + 3] = cv.w - d[c + 3];
                 }
             }
+            // the C tile was read through the generic proxy and the next TMA copy into this stage
+            // writes through the async proxy: order the two before the stage is released
             tc::tc_fence_before();
+            tc::fence_proxy_async();
             __syncwarp();
             if (lane == 0) {
                 asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&acc_empty[a])) : "memory");
@@ -599,7 +610,7 @@ __global__ void __launch_bounds__(192, 1)
 // ------------------------------------------------------------------------------------------------
 
 PFN_cuTensorMapEncodeTiled_v12000 g_enc = nullptr;
-bool g_strip = false;  // row-strip pipelined trailing update (else one block per tile)
+bool g_strip = true;  // row-strip pipelined trailing update (else one block per tile)
 std::once_flag g_enc_once;
 
 bool enc_ready() {
@@ -629,10 +640,13 @@ struct TcMaps {
     CUtensorMap ah, al, bh, bl, c;
 };
 
+// Trailing update C -= L U over rows [r0, r_end) and columns [c0, c_end) of every element, K = jb.
+// Algorithmic bytes: C read and written, the hi/lo splits of L (rows x 64) and U (64 x columns).
 elrt_status update(elrt_ctx* ctx, const TcMaps& mp, float* M, int64_t ld, int64_t estride, int64_t E, int r0, int r_end,
-                   int c0, int c_end, int* err) {
+                   int c0, int c_end, int jb, int* err) {
     if (r_end <= r0 || c_end <= c0) return ELRT_OK;
-    ProfScope ps(ctx, "lu_tc_update");
+    const double R = r_end - r0, C = c_end - c0;
+    ProfScope ps(ctx, "lu_tc_update", 1, (double)E * (8.0 * R * C + 8.0 * (R + C) * NBP), (double)E * 2.0 * R * C * jb);
     if (g_strip) {
         dim3 grid((r_end - r0 + 127) / 128, (unsigned)E);
         k_tc_update_strip<<<grid, 192, StripSmem::TOTAL, ctx->stream>>>(mp.ah, mp.al, mp.bh, mp.bl, mp.c, M, ld, estride,
@@ -660,6 +674,9 @@ elrt_status prepare(elrt_ctx* ctx, const float* Lh, const float* Ll, const float
     if (!enc_ready()) return ctx_fail(ctx, ELRT_ECUDA, "cuTensorMapEncodeTiled unavailable");
     if (E > 65535) return ctx_fail(ctx, ELRT_EINVAL, "tensor-core LU chunk above 65535 elements");
     const int nu = ctx->tab.nu;
+    // every column block starts at a multiple of 64 or at nu, and the vector accesses and TMA copies
+    // need each to start on a 16-byte boundary (n_angles % 4 == 0 already makes nu a multiple of 4)
+    if (nu % 4 != 0 || ld % 4 != 0) return ctx_fail(ctx, ELRT_EINVAL, "tensor-core LU needs nu and ld multiples of 4");
     if (!map3(&mp->ah, Lh, nu, E, 128) || !map3(&mp->al, Ll, nu, E, 128) || !map3(&mp->bh, Uh, ld, E, UBN) ||
         !map3(&mp->bl, Ul, ld, E, UBN) || (M && !mapC(&mp->c, M, nu, ld, estride, E)))
         return ctx_fail(ctx, ELRT_EINVAL, "tensor map encoding failed");
@@ -683,7 +700,15 @@ elrt_status rowcol(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, int64_t
     const int nrt = r_end > r_begin ? (r_end - r_begin + PTILE - 1) / PTILE : 0;
     const int nct = c_end > c_begin ? (c_end - c_begin + PTILE - 1) / PTILE : 0;
     if (nrt + nct == 0) return ELRT_OK;
-    ProfScope ps(ctx, "lu_tc_panel");
+    // algorithmic work per element: row tiles read R x jb (and write it back in mode 0) and write
+    // the hi/lo splits (R x 64); column tiles read and write jb x C and write the splits (C x 64);
+    // triangular products x Uinv (mode 0), Linv x (unit lower, mode 0) or Uinv x (mode 1)
+    const double R = std::max(0, r_end - r_begin), C = std::max(0, c_end - c_begin);
+    const double bytes = (row_mode == 0 ? 8.0 : 4.0) * R * jb + 8.0 * R * NBP + 8.0 * C * jb + 8.0 * C * NBP +
+                         4.0 * NBP * NBP;
+    const double flops = (row_mode == 0 ? R * jb * (jb + 1.0) : 0.0) +
+                         (col_mode == 0 ? C * jb * (jb - 1.0) : C * jb * (jb + 1.0));
+    ProfScope ps(ctx, "lu_tc_rowcol", 1, (double)E * bytes, (double)E * flops);
     k_rowcol<<<dim3((unsigned)E, nrt + nct), 256, RC_SMEM, ctx->stream>>>(
         ctx->tab.nu, ld, estride, M, J, jb, Tinv, panels_of(ctx->tab.nu), r_begin, r_end, row_mode, nrt, c_begin, c_end,
         col_mode, Lh, Ll, Uh, Ul);
@@ -697,7 +722,7 @@ elrt_status backward_sweep_tc(elrt_ctx* ctx, const TcMaps& mp, float* M, int64_t
     for (int J = last; J >= 0; J -= NBP) {
         const int jb = std::min(NBP, nu - J);
         elrt_status s = rowcol(ctx, M, ld, estride, E, J, jb, Tinv, 0, J, 1, nu, nu + nin, 1, Lh, Ll, Uh, Ul);
-        if (!s) s = update(ctx, mp, M, ld, estride, E, 0, J, nu, nu + nin, err);
+        if (!s) s = update(ctx, mp, M, ld, estride, E, 0, J, nu, nu + nin, jb, err);
         if (s) return s;
     }
     return ELRT_OK;
@@ -731,11 +756,13 @@ elrt_status tc_lu_factor_solve(elrt_ctx* ctx, float* M, int64_t ld, int64_t estr
     for (int J = 0; J < nu; J += NBP) {
         const int jb = std::min(NBP, nu - J);
         {
-            ProfScope ps(ctx, "lu_tc_panel");
+            // the diagonal block in, both triangular inverses out; LU plus two triangular inverses
+            const double b3 = (double)jb * jb * jb;
+            ProfScope ps(ctx, "lu_tc_diag", 1, (double)E * (4.0 * jb * jb + 8.0 * NBP * NBP), (double)E * 4.0 / 3.0 * b3);
             k_diag<<<(unsigned)E, 64, 0, ctx->stream>>>(nu, ld, estride, M, J, jb, sd.Tinv, panels_of(nu), estat, 1e-6f);
         }
         s = rowcol(ctx, M, ld, estride, E, J, jb, sd.Tinv, J + jb, nu, 0, J + jb, ncols, 0, sd.Lh, sd.Ll, sd.Uh, sd.Ul);
-        if (!s) s = update(ctx, mp, M, ld, estride, E, J + jb, nu, J + jb, ncols, err);
+        if (!s) s = update(ctx, mp, M, ld, estride, E, J + jb, nu, J + jb, ncols, jb, err);
         if (s) return s;
     }
     return backward_sweep_tc(ctx, mp, M, ld, estride, E, sd.Tinv, sd.Lh, sd.Ll, sd.Uh, sd.Ul, err);
@@ -751,7 +778,7 @@ elrt_status tc_lu_resolve(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, 
     for (int J = 0; J < nu; J += NBP) {
         const int jb = std::min(NBP, nu - J);
         s = rowcol(ctx, M, ld, estride, E, J, jb, sd.Tinv, J + jb, nu, 1, nu, nu + nin, 0, sd.Lh, sd.Ll, sd.Uh, sd.Ul);
-        if (!s) s = update(ctx, mp, M, ld, estride, E, J + jb, nu, nu, nu + nin, err);
+        if (!s) s = update(ctx, mp, M, ld, estride, E, J + jb, nu, nu, nu + nin, jb, err);
         if (s) return s;
     }
     return backward_sweep_tc(ctx, mp, M, ld, estride, E, sd.Tinv, sd.Lh, sd.Ll, sd.Uh, sd.Ul, err);

@@ -881,7 +881,7 @@ extern "C" elrt_status elrt_build_local_learned(elrt_ctx* ctx, elrt_net* net, in
     const int64_t nf = (int64_t)hc;
     if (n_fallback) *n_fallback = nf;
     if (nf > 0) {
-        // classical FP32-IR solve of the flagged elements, then scatter into place
+        // classical TF32-IR solve of the flagged elements, then scatter into place
         void* fb = nullptr;
         const size_t fbytes = (size_t)nf * (t.nm + 2) * sizeof(double) + (size_t)nf * (per_o + per_m) * sizeof(float) + 1024;
         e = cudaMallocAsync(&fb, fbytes, sm);
@@ -895,7 +895,7 @@ extern "C" elrt_status elrt_build_local_learned(elrt_ctx* ctx, elrt_net* net, in
         float* a2 = (float*)(h2 + nf);
         float* m2 = a2 + (size_t)nf * per_o;
         k_gather_inputs<<<grid_of(nf * t.nm), kT, 0, sm>>>(list, nf, t.nm, kappa, omega, h, h_elem, k2, o2, h2);
-        s = local_build(ctx, nf, 1.0, h2, k2, o2, ELRT_LOCAL_FP32_IR, 1, ELRT_F32, a2, m2, nullptr, nullptr);
+        s = local_build(ctx, nf, 1.0, h2, k2, o2, ELRT_LOCAL_TF32_IR, 1, ELRT_F32, a2, m2, nullptr, nullptr);
         if (!s) {
             k_scatter_ops<<<grid_of(nf * per_o), kT, 0, sm>>>(list, nf, per_o, a2, in2out);
             k_scatter_ops<<<grid_of(nf * per_m), kT, 0, sm>>>(list, nf, per_m, m2, in2sol);

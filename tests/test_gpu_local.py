@@ -143,9 +143,11 @@ def test_bad_inputs_rejected(lib, bad):
     assert ei.value.status == 1
 
 
-def test_full_size_slab_sampled_parity_and_energy_balance(lib):
-    """The 64 x 64, p = 6, N = 16 Gaussian-cloud slab in the benchmark's launch configuration:
-    sampled elements against the oracle one by one; the energy balance on every element."""
+@pytest.mark.parametrize("mode,refine", [("fp32ir", 2), ("tf32ir", 1)])
+def test_full_size_slab_sampled_parity_and_energy_balance(lib, mode, refine):
+    """The 64 x 64, p = 6, N = 16 Gaussian-cloud slab in the benchmark's launch configuration
+    (tf32ir, one refinement sweep): sampled elements against the oracle one by one; the energy
+    balance on every element."""
     import torch
     import workloads as W
     prob = W.problem_gaussian_slab()
@@ -155,7 +157,8 @@ def test_full_size_slab_sampled_parity_and_energy_balance(lib):
     n = prob.n_elems
     i2o = torch.empty(n, ctx.nin, ctx.nin, dtype=torch.float32, device="cuda")
     i2m = torch.empty(n, ctx.nm, ctx.nin, dtype=torch.float32, device="cuda")
-    st = ctx.elrt_build_local(kap, om, prob.h, i2o, i2m, mode=lib.LOCAL_FP32_IR, refine_steps=2)
+    st = ctx.elrt_build_local(kap, om, prob.h, i2o, i2m,
+                              mode=lib.LOCAL_FP32_IR if mode == "fp32ir" else lib.LOCAL_TF32_IR, refine_steps=refine)
     assert st.n_flagged == 0
     d = hdg.Disc(6, 16, 0.85)
     mesh = hdg.Mesh(prob.nx, prob.nz, prob.h)
@@ -199,3 +202,4 @@ def test_local_tensor_core_lu_matches_oracle(lib, p, N, ang, n):
     assert err0 < 1e-4 and st0.max_rel_residual > 1e-10, err0   # 3xTF32: FP32-level before refinement
     assert err2 < 1e-10 and st.max_rel_residual < 1e-12, (err0, err2, st.max_rel_residual)
     np.testing.assert_allclose(i2m.cpu().numpy(), o_i2m, atol=1e-10)
+
