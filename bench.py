@@ -40,11 +40,13 @@ KERNEL_BOUND = {
     "residual": ("alu", "ff"), "restrict": ("hbm", None), "gemv": ("hbm", None), "krylov": ("hbm", None),
 }
 # DRAM bytes (read + write) per element and step of each kernel group, from one ncu capture of
-# the 16 x 16 slab (its summary is kept under profiles/); groups missing here have no capture of
-# their current kernel (or, like the matvec, fit in L2 at 16 x 16).  Scaled to a launch of the
-# benchmark by elements / launches.
+# the 32 x 32 slab (1024 elements, 3.3 GB of local workspace; summary kept under profiles/); a
+# group missing here has no capture of its current kernel.  The 32 x 32 operators (205 MB) still
+# partly fit in the 126 MB L2, so the matvec figure is a lower bound at 64 x 64.  Scaled to a
+# launch of the benchmark by elements / launches.
 DRAM_BYTES_PER_ELEMENT_STEP = {
-    "lu_tc_update": 6.478e7, "lu_tc_diag": 2.109e5, "assemble": 2.963e6, "restrict": 1.987e6,
+    "lu_tc_update": 7.053e7, "lu_tc_rowcol": 3.033e7, "lu_tc_diag": 2.359e5, "residual": 6.748e6,
+    "assemble": 3.277e6, "restrict": 2.019e6, "gemv": 2.431e7,
 }
 
 

@@ -321,32 +321,53 @@ __global__ void __launch_bounds__(kGvThreads, 2)
         }
         return;
     }
-    // consumers
+    // consumers.  The inflow (and the self term) of the next element are loaded into registers
+    // before the chunks of the current one are processed, and published to shared memory after.
     const int ctid = threadIdx.x;  // 0 .. 32 kGvWarps - 1
+    constexpr int PF = (4 * ELRT_MAX_N1 * (ELRT_MAX_ANG / 2) + 32 * kGvWarps - 1) / (32 * kGvWarps);
+    V* xsv = reinterpret_cast<V*>(xs + 2 * nin);  // [2][rows] self term
+    ff pin[PF];
+    V pself[PF];
+    auto prefetch = [&](int64_t e) {
+        const int ix = (int)(e % nx), iz = (int)(e / nx);
+#pragma unroll
+        for (int u = 0; u < PF; ++u) {
+            const int c = ctid + u * 32 * kGvWarps;
+            ff v{0.f, 0.f};
+            if (c < nin) {
+                const int F = c / nface, off = c - F * nface;
+                const int jx = ix + (F == 1) - (F == 3), jz = iz + (F == 2) - (F == 0);
+                if (jx >= 0 && jx < nx && jz >= 0 && jz < nz) {
+                    if (x) v = to_ff(x[((int64_t)jz * nx + jx) * nin + ((F + 2) & 3) * nface + off]);
+                } else if (g) {
+                    int64_t side0;
+                    int face;
+                    switch (F) {
+                        case 0: side0 = 0; face = ix; break;
+                        case 1: side0 = (int64_t)nx * nface; face = iz; break;
+                        case 2: side0 = (int64_t)(nx + nz) * nface; face = ix; break;
+                        default: side0 = (int64_t)(2 * nx + nz) * nface; face = iz; break;
+                    }
+                    v = ff_from_double(g[side0 + (int64_t)face * nface + off]);
+                }
+            }
+            pin[u] = v;
+            if (alpha && c < rows) pself[u] = xself[e * rows + c];
+        }
+    };
     int it = 0, buf = 0;
+    if (blockIdx.x < E) prefetch(blockIdx.x);
     for (int64_t e = blockIdx.x; e < E; e += gridDim.x, buf ^= 1) {
         ff* xe = xs + buf * nin;
-        const int ix = (int)(e % nx), iz = (int)(e / nx);
-        for (int c = ctid; c < nin; c += 32 * kGvWarps) {
-            const int F = c / nface, off = c - F * nface;
-            const int jx = ix + (F == 1) - (F == 3), jz = iz + (F == 2) - (F == 0);
-            ff v{0.f, 0.f};
-            if (jx >= 0 && jx < nx && jz >= 0 && jz < nz) {
-                if (x) v = to_ff(x[((int64_t)jz * nx + jx) * nin + ((F + 2) & 3) * nface + off]);
-            } else if (g) {
-                int64_t side0;
-                int face;
-                switch (F) {
-                    case 0: side0 = 0; face = ix; break;
-                    case 1: side0 = (int64_t)nx * nface; face = iz; break;
-                    case 2: side0 = (int64_t)(nx + nz) * nface; face = ix; break;
-                    default: side0 = (int64_t)(2 * nx + nz) * nface; face = iz; break;
-                }
-                v = ff_from_double(g[side0 + (int64_t)face * nface + off]);
-            }
-            xe[c] = v;
+        V* se = xsv + buf * rows;
+#pragma unroll
+        for (int u = 0; u < PF; ++u) {
+            const int c = ctid + u * 32 * kGvWarps;
+            if (c < nin) xe[c] = pin[u];
+            if (alpha && c < rows) se[c] = pself[u];
         }
         asm volatile("bar.sync 1, %0;" ::"r"(32 * kGvWarps) : "memory");  // consumers only
+        if (e + gridDim.x < E) prefetch(e + gridDim.x);
         for (int c = 0; c < nch; ++c, ++it) {
             const int s = it % kGvStages;
             if (!__all_sync(0xffffffffu, tc::mbar_wait(&full[s], (it / kGvStages) & 1, abort))) {
@@ -358,22 +379,33 @@ __global__ void __launch_bounds__(kGvThreads, 2)
             }
             const float* Ac = stages + (size_t)s * (kGvStageBytes / 4) + (size_t)warp * RPW * nin;
             const int rbase = c * CR + warp * RPW;
-            ff acc[RPW];
+            // two independent float-float chains per row (even / odd 32-column blocks)
+            ff acc[RPW], acc2[RPW];
 #pragma unroll
-            for (int q = 0; q < RPW; ++q) acc[q] = ff{0.f, 0.f};
-            for (int col = lane; col < nin; col += 32) {
+            for (int q = 0; q < RPW; ++q) acc[q] = acc2[q] = ff{0.f, 0.f};
+            int col = lane;
+            for (; col + 32 < nin; col += 64) {
+                const ff xv = xe[col], xw = xe[col + 32];
+#pragma unroll
+                for (int q = 0; q < RPW; ++q)
+                    if (rbase + q < rows) {
+                        ff_fma_f(acc[q], Ac[q * nin + col], xv);
+                        ff_fma_f(acc2[q], Ac[q * nin + col + 32], xw);
+                    }
+            }
+            if (col < nin) {
                 const ff xv = xe[col];
 #pragma unroll
                 for (int q = 0; q < RPW; ++q)
                     if (rbase + q < rows) ff_fma_f(acc[q], Ac[q * nin + col], xv);
             }
+#pragma unroll
+            for (int q = 0; q < RPW; ++q) acc[q] = ff_add(ff_norm(acc[q].h, acc[q].l), ff_norm(acc2[q].h, acc2[q].l));
             // the stage was read through the generic proxy; the next bulk copy into it writes
             // through the async proxy
             tc::fence_proxy_async();
             __syncwarp();
             if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&empty[s])) : "memory");
-#pragma unroll
-            for (int q = 0; q < RPW; ++q) acc[q] = ff_norm(acc[q].h, acc[q].l);
             const ff sum = warp_rows_reduce<RPW>(acc, lane);
             constexpr int span = 32 / RPW;
             const int r = rbase + lane / span;
@@ -381,10 +413,9 @@ __global__ void __launch_bounds__(kGvThreads, 2)
                 Acc sv;
                 if constexpr (std::is_same<Acc, double>::value) sv = ff_to_double(sum);
                 else sv = sum;
-                const int64_t o = e * rows + r;
                 Acc t = beta > 0 ? sv : (beta < 0 ? K::neg(sv) : K::zero());
-                if (alpha) t = K::add(alpha > 0 ? K::load(xself[o]) : K::neg(K::load(xself[o])), t);
-                y[o] = K::store(t);
+                if (alpha) t = K::add(alpha > 0 ? K::load(se[r]) : K::neg(K::load(se[r])), t);
+                y[e * rows + r] = K::store(t);
             }
         }
     }
@@ -416,6 +447,14 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
     return s;
 }
 
+// 16 bytes of consecutive vector entries (the Krylov length is a multiple of 4, every vector starts
+// on a 16-byte boundary)
+template <typename V>
+struct alignas(16) Pack16 {
+    static constexpr int P = 16 / sizeof(V);
+    V v[P];
+};
+
 // partial[i * nblk + blk] = sum over this block's slice of V[i] . w   (grid: nblk x nvec)
 template <typename V>
 __global__ void __launch_bounds__(kThreads) k_dots(const V* __restrict__ Vb, int64_t n, const V* __restrict__ w,
@@ -423,13 +462,20 @@ __global__ void __launch_bounds__(kThreads) k_dots(const V* __restrict__ Vb, int
     if (st && st->done) return;
     using K = KV<V>;
     using Acc = typename K::acc;
+    using Pk = Pack16<V>;
+    constexpr int P = Pk::P;
     __shared__ Acc red[kThreads / 32];
     const int i = blockIdx.y;
-    const V* v = Vb + (int64_t)i * n;
-    Acc s = K::zero();
-    for (int64_t k = blockIdx.x * (int64_t)kThreads + threadIdx.x; k < n; k += (int64_t)gridDim.x * kThreads)
-        K::fma_vv(s, v[k], w[k]);
-    const double tot = block_sum_to_double<Acc, K>(s, red);
+    const Pk* v = reinterpret_cast<const Pk*>(Vb + (int64_t)i * n);
+    const Pk* wp = reinterpret_cast<const Pk*>(w);
+    const int64_t np = n / P;
+    Acc sa[2] = {K::zero(), K::zero()};
+    for (int64_t k = blockIdx.x * (int64_t)kThreads + threadIdx.x; k < np; k += (int64_t)gridDim.x * kThreads) {
+        const Pk a = v[k], b = wp[k];
+#pragma unroll
+        for (int q = 0; q < P; ++q) K::fma_vv(sa[q & 1], a.v[q], b.v[q]);
+    }
+    const double tot = block_sum_to_double<Acc, K>(K::add(sa[0], sa[1]), red);
     if (threadIdx.x == 0) partial[(int64_t)i * gridDim.x + blockIdx.x] = tot;
 }
 
@@ -457,13 +503,28 @@ __global__ void __launch_bounds__(kThreads) k_axpy_multi(const V* __restrict__ V
     if (st && st->done) return;
     using K = KV<V>;
     using Acc = typename K::acc;
+    using Pk = Pack16<V>;
+    constexpr int P = Pk::P;
     __shared__ Acc hs[kMaxRestart + 1];
     for (int i = threadIdx.x; i < nvec; i += blockDim.x) hs[i] = K::coef(sign < 0 ? -h[i] : h[i]);
     __syncthreads();
-    for (int64_t k = blockIdx.x * (int64_t)kThreads + threadIdx.x; k < n; k += (int64_t)gridDim.x * kThreads) {
-        Acc s = K::load(w[k]);
-        for (int i = 0; i < nvec; ++i) K::fma_cv(s, hs[i], Vb[(int64_t)i * n + k]);
-        w[k] = K::store(s);
+    const Pk* vb = reinterpret_cast<const Pk*>(Vb);
+    Pk* wp = reinterpret_cast<Pk*>(w);
+    const int64_t np = n / P;
+    for (int64_t k = blockIdx.x * (int64_t)kThreads + threadIdx.x; k < np; k += (int64_t)gridDim.x * kThreads) {
+        Pk wv = wp[k];
+        Acc s[P];
+#pragma unroll
+        for (int q = 0; q < P; ++q) s[q] = K::load(wv.v[q]);
+#pragma unroll 4
+        for (int i = 0; i < nvec; ++i) {
+            const Pk a = vb[(int64_t)i * np + k];
+#pragma unroll
+            for (int q = 0; q < P; ++q) K::fma_cv(s[q], hs[i], a.v[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < P; ++q) wv.v[q] = K::store(s[q]);
+        wp[k] = wv;
     }
 }
 
@@ -479,6 +540,7 @@ __global__ void k_scale(const VI* in, VO* out, int64_t n, const double* __restri
     const auto inv = KV<VI>::coef(1.0 / dv);
     for (int64_t k = blockIdx.x * (int64_t)kThreads + threadIdx.x; k < n; k += (int64_t)gridDim.x * kThreads)
         out[k] = KV<VO>::store(KV<VI>::mul(KV<VI>::load(in[k]), inv));
+    // (element-wise: the in-place case needs no ordering beyond each thread's own entries)
 }
 
 // r = b - r
@@ -549,6 +611,7 @@ __global__ void __launch_bounds__(kThreads) k_update_x(const V* __restrict__ Vb,
     __syncthreads();
     for (int64_t k = blockIdx.x * (int64_t)kThreads + threadIdx.x; k < n; k += (int64_t)gridDim.x * kThreads) {
         Acc s = KV<X>::load(x[k]);
+#pragma unroll 4
         for (int i = 0; i < nj; ++i) KV<V>::fma_cv(s, ys[i], Vb[(int64_t)i * n + k]);
         x[k] = KV<X>::store(s);
     }
@@ -578,7 +641,8 @@ elrt_status launch_gemv(elrt_ctx* ctx, int nx, int nz, int rows, const void* Aop
         // streaming kernel: 16-byte aligned row chunks (nin % 4 == 0 holds for every valid disc)
         const int rpw = t.nin * 4 * 32 <= kGvStageBytes ? 4 : (t.nin * 4 * 16 <= kGvStageBytes ? 2 : 1);
         if (((uintptr_t)Aop & 15) == 0 && t.nin % 4 == 0 && t.nin * 4 * 8 <= kGvStageBytes) {
-            const size_t smem = (size_t)kGvStages * kGvStageBytes + 2 * (size_t)t.nin * sizeof(ff);
+            const size_t smem = (size_t)kGvStages * kGvStageBytes + 2 * (size_t)t.nin * sizeof(ff) +
+                                2 * (size_t)rows * sizeof(V);
             const unsigned grid = (unsigned)std::min<int64_t>(E, 2 * 152);
             cudaError_t ce = cudaSuccess;
             if (rpw == 4) {

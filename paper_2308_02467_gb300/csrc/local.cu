@@ -15,6 +15,7 @@
 #include <stdio.h>
 
 #include <algorithm>
+#include <type_traits>
 #include <string>
 
 #include "elrt_internal.h"
@@ -96,7 +97,43 @@ __global__ void __launch_bounds__(kThreads) k_assemble(Tab t, double h, const do
             for (int c = lane; c < t.nin; c += 32)
                 rhs_out[e * (int64_t)t.nu * rhs_ld + (int64_t)r * rhs_ld + c] = (T)aug_entry(t, k, i, t.nu + c, kh, om);
         } else {
-            for (int c = lane; c < ld; c += 32) Me[(int64_t)r * ld + c] = (T)aug_entry(t, k, i, c, kh, om);
+            // the row is zero apart from 2 n1 + N - 2 operator entries (x-line and z-line through
+            // node i, node i in the other angular cells) and at most two of -B^: zero-fill it with
+            // vector stores, then evaluate only those candidates
+            T* row = Me + (int64_t)r * ld;
+            constexpr int VW = 16 / sizeof(T);
+            using V4 = typename std::conditional<sizeof(T) == 4, float4, double2>::type;
+            const V4 z{};
+            for (int c = lane; c < ld / VW; c += 32) reinterpret_cast<V4*>(row)[c] = z;
+            __syncwarp();
+            const int n1 = t.n1, a = i % n1, b = i / n1;
+            const int ncand = 1 + 2 * (n1 - 1) + (t.N - 1) + 4;
+            for (int q = lane; q < ncand; q += 32) {
+                int c = -1;
+                if (q == 0) {
+                    c = k * t.nm + i;  // diagonal
+                } else if (q < n1) {   // x-line, j = (q', b) with q' != a
+                    const int qq = q - 1 + (q - 1 >= a);
+                    c = k * t.nm + qq + n1 * b;
+                } else if (q < 2 * n1 - 1) {  // z-line, j = (a, q') with q' != b
+                    const int q0 = q - n1;
+                    const int qq = q0 + (q0 >= b);
+                    c = k * t.nm + a + n1 * qq;
+                } else if (q < 2 * n1 - 1 + t.N - 1) {  // node i in angular cell l != k
+                    const int l0 = q - (2 * n1 - 1);
+                    const int l = l0 + (l0 >= k);
+                    c = l * t.nm + i;
+                } else {  // -B^ on face F if node i lies on it and cell k enters through it
+                    const int F = q - (2 * n1 - 1 + t.N - 1);
+                    int m = -1, kk = -1;
+                    for (int mm = 0; mm < n1; ++mm)
+                        if (face_node(F, mm, t.p) == i) m = mm;
+                    for (int x = 0; x < t.half; ++x)
+                        if (t.inc[F][x] == k) kk = x;
+                    if (m >= 0 && kk >= 0) c = t.nu + F * t.nface + m * t.half + kk;
+                }
+                if (c >= 0) row[c] = (T)aug_entry(t, k, i, c, kh, om);
+            }
         }
     }
 }
@@ -525,8 +562,16 @@ __global__ void __launch_bounds__(kThreads) k_residual(Tab t, double h, const do
 constexpr int kResThreads = 512;
 
 __device__ __forceinline__ ff ff_neg(ff a) { return ff{-a.h, -a.l}; }
+// acc += c x for a float-float coefficient c and a staged entry x (FP32 in the first pass, where
+// X = D exactly, float-float afterwards)
+__device__ __forceinline__ void fma_cx(ff& acc, ff c, float x) { ff_fma_f(acc, x, c); }
+__device__ __forceinline__ void fma_cx(ff& acc, ff c, ff x) { ff_fma(acc, c, x); }
+__device__ __forceinline__ ff as_ff(float x) { return ff{x, 0.f}; }
+__device__ __forceinline__ ff as_ff(ff x) { return x; }
 
-template <int N1T, int NAT>
+// XS: type of the staged X chunk: float for mode 0 (half the shared memory, so twice the
+// columns per pass), float-float for modes 1 and 2
+template <int N1T, int NAT, typename XS>
 __global__ void __launch_bounds__(kResThreads, 2) k_residual_ff(Tab t, double h, const double* __restrict__ h_elem,
                                                              const double* __restrict__ kappa,
                                                              const double* __restrict__ omega, float* __restrict__ Mall,
@@ -537,8 +582,8 @@ __global__ void __launch_bounds__(kResThreads, 2) k_residual_ff(Tab t, double h,
     const int N = NAT > 0 ? NAT : t.N;
     const int nm = n1 * n1, nu = nm * N, nin = t.nin, p = n1 - 1;
     // shared memory (residual_ff_smem): X chunk, then the per-element tables at their exact sizes
-    ff* Xs = reinterpret_cast<ff*>(smem_raw);  // [nu][CWR]
-    ff* dcoef = Xs + (size_t)nu * CWR;         // [nu]: B^k_ii + w_i kappa_hat_i
+    XS* Xs = reinterpret_cast<XS*>(smem_raw);  // [nu][CWR]
+    ff* dcoef = reinterpret_cast<ff*>(Xs + (size_t)nu * CWR);  // [nu]: B^k_ii + w_i kappa_hat_i
     ff* wd = dcoef + nu;                       // [n1][n1]: w_q D[q][a]
     ff* sxw = wd + nm;                         // [N][n1]: sx_k w_b
     ff* szw = sxw + N * n1;                    // [N][n1]: sz_k w_a
@@ -580,15 +625,35 @@ __global__ void __launch_bounds__(kResThreads, 2) k_residual_ff(Tab t, double h,
         const int col = cs + tcol;
         const bool colok = col < nin;
         __syncthreads();
-        for (int r = trow; r < nu; r += rpp) {
-            ff v{0.f, 0.f};
-            if (colok) {
-                const float d = M[(int64_t)r * ld + nu + col];
-                ff* xp = X + (int64_t)r * nin + col;
-                v = (mode == 0) ? ff{d, 0.f} : ff_add(*xp, ff{d, 0.f});
-                *xp = v;
+        // stage D (and X) of this column chunk: batches of independent loads, then the updates
+        constexpr int SB = 8;
+        for (int rb = trow; rb < nu; rb += SB * rpp) {
+            float d[SB];
+            ff xo[SB];
+#pragma unroll
+            for (int u = 0; u < SB; ++u) {
+                const int r = rb + u * rpp;
+                d[u] = 0.f;
+                xo[u] = ff{0.f, 0.f};
+                if (colok && r < nu) {
+                    d[u] = M[(int64_t)r * ld + nu + col];
+                    if (mode != 0) xo[u] = X[(int64_t)r * nin + col];
+                }
             }
-            if (mode != 2) Xs[r * CWR + tcol] = v;
+#pragma unroll
+            for (int u = 0; u < SB; ++u) {
+                const int r = rb + u * rpp;
+                if (r >= nu) break;
+                ff v{0.f, 0.f};
+                if (colok) {
+                    v = (mode == 0) ? ff{d[u], 0.f} : ff_add(xo[u], ff{d[u], 0.f});
+                    X[(int64_t)r * nin + col] = v;
+                }
+                if (mode != 2) {
+                    if constexpr (sizeof(XS) == 4) Xs[r * CWR + tcol] = v.h;  // mode 0: v = (d, 0)
+                    else Xs[r * CWR + tcol] = v;
+                }
+            }
         }
         if (mode == 2) continue;
         __syncthreads();
@@ -607,26 +672,26 @@ __global__ void __launch_bounds__(kResThreads, 2) k_residual_ff(Tab t, double h,
             if (colok) {
                 const int ab = abv[i];
                 const int a = ab & 0xff, b = ab >> 8;
-                const ff* xk = Xs + (size_t)k * nm * CWR + tcol;  // angle block k, this column
-                ff acc = ff_mul(dcoef[r], xk[i * CWR]);
+                const XS* xk = Xs + (size_t)k * nm * CWR + tcol;  // angle block k, this column
+                ff acc = ff_mul(dcoef[r], as_ff(xk[i * CWR]));
                 ff tx{0.f, 0.f}, tz{0.f, 0.f};
-                const ff* xrow = xk + n1 * b * CWR;  // x-line through node i
-                const ff* xcol = xk + a * CWR;       // z-line through node i
+                const XS* xrow = xk + n1 * b * CWR;  // x-line through node i
+                const XS* xcol = xk + a * CWR;       // z-line through node i
 #pragma unroll
                 for (int q = 0; q < n1; ++q) {
-                    ff_fma(tx, wd[q * n1 + a], xrow[q * CWR]);
-                    ff_fma(tz, wd[q * n1 + b], xcol[q * n1 * CWR]);
+                    fma_cx(tx, wd[q * n1 + a], xrow[q * CWR]);
+                    fma_cx(tz, wd[q * n1 + b], xcol[q * n1 * CWR]);
                 }
                 tx = ff_norm(tx.h, tx.l);
                 tz = ff_norm(tz.h, tz.l);
                 const ff cxz = ff_add(ff_mul(sxw[k * n1 + b], tx), ff_mul(szw[k * n1 + a], tz));
-                const ff* xi = Xs + (size_t)i * CWR + tcol;  // node i across angles
+                const XS* xi = Xs + (size_t)i * CWR + tcol;  // node i across angles
                 ff sc{0.f, 0.f};
 #pragma unroll
                 for (int l = 0; l < N; ++l) {
                     int d = k - l;
                     d += d < 0 ? N : 0;
-                    ff_fma(sc, wcf[d], xi[(size_t)l * nm * CWR]);
+                    fma_cx(sc, wcf[d], xi[(size_t)l * nm * CWR]);
                 }
                 sc = ff_norm(sc.h, sc.l);
                 acc = ff_add(acc, ff_neg(cxz));
@@ -844,31 +909,41 @@ elrt_status run_residual(elrt_ctx* ctx, double h, const double* h_elem, const do
     return cuda_check(ctx, cudaGetLastError(), "residual launch");
 }
 
-// shared memory of the float-float residual for cwr staged columns
-size_t residual_ff_smem(const Tab& t, int cwr) {
-    return ((size_t)t.nu * (cwr + 1) + t.nm + 2 * (size_t)t.N * t.n1 + t.N + t.nm) * sizeof(ff) + t.nm * sizeof(int);
+// shared memory of the float-float residual for cwr staged columns of xs-byte entries
+size_t residual_ff_smem(const Tab& t, int cwr, size_t xs) {
+    return (size_t)t.nu * cwr * xs + ((size_t)t.nu + t.nm + 2 * (size_t)t.N * t.n1 + t.N + t.nm) * sizeof(ff) +
+           t.nm * sizeof(int);
 }
 // columns staged per pass: as many as leave room for two blocks per SM (one stages its next
 // chunk from HBM while the other computes)
-int residual_ff_cwr(const Tab& t) {
+int residual_ff_cwr(const Tab& t, size_t xs) {
     int cwr = 32;
-    while (cwr > 1 && residual_ff_smem(t, cwr) > 110 * 1024) cwr >>= 1;
+    while (cwr > 1 && residual_ff_smem(t, cwr, xs) > 110 * 1024) cwr >>= 1;
     return cwr;
 }
 
-template <int N1T, int NAT>
+template <int N1T, int NAT, typename XS>
 elrt_status launch_residual_ff(elrt_ctx* ctx, double h, const double* h_elem, const double* kappa, const double* omega,
                                float* M, int64_t ld, int64_t estride, ff* X, int mode, double* maxres, int64_t n) {
     const Tab& t = ctx->tab;
-    const int cwr = residual_ff_cwr(t);
-    const size_t smem = residual_ff_smem(t, cwr);
+    const int cwr = residual_ff_cwr(t, sizeof(XS));
+    const size_t smem = residual_ff_smem(t, cwr, sizeof(XS));
     cudaError_t e =
-        cudaFuncSetAttribute(k_residual_ff<N1T, NAT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_residual_ff<N1T, NAT, XS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_check(ctx, e, "smem attribute");
     ProfScope ps(ctx, "residual", 1, residual_bytes(t, sizeof(float), mode, n), residual_flops(t, mode, n));
-    k_residual_ff<N1T, NAT><<<(unsigned)n, kResThreads, smem, ctx->stream>>>(t, h, h_elem, kappa, omega, M, ld, estride,
-                                                                             X, mode, cwr, maxres, n);
+    k_residual_ff<N1T, NAT, XS><<<(unsigned)n, kResThreads, smem, ctx->stream>>>(t, h, h_elem, kappa, omega, M, ld,
+                                                                                 estride, X, mode, cwr, maxres, n);
     return cuda_check(ctx, cudaGetLastError(), "residual launch");
+}
+
+template <int N1T, int NAT>
+elrt_status launch_residual_mode(elrt_ctx* ctx, double h, const double* h_elem, const double* kappa,
+                                 const double* omega, float* M, int64_t ld, int64_t estride, ff* X, int mode,
+                                 double* maxres, int64_t n) {
+    if (mode == 0)
+        return launch_residual_ff<N1T, NAT, float>(ctx, h, h_elem, kappa, omega, M, ld, estride, X, mode, maxres, n);
+    return launch_residual_ff<N1T, NAT, ff>(ctx, h, h_elem, kappa, omega, M, ld, estride, X, mode, maxres, n);
 }
 
 // unrolled shapes for Q6 elements with 16 or 28 angular cells; any other shape reads the table
@@ -876,10 +951,10 @@ elrt_status run_residual_ff(elrt_ctx* ctx, double h, const double* h_elem, const
                             float* M, int64_t ld, int64_t estride, ff* X, int mode, double* maxres, int64_t n) {
     const Tab& t = ctx->tab;
     if (t.n1 == 7 && t.N == 16)
-        return launch_residual_ff<7, 16>(ctx, h, h_elem, kappa, omega, M, ld, estride, X, mode, maxres, n);
+        return launch_residual_mode<7, 16>(ctx, h, h_elem, kappa, omega, M, ld, estride, X, mode, maxres, n);
     if (t.n1 == 7 && t.N == 28)
-        return launch_residual_ff<7, 28>(ctx, h, h_elem, kappa, omega, M, ld, estride, X, mode, maxres, n);
-    return launch_residual_ff<0, 0>(ctx, h, h_elem, kappa, omega, M, ld, estride, X, mode, maxres, n);
+        return launch_residual_mode<7, 28>(ctx, h, h_elem, kappa, omega, M, ld, estride, X, mode, maxres, n);
+    return launch_residual_mode<0, 0>(ctx, h, h_elem, kappa, omega, M, ld, estride, X, mode, maxres, n);
 }
 
 template <typename O>

@@ -139,6 +139,26 @@ __global__ void __launch_bounds__(64) k_diag(int nu, int64_t ld, int64_t estride
 //   row_mode 1: rows copied into the L split buffers (sweeps).
 //   col_mode 0: y = L11^{-1} a (factorisation and forward sweep); 1: y = U11^{-1} a (backward sweep);
 //   y goes back to M and, transposed, to the U split buffers.
+// out[4b .. 4b+3] = sum_k a[k] T[k][4b .. 4b+3] over the nonzero part of a triangular T (stored
+// with row stride TI): k in [0, 4b + 4) when LOWER_K (T[k][j] = 0 for k > j), k in [4b, 64)
+// otherwise.  Each 4-wide block is handed to put(b, float4) as soon as it is complete.
+template <bool LOWER_K, typename Put>
+__device__ __forceinline__ void tri_apply(const float (&a)[NBP], const float* __restrict__ T, Put put) {
+#pragma unroll
+    for (int b = 0; b < NBP / 4; ++b) {
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int k = LOWER_K ? 0 : 4 * b; k < (LOWER_K ? 4 * b + 4 : NBP); ++k) {
+            const float4 u = reinterpret_cast<const float4*>(T + k * TI)[b];
+            acc.x = fmaf(a[k], u.x, acc.x);
+            acc.y = fmaf(a[k], u.y, acc.y);
+            acc.z = fmaf(a[k], u.z, acc.z);
+            acc.w = fmaf(a[k], u.w, acc.w);
+        }
+        put(b, acc);
+    }
+}
+
 __global__ void __launch_bounds__(256, 2) k_rowcol(int nu, int64_t ld, int64_t estride, float* __restrict__ Mall, int J,
                                                    int jb, const float* __restrict__ Tinv, int npanels, int r_begin,
                                                    int r_end, int row_mode, int nrt, int c_begin, int c_end,
@@ -166,29 +186,31 @@ __global__ void __launch_bounds__(256, 2) k_rowcol(int nu, int64_t ld, int64_t e
         }
         const float* Ui = Li + NBP * NBP;
         for (int idx = t; idx < NBP * NBP; idx += 256) T[(idx / NBP) * TI + idx % NBP] = Ui[idx];
-        for (int rr = warp; rr < nr; rr += 8) {
-            const float* src = M + (int64_t)(r0 + rr) * ld + J;
-            for (int j = lane; j < NBP; j += 32) S[rr * TS + j] = j < jb ? src[j] : 0.f;
+        // stage the nr x jb block A21 (zero beyond jb, a multiple of 4): 16-byte loads, all of a
+        // thread's issued before any is stored
+#pragma unroll 8
+        for (int idx = t; idx < PTILE * (NBP / 4); idx += 256) {
+            const int rr = idx >> 4, j4 = idx & 15;
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (rr < nr && 4 * j4 < jb) v = *reinterpret_cast<const float4*>(M + (int64_t)(r0 + rr) * ld + J + 4 * j4);
+            float* d = S + rr * TS + 4 * j4;
+            d[0] = v.x;
+            d[1] = v.y;
+            d[2] = v.z;
+            d[3] = v.w;
         }
         __syncthreads();
-        if (t < nr) {
-            float x[NBP];
+        if (t < nr) {  // x_j = sum_{i <= j} a_i Uinv[i][j], written over the row it came from
+            float a[NBP];
 #pragma unroll
-            for (int j = 0; j < NBP; ++j) x[j] = 0.f;
-            for (int i = 0; i < NBP; ++i) {  // x_j += a_i Uinv[i][j] (Uinv[i][j] = 0 for j < i)
-                const float ai = S[t * TS + i];
-                const float4* Tr = reinterpret_cast<const float4*>(T + i * TI);
-#pragma unroll
-                for (int j4 = 0; j4 < NBP / 4; ++j4) {
-                    const float4 u = Tr[j4];
-                    x[4 * j4] = fmaf(ai, u.x, x[4 * j4]);
-                    x[4 * j4 + 1] = fmaf(ai, u.y, x[4 * j4 + 1]);
-                    x[4 * j4 + 2] = fmaf(ai, u.z, x[4 * j4 + 2]);
-                    x[4 * j4 + 3] = fmaf(ai, u.w, x[4 * j4 + 3]);
-                }
-            }
-#pragma unroll
-            for (int j = 0; j < NBP; ++j) S[t * TS + j] = x[j];
+            for (int i = 0; i < NBP; ++i) a[i] = S[t * TS + i];
+            float* out = S + t * TS;
+            tri_apply<true>(a, T, [&](int b, float4 v) {
+                out[4 * b] = v.x;
+                out[4 * b + 1] = v.y;
+                out[4 * b + 2] = v.z;
+                out[4 * b + 3] = v.w;
+            });
         }
         __syncthreads();
         for (int rr = warp; rr < nr; rr += 8) {
@@ -204,36 +226,41 @@ __global__ void __launch_bounds__(256, 2) k_rowcol(int nu, int64_t ld, int64_t e
     const int nc = min(PTILE, c_end - c0);
     const float* Ti = col_mode == 0 ? Li : Li + NBP * NBP;
     for (int idx = t; idx < NBP * NBP; idx += 256) T[(idx % NBP) * TI + idx / NBP] = Ti[idx];  // transposed
-    // stage the jb x nc block A12 (row k of the panel in S[k][*]) with independent coalesced loads
-    for (int k = warp; k < NBP; k += 8)
-        for (int cc = lane; cc < PTILE; cc += 32)
-            S[k * PTILE + cc] = (k < jb && cc < nc) ? M[(int64_t)(J + k) * ld + c0 + cc] : 0.f;
+    // stage the jb x nc block A12 (row k of the panel in S[k][*]; c0 and nc are multiples of 4)
+    // with 16-byte loads, all of a thread's issued before any is stored
+#pragma unroll 8
+    for (int idx = t; idx < NBP * (PTILE / 4); idx += 256) {
+        const int k = idx / (PTILE / 4), c4 = idx % (PTILE / 4);
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (k < jb && 4 * c4 < nc) v = *reinterpret_cast<const float4*>(M + (int64_t)(J + k) * ld + c0 + 4 * c4);
+        *reinterpret_cast<float4*>(S + k * PTILE + 4 * c4) = v;
+    }
     __syncthreads();
-    float y[NBP];
+    float a[NBP];
     if (t < nc) {
 #pragma unroll
-        for (int i = 0; i < NBP; ++i) y[i] = 0.f;
-        for (int k = 0; k < NBP; ++k) {  // y_i += Tinv[i][k] a_k (the inverse is triangular: zeros elsewhere)
-            const float ak = S[k * PTILE + t];
-            const float4* Tc = reinterpret_cast<const float4*>(T + k * TI);
-#pragma unroll
-            for (int i4 = 0; i4 < NBP / 4; ++i4) {
-                const float4 u = Tc[i4];
-                y[4 * i4] = fmaf(u.x, ak, y[4 * i4]);
-                y[4 * i4 + 1] = fmaf(u.y, ak, y[4 * i4 + 1]);
-                y[4 * i4 + 2] = fmaf(u.z, ak, y[4 * i4 + 2]);
-                y[4 * i4 + 3] = fmaf(u.w, ak, y[4 * i4 + 3]);
-            }
-        }
+        for (int k = 0; k < NBP; ++k) a[k] = S[k * PTILE + t];
     }
     __syncthreads();  // S is reused: from [k][column] staging to [column][i] results
     if (t < nc) {
+        // y_i = sum_k Tinv[i][k] a_k with T[k][i] = Tinv[i][k]: the unit-lower L11^-1 (k <= i)
+        // or the upper U11^-1 (k >= i)
         const int c = c0 + t;
-#pragma unroll
-        for (int i = 0; i < NBP; ++i) {
-            if (i < jb) M[(int64_t)(J + i) * ld + c] = y[i];
-            S[t * TS + i] = y[i];
-        }
+        float* mc = M + (int64_t)J * ld + c;
+        float* sr = S + t * TS;
+        auto put = [&](int b, float4 v) {
+            const int i = 4 * b;
+            if (i < jb) mc[(int64_t)i * ld] = v.x;
+            if (i + 1 < jb) mc[(int64_t)(i + 1) * ld] = v.y;
+            if (i + 2 < jb) mc[(int64_t)(i + 2) * ld] = v.z;
+            if (i + 3 < jb) mc[(int64_t)(i + 3) * ld] = v.w;
+            sr[i] = v.x;
+            sr[i + 1] = v.y;
+            sr[i + 2] = v.z;
+            sr[i + 3] = v.w;
+        };
+        if (col_mode == 0) tri_apply<true>(a, T, put);
+        else tri_apply<false>(a, T, put);
     }
     __syncthreads();
     float* uh = Uh + e * ld * NBP;
