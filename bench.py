@@ -45,8 +45,7 @@ KERNEL_BOUND = {
 # partly fit in the 126 MB L2, so the matvec figure is a lower bound at 64 x 64.  Scaled to a
 # launch of the benchmark by elements / launches.
 DRAM_BYTES_PER_ELEMENT_STEP = {
-    "lu_tc_update": 7.053e7, "lu_tc_rowcol": 3.033e7, "lu_tc_diag": 2.359e5, "residual": 6.748e6,
-    "assemble": 3.277e6, "restrict": 2.019e6, "gemv": 2.431e7,
+    "lu_tc_diag": 2.359e5, "residual": 6.748e6, "assemble": 3.277e6, "restrict": 2.019e6, "gemv": 2.431e7,
 }
 
 
@@ -68,6 +67,7 @@ def parse():
     ap.add_argument("--mode", default="tf32ir", choices=["tf32ir", "fp32ir", "fp64"])
     ap.add_argument("--refine", type=int, default=1)
     ap.add_argument("--rtol", type=float, default=1e-8)
+    ap.add_argument("--restart", type=int, default=20, help="GMRES restart length")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nx", type=int, default=64, help="elements per side of the slab (64: the benchmark workload)")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-path section")
@@ -251,7 +251,7 @@ def learned_section(args, E, W, ctx, prob, kap, om, g, um_classical, peaks):
 
     def lstep():
         stats["nf"] = E.elrt_build_local_learned(ctx, net, kap, om, prob.h, i2o, i2m, tol=args.learned_tol)
-        stats["g"] = ctx.elrt_solve_global(prob.nx, prob.nz, i2o, g, sk, rtol=args.rtol, max_iter=20000, restart=50)
+        stats["g"] = ctx.elrt_solve_global(prob.nx, prob.nz, i2o, g, sk, rtol=args.rtol, max_iter=20000, restart=args.restart)
         ctx.elrt_recover_mean(prob.nx, prob.nz, i2m, sk, g, um)
 
     lstep()
@@ -272,7 +272,7 @@ def learned_section(args, E, W, ctx, prob, kap, om, g, um_classical, peaks):
     torch.cuda.synchronize()
     e0.record(stream)
     ctx.elrt_build_local(kap, om, prob.h, i2o64, i2m64, mode=E.LOCAL_FP64, stats=False)
-    g64 = ctx.elrt_solve_global(prob.nx, prob.nz, i2o64, g, sk, rtol=args.rtol, max_iter=20000, restart=50)
+    g64 = ctx.elrt_solve_global(prob.nx, prob.nz, i2o64, g, sk, rtol=args.rtol, max_iter=20000, restart=args.restart)
     ctx.elrt_recover_mean(prob.nx, prob.nz, i2m64, sk, g, um)
     e1.record(stream)
     torch.cuda.synchronize()
@@ -316,7 +316,7 @@ def run_ours(args, rank, world, local_rank):
 
     def step(k_, o_, g_, with_stats=False):
         lst = ctx.elrt_build_local(k_, o_, prob.h, i2o, i2m, mode=mode, refine_steps=args.refine, stats=with_stats)
-        gst = ctx.elrt_solve_global(nx, nz, i2o, g_, sk, rtol=args.rtol, max_iter=20000, restart=50)
+        gst = ctx.elrt_solve_global(nx, nz, i2o, g_, sk, rtol=args.rtol, max_iter=20000, restart=args.restart)
         ctx.elrt_recover_mean(nx, nz, i2m, sk, g_, um)
         info["local"], info["global"] = lst, gst
 
@@ -424,7 +424,7 @@ def run_ours(args, rank, world, local_rank):
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": {"tf32ir": "tf32x3+f32+ff", "fp32ir": "f32+ff", "fp64": "f64"}[args.mode], "data": "synthetic",
         "config": {"workload": workload_name(args.nx), "elements": n, "p": prob.p, "n_angles": prob.n_angles,
-                   "local_mode": args.mode, "refine_steps": args.refine, "gmres_rtol": args.rtol, "gmres_restart": 50,
+                   "local_mode": args.mode, "refine_steps": args.refine, "gmres_rtol": args.rtol, "gmres_restart": args.restart,
                    "operator_dtype": "f32", "parallelism": f"replicas x{world}",
                    "l2": "working set larger than L2 (in2out 822 MB, local workspace > 10 GB) on every step"},
         "breakdown_ms": {k: v[0] / args.steps for k, v in prof.items() if v[1]},

@@ -7,15 +7,18 @@
 //
 // The augmented matrix [A | -B^] of each element (FP32, row-major, leading dimension ld) is
 // factored in panels of 64 columns.  Per panel J:
-//   k_panel      (CUDA cores, one block per element): LU of the 64 x 64 diagonal block, then
-//                L21 = A21 U11^{-1} and U12 = L11^{-1} A12 (this also runs the forward substitution
-//                on the right-hand-side columns); L21 and U12^T are written, split into TF32 high
-//                and low parts, to K-major side buffers;
-//   k_tc_update  (tensor cores, one block per 128 x 64 tile of one element): C -= L21 U12 with
-//                three TF32 products hi*hi + hi*lo + lo*hi (FP32-level accuracy), operands by 3-D
-//                TMA (coordinates: k, row, element), C prefetched into registers while the MMAs run.
-// The backward substitution and the forward/backward sweeps of the refinement re-solves use the
-// same two-step pattern on the right-hand-side columns.
+//   k_diag             (one small block per element): LU of the 64 x 64 diagonal block and the
+//                      explicit inverses L11^{-1}, U11^{-1};
+//   k_rowcol           (blocks of 256 rows or columns per element): L21 = A21 U11^{-1} written
+//                      back to the matrix; U12 = L11^{-1} A12 written back to the matrix and,
+//                      transposed (K-major), to one FP32 side buffer.  On the right-hand-side
+//                      columns this is the forward substitution;
+//   k_tc_update_strip  (tensor cores): C -= L21 U12 with three TF32 products hi*hi + hi*lo +
+//                      lo*hi (FP32-level accuracy).  The FP32 operands come in by TMA (L21 straight
+//                      from the matrix, U12^T from the side buffer) and are split into TF32 high
+//                      and low parts in shared memory by four dedicated warps.
+// The backward substitution and the forward/backward sweeps of the refinement re-solves reuse
+// the stored factors (L21 and U12 in the matrix, the inverses) with the same kernels.
 #include <math.h>
 #include <stdio.h>
 
@@ -31,25 +34,11 @@ namespace {
 
 constexpr int NBP = 64;     // panel width (= K of the trailing update)
 constexpr int UBN = 64;     // trailing-update tile width
-constexpr int UTHREADS = 128;
 
 __device__ __forceinline__ float tf32_hi(float a) { return __uint_as_float(__float_as_uint(a) & 0xFFFFE000u); }
 
-__device__ __forceinline__ void put_split(float* hi, float* lo, int64_t idx, float v) {
-    const float h = tf32_hi(v);
-    hi[idx] = h;
-    lo[idx] = v - h;
-}
-
 // ------------------------------------------------------------------------------------------------
 // panel kernels (CUDA cores)
-//   k_diag:   one small block per element factors the 64 x 64 diagonal block and stores the
-//             explicit inverses L11^{-1} (unit lower) and U11^{-1} of every panel;
-//   k_rowcol: many blocks per element; a row tile forms L21 rows x = a U11^{-1}, a column tile
-//             forms U12 columns y = L11^{-1} a (or, in the sweeps of a re-solve, applies L^{-1} or
-//             U^{-1} to right-hand-side columns).  Both are 64 x 64 triangular matvecs with 64
-//             independent accumulators per thread; rows and columns are staged through shared
-//             memory (stride 65) so every global access is coalesced.
 // ------------------------------------------------------------------------------------------------
 
 constexpr int TS = NBP + 1;
@@ -133,12 +122,6 @@ __global__ void __launch_bounds__(64) k_diag(int nu, int64_t ld, int64_t estride
     }
 }
 
-// Row/column work of one panel.  Tiles 0 .. nrt-1 are row tiles over rows [r_begin, r_end), the
-// remaining ones column tiles over columns [c_begin, c_end).
-//   row_mode 0: x = a U11^{-1} written to M and to the L split buffers (factorisation);
-//   row_mode 1: rows copied into the L split buffers (sweeps).
-//   col_mode 0: y = L11^{-1} a (factorisation and forward sweep); 1: y = U11^{-1} a (backward sweep);
-//   y goes back to M and, transposed, to the U split buffers.
 // out[4b .. 4b+3] = sum_k a[k] T[k][4b .. 4b+3] over the nonzero part of a triangular T (stored
 // with row stride TI): k in [0, 4b + 4) when LOWER_K (T[k][j] = 0 for k > j), k in [4b, 64)
 // otherwise.  Each 4-wide block is handed to put(b, float4) as soon as it is complete.
@@ -159,14 +142,18 @@ __device__ __forceinline__ void tri_apply(const float (&a)[NBP], const float* __
     }
 }
 
+// Row/column work of one panel.  Tiles 0 .. nrt-1 are row tiles over rows [r_begin, r_end) (the
+// factorisation only): x = a U11^{-1} written back to the matrix.  The remaining tiles are column
+// tiles over columns [c_begin, c_end): y = L11^{-1} a (col_mode 0: factorisation and forward
+// sweep) or y = U11^{-1} a (col_mode 1: backward sweep), written back to the matrix (rows < jb)
+// and, transposed, to the side buffer Ut[e][column][0..63] (zero beyond jb).
 __global__ void __launch_bounds__(256, 2) k_rowcol(int nu, int64_t ld, int64_t estride, float* __restrict__ Mall, int J,
                                                    int jb, const float* __restrict__ Tinv, int npanels, int r_begin,
-                                                   int r_end, int row_mode, int nrt, int c_begin, int c_end,
-                                                   int col_mode, float* __restrict__ Lh, float* __restrict__ Ll,
-                                                   float* __restrict__ Uh, float* __restrict__ Ul) {
+                                                   int r_end, int nrt, int c_begin, int c_end, int col_mode,
+                                                   float* __restrict__ Ut) {
     extern __shared__ float sm[];
     float* S = sm;                 // PTILE x TS staging
-    float* T = sm + PTILE * TS;    // 64 x TS inverse
+    float* T = sm + PTILE * TS;    // 64 x TI inverse
     const int64_t e = blockIdx.x;
     float* M = Mall + e * estride;
     const int tile = blockIdx.y;
@@ -175,15 +162,6 @@ __global__ void __launch_bounds__(256, 2) k_rowcol(int nu, int64_t ld, int64_t e
     if (tile < nrt) {
         const int r0 = r_begin + tile * PTILE;
         const int nr = min(PTILE, r_end - r0);
-        float* lh = Lh + e * (int64_t)nu * NBP;
-        float* ll = Ll + e * (int64_t)nu * NBP;
-        if (row_mode == 1) {
-            for (int r = r0 + warp; r < r0 + nr; r += 8) {
-                const float* src = M + (int64_t)r * ld + J;
-                for (int j = lane; j < NBP; j += 32) put_split(lh, ll, (int64_t)r * NBP + j, j < jb ? src[j] : 0.f);
-            }
-            return;
-        }
         const float* Ui = Li + NBP * NBP;
         for (int idx = t; idx < NBP * NBP; idx += 256) T[(idx / NBP) * TI + idx % NBP] = Ui[idx];
         // stage the nr x jb block A21 (zero beyond jb, a multiple of 4): 16-byte loads, all of a
@@ -213,13 +191,8 @@ __global__ void __launch_bounds__(256, 2) k_rowcol(int nu, int64_t ld, int64_t e
             });
         }
         __syncthreads();
-        for (int rr = warp; rr < nr; rr += 8) {
-            for (int j = lane; j < NBP; j += 32) {
-                const float v = S[rr * TS + j];
-                if (j < jb) M[(int64_t)(r0 + rr) * ld + J + j] = v;
-                put_split(lh, ll, (int64_t)(r0 + rr) * NBP + j, v);
-            }
-        }
+        for (int rr = warp; rr < nr; rr += 8)
+            for (int j = lane; j < jb; j += 32) M[(int64_t)(r0 + rr) * ld + J + j] = S[rr * TS + j];
         return;
     }
     const int c0 = c_begin + (tile - nrt) * PTILE;
@@ -263,10 +236,9 @@ __global__ void __launch_bounds__(256, 2) k_rowcol(int nu, int64_t ld, int64_t e
         else tri_apply<false>(a, T, put);
     }
     __syncthreads();
-    float* uh = Uh + e * ld * NBP;
-    float* ul = Ul + e * ld * NBP;
+    float* ut = Ut + e * ld * NBP;
     for (int cc = warp; cc < nc; cc += 8)
-        for (int i = lane; i < NBP; i += 32) put_split(uh, ul, (int64_t)(c0 + cc) * NBP + i, S[cc * TS + i]);
+        for (int i = lane; i < NBP; i += 32) ut[(int64_t)(c0 + cc) * NBP + i] = S[cc * TS + i];
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -293,177 +265,65 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint6
         "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate));
 }
 
-struct UpdSmem {
-    static constexpr int A_KB = 128 * 32 * 4;   // one 128-row x 32-k block (128-byte rows)
-    static constexpr int B_KB = UBN * 32 * 4;
-    static constexpr int BYTES = 4 * A_KB + 4 * B_KB;  // {hi, lo} x 2 k-blocks for A and B
-    static constexpr int TOTAL = BYTES + 1024 + 64;
-};
-
-// C[m][n] -= sum_k A[m][k] B[n][k] for rows m in [r0, r_end) and columns n in [c0, c_end) of every
-// element.  A rows come from the A side buffers at row index m, B rows at index n.
-__global__ void __launch_bounds__(UTHREADS, 2)
-    k_tc_update(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUtensorMap tAl,
-                const __grid_constant__ CUtensorMap tBh, const __grid_constant__ CUtensorMap tBl, float* __restrict__ Mall,
-                int64_t ld, int64_t estride, int r0, int r_end, int c0, int c_end, int* __restrict__ err) {
-    extern __shared__ __align__(1024) unsigned char usm_raw[];
-    unsigned char* base = (unsigned char*)(((uintptr_t)usm_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char* Ah = base;                        // [2 kb]
-    unsigned char* Al = Ah + 2 * UpdSmem::A_KB;
-    unsigned char* Bh = Al + 2 * UpdSmem::A_KB;
-    unsigned char* Bl = Bh + 2 * UpdSmem::B_KB;
-    uint64_t* full = (uint64_t*)(base + UpdSmem::BYTES);
-    uint64_t* accb = full + 1;
-    uint32_t* tmem_slot = (uint32_t*)(accb + 1);
-    volatile int* abort = (volatile int*)(tmem_slot + 1);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int e = blockIdx.z;
-    const int m0 = r0 + blockIdx.x * 128, n0 = c0 + blockIdx.y * UBN;
-    if (threadIdx.x == 0) {
-        tc::mbar_init(full, 1);
-        tc::mbar_init(accb, 1);
-        *abort = 0;
-        tc::fence_barrier_init();
-    }
-    if (warp == 1) {
-        tc::tmem_alloc(tmem_slot, UBN);
-        tc::tmem_relinquish();
-    }
-    tc::tc_fence_before();
-    __syncthreads();
-    tc::tc_fence_after();
-    const uint32_t tmem = *tmem_slot;
-    if (threadIdx.x == 0) {
-        tc::mbar_expect_tx(full, UpdSmem::BYTES);
-        for (int kb = 0; kb < 2; ++kb) {
-            tma_load_3d(&tAh, full, Ah + kb * UpdSmem::A_KB, kb * 32, m0, e);
-            tma_load_3d(&tAl, full, Al + kb * UpdSmem::A_KB, kb * 32, m0, e);
-            tma_load_3d(&tBh, full, Bh + kb * UpdSmem::B_KB, kb * 32, n0, e);
-            tma_load_3d(&tBl, full, Bl + kb * UpdSmem::B_KB, kb * 32, n0, e);
-        }
-    }
-    // prefetch this thread's row of the C tile while the copies and MMAs run
-    float* M = Mall + (int64_t)e * estride;
-    const int m = m0 + warp * 32 + lane;
-    const bool row_ok = m < r_end;
-    float cv[UBN];
-    const bool full_cols = n0 + UBN <= c_end;
-#pragma unroll
-    for (int q = 0; q < UBN / 4; ++q) {
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (row_ok) {
-            if (full_cols) {
-                v = *reinterpret_cast<const float4*>(M + (int64_t)m * ld + n0 + 4 * q);
-            } else {
-                const float* src = M + (int64_t)m * ld + n0 + 4 * q;
-                if (n0 + 4 * q + 0 < c_end) v.x = src[0];
-                if (n0 + 4 * q + 1 < c_end) v.y = src[1];
-                if (n0 + 4 * q + 2 < c_end) v.z = src[2];
-                if (n0 + 4 * q + 3 < c_end) v.w = src[3];
-            }
-        }
-        cv[4 * q] = v.x;
-        cv[4 * q + 1] = v.y;
-        cv[4 * q + 2] = v.z;
-        cv[4 * q + 3] = v.w;
-    }
-    if (threadIdx.x == 32) {
-        constexpr uint32_t idesc = idesc_tf32(128, UBN);
-        if (tc::mbar_wait(full, 0, abort)) {
-            tc::tc_fence_after();
-            uint32_t acc = 0;
-            for (int kb = 0; kb < 2; ++kb) {
-                const uint64_t ah = tc::sw128_desc(tc::smem_u32(Ah + kb * UpdSmem::A_KB));
-                const uint64_t al = tc::sw128_desc(tc::smem_u32(Al + kb * UpdSmem::A_KB));
-                const uint64_t bh = tc::sw128_desc(tc::smem_u32(Bh + kb * UpdSmem::B_KB));
-                const uint64_t bl = tc::sw128_desc(tc::smem_u32(Bl + kb * UpdSmem::B_KB));
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {  // K = 8 per instruction: 32 bytes of each 128-byte row
-                    mma_tf32(tmem, ah + 2 * k, bh + 2 * k, idesc, acc);
-                    acc = 1;
-                    mma_tf32(tmem, ah + 2 * k, bl + 2 * k, idesc, 1);
-                    mma_tf32(tmem, al + 2 * k, bh + 2 * k, idesc, 1);
-                }
-            }
-        } else {
-            if (err) atomicOr(err, 16);
-            *abort = 1;
-        }
-        tc::mma_commit(accb);
-    }
-    const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(accb, 0, abort) && !*abort);
-    tc::tc_fence_after();
-    if (ok) {
-#pragma unroll
-        for (int c = 0; c < UBN; c += 16) {
-            float d[16];
-            tc::tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c, d);
-#pragma unroll
-            for (int j = 0; j < 16; ++j) cv[c + j] -= d[j];
-        }
-        if (row_ok) {
-#pragma unroll
-            for (int q = 0; q < UBN / 4; ++q) {
-                float* dst = M + (int64_t)m * ld + n0 + 4 * q;
-                if (full_cols) {
-                    *reinterpret_cast<float4*>(dst) = make_float4(cv[4 * q], cv[4 * q + 1], cv[4 * q + 2], cv[4 * q + 3]);
-                } else {
-                    if (n0 + 4 * q + 0 < c_end) dst[0] = cv[4 * q];
-                    if (n0 + 4 * q + 1 < c_end) dst[1] = cv[4 * q + 1];
-                    if (n0 + 4 * q + 2 < c_end) dst[2] = cv[4 * q + 2];
-                    if (n0 + 4 * q + 3 < c_end) dst[3] = cv[4 * q + 3];
-                }
-            }
-        }
-    } else if (lane == 0 && err) {
-        atomicOr(err, 32);
-    }
-    tc::tc_fence_before();
-    __syncthreads();
-    if (warp == 1) {
-        if (lane == 0) {  // never free TMEM under an MMA in flight
-            const long long t0 = clock64();
-            while (!tc::mbar_try_wait(accb, 0) && clock64() - t0 < tc::kWaitCycles) {
-            }
-            const long long t1 = clock64();  // and let the operand copies land
-            while (!tc::mbar_try_wait(full, 0) && clock64() - t1 < tc::kWaitCycles / 4) {
-            }
-        }
-        __syncwarp();
-        tc::tc_fence_after();
-        tc::tmem_dealloc(tmem, UBN);
-    }
-}
-
-// Row-strip variant: one block per (128-row block, element) keeps its L21 tile resident and walks
-// the column tiles of [c0, c_end) through a two-stage ring: warp 0 loads the next U12 tile (hi/lo)
-// and the C tile (fp32, 128-byte swizzle, two 32-column boxes) by TMA, warp 1 issues the 3xTF32
-// MMAs into one of two TMEM accumulators, warps 2-5 read the accumulator and the staged C tile,
-// subtract and store.  Stage s is free again after the MMA commit and the four epilogue warps
-// have arrived (count 5).
+// One CTA per (128-row strip, element) keeps its L21 strip resident and walks the column tiles of
+// [c0, c_end) through a two-stage ring.  Warp 0 loads (TMA, 128-byte swizzle) the FP32 L21 strip
+// straight from the matrix (columns J .. J+63) once, and per tile the FP32 U12^T tile and the C
+// tile (two 32-column boxes); warps 6-9 split the FP32 operands in place into TF32 high parts and
+// write the low parts beside them (the columns of L21 at or beyond jb are zeroed); warp 1 issues
+// the 3xTF32 MMAs into one of two TMEM accumulators; warps 2-5 read the accumulator and the
+// staged C tile, subtract and store.  Stage s is free again after the MMA commit and the four
+// epilogue warps have arrived (count 5).  Every wait is bounded; on a timeout the CTA records a
+// code in *err, stops issuing work, lets its copies land and frees its TMEM.
 struct StripSmem {
-    static constexpr int A_KB = 128 * 32 * 4;
-    static constexpr int B_KB = UBN * 32 * 4;
+    static constexpr int A_KB = 128 * 32 * 4;                 // one 32-column box of the strip
+    static constexpr int B_KB = UBN * 32 * 4;                 // one 32-column box of a U12^T tile
     static constexpr int C_HALF = 128 * 32 * 4;               // one 32-column box of the C tile
     static constexpr int A_BYTES = 4 * A_KB;                  // {hi, lo} x 2 k-blocks
     static constexpr int STAGE = 4 * B_KB + 2 * C_HALF;       // B {hi, lo} x 2 k-blocks + C tile
+    static constexpr int A_TX = 2 * A_KB;                     // FP32 strip copied per CTA
+    static constexpr int STAGE_TX = 2 * B_KB + 2 * C_HALF;    // FP32 U12^T tile + C tile per stage
     static constexpr int BYTES = A_BYTES + 2 * STAGE;
     static constexpr int TOTAL = BYTES + 1024 + 128;
 };
+constexpr int kStripThreads = 320;
 
-__global__ void __launch_bounds__(192, 1)
-    k_tc_update_strip(const __grid_constant__ CUtensorMap tAh, const __grid_constant__ CUtensorMap tAl,
-                      const __grid_constant__ CUtensorMap tBh, const __grid_constant__ CUtensorMap tBl,
-                      const __grid_constant__ CUtensorMap tC, float* __restrict__ Mall, int64_t ld, int64_t estride,
-                      int r0, int r_end, int c0, int c_end, int* __restrict__ err) {
+// In-place TF32 split of one 128-byte-swizzled box of `rows` rows x 32 FP32 (k-block kb): hi
+// stays, lo goes to the same offset in `lo`; with kmask, entries whose column kb*32 + k is at or
+// beyond jb become 0.  Threads tid .. of nthr cooperate, 16 bytes each.
+__device__ __forceinline__ void split_box(unsigned char* box, unsigned char* lo, int rows, int kb, int jb, bool kmask,
+                                          int tid, int nthr) {
+    for (int q = tid; q < rows * 8; q += nthr) {
+        const int row = q >> 3, pc = q & 7;          // physical 16-byte chunk of the row
+        const int kcol = kb * 32 + ((pc ^ (row & 7)) << 2);
+        float4* hp = reinterpret_cast<float4*>(box + row * 128 + pc * 16);
+        float4 v = *hp;
+        if (kmask) {
+            if (kcol + 0 >= jb) v.x = 0.f;
+            if (kcol + 1 >= jb) v.y = 0.f;
+            if (kcol + 2 >= jb) v.z = 0.f;
+            if (kcol + 3 >= jb) v.w = 0.f;
+        }
+        const float4 h = make_float4(tf32_hi(v.x), tf32_hi(v.y), tf32_hi(v.z), tf32_hi(v.w));
+        *hp = h;
+        *reinterpret_cast<float4*>(lo + row * 128 + pc * 16) =
+            make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+    }
+}
+
+__global__ void __launch_bounds__(kStripThreads, 1)
+    k_tc_update_strip(const __grid_constant__ CUtensorMap tM, const __grid_constant__ CUtensorMap tU, float* __restrict__ Mall,
+                      int64_t ld, int64_t estride, int J, int jb, int r0, int r_end, int c0, int c_end,
+                      int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char ssm_raw[];
     unsigned char* base = (unsigned char*)(((uintptr_t)ssm_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* Ah = base;
     unsigned char* Al = Ah + 2 * StripSmem::A_KB;
     unsigned char* stage0 = base + StripSmem::A_BYTES;
     uint64_t* a_full = (uint64_t*)(base + StripSmem::BYTES);
-    uint64_t* full = a_full + 1;       // [2]
-    uint64_t* empty = full + 2;        // [2]
+    uint64_t* a_ready = a_full + 1;
+    uint64_t* full = a_ready + 1;      // [2]
+    uint64_t* bready = full + 2;       // [2]
+    uint64_t* empty = bready + 2;      // [2]
     uint64_t* acc_full = empty + 2;    // [2]
     uint64_t* acc_empty = acc_full + 2;  // [2]
     uint32_t* tmem_slot = (uint32_t*)(acc_empty + 2);
@@ -474,8 +334,10 @@ __global__ void __launch_bounds__(192, 1)
     const int ntile = (c_end - c0 + UBN - 1) / UBN;
     if (threadIdx.x == 0) {
         tc::mbar_init(a_full, 1);
+        tc::mbar_init(a_ready, 4);
         for (int i = 0; i < 2; ++i) {
             tc::mbar_init(&full[i], 1);
+            tc::mbar_init(&bready[i], 4);
             tc::mbar_init(&empty[i], 5);
             tc::mbar_init(&acc_full[i], 1);
             tc::mbar_init(&acc_empty[i], 4);
@@ -491,13 +353,10 @@ __global__ void __launch_bounds__(192, 1)
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    int committed = 0;
+    int committed = 0, issued = 0;
     if (warp == 0 && lane == 0) {
-        tc::mbar_expect_tx(a_full, StripSmem::A_BYTES);
-        for (int kb = 0; kb < 2; ++kb) {
-            tma_load_3d(&tAh, a_full, Ah + kb * StripSmem::A_KB, kb * 32, m0, e);
-            tma_load_3d(&tAl, a_full, Al + kb * StripSmem::A_KB, kb * 32, m0, e);
-        }
+        tc::mbar_expect_tx(a_full, StripSmem::A_TX);
+        for (int kb = 0; kb < 2; ++kb) tma_load_3d(&tM, a_full, Ah + kb * StripSmem::A_KB, J + kb * 32, m0, e);
         for (int t = 0; t < ntile; ++t) {
             const int s = t & 1;
             if (!tc::mbar_wait(&empty[s], ((t >> 1) & 1) ^ 1, abort)) {
@@ -507,20 +366,19 @@ __global__ void __launch_bounds__(192, 1)
             }
             unsigned char* st = stage0 + s * StripSmem::STAGE;
             const int n0 = c0 + t * UBN;
-            tc::mbar_expect_tx(&full[s], StripSmem::STAGE);
-            for (int kb = 0; kb < 2; ++kb) {
-                tma_load_3d(&tBh, &full[s], st + kb * StripSmem::B_KB, kb * 32, n0, e);
-                tma_load_3d(&tBl, &full[s], st + (2 + kb) * StripSmem::B_KB, kb * 32, n0, e);
-            }
-            tma_load_3d(&tC, &full[s], st + 4 * StripSmem::B_KB, n0, m0, e);
-            tma_load_3d(&tC, &full[s], st + 4 * StripSmem::B_KB + StripSmem::C_HALF, n0 + 32, m0, e);
+            tc::mbar_expect_tx(&full[s], StripSmem::STAGE_TX);
+            for (int kb = 0; kb < 2; ++kb) tma_load_3d(&tU, &full[s], st + kb * StripSmem::B_KB, kb * 32, n0, e);
+            tma_load_3d(&tM, &full[s], st + 4 * StripSmem::B_KB, n0, m0, e);
+            tma_load_3d(&tM, &full[s], st + 4 * StripSmem::B_KB + StripSmem::C_HALF, n0 + 32, m0, e);
+            ++issued;
         }
     } else if (warp == 1 && lane == 0) {
         constexpr uint32_t idesc = idesc_tf32(128, UBN);
-        bool ok = tc::mbar_wait(a_full, 0, abort);
+        bool ok = tc::mbar_wait(a_ready, 0, abort);
         for (int t = 0; t < ntile && ok; ++t) {
             const int s = t & 1, a = t & 1;
-            if (!tc::mbar_wait(&acc_empty[a], ((t >> 1) & 1) ^ 1, abort) || !tc::mbar_wait(&full[s], (t >> 1) & 1, abort)) {
+            if (!tc::mbar_wait(&acc_empty[a], ((t >> 1) & 1) ^ 1, abort) ||
+                !tc::mbar_wait(&bready[s], (t >> 1) & 1, abort)) {
                 ok = false;
                 break;
             }
@@ -547,6 +405,34 @@ __global__ void __launch_bounds__(192, 1)
         }
         if (!ok) {
             if (err) atomicOr(err, 128);
+            *abort = 1;
+        }
+    } else if (warp >= 6) {  // splitters
+        const int tid = threadIdx.x - 6 * 32;
+        bool ok = __all_sync(0xffffffffu, tc::mbar_wait(a_full, 0, abort));
+        if (ok) {
+            for (int kb = 0; kb < 2; ++kb)
+                split_box(Ah + kb * StripSmem::A_KB, Al + kb * StripSmem::A_KB, 128, kb, jb, true, tid, 128);
+            // generic-proxy writes, read next by the tensor cores (async proxy)
+            tc::fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(a_ready)) : "memory");
+        }
+        for (int t = 0; t < ntile && ok; ++t) {
+            const int s = t & 1;
+            if (!__all_sync(0xffffffffu, tc::mbar_wait(&full[s], (t >> 1) & 1, abort) && !*abort)) {
+                ok = false;
+                break;
+            }
+            unsigned char* st = stage0 + s * StripSmem::STAGE;
+            for (int kb = 0; kb < 2; ++kb)
+                split_box(st + kb * StripSmem::B_KB, st + (2 + kb) * StripSmem::B_KB, UBN, kb, jb, false, tid, 128);
+            tc::fence_proxy_async();
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&bready[s])) : "memory");
+        }
+        if (!ok && lane == 0) {
+            if (err) atomicOr(err, 512);
             *abort = 1;
         }
     } else if (warp >= 2) {
@@ -614,16 +500,21 @@ __global__ void __launch_bounds__(192, 1)
     }
     tc::tc_fence_before();
     __syncthreads();
-    if (warp == 1) {
-        if (lane == 0) {
-            if (committed > 0) {
-                const int last = committed - 1;
-                const long long t0 = clock64();
-                while (!tc::mbar_try_wait(&acc_full[last & 1], (last >> 1) & 1) && clock64() - t0 < tc::kWaitCycles) {
-                }
+    if (warp == 0 && lane == 0) {  // let every copy this CTA issued land before the CTA exits
+        const long long t0 = clock64();
+        while (!tc::mbar_try_wait(a_full, 0) && clock64() - t0 < tc::kWaitCycles / 4) {
+        }
+        for (int q = (issued > 2 ? issued - 2 : 0); q < issued; ++q) {
+            const long long t1 = clock64();
+            while (!tc::mbar_try_wait(&full[q & 1], (q >> 1) & 1) && clock64() - t1 < tc::kWaitCycles / 4) {
             }
-            const long long t1 = clock64();  // the resident tile's copy
-            while (!tc::mbar_try_wait(a_full, 0) && clock64() - t1 < tc::kWaitCycles / 4) {
+        }
+    }
+    if (warp == 1) {
+        if (lane == 0 && committed > 0) {  // never free TMEM under an MMA in flight
+            const int last = committed - 1;
+            const long long t0 = clock64();
+            while (!tc::mbar_try_wait(&acc_full[last & 1], (last >> 1) & 1) && clock64() - t0 < tc::kWaitCycles) {
             }
         }
         __syncwarp();
@@ -637,7 +528,6 @@ __global__ void __launch_bounds__(192, 1)
 // ------------------------------------------------------------------------------------------------
 
 PFN_cuTensorMapEncodeTiled_v12000 g_enc = nullptr;
-bool g_strip = true;  // row-strip pipelined trailing update (else one block per tile)
 std::once_flag g_enc_once;
 
 bool enc_ready() {
@@ -652,7 +542,7 @@ bool enc_ready() {
     return g_enc != nullptr;
 }
 
-// [E][rows][64] fp32 side buffer, box 32 (k) x box_rows x 1 element, 128-byte swizzle
+// [E][rows][64] FP32 side buffer, box 32 (k) x box_rows x 1 element, 128-byte swizzle
 bool map3(CUtensorMap* m, const float* p, int64_t rows, int64_t E, int box_rows) {
     cuuint64_t dims[3] = {(cuuint64_t)NBP, (cuuint64_t)rows, (cuuint64_t)E};
     cuuint64_t strides[2] = {(cuuint64_t)NBP * 4, (cuuint64_t)rows * NBP * 4};
@@ -663,30 +553,9 @@ bool map3(CUtensorMap* m, const float* p, int64_t rows, int64_t E, int box_rows)
                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-struct TcMaps {
-    CUtensorMap ah, al, bh, bl, c;
-};
-
-// Trailing update C -= L U over rows [r0, r_end) and columns [c0, c_end) of every element, K = jb.
-// Algorithmic bytes: C read and written, the hi/lo splits of L (rows x 64) and U (64 x columns).
-elrt_status update(elrt_ctx* ctx, const TcMaps& mp, float* M, int64_t ld, int64_t estride, int64_t E, int r0, int r_end,
-                   int c0, int c_end, int jb, int* err) {
-    if (r_end <= r0 || c_end <= c0) return ELRT_OK;
-    const double R = r_end - r0, C = c_end - c0;
-    ProfScope ps(ctx, "lu_tc_update", 1, (double)E * (8.0 * R * C + 8.0 * (R + C) * NBP), (double)E * 2.0 * R * C * jb);
-    if (g_strip) {
-        dim3 grid((r_end - r0 + 127) / 128, (unsigned)E);
-        k_tc_update_strip<<<grid, 192, StripSmem::TOTAL, ctx->stream>>>(mp.ah, mp.al, mp.bh, mp.bl, mp.c, M, ld, estride,
-                                                                          r0, r_end, c0, c_end, err);
-    } else {
-        dim3 grid((r_end - r0 + 127) / 128, (c_end - c0 + UBN - 1) / UBN, (unsigned)E);
-        k_tc_update<<<grid, UTHREADS, UpdSmem::TOTAL, ctx->stream>>>(mp.ah, mp.al, mp.bh, mp.bl, M, ld, estride, r0,
-                                                                     r_end, c0, c_end, err);
-    }
-    return cuda_check(ctx, cudaGetLastError(), "tc update launch");
-}
-
-bool mapC(CUtensorMap* m, const float* M, int64_t nu, int64_t ld, int64_t estride, int64_t E) {
+// the matrix of every element, [E][nu][ld], box 32 columns x 128 rows x 1 element, 128-byte swizzle
+// (the L21 / U column block of a strip and the C tiles)
+bool mapM(CUtensorMap* m, const float* M, int64_t nu, int64_t ld, int64_t estride, int64_t E) {
     cuuint64_t dims[3] = {(cuuint64_t)ld, (cuuint64_t)nu, (cuuint64_t)E};
     cuuint64_t strides[2] = {(cuuint64_t)ld * 4, (cuuint64_t)estride * 4};
     cuuint32_t box[3] = {32, 128, 1};
@@ -696,21 +565,36 @@ bool mapC(CUtensorMap* m, const float* M, int64_t nu, int64_t ld, int64_t estrid
                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-elrt_status prepare(elrt_ctx* ctx, const float* Lh, const float* Ll, const float* Uh, const float* Ul, int64_t ld,
-                    int64_t E, TcMaps* mp, const float* M = nullptr, int64_t estride = 0) {
+struct TcMaps {
+    CUtensorMap m, u;
+};
+
+// Trailing update C -= L U over rows [r0, r_end) and columns [c0, c_end) of every element, with
+// L = M[rows, J .. J+jb) and U^T from the side buffer.  Algorithmic bytes: C read and written, the
+// FP32 L strip (R x 64) and U^T tile (C x 64).
+elrt_status update(elrt_ctx* ctx, const TcMaps& mp, float* M, int64_t ld, int64_t estride, int64_t E, int J, int jb,
+                   int r0, int r_end, int c0, int c_end, int* err) {
+    if (r_end <= r0 || c_end <= c0) return ELRT_OK;
+    const double R = r_end - r0, C = c_end - c0;
+    ProfScope ps(ctx, "lu_tc_update", 1, (double)E * (8.0 * R * C + 4.0 * (R + C) * NBP), (double)E * 2.0 * R * C * jb);
+    dim3 grid((r_end - r0 + 127) / 128, (unsigned)E);
+    k_tc_update_strip<<<grid, kStripThreads, StripSmem::TOTAL, ctx->stream>>>(mp.m, mp.u, M, ld, estride, J, jb, r0,
+                                                                              r_end, c0, c_end, err);
+    return cuda_check(ctx, cudaGetLastError(), "tc update launch");
+}
+
+elrt_status prepare(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, const float* Ut, int64_t E, TcMaps* mp) {
     if (!enc_ready()) return ctx_fail(ctx, ELRT_ECUDA, "cuTensorMapEncodeTiled unavailable");
     if (E > 65535) return ctx_fail(ctx, ELRT_EINVAL, "tensor-core LU chunk above 65535 elements");
     const int nu = ctx->tab.nu;
     // every column block starts at a multiple of 64 or at nu, and the vector accesses and TMA copies
     // need each to start on a 16-byte boundary (n_angles % 4 == 0 already makes nu a multiple of 4)
     if (nu % 4 != 0 || ld % 4 != 0) return ctx_fail(ctx, ELRT_EINVAL, "tensor-core LU needs nu and ld multiples of 4");
-    if (!map3(&mp->ah, Lh, nu, E, 128) || !map3(&mp->al, Ll, nu, E, 128) || !map3(&mp->bh, Uh, ld, E, UBN) ||
-        !map3(&mp->bl, Ul, ld, E, UBN) || (M && !mapC(&mp->c, M, nu, ld, estride, E)))
+    if (!mapM(&mp->m, M, nu, ld, estride, E) || !map3(&mp->u, Ut, ld, E, UBN))
         return ctx_fail(ctx, ELRT_EINVAL, "tensor map encoding failed");
     static bool attr_done = false;
     if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(k_tc_update, cudaFuncAttributeMaxDynamicSharedMemorySize, UpdSmem::TOTAL);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rowcol, cudaFuncAttributeMaxDynamicSharedMemorySize, RC_SMEM);
+        cudaError_t e = cudaFuncSetAttribute(k_rowcol, cudaFuncAttributeMaxDynamicSharedMemorySize, RC_SMEM);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_tc_update_strip, cudaFuncAttributeMaxDynamicSharedMemorySize, StripSmem::TOTAL);
         if (e != cudaSuccess) return cuda_check(ctx, e, "smem attribute");
@@ -722,50 +606,46 @@ elrt_status prepare(elrt_ctx* ctx, const float* Lh, const float* Ll, const float
 int panels_of(int nu) { return (nu + NBP - 1) / NBP; }
 
 elrt_status rowcol(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, int64_t E, int J, int jb, const float* Tinv,
-                   int r_begin, int r_end, int row_mode, int c_begin, int c_end, int col_mode, float* Lh, float* Ll,
-                   float* Uh, float* Ul) {
+                   int r_begin, int r_end, int c_begin, int c_end, int col_mode, float* Ut) {
     const int nrt = r_end > r_begin ? (r_end - r_begin + PTILE - 1) / PTILE : 0;
     const int nct = c_end > c_begin ? (c_end - c_begin + PTILE - 1) / PTILE : 0;
     if (nrt + nct == 0) return ELRT_OK;
-    // algorithmic work per element: row tiles read R x jb (and write it back in mode 0) and write
-    // the hi/lo splits (R x 64); column tiles read and write jb x C and write the splits (C x 64);
-    // triangular products x Uinv (mode 0), Linv x (unit lower, mode 0) or Uinv x (mode 1)
+    // algorithmic work per element: row tiles read R x jb and write it back; column tiles read and
+    // write jb x C and write U^T (C x 64); triangular products x Uinv, Linv x (unit lower) or
+    // Uinv x
     const double R = std::max(0, r_end - r_begin), C = std::max(0, c_end - c_begin);
-    const double bytes = (row_mode == 0 ? 8.0 : 4.0) * R * jb + 8.0 * R * NBP + 8.0 * C * jb + 8.0 * C * NBP +
-                         4.0 * NBP * NBP;
-    const double flops = (row_mode == 0 ? R * jb * (jb + 1.0) : 0.0) +
-                         (col_mode == 0 ? C * jb * (jb - 1.0) : C * jb * (jb + 1.0));
+    const double bytes = 8.0 * R * jb + 8.0 * C * jb + 4.0 * C * NBP + 4.0 * NBP * NBP * ((R > 0) + (C > 0));
+    const double flops = R * jb * (jb + 1.0) + (col_mode == 0 ? C * jb * (jb - 1.0) : C * jb * (jb + 1.0));
     ProfScope ps(ctx, "lu_tc_rowcol", 1, (double)E * bytes, (double)E * flops);
     k_rowcol<<<dim3((unsigned)E, nrt + nct), 256, RC_SMEM, ctx->stream>>>(
-        ctx->tab.nu, ld, estride, M, J, jb, Tinv, panels_of(ctx->tab.nu), r_begin, r_end, row_mode, nrt, c_begin, c_end,
-        col_mode, Lh, Ll, Uh, Ul);
+        ctx->tab.nu, ld, estride, M, J, jb, Tinv, panels_of(ctx->tab.nu), r_begin, r_end, nrt, c_begin, c_end,
+        col_mode, Ut);
     return cuda_check(ctx, cudaGetLastError(), "rowcol launch");
 }
 
+// backward substitution on the right-hand-side columns: X_J = U11^{-1} X_J, then the rows above
+// lose U[0..J, J..J+jb) X_J
 elrt_status backward_sweep_tc(elrt_ctx* ctx, const TcMaps& mp, float* M, int64_t ld, int64_t estride, int64_t E,
-                              const float* Tinv, float* Lh, float* Ll, float* Uh, float* Ul, int* err) {
+                              const float* Tinv, float* Ut, int* err) {
     const int nu = ctx->tab.nu, nin = ctx->tab.nin;
     const int last = ((nu - 1) / NBP) * NBP;
     for (int J = last; J >= 0; J -= NBP) {
         const int jb = std::min(NBP, nu - J);
-        elrt_status s = rowcol(ctx, M, ld, estride, E, J, jb, Tinv, 0, J, 1, nu, nu + nin, 1, Lh, Ll, Uh, Ul);
-        if (!s) s = update(ctx, mp, M, ld, estride, E, 0, J, nu, nu + nin, jb, err);
+        elrt_status s = rowcol(ctx, M, ld, estride, E, J, jb, Tinv, 0, 0, nu, nu + nin, 1, Ut);
+        if (!s) s = update(ctx, mp, M, ld, estride, E, J, jb, 0, J, nu, nu + nin, err);
         if (s) return s;
     }
     return ELRT_OK;
 }
 
 struct Side {
-    float *Lh, *Ll, *Uh, *Ul, *Tinv;
+    float *Ut, *Tinv;
 };
 
-Side carve(float* side, int64_t E, int nu, int64_t ld) {
+Side carve(float* side, int64_t E, int64_t ld) {
     Side sd;
-    sd.Lh = side;
-    sd.Ll = sd.Lh + (size_t)E * nu * NBP;
-    sd.Uh = sd.Ll + (size_t)E * nu * NBP;
-    sd.Ul = sd.Uh + (size_t)E * ld * NBP;
-    sd.Tinv = sd.Ul + (size_t)E * ld * NBP;
+    sd.Ut = side;
+    sd.Tinv = sd.Ut + (size_t)E * ld * NBP;
     return sd;
 }
 
@@ -776,9 +656,9 @@ Side carve(float* side, int64_t E, int nu, int64_t ld) {
 elrt_status tc_lu_factor_solve(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, int64_t E, int* estat, float* side,
                                int* err) {
     const int nu = ctx->tab.nu, nin = ctx->tab.nin, ncols = nu + nin;
-    const Side sd = carve(side, E, nu, ld);
+    const Side sd = carve(side, E, ld);
     TcMaps mp;
-    elrt_status s = prepare(ctx, sd.Lh, sd.Ll, sd.Uh, sd.Ul, ld, E, &mp, M, estride);
+    elrt_status s = prepare(ctx, M, ld, estride, sd.Ut, E, &mp);
     if (s) return s;
     for (int J = 0; J < nu; J += NBP) {
         const int jb = std::min(NBP, nu - J);
@@ -788,29 +668,29 @@ elrt_status tc_lu_factor_solve(elrt_ctx* ctx, float* M, int64_t ld, int64_t estr
             ProfScope ps(ctx, "lu_tc_diag", 1, (double)E * (4.0 * jb * jb + 8.0 * NBP * NBP), (double)E * 4.0 / 3.0 * b3);
             k_diag<<<(unsigned)E, 64, 0, ctx->stream>>>(nu, ld, estride, M, J, jb, sd.Tinv, panels_of(nu), estat, 1e-6f);
         }
-        s = rowcol(ctx, M, ld, estride, E, J, jb, sd.Tinv, J + jb, nu, 0, J + jb, ncols, 0, sd.Lh, sd.Ll, sd.Uh, sd.Ul);
-        if (!s) s = update(ctx, mp, M, ld, estride, E, J + jb, nu, J + jb, ncols, jb, err);
+        s = rowcol(ctx, M, ld, estride, E, J, jb, sd.Tinv, J + jb, nu, J + jb, ncols, 0, sd.Ut);
+        if (!s) s = update(ctx, mp, M, ld, estride, E, J, jb, J + jb, nu, J + jb, ncols, err);
         if (s) return s;
     }
-    return backward_sweep_tc(ctx, mp, M, ld, estride, E, sd.Tinv, sd.Lh, sd.Ll, sd.Uh, sd.Ul, err);
+    return backward_sweep_tc(ctx, mp, M, ld, estride, E, sd.Tinv, sd.Ut, err);
 }
 
 // Re-solve A D = R for the right-hand sides in columns [nu, nu + nin) with the stored factors.
 elrt_status tc_lu_resolve(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, int64_t E, float* side, int* err) {
     const int nu = ctx->tab.nu, nin = ctx->tab.nin;
-    const Side sd = carve(side, E, nu, ld);
+    const Side sd = carve(side, E, ld);
     TcMaps mp;
-    elrt_status s = prepare(ctx, sd.Lh, sd.Ll, sd.Uh, sd.Ul, ld, E, &mp, M, estride);
+    elrt_status s = prepare(ctx, M, ld, estride, sd.Ut, E, &mp);
     if (s) return s;
     for (int J = 0; J < nu; J += NBP) {
         const int jb = std::min(NBP, nu - J);
-        s = rowcol(ctx, M, ld, estride, E, J, jb, sd.Tinv, J + jb, nu, 1, nu, nu + nin, 0, sd.Lh, sd.Ll, sd.Uh, sd.Ul);
-        if (!s) s = update(ctx, mp, M, ld, estride, E, J + jb, nu, nu, nu + nin, jb, err);
+        s = rowcol(ctx, M, ld, estride, E, J, jb, sd.Tinv, 0, 0, nu, nu + nin, 0, sd.Ut);
+        if (!s) s = update(ctx, mp, M, ld, estride, E, J, jb, J + jb, nu, nu, nu + nin, err);
         if (s) return s;
     }
-    return backward_sweep_tc(ctx, mp, M, ld, estride, E, sd.Tinv, sd.Lh, sd.Ll, sd.Uh, sd.Ul, err);
+    return backward_sweep_tc(ctx, mp, M, ld, estride, E, sd.Tinv, sd.Ut, err);
 }
 
 size_t tc_lu_side_floats(const Tab& t, int64_t ld) {
-    return (size_t)2 * NBP * (t.nu + ld) + (size_t)panels_of(t.nu) * 2 * NBP * NBP;
+    return (size_t)NBP * ld + (size_t)panels_of(t.nu) * 2 * NBP * NBP;
 }
