@@ -33,7 +33,7 @@
 namespace {
 
 constexpr int NBP = 64;     // panel width (= K of the trailing update)
-constexpr int UBN = 64;     // trailing-update tile width
+constexpr int UBN = 32;     // trailing-update tile width (N of the MMAs)
 
 __device__ __forceinline__ float tf32_hi(float a) { return __uint_as_float(__float_as_uint(a) & 0xFFFFE000u); }
 
@@ -265,26 +265,34 @@ __device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint6
         "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate));
 }
 
-// One CTA per (128-row strip, element) keeps its L21 strip resident and walks the column tiles of
-// [c0, c_end) through a two-stage ring.  Warp 0 loads (TMA, 128-byte swizzle) the FP32 L21 strip
-// straight from the matrix (columns J .. J+63) once, and per tile the FP32 U12^T tile and the C
-// tile (two 32-column boxes); warps 6-9 split the FP32 operands in place into TF32 high parts and
-// write the low parts beside them (the columns of L21 at or beyond jb are zeroed); warp 1 issues
-// the 3xTF32 MMAs into one of two TMEM accumulators; warps 2-5 read the accumulator and the
-// staged C tile, subtract and store.  Stage s is free again after the MMA commit and the four
-// epilogue warps have arrived (count 5).  Every wait is bounded; on a timeout the CTA records a
-// code in *err, stops issuing work, lets its copies land and frees its TMEM.
+// Persistent trailing update: one CTA per SM walks the work items (element, 128-row strip) of the
+// launch, items of one element consecutively (their U12^T tiles are shared through L2).  Per item
+// the FP32 L21 strip (columns J .. J+63 of the strip's rows, straight from the matrix) is loaded
+// by TMA into one of two strip buffers, so the next item's strip is copied and split while the
+// current item's tiles run; the 32-column tiles (FP32 U12^T tile + C tile) flow through a
+// three-stage ring that does not drain between items.
+//   warp 0       TMA producer (strips, tiles);
+//   warp 1       one thread issues the 3xTF32 MMAs (hi*hi + hi*lo + lo*hi, M = 128, N = 32) into
+//                one of two TMEM accumulators;
+//   warps 2-5    epilogue: accumulator (tcgen05.ld) and staged C tile -> C - L U -> global;
+//   warps 6-9    split the FP32 operands in place into TF32 high parts and write the low parts
+//                beside them (strip columns at or beyond jb are zeroed).
+// Stage s is free again after the MMA commit and the four epilogue warps (count 5); a strip
+// buffer after the MMA commit of its item's last tile.  Every wait is bounded; on a timeout the
+// CTA records a code in *err, stops issuing work, lets its copies land and frees its TMEM.
+constexpr int kUStages = 3;
 struct StripSmem {
-    static constexpr int A_KB = 128 * 32 * 4;                 // one 32-column box of the strip
+    static constexpr int A_KB = 128 * 32 * 4;                 // one 32-column box of a strip
+    static constexpr int A_BUF = 4 * A_KB;                    // {hi, lo} x 2 k-blocks
     static constexpr int B_KB = UBN * 32 * 4;                 // one 32-column box of a U12^T tile
-    static constexpr int C_HALF = 128 * 32 * 4;               // one 32-column box of the C tile
-    static constexpr int A_BYTES = 4 * A_KB;                  // {hi, lo} x 2 k-blocks
-    static constexpr int STAGE = 4 * B_KB + 2 * C_HALF;       // B {hi, lo} x 2 k-blocks + C tile
-    static constexpr int A_TX = 2 * A_KB;                     // FP32 strip copied per CTA
-    static constexpr int STAGE_TX = 2 * B_KB + 2 * C_HALF;    // FP32 U12^T tile + C tile per stage
-    static constexpr int BYTES = A_BYTES + 2 * STAGE;
-    static constexpr int TOTAL = BYTES + 1024 + 128;
+    static constexpr int C_BOX = 128 * UBN * 4;               // the C tile (one box)
+    static constexpr int STAGE = 4 * B_KB + C_BOX;            // B {hi, lo} x 2 k-blocks + C tile
+    static constexpr int A_TX = 2 * A_KB;                     // FP32 strip copied per item
+    static constexpr int STAGE_TX = 2 * B_KB + C_BOX;         // FP32 U12^T tile + C tile per stage
+    static constexpr int BYTES = 2 * A_BUF + kUStages * STAGE;
+    static constexpr int TOTAL = BYTES + 1024 + 256;
 };
+static_assert(StripSmem::TOTAL <= 227 * 1024, "trailing-update shared memory");
 constexpr int kStripThreads = 320;
 
 // In-place TF32 split of one 128-byte-swizzled box of `rows` rows x 32 FP32 (k-block kb): hi
@@ -310,37 +318,44 @@ __device__ __forceinline__ void split_box(unsigned char* box, unsigned char* lo,
     }
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
+}
+
 __global__ void __launch_bounds__(kStripThreads, 1)
     k_tc_update_strip(const __grid_constant__ CUtensorMap tM, const __grid_constant__ CUtensorMap tU, float* __restrict__ Mall,
-                      int64_t ld, int64_t estride, int J, int jb, int r0, int r_end, int c0, int c_end,
+                      int64_t ld, int64_t estride, int64_t E, int J, int jb, int r0, int r_end, int c0, int c_end,
                       int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char ssm_raw[];
     unsigned char* base = (unsigned char*)(((uintptr_t)ssm_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char* Ah = base;
-    unsigned char* Al = Ah + 2 * StripSmem::A_KB;
-    unsigned char* stage0 = base + StripSmem::A_BYTES;
-    uint64_t* a_full = (uint64_t*)(base + StripSmem::BYTES);
-    uint64_t* a_ready = a_full + 1;
-    uint64_t* full = a_ready + 1;      // [2]
-    uint64_t* bready = full + 2;       // [2]
-    uint64_t* empty = bready + 2;      // [2]
-    uint64_t* acc_full = empty + 2;    // [2]
-    uint64_t* acc_empty = acc_full + 2;  // [2]
+    unsigned char* abuf = base;                            // [2] strip buffers: Ah (2 boxes), Al (2 boxes)
+    unsigned char* stage0 = base + 2 * StripSmem::A_BUF;   // [kUStages]: Bh (2), Bl (2), C
+    uint64_t* a_full = (uint64_t*)(base + StripSmem::BYTES);  // [2]
+    uint64_t* a_ready = a_full + 2;                        // [2]
+    uint64_t* a_empty = a_ready + 2;                       // [2]
+    uint64_t* full = a_empty + 2;                          // [kUStages]
+    uint64_t* bready = full + kUStages;                    // [kUStages]
+    uint64_t* empty = bready + kUStages;                   // [kUStages]
+    uint64_t* acc_full = empty + kUStages;                 // [2]
+    uint64_t* acc_empty = acc_full + 2;                    // [2]
     uint32_t* tmem_slot = (uint32_t*)(acc_empty + 2);
     volatile int* abort = (volatile int*)(tmem_slot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int e = blockIdx.y;
-    const int m0 = r0 + blockIdx.x * 128;
+    const int nstrips = (r_end - r0 + 127) / 128;
+    const int64_t W = (int64_t)nstrips * E;
     const int ntile = (c_end - c0 + UBN - 1) / UBN;
     if (threadIdx.x == 0) {
-        tc::mbar_init(a_full, 1);
-        tc::mbar_init(a_ready, 4);
         for (int i = 0; i < 2; ++i) {
+            tc::mbar_init(&a_full[i], 1);
+            tc::mbar_init(&a_ready[i], 4);
+            tc::mbar_init(&a_empty[i], 1);
+            tc::mbar_init(&acc_full[i], 1);
+            tc::mbar_init(&acc_empty[i], 4);
+        }
+        for (int i = 0; i < kUStages; ++i) {
             tc::mbar_init(&full[i], 1);
             tc::mbar_init(&bready[i], 4);
             tc::mbar_init(&empty[i], 5);
-            tc::mbar_init(&acc_full[i], 1);
-            tc::mbar_init(&acc_empty[i], 4);
         }
         *abort = 0;
         tc::fence_barrier_init();
@@ -353,55 +368,85 @@ __global__ void __launch_bounds__(kStripThreads, 1)
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    int committed = 0, issued = 0;
+    int committed = 0, issued_t = 0, issued_a = 0;
     if (warp == 0 && lane == 0) {
-        tc::mbar_expect_tx(a_full, StripSmem::A_TX);
-        for (int kb = 0; kb < 2; ++kb) tma_load_3d(&tM, a_full, Ah + kb * StripSmem::A_KB, J + kb * 32, m0, e);
-        for (int t = 0; t < ntile; ++t) {
-            const int s = t & 1;
-            if (!tc::mbar_wait(&empty[s], ((t >> 1) & 1) ^ 1, abort)) {
-                if (err) atomicOr(err, 64);
-                *abort = 1;
-                break;
+        // strip j of this CTA into buffer j & 1 (free once item j - 2 is done)
+        auto load_strip = [&](int64_t w, int j) -> bool {
+            if (!tc::mbar_wait(&a_empty[j & 1], ((j >> 1) & 1) ^ 1, abort)) return false;
+            const int64_t e = w / nstrips;
+            const int m0 = r0 + (int)(w - e * nstrips) * 128;
+            unsigned char* ab = abuf + (j & 1) * StripSmem::A_BUF;
+            tc::mbar_expect_tx(&a_full[j & 1], StripSmem::A_TX);
+            for (int kb = 0; kb < 2; ++kb)
+                tma_load_3d(&tM, &a_full[j & 1], ab + kb * StripSmem::A_KB, J + kb * 32, m0, (int)e);
+            ++issued_a;
+            return true;
+        };
+        bool ok = load_strip(blockIdx.x, 0);
+        int g = 0, i = 0;
+        for (int64_t w = blockIdx.x; w < W && ok; w += gridDim.x, ++i) {
+            const int64_t e = w / nstrips;
+            const int m0 = r0 + (int)(w - e * nstrips) * 128;
+            for (int t = 0; t < ntile && ok; ++t, ++g) {
+                const int s = g % kUStages;
+                if (!tc::mbar_wait(&empty[s], ((g / kUStages) & 1) ^ 1, abort)) {
+                    ok = false;
+                    break;
+                }
+                unsigned char* st = stage0 + s * StripSmem::STAGE;
+                const int n0 = c0 + t * UBN;
+                tc::mbar_expect_tx(&full[s], StripSmem::STAGE_TX);
+                for (int kb = 0; kb < 2; ++kb) tma_load_3d(&tU, &full[s], st + kb * StripSmem::B_KB, kb * 32, n0, (int)e);
+                tma_load_3d(&tM, &full[s], st + 4 * StripSmem::B_KB, n0, m0, (int)e);
+                ++issued_t;
+                if (t == 0 && w + gridDim.x < W) ok = load_strip(w + gridDim.x, i + 1);  // next item's strip
             }
-            unsigned char* st = stage0 + s * StripSmem::STAGE;
-            const int n0 = c0 + t * UBN;
-            tc::mbar_expect_tx(&full[s], StripSmem::STAGE_TX);
-            for (int kb = 0; kb < 2; ++kb) tma_load_3d(&tU, &full[s], st + kb * StripSmem::B_KB, kb * 32, n0, e);
-            tma_load_3d(&tM, &full[s], st + 4 * StripSmem::B_KB, n0, m0, e);
-            tma_load_3d(&tM, &full[s], st + 4 * StripSmem::B_KB + StripSmem::C_HALF, n0 + 32, m0, e);
-            ++issued;
+        }
+        if (!ok) {
+            if (err) atomicOr(err, 64);
+            *abort = 1;
         }
     } else if (warp == 1 && lane == 0) {
         constexpr uint32_t idesc = idesc_tf32(128, UBN);
-        bool ok = tc::mbar_wait(a_ready, 0, abort);
-        for (int t = 0; t < ntile && ok; ++t) {
-            const int s = t & 1, a = t & 1;
-            if (!tc::mbar_wait(&acc_empty[a], ((t >> 1) & 1) ^ 1, abort) ||
-                !tc::mbar_wait(&bready[s], (t >> 1) & 1, abort)) {
+        bool ok = true;
+        int g = 0, i = 0;
+        for (int64_t w = blockIdx.x; w < W && ok; w += gridDim.x, ++i) {
+            const int ab = i & 1;
+            if (!tc::mbar_wait(&a_ready[ab], (i >> 1) & 1, abort)) {
                 ok = false;
                 break;
             }
-            tc::tc_fence_after();
-            unsigned char* st = stage0 + s * StripSmem::STAGE;
-            const uint32_t d = tmem + (uint32_t)(a * UBN);
-            uint32_t acc = 0;
-            for (int kb = 0; kb < 2; ++kb) {
-                const uint64_t ah = tc::sw128_desc(tc::smem_u32(Ah + kb * StripSmem::A_KB));
-                const uint64_t al = tc::sw128_desc(tc::smem_u32(Al + kb * StripSmem::A_KB));
-                const uint64_t bh = tc::sw128_desc(tc::smem_u32(st + kb * StripSmem::B_KB));
-                const uint64_t bl = tc::sw128_desc(tc::smem_u32(st + (2 + kb) * StripSmem::B_KB));
-#pragma unroll
-                for (int k = 0; k < 4; ++k) {
-                    mma_tf32(d, ah + 2 * k, bh + 2 * k, idesc, acc);
-                    acc = 1;
-                    mma_tf32(d, ah + 2 * k, bl + 2 * k, idesc, 1);
-                    mma_tf32(d, al + 2 * k, bh + 2 * k, idesc, 1);
+            unsigned char* Ah = abuf + ab * StripSmem::A_BUF;
+            unsigned char* Al = Ah + 2 * StripSmem::A_KB;
+            for (int t = 0; t < ntile; ++t, ++g) {
+                const int s = g % kUStages, a = g & 1;
+                if (!tc::mbar_wait(&acc_empty[a], ((g >> 1) & 1) ^ 1, abort) ||
+                    !tc::mbar_wait(&bready[s], (g / kUStages) & 1, abort)) {
+                    ok = false;
+                    break;
                 }
+                tc::tc_fence_after();
+                unsigned char* st = stage0 + s * StripSmem::STAGE;
+                const uint32_t d = tmem + (uint32_t)(a * UBN);
+                uint32_t acc = 0;
+                for (int kb = 0; kb < 2; ++kb) {
+                    const uint64_t ah = tc::sw128_desc(tc::smem_u32(Ah + kb * StripSmem::A_KB));
+                    const uint64_t al = tc::sw128_desc(tc::smem_u32(Al + kb * StripSmem::A_KB));
+                    const uint64_t bh = tc::sw128_desc(tc::smem_u32(st + kb * StripSmem::B_KB));
+                    const uint64_t bl = tc::sw128_desc(tc::smem_u32(st + (2 + kb) * StripSmem::B_KB));
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        mma_tf32(d, ah + 2 * k, bh + 2 * k, idesc, acc);
+                        acc = 1;
+                        mma_tf32(d, ah + 2 * k, bl + 2 * k, idesc, 1);
+                        mma_tf32(d, al + 2 * k, bh + 2 * k, idesc, 1);
+                    }
+                }
+                tc::mma_commit(&empty[s]);
+                tc::mma_commit(&acc_full[a]);
+                ++committed;
             }
-            tc::mma_commit(&empty[s]);
-            tc::mma_commit(&acc_full[a]);
-            ++committed;
+            if (ok) tc::mma_commit(&a_empty[ab]);
         }
         if (!ok) {
             if (err) atomicOr(err, 128);
@@ -409,27 +454,34 @@ __global__ void __launch_bounds__(kStripThreads, 1)
         }
     } else if (warp >= 6) {  // splitters
         const int tid = threadIdx.x - 6 * 32;
-        bool ok = __all_sync(0xffffffffu, tc::mbar_wait(a_full, 0, abort));
-        if (ok) {
-            for (int kb = 0; kb < 2; ++kb)
-                split_box(Ah + kb * StripSmem::A_KB, Al + kb * StripSmem::A_KB, 128, kb, jb, true, tid, 128);
-            // generic-proxy writes, read next by the tensor cores (async proxy)
-            tc::fence_proxy_async();
-            __syncwarp();
-            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(a_ready)) : "memory");
-        }
-        for (int t = 0; t < ntile && ok; ++t) {
-            const int s = t & 1;
-            if (!__all_sync(0xffffffffu, tc::mbar_wait(&full[s], (t >> 1) & 1, abort) && !*abort)) {
+        bool ok = true;
+        int g = 0, i = 0;
+        for (int64_t w = blockIdx.x; w < W && ok; w += gridDim.x, ++i) {
+            const int ab = i & 1;
+            if (!__all_sync(0xffffffffu, tc::mbar_wait(&a_full[ab], (i >> 1) & 1, abort) && !*abort)) {
                 ok = false;
                 break;
             }
-            unsigned char* st = stage0 + s * StripSmem::STAGE;
+            unsigned char* Ah = abuf + ab * StripSmem::A_BUF;
             for (int kb = 0; kb < 2; ++kb)
-                split_box(st + kb * StripSmem::B_KB, st + (2 + kb) * StripSmem::B_KB, UBN, kb, jb, false, tid, 128);
+                split_box(Ah + kb * StripSmem::A_KB, Ah + (2 + kb) * StripSmem::A_KB, 128, kb, jb, true, tid, 128);
+            // generic-proxy writes, read next by the tensor cores (async proxy)
             tc::fence_proxy_async();
             __syncwarp();
-            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&bready[s])) : "memory");
+            if (lane == 0) mbar_arrive(&a_ready[ab]);
+            for (int t = 0; t < ntile; ++t, ++g) {
+                const int s = g % kUStages;
+                if (!__all_sync(0xffffffffu, tc::mbar_wait(&full[s], (g / kUStages) & 1, abort) && !*abort)) {
+                    ok = false;
+                    break;
+                }
+                unsigned char* st = stage0 + s * StripSmem::STAGE;
+                for (int kb = 0; kb < 2; ++kb)
+                    split_box(st + kb * StripSmem::B_KB, st + (2 + kb) * StripSmem::B_KB, UBN, kb, jb, false, tid, 128);
+                tc::fence_proxy_async();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&bready[s]);
+            }
         }
         if (!ok && lane == 0) {
             if (err) atomicOr(err, 512);
@@ -438,62 +490,62 @@ __global__ void __launch_bounds__(kStripThreads, 1)
     } else if (warp >= 2) {
         const int q = warp & 3;
         const int row = q * 32 + lane;
-        const int m = m0 + row;
-        float* M = Mall + (int64_t)e * estride;
-        for (int t = 0; t < ntile; ++t) {
-            const int s = t & 1, a = t & 1;
-            const bool ok = __all_sync(0xffffffffu, tc::mbar_wait(&acc_full[a], (t >> 1) & 1, abort) &&
-                                                        tc::mbar_wait(&full[s], (t >> 1) & 1, abort) && !*abort);
-            if (!ok) {
-                if (err && lane == 0) atomicOr(err, 256);
-                break;
-            }
-            tc::tc_fence_after();
-            const unsigned char* cst = stage0 + s * StripSmem::STAGE + 4 * StripSmem::B_KB;
-            const int n0 = c0 + t * UBN;
-            float d[UBN];
+        int g = 0;
+        bool ok = true;
+        for (int64_t w = blockIdx.x; w < W && ok; w += gridDim.x) {
+            const int64_t e = w / nstrips;
+            const int m = r0 + (int)(w - e * nstrips) * 128 + row;
+            float* M = Mall + e * estride;
+            for (int t = 0; t < ntile; ++t, ++g) {
+                const int s = g % kUStages, a = g & 1;
+                ok = __all_sync(0xffffffffu, tc::mbar_wait(&acc_full[a], (g >> 1) & 1, abort) &&
+                                                 tc::mbar_wait(&full[s], (g / kUStages) & 1, abort) && !*abort);
+                if (!ok) {
+                    if (err && lane == 0) atomicOr(err, 256);
+                    break;
+                }
+                tc::tc_fence_after();
+                const unsigned char* cst = stage0 + s * StripSmem::STAGE + 4 * StripSmem::B_KB;
+                const int n0 = c0 + t * UBN;
+                float d[UBN];
 #pragma unroll
-            for (int c = 0; c < UBN; c += 16) {
-                float v[16];
-                tc::tmem_ld16(tmem + (uint32_t)(a * UBN) + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
+                for (int c = 0; c < UBN; c += 16) {
+                    float v[16];
+                    tc::tmem_ld16(tmem + (uint32_t)(a * UBN) + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
 #pragma unroll
-                for (int j = 0; j < 16; ++j) d[c + j] = v[j];
-            }
-            // C tile in shared memory: box half hb holds columns n0 + 32 hb .. + 31 of rows m0 .. m0 + 127,
-            // 128-byte rows with the 16-byte chunk index XOR-ed by (row % 8)
-            float out[UBN];
-#pragma unroll
-            for (int hb = 0; hb < 2; ++hb) {
+                    for (int j = 0; j < 16; ++j) d[c + j] = v[j];
+                }
+                // C tile in shared memory: rows m0 .. m0 + 127 of columns n0 .. n0 + 31, 128-byte
+                // rows with the 16-byte chunk index XOR-ed by (row % 8)
+                float out[UBN];
 #pragma unroll
                 for (int ch = 0; ch < 8; ++ch) {
-                    const float4 cv = *reinterpret_cast<const float4*>(cst + hb * StripSmem::C_HALF + row * 128 +
-                                                                       ((ch ^ (row & 7)) << 4));
-                    const int c = hb * 32 + ch * 4;
-                    out[c] = cv.x - d[c];
-                    out[c + 1] = cv.y - d[c + 1];
-                    out[c + 2] = cv.z - d[c + 2];
-                    out[c + 3] = cv.w - d[c + 3];
+                    const float4 cv = *reinterpret_cast<const float4*>(cst + row * 128 + ((ch ^ (row & 7)) << 4));
+                    out[4 * ch] = cv.x - d[4 * ch];
+                    out[4 * ch + 1] = cv.y - d[4 * ch + 1];
+                    out[4 * ch + 2] = cv.z - d[4 * ch + 2];
+                    out[4 * ch + 3] = cv.w - d[4 * ch + 3];
                 }
-            }
-            // the C tile was read through the generic proxy and the next TMA copy into this stage
-            // writes through the async proxy: order the two before the stage is released
-            tc::tc_fence_before();
-            tc::fence_proxy_async();
-            __syncwarp();
-            if (lane == 0) {
-                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&acc_empty[a])) : "memory");
-                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&empty[s])) : "memory");
-            }
-            if (m < r_end) {
-                float* dst = M + (int64_t)m * ld + n0;
-                if (n0 + UBN <= c_end) {
+                // the C tile was read through the generic proxy and the next TMA copy into this
+                // stage writes through the async proxy: order the two before the stage is released
+                tc::tc_fence_before();
+                tc::fence_proxy_async();
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(&acc_empty[a]);
+                    mbar_arrive(&empty[s]);
+                }
+                if (m < r_end) {
+                    float* dst = M + (int64_t)m * ld + n0;
+                    if (n0 + UBN <= c_end) {
 #pragma unroll
-                    for (int c = 0; c < UBN; c += 4)
-                        *reinterpret_cast<float4*>(dst + c) = make_float4(out[c], out[c + 1], out[c + 2], out[c + 3]);
-                } else {
+                        for (int c = 0; c < UBN; c += 4)
+                            *reinterpret_cast<float4*>(dst + c) = make_float4(out[c], out[c + 1], out[c + 2], out[c + 3]);
+                    } else {
 #pragma unroll
-                    for (int c = 0; c < UBN; ++c)
-                        if (n0 + c < c_end) dst[c] = out[c];
+                        for (int c = 0; c < UBN; ++c)
+                            if (n0 + c < c_end) dst[c] = out[c];
+                    }
                 }
             }
         }
@@ -501,12 +553,14 @@ __global__ void __launch_bounds__(kStripThreads, 1)
     tc::tc_fence_before();
     __syncthreads();
     if (warp == 0 && lane == 0) {  // let every copy this CTA issued land before the CTA exits
-        const long long t0 = clock64();
-        while (!tc::mbar_try_wait(a_full, 0) && clock64() - t0 < tc::kWaitCycles / 4) {
+        for (int q = (issued_a > 2 ? issued_a - 2 : 0); q < issued_a; ++q) {
+            const long long t0 = clock64();
+            while (!tc::mbar_try_wait(&a_full[q & 1], (q >> 1) & 1) && clock64() - t0 < tc::kWaitCycles / 4) {
+            }
         }
-        for (int q = (issued > 2 ? issued - 2 : 0); q < issued; ++q) {
+        for (int q = (issued_t > kUStages ? issued_t - kUStages : 0); q < issued_t; ++q) {
             const long long t1 = clock64();
-            while (!tc::mbar_try_wait(&full[q & 1], (q >> 1) & 1) && clock64() - t1 < tc::kWaitCycles / 4) {
+            while (!tc::mbar_try_wait(&full[q % kUStages], (q / kUStages) & 1) && clock64() - t1 < tc::kWaitCycles / 4) {
             }
         }
     }
@@ -577,8 +631,9 @@ elrt_status update(elrt_ctx* ctx, const TcMaps& mp, float* M, int64_t ld, int64_
     if (r_end <= r0 || c_end <= c0) return ELRT_OK;
     const double R = r_end - r0, C = c_end - c0;
     ProfScope ps(ctx, "lu_tc_update", 1, (double)E * (8.0 * R * C + 4.0 * (R + C) * NBP), (double)E * 2.0 * R * C * jb);
-    dim3 grid((r_end - r0 + 127) / 128, (unsigned)E);
-    k_tc_update_strip<<<grid, kStripThreads, StripSmem::TOTAL, ctx->stream>>>(mp.m, mp.u, M, ld, estride, J, jb, r0,
+    const int64_t items = (int64_t)((r_end - r0 + 127) / 128) * E;
+    const unsigned grid = (unsigned)std::min<int64_t>(items, 152);
+    k_tc_update_strip<<<grid, kStripThreads, StripSmem::TOTAL, ctx->stream>>>(mp.m, mp.u, M, ld, estride, E, J, jb, r0,
                                                                               r_end, c0, c_end, err);
     return cuda_check(ctx, cudaGetLastError(), "tc update launch");
 }
