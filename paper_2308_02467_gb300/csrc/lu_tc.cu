@@ -257,64 +257,65 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
-__device__ __forceinline__ void mma_tf32(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
-                                         uint32_t accumulate) {
+// 32 consecutive 32-bit TMEM columns of this thread's lane (shape 32x32b: the warp covers the 32
+// lanes of its quarter) from registers; visible to later tcgen05 operations after tmem_st_wait
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const float (&v)[32]) {
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr), "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])), "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15])), "r"(__float_as_uint(v[16])), "r"(__float_as_uint(v[17])), "r"(__float_as_uint(v[18])), "r"(__float_as_uint(v[19])), "r"(__float_as_uint(v[20])), "r"(__float_as_uint(v[21])), "r"(__float_as_uint(v[22])), "r"(__float_as_uint(v[23])), "r"(__float_as_uint(v[24])), "r"(__float_as_uint(v[25])), "r"(__float_as_uint(v[26])), "r"(__float_as_uint(v[27])), "r"(__float_as_uint(v[28])), "r"(__float_as_uint(v[29])), "r"(__float_as_uint(v[30])), "r"(__float_as_uint(v[31])) : "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// D (TMEM) (+)= A (TMEM, M x K, one row per lane, one 32-bit element per column) x B (shared memory)
+__device__ __forceinline__ void mma_tf32_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
+                                            uint32_t accumulate) {
     asm volatile(
-        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::tf32 [%0], [%1], %2, %3, p;\n}\n" ::"r"(
             d_tmem),
-        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate));
+        "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate));
 }
 
+
 // Persistent trailing update: one CTA per SM walks the work items (element, 128-row strip) of the
-// launch, items of one element consecutively (their U12^T tiles are shared through L2).  Per item
-// the FP32 L21 strip (columns J .. J+63 of the strip's rows, straight from the matrix) is loaded
-// by TMA into one of two strip buffers, so the next item's strip is copied and split while the
-// current item's tiles run; the 32-column tiles (FP32 U12^T tile + C tile) flow through a
-// three-stage ring that does not drain between items.
-//   warp 0       TMA producer (strips, tiles);
-//   warp 1       one thread issues the 3xTF32 MMAs (hi*hi + hi*lo + lo*hi, M = 128, N = 32) into
-//                one of two TMEM accumulators;
+// launch, the strips of one element consecutively (their U12^T tiles are shared through L2).  The
+// L21 strip of an item (columns J .. J+63 of its 128 rows, FP32, straight from the matrix) lives
+// in tensor memory as TF32 high and low parts, double-buffered, so the next item's strip is
+// prepared while the current item's tiles run; shared memory holds only the ring of 32-column
+// tiles (FP32 U12^T tile, its low part, the C tile), six stages deep, which does not drain
+// between items.
+//   warp 0       TMA producer of the tiles;
+//   warp 1       TMEM allocation; one thread issues the 3xTF32 MMAs (hi*hi + hi*lo + lo*hi,
+//                M = 128, N = 32, A from tensor memory) into one of two TMEM accumulators;
 //   warps 2-5    epilogue: accumulator (tcgen05.ld) and staged C tile -> C - L U -> global;
-//   warps 6-9    split the FP32 operands in place into TF32 high parts and write the low parts
-//                beside them (strip columns at or beyond jb are zeroed).
-// Stage s is free again after the MMA commit and the four epilogue warps (count 5); a strip
+//   warps 6-9    strip preparation: each thread loads one row of the strip (columns at or beyond
+//                jb are 0), splits it and writes it to its TMEM lane (tcgen05.st);
+//   warps 10-13  split the staged FP32 U12^T tile in place (high part) and write the low part.
+// A stage is free again after the MMA commit and the four epilogue warps (count 5); a strip
 // buffer after the MMA commit of its item's last tile.  Every wait is bounded; on a timeout the
 // CTA records a code in *err, stops issuing work, lets its copies land and frees its TMEM.
-constexpr int kUStages = 3;
+constexpr int kUStages = 6;
 struct StripSmem {
-    static constexpr int A_KB = 128 * 32 * 4;                 // one 32-column box of a strip
-    static constexpr int A_BUF = 4 * A_KB;                    // {hi, lo} x 2 k-blocks
     static constexpr int B_KB = UBN * 32 * 4;                 // one 32-column box of a U12^T tile
     static constexpr int C_BOX = 128 * UBN * 4;               // the C tile (one box)
     static constexpr int STAGE = 4 * B_KB + C_BOX;            // B {hi, lo} x 2 k-blocks + C tile
-    static constexpr int A_TX = 2 * A_KB;                     // FP32 strip copied per item
     static constexpr int STAGE_TX = 2 * B_KB + C_BOX;         // FP32 U12^T tile + C tile per stage
-    static constexpr int BYTES = 2 * A_BUF + kUStages * STAGE;
+    static constexpr int BYTES = kUStages * STAGE;
     static constexpr int TOTAL = BYTES + 1024 + 256;
 };
 static_assert(StripSmem::TOTAL <= 227 * 1024, "trailing-update shared memory");
-constexpr int kStripThreads = 320;
+constexpr int kStripThreads = 448;
+// tensor memory: accumulators at columns [0, 2 UBN); strip buffer b: high part at 128 + 128 b,
+// low part 64 columns further
+constexpr uint32_t kTmemCols = 512;
+__host__ __device__ constexpr uint32_t strip_col(int b, int lo) { return 128u + 128u * (uint32_t)b + 64u * (uint32_t)lo; }
 
-// In-place TF32 split of one 128-byte-swizzled box of `rows` rows x 32 FP32 (k-block kb): hi
-// stays, lo goes to the same offset in `lo`; with kmask, entries whose column kb*32 + k is at or
-// beyond jb become 0.  Threads tid .. of nthr cooperate, 16 bytes each.
-__device__ __forceinline__ void split_box(unsigned char* box, unsigned char* lo, int rows, int kb, int jb, bool kmask,
-                                          int tid, int nthr) {
+// In-place TF32 split of one 128-byte-swizzled box of `rows` rows x 32 FP32: hi stays, lo goes to
+// the same offset in `lo`.  Threads tid .. of nthr cooperate, 16 bytes each.
+__device__ __forceinline__ void split_box(unsigned char* box, unsigned char* lo, int rows, int tid, int nthr) {
     for (int q = tid; q < rows * 8; q += nthr) {
-        const int row = q >> 3, pc = q & 7;          // physical 16-byte chunk of the row
-        const int kcol = kb * 32 + ((pc ^ (row & 7)) << 2);
-        float4* hp = reinterpret_cast<float4*>(box + row * 128 + pc * 16);
-        float4 v = *hp;
-        if (kmask) {
-            if (kcol + 0 >= jb) v.x = 0.f;
-            if (kcol + 1 >= jb) v.y = 0.f;
-            if (kcol + 2 >= jb) v.z = 0.f;
-            if (kcol + 3 >= jb) v.w = 0.f;
-        }
+        float4* hp = reinterpret_cast<float4*>(box + q * 16);
+        const float4 v = *hp;
         const float4 h = make_float4(tf32_hi(v.x), tf32_hi(v.y), tf32_hi(v.z), tf32_hi(v.w));
         *hp = h;
-        *reinterpret_cast<float4*>(lo + row * 128 + pc * 16) =
-            make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+        *reinterpret_cast<float4*>(lo + q * 16) = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
     }
 }
 
@@ -323,15 +324,13 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 }
 
 __global__ void __launch_bounds__(kStripThreads, 1)
-    k_tc_update_strip(const __grid_constant__ CUtensorMap tM, const __grid_constant__ CUtensorMap tU, float* __restrict__ Mall,
-                      int64_t ld, int64_t estride, int64_t E, int J, int jb, int r0, int r_end, int c0, int c_end,
-                      int* __restrict__ err) {
+    k_tc_update_strip(const __grid_constant__ CUtensorMap tM, const __grid_constant__ CUtensorMap tU,
+                      float* __restrict__ Mall, int nu, int64_t ld, int64_t estride, int64_t E, int J, int jb, int r0,
+                      int r_end, int c0, int c_end, int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char ssm_raw[];
     unsigned char* base = (unsigned char*)(((uintptr_t)ssm_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char* abuf = base;                            // [2] strip buffers: Ah (2 boxes), Al (2 boxes)
-    unsigned char* stage0 = base + 2 * StripSmem::A_BUF;   // [kUStages]: Bh (2), Bl (2), C
-    uint64_t* a_full = (uint64_t*)(base + StripSmem::BYTES);  // [2]
-    uint64_t* a_ready = a_full + 2;                        // [2]
+    unsigned char* stage0 = base;                          // [kUStages]: Bh (2 boxes), Bl (2 boxes), C
+    uint64_t* a_ready = (uint64_t*)(base + StripSmem::BYTES);  // [2]
     uint64_t* a_empty = a_ready + 2;                       // [2]
     uint64_t* full = a_empty + 2;                          // [kUStages]
     uint64_t* bready = full + kUStages;                    // [kUStages]
@@ -346,7 +345,6 @@ __global__ void __launch_bounds__(kStripThreads, 1)
     const int ntile = (c_end - c0 + UBN - 1) / UBN;
     if (threadIdx.x == 0) {
         for (int i = 0; i < 2; ++i) {
-            tc::mbar_init(&a_full[i], 1);
             tc::mbar_init(&a_ready[i], 4);
             tc::mbar_init(&a_empty[i], 1);
             tc::mbar_init(&acc_full[i], 1);
@@ -361,33 +359,21 @@ __global__ void __launch_bounds__(kStripThreads, 1)
         tc::fence_barrier_init();
     }
     if (warp == 1) {
-        tc::tmem_alloc(tmem_slot, 2 * UBN);
+        tc::tmem_alloc(tmem_slot, kTmemCols);
         tc::tmem_relinquish();
     }
     tc::tc_fence_before();
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    int committed = 0, issued_t = 0, issued_a = 0;
+    int committed = 0, issued_t = 0;
     if (warp == 0 && lane == 0) {
-        // strip j of this CTA into buffer j & 1 (free once item j - 2 is done)
-        auto load_strip = [&](int64_t w, int j) -> bool {
-            if (!tc::mbar_wait(&a_empty[j & 1], ((j >> 1) & 1) ^ 1, abort)) return false;
+        bool ok = true;
+        int g = 0;
+        for (int64_t w = blockIdx.x; w < W && ok; w += gridDim.x) {
             const int64_t e = w / nstrips;
             const int m0 = r0 + (int)(w - e * nstrips) * 128;
-            unsigned char* ab = abuf + (j & 1) * StripSmem::A_BUF;
-            tc::mbar_expect_tx(&a_full[j & 1], StripSmem::A_TX);
-            for (int kb = 0; kb < 2; ++kb)
-                tma_load_3d(&tM, &a_full[j & 1], ab + kb * StripSmem::A_KB, J + kb * 32, m0, (int)e);
-            ++issued_a;
-            return true;
-        };
-        bool ok = load_strip(blockIdx.x, 0);
-        int g = 0, i = 0;
-        for (int64_t w = blockIdx.x; w < W && ok; w += gridDim.x, ++i) {
-            const int64_t e = w / nstrips;
-            const int m0 = r0 + (int)(w - e * nstrips) * 128;
-            for (int t = 0; t < ntile && ok; ++t, ++g) {
+            for (int t = 0; t < ntile; ++t, ++g) {
                 const int s = g % kUStages;
                 if (!tc::mbar_wait(&empty[s], ((g / kUStages) & 1) ^ 1, abort)) {
                     ok = false;
@@ -399,7 +385,6 @@ __global__ void __launch_bounds__(kStripThreads, 1)
                 for (int kb = 0; kb < 2; ++kb) tma_load_3d(&tU, &full[s], st + kb * StripSmem::B_KB, kb * 32, n0, (int)e);
                 tma_load_3d(&tM, &full[s], st + 4 * StripSmem::B_KB, n0, m0, (int)e);
                 ++issued_t;
-                if (t == 0 && w + gridDim.x < W) ok = load_strip(w + gridDim.x, i + 1);  // next item's strip
             }
         }
         if (!ok) {
@@ -416,8 +401,8 @@ __global__ void __launch_bounds__(kStripThreads, 1)
                 ok = false;
                 break;
             }
-            unsigned char* Ah = abuf + ab * StripSmem::A_BUF;
-            unsigned char* Al = Ah + 2 * StripSmem::A_KB;
+            tc::tc_fence_after();
+            const uint32_t a_hi = tmem + strip_col(ab, 0), a_lo = tmem + strip_col(ab, 1);
             for (int t = 0; t < ntile; ++t, ++g) {
                 const int s = g % kUStages, a = g & 1;
                 if (!tc::mbar_wait(&acc_empty[a], ((g >> 1) & 1) ^ 1, abort) ||
@@ -430,16 +415,15 @@ __global__ void __launch_bounds__(kStripThreads, 1)
                 const uint32_t d = tmem + (uint32_t)(a * UBN);
                 uint32_t acc = 0;
                 for (int kb = 0; kb < 2; ++kb) {
-                    const uint64_t ah = tc::sw128_desc(tc::smem_u32(Ah + kb * StripSmem::A_KB));
-                    const uint64_t al = tc::sw128_desc(tc::smem_u32(Al + kb * StripSmem::A_KB));
                     const uint64_t bh = tc::sw128_desc(tc::smem_u32(st + kb * StripSmem::B_KB));
                     const uint64_t bl = tc::sw128_desc(tc::smem_u32(st + (2 + kb) * StripSmem::B_KB));
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        mma_tf32(d, ah + 2 * k, bh + 2 * k, idesc, acc);
+                    for (int k = 0; k < 4; ++k) {  // K = 8 per instruction
+                        const uint32_t kc = (uint32_t)(kb * 32 + k * 8);
+                        mma_tf32_ta(d, a_hi + kc, bh + 2 * k, idesc, acc);
                         acc = 1;
-                        mma_tf32(d, ah + 2 * k, bl + 2 * k, idesc, 1);
-                        mma_tf32(d, al + 2 * k, bh + 2 * k, idesc, 1);
+                        mma_tf32_ta(d, a_hi + kc, bl + 2 * k, idesc, 1);
+                        mma_tf32_ta(d, a_lo + kc, bh + 2 * k, idesc, 1);
                     }
                 }
                 tc::mma_commit(&empty[s]);
@@ -452,23 +436,58 @@ __global__ void __launch_bounds__(kStripThreads, 1)
             if (err) atomicOr(err, 128);
             *abort = 1;
         }
-    } else if (warp >= 6) {  // splitters
-        const int tid = threadIdx.x - 6 * 32;
+    } else if (warp >= 6 && warp < 10) {  // strip preparation: one row per thread, into its TMEM lane
+        const int qa = warp & 3;
+        const int row = qa * 32 + lane;
+        const uint32_t lane_off = (uint32_t)(qa * 32) << 16;
         bool ok = true;
-        int g = 0, i = 0;
+        int i = 0;
         for (int64_t w = blockIdx.x; w < W && ok; w += gridDim.x, ++i) {
             const int ab = i & 1;
-            if (!__all_sync(0xffffffffu, tc::mbar_wait(&a_full[ab], (i >> 1) & 1, abort) && !*abort)) {
+            if (!__all_sync(0xffffffffu, tc::mbar_wait(&a_empty[ab], ((i >> 1) & 1) ^ 1, abort) && !*abort)) {
                 ok = false;
                 break;
             }
-            unsigned char* Ah = abuf + ab * StripSmem::A_BUF;
-            for (int kb = 0; kb < 2; ++kb)
-                split_box(Ah + kb * StripSmem::A_KB, Ah + (2 + kb) * StripSmem::A_KB, 128, kb, jb, true, tid, 128);
-            // generic-proxy writes, read next by the tensor cores (async proxy)
-            tc::fence_proxy_async();
+            tc::tc_fence_after();
+            const int64_t e = w / nstrips;
+            const int m = r0 + (int)(w - e * nstrips) * 128 + row;
+            const float* src = Mall + e * estride + (int64_t)m * ld + J;
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                float v[32], lo[32];
+#pragma unroll
+                for (int k4 = 0; k4 < 8; ++k4) {
+                    const int k = half * 32 + 4 * k4;
+                    float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (m < nu && k < jb) x = *reinterpret_cast<const float4*>(src + k);  // jb is a multiple of 4
+                    v[4 * k4] = x.x;
+                    v[4 * k4 + 1] = x.y;
+                    v[4 * k4 + 2] = x.z;
+                    v[4 * k4 + 3] = x.w;
+                }
+#pragma unroll
+                for (int k = 0; k < 32; ++k) {
+                    const float h = tf32_hi(v[k]);
+                    lo[k] = v[k] - h;
+                    v[k] = h;
+                }
+                tmem_st32(tmem + lane_off + strip_col(ab, 0) + half * 32, v);
+                tmem_st32(tmem + lane_off + strip_col(ab, 1) + half * 32, lo);
+            }
+            tmem_st_wait();
+            tc::tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&a_ready[ab]);
+        }
+        if (!ok && lane == 0) {
+            if (err) atomicOr(err, 1024);
+            *abort = 1;
+        }
+    } else if (warp >= 10) {  // U12^T tile splitters
+        const int tid = threadIdx.x - 10 * 32;
+        bool ok = true;
+        int g = 0;
+        for (int64_t w = blockIdx.x; w < W && ok; w += gridDim.x) {
             for (int t = 0; t < ntile; ++t, ++g) {
                 const int s = g % kUStages;
                 if (!__all_sync(0xffffffffu, tc::mbar_wait(&full[s], (g / kUStages) & 1, abort) && !*abort)) {
@@ -477,7 +496,8 @@ __global__ void __launch_bounds__(kStripThreads, 1)
                 }
                 unsigned char* st = stage0 + s * StripSmem::STAGE;
                 for (int kb = 0; kb < 2; ++kb)
-                    split_box(st + kb * StripSmem::B_KB, st + (2 + kb) * StripSmem::B_KB, UBN, kb, jb, false, tid, 128);
+                    split_box(st + kb * StripSmem::B_KB, st + (2 + kb) * StripSmem::B_KB, UBN, tid, 128);
+                // generic-proxy writes, read next by the tensor cores (async proxy)
                 tc::fence_proxy_async();
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&bready[s]);
@@ -553,11 +573,6 @@ __global__ void __launch_bounds__(kStripThreads, 1)
     tc::tc_fence_before();
     __syncthreads();
     if (warp == 0 && lane == 0) {  // let every copy this CTA issued land before the CTA exits
-        for (int q = (issued_a > 2 ? issued_a - 2 : 0); q < issued_a; ++q) {
-            const long long t0 = clock64();
-            while (!tc::mbar_try_wait(&a_full[q & 1], (q >> 1) & 1) && clock64() - t0 < tc::kWaitCycles / 4) {
-            }
-        }
         for (int q = (issued_t > kUStages ? issued_t - kUStages : 0); q < issued_t; ++q) {
             const long long t1 = clock64();
             while (!tc::mbar_try_wait(&full[q % kUStages], (q / kUStages) & 1) && clock64() - t1 < tc::kWaitCycles / 4) {
@@ -573,7 +588,7 @@ __global__ void __launch_bounds__(kStripThreads, 1)
         }
         __syncwarp();
         tc::tc_fence_after();
-        tc::tmem_dealloc(tmem, 2 * UBN);
+        tc::tmem_dealloc(tmem, kTmemCols);
     }
 }
 
@@ -633,8 +648,8 @@ elrt_status update(elrt_ctx* ctx, const TcMaps& mp, float* M, int64_t ld, int64_
     ProfScope ps(ctx, "lu_tc_update", 1, (double)E * (8.0 * R * C + 4.0 * (R + C) * NBP), (double)E * 2.0 * R * C * jb);
     const int64_t items = (int64_t)((r_end - r0 + 127) / 128) * E;
     const unsigned grid = (unsigned)std::min<int64_t>(items, 152);
-    k_tc_update_strip<<<grid, kStripThreads, StripSmem::TOTAL, ctx->stream>>>(mp.m, mp.u, M, ld, estride, E, J, jb, r0,
-                                                                              r_end, c0, c_end, err);
+    k_tc_update_strip<<<grid, kStripThreads, StripSmem::TOTAL, ctx->stream>>>(mp.m, mp.u, M, ctx->tab.nu, ld, estride, E,
+                                                                              J, jb, r0, r_end, c0, c_end, err);
     return cuda_check(ctx, cudaGetLastError(), "tc update launch");
 }
 
