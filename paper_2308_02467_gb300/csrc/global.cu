@@ -379,28 +379,60 @@ __global__ void __launch_bounds__(kGvThreads, 2)
             }
             const float* Ac = stages + (size_t)s * (kGvStageBytes / 4) + (size_t)warp * RPW * nin;
             const int rbase = c * CR + warp * RPW;
-            // two independent float-float chains per row (even / odd 32-column blocks)
-            ff acc[RPW], acc2[RPW];
+            ff acc[RPW];
+            if constexpr (std::is_same<V, float>::value) {
+                // Arnoldi step (FP32 basis vector in, FP32 vector out): each lane's partial sum of
+                // its ~nin/32 products in FP32, two chains per row; the lanes' partials, the self
+                // term and the final rounding in float-float
+                float f1[RPW], f2[RPW];
 #pragma unroll
-            for (int q = 0; q < RPW; ++q) acc[q] = acc2[q] = ff{0.f, 0.f};
-            int col = lane;
-            for (; col + 32 < nin; col += 64) {
-                const ff xv = xe[col], xw = xe[col + 32];
+                for (int q = 0; q < RPW; ++q) f1[q] = f2[q] = 0.f;
+                int col = lane;
+                for (; col + 32 < nin; col += 64) {
+                    const float xv = xe[col].h, xw = xe[col + 32].h;
 #pragma unroll
-                for (int q = 0; q < RPW; ++q)
-                    if (rbase + q < rows) {
-                        ff_fma_f(acc[q], Ac[q * nin + col], xv);
-                        ff_fma_f(acc2[q], Ac[q * nin + col + 32], xw);
+                    for (int q = 0; q < RPW; ++q) {
+                        f1[q] = fmaf(Ac[q * nin + col], xv, f1[q]);
+                        f2[q] = fmaf(Ac[q * nin + col + 32], xw, f2[q]);
                     }
-            }
-            if (col < nin) {
-                const ff xv = xe[col];
+                }
+                if (col < nin) {
+                    const float xv = xe[col].h;
+#pragma unroll
+                    for (int q = 0; q < RPW; ++q) f1[q] = fmaf(Ac[q * nin + col], xv, f1[q]);
+                }
+#pragma unroll
+                for (int q = 0; q < RPW; ++q) {
+                    float h, l;
+                    two_sum(f1[q], f2[q], h, l);
+                    acc[q] = (rbase + q < rows) ? ff{h, l} : ff{0.f, 0.f};
+                }
+            } else {
+                // restart residual, right-hand side, recovery: float-float products and sums,
+                // two independent chains per row (even / odd 32-column blocks)
+                ff acc2[RPW];
+#pragma unroll
+                for (int q = 0; q < RPW; ++q) acc[q] = acc2[q] = ff{0.f, 0.f};
+                int col = lane;
+                for (; col + 32 < nin; col += 64) {
+                    const ff xv = xe[col], xw = xe[col + 32];
+#pragma unroll
+                    for (int q = 0; q < RPW; ++q)
+                        if (rbase + q < rows) {
+                            ff_fma_f(acc[q], Ac[q * nin + col], xv);
+                            ff_fma_f(acc2[q], Ac[q * nin + col + 32], xw);
+                        }
+                }
+                if (col < nin) {
+                    const ff xv = xe[col];
+#pragma unroll
+                    for (int q = 0; q < RPW; ++q)
+                        if (rbase + q < rows) ff_fma_f(acc[q], Ac[q * nin + col], xv);
+                }
 #pragma unroll
                 for (int q = 0; q < RPW; ++q)
-                    if (rbase + q < rows) ff_fma_f(acc[q], Ac[q * nin + col], xv);
+                    acc[q] = ff_add(ff_norm(acc[q].h, acc[q].l), ff_norm(acc2[q].h, acc2[q].l));
             }
-#pragma unroll
-            for (int q = 0; q < RPW; ++q) acc[q] = ff_add(ff_norm(acc[q].h, acc[q].l), ff_norm(acc2[q].h, acc2[q].l));
             // the stage was read through the generic proxy; the next bulk copy into it writes
             // through the async proxy
             tc::fence_proxy_async();
