@@ -253,6 +253,17 @@ __device__ __forceinline__ void tma_load_3d(const CUtensorMap* map, uint64_t* ba
         : "memory");
 }
 
+// shared -> global tensor copy (bulk group); the box starts at non-negative coordinates
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, const void* src, int x, int y, int z) {
+    asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.bulk_group [%0, {%2, %3, %4}], [%1];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(tc::smem_u32(src)), "r"(x), "r"(y), "r"(z)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
 __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
@@ -284,11 +295,15 @@ __device__ __forceinline__ void mma_tf32_ta(uint32_t d_tmem, uint32_t a_tmem, ui
 //   warp 0       TMA producer of the tiles;
 //   warp 1       TMEM allocation; one thread issues the 3xTF32 MMAs (hi*hi + hi*lo + lo*hi,
 //                M = 128, N = 32, A from tensor memory) into one of two TMEM accumulators;
-//   warps 2-5    epilogue: accumulator (tcgen05.ld) and staged C tile -> C - L U -> global;
+//   warps 2-5    epilogue: accumulator (tcgen05.ld) and staged C tile -> C - L U, written back
+//                into the staged tile;
+//   warp 14      stores each finished tile with one TMA tensor store (the store map's extents
+//                are r_end rows and c_end columns, so rows and columns outside the update are
+//                clipped) and releases the stage once the store has read it;
 //   warps 6-9    strip preparation: each thread loads one row of the strip (columns at or beyond
 //                jb are 0), splits it and writes it to its TMEM lane (tcgen05.st);
 //   warps 10-13  split the staged FP32 U12^T tile in place (high part) and write the low part.
-// A stage is free again after the MMA commit and the four epilogue warps (count 5); a strip
+// A stage is free again after the MMA commit and the store warp (count 2); a strip
 // buffer after the MMA commit of its item's last tile.  Every wait is bounded; on a timeout the
 // CTA records a code in *err, stops issuing work, lets its copies land and frees its TMEM.
 constexpr int kUStages = 6;
@@ -301,7 +316,7 @@ struct StripSmem {
     static constexpr int TOTAL = BYTES + 1024 + 256;
 };
 static_assert(StripSmem::TOTAL <= 227 * 1024, "trailing-update shared memory");
-constexpr int kStripThreads = 448;
+constexpr int kStripThreads = 480;
 // tensor memory: accumulators at columns [0, 2 UBN); strip buffer b: high part at 128 + 128 b,
 // low part 64 columns further
 constexpr uint32_t kTmemCols = 512;
@@ -325,8 +340,9 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 
 __global__ void __launch_bounds__(kStripThreads, 1)
     k_tc_update_strip(const __grid_constant__ CUtensorMap tM, const __grid_constant__ CUtensorMap tU,
-                      float* __restrict__ Mall, int nu, int64_t ld, int64_t estride, int64_t E, int J, int jb, int r0,
-                      int r_end, int c0, int c_end, int* __restrict__ err) {
+                      const __grid_constant__ CUtensorMap tS, float* __restrict__ Mall, int nu, int64_t ld,
+                      int64_t estride, int64_t E, int J, int jb, int r0, int r_end, int c0, int c_end,
+                      int* __restrict__ err) {
     extern __shared__ __align__(1024) unsigned char ssm_raw[];
     unsigned char* base = (unsigned char*)(((uintptr_t)ssm_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* stage0 = base;                          // [kUStages]: Bh (2 boxes), Bl (2 boxes), C
@@ -335,7 +351,8 @@ __global__ void __launch_bounds__(kStripThreads, 1)
     uint64_t* full = a_empty + 2;                          // [kUStages]
     uint64_t* bready = full + kUStages;                    // [kUStages]
     uint64_t* empty = bready + kUStages;                   // [kUStages]
-    uint64_t* acc_full = empty + kUStages;                 // [2]
+    uint64_t* cdone = empty + kUStages;                    // [kUStages]
+    uint64_t* acc_full = cdone + kUStages;                 // [2]
     uint64_t* acc_empty = acc_full + 2;                    // [2]
     uint32_t* tmem_slot = (uint32_t*)(acc_empty + 2);
     volatile int* abort = (volatile int*)(tmem_slot + 1);
@@ -353,7 +370,8 @@ __global__ void __launch_bounds__(kStripThreads, 1)
         for (int i = 0; i < kUStages; ++i) {
             tc::mbar_init(&full[i], 1);
             tc::mbar_init(&bready[i], 4);
-            tc::mbar_init(&empty[i], 5);
+            tc::mbar_init(&empty[i], 2);
+            tc::mbar_init(&cdone[i], 4);
         }
         *abort = 0;
         tc::fence_barrier_init();
@@ -483,6 +501,31 @@ __global__ void __launch_bounds__(kStripThreads, 1)
             if (err) atomicOr(err, 1024);
             *abort = 1;
         }
+    } else if (warp == 14) {  // tile stores
+        if (lane == 0) {
+            int g = 0;
+            bool ok = true;
+            for (int64_t w = blockIdx.x; w < W && ok; w += gridDim.x) {
+                const int64_t e = w / nstrips;
+                const int m0 = r0 + (int)(w - e * nstrips) * 128;
+                for (int t = 0; t < ntile; ++t, ++g) {
+                    const int s = g % kUStages;
+                    if (!tc::mbar_wait(&cdone[s], (g / kUStages) & 1, abort)) {
+                        ok = false;
+                        break;
+                    }
+                    tma_store_3d(&tS, stage0 + s * StripSmem::STAGE + 4 * StripSmem::B_KB, c0 + t * UBN, m0, (int)e);
+                    bulk_commit();
+                    bulk_wait_read0();  // the stage may be refilled once the store has read it
+                    mbar_arrive(&empty[s]);
+                }
+            }
+            bulk_wait0();
+            if (!ok) {
+                if (err) atomicOr(err, 2048);
+                *abort = 1;
+            }
+        }
     } else if (warp >= 10) {  // U12^T tile splitters
         const int tid = threadIdx.x - 10 * 32;
         bool ok = true;
@@ -513,9 +556,6 @@ __global__ void __launch_bounds__(kStripThreads, 1)
         int g = 0;
         bool ok = true;
         for (int64_t w = blockIdx.x; w < W && ok; w += gridDim.x) {
-            const int64_t e = w / nstrips;
-            const int m = r0 + (int)(w - e * nstrips) * 128 + row;
-            float* M = Mall + e * estride;
             for (int t = 0; t < ntile; ++t, ++g) {
                 const int s = g % kUStages, a = g & 1;
                 ok = __all_sync(0xffffffffu, tc::mbar_wait(&acc_full[a], (g >> 1) & 1, abort) &&
@@ -526,7 +566,6 @@ __global__ void __launch_bounds__(kStripThreads, 1)
                 }
                 tc::tc_fence_after();
                 const unsigned char* cst = stage0 + s * StripSmem::STAGE + 4 * StripSmem::B_KB;
-                const int n0 = c0 + t * UBN;
                 float d[UBN];
 #pragma unroll
                 for (int c = 0; c < UBN; c += 16) {
@@ -536,36 +575,21 @@ __global__ void __launch_bounds__(kStripThreads, 1)
                     for (int j = 0; j < 16; ++j) d[c + j] = v[j];
                 }
                 // C tile in shared memory: rows m0 .. m0 + 127 of columns n0 .. n0 + 31, 128-byte
-                // rows with the 16-byte chunk index XOR-ed by (row % 8)
-                float out[UBN];
+                // rows with the 16-byte chunk index XOR-ed by (row % 8); C - L U goes back in place
+                unsigned char* crow = const_cast<unsigned char*>(cst) + row * 128;
 #pragma unroll
                 for (int ch = 0; ch < 8; ++ch) {
-                    const float4 cv = *reinterpret_cast<const float4*>(cst + row * 128 + ((ch ^ (row & 7)) << 4));
-                    out[4 * ch] = cv.x - d[4 * ch];
-                    out[4 * ch + 1] = cv.y - d[4 * ch + 1];
-                    out[4 * ch + 2] = cv.z - d[4 * ch + 2];
-                    out[4 * ch + 3] = cv.w - d[4 * ch + 3];
+                    float4* p = reinterpret_cast<float4*>(crow + ((ch ^ (row & 7)) << 4));
+                    const float4 cv = *p;
+                    *p = make_float4(cv.x - d[4 * ch], cv.y - d[4 * ch + 1], cv.z - d[4 * ch + 2], cv.w - d[4 * ch + 3]);
                 }
-                // the C tile was read through the generic proxy and the next TMA copy into this
-                // stage writes through the async proxy: order the two before the stage is released
+                // written through the generic proxy, read next by the TMA store (async proxy)
                 tc::tc_fence_before();
                 tc::fence_proxy_async();
                 __syncwarp();
                 if (lane == 0) {
                     mbar_arrive(&acc_empty[a]);
-                    mbar_arrive(&empty[s]);
-                }
-                if (m < r_end) {
-                    float* dst = M + (int64_t)m * ld + n0;
-                    if (n0 + UBN <= c_end) {
-#pragma unroll
-                        for (int c = 0; c < UBN; c += 4)
-                            *reinterpret_cast<float4*>(dst + c) = make_float4(out[c], out[c + 1], out[c + 2], out[c + 3]);
-                    } else {
-#pragma unroll
-                        for (int c = 0; c < UBN; ++c)
-                            if (n0 + c < c_end) dst[c] = out[c];
-                    }
+                    mbar_arrive(&cdone[s]);
                 }
             }
         }
@@ -622,10 +646,11 @@ bool map3(CUtensorMap* m, const float* p, int64_t rows, int64_t E, int box_rows)
                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// the matrix of every element, [E][nu][ld], box 32 columns x 128 rows x 1 element, 128-byte swizzle
-// (the L21 / U column block of a strip and the C tiles)
-bool mapM(CUtensorMap* m, const float* M, int64_t nu, int64_t ld, int64_t estride, int64_t E) {
-    cuuint64_t dims[3] = {(cuuint64_t)ld, (cuuint64_t)nu, (cuuint64_t)E};
+// the matrix of every element seen as [E][rows][cols] (row pitch ld), box 32 columns x 128 rows x 1
+// element, 128-byte swizzle: with rows = nu, cols = ld the C tiles of the loads; with rows = r_end,
+// cols = c_end the stores of an update (whatever lies outside is clipped)
+bool mapM(CUtensorMap* m, const float* M, int64_t rows, int64_t cols, int64_t ld, int64_t estride, int64_t E) {
+    cuuint64_t dims[3] = {(cuuint64_t)cols, (cuuint64_t)rows, (cuuint64_t)E};
     cuuint64_t strides[2] = {(cuuint64_t)ld * 4, (cuuint64_t)estride * 4};
     cuuint32_t box[3] = {32, 128, 1};
     cuuint32_t es[3] = {1, 1, 1};
@@ -646,10 +671,12 @@ elrt_status update(elrt_ctx* ctx, const TcMaps& mp, float* M, int64_t ld, int64_
     if (r_end <= r0 || c_end <= c0) return ELRT_OK;
     const double R = r_end - r0, C = c_end - c0;
     ProfScope ps(ctx, "lu_tc_update", 1, (double)E * (8.0 * R * C + 4.0 * (R + C) * NBP), (double)E * 2.0 * R * C * jb);
+    CUtensorMap tS;  // stores: rows [0, r_end), columns [0, c_end)
+    if (!mapM(&tS, M, r_end, c_end, ld, estride, E)) return ctx_fail(ctx, ELRT_EINVAL, "tensor map encoding failed");
     const int64_t items = (int64_t)((r_end - r0 + 127) / 128) * E;
     const unsigned grid = (unsigned)std::min<int64_t>(items, 152);
-    k_tc_update_strip<<<grid, kStripThreads, StripSmem::TOTAL, ctx->stream>>>(mp.m, mp.u, M, ctx->tab.nu, ld, estride, E,
-                                                                              J, jb, r0, r_end, c0, c_end, err);
+    k_tc_update_strip<<<grid, kStripThreads, StripSmem::TOTAL, ctx->stream>>>(mp.m, mp.u, tS, M, ctx->tab.nu, ld, estride,
+                                                                              E, J, jb, r0, r_end, c0, c_end, err);
     return cuda_check(ctx, cudaGetLastError(), "tc update launch");
 }
 
@@ -660,7 +687,7 @@ elrt_status prepare(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, const 
     // every column block starts at a multiple of 64 or at nu, and the vector accesses and TMA copies
     // need each to start on a 16-byte boundary (n_angles % 4 == 0 already makes nu a multiple of 4)
     if (nu % 4 != 0 || ld % 4 != 0) return ctx_fail(ctx, ELRT_EINVAL, "tensor-core LU needs nu and ld multiples of 4");
-    if (!mapM(&mp->m, M, nu, ld, estride, E) || !map3(&mp->u, Ut, ld, E, UBN))
+    if (!mapM(&mp->m, M, nu, ld, ld, estride, E) || !map3(&mp->u, Ut, ld, E, UBN))
         return ctx_fail(ctx, ELRT_EINVAL, "tensor map encoding failed");
     static bool attr_done = false;
     if (!attr_done) {
