@@ -618,6 +618,214 @@ __global__ void k_givens(double* __restrict__ H, int ldh, double* __restrict__ c
     if (st->res <= st->tol || hnext == 0.0) st->done = 1;
 }
 
+// ------------------------------------------------------------------------------------------------
+// Arnoldi step for the FP32 basis in four launches (after the matvec of step j):
+//   k_arn_dots   h1 = V^T w                            per-block partials, last block reduces
+//   k_arn_axdots w -= V h1; h2 = V^T w on the block's slice (the dots need only that slice)
+//   k_arn_axnorm w -= V h2; ||w||^2; the last block writes the Hessenberg column h1 + h2, ||w||
+//                and applies the Givens rotations (as k_givens)
+//   k_arn_scale  v_{j+1} = w / ||w||
+// The block that finishes last (a ticket counter behind a __threadfence of every block's partial
+// writes) reduces the blocks' partials in a fixed order, so the results are deterministic; no
+// block ever waits for another.  Sums accumulate in float-float, block results in FP64.
+// ------------------------------------------------------------------------------------------------
+constexpr int kArnThreads = 256;
+constexpr int kArnMaxV = 32;  // restart length + 1 supported by this path
+
+struct ArnState {
+    unsigned ticket[4];
+    double h1[kArnMaxV], h2[kArnMaxV], nrm;
+};
+
+// true in exactly one block: the last to finish its partial writes (all of which are then visible)
+__device__ bool arn_last_block(unsigned* ticket) {
+    __shared__ bool last;
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (last) __threadfence();
+    return last;
+}
+
+// out[i] = sum_b P[i * nb + b] (i < nv), one warp per vector, fixed order; ticket reset to 0
+__device__ void arn_finish(const double* P, unsigned nb, int nv, double* out, unsigned* ticket) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = warp; i < nv; i += kArnThreads / 32) {
+        double t = 0.0;
+        for (unsigned b = lane; b < nb; b += 32) t += ((volatile const double*)P)[(int64_t)i * nb + b];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
+        if (lane == 0) out[i] = t;
+    }
+    if (threadIdx.x == 0) *ticket = 0u;
+}
+
+// P[i * nb + blk] = sum over packs [p0, p1) of V_i . w (i < nv), eight vectors per sweep
+__device__ void arn_block_dots(const float4* __restrict__ V4, int64_t np, const float4* __restrict__ w4, int nv,
+                               int64_t p0, int64_t p1, double* __restrict__ P, unsigned nb) {
+    __shared__ ff red[kArnThreads / 32][8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int ib = 0; ib < nv; ib += 8) {
+        ff acc[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc[u] = ff{0.f, 0.f};
+        for (int64_t p = p0 + threadIdx.x; p < p1; p += kArnThreads) {
+            const float4 w = w4[p];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (ib + u < nv) {
+                    const float4 v = V4[(int64_t)(ib + u) * np + p];
+                    KV<float>::fma_vv(acc[u], v.x, w.x);
+                    KV<float>::fma_vv(acc[u], v.y, w.y);
+                    KV<float>::fma_vv(acc[u], v.z, w.z);
+                    KV<float>::fma_vv(acc[u], v.w, w.w);
+                }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const ff sum = ff_warp_sum(ff_norm(acc[u].h, acc[u].l));
+            if (lane == 0) red[warp][u] = sum;
+        }
+        __syncthreads();
+        if (threadIdx.x < 8 && ib + (int)threadIdx.x < nv) {
+            ff t{0.f, 0.f};
+            for (int wp = 0; wp < kArnThreads / 32; ++wp) t = ff_add(t, red[wp][threadIdx.x]);
+            P[(int64_t)(ib + threadIdx.x) * nb + blockIdx.x] = ff_to_double(t);
+        }
+        __syncthreads();
+    }
+}
+
+// w -= sum_i c[i] V_i on packs [p0, p1)
+__device__ void arn_axpy(const float4* __restrict__ V4, int64_t np, float4* __restrict__ w4, int nv,
+                         const double* c, int64_t p0, int64_t p1) {
+    __shared__ ff cf[kArnMaxV];
+    if (threadIdx.x < nv) cf[threadIdx.x] = KV<float>::coef(-c[threadIdx.x]);
+    __syncthreads();
+    for (int64_t p = p0 + threadIdx.x; p < p1; p += kArnThreads) {
+        const float4 w = w4[p];
+        ff a0 = KV<float>::load(w.x), a1 = KV<float>::load(w.y), a2 = KV<float>::load(w.z), a3 = KV<float>::load(w.w);
+#pragma unroll 4
+        for (int i = 0; i < nv; ++i) {
+            const float4 v = V4[(int64_t)i * np + p];
+            KV<float>::fma_cv(a0, cf[i], v.x);
+            KV<float>::fma_cv(a1, cf[i], v.y);
+            KV<float>::fma_cv(a2, cf[i], v.z);
+            KV<float>::fma_cv(a3, cf[i], v.w);
+        }
+        w4[p] = make_float4(KV<float>::store(a0), KV<float>::store(a1), KV<float>::store(a2), KV<float>::store(a3));
+    }
+}
+
+__device__ __forceinline__ void arn_slice(int64_t n, int64_t& np, int64_t& p0, int64_t& p1) {
+    np = n / 4;
+    p0 = np * blockIdx.x / gridDim.x;
+    p1 = np * (blockIdx.x + 1) / gridDim.x;
+}
+
+__global__ void __launch_bounds__(kArnThreads) k_arn_dots(const float* __restrict__ Vb, int64_t n, int j,
+                                                          double* __restrict__ P, ArnState* __restrict__ as,
+                                                          const GmState* __restrict__ st) {
+    if (st->done) return;
+    int64_t np, p0, p1;
+    arn_slice(n, np, p0, p1);
+    const int nv = j + 1;
+    arn_block_dots(reinterpret_cast<const float4*>(Vb), np, reinterpret_cast<const float4*>(Vb + (int64_t)nv * n), nv,
+                   p0, p1, P, gridDim.x);
+    if (arn_last_block(&as->ticket[0])) arn_finish(P, gridDim.x, nv, as->h1, &as->ticket[0]);
+}
+
+__global__ void __launch_bounds__(kArnThreads) k_arn_axdots(float* __restrict__ Vb, int64_t n, int j,
+                                                            double* __restrict__ P, ArnState* __restrict__ as,
+                                                            const GmState* __restrict__ st) {
+    if (st->done) return;
+    int64_t np, p0, p1;
+    arn_slice(n, np, p0, p1);
+    const int nv = j + 1;
+    const float4* V4 = reinterpret_cast<const float4*>(Vb);
+    float4* w4 = reinterpret_cast<float4*>(Vb + (int64_t)nv * n);
+    arn_axpy(V4, np, w4, nv, as->h1, p0, p1);
+    __syncthreads();  // the block's slice of w is final before its dots (each thread reads only its own packs)
+    arn_block_dots(V4, np, w4, nv, p0, p1, P, gridDim.x);
+    if (arn_last_block(&as->ticket[1])) arn_finish(P, gridDim.x, nv, as->h2, &as->ticket[1]);
+}
+
+__global__ void __launch_bounds__(kArnThreads) k_arn_axnorm(float* __restrict__ Vb, int64_t n, int j,
+                                                            double* __restrict__ P, ArnState* __restrict__ as,
+                                                            double* __restrict__ H, int ldh, double* __restrict__ cs,
+                                                            double* __restrict__ sn, double* __restrict__ gv,
+                                                            GmState* __restrict__ st) {
+    if (st->done) return;
+    int64_t np, p0, p1;
+    arn_slice(n, np, p0, p1);
+    const int nv = j + 1;
+    const float4* V4 = reinterpret_cast<const float4*>(Vb);
+    float4* w4 = reinterpret_cast<float4*>(Vb + (int64_t)nv * n);
+    arn_axpy(V4, np, w4, nv, as->h2, p0, p1);
+    {
+        __shared__ ff red[kArnThreads / 32];
+        ff acc{0.f, 0.f};
+        for (int64_t p = p0 + threadIdx.x; p < p1; p += kArnThreads) {
+            const float4 w = w4[p];
+            KV<float>::fma_vv(acc, w.x, w.x);
+            KV<float>::fma_vv(acc, w.y, w.y);
+            KV<float>::fma_vv(acc, w.z, w.z);
+            KV<float>::fma_vv(acc, w.w, w.w);
+        }
+        const ff sum = ff_warp_sum(ff_norm(acc.h, acc.l));
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sum;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            ff t{0.f, 0.f};
+            for (int wp = 0; wp < kArnThreads / 32; ++wp) t = ff_add(t, red[wp]);
+            P[blockIdx.x] = ff_to_double(t);
+        }
+    }
+    if (!arn_last_block(&as->ticket[2])) return;
+    __shared__ double nrm2;
+    arn_finish(P, gridDim.x, 1, &nrm2, &as->ticket[2]);
+    __syncthreads();
+    if (threadIdx.x == 0) {  // Hessenberg column j and the Givens rotations
+        const double nrm = sqrt(nrm2);
+        as->nrm = nrm;
+        double* h = H + (int64_t)j * ldh;
+        for (int i = 0; i < nv; ++i) h[i] = ((volatile double*)as->h1)[i] + ((volatile double*)as->h2)[i];
+        h[j + 1] = nrm;
+        for (int i = 0; i < j; ++i) {
+            const double t = cs[i] * h[i] + sn[i] * h[i + 1];
+            h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];
+            h[i] = t;
+        }
+        const double d = hypot(h[j], h[j + 1]);
+        const double c = d > 0 ? h[j] / d : 1.0, s = d > 0 ? h[j + 1] / d : 0.0;
+        cs[j] = c;
+        sn[j] = s;
+        h[j] = d;
+        h[j + 1] = 0.0;
+        gv[j + 1] = -s * gv[j];
+        gv[j] = c * gv[j];
+        st->j_done = j + 1;
+        st->res = fabs(gv[j + 1]);
+        if (st->res <= st->tol || nrm == 0.0) st->done = 1;
+    }
+}
+
+// v_{j+1} = w / ||w|| (runs even on the step that set the convergence flag, so the basis is whole)
+__global__ void __launch_bounds__(kArnThreads) k_arn_scale(float* __restrict__ Vb, int64_t n, int j,
+                                                           const ArnState* __restrict__ as) {
+    const double nrm = as->nrm;
+    if (!(nrm > 0.0)) return;
+    const ff inv = KV<float>::coef(1.0 / nrm);
+    float4* w4 = reinterpret_cast<float4*>(Vb + (int64_t)(j + 1) * n);
+    const int64_t np = n / 4;
+    for (int64_t p = blockIdx.x * (int64_t)kArnThreads + threadIdx.x; p < np; p += (int64_t)gridDim.x * kArnThreads) {
+        const float4 w = w4[p];
+        w4[p] = make_float4(KV<float>::store(ff_mul(ff{w.x, 0.f}, inv)), KV<float>::store(ff_mul(ff{w.y, 0.f}, inv)),
+                            KV<float>::store(ff_mul(ff{w.z, 0.f}, inv)), KV<float>::store(ff_mul(ff{w.w, 0.f}, inv)));
+    }
+}
+
 // y = R^{-1} g on the j_done x j_done upper triangle
 __global__ void k_solve_upper(const double* __restrict__ H, int ldh, const double* __restrict__ gv,
                               double* __restrict__ y, const GmState* __restrict__ st) {
@@ -725,7 +933,10 @@ elrt_status gmres(elrt_ctx* ctx, int nx, int nz, const void* Aop, const double* 
     // then the FP64 small arrays and the state
     const size_t vb_bytes = ((size_t)(m + 1) * n * sizeof(V) + 255) & ~(size_t)255;
     const size_t xbytes = (size_t)n * sizeof(X) * (1 + (own_x ? 1 : 0) + (own_r ? 1 : 0));
-    const size_t small = ((size_t)(m + 1) * m + 4 * (size_t)(m + 1) + (size_t)(m + 1) * nblk + 64) * sizeof(double);
+    // FP64 small arrays: H, cs, sn, gv, yv, partials (two more partial sets and a grid barrier for
+    // the fused Arnoldi step)
+    const size_t small = ((size_t)(m + 1) * m + 4 * (size_t)(m + 1) + (size_t)(m + 1) * nblk + 128) * sizeof(double) +
+                         sizeof(ArnState);
     elrt_status s = ensure_ws(ctx, &ctx->gm, &ctx->gm_bytes, vb_bytes + xbytes + 256 + small + sizeof(GmState) + 512);
     if (s) return s;
     V* Vb = (V*)ctx->gm;
@@ -738,8 +949,11 @@ elrt_status gmres(elrt_ctx* ctx, int nx, int nz, const void* Aop, const double* 
     double* gv = sn + (m + 1);
     double* yv = gv + (m + 1);
     double* partial = yv + (m + 1);
-    double* scal = partial + (size_t)(m + 1) * nblk;  // [0] ||b||, [1] beta
+    ArnState* arn = (ArnState*)(partial + (size_t)(m + 1) * nblk);
+    double* scal = (double*)(arn + 1) + 8;  // [0] ||b||, [1] beta
     GmState* st = (GmState*)(scal + 64);
+    // four-launch Arnoldi step: FP32 basis and restarts up to kArnMaxV - 1
+    const bool arn4 = std::is_same<V, float>::value && m + 1 <= kArnMaxV;
     cudaStream_t sm = ctx->stream;
     const unsigned gb = grid_for(n);
     // algorithmic bytes of a pass that touches nvec vectors of type T once each
@@ -748,6 +962,7 @@ elrt_status gmres(elrt_ctx* ctx, int nx, int nz, const void* Aop, const double* 
     const int rows = t.nin;
 
     s = cuda_check(ctx, cudaMemsetAsync(ctx->d_flags + kGemvFlag, 0, sizeof(int), sm), "clear flag");
+    if (!s) s = cuda_check(ctx, cudaMemsetAsync(arn, 0, sizeof(ArnState), sm), "clear Arnoldi state");
     if (s) return s;
     // b = A g_bnd
     s = launch_gemv<A, X>(ctx, nx, nz, rows, Aop, nullptr, inflow, nullptr, 0, 1, b, nullptr);
@@ -813,6 +1028,19 @@ elrt_status gmres(elrt_ctx* ctx, int nx, int nz, const void* Aop, const double* 
             double* hc = H + (size_t)j * (m + 1);
             s = launch_gemv<A, V>(ctx, nx, nz, rows, Aop, vj, nullptr, vj, 1, -1, w, st);
             if (s) return s;
+            if constexpr (std::is_same<V, float>::value) {
+                if (arn4) {  // Gram-Schmidt twice, normalisation and rotation in four launches
+                    const double vb = 4.0 * n;
+                    { ProfScope ps(ctx, "krylov", 1, (j + 2) * vb); k_arn_dots<<<nblk, kArnThreads, 0, sm>>>(Vb, n, j, partial, arn, st); }
+                    { ProfScope ps(ctx, "krylov", 1, (2 * j + 5) * vb); k_arn_axdots<<<nblk, kArnThreads, 0, sm>>>(Vb, n, j, partial, arn, st); }
+                    {
+                        ProfScope ps(ctx, "krylov", 1, (j + 3) * vb);
+                        k_arn_axnorm<<<nblk, kArnThreads, 0, sm>>>(Vb, n, j, partial, arn, H, m + 1, cs, sn, gv, st);
+                    }
+                    { ProfScope ps(ctx, "krylov", 1, 2 * vb); k_arn_scale<<<gb, kArnThreads, 0, sm>>>(Vb, n, j, arn); }
+                    continue;
+                }
+            }
             // classical Gram-Schmidt, twice
             const size_t sv = sizeof(V);
             { ProfScope ps(ctx, "krylov", 1, kv(j + 2, n, sv)); k_dots<V><<<dim3(nblk, j + 1), kThreads, 0, sm>>>(Vb, n, w, partial, st); }
