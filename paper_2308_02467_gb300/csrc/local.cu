@@ -720,18 +720,26 @@ __global__ void __launch_bounds__(kResThreads, 2) k_residual_ff(Tab t, double h,
 }
 
 // Restriction from the float-float solution: in2out = R^o X, in2sol = (1/N) sum_k X (eqs.
-// hdg_local_i2o and ang_ave), sums in float-float, rounded once to the output type.
+// hdg_local_i2o and ang_ave), sums in float-float, rounded once to the output type.  With D given
+// (the last refinement correction, FP32, in the right-hand-side columns of the matrix), the
+// restriction uses X + D without writing it back.
 __device__ __forceinline__ void ff_store(float* dst, ff v) { *dst = __fadd_rn(v.h, v.l); }
 __device__ __forceinline__ void ff_store(double* dst, ff v) { *dst = (double)v.h + (double)v.l; }
 
 template <typename O>
-__global__ void __launch_bounds__(kThreads) k_restrict_ff(Tab t, const ff* __restrict__ X, ff inv_n,
+__global__ void __launch_bounds__(kThreads) k_restrict_ff(Tab t, const ff* __restrict__ X, const float* __restrict__ D,
+                                                          int64_t dld, int64_t destride, ff inv_n,
                                                           O* __restrict__ in2out, O* __restrict__ in2sol,
                                                           int* __restrict__ estatus, int64_t E) {
     const int nin = t.nin, nm = t.nm, half = t.half;
     const int64_t e = blockIdx.x;
     if (e >= E) return;
     const ff* Xe = X + e * (int64_t)t.nu * nin;
+    const float* De = D ? D + e * destride : nullptr;
+    auto xval = [&](int row, int c) {
+        const ff x = Xe[(int64_t)row * nin + c];
+        return De ? ff_add(x, ff{De[(int64_t)row * dld + c], 0.f}) : x;
+    };
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nrows = nin + nm;
     int bad = 0;
@@ -741,7 +749,7 @@ __global__ void __launch_bounds__(kThreads) k_restrict_ff(Tab t, const ff* __res
             const int m = rem / half, kk = rem - m * half;
             const int row = t.outc[F][kk] * nm + face_node(F, m, t.p);
             for (int c = lane; c < nin; c += 32) {
-                const ff v = Xe[(int64_t)row * nin + c];
+                const ff v = xval(row, c);
                 if (!isfinite(v.h) || !isfinite(v.l)) bad = 1;
                 ff_store(in2out + e * (int64_t)nin * nin + (int64_t)r * nin + c, v);
             }
@@ -749,7 +757,7 @@ __global__ void __launch_bounds__(kThreads) k_restrict_ff(Tab t, const ff* __res
             const int i = r - nin;
             for (int c = lane; c < nin; c += 32) {
                 ff s{0.f, 0.f};
-                for (int k = 0; k < t.N; ++k) s = ff_add(s, Xe[(int64_t)(k * nm + i) * nin + c]);
+                for (int k = 0; k < t.N; ++k) s = ff_add(s, xval(k * nm + i, c));
                 s = ff_mul(s, inv_n);
                 if (!isfinite(s.h) || !isfinite(s.l)) bad = 1;
                 ff_store(in2sol + e * (int64_t)nm * nin + (int64_t)i * nin + c, s);
@@ -958,10 +966,12 @@ elrt_status run_residual_ff(elrt_ctx* ctx, double h, const double* h_elem, const
 }
 
 template <typename O>
-elrt_status run_restrict_ff(elrt_ctx* ctx, const ff* X, O* in2out, O* in2sol, int* estatus, int64_t n) {
+elrt_status run_restrict_ff(elrt_ctx* ctx, const ff* X, const float* D, int64_t dld, int64_t destride, O* in2out,
+                            O* in2sol, int* estatus, int64_t n) {
     const ff inv_n = ff_from_double_host(1.0 / ctx->tab.N);
-    ProfScope ps(ctx, "restrict", 1, restrict_bytes(ctx->tab, sizeof(ff), sizeof(O), n));
-    k_restrict_ff<O><<<(unsigned)n, kThreads, 0, ctx->stream>>>(ctx->tab, X, inv_n, in2out, in2sol, estatus, n);
+    ProfScope ps(ctx, "restrict", 1, restrict_bytes(ctx->tab, D ? sizeof(ff) + sizeof(float) : sizeof(ff), sizeof(O), n));
+    k_restrict_ff<O><<<(unsigned)n, kThreads, 0, ctx->stream>>>(ctx->tab, X, D, dld, destride, inv_n, in2out, in2sol,
+                                                                estatus, n);
     return cuda_check(ctx, cudaGetLastError(), "restrict launch");
 }
 
@@ -1042,8 +1052,10 @@ elrt_status build_chunked(elrt_ctx* ctx, int64_t E, double h, const double* h_el
                 s = run_residual_ff(ctx, h, he, ka, om, M, ld, estride, (ff*)X64, 0, maxres, n);
             else
                 s = run_residual<T>(ctx, h, he, ka, om, M, ld, estride, X64, 0, maxres, n);
-            // the last correction needs no residual unless statistics or status words are wanted
+            // the last correction needs no residual unless statistics or status words are wanted;
+            // on the FP32 path the restriction then adds it on the fly (no pass over X)
             const bool last_residual = stats || elem_status;
+            bool pending_d = false;
             for (int it = 0; it < (ir ? steps : 0) && !s; ++it) {
                 if constexpr (sizeof(T) == 4) {
                     if (tc) s = tc_lu_resolve(ctx, M, ld, estride, n, side, ctx->d_flags + 2);
@@ -1053,10 +1065,12 @@ elrt_status build_chunked(elrt_ctx* ctx, int64_t E, double h, const double* h_el
                 }
                 if (s) break;
                 const int rmode = (it + 1 == steps && !last_residual) ? 2 : 1;
-                if constexpr (sizeof(T) == 4)
-                    s = run_residual_ff(ctx, h, he, ka, om, M, ld, estride, (ff*)X64, rmode, maxres, n);
-                else
+                if constexpr (sizeof(T) == 4) {
+                    if (rmode == 2) pending_d = true;
+                    else s = run_residual_ff(ctx, h, he, ka, om, M, ld, estride, (ff*)X64, rmode, maxres, n);
+                } else {
                     s = run_residual<T>(ctx, h, he, ka, om, M, ld, estride, X64, rmode, maxres, n);
+                }
             }
             if (s) return s;
             // flag elements whose residual exceeds 1e-10 max|B^| (when the last residual was computed)
@@ -1065,10 +1079,13 @@ elrt_status build_chunked(elrt_ctx* ctx, int64_t E, double h, const double* h_el
                 k_flag_residual<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(maxres, estat, 1e-10 * bmax, n);
             }
             if constexpr (sizeof(T) == 4) {
+                const float* D = pending_d ? (const float*)M + t.nu : nullptr;
                 if (out_dtype == ELRT_F32)
-                    s = run_restrict_ff<float>(ctx, (const ff*)X64, (float*)o_i2o, (float*)o_i2m, estat, n);
+                    s = run_restrict_ff<float>(ctx, (const ff*)X64, D, ld, estride, (float*)o_i2o, (float*)o_i2m, estat,
+                                               n);
                 else
-                    s = run_restrict_ff<double>(ctx, (const ff*)X64, (double*)o_i2o, (double*)o_i2m, estat, n);
+                    s = run_restrict_ff<double>(ctx, (const ff*)X64, D, ld, estride, (double*)o_i2o, (double*)o_i2m,
+                                                estat, n);
             } else {
                 if (out_dtype == ELRT_F32)
                     s = run_restrict<double, float>(ctx, X64, t.nin, (int64_t)t.nu * t.nin, 0, (float*)o_i2o,

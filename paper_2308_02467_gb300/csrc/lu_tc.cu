@@ -44,10 +44,10 @@ __device__ __forceinline__ float tf32_hi(float a) { return __uint_as_float(__flo
 constexpr int TS = NBP + 1;
 constexpr int TI = NBP + 4;                                        // inverse row stride: 16-byte aligned rows
 constexpr int PTILE = 256;                                         // rows or columns per tile
-constexpr int RC_SMEM = (PTILE * TS + NBP * TI) * (int)sizeof(float);  // staging + one inverse
-static_assert(PTILE * TS >= NBP * PTILE, "the staging area holds a 64 x PTILE column block");
 
-// Tinv layout per element: [panel][2][64][64]: [0] = L11^{-1} (unit lower), [1] = U11^{-1} (upper)
+// Tinv layout per element: [panel][4][64][64]: [0] = L11^{-1} (unit lower), [1] = U11^{-1} (upper),
+// [2], [3] their transposes (so that every consumer copies its layout with 16-byte copies)
+constexpr int kInvMats = 4;
 __global__ void __launch_bounds__(64) k_diag(int nu, int64_t ld, int64_t estride, float* __restrict__ Mall, int J,
                                              int jb, float* __restrict__ Tinv, int npanels, int* __restrict__ estat,
                                              float piv_tol) {
@@ -81,8 +81,10 @@ __global__ void __launch_bounds__(64) k_diag(int nu, int64_t ld, int64_t estride
         const int r = idx / jb, c = idx % jb;
         M[(int64_t)(J + r) * ld + J + c] = D[r][c];
     }
-    float* Li = Tinv + ((int64_t)e * npanels + J / NBP) * 2 * NBP * NBP;
+    float* Li = Tinv + ((int64_t)e * npanels + J / NBP) * kInvMats * NBP * NBP;
     float* Ui = Li + NBP * NBP;
+    float* LiT = Ui + NBP * NBP;
+    float* UiT = LiT + NBP * NBP;
     // column t of L^{-1}: x_t = 1, x_i = -sum_{k=t..i-1} L_ik x_k (i > t)
     {
         float x[NBP];
@@ -98,6 +100,9 @@ __global__ void __launch_bounds__(64) k_diag(int nu, int64_t ld, int64_t estride
         }
 #pragma unroll
         for (int i = 0; i < NBP; ++i) Li[i * NBP + t] = x[i];
+#pragma unroll
+        for (int i = 0; i < NBP; i += 4)
+            *reinterpret_cast<float4*>(LiT + t * NBP + i) = make_float4(x[i], x[i + 1], x[i + 2], x[i + 3]);
     }
     // column t of U^{-1}: x_i = 0 (i > t), x_t = 1 / U_tt, x_i = -(sum_{k=i+1..t} U_ik x_k) / U_ii
     {
@@ -119,6 +124,9 @@ __global__ void __launch_bounds__(64) k_diag(int nu, int64_t ld, int64_t estride
         }
 #pragma unroll
         for (int i = 0; i < NBP; ++i) Ui[i * NBP + t] = x[i];
+#pragma unroll
+        for (int i = 0; i < NBP; i += 4)
+            *reinterpret_cast<float4*>(UiT + t * NBP + i) = make_float4(x[i], x[i + 1], x[i + 2], x[i + 3]);
     }
 }
 
@@ -142,103 +150,124 @@ __device__ __forceinline__ void tri_apply(const float (&a)[NBP], const float* __
     }
 }
 
-// Row/column work of one panel.  Tiles 0 .. nrt-1 are row tiles over rows [r_begin, r_end) (the
-// factorisation only): x = a U11^{-1} written back to the matrix.  The remaining tiles are column
-// tiles over columns [c_begin, c_end): y = L11^{-1} a (col_mode 0: factorisation and forward
-// sweep) or y = U11^{-1} a (col_mode 1: backward sweep), written back to the matrix (rows < jb)
-// and, transposed, to the side buffer Ut[e][column][0..63] (zero beyond jb).
-__global__ void __launch_bounds__(256, 2) k_rowcol(int nu, int64_t ld, int64_t estride, float* __restrict__ Mall, int J,
-                                                   int jb, const float* __restrict__ Tinv, int npanels, int r_begin,
-                                                   int r_end, int nrt, int c_begin, int c_end, int col_mode,
-                                                   float* __restrict__ Ut) {
-    extern __shared__ float sm[];
-    float* S = sm;                 // PTILE x TS staging
-    float* T = sm + PTILE * TS;    // 64 x TI inverse
-    const int64_t e = blockIdx.x;
-    float* M = Mall + e * estride;
-    const int tile = blockIdx.y;
+// Row/column work of one panel.  The work items are (element, tile): tiles 0 .. nrt-1 of an
+// element are row tiles over rows [r_begin, r_end) (the factorisation only): x = a U11^{-1}
+// written back to the matrix; the remaining nct tiles are column tiles over columns [c_begin,
+// c_end): y = L11^{-1} a (col_mode 0: factorisation and forward sweep) or y = U11^{-1} a
+// (col_mode 1: backward sweep), written back to the matrix (rows < jb) and, transposed, to the side
+// buffer Ut[e][column][0..63] (zero beyond jb).  Persistent: each block walks its items with two
+// staging buffers; the 16-byte cp.async copies of the next item (its 64-wide block and its
+// inverse) are in flight while the current item is computed and stored.
+constexpr int RS = NBP + 4;                        // staging row stride: 16-byte aligned rows
+constexpr int RC_BUF = PTILE * RS + NBP * RS;      // floats per buffer: staging + inverse
+constexpr int RC_SMEM = 2 * RC_BUF * (int)sizeof(float);
+static_assert(PTILE * RS >= NBP * PTILE, "the staging area holds a 64 x PTILE column block");
+
+__device__ __forceinline__ void cp_async16(float* smem, const float* gmem, bool valid) {
+    // src-size 0 fills the 16 bytes with zeros and reads nothing
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(tc::smem_u32(smem)), "l"(gmem),
+                 "r"(valid ? 16 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+__global__ void __launch_bounds__(256, 1) k_rowcol(int nu, int64_t ld, int64_t estride, float* __restrict__ Mall, int J,
+                                                   int jb, const float* __restrict__ Tinv, int npanels, int64_t E,
+                                                   int r_begin, int r_end, int nrt, int c_begin, int c_end, int nct,
+                                                   int col_mode, float* __restrict__ Ut) {
+    extern __shared__ __align__(16) float sm[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, t = threadIdx.x;
-    const float* Li = Tinv + ((int64_t)e * npanels + J / NBP) * 2 * NBP * NBP;
-    if (tile < nrt) {
-        const int r0 = r_begin + tile * PTILE;
-        const int nr = min(PTILE, r_end - r0);
-        const float* Ui = Li + NBP * NBP;
-        for (int idx = t; idx < NBP * NBP; idx += 256) T[(idx / NBP) * TI + idx % NBP] = Ui[idx];
-        // stage the nr x jb block A21 (zero beyond jb, a multiple of 4): 16-byte loads, all of a
-        // thread's issued before any is stored
-#pragma unroll 8
-        for (int idx = t; idx < PTILE * (NBP / 4); idx += 256) {
-            const int rr = idx >> 4, j4 = idx & 15;
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (rr < nr && 4 * j4 < jb) v = *reinterpret_cast<const float4*>(M + (int64_t)(r0 + rr) * ld + J + 4 * j4);
-            float* d = S + rr * TS + 4 * j4;
-            d[0] = v.x;
-            d[1] = v.y;
-            d[2] = v.z;
-            d[3] = v.w;
+    const int ntl = nrt + nct;
+    const int64_t W = E * ntl;
+    // issue the copies of item w into buffer b
+    auto load = [&](int64_t w, int b) {
+        float* S = sm + b * RC_BUF;
+        float* T = S + PTILE * RS;
+        const int64_t e = w / ntl;
+        const int tile = (int)(w - e * ntl);
+        const float* M = Mall + e * estride;
+        const float* inv = Tinv + ((int64_t)e * npanels + J / NBP) * kInvMats * NBP * NBP;
+        if (tile < nrt) {
+            const int r0 = r_begin + tile * PTILE, nr = min(PTILE, r_end - r0);
+            for (int idx = t; idx < PTILE * (NBP / 4); idx += 256) {
+                const int rr = idx >> 4, j4 = idx & 15;
+                const bool ok = rr < nr && 4 * j4 < jb;
+                cp_async16(S + rr * RS + 4 * j4, ok ? M + (int64_t)(r0 + rr) * ld + J + 4 * j4 : M, ok);
+            }
+            inv += NBP * NBP;  // U11^{-1}, T[i][j] = Uinv[i][j]
+        } else {
+            const int c0 = c_begin + (tile - nrt) * PTILE, nc = min(PTILE, c_end - c0);
+            for (int idx = t; idx < NBP * (PTILE / 4); idx += 256) {
+                const int k = idx / (PTILE / 4), c4 = idx % (PTILE / 4);
+                const bool ok = k < jb && 4 * c4 < nc;
+                cp_async16(S + k * PTILE + 4 * c4, ok ? M + (int64_t)(J + k) * ld + c0 + 4 * c4 : M, ok);
+            }
+            inv += (col_mode == 0 ? 2 : 3) * NBP * NBP;  // T[k][i] = Tinv[i][k]
         }
+        for (int idx = t; idx < NBP * (NBP / 4); idx += 256) {
+            const int r = idx >> 4, c4 = idx & 15;
+            cp_async16(T + r * RS + 4 * c4, inv + r * NBP + 4 * c4, true);
+        }
+    };
+    int b = 0;
+    if (blockIdx.x < W) load(blockIdx.x, 0);
+    cp_async_commit();
+    for (int64_t w = blockIdx.x; w < W; w += gridDim.x, b ^= 1) {
+        if (w + gridDim.x < W) load(w + gridDim.x, b ^ 1);
+        cp_async_commit();
+        cp_async_wait1();  // this item's copies have landed (the next item's may still be in flight)
         __syncthreads();
-        if (t < nr) {  // x_j = sum_{i <= j} a_i Uinv[i][j], written over the row it came from
+        float* S = sm + b * RC_BUF;
+        const float* T = S + PTILE * RS;
+        const int64_t e = w / ntl;
+        const int tile = (int)(w - e * ntl);
+        float* M = Mall + e * estride;
+        if (tile < nrt) {
+            const int r0 = r_begin + tile * PTILE, nr = min(PTILE, r_end - r0);
+            if (t < nr) {  // x_j = sum_{i <= j} a_i Uinv[i][j], written over the row it came from
+                float a[NBP];
+#pragma unroll
+                for (int i = 0; i < NBP; ++i) a[i] = S[t * RS + i];
+                float* out = S + t * RS;
+                tri_apply<true>(a, T, [&](int bb, float4 v) { *reinterpret_cast<float4*>(out + 4 * bb) = v; });
+            }
+            __syncthreads();
+            for (int rr = warp; rr < nr; rr += 8)
+                for (int j = lane; j < jb; j += 32) M[(int64_t)(r0 + rr) * ld + J + j] = S[rr * RS + j];
+        } else {
+            const int c0 = c_begin + (tile - nrt) * PTILE, nc = min(PTILE, c_end - c0);
             float a[NBP];
+            if (t < nc) {
 #pragma unroll
-            for (int i = 0; i < NBP; ++i) a[i] = S[t * TS + i];
-            float* out = S + t * TS;
-            tri_apply<true>(a, T, [&](int b, float4 v) {
-                out[4 * b] = v.x;
-                out[4 * b + 1] = v.y;
-                out[4 * b + 2] = v.z;
-                out[4 * b + 3] = v.w;
-            });
+                for (int k = 0; k < NBP; ++k) a[k] = S[k * PTILE + t];
+            }
+            __syncthreads();  // S is reused: from [k][column] staging to [column][i] results
+            if (t < nc) {
+                // y_i = sum_k Tinv[i][k] a_k with T[k][i] = Tinv[i][k]: the unit-lower L11^-1 (k <= i)
+                // or the upper U11^-1 (k >= i)
+                const int c = c0 + t;
+                float* mc = M + (int64_t)J * ld + c;
+                float* sr = S + t * RS;
+                auto put = [&](int bb, float4 v) {
+                    const int i = 4 * bb;
+                    if (i < jb) mc[(int64_t)i * ld] = v.x;
+                    if (i + 1 < jb) mc[(int64_t)(i + 1) * ld] = v.y;
+                    if (i + 2 < jb) mc[(int64_t)(i + 2) * ld] = v.z;
+                    if (i + 3 < jb) mc[(int64_t)(i + 3) * ld] = v.w;
+                    *reinterpret_cast<float4*>(sr + i) = v;
+                };
+                if (col_mode == 0) tri_apply<true>(a, T, put);
+                else tri_apply<false>(a, T, put);
+            }
+            __syncthreads();
+            float* ut = Ut + e * ld * NBP;
+            for (int cc = warp; cc < nc; cc += 8)
+                for (int i = lane; i < NBP; i += 32) ut[(int64_t)(c0 + cc) * NBP + i] = S[cc * RS + i];
         }
-        __syncthreads();
-        for (int rr = warp; rr < nr; rr += 8)
-            for (int j = lane; j < jb; j += 32) M[(int64_t)(r0 + rr) * ld + J + j] = S[rr * TS + j];
-        return;
+        __syncthreads();  // buffer b is refilled by the copies issued two items later
     }
-    const int c0 = c_begin + (tile - nrt) * PTILE;
-    const int nc = min(PTILE, c_end - c0);
-    const float* Ti = col_mode == 0 ? Li : Li + NBP * NBP;
-    for (int idx = t; idx < NBP * NBP; idx += 256) T[(idx % NBP) * TI + idx / NBP] = Ti[idx];  // transposed
-    // stage the jb x nc block A12 (row k of the panel in S[k][*]; c0 and nc are multiples of 4)
-    // with 16-byte loads, all of a thread's issued before any is stored
-#pragma unroll 8
-    for (int idx = t; idx < NBP * (PTILE / 4); idx += 256) {
-        const int k = idx / (PTILE / 4), c4 = idx % (PTILE / 4);
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        if (k < jb && 4 * c4 < nc) v = *reinterpret_cast<const float4*>(M + (int64_t)(J + k) * ld + c0 + 4 * c4);
-        *reinterpret_cast<float4*>(S + k * PTILE + 4 * c4) = v;
-    }
-    __syncthreads();
-    float a[NBP];
-    if (t < nc) {
-#pragma unroll
-        for (int k = 0; k < NBP; ++k) a[k] = S[k * PTILE + t];
-    }
-    __syncthreads();  // S is reused: from [k][column] staging to [column][i] results
-    if (t < nc) {
-        // y_i = sum_k Tinv[i][k] a_k with T[k][i] = Tinv[i][k]: the unit-lower L11^-1 (k <= i)
-        // or the upper U11^-1 (k >= i)
-        const int c = c0 + t;
-        float* mc = M + (int64_t)J * ld + c;
-        float* sr = S + t * TS;
-        auto put = [&](int b, float4 v) {
-            const int i = 4 * b;
-            if (i < jb) mc[(int64_t)i * ld] = v.x;
-            if (i + 1 < jb) mc[(int64_t)(i + 1) * ld] = v.y;
-            if (i + 2 < jb) mc[(int64_t)(i + 2) * ld] = v.z;
-            if (i + 3 < jb) mc[(int64_t)(i + 3) * ld] = v.w;
-            sr[i] = v.x;
-            sr[i + 1] = v.y;
-            sr[i + 2] = v.z;
-            sr[i + 3] = v.w;
-        };
-        if (col_mode == 0) tri_apply<true>(a, T, put);
-        else tri_apply<false>(a, T, put);
-    }
-    __syncthreads();
-    float* ut = Ut + e * ld * NBP;
-    for (int cc = warp; cc < nc; cc += 8)
-        for (int i = lane; i < NBP; i += 32) ut[(int64_t)(c0 + cc) * NBP + i] = S[cc * TS + i];
+    asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -714,9 +743,9 @@ elrt_status rowcol(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, int64_t
     const double bytes = 8.0 * R * jb + 8.0 * C * jb + 4.0 * C * NBP + 4.0 * NBP * NBP * ((R > 0) + (C > 0));
     const double flops = R * jb * (jb + 1.0) + (col_mode == 0 ? C * jb * (jb - 1.0) : C * jb * (jb + 1.0));
     ProfScope ps(ctx, "lu_tc_rowcol", 1, (double)E * bytes, (double)E * flops);
-    k_rowcol<<<dim3((unsigned)E, nrt + nct), 256, RC_SMEM, ctx->stream>>>(
-        ctx->tab.nu, ld, estride, M, J, jb, Tinv, panels_of(ctx->tab.nu), r_begin, r_end, nrt, c_begin, c_end,
-        col_mode, Ut);
+    const unsigned grid = (unsigned)std::min<int64_t>(E * (nrt + nct), 152);
+    k_rowcol<<<grid, 256, RC_SMEM, ctx->stream>>>(ctx->tab.nu, ld, estride, M, J, jb, Tinv, panels_of(ctx->tab.nu), E,
+                                                  r_begin, r_end, nrt, c_begin, c_end, nct, col_mode, Ut);
     return cuda_check(ctx, cudaGetLastError(), "rowcol launch");
 }
 
@@ -789,5 +818,5 @@ elrt_status tc_lu_resolve(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, 
 }
 
 size_t tc_lu_side_floats(const Tab& t, int64_t ld) {
-    return (size_t)NBP * ld + (size_t)panels_of(t.nu) * 2 * NBP * NBP;
+    return (size_t)NBP * ld + (size_t)panels_of(t.nu) * kInvMats * NBP * NBP;
 }
