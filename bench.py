@@ -67,7 +67,7 @@ def parse():
     ap.add_argument("--mode", default="tf32ir", choices=["tf32ir", "fp32ir", "fp64"])
     ap.add_argument("--refine", type=int, default=1)
     ap.add_argument("--rtol", type=float, default=1e-8)
-    ap.add_argument("--restart", type=int, default=20, help="GMRES restart length")
+    ap.add_argument("--restart", type=int, default=12, help="GMRES restart length")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nx", type=int, default=64, help="elements per side of the slab (64: the benchmark workload)")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-path section")

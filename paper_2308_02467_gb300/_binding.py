@@ -294,7 +294,7 @@ class Context:
         _check(_lib.elrt_global_apply(self._h, nx, nz, _ptr(in2out, None, n * self.nin, "in2out"), _dt(in2out),
                                       _ptr(x, torch.float64, n, "x"), _ptr(y, torch.float64, n, "y")), self._h)
 
-    def elrt_solve_global(self, nx, nz, in2out, inflow, skeleton, rtol=1e-10, max_iter=5000, restart=20,
+    def elrt_solve_global(self, nx, nz, in2out, inflow, skeleton, rtol=1e-10, max_iter=5000, restart=12,
                           use_guess=False, raise_on_noconv=True):
         import torch
         n = nx * nz * self.nin
@@ -311,7 +311,7 @@ class Context:
         return st
 
     def elrt_solve_field(self, nx, nz, h, kappa, omega, inflow, mean, skeleton=None, mode=LOCAL_FP32_IR,
-                         refine_steps=1, rtol=1e-8, max_iter=20000, restart=20, net=None, learned_tol=1e-3,
+                         refine_steps=1, rtol=1e-8, max_iter=20000, restart=12, net=None, learned_tol=1e-3,
                          raise_on_noconv=True):
         import torch
         E = nx * nz
@@ -461,7 +461,7 @@ def _opts(mode, refine_steps, rtol, max_iter, restart, net, learned_tol):
 
 
 def elrt_solve_batch(ctxs, fields, field_ctx, means, mode=LOCAL_FP32_IR, refine_steps=1, rtol=1e-8, max_iter=20000,
-                     restart=20, net=None, learned_tol=1e-3, wave_bytes=0, workers=0):
+                     restart=12, net=None, learned_tol=1e-3, wave_bytes=0, workers=0):
     """Many uneven fields: fields[f] = (nx, nz, h, kappa, omega, inflow) tensors; field_ctx[f] indexes ctxs.
     Returns the per-field FieldStats."""
     import torch

@@ -620,10 +620,14 @@ __global__ void k_givens(double* __restrict__ H, int ldh, double* __restrict__ c
 
 // ------------------------------------------------------------------------------------------------
 // Arnoldi step for the FP32 basis in four launches (after the matvec of step j):
-//   k_arn_dots   h1 = V^T w                            per-block partials, last block reduces
-//   k_arn_axdots w -= V h1; h2 = V^T w on the block's slice (the dots need only that slice)
-//   k_arn_axnorm w -= V h2; ||w||^2; the last block writes the Hessenberg column h1 + h2, ||w||
-//                and applies the Givens rotations (as k_givens)
+//   k_arn_dots   h1 = V^T w and ||w||^2                per-block partials, last block reduces and
+//                decides whether a second Gram-Schmidt pass is needed: only if the first pass
+//                cancelled more than half of ||w||^2 (||w||^2 - ||h1||^2 < ||w||^2 / 2, the usual
+//                criterion of classical Gram-Schmidt with selective reorthogonalisation)
+//   k_arn_axdots w -= V h1; then either h2 = V^T w (second pass) or ||w||^2 on the block's slice
+//   k_arn_axnorm second pass only: w -= V h2 and ||w||^2; the last block (or block 0 without a
+//                second pass) writes the Hessenberg column h1 + h2, ||w|| and applies the Givens
+//                rotations (as k_givens)
 //   k_arn_scale  v_{j+1} = w / ||w||
 // The block that finishes last (a ticket counter behind a __threadfence of every block's partial
 // writes) reduces the blocks' partials in a fixed order, so the results are deterministic; no
@@ -634,6 +638,7 @@ constexpr int kArnMaxV = 32;  // restart length + 1 supported by this path
 
 struct ArnState {
     unsigned ticket[4];
+    int reorth;  // second Gram-Schmidt pass in this step
     double h1[kArnMaxV], h2[kArnMaxV], nrm;
 };
 
@@ -731,9 +736,65 @@ __global__ void __launch_bounds__(kArnThreads) k_arn_dots(const float* __restric
     int64_t np, p0, p1;
     arn_slice(n, np, p0, p1);
     const int nv = j + 1;
-    arn_block_dots(reinterpret_cast<const float4*>(Vb), np, reinterpret_cast<const float4*>(Vb + (int64_t)nv * n), nv,
-                   p0, p1, P, gridDim.x);
-    if (arn_last_block(&as->ticket[0])) arn_finish(P, gridDim.x, nv, as->h1, &as->ticket[0]);
+    // vectors 0 .. nv-1 of the basis and w itself (stored as vector nv): h1 and ||w||^2
+    arn_block_dots(reinterpret_cast<const float4*>(Vb), np, reinterpret_cast<const float4*>(Vb + (int64_t)nv * n),
+                   nv + 1, p0, p1, P, gridDim.x);
+    if (!arn_last_block(&as->ticket[0])) return;
+    arn_finish(P, gridDim.x, nv + 1, as->h1, &as->ticket[0]);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const double w2 = as->h1[nv];
+        double s = 0.0;
+        for (int i = 0; i < nv; ++i) s += as->h1[i] * as->h1[i];
+        as->reorth = (w2 - s < 0.5 * w2) ? 1 : 0;
+        for (int i = 0; i < nv; ++i) as->h2[i] = 0.0;
+    }
+}
+
+// partial ||w||^2 of the block's slice into P[blockIdx.x]
+__device__ void arn_block_norm(const float4* __restrict__ w4, int64_t p0, int64_t p1, double* __restrict__ P) {
+    __shared__ ff red[kArnThreads / 32];
+    ff acc{0.f, 0.f};
+    for (int64_t p = p0 + threadIdx.x; p < p1; p += kArnThreads) {
+        const float4 w = w4[p];
+        KV<float>::fma_vv(acc, w.x, w.x);
+        KV<float>::fma_vv(acc, w.y, w.y);
+        KV<float>::fma_vv(acc, w.z, w.z);
+        KV<float>::fma_vv(acc, w.w, w.w);
+    }
+    const ff sum = ff_warp_sum(ff_norm(acc.h, acc.l));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ff t{0.f, 0.f};
+        for (int wp = 0; wp < kArnThreads / 32; ++wp) t = ff_add(t, red[wp]);
+        P[blockIdx.x] = ff_to_double(t);
+    }
+}
+
+// Hessenberg column j from h1 + h2 and ||w||, then the Givens rotations (one thread)
+__device__ void arn_column(const ArnState* as, int j, double nrm, double* H, int ldh, double* cs, double* sn,
+                           double* gv, GmState* st) {
+    const int nv = j + 1;
+    double* h = H + (int64_t)j * ldh;
+    for (int i = 0; i < nv; ++i) h[i] = ((volatile const double*)as->h1)[i] + ((volatile const double*)as->h2)[i];
+    h[j + 1] = nrm;
+    for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * h[i] + sn[i] * h[i + 1];
+        h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];
+        h[i] = t;
+    }
+    const double d = hypot(h[j], h[j + 1]);
+    const double c = d > 0 ? h[j] / d : 1.0, s = d > 0 ? h[j + 1] / d : 0.0;
+    cs[j] = c;
+    sn[j] = s;
+    h[j] = d;
+    h[j + 1] = 0.0;
+    gv[j + 1] = -s * gv[j];
+    gv[j] = c * gv[j];
+    st->j_done = j + 1;
+    st->res = fabs(gv[j + 1]);
+    if (st->res <= st->tol || nrm == 0.0) st->done = 1;
 }
 
 __global__ void __launch_bounds__(kArnThreads) k_arn_axdots(float* __restrict__ Vb, int64_t n, int j,
@@ -743,12 +804,23 @@ __global__ void __launch_bounds__(kArnThreads) k_arn_axdots(float* __restrict__ 
     int64_t np, p0, p1;
     arn_slice(n, np, p0, p1);
     const int nv = j + 1;
+    const bool reorth = ((volatile const int*)&as->reorth)[0] != 0;
     const float4* V4 = reinterpret_cast<const float4*>(Vb);
     float4* w4 = reinterpret_cast<float4*>(Vb + (int64_t)nv * n);
     arn_axpy(V4, np, w4, nv, as->h1, p0, p1);
-    __syncthreads();  // the block's slice of w is final before its dots (each thread reads only its own packs)
-    arn_block_dots(V4, np, w4, nv, p0, p1, P, gridDim.x);
-    if (arn_last_block(&as->ticket[1])) arn_finish(P, gridDim.x, nv, as->h2, &as->ticket[1]);
+    __syncthreads();  // the block's slice of w is final (each thread reads only its own packs)
+    if (reorth) {
+        arn_block_dots(V4, np, w4, nv, p0, p1, P, gridDim.x);
+        if (arn_last_block(&as->ticket[1])) arn_finish(P, gridDim.x, nv, as->h2, &as->ticket[1]);
+    } else {
+        arn_block_norm(w4, p0, p1, P);
+        if (arn_last_block(&as->ticket[1])) {
+            __shared__ double nrm2;
+            arn_finish(P, gridDim.x, 1, &nrm2, &as->ticket[1]);
+            __syncthreads();
+            if (threadIdx.x == 0) as->nrm = sqrt(nrm2);
+        }
+    }
 }
 
 __global__ void __launch_bounds__(kArnThreads) k_arn_axnorm(float* __restrict__ Vb, int64_t n, int j,
@@ -757,57 +829,26 @@ __global__ void __launch_bounds__(kArnThreads) k_arn_axnorm(float* __restrict__ 
                                                             double* __restrict__ sn, double* __restrict__ gv,
                                                             GmState* __restrict__ st) {
     if (st->done) return;
+    if (!((volatile const int*)&as->reorth)[0]) {  // single pass: the column and the rotation only
+        if (blockIdx.x == 0 && threadIdx.x == 0) arn_column(as, j, ((volatile const double*)&as->nrm)[0], H, ldh, cs, sn, gv, st);
+        return;
+    }
     int64_t np, p0, p1;
     arn_slice(n, np, p0, p1);
     const int nv = j + 1;
     const float4* V4 = reinterpret_cast<const float4*>(Vb);
     float4* w4 = reinterpret_cast<float4*>(Vb + (int64_t)nv * n);
     arn_axpy(V4, np, w4, nv, as->h2, p0, p1);
-    {
-        __shared__ ff red[kArnThreads / 32];
-        ff acc{0.f, 0.f};
-        for (int64_t p = p0 + threadIdx.x; p < p1; p += kArnThreads) {
-            const float4 w = w4[p];
-            KV<float>::fma_vv(acc, w.x, w.x);
-            KV<float>::fma_vv(acc, w.y, w.y);
-            KV<float>::fma_vv(acc, w.z, w.z);
-            KV<float>::fma_vv(acc, w.w, w.w);
-        }
-        const ff sum = ff_warp_sum(ff_norm(acc.h, acc.l));
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sum;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            ff t{0.f, 0.f};
-            for (int wp = 0; wp < kArnThreads / 32; ++wp) t = ff_add(t, red[wp]);
-            P[blockIdx.x] = ff_to_double(t);
-        }
-    }
+    __syncthreads();
+    arn_block_norm(w4, p0, p1, P);
     if (!arn_last_block(&as->ticket[2])) return;
     __shared__ double nrm2;
     arn_finish(P, gridDim.x, 1, &nrm2, &as->ticket[2]);
     __syncthreads();
-    if (threadIdx.x == 0) {  // Hessenberg column j and the Givens rotations
+    if (threadIdx.x == 0) {
         const double nrm = sqrt(nrm2);
         as->nrm = nrm;
-        double* h = H + (int64_t)j * ldh;
-        for (int i = 0; i < nv; ++i) h[i] = ((volatile double*)as->h1)[i] + ((volatile double*)as->h2)[i];
-        h[j + 1] = nrm;
-        for (int i = 0; i < j; ++i) {
-            const double t = cs[i] * h[i] + sn[i] * h[i + 1];
-            h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];
-            h[i] = t;
-        }
-        const double d = hypot(h[j], h[j + 1]);
-        const double c = d > 0 ? h[j] / d : 1.0, s = d > 0 ? h[j + 1] / d : 0.0;
-        cs[j] = c;
-        sn[j] = s;
-        h[j] = d;
-        h[j + 1] = 0.0;
-        gv[j + 1] = -s * gv[j];
-        gv[j] = c * gv[j];
-        st->j_done = j + 1;
-        st->res = fabs(gv[j + 1]);
-        if (st->res <= st->tol || nrm == 0.0) st->done = 1;
+        arn_column(as, j, nrm, H, ldh, cs, sn, gv, st);
     }
 }
 
@@ -1031,6 +1072,7 @@ elrt_status gmres(elrt_ctx* ctx, int nx, int nz, const void* Aop, const double* 
             if constexpr (std::is_same<V, float>::value) {
                 if (arn4) {  // Gram-Schmidt twice, normalisation and rotation in four launches
                     const double vb = 4.0 * n;
+                    // (bytes counted as if the second pass ran: the bound on what these launches move)
                     { ProfScope ps(ctx, "krylov", 1, (j + 2) * vb); k_arn_dots<<<nblk, kArnThreads, 0, sm>>>(Vb, n, j, partial, arn, st); }
                     { ProfScope ps(ctx, "krylov", 1, (2 * j + 5) * vb); k_arn_axdots<<<nblk, kArnThreads, 0, sm>>>(Vb, n, j, partial, arn, st); }
                     {

@@ -7,10 +7,10 @@
 //
 // The augmented matrix [A | -B^] of each element (FP32, row-major, leading dimension ld) is
 // factored in panels of 64 columns.  Per panel J:
-//   k_diag             (one small block per element): LU of the 64 x 64 diagonal block and the
-//                      explicit inverses L11^{-1}, U11^{-1};
-//   k_rowcol           (blocks of 256 rows or columns per element): L21 = A21 U11^{-1} written
-//                      back to the matrix; U12 = L11^{-1} A12 written back to the matrix and,
+//   k_diag             (one small block per element): LU of the 64 x 64 diagonal block, published
+//                      as U11, L11^T, U11^T and 1 / diag(U11);
+//   k_rowcol           (blocks of 256 rows or columns per element): L21 from L21 U11 = A21 written
+//                      back to the matrix; U12 from L11 U12 = A12 written back to the matrix and,
 //                      transposed (K-major), to one FP32 side buffer.  On the right-hand-side
 //                      columns this is the forward substitution;
 //   k_tc_update_strip  (tensor cores): C -= L21 U12 with three TF32 products hi*hi + hi*lo +
@@ -18,7 +18,7 @@
 //                      from the matrix, U12^T from the side buffer) and are split into TF32 high
 //                      and low parts in shared memory by four dedicated warps.
 // The backward substitution and the forward/backward sweeps of the refinement re-solves reuse
-// the stored factors (L21 and U12 in the matrix, the inverses) with the same kernels.
+// the stored factors (L21 and U12 in the matrix, the diagonal blocks) with the same kernels.
 #include <math.h>
 #include <stdio.h>
 
@@ -42,111 +42,130 @@ __device__ __forceinline__ float tf32_hi(float a) { return __uint_as_float(__flo
 // ------------------------------------------------------------------------------------------------
 
 constexpr int TS = NBP + 1;
-constexpr int TI = NBP + 4;                                        // inverse row stride: 16-byte aligned rows
+constexpr int TI = NBP + 4;                                        // factor row stride: 16-byte aligned rows
 constexpr int PTILE = 256;                                         // rows or columns per tile
 
-// Tinv layout per element: [panel][4][64][64]: [0] = L11^{-1} (unit lower), [1] = U11^{-1} (upper),
-// [2], [3] their transposes (so that every consumer copies its layout with 16-byte copies)
+// Factor layout per element and panel (the side buffer Tinv): [panel][4][64][64]:
+//   [0] U11 (upper, row-major), [1] L11^T (the strictly lower part of the unit-lower L11, transposed),
+//   [2] U11^T, [3] row 0: 1 / diag(U11).
+// Beyond jb the block is padded with the identity (U_ii = 1), so every consumer can run all 64 steps.
 constexpr int kInvMats = 4;
-__global__ void __launch_bounds__(64) k_diag(int nu, int64_t ld, int64_t estride, float* __restrict__ Mall, int J,
-                                             int jb, float* __restrict__ Tinv, int npanels, int* __restrict__ estat,
-                                             float piv_tol) {
+constexpr int kDiagThreads = 128;
+__global__ void __launch_bounds__(kDiagThreads) k_diag(int nu, int64_t ld, int64_t estride, float* __restrict__ Mall,
+                                                       int J, int jb, float* __restrict__ Tinv, int npanels,
+                                                       int* __restrict__ estat, float piv_tol) {
     __shared__ float D[NBP][TS];
+    __shared__ float lcol[NBP];
     const int64_t e = blockIdx.x;
     float* M = Mall + e * estride;
     const int t = threadIdx.x;
-    for (int idx = t; idx < NBP * NBP; idx += 64) {
+    for (int idx = t; idx < NBP * NBP; idx += kDiagThreads) {
         const int r = idx / NBP, c = idx % NBP;
         D[r][c] = (r < jb && c < jb) ? M[(int64_t)(J + r) * ld + J + c] : (r == c ? 1.f : 0.f);
     }
     __syncthreads();
+    // right-looking LU without pivoting: per step the multipliers, then the trailing block
     int bad = 0;
     for (int j = 0; j < jb; ++j) {
+        __syncthreads();  // the trailing update of step j - 1 is complete
         float piv = D[j][j];
         if (!(fabsf(piv) >= piv_tol)) {
             bad = 1;
             piv = piv < 0.f ? -piv_tol : piv_tol;
         }
-        __syncthreads();
-        if (t == j) D[j][j] = piv;
-        if (t > j && t < jb) {  // thread t eliminates row t
-            const float l = D[t][j] / piv;
+        const float rp = 1.f / piv;
+        // (thread 0 may write the clamped pivot while others read it: both clamp to the same value)
+        if (t == 0) D[j][j] = piv;
+        if (t > j && t < jb) {
+            const float l = D[t][j] * rp;
             D[t][j] = l;
-            for (int c = j + 1; c < jb; ++c) D[t][c] -= l * D[j][c];
+            lcol[t] = l;
         }
         __syncthreads();
+        // trailing block, rows and columns j+1 .. jb-1: column t % 64, every other row
+        const int c = t & (NBP - 1);
+        if (c > j && c < jb) {
+            const float ujc = D[j][c];
+            for (int r = j + 1 + (t >> 6); r < jb; r += kDiagThreads / NBP) D[r][c] -= lcol[r] * ujc;
+        }
     }
+    __syncthreads();
     if (bad && t == 0) atomicOr(&estat[e], 1);
-    for (int idx = t; idx < jb * jb; idx += 64) {
+    for (int idx = t; idx < jb * jb; idx += kDiagThreads) {
         const int r = idx / jb, c = idx % jb;
         M[(int64_t)(J + r) * ld + J + c] = D[r][c];
     }
-    float* Li = Tinv + ((int64_t)e * npanels + J / NBP) * kInvMats * NBP * NBP;
-    float* Ui = Li + NBP * NBP;
-    float* LiT = Ui + NBP * NBP;
-    float* UiT = LiT + NBP * NBP;
-    // column t of L^{-1}: x_t = 1, x_i = -sum_{k=t..i-1} L_ik x_k (i > t)
-    {
-        float x[NBP];
-#pragma unroll
-        for (int i = 0; i < NBP; ++i) {
-            float v = i == t ? 1.f : 0.f;
-            if (i > t) {
-#pragma unroll
-                for (int k = 0; k < i; ++k)
-                    if (k >= t) v -= D[i][k] * x[k];
-            }
-            x[i] = v;
-        }
-#pragma unroll
-        for (int i = 0; i < NBP; ++i) Li[i * NBP + t] = x[i];
-#pragma unroll
-        for (int i = 0; i < NBP; i += 4)
-            *reinterpret_cast<float4*>(LiT + t * NBP + i) = make_float4(x[i], x[i + 1], x[i + 2], x[i + 3]);
+    float* Uo = Tinv + ((int64_t)e * npanels + J / NBP) * kInvMats * NBP * NBP;
+    float* LT = Uo + NBP * NBP;
+    float* UT = LT + NBP * NBP;
+    float* rd = UT + NBP * NBP;
+    for (int idx = t; idx < NBP * NBP; idx += kDiagThreads) {
+        const int r = idx / NBP, c = idx % NBP;
+        Uo[idx] = c >= r ? D[r][c] : 0.f;   // U11
+        LT[idx] = c > r ? D[c][r] : 0.f;    // LT[r][c] = L[c][r], strictly lower part
+        UT[idx] = c <= r ? D[c][r] : 0.f;   // UT[r][c] = U[c][r]
     }
-    // column t of U^{-1}: x_i = 0 (i > t), x_t = 1 / U_tt, x_i = -(sum_{k=i+1..t} U_ik x_k) / U_ii
-    {
-        float x[NBP];
-#pragma unroll
-        for (int ii = 0; ii < NBP; ++ii) {
-            const int i = NBP - 1 - ii;
-            float v = 0.f;
-            if (i == t) {
-                v = 1.f / D[i][i];
-            } else if (i < t) {
-                float s = 0.f;
-#pragma unroll
-                for (int k = i + 1; k < NBP; ++k)
-                    if (k <= t) s += D[i][k] * x[k];
-                v = -s / D[i][i];
-            }
-            x[i] = v;
-        }
-#pragma unroll
-        for (int i = 0; i < NBP; ++i) Ui[i * NBP + t] = x[i];
-#pragma unroll
-        for (int i = 0; i < NBP; i += 4)
-            *reinterpret_cast<float4*>(UiT + t * NBP + i) = make_float4(x[i], x[i + 1], x[i + 2], x[i + 3]);
-    }
+    if (t < NBP) rd[t] = 1.f / D[t][t];
 }
 
-// out[4b .. 4b+3] = sum_k a[k] T[k][4b .. 4b+3] over the nonzero part of a triangular T (stored
-// with row stride TI): k in [0, 4b + 4) when LOWER_K (T[k][j] = 0 for k > j), k in [4b, 64)
-// otherwise.  Each 4-wide block is handed to put(b, float4) as soon as it is complete.
-template <bool LOWER_K, typename Put>
-__device__ __forceinline__ void tri_apply(const float (&a)[NBP], const float* __restrict__ T, Put put) {
+// Triangular solves of one row or column held in registers, with the factor in shared memory
+// (row stride TI) and the reciprocal diagonal rd:
+//   SolveKind 0 (row of L21):  x U = a     ->  x_i = a_i / U_ii, a_j -= x_i U[i][j] for j > i
+//   SolveKind 1 (forward):     L y = a     ->  y_i = a_i,        a_j -= LT[i][j] y_i for j > i
+//   SolveKind 2 (backward):    U y = a     ->  y_i = a_i / U_ii, a_j -= UT[i][j] y_i for j < i
+// (right-looking: every step updates independent accumulators).  Each finished 4-wide block of the
+// result is handed to put(b, float4): ascending b for kinds 0 and 1, descending for kind 2.
+template <int SolveKind, typename Put>
+__device__ __forceinline__ void tri_solve(float (&a)[NBP], const float* __restrict__ T, const float* __restrict__ rd,
+                                          Put put) {
+    if constexpr (SolveKind != 2) {
 #pragma unroll
-    for (int b = 0; b < NBP / 4; ++b) {
-        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int b = 0; b < NBP / 4; ++b) {
+            float y[4];
 #pragma unroll
-        for (int k = LOWER_K ? 0 : 4 * b; k < (LOWER_K ? 4 * b + 4 : NBP); ++k) {
-            const float4 u = reinterpret_cast<const float4*>(T + k * TI)[b];
-            acc.x = fmaf(a[k], u.x, acc.x);
-            acc.y = fmaf(a[k], u.y, acc.y);
-            acc.z = fmaf(a[k], u.z, acc.z);
-            acc.w = fmaf(a[k], u.w, acc.w);
+            for (int q = 0; q < 4; ++q) {
+                const int i = 4 * b + q;
+                const float x = SolveKind == 0 ? a[i] * rd[i] : a[i];
+                y[q] = x;
+                const float* Ti = T + i * TI;
+                const int j0 = (i + 4) & ~3;  // scalars up to the next 16-byte boundary, then float4
+#pragma unroll
+                for (int j = i + 1; j < j0; ++j) a[j] = fmaf(-x, Ti[j], a[j]);
+#pragma unroll
+                for (int j = j0; j < NBP; j += 4) {
+                    const float4 u = *reinterpret_cast<const float4*>(Ti + j);
+                    a[j] = fmaf(-x, u.x, a[j]);
+                    a[j + 1] = fmaf(-x, u.y, a[j + 1]);
+                    a[j + 2] = fmaf(-x, u.z, a[j + 2]);
+                    a[j + 3] = fmaf(-x, u.w, a[j + 3]);
+                }
+            }
+            put(b, make_float4(y[0], y[1], y[2], y[3]));
         }
-        put(b, acc);
+    } else {
+#pragma unroll
+        for (int b = NBP / 4 - 1; b >= 0; --b) {
+            float y[4];
+#pragma unroll
+            for (int q = 3; q >= 0; --q) {
+                const int i = 4 * b + q;
+                const float x = a[i] * rd[i];
+                y[q] = x;
+                const float* Ti = T + i * TI;
+                const int j1 = i & ~3;  // float4 below the 16-byte boundary, then scalars
+#pragma unroll
+                for (int j = 0; j < j1; j += 4) {
+                    const float4 u = *reinterpret_cast<const float4*>(Ti + j);
+                    a[j] = fmaf(-x, u.x, a[j]);
+                    a[j + 1] = fmaf(-x, u.y, a[j + 1]);
+                    a[j + 2] = fmaf(-x, u.z, a[j + 2]);
+                    a[j + 3] = fmaf(-x, u.w, a[j + 3]);
+                }
+#pragma unroll
+                for (int j = j1; j < i; ++j) a[j] = fmaf(-x, Ti[j], a[j]);
+            }
+            put(b, make_float4(y[0], y[1], y[2], y[3]));
+        }
     }
 }
 
@@ -156,10 +175,10 @@ __device__ __forceinline__ void tri_apply(const float (&a)[NBP], const float* __
 // c_end): y = L11^{-1} a (col_mode 0: factorisation and forward sweep) or y = U11^{-1} a
 // (col_mode 1: backward sweep), written back to the matrix (rows < jb) and, transposed, to the side
 // buffer Ut[e][column][0..63] (zero beyond jb).  Persistent: each block walks its items with two
-// staging buffers; the 16-byte cp.async copies of the next item (its 64-wide block and its
-// inverse) are in flight while the current item is computed and stored.
+// staging buffers; the 16-byte cp.async copies of the next item (its 64-wide block and the factor
+// of the diagonal block) are in flight while the current item is computed and stored.
 constexpr int RS = NBP + 4;                        // staging row stride: 16-byte aligned rows
-constexpr int RC_BUF = PTILE * RS + NBP * RS;      // floats per buffer: staging + inverse
+constexpr int RC_BUF = PTILE * RS + (NBP + 1) * RS;  // floats per buffer: staging + factor + 1/diag
 constexpr int RC_SMEM = 2 * RC_BUF * (int)sizeof(float);
 static_assert(PTILE * RS >= NBP * PTILE, "the staging area holds a 64 x PTILE column block");
 
@@ -172,10 +191,14 @@ __device__ __forceinline__ void cp_async16(float* smem, const float* gmem, bool 
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
+// KIND: 0 = row tiles (factorisation), 1 = column tiles of the factorisation / forward sweep,
+// 2 = column tiles of the backward sweep; one unrolled solve per instantiation
+template <int KIND>
 __global__ void __launch_bounds__(256, 1) k_rowcol(int nu, int64_t ld, int64_t estride, float* __restrict__ Mall, int J,
                                                    int jb, const float* __restrict__ Tinv, int npanels, int64_t E,
                                                    int r_begin, int r_end, int nrt, int c_begin, int c_end, int nct,
-                                                   int col_mode, float* __restrict__ Ut) {
+                                                   float* __restrict__ Ut) {
+    constexpr int col_mode = KIND == 2 ? 1 : 0;
     extern __shared__ __align__(16) float sm[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, t = threadIdx.x;
     const int ntl = nrt + nct;
@@ -195,7 +218,7 @@ __global__ void __launch_bounds__(256, 1) k_rowcol(int nu, int64_t ld, int64_t e
                 const bool ok = rr < nr && 4 * j4 < jb;
                 cp_async16(S + rr * RS + 4 * j4, ok ? M + (int64_t)(r0 + rr) * ld + J + 4 * j4 : M, ok);
             }
-            inv += NBP * NBP;  // U11^{-1}, T[i][j] = Uinv[i][j]
+            // U11 (row i: U[i][j])
         } else {
             const int c0 = c_begin + (tile - nrt) * PTILE, nc = min(PTILE, c_end - c0);
             for (int idx = t; idx < NBP * (PTILE / 4); idx += 256) {
@@ -203,11 +226,15 @@ __global__ void __launch_bounds__(256, 1) k_rowcol(int nu, int64_t ld, int64_t e
                 const bool ok = k < jb && 4 * c4 < nc;
                 cp_async16(S + k * PTILE + 4 * c4, ok ? M + (int64_t)(J + k) * ld + c0 + 4 * c4 : M, ok);
             }
-            inv += (col_mode == 0 ? 2 : 3) * NBP * NBP;  // T[k][i] = Tinv[i][k]
+            inv += (col_mode == 0 ? 1 : 2) * NBP * NBP;  // L11^T or U11^T
         }
         for (int idx = t; idx < NBP * (NBP / 4); idx += 256) {
             const int r = idx >> 4, c4 = idx & 15;
             cp_async16(T + r * RS + 4 * c4, inv + r * NBP + 4 * c4, true);
+        }
+        if (t < NBP / 4) {  // 1 / diag(U11)
+            const float* rdg = Tinv + ((int64_t)e * npanels + J / NBP) * kInvMats * NBP * NBP + 3 * NBP * NBP;
+            cp_async16(T + NBP * RS + 4 * t, rdg + 4 * t, true);
         }
     };
     int b = 0;
@@ -223,19 +250,19 @@ __global__ void __launch_bounds__(256, 1) k_rowcol(int nu, int64_t ld, int64_t e
         const int64_t e = w / ntl;
         const int tile = (int)(w - e * ntl);
         float* M = Mall + e * estride;
-        if (tile < nrt) {
+        if constexpr (KIND == 0) {
             const int r0 = r_begin + tile * PTILE, nr = min(PTILE, r_end - r0);
-            if (t < nr) {  // x_j = sum_{i <= j} a_i Uinv[i][j], written over the row it came from
+            if (t < nr) {  // x U11 = a, written over the row it came from
                 float a[NBP];
 #pragma unroll
                 for (int i = 0; i < NBP; ++i) a[i] = S[t * RS + i];
                 float* out = S + t * RS;
-                tri_apply<true>(a, T, [&](int bb, float4 v) { *reinterpret_cast<float4*>(out + 4 * bb) = v; });
+                tri_solve<0>(a, T, T + NBP * RS, [&](int bb, float4 v) { *reinterpret_cast<float4*>(out + 4 * bb) = v; });
             }
             __syncthreads();
             for (int rr = warp; rr < nr; rr += 8)
                 for (int j = lane; j < jb; j += 32) M[(int64_t)(r0 + rr) * ld + J + j] = S[rr * RS + j];
-        } else {
+        } else if constexpr (KIND != 0) {
             const int c0 = c_begin + (tile - nrt) * PTILE, nc = min(PTILE, c_end - c0);
             float a[NBP];
             if (t < nc) {
@@ -244,8 +271,7 @@ __global__ void __launch_bounds__(256, 1) k_rowcol(int nu, int64_t ld, int64_t e
             }
             __syncthreads();  // S is reused: from [k][column] staging to [column][i] results
             if (t < nc) {
-                // y_i = sum_k Tinv[i][k] a_k with T[k][i] = Tinv[i][k]: the unit-lower L11^-1 (k <= i)
-                // or the upper U11^-1 (k >= i)
+                // L11 y = a (forward) or U11 y = a (backward)
                 const int c = c0 + t;
                 float* mc = M + (int64_t)J * ld + c;
                 float* sr = S + t * RS;
@@ -257,8 +283,7 @@ __global__ void __launch_bounds__(256, 1) k_rowcol(int nu, int64_t ld, int64_t e
                     if (i + 3 < jb) mc[(int64_t)(i + 3) * ld] = v.w;
                     *reinterpret_cast<float4*>(sr + i) = v;
                 };
-                if (col_mode == 0) tri_apply<true>(a, T, put);
-                else tri_apply<false>(a, T, put);
+                tri_solve<KIND>(a, T, T + NBP * RS, put);
             }
             __syncthreads();
             float* ut = Ut + e * ld * NBP;
@@ -720,7 +745,9 @@ elrt_status prepare(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, const 
         return ctx_fail(ctx, ELRT_EINVAL, "tensor map encoding failed");
     static bool attr_done = false;
     if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(k_rowcol, cudaFuncAttributeMaxDynamicSharedMemorySize, RC_SMEM);
+        cudaError_t e = cudaFuncSetAttribute(k_rowcol<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, RC_SMEM);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rowcol<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, RC_SMEM);
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rowcol<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, RC_SMEM);
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_tc_update_strip, cudaFuncAttributeMaxDynamicSharedMemorySize, StripSmem::TOTAL);
         if (e != cudaSuccess) return cuda_check(ctx, e, "smem attribute");
@@ -737,15 +764,26 @@ elrt_status rowcol(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, int64_t
     const int nct = c_end > c_begin ? (c_end - c_begin + PTILE - 1) / PTILE : 0;
     if (nrt + nct == 0) return ELRT_OK;
     // algorithmic work per element: row tiles read R x jb and write it back; column tiles read and
-    // write jb x C and write U^T (C x 64); triangular products x Uinv, Linv x (unit lower) or
-    // Uinv x
+    // write jb x C and write U^T (C x 64); triangular solves with U11, L11 (unit lower) or U11
     const double R = std::max(0, r_end - r_begin), C = std::max(0, c_end - c_begin);
     const double bytes = 8.0 * R * jb + 8.0 * C * jb + 4.0 * C * NBP + 4.0 * NBP * NBP * ((R > 0) + (C > 0));
     const double flops = R * jb * (jb + 1.0) + (col_mode == 0 ? C * jb * (jb - 1.0) : C * jb * (jb + 1.0));
-    ProfScope ps(ctx, "lu_tc_rowcol", 1, (double)E * bytes, (double)E * flops);
-    const unsigned grid = (unsigned)std::min<int64_t>(E * (nrt + nct), 152);
-    k_rowcol<<<grid, 256, RC_SMEM, ctx->stream>>>(ctx->tab.nu, ld, estride, M, J, jb, Tinv, panels_of(ctx->tab.nu), E,
-                                                  r_begin, r_end, nrt, c_begin, c_end, nct, col_mode, Ut);
+    ProfScope ps(ctx, "lu_tc_rowcol", (nrt > 0) + (nct > 0), (double)E * bytes, (double)E * flops);
+    const int np = panels_of(ctx->tab.nu), nu = ctx->tab.nu;
+    if (nrt > 0) {  // items: (element, row tile)
+        const unsigned grid = (unsigned)std::min<int64_t>(E * nrt, 152);
+        k_rowcol<0><<<grid, 256, RC_SMEM, ctx->stream>>>(nu, ld, estride, M, J, jb, Tinv, np, E, r_begin, r_end, nrt,
+                                                         c_begin, c_end, 0, Ut);
+    }
+    if (nct > 0) {  // items: (element, column tile)
+        const unsigned grid = (unsigned)std::min<int64_t>(E * nct, 152);
+        if (col_mode == 0)
+            k_rowcol<1><<<grid, 256, RC_SMEM, ctx->stream>>>(nu, ld, estride, M, J, jb, Tinv, np, E, r_begin, r_end, 0,
+                                                             c_begin, c_end, nct, Ut);
+        else
+            k_rowcol<2><<<grid, 256, RC_SMEM, ctx->stream>>>(nu, ld, estride, M, J, jb, Tinv, np, E, r_begin, r_end, 0,
+                                                             c_begin, c_end, nct, Ut);
+    }
     return cuda_check(ctx, cudaGetLastError(), "rowcol launch");
 }
 
@@ -789,10 +827,12 @@ elrt_status tc_lu_factor_solve(elrt_ctx* ctx, float* M, int64_t ld, int64_t estr
     for (int J = 0; J < nu; J += NBP) {
         const int jb = std::min(NBP, nu - J);
         {
-            // the diagonal block in, both triangular inverses out; LU plus two triangular inverses
+            // the diagonal block in and out, its factor in three layouts plus the reciprocal pivots
             const double b3 = (double)jb * jb * jb;
-            ProfScope ps(ctx, "lu_tc_diag", 1, (double)E * (4.0 * jb * jb + 8.0 * NBP * NBP), (double)E * 4.0 / 3.0 * b3);
-            k_diag<<<(unsigned)E, 64, 0, ctx->stream>>>(nu, ld, estride, M, J, jb, sd.Tinv, panels_of(nu), estat, 1e-6f);
+            ProfScope ps(ctx, "lu_tc_diag", 1, (double)E * (8.0 * jb * jb + 4.0 * kInvMats * NBP * NBP),
+                         (double)E * 2.0 / 3.0 * b3);
+            k_diag<<<(unsigned)E, kDiagThreads, 0, ctx->stream>>>(nu, ld, estride, M, J, jb, sd.Tinv, panels_of(nu), estat,
+                                                                1e-6f);
         }
         s = rowcol(ctx, M, ld, estride, E, J, jb, sd.Tinv, J + jb, nu, J + jb, ncols, 0, sd.Ut);
         if (!s) s = update(ctx, mp, M, ld, estride, E, J, jb, J + jb, nu, J + jb, ncols, err);
