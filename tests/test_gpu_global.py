@@ -134,3 +134,15 @@ def test_flux_conservation_albedo_one(lib):
                     net += v
                     tot += abs(v)
     assert abs(net) < 1e-11 * tot
+
+
+@pytest.mark.parametrize("restart", [8, 31, 32, 50])
+def test_fp32_gmres_paths_agree(lib, restart):
+    """FP32 operators: restarts up to 31 run the four-launch Arnoldi step (last-block reductions,
+    selective second Gram-Schmidt pass), larger ones the general Krylov kernels; both reach the
+    oracle's mean intensity to the float-float level."""
+    prob = H.small_cloud(8, 6, 4, 8)
+    ref = hdg.solve_problem(prob, rtol=1e-13)
+    out = H.gpu_pipeline(prob, lib.LOCAL_FP32_IR, lib.F32, rtol=1e-12, restart=restart)
+    assert out["solve_stats"].converged == 1
+    assert hdg.rel_l2(out["u_mean"], ref["u_mean"], ref["disc"]) < 1e-6
