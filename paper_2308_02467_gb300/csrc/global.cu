@@ -25,7 +25,7 @@
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kDotBlocks = 304;  // 2 per SM
+constexpr int kDotBlocks = 608;  // 4 per SM: enough warps in flight for the Krylov passes
 constexpr int kMaxRestart = 200;
 
 struct GmState {
@@ -974,8 +974,7 @@ elrt_status gmres(elrt_ctx* ctx, int nx, int nz, const void* Aop, const double* 
     // then the FP64 small arrays and the state
     const size_t vb_bytes = ((size_t)(m + 1) * n * sizeof(V) + 255) & ~(size_t)255;
     const size_t xbytes = (size_t)n * sizeof(X) * (1 + (own_x ? 1 : 0) + (own_r ? 1 : 0));
-    // FP64 small arrays: H, cs, sn, gv, yv, partials (two more partial sets and a grid barrier for
-    // the fused Arnoldi step)
+    // FP64 small arrays: H, cs, sn, gv, yv, the per-block partials, then the Arnoldi-step state
     const size_t small = ((size_t)(m + 1) * m + 4 * (size_t)(m + 1) + (size_t)(m + 1) * nblk + 128) * sizeof(double) +
                          sizeof(ArnState);
     elrt_status s = ensure_ws(ctx, &ctx->gm, &ctx->gm_bytes, vb_bytes + xbytes + 256 + small + sizeof(GmState) + 512);
