@@ -66,6 +66,9 @@ typedef enum {
 
 typedef enum { ELRT_F32 = 0, ELRT_F64 = 1 } elrt_dtype;
 
+/* Operator used by the Arnoldi steps of the skeleton GMRES when in2out is FP32 (elrt_set_krylov_op). */
+typedef enum { ELRT_KRYLOV_F32 = 0, ELRT_KRYLOV_F16 = 1 } elrt_krylov_op;
+
 /* Element discretisation: degree p (1..10), N angular cells (4..32, multiple of 4), HG asymmetry g. */
 typedef struct {
     int32_t p;
@@ -118,6 +121,16 @@ elrt_status elrt_node_coords(const elrt_disc* disc, int32_t nx, int32_t nz, doub
 elrt_status elrt_create(elrt_ctx** ctx, const elrt_disc* disc, void* stream);
 elrt_status elrt_destroy(elrt_ctx* ctx);
 elrt_status elrt_set_stream(elrt_ctx* ctx, void* stream);
+/* Operator of the Arnoldi-step matvecs of elrt_solve_global / elrt_solve_field / elrt_solve_batch
+ * with FP32 in2out.  ELRT_KRYLOV_F16 (the default): each solve first writes an FP16 copy of in2out
+ * into the context's workspace (2 bytes per entry) and builds the Krylov basis with it, while the
+ * right-hand side and every restart residual use the FP32 operator, so the restarts still refine
+ * the iterate to rtol in the FP32 system (restarted GMRES as the inner solver of a mixed-precision
+ * iterative refinement; half the operator bytes per Arnoldi step).  A solve keeps the FP32
+ * operator throughout when in2out holds an entry beyond +-6e4 or a non-finite one, and switches to
+ * it when a restart cycle lowers the true residual by less than 10%.  ELRT_KRYLOV_F32: the FP32
+ * operator everywhere.  FP64 operators ignore the setting.  ELRT_EINVAL on another value. */
+elrt_status elrt_set_krylov_op(elrt_ctx* ctx, int32_t op);
 const char* elrt_status_str(elrt_status s);
 const char* elrt_last_error(const elrt_ctx* ctx);   /* message of the last failing call (or "") */
 
@@ -197,8 +210,11 @@ elrt_status elrt_global_apply(elrt_ctx* ctx, int32_t nx, int32_t nz, const void*
                               const double* x, double* y);
 
 /* Solves eq. hdg_global_mat, sum_K (R^o_K - A_i2o^K) u^ = 0 with the boundary inflow moved to the
- * right-hand side, by restarted GMRES(restart) with classical Gram-Schmidt applied twice, FP64
- * vectors and reductions, until ||b - A x|| <= rtol ||b|| or max_iter Arnoldi steps.
+ * right-hand side, by restarted GMRES(restart) with classical Gram-Schmidt (a second pass where
+ * the first cancels more than half of the norm), until ||b - A x|| <= rtol ||b|| (recomputed at
+ * every restart) or max_iter Arnoldi steps.  FP64 in2out: FP64 vectors.  FP32 in2out: FP32 Krylov
+ * basis, float-float iterate, right-hand side and restart residual, FP64 reductions; the Arnoldi
+ * steps use the operator that elrt_set_krylov_op selects.
  * inflow: device boundary data (layout above); skeleton: device [E][n_out] FP64, read as the
  * initial guess if use_guess != 0, else zeroed; on return it holds the outflow DOFs.
  * Synchronises.  Returns ELRT_ENOCONV (stats filled, skeleton = last iterate) if not converged. */

@@ -19,6 +19,7 @@ _lib = C.CDLL(LIB_PATH)
 ANG_FV0, ANG_DO = 0, 1
 LOCAL_FP64, LOCAL_FP32_IR, LOCAL_TF32_IR = 0, 1, 2
 F32, F64 = 0, 1
+KRYLOV_F32, KRYLOV_F16 = 0, 1
 STATUS = {0: "ok", 1: "EINVAL", 2: "ENOMEM", 3: "ESINGULAR", 4: "ENOCONV", 5: "ETIMEOUT", 6: "ECUDA", 7: "ENOTRAINED"}
 
 
@@ -79,6 +80,7 @@ _sig = {
     "elrt_create": (_i32, [_P(_vp), _P(Disc), _vp]),
     "elrt_destroy": (_i32, [_vp]),
     "elrt_set_stream": (_i32, [_vp, _vp]),
+    "elrt_set_krylov_op": (_i32, [_vp, _i32]),
     "elrt_status_str": (C.c_char_p, [_i32]),
     "elrt_last_error": (C.c_char_p, [_vp]),
     "elrt_assemble": (_i32, [_vp, _i64, _d, _vp, _vp, _vp, _vp, _vp]),
@@ -257,6 +259,10 @@ class Context:
 
     def elrt_launch_count(self):
         return _lib.elrt_launch_count(self._h)
+
+    def elrt_set_krylov_op(self, op):
+        """KRYLOV_F16 (default) or KRYLOV_F32: operator of the Arnoldi-step matvecs (FP32 in2out)."""
+        _check(_lib.elrt_set_krylov_op(self._h, int(op)), self._h)
 
     # ---- local stage
     def elrt_assemble(self, kappa, omega, h, A, rhs, h_elem=None):

@@ -48,6 +48,9 @@ struct elrt_ctx {
     size_t ws_bytes = 0;
     void* gm = nullptr;     // GMRES workspace
     size_t gm_bytes = 0;
+    void* gm16 = nullptr;   // FP16 copy of the skeleton operator (Arnoldi steps)
+    size_t gm16_bytes = 0;
+    int krylov_op = ELRT_KRYLOV_F16;
     void* ops = nullptr;    // in2out / in2sol of elrt_solve_field
     size_t ops_bytes = 0;
     void* vec = nullptr;    // skeleton of elrt_solve_field when the caller passes none

@@ -18,6 +18,8 @@
 #include <type_traits>
 #include <vector>
 
+#include <cuda_fp16.h>
+
 #include "elrt_internal.h"
 #include "ff.h"
 #include "tc_gemm.cuh"
@@ -96,6 +98,212 @@ template <> struct KV<float> : KVff {
 __device__ __forceinline__ ff to_ff(double v) { return ff_from_double(v); }
 __device__ __forceinline__ ff to_ff(ff v) { return v; }
 __device__ __forceinline__ ff to_ff(float v) { return ff{v, 0.f}; }
+
+// ------------------------------------------------------------------------------------------------
+// Arnoldi step for the FP32 basis (restart length below kArnMaxV), after the matvec of step j:
+//   matvec       w = v_j - A v_j; with the streaming matvec its blocks then form h1 = V^T w and
+//                ||w||^2 over their own output rows (k_arn_dots otherwise); the last block reduces
+//                and decides whether a second Gram-Schmidt pass is needed: only if the first pass
+//                cancelled more than half of ||w||^2 (||w||^2 - ||h1||^2 < ||w||^2 / 2, the usual
+//                criterion of classical Gram-Schmidt with selective reorthogonalisation)
+//   k_arn_axdots w -= V h1; then either h2 = V^T w (second pass) or ||w||^2 on the block's slice
+//   k_arn_axnorm second pass only: w -= V h2 and ||w||^2; the last block (or block 0 without a
+//                second pass) writes the Hessenberg column h1 + h2, ||w|| and applies the Givens
+//                rotations (as k_givens)
+// The basis is kept unnormalised: slot i holds W_i with v_i = s_i W_i, s_i = 1 / ||w|| of the step
+// that made it (s_0 = 1, the restart residual is scaled when it enters slot 0).  Every consumer
+// folds s_i into its coefficients (dots, updates, the iterate) or, in the matvec, into the gathered
+// input, so no pass over the vector is spent on the normalisation.
+// The block that finishes last (a ticket counter behind a __threadfence of every block's partial
+// writes) reduces the blocks' partials in a fixed order, so the results are deterministic; no
+// block ever waits for another.  Sums accumulate in float-float, block results in FP64.
+// ------------------------------------------------------------------------------------------------
+constexpr int kArnThreads = 256;
+constexpr int kArnMaxV = 32;  // restart length + 1 supported by this path
+
+struct ArnState {
+    unsigned ticket[4];
+    int reorth;  // second Gram-Schmidt pass in this step
+    double h1[kArnMaxV], h2[kArnMaxV], nrm;
+    double sc[kArnMaxV + 1];  // s_i of the basis slots
+};
+
+// block barrier: all threads, or (kNamed) the kArnThreads threads of a block whose other warps
+// have left (the streaming matvec's producer warp)
+template <bool kNamed>
+__device__ __forceinline__ void arn_sync() {
+    if constexpr (kNamed) asm volatile("bar.sync 2, %0;" ::"r"(kArnThreads) : "memory");
+    else __syncthreads();
+}
+
+// true in exactly one block: the last to finish its partial writes (all of which are then visible)
+template <bool kNamed = false>
+__device__ bool arn_last_block(unsigned* ticket) {
+    __shared__ bool last;
+    __threadfence();
+    arn_sync<kNamed>();
+    if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+    arn_sync<kNamed>();
+    if (last) __threadfence();
+    return last;
+}
+
+// out[i] = s_i sum_b P[i * nb + b] (i < nv; s_i = sc[i] for i < nsc, else 1), one warp per
+// vector, fixed order; ticket reset to 0
+__device__ void arn_finish(const double* P, unsigned nb, int nv, double* out, unsigned* ticket, const double* sc,
+                           int nsc) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = warp; i < nv; i += kArnThreads / 32) {
+        double t = 0.0;
+        for (unsigned b = lane; b < nb; b += 32) t += ((volatile const double*)P)[(int64_t)i * nb + b];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
+        if (lane == 0) out[i] = i < nsc ? t * ((volatile const double*)sc)[i] : t;
+    }
+    if (threadIdx.x == 0) *ticket = 0u;
+}
+
+// P[i * nb + blk] = sum over the block's packs V_i . w (i < nv), eight vectors per sweep; the
+// block's packs are map(t) for t < cnt (float4 indices into each vector)
+template <bool kNamed, typename Map>
+__device__ void arn_block_dots(const float4* __restrict__ V4, int64_t np, const float4* __restrict__ w4, int nv,
+                               int64_t cnt, Map map, double* __restrict__ P, unsigned nb) {
+    __shared__ ff red[kArnThreads / 32][8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int ib = 0; ib < nv; ib += 8) {
+        ff acc[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc[u] = ff{0.f, 0.f};
+        for (int64_t t = threadIdx.x; t < cnt; t += kArnThreads) {
+            const int64_t p = map(t);
+            const float4 w = w4[p];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (ib + u < nv) {
+                    const float4 v = V4[(int64_t)(ib + u) * np + p];
+                    KV<float>::fma_vv(acc[u], v.x, w.x);
+                    KV<float>::fma_vv(acc[u], v.y, w.y);
+                    KV<float>::fma_vv(acc[u], v.z, w.z);
+                    KV<float>::fma_vv(acc[u], v.w, w.w);
+                }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const ff sum = ff_warp_sum(ff_norm(acc[u].h, acc[u].l));
+            if (lane == 0) red[warp][u] = sum;
+        }
+        arn_sync<kNamed>();
+        if (threadIdx.x < 8 && ib + (int)threadIdx.x < nv) {
+            ff t{0.f, 0.f};
+            for (int wp = 0; wp < kArnThreads / 32; ++wp) t = ff_add(t, red[wp][threadIdx.x]);
+            P[(int64_t)(ib + threadIdx.x) * nb + blockIdx.x] = ff_to_double(t);
+        }
+        arn_sync<kNamed>();
+    }
+}
+
+// the last block of the first pass: h1 = s_i (W_i . w) (i <= j), ||w||^2 in h1[j + 1], and the
+// decision on the second pass
+template <bool kNamed>
+__device__ void arn_first_pass_finish(const double* P, unsigned nb, int j, ArnState* as) {
+    const int nv = j + 1;
+    arn_finish(P, nb, nv + 1, as->h1, &as->ticket[0], as->sc, nv);
+    arn_sync<kNamed>();
+    if (threadIdx.x == 0) {
+        const double w2 = ((volatile const double*)as->h1)[nv];
+        double s = 0.0;
+        for (int i = 0; i < nv; ++i) {
+            const double h = ((volatile const double*)as->h1)[i];
+            s += h * h;
+        }
+        as->reorth = (w2 - s < 0.5 * w2) ? 1 : 0;
+        for (int i = 0; i < nv; ++i) as->h2[i] = 0.0;
+    }
+}
+
+// w -= sum_i c[i] s_i W_i on packs [p0, p1)
+__device__ void arn_axpy(const float4* __restrict__ V4, int64_t np, float4* __restrict__ w4, int nv,
+                         const double* c, const double* sc, int64_t p0, int64_t p1) {
+    __shared__ ff cf[kArnMaxV];
+    if (threadIdx.x < nv) cf[threadIdx.x] = KV<float>::coef(-c[threadIdx.x] * sc[threadIdx.x]);
+    __syncthreads();
+    for (int64_t p = p0 + threadIdx.x; p < p1; p += kArnThreads) {
+        const float4 w = w4[p];
+        ff a0 = KV<float>::load(w.x), a1 = KV<float>::load(w.y), a2 = KV<float>::load(w.z), a3 = KV<float>::load(w.w);
+#pragma unroll 4
+        for (int i = 0; i < nv; ++i) {
+            const float4 v = V4[(int64_t)i * np + p];
+            KV<float>::fma_cv(a0, cf[i], v.x);
+            KV<float>::fma_cv(a1, cf[i], v.y);
+            KV<float>::fma_cv(a2, cf[i], v.z);
+            KV<float>::fma_cv(a3, cf[i], v.w);
+        }
+        w4[p] = make_float4(KV<float>::store(a0), KV<float>::store(a1), KV<float>::store(a2), KV<float>::store(a3));
+    }
+}
+
+__device__ __forceinline__ void arn_slice(int64_t n, int64_t& np, int64_t& p0, int64_t& p1) {
+    np = n / 4;
+    p0 = np * blockIdx.x / gridDim.x;
+    p1 = np * (blockIdx.x + 1) / gridDim.x;
+}
+
+// partial ||w||^2 of the block's slice into P[blockIdx.x]
+__device__ void arn_block_norm(const float4* __restrict__ w4, int64_t p0, int64_t p1, double* __restrict__ P) {
+    __shared__ ff red[kArnThreads / 32];
+    ff acc{0.f, 0.f};
+    for (int64_t p = p0 + threadIdx.x; p < p1; p += kArnThreads) {
+        const float4 w = w4[p];
+        KV<float>::fma_vv(acc, w.x, w.x);
+        KV<float>::fma_vv(acc, w.y, w.y);
+        KV<float>::fma_vv(acc, w.z, w.z);
+        KV<float>::fma_vv(acc, w.w, w.w);
+    }
+    const ff sum = ff_warp_sum(ff_norm(acc.h, acc.l));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sum;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ff t{0.f, 0.f};
+        for (int wp = 0; wp < kArnThreads / 32; ++wp) t = ff_add(t, red[wp]);
+        P[blockIdx.x] = ff_to_double(t);
+    }
+}
+
+// Hessenberg column j from h1 + h2 and ||w||, s_{j+1} = 1 / ||w||, then the Givens rotations
+// (one thread)
+__device__ void arn_column(ArnState* as, int j, double nrm, double* H, int ldh, double* cs, double* sn, double* gv,
+                           GmState* st) {
+    const int nv = j + 1;
+    double* h = H + (int64_t)j * ldh;
+    for (int i = 0; i < nv; ++i) h[i] = ((volatile const double*)as->h1)[i] + ((volatile const double*)as->h2)[i];
+    h[j + 1] = nrm;
+    as->sc[j + 1] = nrm > 0.0 ? 1.0 / nrm : 0.0;
+    for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * h[i] + sn[i] * h[i + 1];
+        h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];
+        h[i] = t;
+    }
+    const double d = hypot(h[j], h[j + 1]);
+    const double c = d > 0 ? h[j] / d : 1.0, s = d > 0 ? h[j + 1] / d : 0.0;
+    cs[j] = c;
+    sn[j] = s;
+    h[j] = d;
+    h[j + 1] = 0.0;
+    gv[j + 1] = -s * gv[j];
+    gv[j] = c * gv[j];
+    st->j_done = j + 1;
+    st->res = fabs(gv[j + 1]);
+    if (st->res <= st->tol || nrm == 0.0) st->done = 1;
+}
+
+// Fused first Gram-Schmidt pass of the streaming matvec (null: plain matvec)
+struct ArnFuse {
+    ArnState* as;
+    double* P;         // per-block partials, (j + 2) x gridDim.x
+    const float* Vb;   // basis slots 0 .. j + 1 (slot j + 1 = the matvec's output w)
+    int64_t n;         // vector length
+    int j;
+};
 
 // ------------------------------------------------------------------------------------------------
 // block-sparse matvec
@@ -217,13 +425,15 @@ __global__ void __launch_bounds__(kThreads) k_elem_gemv(int nx, int nz, int nin,
     }
 }
 
-// Streaming variant for FP32 operators (the same y_K): a persistent grid walks the elements; per
-// block one producer warp copies each element's operator in chunks of 8 RPW rows (contiguous in
-// memory) into a ring of shared-memory stages with bulk asynchronous copies, and eight consumer
-// warps, RPW rows each, form the float-float row sums from shared memory against the gathered
-// inflow (double-buffered per element) and combine them with the self term.
+// Streaming variant for FP32 operators and their FP16 copy (the same y_K): a persistent grid walks
+// the elements; per block one producer warp copies each element's operator in chunks of 8 RPW rows
+// (contiguous in memory) into a ring of shared-memory stages with bulk asynchronous copies, and
+// eight consumer warps, RPW rows each, form the row sums from shared memory against the gathered
+// inflow (double-buffered per element) and combine them with the self term.  The FP16 copy only
+// serves the Arnoldi steps (FP32 vectors in and out).
 constexpr int kGvWarps = 8;           // consumer warps
 constexpr int kGemvFlag = 16;         // d_flags slot: a copy wait of the streaming matvec timed out
+constexpr int kF16Flag = 17;          // d_flags slot: the operator holds a value outside the FP16 range
 constexpr int kGvStages = 3;
 constexpr int kGvStageBytes = 32768;
 constexpr int kGvThreads = 32 * (kGvWarps + 1);
@@ -267,17 +477,39 @@ __device__ __forceinline__ ff warp_rows_reduce(ff (&acc)[RPW], int lane) {
     return v;
 }
 
-template <typename V, int RPW>
+// The same exchange for plain FP32 partial sums (any power-of-two RPW up to 32): each step halves
+// the set of rows a lane keeps, selected by one lane bit from the top.
+template <int RPW>
+__device__ __forceinline__ float warp_rows_reduce_f(float (&v)[RPW], int lane) {
+#pragma unroll
+    for (int n = RPW, m = 16; n > 1; n >>= 1, m >>= 1) {
+        const bool P = lane & m;
+#pragma unroll
+        for (int i = 0; i < n / 2; ++i) {
+            const float mine = P ? v[n / 2 + i] : v[i];
+            const float other = P ? v[i] : v[n / 2 + i];
+            v[i] = mine + __shfl_xor_sync(0xffffffffu, other, m);
+        }
+    }
+#pragma unroll
+    for (int m = 16 / RPW; m > 0; m >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], m);
+    return v[0];
+}
+
+template <typename V, int RPW, typename AT>
 __global__ void __launch_bounds__(kGvThreads, 2)
-    k_gemv_stream(int nx, int nz, int nin, int nface, int rows, const float* __restrict__ Aop,
+    k_gemv_stream(int nx, int nz, int nin, int nface, int rows, const AT* __restrict__ Aop,
                   const V* __restrict__ x, const double* __restrict__ g, const V* __restrict__ xself, int alpha,
-                  int beta, V* __restrict__ y, const GmState* __restrict__ st, int* __restrict__ err) {
+                  int beta, V* __restrict__ y, const GmState* __restrict__ st, int* __restrict__ err, ArnFuse fz) {
+    static_assert(std::is_same<AT, float>::value || std::is_same<V, float>::value, "FP16 operators: Arnoldi steps only");
+    static_assert(32 * kGvWarps == kArnThreads, "the fused dots run on the consumer warps");
     if (st && st->done) return;
     using K = KV<V>;
     using Acc = typename K::acc;
     constexpr int CR = kGvWarps * RPW;  // rows per chunk
+    constexpr int kStageElems = kGvStageBytes / (int)sizeof(AT);
     extern __shared__ __align__(128) unsigned char gsm[];
-    float* stages = reinterpret_cast<float*>(gsm);
+    AT* stages = reinterpret_cast<AT*>(gsm);
     ff* xs = reinterpret_cast<ff*>(gsm + kGvStages * kGvStageBytes);  // [2][nin]
     __shared__ uint64_t full[kGvStages], empty[kGvStages];
     __shared__ int abort_flag;
@@ -296,6 +528,7 @@ __global__ void __launch_bounds__(kGvThreads, 2)
     __syncthreads();
     if (warp == kGvWarps) {  // producer
         if (lane == 0) {
+            const uint64_t pol = tc::l2_evict_first();  // the operator is read once per matvec
             int it = 0;
             for (int64_t e = blockIdx.x; e < E && !*abort; e += gridDim.x) {
                 for (int c = 0; c < nch; ++c, ++it) {
@@ -306,10 +539,10 @@ __global__ void __launch_bounds__(kGvThreads, 2)
                         break;
                     }
                     const int nr = min(CR, rows - c * CR);
-                    const uint32_t bytes = (uint32_t)nr * nin * 4u;
+                    const uint32_t bytes = (uint32_t)nr * nin * (uint32_t)sizeof(AT);
                     tc::mbar_expect_tx(&full[s], bytes);
-                    tc::bulk_load(stages + (size_t)s * (kGvStageBytes / 4), Aop + (e * rows + c * CR) * (int64_t)nin,
-                                  bytes, &full[s]);
+                    tc::bulk_load_hint(stages + (size_t)s * kStageElems, Aop + (e * rows + c * CR) * (int64_t)nin,
+                                       bytes, &full[s], pol);
                 }
             }
             // let the copies in flight land before the block can exit
@@ -328,6 +561,14 @@ __global__ void __launch_bounds__(kGvThreads, 2)
     V* xsv = reinterpret_cast<V*>(xs + 2 * nin);  // [2][rows] self term
     ff pin[PF];
     V pself[PF];
+    // fused Arnoldi step: the input is the unnormalised slot W_j, v_j = s_j W_j
+    float xsc = 1.f;
+    if constexpr (std::is_same<V, float>::value)
+        if (fz.as) xsc = (float)((volatile const double*)fz.as->sc)[fz.j];
+    auto in_val = [&](V v) -> V {
+        if constexpr (std::is_same<V, float>::value) return v * xsc;
+        else return v;
+    };
     auto prefetch = [&](int64_t e) {
         const int ix = (int)(e % nx), iz = (int)(e / nx);
 #pragma unroll
@@ -362,9 +603,15 @@ __global__ void __launch_bounds__(kGvThreads, 2)
         V* se = xsv + buf * rows;
 #pragma unroll
         for (int u = 0; u < PF; ++u) {
+            // (the scale of a fused Arnoldi step is applied here, after the loads have landed: the
+            // prefetch itself never waits on them)
             const int c = ctid + u * 32 * kGvWarps;
-            if (c < nin) xe[c] = pin[u];
-            if (alpha && c < rows) se[c] = pself[u];
+            if (c < nin) {
+                ff v = pin[u];
+                if constexpr (std::is_same<V, float>::value) v.h *= xsc;  // fused step: no boundary data, v = (x, 0)
+                xe[c] = v;
+            }
+            if (alpha && c < rows) se[c] = in_val(pself[u]);
         }
         asm volatile("bar.sync 1, %0;" ::"r"(32 * kGvWarps) : "memory");  // consumers only
         if (e + gridDim.x < E) prefetch(e + gridDim.x);
@@ -377,8 +624,42 @@ __global__ void __launch_bounds__(kGvThreads, 2)
                 *abort = 1;
                 continue;
             }
-            const float* Ac = stages + (size_t)s * (kGvStageBytes / 4) + (size_t)warp * RPW * nin;
+            const AT* Ac = stages + (size_t)s * kStageElems + (size_t)warp * RPW * nin;
             const int rbase = c * CR + warp * RPW;
+            if constexpr (std::is_same<AT, __half>::value) {
+                // Arnoldi step on the FP16 copy: FP32 throughout (the copy's rounding, ~5e-4, is
+                // far above FP32's).  Lanes take column pairs (2 q, 2 q + 1), even and odd columns
+                // in separate chains; nin is even.
+                const int np = nin >> 1;
+                const __half2* A2 = reinterpret_cast<const __half2*>(Ac);
+                const float4* x4 = reinterpret_cast<const float4*>(xe);  // (h, l) of two columns
+                float f1[RPW], f2[RPW];
+#pragma unroll
+                for (int q = 0; q < RPW; ++q) f1[q] = f2[q] = 0.f;
+                for (int pc = lane; pc < np; pc += 32) {
+                    const float4 xv = x4[pc];
+#pragma unroll
+                    for (int q = 0; q < RPW; ++q) {
+                        const float2 a = __half22float2(A2[q * np + pc]);
+                        f1[q] = fmaf(a.x, xv.x, f1[q]);
+                        f2[q] = fmaf(a.y, xv.z, f2[q]);
+                    }
+                }
+                tc::fence_proxy_async();
+                __syncwarp();
+                if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&empty[s])) : "memory");
+#pragma unroll
+                for (int q = 0; q < RPW; ++q) f1[q] += f2[q];
+                const float sum = warp_rows_reduce_f<RPW>(f1, lane);
+                constexpr int span = 32 / RPW;
+                const int r = rbase + lane / span;
+                if (lane % span == 0 && r < rows) {
+                    float t = beta > 0 ? sum : (beta < 0 ? -sum : 0.f);
+                    if (alpha) t = (alpha > 0 ? (float)se[r] : -(float)se[r]) + t;
+                    y[e * rows + r] = (V)t;
+                }
+                continue;
+            }
             ff acc[RPW];
             if constexpr (std::is_same<V, float>::value) {
                 // Arnoldi step (FP32 basis vector in, FP32 vector out): each lane's partial sum of
@@ -449,6 +730,26 @@ __global__ void __launch_bounds__(kGvThreads, 2)
                 if (alpha) t = K::add(alpha > 0 ? K::load(se[r]) : K::neg(K::load(se[r])), t);
                 y[e * rows + r] = K::store(t);
             }
+        }
+    }
+    if constexpr (std::is_same<V, float>::value) {
+        if (fz.as) {
+            // first Gram-Schmidt pass on this block's output rows: W_i . w (i <= j) and w . w
+            // (slot j + 1 is w itself); the rows are the block's elements, rows / 4 packs each
+            asm volatile("bar.sync 1, %0;" ::"r"(32 * kGvWarps) : "memory");  // the block's rows of w are stored
+            const int q4 = rows >> 2;
+            const int64_t nel = (E - blockIdx.x + gridDim.x - 1) / gridDim.x;
+            const int64_t np = fz.n >> 2;
+            const unsigned G = gridDim.x, B = blockIdx.x;
+            arn_block_dots<true>(reinterpret_cast<const float4*>(fz.Vb), np,
+                                 reinterpret_cast<const float4*>(fz.Vb + (int64_t)(fz.j + 1) * fz.n), fz.j + 2,
+                                 nel * q4,
+                                 [=](int64_t t) {
+                                     const int64_t k = t / q4;
+                                     return (int64_t)(B + k * G) * q4 + (t - k * q4);
+                                 },
+                                 fz.P, G);
+            if (arn_last_block<true>(&fz.as->ticket[0])) arn_first_pass_finish<true>(fz.P, G, fz.j, fz.as);
         }
     }
 }
@@ -618,185 +919,6 @@ __global__ void k_givens(double* __restrict__ H, int ldh, double* __restrict__ c
     if (st->res <= st->tol || hnext == 0.0) st->done = 1;
 }
 
-// ------------------------------------------------------------------------------------------------
-// Arnoldi step for the FP32 basis in four launches (after the matvec of step j):
-//   k_arn_dots   h1 = V^T w and ||w||^2                per-block partials, last block reduces and
-//                decides whether a second Gram-Schmidt pass is needed: only if the first pass
-//                cancelled more than half of ||w||^2 (||w||^2 - ||h1||^2 < ||w||^2 / 2, the usual
-//                criterion of classical Gram-Schmidt with selective reorthogonalisation)
-//   k_arn_axdots w -= V h1; then either h2 = V^T w (second pass) or ||w||^2 on the block's slice
-//   k_arn_axnorm second pass only: w -= V h2 and ||w||^2; the last block (or block 0 without a
-//                second pass) writes the Hessenberg column h1 + h2, ||w|| and applies the Givens
-//                rotations (as k_givens)
-//   k_arn_scale  v_{j+1} = w / ||w||
-// The block that finishes last (a ticket counter behind a __threadfence of every block's partial
-// writes) reduces the blocks' partials in a fixed order, so the results are deterministic; no
-// block ever waits for another.  Sums accumulate in float-float, block results in FP64.
-// ------------------------------------------------------------------------------------------------
-constexpr int kArnThreads = 256;
-constexpr int kArnMaxV = 32;  // restart length + 1 supported by this path
-
-struct ArnState {
-    unsigned ticket[4];
-    int reorth;  // second Gram-Schmidt pass in this step
-    double h1[kArnMaxV], h2[kArnMaxV], nrm;
-};
-
-// true in exactly one block: the last to finish its partial writes (all of which are then visible)
-__device__ bool arn_last_block(unsigned* ticket) {
-    __shared__ bool last;
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) last = atomicAdd(ticket, 1u) == gridDim.x - 1;
-    __syncthreads();
-    if (last) __threadfence();
-    return last;
-}
-
-// out[i] = sum_b P[i * nb + b] (i < nv), one warp per vector, fixed order; ticket reset to 0
-__device__ void arn_finish(const double* P, unsigned nb, int nv, double* out, unsigned* ticket) {
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int i = warp; i < nv; i += kArnThreads / 32) {
-        double t = 0.0;
-        for (unsigned b = lane; b < nb; b += 32) t += ((volatile const double*)P)[(int64_t)i * nb + b];
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
-        if (lane == 0) out[i] = t;
-    }
-    if (threadIdx.x == 0) *ticket = 0u;
-}
-
-// P[i * nb + blk] = sum over packs [p0, p1) of V_i . w (i < nv), eight vectors per sweep
-__device__ void arn_block_dots(const float4* __restrict__ V4, int64_t np, const float4* __restrict__ w4, int nv,
-                               int64_t p0, int64_t p1, double* __restrict__ P, unsigned nb) {
-    __shared__ ff red[kArnThreads / 32][8];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int ib = 0; ib < nv; ib += 8) {
-        ff acc[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) acc[u] = ff{0.f, 0.f};
-        for (int64_t p = p0 + threadIdx.x; p < p1; p += kArnThreads) {
-            const float4 w = w4[p];
-#pragma unroll
-            for (int u = 0; u < 8; ++u)
-                if (ib + u < nv) {
-                    const float4 v = V4[(int64_t)(ib + u) * np + p];
-                    KV<float>::fma_vv(acc[u], v.x, w.x);
-                    KV<float>::fma_vv(acc[u], v.y, w.y);
-                    KV<float>::fma_vv(acc[u], v.z, w.z);
-                    KV<float>::fma_vv(acc[u], v.w, w.w);
-                }
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const ff sum = ff_warp_sum(ff_norm(acc[u].h, acc[u].l));
-            if (lane == 0) red[warp][u] = sum;
-        }
-        __syncthreads();
-        if (threadIdx.x < 8 && ib + (int)threadIdx.x < nv) {
-            ff t{0.f, 0.f};
-            for (int wp = 0; wp < kArnThreads / 32; ++wp) t = ff_add(t, red[wp][threadIdx.x]);
-            P[(int64_t)(ib + threadIdx.x) * nb + blockIdx.x] = ff_to_double(t);
-        }
-        __syncthreads();
-    }
-}
-
-// w -= sum_i c[i] V_i on packs [p0, p1)
-__device__ void arn_axpy(const float4* __restrict__ V4, int64_t np, float4* __restrict__ w4, int nv,
-                         const double* c, int64_t p0, int64_t p1) {
-    __shared__ ff cf[kArnMaxV];
-    if (threadIdx.x < nv) cf[threadIdx.x] = KV<float>::coef(-c[threadIdx.x]);
-    __syncthreads();
-    for (int64_t p = p0 + threadIdx.x; p < p1; p += kArnThreads) {
-        const float4 w = w4[p];
-        ff a0 = KV<float>::load(w.x), a1 = KV<float>::load(w.y), a2 = KV<float>::load(w.z), a3 = KV<float>::load(w.w);
-#pragma unroll 4
-        for (int i = 0; i < nv; ++i) {
-            const float4 v = V4[(int64_t)i * np + p];
-            KV<float>::fma_cv(a0, cf[i], v.x);
-            KV<float>::fma_cv(a1, cf[i], v.y);
-            KV<float>::fma_cv(a2, cf[i], v.z);
-            KV<float>::fma_cv(a3, cf[i], v.w);
-        }
-        w4[p] = make_float4(KV<float>::store(a0), KV<float>::store(a1), KV<float>::store(a2), KV<float>::store(a3));
-    }
-}
-
-__device__ __forceinline__ void arn_slice(int64_t n, int64_t& np, int64_t& p0, int64_t& p1) {
-    np = n / 4;
-    p0 = np * blockIdx.x / gridDim.x;
-    p1 = np * (blockIdx.x + 1) / gridDim.x;
-}
-
-__global__ void __launch_bounds__(kArnThreads) k_arn_dots(const float* __restrict__ Vb, int64_t n, int j,
-                                                          double* __restrict__ P, ArnState* __restrict__ as,
-                                                          const GmState* __restrict__ st) {
-    if (st->done) return;
-    int64_t np, p0, p1;
-    arn_slice(n, np, p0, p1);
-    const int nv = j + 1;
-    // vectors 0 .. nv-1 of the basis and w itself (stored as vector nv): h1 and ||w||^2
-    arn_block_dots(reinterpret_cast<const float4*>(Vb), np, reinterpret_cast<const float4*>(Vb + (int64_t)nv * n),
-                   nv + 1, p0, p1, P, gridDim.x);
-    if (!arn_last_block(&as->ticket[0])) return;
-    arn_finish(P, gridDim.x, nv + 1, as->h1, &as->ticket[0]);
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        const double w2 = as->h1[nv];
-        double s = 0.0;
-        for (int i = 0; i < nv; ++i) s += as->h1[i] * as->h1[i];
-        as->reorth = (w2 - s < 0.5 * w2) ? 1 : 0;
-        for (int i = 0; i < nv; ++i) as->h2[i] = 0.0;
-    }
-}
-
-// partial ||w||^2 of the block's slice into P[blockIdx.x]
-__device__ void arn_block_norm(const float4* __restrict__ w4, int64_t p0, int64_t p1, double* __restrict__ P) {
-    __shared__ ff red[kArnThreads / 32];
-    ff acc{0.f, 0.f};
-    for (int64_t p = p0 + threadIdx.x; p < p1; p += kArnThreads) {
-        const float4 w = w4[p];
-        KV<float>::fma_vv(acc, w.x, w.x);
-        KV<float>::fma_vv(acc, w.y, w.y);
-        KV<float>::fma_vv(acc, w.z, w.z);
-        KV<float>::fma_vv(acc, w.w, w.w);
-    }
-    const ff sum = ff_warp_sum(ff_norm(acc.h, acc.l));
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = sum;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        ff t{0.f, 0.f};
-        for (int wp = 0; wp < kArnThreads / 32; ++wp) t = ff_add(t, red[wp]);
-        P[blockIdx.x] = ff_to_double(t);
-    }
-}
-
-// Hessenberg column j from h1 + h2 and ||w||, then the Givens rotations (one thread)
-__device__ void arn_column(const ArnState* as, int j, double nrm, double* H, int ldh, double* cs, double* sn,
-                           double* gv, GmState* st) {
-    const int nv = j + 1;
-    double* h = H + (int64_t)j * ldh;
-    for (int i = 0; i < nv; ++i) h[i] = ((volatile const double*)as->h1)[i] + ((volatile const double*)as->h2)[i];
-    h[j + 1] = nrm;
-    for (int i = 0; i < j; ++i) {
-        const double t = cs[i] * h[i] + sn[i] * h[i + 1];
-        h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];
-        h[i] = t;
-    }
-    const double d = hypot(h[j], h[j + 1]);
-    const double c = d > 0 ? h[j] / d : 1.0, s = d > 0 ? h[j + 1] / d : 0.0;
-    cs[j] = c;
-    sn[j] = s;
-    h[j] = d;
-    h[j + 1] = 0.0;
-    gv[j + 1] = -s * gv[j];
-    gv[j] = c * gv[j];
-    st->j_done = j + 1;
-    st->res = fabs(gv[j + 1]);
-    if (st->res <= st->tol || nrm == 0.0) st->done = 1;
-}
-
 __global__ void __launch_bounds__(kArnThreads) k_arn_axdots(float* __restrict__ Vb, int64_t n, int j,
                                                             double* __restrict__ P, ArnState* __restrict__ as,
                                                             const GmState* __restrict__ st) {
@@ -807,16 +929,16 @@ __global__ void __launch_bounds__(kArnThreads) k_arn_axdots(float* __restrict__ 
     const bool reorth = ((volatile const int*)&as->reorth)[0] != 0;
     const float4* V4 = reinterpret_cast<const float4*>(Vb);
     float4* w4 = reinterpret_cast<float4*>(Vb + (int64_t)nv * n);
-    arn_axpy(V4, np, w4, nv, as->h1, p0, p1);
+    arn_axpy(V4, np, w4, nv, as->h1, as->sc, p0, p1);
     __syncthreads();  // the block's slice of w is final (each thread reads only its own packs)
     if (reorth) {
-        arn_block_dots(V4, np, w4, nv, p0, p1, P, gridDim.x);
-        if (arn_last_block(&as->ticket[1])) arn_finish(P, gridDim.x, nv, as->h2, &as->ticket[1]);
+        arn_block_dots<false>(V4, np, w4, nv, p1 - p0, [=](int64_t t) { return p0 + t; }, P, gridDim.x);
+        if (arn_last_block(&as->ticket[1])) arn_finish(P, gridDim.x, nv, as->h2, &as->ticket[1], as->sc, nv);
     } else {
         arn_block_norm(w4, p0, p1, P);
         if (arn_last_block(&as->ticket[1])) {
             __shared__ double nrm2;
-            arn_finish(P, gridDim.x, 1, &nrm2, &as->ticket[1]);
+            arn_finish(P, gridDim.x, 1, &nrm2, &as->ticket[1], nullptr, 0);
             __syncthreads();
             if (threadIdx.x == 0) as->nrm = sqrt(nrm2);
         }
@@ -838,32 +960,17 @@ __global__ void __launch_bounds__(kArnThreads) k_arn_axnorm(float* __restrict__ 
     const int nv = j + 1;
     const float4* V4 = reinterpret_cast<const float4*>(Vb);
     float4* w4 = reinterpret_cast<float4*>(Vb + (int64_t)nv * n);
-    arn_axpy(V4, np, w4, nv, as->h2, p0, p1);
+    arn_axpy(V4, np, w4, nv, as->h2, as->sc, p0, p1);
     __syncthreads();
     arn_block_norm(w4, p0, p1, P);
     if (!arn_last_block(&as->ticket[2])) return;
     __shared__ double nrm2;
-    arn_finish(P, gridDim.x, 1, &nrm2, &as->ticket[2]);
+    arn_finish(P, gridDim.x, 1, &nrm2, &as->ticket[2], nullptr, 0);
     __syncthreads();
     if (threadIdx.x == 0) {
         const double nrm = sqrt(nrm2);
         as->nrm = nrm;
         arn_column(as, j, nrm, H, ldh, cs, sn, gv, st);
-    }
-}
-
-// v_{j+1} = w / ||w|| (runs even on the step that set the convergence flag, so the basis is whole)
-__global__ void __launch_bounds__(kArnThreads) k_arn_scale(float* __restrict__ Vb, int64_t n, int j,
-                                                           const ArnState* __restrict__ as) {
-    const double nrm = as->nrm;
-    if (!(nrm > 0.0)) return;
-    const ff inv = KV<float>::coef(1.0 / nrm);
-    float4* w4 = reinterpret_cast<float4*>(Vb + (int64_t)(j + 1) * n);
-    const int64_t np = n / 4;
-    for (int64_t p = blockIdx.x * (int64_t)kArnThreads + threadIdx.x; p < np; p += (int64_t)gridDim.x * kArnThreads) {
-        const float4 w = w4[p];
-        w4[p] = make_float4(KV<float>::store(ff_mul(ff{w.x, 0.f}, inv)), KV<float>::store(ff_mul(ff{w.y, 0.f}, inv)),
-                            KV<float>::store(ff_mul(ff{w.z, 0.f}, inv)), KV<float>::store(ff_mul(ff{w.w, 0.f}, inv)));
     }
 }
 
@@ -879,16 +986,17 @@ __global__ void k_solve_upper(const double* __restrict__ H, int ldh, const doubl
     }
 }
 
-// x += sum_{i < j_done} y_i V_i (x of type X, basis of type V, one accumulator type)
+// x += sum_{i < j_done} y_i s_i W_i (x of type X, basis of type V, one accumulator type; sc NULL:
+// s_i = 1)
 template <typename V, typename X>
 __global__ void __launch_bounds__(kThreads) k_update_x(const V* __restrict__ Vb, int64_t n,
-                                                       const double* __restrict__ y, X* __restrict__ x,
-                                                       const GmState* __restrict__ st) {
+                                                       const double* __restrict__ y, const double* __restrict__ sc,
+                                                       X* __restrict__ x, const GmState* __restrict__ st) {
     using Acc = typename KV<X>::acc;
     static_assert(std::is_same<Acc, typename KV<V>::acc>::value, "one accumulator type");
     __shared__ Acc ys[kMaxRestart + 1];
     const int nj = st->j_done;
-    for (int i = threadIdx.x; i < nj; i += blockDim.x) ys[i] = KV<X>::coef(y[i]);
+    for (int i = threadIdx.x; i < nj; i += blockDim.x) ys[i] = KV<X>::coef(sc ? y[i] * sc[i] : y[i]);
     __syncthreads();
     for (int64_t k = blockIdx.x * (int64_t)kThreads + threadIdx.x; k < n; k += (int64_t)gridDim.x * kThreads) {
         Acc s = KV<X>::load(x[k]);
@@ -898,7 +1006,8 @@ __global__ void __launch_bounds__(kThreads) k_update_x(const V* __restrict__ Vb,
     }
 }
 
-__global__ void k_cycle_start(GmState* st, double* gv, int m, const double* beta) {
+__global__ void k_cycle_start(GmState* st, double* gv, int m, const double* beta, double* sc0) {
+    if (sc0) *sc0 = 1.0;
     st->done = 0;
     st->j_done = 0;
     st->beta = *beta;
@@ -907,51 +1016,85 @@ __global__ void k_cycle_start(GmState* st, double* gv, int m, const double* beta
     for (int i = 1; i <= m; ++i) gv[i] = 0.0;
 }
 
+template <typename V, int RPW, typename AT>
+cudaError_t launch_stream(elrt_ctx* ctx, unsigned grid, size_t smem, int nx, int nz, int rows, const AT* Aop,
+                          const V* x, const double* g, const V* xself, int alpha, int beta, V* y, const GmState* st,
+                          const ArnFuse& fz) {
+    const Tab& t = ctx->tab;
+    cudaError_t ce = cudaFuncSetAttribute(k_gemv_stream<V, RPW, AT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (ce != cudaSuccess) return ce;
+    k_gemv_stream<V, RPW, AT><<<grid, kGvThreads, smem, ctx->stream>>>(nx, nz, t.nin, t.nface, rows, Aop, x, g, xself,
+                                                                     alpha, beta, y, st, ctx->d_flags + kGemvFlag, fz);
+    return cudaGetLastError();
+}
+
+// the streaming kernel serves operators of element size es at this address
+bool gemv_streams(const Tab& t, const void* Aop, int es) {
+    return ((uintptr_t)Aop & 15) == 0 && (t.nin * es) % 16 == 0 && t.nin * es * 8 <= kGvStageBytes;
+}
+
+// A: float or double (operators as given), or __half (the FP16 copy, FP32 vectors only).  fz: fused
+// first Gram-Schmidt pass (streaming kernel, FP32 vectors; the caller checks gemv_streams).
 template <typename A, typename V>
 elrt_status launch_gemv(elrt_ctx* ctx, int nx, int nz, int rows, const void* Aop, const V* x, const double* g,
-                        const V* xself, int alpha, int beta, V* y, const GmState* st) {
+                        const V* xself, int alpha, int beta, V* y, const GmState* st, ArnFuse fz = ArnFuse{}) {
     const Tab& t = ctx->tab;
     const int64_t E = (int64_t)nx * nz;
     if (E > 0x7fffffffLL) return ctx_fail(ctx, ELRT_EINVAL, "too many elements");
-    // algorithmic bytes: the operators once, the gathered inflow (x or g), the self term, the result
+    // algorithmic bytes: the operators once, the gathered inflow (x or g), the self term, the result,
+    // and for the fused pass the basis slots 0 .. j and w once more
     const double bytes = (double)E * ((double)rows * t.nin * sizeof(A) + (x ? (double)t.nin * sizeof(V) : 0.0) +
                                       (g ? 8.0 * t.nin : 0.0) + (xself && beta ? (double)rows * sizeof(V) : 0.0) +
-                                      (double)rows * sizeof(V));
+                                      (double)rows * sizeof(V)) +
+                         (fz.as ? (double)(fz.j + 2) * fz.n * sizeof(float) : 0.0);
     ProfScope ps(ctx, "gemv", 1, bytes, 2.0 * (double)E * rows * t.nin);
-    if constexpr (sizeof(A) == 4) {
-        // streaming kernel: 16-byte aligned row chunks (nin % 4 == 0 holds for every valid disc)
-        const int rpw = t.nin * 4 * 32 <= kGvStageBytes ? 4 : (t.nin * 4 * 16 <= kGvStageBytes ? 2 : 1);
-        if (((uintptr_t)Aop & 15) == 0 && t.nin % 4 == 0 && t.nin * 4 * 8 <= kGvStageBytes) {
+    if constexpr (sizeof(A) <= 4) {
+        // streaming kernel: 16-byte aligned row chunks (nin % 8 == 0 holds for every valid disc)
+        constexpr int es = (int)sizeof(A);
+        int rpw = t.nin * es * 32 <= kGvStageBytes ? 4 : (t.nin * es * 16 <= kGvStageBytes ? 2 : 1);
+        if (sizeof(A) == 2 && t.nin * es * 64 <= kGvStageBytes) rpw = 8;
+        if (gemv_streams(t, Aop, es)) {
             const size_t smem = (size_t)kGvStages * kGvStageBytes + 2 * (size_t)t.nin * sizeof(ff) +
                                 2 * (size_t)rows * sizeof(V);
             const unsigned grid = (unsigned)std::min<int64_t>(E, 2 * 152);
-            cudaError_t ce = cudaSuccess;
-            if (rpw == 4) {
-                ce = cudaFuncSetAttribute(k_gemv_stream<V, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-                if (ce == cudaSuccess)
-                    k_gemv_stream<V, 4><<<grid, kGvThreads, smem, ctx->stream>>>(nx, nz, t.nin, t.nface, rows,
-                                                                             (const float*)Aop, x, g, xself, alpha,
-                                                                             beta, y, st, ctx->d_flags + kGemvFlag);
-            } else if (rpw == 2) {
-                ce = cudaFuncSetAttribute(k_gemv_stream<V, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-                if (ce == cudaSuccess)
-                    k_gemv_stream<V, 2><<<grid, kGvThreads, smem, ctx->stream>>>(nx, nz, t.nin, t.nface, rows,
-                                                                             (const float*)Aop, x, g, xself, alpha,
-                                                                             beta, y, st, ctx->d_flags + kGemvFlag);
-            } else {
-                ce = cudaFuncSetAttribute(k_gemv_stream<V, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-                if (ce == cudaSuccess)
-                    k_gemv_stream<V, 1><<<grid, kGvThreads, smem, ctx->stream>>>(nx, nz, t.nin, t.nface, rows,
-                                                                             (const float*)Aop, x, g, xself, alpha,
-                                                                             beta, y, st, ctx->d_flags + kGemvFlag);
+            const A* Ap = (const A*)Aop;
+            cudaError_t ce;
+            if constexpr (sizeof(A) == 2) {
+                if (rpw == 8) {
+                    ce = launch_stream<V, 8, A>(ctx, grid, smem, nx, nz, rows, Ap, x, g, xself, alpha, beta, y, st, fz);
+                    return cuda_check(ctx, ce, "gemv launch");
+                }
             }
-            if (ce != cudaSuccess) return cuda_check(ctx, ce, "smem attribute");
-            return cuda_check(ctx, cudaGetLastError(), "gemv launch");
+            if (rpw == 4) ce = launch_stream<V, 4, A>(ctx, grid, smem, nx, nz, rows, Ap, x, g, xself, alpha, beta, y, st, fz);
+            else if (rpw == 2) ce = launch_stream<V, 2, A>(ctx, grid, smem, nx, nz, rows, Ap, x, g, xself, alpha, beta, y, st, fz);
+            else ce = launch_stream<V, 1, A>(ctx, grid, smem, nx, nz, rows, Ap, x, g, xself, alpha, beta, y, st, fz);
+            return cuda_check(ctx, ce, "gemv launch");
         }
+        if constexpr (sizeof(A) == 2) return ctx_fail(ctx, ELRT_EINVAL, "FP16 operator copy not 16-byte aligned");
     }
-    k_elem_gemv<A, V><<<(unsigned)E, kThreads, 0, ctx->stream>>>(nx, nz, t.nin, t.nface, rows, (const A*)Aop, x, g,
-                                                                 xself, alpha, beta, y, st);
-    return cuda_check(ctx, cudaGetLastError(), "gemv launch");
+    if (fz.as) return ctx_fail(ctx, ELRT_EINVAL, "fused Arnoldi pass needs the streaming matvec");
+    if constexpr (sizeof(A) != 2) {
+        k_elem_gemv<A, V><<<(unsigned)E, kThreads, 0, ctx->stream>>>(nx, nz, t.nin, t.nface, rows, (const A*)Aop, x,
+                                                                     g, xself, alpha, beta, y, st);
+        return cuda_check(ctx, cudaGetLastError(), "gemv launch");
+    }
+}
+
+// FP16 copy of an FP32 operator (n4 groups of four entries) for the Arnoldi-step matvecs; *err is
+// set when an entry is not finite or lies beyond +-6e4 (the FP16 range ends at 65504)
+__global__ void __launch_bounds__(kThreads) k_op_to_f16(const float4* __restrict__ src, uint2* __restrict__ dst,
+                                                        int64_t n4, int* __restrict__ err) {
+    bool bad = false;
+    for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n4; i += (int64_t)gridDim.x * kThreads) {
+        const float4 v = __ldcs(src + i);
+        bad |= !(fabsf(v.x) <= 6e4f) || !(fabsf(v.y) <= 6e4f) || !(fabsf(v.z) <= 6e4f) || !(fabsf(v.w) <= 6e4f);
+        const __half2 a = __floats2half2_rn(v.x, v.y), b = __floats2half2_rn(v.z, v.w);
+        uint2 o;
+        o.x = *reinterpret_cast<const uint32_t*>(&a);
+        o.y = *reinterpret_cast<const uint32_t*>(&b);
+        __stcs(dst + i, o);
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(err, 1);
 }
 
 unsigned grid_for(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<int64_t>(4 * 152, (n + kThreads - 1) / kThreads)); }
@@ -992,8 +1135,8 @@ elrt_status gmres(elrt_ctx* ctx, int nx, int nz, const void* Aop, const double* 
     ArnState* arn = (ArnState*)(partial + (size_t)(m + 1) * nblk);
     double* scal = (double*)(arn + 1) + 8;  // [0] ||b||, [1] beta
     GmState* st = (GmState*)(scal + 64);
-    // four-launch Arnoldi step: FP32 basis and restarts up to kArnMaxV - 1
-    const bool arn4 = std::is_same<V, float>::value && m + 1 <= kArnMaxV;
+    // three-launch Arnoldi step: FP32 basis, restarts up to kArnMaxV - 1 and the streaming matvec
+    const bool arn4 = std::is_same<V, float>::value && m + 1 <= kArnMaxV && gemv_streams(t, Aop, (int)sizeof(A));
     cudaStream_t sm = ctx->stream;
     const unsigned gb = grid_for(n);
     // algorithmic bytes of a pass that touches nvec vectors of type T once each
@@ -1001,9 +1144,27 @@ elrt_status gmres(elrt_ctx* ctx, int nx, int nz, const void* Aop, const double* 
     GmState* hst = (GmState*)ctx->h_pinned;
     const int rows = t.nin;
 
-    s = cuda_check(ctx, cudaMemsetAsync(ctx->d_flags + kGemvFlag, 0, sizeof(int), sm), "clear flag");
+    s = cuda_check(ctx, cudaMemsetAsync(ctx->d_flags + kGemvFlag, 0, 2 * sizeof(int), sm), "clear flags");
     if (!s) s = cuda_check(ctx, cudaMemsetAsync(arn, 0, sizeof(ArnState), sm), "clear Arnoldi state");
     if (s) return s;
+    // FP16 copy of the operator for the Arnoldi steps (FP32 operators, unless switched off): the
+    // basis is built with it, while b and every restart residual use the operator itself, so the
+    // restarts refine the iterate to the solution of the FP32 system (GMRES as the inner solver of
+    // a mixed-precision iterative refinement)
+    bool use16 = false;
+    const __half* A16 = nullptr;
+    if constexpr (std::is_same<V, float>::value) {
+        const int64_t nop = (int64_t)nx * nz * rows * t.nin;
+        if (ctx->krylov_op == ELRT_KRYLOV_F16 && nop % 4 == 0 && ((uintptr_t)Aop & 15) == 0) {
+            s = ensure_ws(ctx, &ctx->gm16, &ctx->gm16_bytes, (size_t)nop * sizeof(__half));
+            if (s) return s;
+            A16 = (const __half*)ctx->gm16;
+            ProfScope ps(ctx, "gemv", 1, 6.0 * nop);
+            k_op_to_f16<<<4 * 152, kThreads, 0, sm>>>((const float4*)Aop, (uint2*)ctx->gm16, nop / 4,
+                                                      ctx->d_flags + kF16Flag);
+            use16 = true;
+        }
+    }
     // b = A g_bnd
     s = launch_gemv<A, X>(ctx, nx, nz, rows, Aop, nullptr, inflow, nullptr, 0, 1, b, nullptr);
     if (s) return s;
@@ -1016,10 +1177,15 @@ elrt_status gmres(elrt_ctx* ctx, int nx, int nz, const void* Aop, const double* 
         ProfScope ps(ctx, "krylov", 1, 16.0 * n);
         k_d2ff<<<gb, kThreads, 0, sm>>>(xout, x, n);
     }
+    int* h16 = (int*)((unsigned char*)ctx->h_pinned + 2048 + 64);
     s = cuda_check(ctx, cudaMemcpyAsync(ctx->h_pinned, scal, sizeof(double), cudaMemcpyDeviceToHost, sm), "read ||b||");
+    if (!s && use16)
+        s = cuda_check(ctx, cudaMemcpyAsync(h16, ctx->d_flags + kF16Flag, sizeof(int), cudaMemcpyDeviceToHost, sm),
+                       "read range flag");
     if (!s) s = cuda_check(ctx, cudaStreamSynchronize(sm), "sync ||b||");
     if (s) return s;
     prof_flush(ctx);
+    if (use16 && *h16) use16 = false;  // an entry beyond the FP16 range: FP32 operator throughout
     const double bnorm = *(double*)ctx->h_pinned;
     if (!(bnorm > 0.0)) {
         s = cuda_check(ctx, cudaMemsetAsync(xout, 0, n * sizeof(double), sm), "zero x");
@@ -1036,7 +1202,7 @@ elrt_status gmres(elrt_ctx* ctx, int nx, int nz, const void* Aop, const double* 
     s = cuda_check(ctx, cudaMemcpyAsync(st, &init, sizeof(GmState), cudaMemcpyHostToDevice, sm), "state init");
     if (s) return s;
     int its = 0, cycles = 0;
-    double rel = 1.0;
+    double rel = 1.0, beta_prev = 0.0;
     bool converged = false;
     for (;;) {
         // r = b - (I - A_int) x, beta = ||r||
@@ -1056,32 +1222,41 @@ elrt_status gmres(elrt_ctx* ctx, int nx, int nz, const void* Aop, const double* 
             break;
         }
         if (its >= max_iter) break;
+        // a cycle on the FP16 copy that took the true residual down by less than 10%: the rounding
+        // of the copy limits the refinement, continue with the FP32 operator
+        if (use16 && cycles > 0 && beta > 0.9 * beta_prev) use16 = false;
+        beta_prev = beta;
         {
             ProfScope ps(ctx, "krylov", 1, kv(1, n, sizeof(X)) + kv(1, n, sizeof(V)));
             k_scale<X, V><<<gb, kThreads, 0, sm>>>(r, Vb, n, scal + 1, nullptr);
         }
-        { ProfScope ps(ctx, "krylov"); k_cycle_start<<<1, 1, 0, sm>>>(st, gv, m, scal + 1); }
+        { ProfScope ps(ctx, "krylov"); k_cycle_start<<<1, 1, 0, sm>>>(st, gv, m, scal + 1, arn4 ? arn->sc : nullptr); }
         const int mj = std::min(m, max_iter - its);
         for (int j = 0; j < mj; ++j) {
             V* vj = Vb + (size_t)j * n;
             V* w = Vb + (size_t)(j + 1) * n;
             double* hc = H + (size_t)j * (m + 1);
-            s = launch_gemv<A, V>(ctx, nx, nz, rows, Aop, vj, nullptr, vj, 1, -1, w, st);
-            if (s) return s;
             if constexpr (std::is_same<V, float>::value) {
-                if (arn4) {  // Gram-Schmidt twice, normalisation and rotation in four launches
+                if (arn4) {  // matvec with the first Gram-Schmidt pass, then two launches
+                    const ArnFuse fz{arn, partial, Vb, n, j};
+                    if (use16) s = launch_gemv<__half, V>(ctx, nx, nz, rows, A16, vj, nullptr, vj, 1, -1, w, st, fz);
+                    else s = launch_gemv<A, V>(ctx, nx, nz, rows, Aop, vj, nullptr, vj, 1, -1, w, st, fz);
+                    if (s) return s;
                     const double vb = 4.0 * n;
                     // (bytes counted as if the second pass ran: the bound on what these launches move)
-                    { ProfScope ps(ctx, "krylov", 1, (j + 2) * vb); k_arn_dots<<<nblk, kArnThreads, 0, sm>>>(Vb, n, j, partial, arn, st); }
                     { ProfScope ps(ctx, "krylov", 1, (2 * j + 5) * vb); k_arn_axdots<<<nblk, kArnThreads, 0, sm>>>(Vb, n, j, partial, arn, st); }
                     {
                         ProfScope ps(ctx, "krylov", 1, (j + 3) * vb);
                         k_arn_axnorm<<<nblk, kArnThreads, 0, sm>>>(Vb, n, j, partial, arn, H, m + 1, cs, sn, gv, st);
                     }
-                    { ProfScope ps(ctx, "krylov", 1, 2 * vb); k_arn_scale<<<gb, kArnThreads, 0, sm>>>(Vb, n, j, arn); }
                     continue;
                 }
+                if (use16) s = launch_gemv<__half, V>(ctx, nx, nz, rows, A16, vj, nullptr, vj, 1, -1, w, st);
+                else s = launch_gemv<A, V>(ctx, nx, nz, rows, Aop, vj, nullptr, vj, 1, -1, w, st);
+            } else {
+                s = launch_gemv<A, V>(ctx, nx, nz, rows, Aop, vj, nullptr, vj, 1, -1, w, st);
             }
+            if (s) return s;
             // classical Gram-Schmidt, twice
             const size_t sv = sizeof(V);
             { ProfScope ps(ctx, "krylov", 1, kv(j + 2, n, sv)); k_dots<V><<<dim3(nblk, j + 1), kThreads, 0, sm>>>(Vb, n, w, partial, st); }
@@ -1100,7 +1275,7 @@ elrt_status gmres(elrt_ctx* ctx, int nx, int nz, const void* Aop, const double* 
         { ProfScope ps(ctx, "krylov"); k_solve_upper<<<1, 1, 0, sm>>>(H, m + 1, gv, yv, st); }
         {
             ProfScope ps(ctx, "krylov", 1, kv(m, n, sizeof(V)) + kv(2, n, sizeof(X)));
-            k_update_x<V, X><<<gb, kThreads, 0, sm>>>(Vb, n, yv, x, st);
+            k_update_x<V, X><<<gb, kThreads, 0, sm>>>(Vb, n, yv, arn4 ? arn->sc : nullptr, x, st);
         }
         s = cuda_check(ctx, cudaGetLastError(), "gmres launches");
         if (s) return s;

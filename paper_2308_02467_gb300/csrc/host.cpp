@@ -372,6 +372,7 @@ elrt_status elrt_destroy(elrt_ctx* ctx) {
     for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
     if (ctx->ws) cudaFree(ctx->ws);
     if (ctx->gm) cudaFree(ctx->gm);
+    if (ctx->gm16) cudaFree(ctx->gm16);
     if (ctx->ops) cudaFree(ctx->ops);
     if (ctx->vec) cudaFree(ctx->vec);
     if (ctx->d_flags) cudaFree(ctx->d_flags);
@@ -383,6 +384,13 @@ elrt_status elrt_destroy(elrt_ctx* ctx) {
 elrt_status elrt_set_stream(elrt_ctx* ctx, void* stream) {
     if (!ctx) return ctx_fail(nullptr, ELRT_EINVAL, "elrt_set_stream: null context");
     ctx->stream = (cudaStream_t)stream;
+    return ELRT_OK;
+}
+
+elrt_status elrt_set_krylov_op(elrt_ctx* ctx, int32_t op) {
+    if (!ctx) return ctx_fail(nullptr, ELRT_EINVAL, "elrt_set_krylov_op: null context");
+    if (op != ELRT_KRYLOV_F32 && op != ELRT_KRYLOV_F16) return ctx_fail(ctx, ELRT_EINVAL, "elrt_set_krylov_op: op");
+    ctx->krylov_op = op;
     return ELRT_OK;
 }
 

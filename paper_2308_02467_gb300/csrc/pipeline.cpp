@@ -108,7 +108,10 @@ extern "C" elrt_status elrt_solve_batch(elrt_ctx* const* ctxs, int32_t n_ctx, co
     for (int w = 0; w < workers && !first; ++w) {
         if (cudaStreamCreateWithFlags(&streams[w], cudaStreamNonBlocking) != cudaSuccess)
             first = ctx_fail(nullptr, ELRT_ECUDA, "worker stream");
-        for (int k = 0; k < n_ctx && !first; ++k) first = elrt_create(&wctx[w][k], &ctxs[k]->disc, streams[w]);
+        for (int k = 0; k < n_ctx && !first; ++k) {
+            first = elrt_create(&wctx[w][k], &ctxs[k]->disc, streams[w]);
+            if (!first) wctx[w][k]->krylov_op = ctxs[k]->krylov_op;
+        }
     }
     auto per_field_ops = [&](int f) {
         const Tab& t = ctxs[field_ctx[f]]->tab;

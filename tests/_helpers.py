@@ -43,11 +43,13 @@ def ang_code(problem):
     return 0 if problem.angular == "fv0" else 1
 
 
-def gpu_pipeline(problem, mode, out_dtype, rtol=1e-12, refine_steps=2, restart=50, max_iter=20000):
+def gpu_pipeline(problem, mode, out_dtype, rtol=1e-12, refine_steps=2, restart=50, max_iter=20000, krylov_op=None):
     """Algorithm 1 through the C ABI: local operators, global GMRES, mean recovery."""
     import torch
     import paper_2308_02467_gb300 as E
     ctx = E.Context(problem.p, problem.n_angles, problem.hg_g, ang_code(problem))
+    if krylov_op is not None:
+        ctx.elrt_set_krylov_op(krylov_op)
     dev = "cuda"
     kappa = torch.tensor(lib_kappa(problem), device=dev, dtype=torch.float64).contiguous()
     omega = torch.tensor(problem.omega, device=dev, dtype=torch.float64)

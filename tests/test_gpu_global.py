@@ -136,13 +136,70 @@ def test_flux_conservation_albedo_one(lib):
     assert abs(net) < 1e-11 * tot
 
 
+@pytest.mark.parametrize("op", ["f16", "f32"])
 @pytest.mark.parametrize("restart", [8, 31, 32, 50])
-def test_fp32_gmres_paths_agree(lib, restart):
+def test_fp32_gmres_paths_agree(lib, restart, op):
     """FP32 operators: restarts up to 31 run the four-launch Arnoldi step (last-block reductions,
-    selective second Gram-Schmidt pass), larger ones the general Krylov kernels; both reach the
-    oracle's mean intensity to the float-float level."""
+    selective second Gram-Schmidt pass), larger ones the general Krylov kernels; with the Arnoldi
+    steps on the FP16 copy of in2out or on in2out itself, all reach the oracle's mean intensity to
+    the float-float level."""
     prob = H.small_cloud(8, 6, 4, 8)
     ref = hdg.solve_problem(prob, rtol=1e-13)
-    out = H.gpu_pipeline(prob, lib.LOCAL_FP32_IR, lib.F32, rtol=1e-12, restart=restart)
-    assert out["solve_stats"].converged == 1
+    out = H.gpu_pipeline(prob, lib.LOCAL_FP32_IR, lib.F32, rtol=1e-12, restart=restart,
+                         krylov_op=lib.KRYLOV_F16 if op == "f16" else lib.KRYLOV_F32)
+    assert out["solve_stats"].converged == 1 and out["solve_stats"].rel_residual <= 1e-12
     assert hdg.rel_l2(out["u_mean"], ref["u_mean"], ref["disc"]) < 1e-6
+
+
+def _solve_f32(lib, prob, A32, op, rtol, restart=12):
+    import torch
+    ctx = lib.Context(prob.p, prob.n_angles, prob.hg_g, 0)
+    ctx.elrt_set_krylov_op(op)
+    x = torch.empty(prob.nx * prob.nz * ctx.nin, dtype=torch.float64, device="cuda")
+    st = ctx.elrt_solve_global(prob.nx, prob.nz, torch.tensor(A32, device="cuda"),
+                               torch.tensor(prob.inflow, device="cuda"), x, rtol=rtol, restart=restart)
+    out = x.cpu().numpy()
+    ctx.close()
+    return out, st
+
+
+def test_f16_arnoldi_refines_to_fp32_system(lib):
+    """The FP16 copy only builds the Krylov basis: the restarts measure the residual with the FP32
+    operator, so the iterate solves the FP32 system to rtol, as with FP32 Arnoldi steps.  Both are
+    checked against a dense FP64 solve of the same (FP32-rounded) operator."""
+    prob = H.small_cloud(6, 5, 4, 8, random_inflow=True)
+    d, m, A_i2o, A_i2m = _oracle_ops(prob)
+    A32 = A_i2o.astype(np.float32)
+    ref = hdg.solve_problem(prob, dense=True, ops=(A32.astype(np.float64), A_i2m))
+    x16, st16 = _solve_f32(lib, prob, A32, lib.KRYLOV_F16, 1e-11)
+    x32, st32 = _solve_f32(lib, prob, A32, lib.KRYLOV_F32, 1e-11)
+    for x, st in ((x16, st16), (x32, st32)):
+        assert st.converged == 1 and st.rel_residual <= 1e-11
+        np.testing.assert_allclose(x, ref["x"], atol=1e-9 * np.abs(ref["x"]).max())
+
+
+def test_f16_copy_out_of_range_keeps_fp32(lib):
+    """An in2out entry beyond the FP16 range (here 1e5 on a column that only ever multiplies zero
+    boundary data) must not reach the Arnoldi steps: the FP16 copy would hold inf and inf * 0 = NaN.
+    The solve detects the range and stays on the FP32 operator, giving the FP32-path result."""
+    prob = H.small_cloud(4, 4, 3, 8, random_inflow=True)
+    d, m, A_i2o, _ = _oracle_ops(prob)
+    offs, _ = hdg.inflow_side_offsets(m, d)
+    s0 = offs[0] + m.boundary_face(0, 0) * d.n_face     # element 0, bottom face: domain boundary
+    inflow = prob.inflow.copy()
+    inflow[s0:s0 + d.n_face] = 0.0
+    prob = dataclasses.replace(prob, inflow=inflow)
+    A32 = A_i2o.astype(np.float32)
+    A32[0, 0, 0] = 1e5                                   # row 0, inflow column 0 (bottom face)
+    x16, st16 = _solve_f32(lib, prob, A32, lib.KRYLOV_F16, 1e-11)
+    x32, st32 = _solve_f32(lib, prob, A32, lib.KRYLOV_F32, 1e-11)
+    assert np.all(np.isfinite(x16)) and st16.converged == 1
+    np.testing.assert_allclose(x16, x32, atol=1e-9 * np.abs(x32).max())
+
+
+def test_krylov_op_rejects_unknown_value(lib):
+    ctx = lib.Context(3, 8, 0.0, 0)
+    with pytest.raises(lib.ElrtError) as ei:
+        ctx.elrt_set_krylov_op(7)
+    assert ei.value.status == 1
+    ctx.close()
