@@ -174,12 +174,15 @@ __device__ __forceinline__ void tri_solve(float (&a)[NBP], const float* __restri
 // written back to the matrix; the remaining nct tiles are column tiles over columns [c_begin,
 // c_end): y = L11^{-1} a (col_mode 0: factorisation and forward sweep) or y = U11^{-1} a
 // (col_mode 1: backward sweep), written back to the matrix (rows < jb) and, transposed, to the side
-// buffer Ut[e][column][0..63] (zero beyond jb).  Persistent: each block walks its items with two
-// staging buffers; the 16-byte cp.async copies of the next item (its 64-wide block and the factor
-// of the diagonal block) are in flight while the current item is computed and stored.
+// buffer Ut[e][column][0..63] (zero beyond jb).  Persistent, two blocks per SM (one staging buffer
+// each, 128 registers per thread): each block walks its items, copying an item's 64-wide block and
+// the factor of the diagonal block with 16-byte cp.async copies, solving and storing it; the two
+// blocks of an SM overlap one another's copies and stores.  (One block per SM with two staging
+// buffers, copies of the next item in flight, measured 23% slower: 8 warps per SM were too few to
+// hide the shared-memory latency of the substitutions.)
 constexpr int RS = NBP + 4;                        // staging row stride: 16-byte aligned rows
 constexpr int RC_BUF = PTILE * RS + (NBP + 1) * RS;  // floats per buffer: staging + factor + 1/diag
-constexpr int RC_SMEM = 2 * RC_BUF * (int)sizeof(float);
+constexpr int RC_SMEM = RC_BUF * (int)sizeof(float);  // one buffer: two CTAs per SM overlap each other's copies
 static_assert(PTILE * RS >= NBP * PTILE, "the staging area holds a 64 x PTILE column block");
 
 __device__ __forceinline__ void cp_async16(float* smem, const float* gmem, bool valid) {
@@ -189,12 +192,11 @@ __device__ __forceinline__ void cp_async16(float* smem, const float* gmem, bool 
                  : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
 
 // KIND: 0 = row tiles (factorisation), 1 = column tiles of the factorisation / forward sweep,
 // 2 = column tiles of the backward sweep; one unrolled solve per instantiation
 template <int KIND>
-__global__ void __launch_bounds__(256, 1) k_rowcol(int nu, int64_t ld, int64_t estride, float* __restrict__ Mall, int J,
+__global__ void __launch_bounds__(256, 2) k_rowcol(int nu, int64_t ld, int64_t estride, float* __restrict__ Mall, int J,
                                                    int jb, const float* __restrict__ Tinv, int npanels, int64_t E,
                                                    int r_begin, int r_end, int nrt, int c_begin, int c_end, int nct,
                                                    float* __restrict__ Ut) {
@@ -237,13 +239,11 @@ __global__ void __launch_bounds__(256, 1) k_rowcol(int nu, int64_t ld, int64_t e
             cp_async16(T + NBP * RS + 4 * t, rdg + 4 * t, true);
         }
     };
-    int b = 0;
-    if (blockIdx.x < W) load(blockIdx.x, 0);
-    cp_async_commit();
-    for (int64_t w = blockIdx.x; w < W; w += gridDim.x, b ^= 1) {
-        if (w + gridDim.x < W) load(w + gridDim.x, b ^ 1);
+    const int b = 0;
+    for (int64_t w = blockIdx.x; w < W; w += gridDim.x) {
+        load(w, b);
         cp_async_commit();
-        cp_async_wait1();  // this item's copies have landed (the next item's may still be in flight)
+        asm volatile("cp.async.wait_all;" ::: "memory");
         __syncthreads();
         float* S = sm + b * RC_BUF;
         const float* T = S + PTILE * RS;
@@ -290,7 +290,7 @@ __global__ void __launch_bounds__(256, 1) k_rowcol(int nu, int64_t ld, int64_t e
             for (int cc = warp; cc < nc; cc += 8)
                 for (int i = lane; i < NBP; i += 32) ut[(int64_t)(c0 + cc) * NBP + i] = S[cc * RS + i];
         }
-        __syncthreads();  // buffer b is refilled by the copies issued two items later
+        __syncthreads();  // the buffer is refilled by the next item's copies
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
 }
@@ -771,12 +771,12 @@ elrt_status rowcol(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, int64_t
     ProfScope ps(ctx, "lu_tc_rowcol", (nrt > 0) + (nct > 0), (double)E * bytes, (double)E * flops);
     const int np = panels_of(ctx->tab.nu), nu = ctx->tab.nu;
     if (nrt > 0) {  // items: (element, row tile)
-        const unsigned grid = (unsigned)std::min<int64_t>(E * nrt, 152);
+        const unsigned grid = (unsigned)std::min<int64_t>(E * nrt, 2 * 152);
         k_rowcol<0><<<grid, 256, RC_SMEM, ctx->stream>>>(nu, ld, estride, M, J, jb, Tinv, np, E, r_begin, r_end, nrt,
                                                          c_begin, c_end, 0, Ut);
     }
     if (nct > 0) {  // items: (element, column tile)
-        const unsigned grid = (unsigned)std::min<int64_t>(E * nct, 152);
+        const unsigned grid = (unsigned)std::min<int64_t>(E * nct, 2 * 152);
         if (col_mode == 0)
             k_rowcol<1><<<grid, 256, RC_SMEM, ctx->stream>>>(nu, ld, estride, M, J, jb, Tinv, np, E, r_begin, r_end, 0,
                                                              c_begin, c_end, nct, Ut);
