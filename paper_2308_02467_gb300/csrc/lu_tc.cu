@@ -33,7 +33,8 @@
 namespace {
 
 constexpr int NBP = 64;     // panel width (= K of the trailing update)
-constexpr int UBN = 32;     // trailing-update tile width (N of the MMAs)
+constexpr int UBN = 64;     // trailing-update tile width (N of the MMAs)
+constexpr int UCB = UBN / 32;  // 32-column (128-byte) boxes of a C tile
 
 __device__ __forceinline__ float tf32_hi(float a) { return __uint_as_float(__float_as_uint(a) & 0xFFFFE000u); }
 
@@ -343,15 +344,16 @@ __device__ __forceinline__ void mma_tf32_ta(uint32_t d_tmem, uint32_t a_tmem, ui
 // launch, the strips of one element consecutively (their U12^T tiles are shared through L2).  The
 // L21 strip of an item (columns J .. J+63 of its 128 rows, FP32, straight from the matrix) lives
 // in tensor memory as TF32 high and low parts, double-buffered, so the next item's strip is
-// prepared while the current item's tiles run; shared memory holds only the ring of 32-column
-// tiles (FP32 U12^T tile, its low part, the C tile), six stages deep, which does not drain
-// between items.
+// prepared while the current item's tiles run; shared memory holds only the ring of 64-column
+// tiles (FP32 U12^T tile, its low part, the C tile as two 32-column boxes), three stages deep,
+// which does not drain between items.  (32-column tiles in a six-stage ring left the MMA thread
+// busy most of the time issuing N = 32 instructions; N = 64 halves the instructions per byte.)
 //   warp 0       TMA producer of the tiles;
 //   warp 1       TMEM allocation; one thread issues the 3xTF32 MMAs (hi*hi + hi*lo + lo*hi,
-//                M = 128, N = 32, A from tensor memory) into one of two TMEM accumulators;
+//                M = 128, N = 64, A from tensor memory) into one of two TMEM accumulators;
 //   warps 2-5    epilogue: accumulator (tcgen05.ld) and staged C tile -> C - L U, written back
 //                into the staged tile;
-//   warp 14      stores each finished tile with one TMA tensor store (the store map's extents
+//   warp 14      stores each finished tile with TMA tensor stores (the store map's extents
 //                are r_end rows and c_end columns, so rows and columns outside the update are
 //                clipped) and releases the stage once the store has read it;
 //   warps 6-9    strip preparation: each thread loads one row of the strip (columns at or beyond
@@ -360,12 +362,12 @@ __device__ __forceinline__ void mma_tf32_ta(uint32_t d_tmem, uint32_t a_tmem, ui
 // A stage is free again after the MMA commit and the store warp (count 2); a strip
 // buffer after the MMA commit of its item's last tile.  Every wait is bounded; on a timeout the
 // CTA records a code in *err, stops issuing work, lets its copies land and frees its TMEM.
-constexpr int kUStages = 6;
+constexpr int kUStages = 3;
 struct StripSmem {
     static constexpr int B_KB = UBN * 32 * 4;                 // one 32-column box of a U12^T tile
-    static constexpr int C_BOX = 128 * UBN * 4;               // the C tile (one box)
-    static constexpr int STAGE = 4 * B_KB + C_BOX;            // B {hi, lo} x 2 k-blocks + C tile
-    static constexpr int STAGE_TX = 2 * B_KB + C_BOX;         // FP32 U12^T tile + C tile per stage
+    static constexpr int C_BOX = 128 * 32 * 4;                // one 32-column box of the C tile
+    static constexpr int STAGE = 4 * B_KB + UCB * C_BOX;      // B {hi, lo} x 2 k-blocks + C tile
+    static constexpr int STAGE_TX = 2 * B_KB + UCB * C_BOX;   // FP32 U12^T tile + C tile per stage
     static constexpr int BYTES = kUStages * STAGE;
     static constexpr int TOTAL = BYTES + 1024 + 256;
 };
@@ -455,7 +457,8 @@ __global__ void __launch_bounds__(kStripThreads, 1)
                 const int n0 = c0 + t * UBN;
                 tc::mbar_expect_tx(&full[s], StripSmem::STAGE_TX);
                 for (int kb = 0; kb < 2; ++kb) tma_load_3d(&tU, &full[s], st + kb * StripSmem::B_KB, kb * 32, n0, (int)e);
-                tma_load_3d(&tM, &full[s], st + 4 * StripSmem::B_KB, n0, m0, (int)e);
+                for (int cb = 0; cb < UCB; ++cb)
+                    tma_load_3d(&tM, &full[s], st + 4 * StripSmem::B_KB + cb * StripSmem::C_BOX, n0 + 32 * cb, m0, (int)e);
                 ++issued_t;
             }
         }
@@ -568,7 +571,10 @@ __global__ void __launch_bounds__(kStripThreads, 1)
                         ok = false;
                         break;
                     }
-                    tma_store_3d(&tS, stage0 + s * StripSmem::STAGE + 4 * StripSmem::B_KB, c0 + t * UBN, m0, (int)e);
+                    for (int cb = 0; cb < UCB; ++cb)  // (a box wholly beyond c_end is not stored)
+                        if (c0 + t * UBN + 32 * cb < c_end)
+                            tma_store_3d(&tS, stage0 + s * StripSmem::STAGE + 4 * StripSmem::B_KB + cb * StripSmem::C_BOX,
+                                         c0 + t * UBN + 32 * cb, m0, (int)e);
                     bulk_commit();
                     bulk_wait_read0();  // the stage may be refilled once the store has read it
                     mbar_arrive(&empty[s]);
@@ -620,22 +626,27 @@ __global__ void __launch_bounds__(kStripThreads, 1)
                 }
                 tc::tc_fence_after();
                 const unsigned char* cst = stage0 + s * StripSmem::STAGE + 4 * StripSmem::B_KB;
-                float d[UBN];
 #pragma unroll
-                for (int c = 0; c < UBN; c += 16) {
-                    float v[16];
-                    tc::tmem_ld16(tmem + (uint32_t)(a * UBN) + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
+                for (int cb = 0; cb < UCB; ++cb) {
+                    float d[32];
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) d[c + j] = v[j];
-                }
-                // C tile in shared memory: rows m0 .. m0 + 127 of columns n0 .. n0 + 31, 128-byte
-                // rows with the 16-byte chunk index XOR-ed by (row % 8); C - L U goes back in place
-                unsigned char* crow = const_cast<unsigned char*>(cst) + row * 128;
+                    for (int c = 0; c < 32; c += 16) {
+                        float v[16];
+                        tc::tmem_ld16(tmem + (uint32_t)(a * UBN + 32 * cb) + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
 #pragma unroll
-                for (int ch = 0; ch < 8; ++ch) {
-                    float4* p = reinterpret_cast<float4*>(crow + ((ch ^ (row & 7)) << 4));
-                    const float4 cv = *p;
-                    *p = make_float4(cv.x - d[4 * ch], cv.y - d[4 * ch + 1], cv.z - d[4 * ch + 2], cv.w - d[4 * ch + 3]);
+                        for (int j = 0; j < 16; ++j) d[c + j] = v[j];
+                    }
+                    // C box cb in shared memory: rows m0 .. m0 + 127 of columns n0 + 32 cb .. + 31,
+                    // 128-byte rows with the 16-byte chunk index XOR-ed by (row % 8); C - L U goes
+                    // back in place
+                    unsigned char* crow = const_cast<unsigned char*>(cst) + cb * StripSmem::C_BOX + row * 128;
+#pragma unroll
+                    for (int ch = 0; ch < 8; ++ch) {
+                        float4* p = reinterpret_cast<float4*>(crow + ((ch ^ (row & 7)) << 4));
+                        const float4 cv = *p;
+                        *p = make_float4(cv.x - d[4 * ch], cv.y - d[4 * ch + 1], cv.z - d[4 * ch + 2],
+                                         cv.w - d[4 * ch + 3]);
+                    }
                 }
                 // written through the generic proxy, read next by the TMA store (async proxy)
                 tc::tc_fence_before();
