@@ -15,10 +15,12 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <type_traits>
 #include <vector>
 
 #include <cuda_fp16.h>
+#include <cudaTypedefs.h>
 
 #include "elrt_internal.h"
 #include "ff.h"
@@ -1016,6 +1018,320 @@ __global__ void k_cycle_start(GmState* st, double* gv, int m, const double* beta
     for (int i = 1; i <= m; ++i) gv[i] = 0.0;
 }
 
+// ------------------------------------------------------------------------------------------------
+// Arnoldi-step matvec on the tensor cores (FP16 copy of the operator): w = v - A v, v = s_j W_j.
+// The operators of all elements form one flat FP16 matrix [E rows][nin]; a persistent CTA walks its
+// 128-row tiles, which cross element boundaries (at most 5 elements per tile for nin >= 32).  Per
+// tile:
+//   A  the tile's rows, nin columns zero-padded to kTcKc boxes of 64 (TMA, 128-byte swizzle);
+//   B  N = 16 columns: for the k-th element the tile touches, its gathered inflow v_in scaled by
+//      2^12 and split into FP16 high part (column 2k) and FP16 remainder (column 2k + 1);
+//   D  = A B in FP32 (tensor memory, 128 lanes x 16 columns, double-buffered), so that row r of the
+//      k-th element reads (D[r][2k] + D[r][2k + 1]) 2^-12 = (A v_in)_r with v to ~2^-22 and the
+//      operator to its FP16 rounding.
+// Roles: warps 0-3 epilogue (TMEM lane quarter = warp, one thread per tile row: w = v - A v);
+// warps 4-11 build B (one column each); warp 12 TMA producer; warp 13 TMEM allocation and MMA
+// issue.  After the tiles, warps 0-7 run the fused first Gram-Schmidt pass over the CTA's rows (as
+// the streaming kernel).
+// Every wait is bounded; on a timeout the CTA records a code in *err and winds down.
+// ------------------------------------------------------------------------------------------------
+constexpr int kTcKc = 4;                       // K boxes of 64 columns: nin <= 256
+constexpr int kTcStages = 3;
+constexpr int kTcA = 128 * 64 * 2;             // one A box (16 KB)
+constexpr int kTcB = 16 * 64 * 2;              // one B box (2 KB)
+constexpr int kTcStage = kTcKc * (kTcA + kTcB);
+constexpr int kTcThreads = 448;
+constexpr int kTcSmem = kTcStages * kTcStage + 1024;
+constexpr float kTcScale = 4096.f;             // 2^12: keeps the FP16 remainder of |v| <= 1 normal
+
+__device__ __forceinline__ void tma_load_2d_hint(const CUtensorMap* map, uint64_t* bar, void* dst, int x, int y,
+                                                 uint64_t pol) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1, {%3, %4}], [%2], %5;" ::"r"(
+            tc::smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(tc::smem_u32(bar)), "r"(x), "r"(y), "l"(pol)
+        : "memory");
+}
+
+__device__ __forceinline__ uint32_t idesc_f16(int M, int N) {
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);  // FP32 D, FP16 A and B
+}
+
+// byte offset of element (n, c) of a K-major 128-byte-swizzled B tile of 16 rows (boxes of 64 columns)
+__device__ __forceinline__ uint32_t b_off(int n, int c) {
+    const int kc = c >> 6, byte = (c & 63) * 2;
+    return (uint32_t)(kc * kTcB + (n >> 3) * 1024 + (n & 7) * 128 + ((((byte >> 4) ^ (n & 7))) << 4) + (byte & 15));
+}
+
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_gemv_tc(const __grid_constant__ CUtensorMap tA, int nx, int nz, int nin, int nface,
+              const float* __restrict__ x, float* __restrict__ y, const GmState* __restrict__ st,
+              int* __restrict__ err, ArnFuse fz) {
+    if (st && st->done) return;
+    extern __shared__ __align__(1024) unsigned char tsm_raw[];
+    unsigned char* base = (unsigned char*)(((uintptr_t)tsm_raw + 1023) & ~(uintptr_t)1023);
+    __shared__ uint64_t full[kTcStages], bready[kTcStages], empty[kTcStages], acc_full[2], acc_empty[2];
+    __shared__ uint32_t tmem_slot;
+    __shared__ int abort_flag;
+    volatile int* abort = &abort_flag;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t E = (int64_t)nx * nz, NR = E * nin;
+    const int64_t T = (NR + 127) / 128;
+    const int nkc = (nin + 63) >> 6;
+    const float xsc = (float)((volatile const double*)fz.as->sc)[fz.j];
+    // zero the B tiles once: padding columns and unused rows stay zero
+    for (int i = threadIdx.x; i < kTcStages * kTcKc * kTcB / 16; i += kTcThreads) {
+        const int s = i / (kTcKc * kTcB / 16), o = i - s * (kTcKc * kTcB / 16);
+        reinterpret_cast<uint4*>(base + s * kTcStage + kTcKc * kTcA)[o] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < kTcStages; ++i) {
+            tc::mbar_init(&full[i], 1);
+            tc::mbar_init(&bready[i], 8);
+            tc::mbar_init(&empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
+            tc::mbar_init(&acc_full[i], 1);
+            tc::mbar_init(&acc_empty[i], 4);
+        }
+        *abort = 0;
+        tc::fence_barrier_init();
+    }
+    tc::fence_proxy_async();  // the zeroed B tiles are read by the tensor cores
+    if (warp == 13) {
+        tc::tmem_alloc(&tmem_slot, 32);
+        tc::tmem_relinquish();
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+    int issued = 0, committed = 0;
+    if (warp == 12) {  // TMA producer
+        if (lane == 0) {
+            const uint64_t pol = tc::l2_evict_first();  // read once; the Krylov vectors stay in L2
+            int g = 0;
+            for (int64_t t = blockIdx.x; t < T; t += gridDim.x, ++g) {
+                const int s = g % kTcStages;
+                if (!tc::mbar_wait(&empty[s], ((g / kTcStages) & 1) ^ 1, abort)) {
+                    if (err) atomicOr(err, 4);
+                    *abort = 1;
+                    break;
+                }
+                unsigned char* As = base + s * kTcStage;
+                tc::mbar_expect_tx(&full[s], (uint32_t)(nkc * kTcA));
+                for (int kc = 0; kc < nkc; ++kc) tma_load_2d_hint(&tA, &full[s], As + kc * kTcA, kc * 64, (int)(t * 128), pol);
+                ++issued;
+            }
+        }
+    } else if (warp == 13) {  // MMA issue
+        if (lane == 0) {
+            const uint32_t idesc = idesc_f16(128, 16);
+            int g = 0;
+            for (int64_t t = blockIdx.x; t < T; t += gridDim.x, ++g) {
+                const int s = g % kTcStages, a = g & 1;
+                if (!tc::mbar_wait(&acc_empty[a], ((g >> 1) & 1) ^ 1, abort) ||
+                    !tc::mbar_wait(&full[s], (g / kTcStages) & 1, abort) ||
+                    !tc::mbar_wait(&bready[s], (g / kTcStages) & 1, abort)) {
+                    if (err) atomicOr(err, 8);
+                    *abort = 1;
+                    break;
+                }
+                tc::tc_fence_after();
+                unsigned char* As = base + s * kTcStage;
+                unsigned char* Bs = As + kTcKc * kTcA;
+                uint32_t acc = 0;
+                for (int kc = 0; kc < nkc; ++kc) {
+                    const uint64_t ad = tc::sw128_desc(tc::smem_u32(As + kc * kTcA));
+                    const uint64_t bd = tc::sw128_desc(tc::smem_u32(Bs + kc * kTcB));
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {  // K = 16 per instruction
+                        tc::mma_bf16(tmem + (uint32_t)(a * 16), ad + 2 * k, bd + 2 * k, idesc, acc);
+                        acc = 1;
+                    }
+                }
+                tc::mma_commit(&empty[s]);
+                tc::mma_commit(&acc_full[a]);
+                ++committed;
+            }
+        }
+    } else if (warp >= 4) {  // B builders: gathered inflow of the tile's elements, split in FP16
+        // A tile touches at most 127 / nin + 2 <= 5 elements (nin >= 32); builder thread c owns
+        // column c of each (nin <= 256), whose face and source offset in the neighbour's outflow
+        // block are fixed.  The next tile's values are loaded while this one waits.
+        constexpr int kMaxE = 5;
+        const int c = threadIdx.x - 128;
+        const int cF = c < nin ? c / nface : -1;
+        const int csrc = ((cF + 2) & 3) * nface + (c - (c / nface) * nface);
+        // (loads are unconditional, from x[0] where there is no value, so that nothing waits on
+        // them here; the validity mask is applied when the tile is built)
+        auto gather = [&](int t, float (&pv)[kMaxE], unsigned& mask) {
+            const int ea = t * 128 / nin, eb = min((int)E - 1, (t * 128 + 127) / nin);
+            mask = 0u;
+#pragma unroll
+            for (int k = 0; k < kMaxE; ++k) {
+                const int e = ea + k;
+                const int iz = e / nx, ix = e - iz * nx;
+                const int jx = ix + (cF == 1) - (cF == 3), jz = iz + (cF == 2) - (cF == 0);
+                const bool ok = e <= eb && cF >= 0 && jx >= 0 && jx < nx && jz >= 0 && jz < nz;
+                mask |= (ok ? 1u : 0u) << k;
+                pv[k] = x[ok ? (jz * nx + jx) * nin + csrc : 0];
+            }
+        };
+        // write tile t's B into its stage; false on a timeout
+        auto build = [&](int t, int g, const float (&pv)[kMaxE], unsigned mask) -> bool {
+            const int s = g % kTcStages;
+            if (!__all_sync(0xffffffffu, tc::mbar_wait(&empty[s], ((g / kTcStages) & 1) ^ 1, abort) && !*abort)) {
+                if (err && lane == 0) atomicOr(err, 16);
+                *abort = 1;
+                return false;
+            }
+            unsigned char* Bs = base + s * kTcStage + kTcKc * kTcA;
+            const int nel = min((int)E - 1, (t * 128 + 127) / nin) - t * 128 / nin + 1;
+#pragma unroll
+            for (int k = 0; k < kMaxE; ++k)
+                if (k < nel && cF >= 0) {
+                    const float v = ((mask >> k) & 1u) ? pv[k] * xsc * kTcScale : 0.f;
+                    const __half hi = __float2half_rn(v);
+                    const __half lo = __float2half_rn(v - __half2float(hi));
+                    *reinterpret_cast<__half*>(Bs + b_off(2 * k, c)) = hi;
+                    *reinterpret_cast<__half*>(Bs + b_off(2 * k + 1, c)) = lo;
+                }
+            tc::fence_proxy_async();  // generic-proxy writes read next by the tensor cores
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&bready[s])) : "memory");
+            return true;
+        };
+        // two register sets: the loads of a tile are issued two tiles before it is built
+        float pa[kMaxE], pb[kMaxE];
+        unsigned ma = 0u, mb = 0u;
+        const int G = gridDim.x, T32 = (int)T;
+        if ((int)blockIdx.x < T32) gather(blockIdx.x, pa, ma);
+        if ((int)blockIdx.x + G < T32) gather(blockIdx.x + G, pb, mb);
+        int g = 0;
+        for (int t = blockIdx.x; t < T32; t += 2 * G, g += 2) {
+            if (!build(t, g, pa, ma)) break;
+            if (t + 2 * G < T32) gather(t + 2 * G, pa, ma);
+            if (t + G >= T32) break;
+            if (!build(t + G, g + 1, pb, mb)) break;
+            if (t + 3 * G < T32) gather(t + 3 * G, pb, mb);
+        }
+    } else {  // epilogue: row r of the tile
+        const int r = warp * 32 + lane;
+        int g = 0;
+        for (int64_t t = blockIdx.x; t < T; t += gridDim.x, ++g) {
+            const int a = g & 1;
+            const int64_t R = t * 128 + r;
+            const float xs = R < NR ? x[R] : 0.f;  // the self term, loaded before the wait
+            if (!__all_sync(0xffffffffu, tc::mbar_wait(&acc_full[a], (g >> 1) & 1, abort) && !*abort)) {
+                if (err && lane == 0) atomicOr(err, 32);
+                *abort = 1;
+                break;
+            }
+            tc::tc_fence_after();
+            float v[16];
+            tc::tmem_ld16(tmem + (uint32_t)(a * 16) + ((uint32_t)(warp * 32) << 16), v);
+            tc::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(&acc_empty[a])) : "memory");
+            if (R < NR) {
+                const int k = (int)R / nin - (int)(t * 128) / nin;
+                float ax = 0.f;
+#pragma unroll
+                for (int kk = 0; kk < 5; ++kk)
+                    if (kk == k) ax = v[2 * kk] + v[2 * kk + 1];
+                y[R] = xsc * xs - ax * (1.f / kTcScale);
+            }
+        }
+    }
+    tc::tc_fence_before();
+    __syncthreads();
+    tc::tc_fence_after();
+    if (warp == 12 && lane == 0) {  // after a timeout: let the copies in flight land before the CTA exits
+        for (int q = (issued > kTcStages ? issued - kTcStages : 0); q < issued; ++q) {
+            const long long t1 = clock64();
+            while (!tc::mbar_try_wait(&full[q % kTcStages], (q / kTcStages) & 1) && clock64() - t1 < tc::kWaitCycles / 4) {
+            }
+        }
+    }
+    if (warp == 13) {
+        if (lane == 0 && committed > 0) {  // never free TMEM under an MMA in flight
+            const int last = committed - 1;
+            const long long t0 = clock64();
+            while (!tc::mbar_try_wait(&acc_full[last & 1], (last >> 1) & 1) && clock64() - t0 < tc::kWaitCycles) {
+            }
+        }
+        __syncwarp();
+        tc::tc_fence_after();
+        tc::tmem_dealloc(tmem, 32);
+    }
+    if (warp < 8) {
+        // first Gram-Schmidt pass on this CTA's rows (its tiles, 32 packs each; the last tile of the
+        // matrix may be shorter): W_i . w (i <= j) and w . w
+        const int64_t np = fz.n >> 2;
+        const unsigned G = gridDim.x, B = blockIdx.x;
+        const int64_t ntb = (T - B + G - 1) / G;
+        const bool owns_last = (T - 1) % G == B;
+        const int64_t cnt = ntb * 32 - (owns_last ? (T * 32 - np) : 0);
+        arn_block_dots<true>(reinterpret_cast<const float4*>(fz.Vb), np,
+                             reinterpret_cast<const float4*>(fz.Vb + (int64_t)(fz.j + 1) * fz.n), fz.j + 2, cnt,
+                             [=](int64_t i) {
+                                 const int64_t k = i >> 5;
+                                 return (int64_t)(B + k * G) * 32 + (i & 31);
+                             },
+                             fz.P, G);
+        if (arn_last_block<true>(&fz.as->ticket[0])) arn_first_pass_finish<true>(fz.P, G, fz.j, fz.as);
+    }
+}
+
+// ---- host side of the tensor-core matvec
+PFN_cuTensorMapEncodeTiled_v12000 g_enc16 = nullptr;
+std::once_flag g_enc16_once;
+
+bool enc16_ready() {
+    std::call_once(g_enc16_once, [] {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_enc16 = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    });
+    return g_enc16 != nullptr;
+}
+
+// the tensor-core matvec serves this element size (tiles touch at most 5 elements, K fits kTcKc boxes)
+bool gemv_tc_ok(const Tab& t) { return t.nin >= 32 && t.nin <= 64 * kTcKc && t.nin % 8 == 0; }
+
+// the FP16 operator copy as a flat [rows][nin] matrix, boxes of 64 columns x 128 rows, 128-byte
+// swizzle (columns beyond nin and rows beyond the end read as zero)
+bool map_op16(CUtensorMap* m, const __half* A, int64_t rows, int nin) {
+    if (((uintptr_t)A & 15) || (nin * 2) % 16 || !enc16_ready()) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)nin, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)nin * 2};
+    cuuint32_t box[2] = {64, 128};
+    cuuint32_t es[2] = {1, 1};
+    return g_enc16(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, (void*)A, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+elrt_status launch_gemv_tc(elrt_ctx* ctx, const CUtensorMap& map, int nx, int nz, const float* x, float* y,
+                           const GmState* st, const ArnFuse& fz) {
+    const Tab& t = ctx->tab;
+    const int64_t E = (int64_t)nx * nz, T = (E * t.nin + 127) / 128;
+    // algorithmic bytes: the FP16 operator once, the gathered inflow and the self term, the result,
+    // and the fused pass's basis slots 0 .. j and w once more
+    const double bytes = (double)E * t.nin * ((double)t.nin * 2 + 12.0) + (double)(fz.j + 2) * fz.n * sizeof(float);
+    ProfScope ps(ctx, "gemv", 1, bytes, 2.0 * (double)E * t.nin * t.nin);
+    cudaError_t ce = cudaFuncSetAttribute(k_gemv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+    if (ce != cudaSuccess) return cuda_check(ctx, ce, "smem attribute");
+    const unsigned grid = (unsigned)std::min<int64_t>(T, 152);
+    k_gemv_tc<<<grid, kTcThreads, kTcSmem, ctx->stream>>>(map, nx, nz, t.nin, t.nface, x, y, st,
+                                                         ctx->d_flags + kGemvFlag, fz);
+    return cuda_check(ctx, cudaGetLastError(), "tensor-core matvec launch");
+}
+
 template <typename V, int RPW, typename AT>
 cudaError_t launch_stream(elrt_ctx* ctx, unsigned grid, size_t smem, int nx, int nz, int rows, const AT* Aop,
                           const V* x, const double* g, const V* xself, int alpha, int beta, V* y, const GmState* st,
@@ -1186,6 +1502,12 @@ elrt_status gmres(elrt_ctx* ctx, int nx, int nz, const void* Aop, const double* 
     if (s) return s;
     prof_flush(ctx);
     if (use16 && *h16) use16 = false;  // an entry beyond the FP16 range: FP32 operator throughout
+    // the Arnoldi-step matvec on the FP16 copy runs on the tensor cores where the element size allows
+    CUtensorMap map16;
+    bool tc16 = false;
+    if constexpr (std::is_same<V, float>::value)
+        tc16 = use16 && gemv_tc_ok(t) && (int64_t)nx * nz * rows < (1LL << 30) &&  // 32-bit row indices
+               map_op16(&map16, A16, (int64_t)nx * nz * rows, t.nin);
     const double bnorm = *(double*)ctx->h_pinned;
     if (!(bnorm > 0.0)) {
         s = cuda_check(ctx, cudaMemsetAsync(xout, 0, n * sizeof(double), sm), "zero x");
@@ -1239,7 +1561,8 @@ elrt_status gmres(elrt_ctx* ctx, int nx, int nz, const void* Aop, const double* 
             if constexpr (std::is_same<V, float>::value) {
                 if (arn4) {  // matvec with the first Gram-Schmidt pass, then two launches
                     const ArnFuse fz{arn, partial, Vb, n, j};
-                    if (use16) s = launch_gemv<__half, V>(ctx, nx, nz, rows, A16, vj, nullptr, vj, 1, -1, w, st, fz);
+                    if (use16 && tc16) s = launch_gemv_tc(ctx, map16, nx, nz, vj, w, st, fz);
+                    else if (use16) s = launch_gemv<__half, V>(ctx, nx, nz, rows, A16, vj, nullptr, vj, 1, -1, w, st, fz);
                     else s = launch_gemv<A, V>(ctx, nx, nz, rows, Aop, vj, nullptr, vj, 1, -1, w, st, fz);
                     if (s) return s;
                     const double vb = 4.0 * n;

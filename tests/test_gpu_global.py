@@ -197,6 +197,21 @@ def test_f16_copy_out_of_range_keeps_fp32(lib):
     np.testing.assert_allclose(x16, x32, atol=1e-9 * np.abs(x32).max())
 
 
+@pytest.mark.parametrize("p,n_angles,nx,nz", [(1, 4, 9, 7), (4, 8, 8, 6), (7, 16, 3, 3), (8, 16, 3, 2)])
+def test_f16_arnoldi_matvec_kernels(lib, p, n_angles, nx, nz):
+    """The FP16 Arnoldi-step matvec runs on the tensor cores for 32 <= n_in <= 256 (128-row tiles of
+    the flat operator crossing element boundaries: n_in = 80 gives tiles over 2-3 elements, n_in =
+    256 the widest K) and on the CUDA cores otherwise (n_in = 16 and 288); every case reaches the
+    dense FP64 solution of the same FP32 operator."""
+    prob = H.small_cloud(nx, nz, p, n_angles, random_inflow=True)
+    d, m, A_i2o, A_i2m = _oracle_ops(prob)
+    A32 = A_i2o.astype(np.float32)
+    ref = hdg.solve_problem(prob, dense=True, ops=(A32.astype(np.float64), A_i2m))
+    x16, st16 = _solve_f32(lib, prob, A32, lib.KRYLOV_F16, 1e-11)
+    assert st16.converged == 1 and st16.rel_residual <= 1e-11
+    np.testing.assert_allclose(x16, ref["x"], atol=1e-9 * np.abs(ref["x"]).max())
+
+
 def test_krylov_op_rejects_unknown_value(lib):
     ctx = lib.Context(3, 8, 0.0, 0)
     with pytest.raises(lib.ElrtError) as ei:
