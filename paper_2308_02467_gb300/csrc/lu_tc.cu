@@ -358,7 +358,8 @@ __device__ __forceinline__ void mma_tf32_ta(uint32_t d_tmem, uint32_t a_tmem, ui
 //                clipped) and releases the stage once the store has read it;
 //   warps 6-9    strip preparation: each thread loads one row of the strip (columns at or beyond
 //                jb are 0), splits it and writes it to its TMEM lane (tcgen05.st);
-//   warps 10-13  split the staged FP32 U12^T tile in place (high part) and write the low part.
+//   warps 10-13  write the low TF32 part of the staged FP32 U12^T tile (the tile itself serves as
+//                the high part: the MMA thread issues hi*hi and lo*hi on it at once, hi*lo after).
 // A stage is free again after the MMA commit and the store warp (count 2); a strip
 // buffer after the MMA commit of its item's last tile.  Every wait is bounded; on a timeout the
 // CTA records a code in *err, stops issuing work, lets its copies land and frees its TMEM.
@@ -378,15 +379,15 @@ constexpr int kStripThreads = 480;
 constexpr uint32_t kTmemCols = 512;
 __host__ __device__ constexpr uint32_t strip_col(int b, int lo) { return 128u + 128u * (uint32_t)b + 64u * (uint32_t)lo; }
 
-// In-place TF32 split of one 128-byte-swizzled box of `rows` rows x 32 FP32: hi stays, lo goes to
-// the same offset in `lo`.  Threads tid .. of nthr cooperate, 16 bytes each.
-__device__ __forceinline__ void split_box(unsigned char* box, unsigned char* lo, int rows, int tid, int nthr) {
+// Low parts of one 128-byte-swizzled box of `rows` rows x 32 FP32: lo = v - tf32(v) at the same
+// offset in `lo`.  The box itself stays FP32: kind::tf32 MMAs read the high 19 bits of each FP32
+// operand and ignore the rest (checked: FP32 and pre-truncated operands give bit-identical
+// factorisations), so it serves as the high part unchanged.  Threads tid .. of nthr, 16 bytes each.
+__device__ __forceinline__ void split_lo(const unsigned char* box, unsigned char* lo, int rows, int tid, int nthr) {
     for (int q = tid; q < rows * 8; q += nthr) {
-        float4* hp = reinterpret_cast<float4*>(box + q * 16);
-        const float4 v = *hp;
-        const float4 h = make_float4(tf32_hi(v.x), tf32_hi(v.y), tf32_hi(v.z), tf32_hi(v.w));
-        *hp = h;
-        *reinterpret_cast<float4*>(lo + q * 16) = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+        const float4 v = *reinterpret_cast<const float4*>(box + q * 16);
+        *reinterpret_cast<float4*>(lo + q * 16) =
+            make_float4(v.x - tf32_hi(v.x), v.y - tf32_hi(v.y), v.z - tf32_hi(v.z), v.w - tf32_hi(v.w));
     }
 }
 
@@ -481,7 +482,7 @@ __global__ void __launch_bounds__(kStripThreads, 1)
             for (int t = 0; t < ntile; ++t, ++g) {
                 const int s = g % kUStages, a = g & 1;
                 if (!tc::mbar_wait(&acc_empty[a], ((g >> 1) & 1) ^ 1, abort) ||
-                    !tc::mbar_wait(&bready[s], (g / kUStages) & 1, abort)) {
+                    !tc::mbar_wait(&full[s], (g / kUStages) & 1, abort)) {
                     ok = false;
                     break;
                 }
@@ -489,17 +490,27 @@ __global__ void __launch_bounds__(kStripThreads, 1)
                 unsigned char* st = stage0 + s * StripSmem::STAGE;
                 const uint32_t d = tmem + (uint32_t)(a * UBN);
                 uint32_t acc = 0;
+                // hi*hi and lo*hi as soon as the FP32 U12^T tile has landed (it is its own high
+                // part), then hi*lo once the splitters have written the low part
                 for (int kb = 0; kb < 2; ++kb) {
                     const uint64_t bh = tc::sw128_desc(tc::smem_u32(st + kb * StripSmem::B_KB));
-                    const uint64_t bl = tc::sw128_desc(tc::smem_u32(st + (2 + kb) * StripSmem::B_KB));
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {  // K = 8 per instruction
                         const uint32_t kc = (uint32_t)(kb * 32 + k * 8);
                         mma_tf32_ta(d, a_hi + kc, bh + 2 * k, idesc, acc);
                         acc = 1;
-                        mma_tf32_ta(d, a_hi + kc, bl + 2 * k, idesc, 1);
                         mma_tf32_ta(d, a_lo + kc, bh + 2 * k, idesc, 1);
                     }
+                }
+                if (!tc::mbar_wait(&bready[s], (g / kUStages) & 1, abort)) {
+                    ok = false;
+                    break;
+                }
+                tc::tc_fence_after();
+                for (int kb = 0; kb < 2; ++kb) {
+                    const uint64_t bl = tc::sw128_desc(tc::smem_u32(st + (2 + kb) * StripSmem::B_KB));
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) mma_tf32_ta(d, a_hi + (uint32_t)(kb * 32 + k * 8), bl + 2 * k, idesc, 1);
                 }
                 tc::mma_commit(&empty[s]);
                 tc::mma_commit(&acc_full[a]);
@@ -599,7 +610,7 @@ __global__ void __launch_bounds__(kStripThreads, 1)
                 }
                 unsigned char* st = stage0 + s * StripSmem::STAGE;
                 for (int kb = 0; kb < 2; ++kb)
-                    split_box(st + kb * StripSmem::B_KB, st + (2 + kb) * StripSmem::B_KB, UBN, tid, 128);
+                    split_lo(st + kb * StripSmem::B_KB, st + (2 + kb) * StripSmem::B_KB, UBN, tid, 128);
                 // generic-proxy writes, read next by the tensor cores (async proxy)
                 tc::fence_proxy_async();
                 __syncwarp();
