@@ -74,9 +74,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nx", type=int, default=64, help="elements per side of the slab (64: the benchmark workload)")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-path section")
-    ap.add_argument("--train-elements", type=int, default=32768)
-    ap.add_argument("--train-epochs", type=int, default=30)
-    ap.add_argument("--learned-tol", type=float, default=1e-3)
+    ap.add_argument("--train-elements", type=int, default=200000,
+                    help="element-network training set (the paper's 200k-element recipe; labels from the classical solver)")
+    ap.add_argument("--train-epochs", type=int, default=100)
+    ap.add_argument("--learned-tol", type=float, default=5e-4,
+                    help="energy-balance threshold above which an element falls back to the classical solve")
     return ap.parse_args()
 
 
@@ -473,7 +475,8 @@ def run_ours(args, rank, world, local_rank):
         lp = out["learned"]["pipeline"]
         f64 = out["learned"]["classical_fp64"]["ms_per_step"]
         out["learned_vs_classical"] = {"classical_ms": ms, "classical_mode": args.mode, "classical_fp64_ms": f64,
-                                       "learned_ms": lp["ms_per_step"],
+                                       "learned_ms": lp["ms_per_step"], "learned_elements_per_s": lp["elements_per_s"],
+                                       "learned_fallback_fraction": lp["fallback_fraction"],
                                        "speedup_vs_classical": ms / lp["ms_per_step"],
                                        "speedup_vs_fp64": f64 / lp["ms_per_step"], "rel_l2": lp["rel_l2_vs_classical"]}
     print(json.dumps(out), flush=True)

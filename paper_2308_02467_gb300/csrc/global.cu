@@ -151,16 +151,28 @@ __device__ bool arn_last_block(unsigned* ticket) {
 }
 
 // out[i] = s_i sum_b P[i * nb + b] (i < nv; s_i = sc[i] for i < nsc, else 1), one warp per
-// vector, fixed order; ticket reset to 0
+// vector, fixed order; ticket reset to 0.  The partials are read through L2 (other blocks wrote
+// them), all of a lane's loads issued before the first add, so they are in flight together.
 __device__ void arn_finish(const double* P, unsigned nb, int nv, double* out, unsigned* ticket, const double* sc,
                            int nsc) {
+    constexpr int kU = 20;  // loads per lane in flight: nb <= 640 in one round
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int i = warp; i < nv; i += kArnThreads / 32) {
+        const double* Pi = P + (int64_t)i * nb;
         double t = 0.0;
-        for (unsigned b = lane; b < nb; b += 32) t += ((volatile const double*)P)[(int64_t)i * nb + b];
+        for (unsigned b0 = 0; b0 < nb; b0 += 32u * kU) {
+            double v[kU];
+#pragma unroll
+            for (int u = 0; u < kU; ++u) {
+                const unsigned b = b0 + lane + 32u * u;
+                v[u] = b < nb ? __ldcg(Pi + b) : 0.0;
+            }
+#pragma unroll
+            for (int u = 0; u < kU; ++u) t += v[u];
+        }
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) t += __shfl_down_sync(0xffffffffu, t, off);
-        if (lane == 0) out[i] = i < nsc ? t * ((volatile const double*)sc)[i] : t;
+        if (lane == 0) out[i] = i < nsc ? t * __ldcg(sc + i) : t;
     }
     if (threadIdx.x == 0) *ticket = 0u;
 }
@@ -210,16 +222,19 @@ template <bool kNamed>
 __device__ void arn_first_pass_finish(const double* P, unsigned nb, int j, ArnState* as) {
     const int nv = j + 1;
     arn_finish(P, nb, nv + 1, as->h1, &as->ticket[0], as->sc, nv);
+    __threadfence_block();
     arn_sync<kNamed>();
-    if (threadIdx.x == 0) {
-        const double w2 = ((volatile const double*)as->h1)[nv];
-        double s = 0.0;
-        for (int i = 0; i < nv; ++i) {
-            const double h = ((volatile const double*)as->h1)[i];
-            s += h * h;
+    if (threadIdx.x < 32) {  // one warp: ||h1||^2 and the decision
+        const int lane = threadIdx.x;
+        const double h = lane < nv ? __ldcg(as->h1 + lane) : 0.0;
+        double s = h * h;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) s += __shfl_down_sync(0xffffffffu, s, off);
+        if (lane < nv) as->h2[lane] = 0.0;
+        if (lane == 0) {
+            const double w2 = __ldcg(as->h1 + nv);
+            as->reorth = (w2 - s < 0.5 * w2) ? 1 : 0;
         }
-        as->reorth = (w2 - s < 0.5 * w2) ? 1 : 0;
-        for (int i = 0; i < nv; ++i) as->h2[i] = 0.0;
     }
 }
 
@@ -271,31 +286,43 @@ __device__ void arn_block_norm(const float4* __restrict__ w4, int64_t p0, int64_
     }
 }
 
-// Hessenberg column j from h1 + h2 and ||w||, s_{j+1} = 1 / ||w||, then the Givens rotations
-// (one thread)
+// Hessenberg column j from h1 + h2 and ||w||, s_{j+1} = 1 / ||w||, then the Givens rotations.
+// Called by one warp: its lanes fetch the column and the rotations (through L2) into shared memory
+// together, lane 0 applies the rotations in order, the lanes write the column back.
 __device__ void arn_column(ArnState* as, int j, double nrm, double* H, int ldh, double* cs, double* sn, double* gv,
                            GmState* st) {
-    const int nv = j + 1;
+    __shared__ double hs[kArnMaxV + 1], css[kArnMaxV], sns[kArnMaxV];
+    const int lane = threadIdx.x & 31, nv = j + 1;
     double* h = H + (int64_t)j * ldh;
-    for (int i = 0; i < nv; ++i) h[i] = ((volatile const double*)as->h1)[i] + ((volatile const double*)as->h2)[i];
-    h[j + 1] = nrm;
-    as->sc[j + 1] = nrm > 0.0 ? 1.0 / nrm : 0.0;
-    for (int i = 0; i < j; ++i) {
-        const double t = cs[i] * h[i] + sn[i] * h[i + 1];
-        h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];
-        h[i] = t;
+    if (lane < nv) hs[lane] = __ldcg(as->h1 + lane) + __ldcg(as->h2 + lane);
+    if (lane < j) {
+        css[lane] = __ldcg(cs + lane);
+        sns[lane] = __ldcg(sn + lane);
     }
-    const double d = hypot(h[j], h[j + 1]);
-    const double c = d > 0 ? h[j] / d : 1.0, s = d > 0 ? h[j + 1] / d : 0.0;
-    cs[j] = c;
-    sn[j] = s;
-    h[j] = d;
-    h[j + 1] = 0.0;
-    gv[j + 1] = -s * gv[j];
-    gv[j] = c * gv[j];
-    st->j_done = j + 1;
-    st->res = fabs(gv[j + 1]);
-    if (st->res <= st->tol || nrm == 0.0) st->done = 1;
+    __syncwarp();
+    if (lane == 0) {
+        hs[nv] = nrm;
+        as->sc[j + 1] = nrm > 0.0 ? 1.0 / nrm : 0.0;
+        for (int i = 0; i < j; ++i) {
+            const double t = css[i] * hs[i] + sns[i] * hs[i + 1];
+            hs[i + 1] = -sns[i] * hs[i] + css[i] * hs[i + 1];
+            hs[i] = t;
+        }
+        const double d = hypot(hs[j], hs[j + 1]);
+        const double c = d > 0 ? hs[j] / d : 1.0, s = d > 0 ? hs[j + 1] / d : 0.0;
+        cs[j] = c;
+        sn[j] = s;
+        hs[j] = d;
+        hs[j + 1] = 0.0;
+        const double g = __ldcg(gv + j);
+        gv[j + 1] = -s * g;
+        gv[j] = c * g;
+        st->j_done = j + 1;
+        st->res = fabs(gv[j + 1]);
+        if (st->res <= st->tol || nrm == 0.0) st->done = 1;
+    }
+    __syncwarp();
+    if (lane <= nv) h[lane] = hs[lane];
 }
 
 // Fused first Gram-Schmidt pass of the streaming matvec (null: plain matvec)
@@ -954,7 +981,7 @@ __global__ void __launch_bounds__(kArnThreads) k_arn_axnorm(float* __restrict__ 
                                                             GmState* __restrict__ st) {
     if (st->done) return;
     if (!((volatile const int*)&as->reorth)[0]) {  // single pass: the column and the rotation only
-        if (blockIdx.x == 0 && threadIdx.x == 0) arn_column(as, j, ((volatile const double*)&as->nrm)[0], H, ldh, cs, sn, gv, st);
+        if (blockIdx.x == 0 && threadIdx.x < 32) arn_column(as, j, __ldcg(&as->nrm), H, ldh, cs, sn, gv, st);
         return;
     }
     int64_t np, p0, p1;
@@ -969,9 +996,9 @@ __global__ void __launch_bounds__(kArnThreads) k_arn_axnorm(float* __restrict__ 
     __shared__ double nrm2;
     arn_finish(P, gridDim.x, 1, &nrm2, &as->ticket[2], nullptr, 0);
     __syncthreads();
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
         const double nrm = sqrt(nrm2);
-        as->nrm = nrm;
+        if (threadIdx.x == 0) as->nrm = nrm;
         arn_column(as, j, nrm, H, ldh, cs, sn, gv, st);
     }
 }
