@@ -45,7 +45,7 @@ KERNEL_BOUND = {
 # partly fit in the 126 MB L2, so the matvec figure is a lower bound at 64 x 64.  Scaled to a
 # launch of the benchmark by elements / launches.
 DRAM_BYTES_PER_ELEMENT_STEP = {
-    "lu_tc_update": 6.107e7, "lu_tc_rowcol": 1.224e7, "lu_tc_diag": 3.262e5, "residual": 3.236e6,
+    "lu_tc_update": 6.109e7, "lu_tc_rowcol": 1.225e7, "lu_tc_diag": 3.264e5, "residual": 3.236e6,
     "assemble": 3.277e6, "restrict": 2.817e6,
 }
 
