@@ -197,7 +197,8 @@ struct GemmSmem {
     static constexpr int A_BYTES = BM * BK * 2;
     static constexpr int B_BYTES = BN * BK * 2;
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-    static constexpr int TOTAL = STAGES * STAGE_BYTES + 1024 /*alignment*/ + 256 /*barriers*/;
+    static constexpr int PARAM_BYTES = 2 * 2 * BN * 4;  // per-tile column parameters (scale and shift, or bias), two tiles
+    static constexpr int TOTAL = STAGES * STAGE_BYTES + 1024 /*alignment*/ + 256 /*barriers*/ + PARAM_BYTES;
     static constexpr int TMEM_COLS = 2 * BN;  // two accumulators: epilogue of one tile overlaps the next
 };
 
@@ -220,8 +221,9 @@ __device__ __forceinline__ void st_bf16x16(__nv_bfloat16* dst, const float (&v)[
 }
 
 // Epilogue of 16 consecutive columns n0c .. n0c+15 of row m (v holds the accumulator values).
+// sb: the tile's bias for these 16 columns, staged in shared memory (EPI_BIAS_ACT, EPI_LOSS)
 __device__ __forceinline__ void epilogue16(int mode, const EpiArgs& ep, int m, int n0c, int N, float (&v)[16],
-                                           float& lsum) {
+                                           float& lsum, const float* sb) {
     const bool full = n0c + 16 <= N;
     if (mode == EPI_F32) {
         if (full) {
@@ -235,7 +237,7 @@ ep.out_f[(size_t)m * ep.ld_out + n0c + j] = v[j];
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
             const int n = n0c + j;
-            z[j] = v[j] + (n < N ? ep.bias[n] : 0.f);
+            z[j] = v[j] + (n < N ? sb[j] : 0.f);
             v[j] = act_f(z[j], ep.act);
         }
         if (full) {
@@ -250,21 +252,6 @@ ep.out_f[(size_t)m * ep.ld_out + n0c + j] = v[j];
         if (ep.out_bf_t)
             _Pragma("unroll") for (int j = 0; j < 16; ++j) if (n0c + j < N)
 ep.out_bf_t[(size_t)(n0c + j) * ep.ld_t + m] = __float2bfloat16_rn(v[j]);
-    } else if (mode == EPI_OUTPUT) {
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            const int n = n0c + j < N ? n0c + j : N - 1;
-            v[j] = (v[j] + ep.bias[n]) * ep.col_std[n] + ep.col_mean[n];
-        }
-        // the split (a multiple of 16) never falls inside a 16-column group
-        float* dst = n0c < ep.split ? ep.out_f + (size_t)m * ep.ld_out + n0c
-                                    : ep.out_f2 + (size_t)m * ep.ld_out2 + (n0c - ep.split);
-        if (full) {
-            st_f32x16(dst, v);
-        } else {
-            _Pragma("unroll") for (int j = 0; j < 16; ++j) if (n0c + j < N)
-dst[j] = v[j];
-        }
     } else if (mode == EPI_LOSS) {
         float tg[16];
         if (full) {
@@ -284,7 +271,7 @@ dst[j] = v[j];
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
             if (n0c + j < N) {
-                const float y = v[j] + ep.bias[n0c + j];
+                const float y = v[j] + sb[j];
                 const float d = y - tg[j];
                 lsum += fabsf(d);
                 v[j] = d > 0.f ? ep.loss_scale : (d < 0.f ? -ep.loss_scale : 0.f);
@@ -334,6 +321,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     uint64_t* acc_empty = acc_full + 2;      // [2]
     uint32_t* tmem_slot = (uint32_t*)(acc_empty + 2);
     volatile int* abort = (volatile int*)(tmem_slot + 1);
+    float* prm = (float*)(base + S::STAGES * S::STAGE_BYTES + 256);  // [2 tiles][scale BN | shift BN]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nk = (K + BK - 1) / BK;
@@ -440,11 +428,56 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             tc_fence_after();
             const int m = m0 + q * 32 + lane;
             const uint32_t tb = tmem_base + (uint32_t)(a * BN) + ((uint32_t)(q * 32) << 16);
-            for (int c0 = 0; c0 < BN; c0 += 16) {
-                if (n0 + c0 >= N) break;
-                float v[16];
-                tmem_ld16(tb + (uint32_t)c0, v);
-                if (m < M) epilogue16(mode, ep, m, n0 + c0, N, v, lsum);
+            if (mode == EPI_OUTPUT) {
+                // the tile's column scale std and shift bias * std + mean, once per tile in shared
+                // memory (two buffers: a warp may start the next tile while others finish this one)
+                float* sc = prm + (t & 1) * 2 * BN;
+                for (int c = threadIdx.x - 64; c < BN; c += 128) {
+                    const int n = min(n0 + c, N - 1);
+                    const float sd = ep.col_std[n];
+                    sc[c] = sd;
+                    sc[BN + c] = ep.bias[n] * sd + ep.col_mean[n];
+                }
+                asm volatile("bar.sync 1, 128;" ::: "memory");  // the four epilogue warps
+                for (int c0 = 0; c0 < BN; c0 += 16) {
+                    if (n0 + c0 >= N) break;
+                    float v[16];
+                    tmem_ld16(tb + (uint32_t)c0, v);
+                    if (m < M) {
+#pragma unroll
+                        for (int j = 0; j < 16; j += 4) {
+                            const float4 s4 = *reinterpret_cast<const float4*>(sc + c0 + j);
+                            const float4 h4 = *reinterpret_cast<const float4*>(sc + BN + c0 + j);
+                            v[j] = fmaf(v[j], s4.x, h4.x);
+                            v[j + 1] = fmaf(v[j + 1], s4.y, h4.y);
+                            v[j + 2] = fmaf(v[j + 2], s4.z, h4.z);
+                            v[j + 3] = fmaf(v[j + 3], s4.w, h4.w);
+                        }
+                        const int n0c = n0 + c0;
+                        // the split (a multiple of 16) never falls inside a 16-column group
+                        float* dst = n0c < ep.split ? ep.out_f + (size_t)m * ep.ld_out + n0c
+                                                    : ep.out_f2 + (size_t)m * ep.ld_out2 + (n0c - ep.split);
+                        if (n0c + 16 <= N) {
+                            st_f32x16(dst, v);
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < 16; ++j)
+                                if (n0c + j < N) dst[j] = v[j];
+                        }
+                    }
+                }
+            } else {
+                float* sb = prm + (t & 1) * 2 * BN;
+                if (mode == EPI_BIAS_ACT || mode == EPI_LOSS) {  // the tile's bias, once per tile
+                    for (int c = threadIdx.x - 64; c < BN; c += 128) sb[c] = ep.bias[min(n0 + c, N - 1)];
+                    asm volatile("bar.sync 1, 128;" ::: "memory");
+                }
+                for (int c0 = 0; c0 < BN; c0 += 16) {
+                    if (n0 + c0 >= N) break;
+                    float v[16];
+                    tmem_ld16(tb + (uint32_t)c0, v);
+                    if (m < M) epilogue16(mode, ep, m, n0 + c0, N, v, lsum, sb + c0);
+                }
             }
             tc_fence_before();
             __syncwarp();
