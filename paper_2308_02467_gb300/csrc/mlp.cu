@@ -157,18 +157,32 @@ __global__ void k_batch_features(const float* __restrict__ F, int fpad, int nfea
     }
 }
 
-// standardised targets of batch rows from the labels in2out | in2sol
+// standardised targets of batch rows from the labels in2out | in2sol: blockIdx.y walks the batch rows
+// (the source row once per row, no division per element), blockIdx.x the columns, four at a time when
+// both label widths are multiples of 4 (V = 4: no group straddles the in2out | in2sol seam)
+template <int V>
 __global__ void k_batch_targets(const float* __restrict__ i2o, int64_t co, const float* __restrict__ i2m, int64_t cm,
                                 const float* __restrict__ mean, const float* __restrict__ stdv, int64_t n, int64_t b0,
                                 int B, uint64_t pa, uint64_t pb, float* __restrict__ T) {
     const int64_t C = co + cm;
-    const int64_t total = (int64_t)B * C;
-    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
-        const int b = (int)(k / C);
-        const int64_t c = k - (int64_t)b * C;
+    for (int b = blockIdx.y; b < B; b += gridDim.y) {
         const int64_t src = (int64_t)(((uint64_t)(b0 + b) * pa + pb) % (uint64_t)n);
-        const float v = c < co ? i2o[src * co + c] : i2m[src * cm + (c - co)];
-        T[k] = (v - mean[c]) / stdv[c];
+        const float* ro = i2o + src * co;
+        const float* rm = i2m + src * cm - co;
+        float* t = T + (int64_t)b * C;
+        for (int64_t c = V * (blockIdx.x * (int64_t)blockDim.x + threadIdx.x); c < C;
+             c += V * (int64_t)gridDim.x * blockDim.x) {
+            if constexpr (V == 4) {
+                const float4 v = __ldcs(reinterpret_cast<const float4*>(c < co ? ro + c : rm + c));
+                const float4 mu = *reinterpret_cast<const float4*>(mean + c);
+                const float4 sd = *reinterpret_cast<const float4*>(stdv + c);
+                *reinterpret_cast<float4*>(t + c) =
+                    make_float4((v.x - mu.x) / sd.x, (v.y - mu.y) / sd.y, (v.z - mu.z) / sd.z, (v.w - mu.w) / sd.w);
+            } else {
+                const float v = c < co ? __ldcs(ro + c) : __ldcs(rm + c);
+                t[c] = (v - mean[c]) / stdv[c];
+            }
+        }
     }
 }
 
@@ -198,6 +212,69 @@ __global__ void k_adam(float* __restrict__ p, const float* __restrict__ g, float
         m[k] = mk;
         v[k] = vk;
         p[k] -= lr * (mk / bc1) / (sqrtf(vk / bc2) + eps);
+    }
+}
+
+// Adam on a weight matrix W (rows x cols) fused with its BF16 copies W and W^T, through 64 x 32 tiles
+// (each element read and written once; the transposed copy leaves in 128-byte rows)
+__global__ void k_adam_weights(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                               float* __restrict__ v, int rows, int cols, float lr, float b1, float b2, float eps,
+                               float bc1, float bc2, bf16* __restrict__ Wb, bf16* __restrict__ Wt) {
+    __shared__ float tile[64][33];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 64;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+    for (int j = ty; j < 64; j += 8) {
+        const int r = r0 + j, c = c0 + tx;
+        float pk = 0.f;
+        if (r < rows && c < cols) {
+            const int64_t k = (int64_t)r * cols + c;
+            const float gk = __ldcs(g + k);
+            const float mk = b1 * m[k] + (1.f - b1) * gk;
+            const float vk = b2 * v[k] + (1.f - b2) * gk * gk;
+            m[k] = mk;
+            v[k] = vk;
+            pk = p[k] - lr * (mk / bc1) / (sqrtf(vk / bc2) + eps);
+            p[k] = pk;
+            Wb[k] = __float2bfloat16_rn(pk);
+        }
+        tile[j][tx] = pk;
+    }
+    __syncthreads();
+    const int r = r0 + 2 * tx;
+    for (int j = ty; j < 32; j += 8) {
+        const int c = c0 + j;
+        if (c >= cols || r >= rows) continue;
+        bf16* dst = Wt + (int64_t)c * rows + r;
+        if ((rows & 1) == 0) {  // r even, rows even: a 4-byte aligned pair
+            *reinterpret_cast<__nv_bfloat162*>(dst) = __floats2bfloat162_rn(tile[2 * tx][j], tile[2 * tx + 1][j]);
+        } else {
+            dst[0] = __float2bfloat16_rn(tile[2 * tx][j]);
+            if (r + 1 < rows) dst[1] = __float2bfloat16_rn(tile[2 * tx + 1][j]);
+        }
+    }
+}
+
+// dZ = (sum over K slices of the partial products) * act'(Z), as BF16 dZ [M][N] and dZ^T [N][M]
+__global__ void k_dact_reduce(const float* __restrict__ part, int S, size_t stride, int M, int N,
+                              const bf16* __restrict__ z, int act, bf16* __restrict__ out, bf16* __restrict__ out_t) {
+    __shared__ float tile[32][33];
+    const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+    for (int j = ty; j < 32; j += 8) {
+        const int r = r0 + j, c = c0 + tx;
+        float a = 0.f;
+        if (r < M && c < N) {
+            const size_t k = (size_t)r * N + c;
+            for (int sl = 0; sl < S; ++sl) a += __ldcs(part + sl * stride + k);
+            a *= tc::act_df(__bfloat162float(z[k]), act);
+            out[k] = __float2bfloat16_rn(a);
+        }
+        tile[j][tx] = a;
+    }
+    __syncthreads();
+    for (int j = ty; j < 32; j += 8) {
+        const int c = c0 + j, r = r0 + tx;
+        if (r < M && c < N) out_t[(size_t)c * M + r] = __float2bfloat16_rn(tile[tx][j]);
     }
 }
 
@@ -238,6 +315,8 @@ struct elrt_net {
     std::vector<bf16*> Z, H, Ht, dZ, dZt;
     bf16 *dY = nullptr, *dYt = nullptr;
     float* T = nullptr;
+    int dh_split = 1;       // K slices of the output layer's input-gradient GEMM
+    float* part = nullptr;  // its FP32 partial products [dh_split][B][width]
 };
 
 namespace {
@@ -254,13 +333,33 @@ elrt_status net_cuda(elrt_net* net, cudaError_t e, const char* what) {
 }
 
 // D = A . B^T with the chosen epilogue (A [M][K], B [N][K] bf16, K % 8 == 0)
+// K slices for a GEMM with few output tiles and a long K (the output layer's input gradient, K = the
+// number of outputs): the count s <= 8 that minimises the rounds of work items per slice length on 152
+// SMs, keeping at least 8 k-blocks per slice
+int k_slices(int M, int N, int K) {
+    const int tiles = ((M + tc::BM - 1) / tc::BM) * ((N + 127) / 128);
+    const int nkb = (K + tc::BK - 1) / tc::BK;
+    int best = 1;
+    double bt = 1.0;
+    for (int sl = 2; sl <= 8 && nkb >= 8 * sl; ++sl) {
+        const double t = (double)((tiles * sl + 151) / 152) / sl;
+        if (t < bt - 1e-9) {
+            bt = t;
+            best = sl;
+        }
+    }
+    return best;
+}
+
 elrt_status gemm(elrt_net* net, const bf16* A, const bf16* Bm, int M, int N, int K, int mode, tc::EpiArgs ep) {
     ep.err = net->d_err;
     CUtensorMap ta, tb;
-    const bool wide = N >= 2048;
+    // 256-column tiles for wide outputs, and for long-M GEMMs with many tiles (the output layer's weight
+    // gradient), where they cut the operand bytes each SM streams per flop by a quarter
+    const bool wide = N >= 2048 || (N % 256 == 0 && ((M + tc::BM - 1) / tc::BM) * (N / 256) >= 4 * 152);
     if (!make_map(&ta, A, M, K, tc::BM) || !make_map(&tb, Bm, N, K, wide ? 256 : 128))
         return net_fail(net, ELRT_EINVAL, "tensor map encoding failed (alignment or stride)");
-    const int tiles = ((M + tc::BM - 1) / tc::BM) * (wide ? (N + 255) / 256 : (N + 127) / 128);
+    const int tiles = ((M + tc::BM - 1) / tc::BM) * (wide ? (N + 255) / 256 : (N + 127) / 128) * std::max(1, ep.ksplit);
     dim3 grid(std::min(tiles, 152));
     if (wide) {
         const int smem = tc::GemmSmem<256>::TOTAL;
@@ -293,6 +392,8 @@ elrt_status ensure_batch(elrt_net* net, int B) {
     add((size_t)B * net->nout * 2);
     add((size_t)B * net->nout * 2);
     add((size_t)B * net->nout * 4);
+    const int dsplit = nh > 0 ? k_slices(B, w, net->nout) : 1;
+    if (dsplit > 1) add((size_t)dsplit * B * w * 4);
     cudaError_t e = cudaMalloc(&net->bbuf, bytes);
     if (e != cudaSuccess) return net_cuda(net, e, "batch buffers");
     net->bbuf_bytes = bytes;
@@ -320,6 +421,8 @@ elrt_status ensure_batch(elrt_net* net, int B) {
     net->dY = (bf16*)take((size_t)B * net->nout * 2);
     net->dYt = (bf16*)take((size_t)B * net->nout * 2);
     net->T = (float*)take((size_t)B * net->nout * 4);
+    net->dh_split = dsplit;
+    net->part = dsplit > 1 ? (float*)take((size_t)dsplit * B * w * 4) : nullptr;
     return ELRT_OK;
 }
 
@@ -389,7 +492,20 @@ elrt_status backward_batch(elrt_net* net, int B) {
         s = gemm(net, net->dYt, hin_t, net->nout, kin, B, tc::EPI_F32, ep);
         if (s) return s;
         k_rowsum_bf16<<<(net->nout + 7) / 8, 256, 0, net->stream>>>(net->dYt, net->nout, B, o.gb);
-        if (nh > 0) {
+        if (nh > 0 && net->dh_split > 1) {
+            // few output tiles, K = the number of outputs: K slices into FP32 partials, then one pass
+            // that sums them and applies the activation derivative
+            tc::EpiArgs ed;
+            ed.out_f = net->part;
+            ed.ld_out = net->width;
+            ed.ksplit = net->dh_split;
+            ed.part_stride = (size_t)B * net->width;
+            s = gemm(net, net->dY, o.Wt, B, net->width, net->nout, tc::EPI_F32, ed);
+            if (s) return s;
+            const dim3 g((net->width + 31) / 32, (B + 31) / 32);
+            k_dact_reduce<<<g, 256, 0, net->stream>>>(net->part, net->dh_split, ed.part_stride, B, net->width,
+                                                      net->Z[nh - 1], net->act, net->dZ[nh - 1], net->dZt[nh - 1]);
+        } else if (nh > 0) {
             tc::EpiArgs ed;
             ed.z_in = net->Z[nh - 1];
             ed.out_bf = net->dZ[nh - 1];
@@ -430,13 +546,12 @@ elrt_status adam_update(elrt_net* net, float lr, float b1, float b2, float eps) 
     net->step += 1;
     const float bc1 = 1.f - powf(b1, (float)net->step), bc2 = 1.f - powf(b2, (float)net->step);
     for (auto& ly : net->L) {
-        const int64_t nw = (int64_t)ly.out * ly.in_pad;
-        k_adam<<<grid_of(nw), kT, 0, net->stream>>>(ly.W, ly.gW, ly.mW, ly.vW, nw, lr, b1, b2, eps, bc1, bc2);
+        const dim3 g((ly.in_pad + 31) / 32, (ly.out + 63) / 64);
+        k_adam_weights<<<g, kT, 0, net->stream>>>(ly.W, ly.gW, ly.mW, ly.vW, ly.out, ly.in_pad, lr, b1, b2, eps, bc1,
+                                                  bc2, ly.Wb, ly.Wt);
         k_adam<<<grid_of(ly.out), kT, 0, net->stream>>>(ly.b, ly.gb, ly.mb, ly.vb, ly.out, lr, b1, b2, eps, bc1, bc2);
     }
-    elrt_status s = net_cuda(net, cudaGetLastError(), "adam");
-    if (s) return s;
-    return refresh_bf16(net);
+    return net_cuda(net, cudaGetLastError(), "adam");
 }
 
 elrt_status check_err(elrt_net* net) {
@@ -686,6 +801,9 @@ elrt_status elrt_net_fit(elrt_net* net, int64_t n, const double* kappa, const do
         return a;
     };
     const int64_t nb = n / B;
+    // float4 target rows: both label widths multiples of 4 and 16-byte aligned label buffers
+    const bool vec4 = co % 4 == 0 && cm % 4 == 0 && (uintptr_t)in2out % 16 == 0 && (uintptr_t)in2sol % 16 == 0;
+    const dim3 tgrid((unsigned)std::min<int64_t>(vec4 ? 4 : 8, (net->nout + kT - 1) / kT), (unsigned)std::min(B, 65535));
     const float b1 = o->beta1 > 0 ? o->beta1 : 0.9f, b2 = o->beta2 > 0 ? o->beta2 : 0.999f;
     const float eps = o->eps > 0 ? o->eps : 1e-8f;
     for (int ep = 0; ep < o->epochs; ++ep) {
@@ -697,8 +815,12 @@ elrt_status elrt_net_fit(elrt_net* net, int64_t n, const double* kappa, const do
         for (int64_t bi = 0; bi < nb; ++bi) {
             k_batch_features<<<grid_of((int64_t)B * net->fpad), kT, 0, sm>>>(
                 F, net->fpad, net->nfeat, net->feat_mean, net->feat_std, n, bi * B, B, pa, pb, net->X0, net->X0t);
-            k_batch_targets<<<grid_of((int64_t)B * net->nout), kT, 0, sm>>>(in2out, co, in2sol, cm, net->out_mean,
-                                                                             net->out_std, n, bi * B, B, pa, pb, net->T);
+            if (vec4)
+                k_batch_targets<4><<<tgrid, kT, 0, sm>>>(in2out, co, in2sol, cm, net->out_mean, net->out_std, n,
+                                                         bi * B, B, pa, pb, net->T);
+            else
+                k_batch_targets<1><<<tgrid, kT, 0, sm>>>(in2out, co, in2sol, cm, net->out_mean, net->out_std, n,
+                                                         bi * B, B, pa, pb, net->T);
             s = forward_batch(net, B, 1, nullptr, nullptr, 0, 0, true);
             if (!s) s = backward_batch(net, B);
             if (!s) s = adam_update(net, lr, b1, b2, eps);

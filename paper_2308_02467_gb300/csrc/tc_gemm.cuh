@@ -21,7 +21,7 @@ namespace tc {
 
 constexpr int BM = 128;
 constexpr int BK = 64;
-constexpr int kGemmThreads = 192;
+constexpr int kGemmThreads = 320;  // TMA producer, MMA issuer, eight epilogue warps
 constexpr long long kWaitCycles = 4000000000LL;  // ~2 s at 2 GHz
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -179,6 +179,8 @@ struct EpiArgs {
     int split = 0;
     int ld_out = 0, ld_out2 = 0, ld_t = 0;
     int act = 0;                           // 0 GELU (exact, erf), 1 ELU
+    int ksplit = 1;                        // K slices (EPI_F32 only): slice s writes out_f + s * part_stride
+    size_t part_stride = 0;
     int* err = nullptr;
 };
 
@@ -220,17 +222,61 @@ __device__ __forceinline__ void st_bf16x16(__nv_bfloat16* dst, const float (&v)[
     d[1] = make_uint4(w[4], w[5], w[6], w[7]);
 }
 
-// Epilogue of 16 consecutive columns n0c .. n0c+15 of row m (v holds the accumulator values).
-// sb: the tile's bias for these 16 columns, staged in shared memory (EPI_BIAS_ACT, EPI_LOSS)
+// the standardised targets of row m, columns n0c .. n0c+15 (zero beyond N)
+__device__ __forceinline__ void load_targets16(const EpiArgs& ep, int m, int n0c, int N, float (&tg)[16]) {
+    if (n0c + 16 <= N) {
+        const float4* src = reinterpret_cast<const float4*>(ep.target + (size_t)m * ep.ld_out + n0c);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float4 v4 = __ldcs(src + q);
+            tg[4 * q] = v4.x;
+            tg[4 * q + 1] = v4.y;
+            tg[4 * q + 2] = v4.z;
+            tg[4 * q + 3] = v4.w;
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) tg[j] = n0c + j < N ? ep.target[(size_t)m * ep.ld_out + n0c + j] : 0.f;
+    }
+}
+
+// EPI_LOSS of 16 consecutive columns n0c .. n0c+15 of row m: v holds the accumulator values, sb the
+// tile's bias for these columns (shared memory), tg their targets (loaded ahead by the caller)
+__device__ __forceinline__ void loss16(const EpiArgs& ep, int m, int n0c, int N, float (&v)[16], float& lsum,
+                                       const float* sb, const float (&tg)[16]) {
+    const bool full = n0c + 16 <= N;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+        if (n0c + j < N) {
+            const float y = v[j] + sb[j];
+            const float d = y - tg[j];
+            lsum += fabsf(d);
+            v[j] = d > 0.f ? ep.loss_scale : (d < 0.f ? -ep.loss_scale : 0.f);
+        }
+    }
+    if (full) {
+        st_bf16x16(ep.out_bf + (size_t)m * ep.ld_out + n0c, v);
+    } else {
+        _Pragma("unroll") for (int j = 0; j < 16; ++j) if (n0c + j < N) ep.out_bf[(size_t)m * ep.ld_out + n0c + j] = __float2bfloat16_rn(v[j]);
+    }
+    if (ep.out_bf_t)
+        _Pragma("unroll") for (int j = 0; j < 16; ++j) if (n0c + j < N)
+            ep.out_bf_t[(size_t)(n0c + j) * ep.ld_t + m] = __float2bfloat16_rn(v[j]);
+}
+
+// Epilogue of 16 consecutive columns n0c .. n0c+15 of row m (v holds the accumulator values) for
+// EPI_F32, EPI_BIAS_ACT and EPI_DACT.  sb: the tile's bias for these 16 columns, staged in shared
+// memory (EPI_BIAS_ACT); slice: the K slice (EPI_F32)
 __device__ __forceinline__ void epilogue16(int mode, const EpiArgs& ep, int m, int n0c, int N, float (&v)[16],
-                                           float& lsum, const float* sb) {
+                                           const float* sb, int slice) {
     const bool full = n0c + 16 <= N;
     if (mode == EPI_F32) {
+        float* out = ep.out_f + (size_t)slice * ep.part_stride;
         if (full) {
-            st_f32x16(ep.out_f + (size_t)m * ep.ld_out + n0c, v);
+            st_f32x16(out + (size_t)m * ep.ld_out + n0c, v);
         } else {
             _Pragma("unroll") for (int j = 0; j < 16; ++j) if (n0c + j < N)
-ep.out_f[(size_t)m * ep.ld_out + n0c + j] = v[j];
+out[(size_t)m * ep.ld_out + n0c + j] = v[j];
         }
     } else if (mode == EPI_BIAS_ACT) {
         float z[16];
@@ -252,43 +298,22 @@ ep.out_f[(size_t)m * ep.ld_out + n0c + j] = v[j];
         if (ep.out_bf_t)
             _Pragma("unroll") for (int j = 0; j < 16; ++j) if (n0c + j < N)
 ep.out_bf_t[(size_t)(n0c + j) * ep.ld_t + m] = __float2bfloat16_rn(v[j]);
-    } else if (mode == EPI_LOSS) {
-        float tg[16];
-        if (full) {
-            const float4* src = reinterpret_cast<const float4*>(ep.target + (size_t)m * ep.ld_out + n0c);
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const float4 v4 = src[q];
-                tg[4 * q] = v4.x;
-                tg[4 * q + 1] = v4.y;
-                tg[4 * q + 2] = v4.z;
-                tg[4 * q + 3] = v4.w;
-            }
-        } else {
-#pragma unroll
-            for (int j = 0; j < 16; ++j) tg[j] = n0c + j < N ? ep.target[(size_t)m * ep.ld_out + n0c + j] : 0.f;
-        }
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            if (n0c + j < N) {
-                const float y = v[j] + sb[j];
-                const float d = y - tg[j];
-                lsum += fabsf(d);
-                v[j] = d > 0.f ? ep.loss_scale : (d < 0.f ? -ep.loss_scale : 0.f);
-            }
-        }
-        if (full) {
-            st_bf16x16(ep.out_bf + (size_t)m * ep.ld_out + n0c, v);
-        } else {
-            _Pragma("unroll") for (int j = 0; j < 16; ++j) if (n0c + j < N) ep.out_bf[(size_t)m * ep.ld_out + n0c + j] = __float2bfloat16_rn(v[j]);
-        }
-        if (ep.out_bf_t)
-            _Pragma("unroll") for (int j = 0; j < 16; ++j) if (n0c + j < N)
-                ep.out_bf_t[(size_t)(n0c + j) * ep.ld_t + m] = __float2bfloat16_rn(v[j]);
     } else {  // EPI_DACT
-        _Pragma("unroll") for (int j = 0; j < 16; ++j) if (n0c + j < N) {
-            const float z = __bfloat162float(ep.z_in[(size_t)m * ep.ld_out + n0c + j]);
-            v[j] = v[j] * act_df(z, ep.act);
+        if (full) {  // the 16 pre-activations in two 16-byte loads
+            const uint4* zp = reinterpret_cast<const uint4*>(ep.z_in + (size_t)m * ep.ld_out + n0c);
+            const uint4 za = zp[0], zb = zp[1];
+            const uint32_t zw[8] = {za.x, za.y, za.z, za.w, zb.x, zb.y, zb.z, zb.w};
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const float2 z2 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&zw[q]));
+                v[2 * q] *= act_df(z2.x, ep.act);
+                v[2 * q + 1] *= act_df(z2.y, ep.act);
+            }
+        } else {
+            _Pragma("unroll") for (int j = 0; j < 16; ++j) if (n0c + j < N) {
+                const float z = __bfloat162float(ep.z_in[(size_t)m * ep.ld_out + n0c + j]);
+                v[j] = v[j] * act_df(z, ep.act);
+            }
         }
         if (full) {
             st_bf16x16(ep.out_bf + (size_t)m * ep.ld_out + n0c, v);
@@ -302,8 +327,32 @@ ep.out_bf_t[(size_t)(n0c + j) * ep.ld_t + m] = __float2bfloat16_rn(v[j]);
     }
 }
 
-// Persistent: each CTA walks tiles blockIdx.x, blockIdx.x + gridDim.x, ... (M tiles fastest, so
-// concurrently running CTAs share the B tile in L2).  The TMA producer streams k-blocks of
+// EPI_OUTPUT of 16 consecutive columns n0c .. n0c+15 of row m: y = acc * scale + shift into out_f
+// (columns below split) or out_f2; the split, a multiple of 16, never falls inside the group
+__device__ __forceinline__ void output16(const EpiArgs& ep, int m, int n0c, int N, float (&v)[16], const float* sc,
+                                         const float* sh) {
+#pragma unroll
+    for (int j = 0; j < 16; j += 4) {
+        const float4 s4 = *reinterpret_cast<const float4*>(sc + j);
+        const float4 h4 = *reinterpret_cast<const float4*>(sh + j);
+        v[j] = fmaf(v[j], s4.x, h4.x);
+        v[j + 1] = fmaf(v[j + 1], s4.y, h4.y);
+        v[j + 2] = fmaf(v[j + 2], s4.z, h4.z);
+        v[j + 3] = fmaf(v[j + 3], s4.w, h4.w);
+    }
+    float* dst = n0c < ep.split ? ep.out_f + (size_t)m * ep.ld_out + n0c
+                                : ep.out_f2 + (size_t)m * ep.ld_out2 + (n0c - ep.split);
+    if (n0c + 16 <= N) {
+        st_f32x16(dst, v);
+    } else {
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            if (n0c + j < N) dst[j] = v[j];
+    }
+}
+
+// Persistent: each CTA walks work items blockIdx.x, blockIdx.x + gridDim.x, ... (the shorter tile
+// dimension fastest, so concurrently running CTAs share the long operand's tile in L2).  The TMA producer streams k-blocks of
 // consecutive tiles through the ring without a break; the MMA issuer alternates between two TMEM
 // accumulators so the epilogue of one tile overlaps the MMAs of the next.
 template <int BN>
@@ -324,9 +373,29 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     float* prm = (float*)(base + S::STAGES * S::STAGE_BYTES + 256);  // [2 tiles][scale BN | shift BN]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int nk = (K + BK - 1) / BK;
+    const int nkb = (K + BK - 1) / BK;
     const int mt = (M + BM - 1) / BM, ntl = (N + BN - 1) / BN;
-    const int ntiles = mt * ntl;
+    const int ks = ep.ksplit > 1 ? ep.ksplit : 1;
+    const int ntiles = mt * ntl * ks;  // work items: output tile, then K slice
+    // tile origin of work item `item`: the shorter tile dimension runs fastest, so that the CTAs
+    // working at the same time share the long operand's slab (read once from DRAM) while the short
+    // operand stays in L2
+    auto origin = [&](int item, int& m0, int& n0) {
+        const int t = item % (mt * ntl);
+        if (mt <= ntl) {
+            m0 = (t % mt) * BM;
+            n0 = (t / mt) * BN;
+        } else {
+            m0 = (t / ntl) * BM;
+            n0 = (t % ntl) * BN;
+        }
+    };
+    // k-blocks [kb0, kb1) of work item `item`
+    auto kslice = [&](int item, int& kb0, int& kb1) {
+        const int sl = item / (mt * ntl);
+        kb0 = (int)((int64_t)nkb * sl / ks);
+        kb1 = (int)((int64_t)nkb * (sl + 1) / ks);
+    };
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < S::STAGES; ++s) {
@@ -335,7 +404,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(&acc_full[a], 1);
-            mbar_init(&acc_empty[a], 4);  // one arrival per epilogue warp
+            mbar_init(&acc_empty[a], 8);  // one arrival per epilogue warp
         }
         *abort = 0;
         fence_barrier_init();
@@ -354,8 +423,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         // TMA producer
         int kbg = 0, issued = 0;
         for (int tile = blockIdx.x; tile < ntiles && !*abort; tile += gridDim.x) {
-            const int m0 = (tile % mt) * BM, n0 = (tile / mt) * BN;
-            for (int kb = 0; kb < nk; ++kb, ++kbg) {
+            int m0, n0, kb0, kb1;
+            origin(tile, m0, n0);
+            kslice(tile, kb0, kb1);
+            for (int kb = kb0; kb < kb1; ++kb, ++kbg) {
                 const int s = kbg % S::STAGES;
                 const uint32_t ph = (kbg / S::STAGES) & 1;
                 if (!mbar_wait(&empty[s], ph ^ 1, abort)) {
@@ -390,7 +461,9 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             tc_fence_after();
             const uint32_t dt = tmem_base + (uint32_t)(a * BN);
             bool ok = true;
-            for (int kb = 0; kb < nk; ++kb, ++kbg) {
+            int kb0, kb1;
+            kslice(tile, kb0, kb1);
+            for (int kb = kb0; kb < kb1; ++kb, ++kbg) {
                 const int s = kbg % S::STAGES;
                 const uint32_t ph = (kbg / S::STAGES) & 1;
                 if (!mbar_wait(&full[s], ph, abort)) {
@@ -404,7 +477,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                 const uint64_t bd = sw128_desc(smem_u32(Bs + s * S::B_BYTES));
 #pragma unroll
                 for (int k = 0; k < BK / 16; ++k)
-                    mma_bf16(dt, ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2), idesc, (kb | k) != 0 ? 1u : 0u);
+                    mma_bf16(dt, ad + (uint64_t)(k * 2), bd + (uint64_t)(k * 2), idesc, (kb != kb0 || k != 0) ? 1u : 0u);
                 mma_commit(&empty[s]);
             }
             mma_commit(&acc_full[a]);
@@ -412,71 +485,76 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             if (!ok) break;
         }
     } else if (warp >= 2) {
-        // epilogue: warp w owns TMEM lanes 32 (w % 4) .. + 31, i.e. tile rows
-        const int q = warp & 3;
+        // epilogue: warp w owns TMEM lanes 32 (w % 4) .. + 31 (tile rows) and half (w - 2) / 4 of the
+        // tile's columns; EPI_LOSS loads its targets D chunks ahead, the first before the MMAs finish.
+        // A warp whose wait gave up stays in the loop without touching memory, so that all eight
+        // epilogue warps pass the same number of named barriers.
+        constexpr int HB = BN / 2, NCH = HB / 16, D = 4;
+        const int q = warp & 3, h = (warp - 2) >> 2, et = threadIdx.x - 64;
         float lsum = 0.f;
+        bool dead = false;
         int t = 0;
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++t) {
             const int a = t & 1;
-            const int m0 = (tile % mt) * BM, n0 = (tile / mt) * BN;
+            int m0, n0;
+            origin(tile, m0, n0);
+            const int m = m0 + q * 32 + lane;
+            float tg[D][16];
+            if (mode == EPI_LOSS && m < M && !dead) {
+#pragma unroll
+                for (int i = 0; i < D; ++i)
+                    if (n0 + h * HB + 16 * i < N) load_targets16(ep, m, n0 + h * HB + 16 * i, N, tg[i]);
+            }
             // tcgen05.ld is .sync.aligned: the whole warp must take the same branch
-            const bool ok = __all_sync(0xffffffffu, mbar_wait(&acc_full[a], (t >> 1) & 1, abort) && !*abort);
-            if (!ok) {
+            if (!dead && !__all_sync(0xffffffffu, mbar_wait(&acc_full[a], (t >> 1) & 1, abort) && !*abort)) {
                 if (ep.err && lane == 0) atomicOr(ep.err, 4);
-                break;
+                dead = true;
             }
             tc_fence_after();
-            const int m = m0 + q * 32 + lane;
             const uint32_t tb = tmem_base + (uint32_t)(a * BN) + ((uint32_t)(q * 32) << 16);
+            // the tile's column parameters, once per tile in shared memory (two buffers: a warp may
+            // start the next tile while others finish this one): scale std and shift bias * std + mean
+            // (EPI_OUTPUT), or the bias (EPI_BIAS_ACT, EPI_LOSS)
+            float* sp = prm + (t & 1) * 2 * BN;
             if (mode == EPI_OUTPUT) {
-                // the tile's column scale std and shift bias * std + mean, once per tile in shared
-                // memory (two buffers: a warp may start the next tile while others finish this one)
-                float* sc = prm + (t & 1) * 2 * BN;
-                for (int c = threadIdx.x - 64; c < BN; c += 128) {
+                for (int c = et; c < BN; c += 256) {
                     const int n = min(n0 + c, N - 1);
                     const float sd = ep.col_std[n];
-                    sc[c] = sd;
-                    sc[BN + c] = ep.bias[n] * sd + ep.col_mean[n];
+                    sp[c] = sd;
+                    sp[BN + c] = ep.bias[n] * sd + ep.col_mean[n];
                 }
-                asm volatile("bar.sync 1, 128;" ::: "memory");  // the four epilogue warps
-                for (int c0 = 0; c0 < BN; c0 += 16) {
-                    if (n0 + c0 >= N) break;
+                asm volatile("bar.sync 1, 256;" ::: "memory");  // the eight epilogue warps
+            } else if (mode == EPI_BIAS_ACT || mode == EPI_LOSS) {
+                for (int c = et; c < BN; c += 256) sp[c] = ep.bias[min(n0 + c, N - 1)];
+                asm volatile("bar.sync 1, 256;" ::: "memory");
+            }
+            if (dead) continue;
+            if (mode == EPI_LOSS) {
+                // unrolled, so that the target ring is indexed statically
+#pragma unroll
+                for (int i = 0; i < NCH; ++i) {
+                    const int c0 = h * HB + 16 * i;
+                    if (n0 + c0 >= N) break;  // warp-uniform
                     float v[16];
                     tmem_ld16(tb + (uint32_t)c0, v);
                     if (m < M) {
-#pragma unroll
-                        for (int j = 0; j < 16; j += 4) {
-                            const float4 s4 = *reinterpret_cast<const float4*>(sc + c0 + j);
-                            const float4 h4 = *reinterpret_cast<const float4*>(sc + BN + c0 + j);
-                            v[j] = fmaf(v[j], s4.x, h4.x);
-                            v[j + 1] = fmaf(v[j + 1], s4.y, h4.y);
-                            v[j + 2] = fmaf(v[j + 2], s4.z, h4.z);
-                            v[j + 3] = fmaf(v[j + 3], s4.w, h4.w);
-                        }
-                        const int n0c = n0 + c0;
-                        // the split (a multiple of 16) never falls inside a 16-column group
-                        float* dst = n0c < ep.split ? ep.out_f + (size_t)m * ep.ld_out + n0c
-                                                    : ep.out_f2 + (size_t)m * ep.ld_out2 + (n0c - ep.split);
-                        if (n0c + 16 <= N) {
-                            st_f32x16(dst, v);
-                        } else {
-#pragma unroll
-                            for (int j = 0; j < 16; ++j)
-                                if (n0c + j < N) dst[j] = v[j];
-                        }
+                        loss16(ep, m, n0 + c0, N, v, lsum, sp + c0, tg[i % D]);
+                        if (i + D < NCH && n0 + c0 + 16 * D < N) load_targets16(ep, m, n0 + c0 + 16 * D, N, tg[i % D]);
                     }
                 }
             } else {
-                float* sb = prm + (t & 1) * 2 * BN;
-                if (mode == EPI_BIAS_ACT || mode == EPI_LOSS) {  // the tile's bias, once per tile
-                    for (int c = threadIdx.x - 64; c < BN; c += 128) sb[c] = ep.bias[min(n0 + c, N - 1)];
-                    asm volatile("bar.sync 1, 128;" ::: "memory");
-                }
-                for (int c0 = 0; c0 < BN; c0 += 16) {
-                    if (n0 + c0 >= N) break;
+#pragma unroll 1
+                for (int i = 0; i < NCH; ++i) {
+                    const int c0 = h * HB + 16 * i;
+                    if (n0 + c0 >= N) break;  // warp-uniform
                     float v[16];
                     tmem_ld16(tb + (uint32_t)c0, v);
-                    if (m < M) epilogue16(mode, ep, m, n0 + c0, N, v, lsum, sb + c0);
+                    if (m < M) {
+                        if (mode == EPI_OUTPUT)
+                            output16(ep, m, n0 + c0, N, v, sp + c0, sp + BN + c0);
+                        else
+                            epilogue16(mode, ep, m, n0 + c0, N, v, sp + c0, tile / (mt * ntl));
+                    }
                 }
             }
             tc_fence_before();

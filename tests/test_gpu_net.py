@@ -67,12 +67,14 @@ def test_mlp_forward_matches_oracle(lib):
     net.close()
 
 
-@pytest.mark.parametrize("act", ["gelu", "elu"])
-def test_gradients_match_oracle(lib, act):
+@pytest.mark.parametrize("act,p,N", [("gelu", 2, 4), ("elu", 2, 4), ("gelu", 4, 8)])
+def test_gradients_match_oracle(lib, act, p, N):
     """Mean-absolute-error gradients of every layer (tcgen05 dgrad / wgrad GEMMs) against the
-    FP64 backward pass of the oracle on the same BF16 weights, inputs and targets."""
+    FP64 backward pass of the oracle on the same BF16 weights, inputs and targets.  p = 4, N = 8
+    (8400 outputs) takes the K-sliced input-gradient GEMM of the output layer and ragged
+    256-column output tiles."""
     import torch
-    net = lib.Net(2, 4, n_hidden=2, width=128, activation=act, seed=3)
+    net = lib.Net(p, N, n_hidden=2, width=128, activation=act, seed=3)
     rng = np.random.default_rng(2)
     Ws, bs = _set_random(net, rng)
     B = 128
@@ -118,6 +120,41 @@ def test_adam_first_step(lib):
         live = np.abs(dW[l]) > 1e-6
         agree = np.isclose(step[live], -lr * np.sign(dW[l][live]), atol=lr * 1e-2)
         assert agree.mean() > 0.98, (l, agree.mean())
+    net.close()
+
+
+def test_adam_step_refreshes_the_bf16_weights(lib):
+    """After an Adam step the forward pass (BF16 W) and the input-gradient GEMMs (BF16 W^T) use the
+    updated weights: the gradients of a second batch match the oracle on the new FP32 masters."""
+    import torch
+    net = lib.Net(4, 8, n_hidden=2, width=128, seed=6)
+    rng = np.random.default_rng(5)
+    _set_random(net, rng)
+    B = 128
+
+    def data():
+        x = rng.normal(size=(B, net.n_feat_pad))
+        x[:, net.n_feat:] = 0.0
+        return x, rng.normal(size=(B, net.n_out))
+
+    def dev(a):
+        return torch.tensor(a, dtype=torch.float32, device="cuda")
+
+    x1, t1 = data()
+    net.elrt_net_train_step(dev(x1), dev(t1), lr=3e-2)
+    Ws = [bf16_round(net.elrt_net_params(l, "W")) for l in range(net.n_layers)]
+    bs = [np.asarray(net.elrt_net_params(l, "b"), dtype=np.float64) for l in range(net.n_layers)]
+    x2, t2 = data()
+    loss = net.elrt_net_train_step(dev(x2), dev(t2), lr=0.0)
+    xb = bf16_round(x2)
+    zs, y = mlp.forward(Ws, bs, xb, "gelu")
+    l_ref, dy = mlp.mae(y, t2)
+    assert abs(loss - l_ref) < 1e-2 * l_ref
+    dW, _ = mlp.backward(Ws, bs, xb, zs, dy, "gelu")
+    for l in range(net.n_layers):
+        gW = net.elrt_net_params(l, "dW")
+        rW = np.linalg.norm(gW - dW[l]) / np.linalg.norm(dW[l])
+        assert rW < 5e-2, (l, rW)
     net.close()
 
 
