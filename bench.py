@@ -50,6 +50,24 @@ DRAM_BYTES_PER_ELEMENT_STEP = {
 }
 
 
+def max_over_ranks(x, device):
+    """The largest of the ranks' values of x (the step time of the slowest replica) when a process
+    group of more than one rank is up, else x itself."""
+    import torch
+    import torch.distributed as td
+    if not (td.is_available() and td.is_initialized()) or td.get_world_size() == 1:
+        return x
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    td.all_reduce(t, op=td.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replicas_throughput(n_per_rank, world, ms_max):
+    """Whole-job elements/s of `world` replicas that each solved n_per_rank elements, timed by the
+    slowest one (weak scaling: the work per rank is fixed)."""
+    return world * n_per_rank / (ms_max / 1000.0)
+
+
 def alu_peak_tflops(kind, mode, clk_mhz):
     fp32 = 152 * 128 * 2 * clk_mhz * 1e6 / 1e12
     if kind == "fp32":
@@ -406,10 +424,7 @@ def run_ours(args, rank, world, local_rank):
     prof = {k: ctx.elrt_profile_get(k) for k in names}
     work = {k: ctx.elrt_profile_work(k) for k in names}
     ctx.elrt_profile_enable(False)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        td.all_reduce(t, op=td.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, "cuda")
 
     # ---- end to end through the public API with host buffers
     barrier()
@@ -426,10 +441,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     barrier()
     ms_e2e = e0.elapsed_time(e1) / args.steps
-    if dist:
-        t = torch.tensor([ms_e2e], device="cuda")
-        td.all_reduce(t, op=td.ReduceOp.MAX)
-        ms_e2e = float(t.item())
+    ms_e2e = max_over_ranks(ms_e2e, "cuda")
 
     if rank != 0:
         return
@@ -472,7 +484,7 @@ def run_ours(args, rank, world, local_rank):
     roof.update({"avg_launch_ms": tk["ms_per_step"] / tk["launches_per_step"], "share_of_timed_kernels": tk["share"],
                  "elements_per_step": n})
     gst, lst = info["global"], local_stats
-    val = world * n / (ms / 1000.0)
+    val = replicas_throughput(n, world, ms)
     out = {
         "metric": "elements/s (classical element pipeline: local operators + skeleton GMRES + mean recovery)",
         "value": val, "unit": "elements/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -491,7 +503,7 @@ def run_ours(args, rank, world, local_rank):
         "roofline": roof,
         "kernels": kernels,
         "gpu_launches": launches,
-        "e2e": {"value": world * n / (ms_e2e / 1000.0), "unit": "elements/s",
+        "e2e": {"value": replicas_throughput(n, world, ms_e2e), "unit": "elements/s",
                 "h2d_bytes_per_step": kap_h.numel() * 8 + om_h.numel() * 8 + g_h.numel() * 8,
                 "d2h_bytes_per_step": um_h.numel() * 8},
         "clocks": clk.summary(),
