@@ -210,11 +210,12 @@ elrt_status elrt_global_apply(elrt_ctx* ctx, int32_t nx, int32_t nz, const void*
                               const double* x, double* y);
 
 /* Solves eq. hdg_global_mat, sum_K (R^o_K - A_i2o^K) u^ = 0 with the boundary inflow moved to the
- * right-hand side, by restarted GMRES(restart) with classical Gram-Schmidt (a second pass where
- * the first cancels more than half of the norm), until ||b - A x|| <= rtol ||b|| (recomputed at
- * every restart) or max_iter Arnoldi steps.  FP64 in2out: FP64 vectors.  FP32 in2out: FP32 Krylov
- * basis, float-float iterate, right-hand side and restart residual, FP64 reductions; the Arnoldi
- * steps use the operator that elrt_set_krylov_op selects.
+ * right-hand side, by restarted GMRES(restart) with classical Gram-Schmidt (FP32 basis and
+ * restart <= 31: a second pass where the first removes more than 90% of ||w||^2; otherwise always
+ * two passes), until ||b - A x|| <= rtol ||b|| (recomputed at every restart) or max_iter Arnoldi
+ * steps.  FP64 in2out: FP64 vectors.  FP32 in2out: FP32 Krylov basis, float-float iterate,
+ * right-hand side and restart residual, FP64 reductions; the Arnoldi steps use the operator that
+ * elrt_set_krylov_op selects.
  * inflow: device boundary data (layout above); skeleton: device [E][n_out] FP64, read as the
  * initial guess if use_guess != 0, else zeroed; on return it holds the outflow DOFs.
  * Synchronises.  Returns ELRT_ENOCONV (stats filled, skeleton = last iterate) if not converged. */

@@ -106,8 +106,8 @@ __device__ __forceinline__ ff to_ff(float v) { return ff{v, 0.f}; }
 //   matvec       w = v_j - A v_j; with the streaming matvec its blocks then form h1 = V^T w and
 //                ||w||^2 over their own output rows (k_arn_dots otherwise); the last block reduces
 //                and decides whether a second Gram-Schmidt pass is needed: only if the first pass
-//                cancelled more than half of ||w||^2 (||w||^2 - ||h1||^2 < ||w||^2 / 2, the usual
-//                criterion of classical Gram-Schmidt with selective reorthogonalisation)
+//                removed more than kReorthCancel of ||w||^2 (||w||^2 - ||h1||^2 < 0.1 ||w||^2:
+//                selective reorthogonalisation with the remaining norm below 0.32 ||w||)
 //   k_arn_axdots w -= V h1; then either h2 = V^T w (second pass) or ||w||^2 on the block's slice
 //   k_arn_axnorm second pass only: w -= V h2 and ||w||^2; the last block (or block 0 without a
 //                second pass) writes the Hessenberg column h1 + h2, ||w|| and applies the Givens
@@ -122,6 +122,11 @@ __device__ __forceinline__ ff to_ff(float v) { return ff{v, 0.f}; }
 // ------------------------------------------------------------------------------------------------
 constexpr int kArnThreads = 256;
 constexpr int kArnMaxV = 32;  // restart length + 1 supported by this path
+// Second Gram-Schmidt pass when the first removed more than this fraction of ||w||^2.  The common
+// choice 1/2 (remaining norm below ||w|| / sqrt 2) ran the second pass on most Arnoldi steps of the
+// benchmark without changing the iteration count or the final residual; each restart recomputes the
+// true residual, so the basis only has to span the Krylov space well enough for the cycle.
+constexpr double kReorthCancel = 0.9;
 
 struct ArnState {
     unsigned ticket[4];
@@ -233,7 +238,7 @@ __device__ void arn_first_pass_finish(const double* P, unsigned nb, int j, ArnSt
         if (lane < nv) as->h2[lane] = 0.0;
         if (lane == 0) {
             const double w2 = __ldcg(as->h1 + nv);
-            as->reorth = (w2 - s < 0.5 * w2) ? 1 : 0;
+            as->reorth = (w2 - s < (1.0 - kReorthCancel) * w2) ? 1 : 0;
         }
     }
 }
