@@ -332,7 +332,6 @@ elrt_status net_cuda(elrt_net* net, cudaError_t e, const char* what) {
                     std::string(what) + ": " + cudaGetErrorString(e));
 }
 
-// D = A . B^T with the chosen epilogue (A [M][K], B [N][K] bf16, K % 8 == 0)
 // K slices for a GEMM with few output tiles and a long K (the output layer's input gradient, K = the
 // number of outputs): the count s <= 8 that minimises the rounds of work items per slice length on 152
 // SMs, keeping at least 8 k-blocks per slice
@@ -351,6 +350,7 @@ int k_slices(int M, int N, int K) {
     return best;
 }
 
+// D = A . B^T with the chosen epilogue (A [M][K], B [N][K] bf16, K % 8 == 0)
 elrt_status gemm(elrt_net* net, const bf16* A, const bf16* Bm, int M, int N, int K, int mode, tc::EpiArgs ep) {
     ep.err = net->d_err;
     CUtensorMap ta, tb;
