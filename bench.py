@@ -77,6 +77,51 @@ def alu_peak_tflops(kind, mode, clk_mhz):
     return None
 
 
+def kernel_rooflines(prof, work, steps, n, hbm, peak_src, mode, clk_max):
+    """Per-group table and the roofline of the dominant group from the library's event timings.
+
+    prof: name -> (total ms, launches) over `steps` steps; work: name -> (algorithmic bytes, flops)
+    of the same launches; n: elements per step; hbm: the measured copy bandwidth (GB/s).  achieved =
+    algorithmic bytes (or flops) / event time; traffic = the ncu DRAM bytes per element and step of
+    the group scaled to one launch, None without a capture of the current kernel."""
+    total_prof = sum(v[0] for v in prof.values())
+    kernels = {}
+    for name, (ms_k, nl) in prof.items():
+        b, f = work.get(name, (0.0, 0.0))
+        if nl == 0 or name not in KERNEL_BOUND:
+            continue
+        bound, pipe = KERNEL_BOUND[name]
+        t_s = ms_k / 1000.0
+        row = {"ms_per_step": ms_k / steps, "launches_per_step": nl / steps, "share": ms_k / total_prof,
+               "bytes_per_launch": b / nl, "achieved_gbs": b / t_s / 1e9, "frac_hbm": b / t_s / 1e9 / hbm}
+        if f > 0:
+            row["tflops"] = f / t_s / 1e12
+            pk = alu_peak_tflops(pipe, mode, clk_max) if pipe else None
+            if pk:
+                row["frac_alu"] = row["tflops"] / pk
+        row["bound"] = bound
+        kernels[name] = row
+    top = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
+    tk = kernels[top]
+    bound, pipe = KERNEL_BOUND[top]
+    dram = DRAM_BYTES_PER_ELEMENT_STEP.get(top)
+    traffic = dram * n / tk["launches_per_step"] if dram else None
+    if bound == "hbm":
+        roof = {"kernel": top, "bound": "hbm", "achieved": tk["achieved_gbs"], "peak": hbm, "unit": "GB/s",
+                "frac": tk["frac_hbm"], "traffic": traffic,
+                "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})",
+                "algorithmic_bytes_per_launch": tk["bytes_per_launch"]}
+    else:
+        pk = alu_peak_tflops(pipe, mode, clk_max)
+        roof = {"kernel": top, "bound": "alu", "achieved": tk["tflops"], "peak": pk, "unit": "TFLOP/s",
+                "frac": tk["tflops"] / pk, "traffic": traffic,
+                "peak_source": f"{pipe} issue rate derived: 152 SMs x 128 FP32 lanes x {clk_max:g} MHz",
+                "algorithmic_bytes_per_launch": tk["bytes_per_launch"]}
+    roof.update({"avg_launch_ms": tk["ms_per_step"] / tk["launches_per_step"], "share_of_timed_kernels": tk["share"],
+                 "elements_per_step": n})
+    return kernels, roof
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -448,41 +493,7 @@ def run_ours(args, rank, world, local_rank):
     peaks, peak_src = load_peaks()
     clk_max = peaks.get("sm_max_mhz", 2070.0)
     hbm = peaks["hbm_gbs"]
-    total_prof = sum(v[0] for v in prof.values())
-    kernels = {}
-    for name, (ms_k, nl) in prof.items():
-        b, f = work.get(name, (0.0, 0.0))
-        if nl == 0 or name not in KERNEL_BOUND:
-            continue
-        bound, pipe = KERNEL_BOUND[name]
-        t_s = ms_k / 1000.0
-        row = {"ms_per_step": ms_k / args.steps, "launches_per_step": nl / args.steps, "share": ms_k / total_prof,
-               "bytes_per_launch": b / nl, "achieved_gbs": b / t_s / 1e9, "frac_hbm": b / t_s / 1e9 / hbm}
-        if f > 0:
-            row["tflops"] = f / t_s / 1e12
-            pk = alu_peak_tflops(pipe, args.mode, clk_max) if pipe else None
-            if pk:
-                row["frac_alu"] = row["tflops"] / pk
-        row["bound"] = bound
-        kernels[name] = row
-    top = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
-    tk = kernels[top]
-    bound, pipe = KERNEL_BOUND[top]
-    dram = DRAM_BYTES_PER_ELEMENT_STEP.get(top)
-    traffic = dram * n / tk["launches_per_step"] if dram else None
-    if bound == "hbm":
-        roof = {"kernel": top, "bound": "hbm", "achieved": tk["achieved_gbs"], "peak": hbm, "unit": "GB/s",
-                "frac": tk["frac_hbm"], "traffic": traffic,
-                "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})",
-                "algorithmic_bytes_per_launch": tk["bytes_per_launch"]}
-    else:
-        pk = alu_peak_tflops(pipe, args.mode, clk_max)
-        roof = {"kernel": top, "bound": "alu", "achieved": tk["tflops"], "peak": pk, "unit": "TFLOP/s",
-                "frac": tk["tflops"] / pk, "traffic": traffic,
-                "peak_source": f"{pipe} issue rate derived: 152 SMs x 128 FP32 lanes x {clk_max:g} MHz",
-                "algorithmic_bytes_per_launch": tk["bytes_per_launch"]}
-    roof.update({"avg_launch_ms": tk["ms_per_step"] / tk["launches_per_step"], "share_of_timed_kernels": tk["share"],
-                 "elements_per_step": n})
+    kernels, roof = kernel_rooflines(prof, work, args.steps, n, hbm, peak_src, args.mode, clk_max)
     gst, lst = info["global"], local_stats
     val = replicas_throughput(n, world, ms)
     out = {

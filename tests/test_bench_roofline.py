@@ -1,0 +1,66 @@
+"""bench.py's roofline arithmetic on synthetic event timings (no GPU): achieved = algorithmic bytes
+or flops / event time, the fraction against the measured or derived peak, the dominant group,
+and the DRAM traffic scaled from the ncu bytes per element to one launch."""
+
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+HBM = 6769.4  # GB/s
+N = 4096      # elements per step
+STEPS = 5
+
+
+def _tables(prof, work, mode="tf32ir", clk=2070.0):
+    return bench.kernel_rooflines(prof, work, STEPS, N, HBM, "measured", mode, clk)
+
+
+def test_hbm_bound_dominant_group():
+    # 96 launches of 2.5 GB in 0.456 ms each; the matvec group is smaller
+    prof = {"lu_tc_update": (96 * 0.456, 96), "gemv": (20.0, 1385), "status": (0.05, 5), "lu_resolve": (0.0, 0)}
+    work = {"lu_tc_update": (96 * 2.5e9, 96 * 1.0e10), "gemv": (1385 * 4.8e8, 0.0), "status": (1e3, 0.0)}
+    kernels, roof = _tables(prof, work)
+    assert "lu_resolve" not in kernels                      # no launches: no row
+    assert roof["kernel"] == "lu_tc_update" and roof["bound"] == "hbm" and roof["unit"] == "GB/s"
+    achieved = 2.5e9 / 0.456e-3 / 1e9
+    assert roof["achieved"] == pytest.approx(achieved)
+    assert roof["frac"] == pytest.approx(achieved / HBM)
+    assert roof["peak"] == HBM
+    assert roof["avg_launch_ms"] == pytest.approx(0.456)
+    assert roof["algorithmic_bytes_per_launch"] == pytest.approx(2.5e9)
+    # ncu bytes per element and step, scaled to one of the step's 96 / 5 launches
+    per_step = 96 / STEPS
+    assert roof["traffic"] == pytest.approx(bench.DRAM_BYTES_PER_ELEMENT_STEP["lu_tc_update"] * N / per_step)
+    assert kernels["lu_tc_update"]["tflops"] == pytest.approx(1.0e10 / 0.456e-3 / 1e12)
+    # shares are of all timed groups; "status" (a flag reduction) is timed but has no roofline row
+    assert "status" not in kernels
+    total = sum(v[0] for v in prof.values())
+    assert sum(r["share"] for r in kernels.values()) == pytest.approx(1.0 - prof["status"][0] / total)
+
+
+def test_alu_bound_dominant_group_uses_the_derived_peak():
+    prof = {"residual": (200.0, 10), "restrict": (10.0, 10)}
+    work = {"residual": (10 * 5.7e9, 10 * 4.4e13), "restrict": (10 * 6e9, 0.0)}
+    kernels, roof = _tables(prof, work)
+    assert roof["kernel"] == "residual" and roof["bound"] == "alu" and roof["unit"] == "TFLOP/s"
+    pk = bench.alu_peak_tflops("ff", "tf32ir", 2070.0)
+    # FP32 issue rate 152 x 128 lanes x 2070 MHz; a float-float multiply-add = 12 issue slots for 2 flops
+    assert pk == pytest.approx(152 * 128 * 2070e6 * 2 / 12 / 1e12)
+    tflops = 4.4e13 / 20e-3 / 1e12
+    assert roof["achieved"] == pytest.approx(tflops)
+    assert roof["frac"] == pytest.approx(tflops / pk)
+    assert kernels["residual"]["frac_alu"] == pytest.approx(tflops / pk)
+    assert "tflops" not in kernels["restrict"]
+
+
+def test_group_without_a_capture_has_no_traffic():
+    prof = {"gemv": (120.0, 1385), "krylov": (40.0, 3000)}
+    work = {"gemv": (1385 * 4.8e8, 0.0), "krylov": (3000 * 3.7e7, 0.0)}
+    _, roof = _tables(prof, work)
+    assert roof["kernel"] == "gemv" and roof["traffic"] is None
