@@ -328,8 +328,13 @@ elrt_status elrt_net_forward(elrt_net* net, int64_t n, const float* x, float* y)
 
 /* One training step on a batch of n (a multiple of 64) standardised samples: forward, mean
  * absolute error against t (device [n][n_out] FP32), backward into the gradient buffers, and,
- * if lr > 0, an Adam update (step counter advanced).  loss (host, may be NULL) gets the batch
- * MAE; synchronises when loss is given. */
+ * if lr > 0, an Adam update (step counter advanced) that also refreshes the BF16 weight copies
+ * the GEMMs read.  loss (host, may be NULL) gets the batch MAE; synchronises when loss is given.
+ * Device memory: the network keeps buffers for the last batch size it saw, n x (4 n_feat_pad +
+ * 10 width n_hidden + 8 n_out) bytes (BF16 activations and their transposes, the output-layer
+ * gradient and its transpose, FP32 targets), plus up to 8 x n x width x 4 bytes of FP32 partial
+ * products when the output layer's input gradient is split along K because its output tiles
+ * alone would not fill the GPU. */
 elrt_status elrt_net_train_step(elrt_net* net, int64_t n, const float* x, const float* t, float lr, float* loss);
 
 /* Training from physical data: kappa device [n][(p+1)^2] (km^-1 at the LGL nodes), omega [n],
