@@ -58,10 +58,18 @@ typedef enum {
     ELRT_ANG_DO = 1       /* direction and phase sampled at cell centres */
 } elrt_angular;
 
+/* Local-solve modes.  "Refinement" below is iterative refinement whose residual -B^ - A X is formed
+ * from the structured operator in float-float arithmetic (pairs of FP32 values, ~44 significant
+ * bits, error-free TwoSum / FMA TwoProduct) with the running solution X also kept in float-float;
+ * no FP64 instruction runs per matrix entry.  Measured: one sweep takes the FP32-level solution to a
+ * maximum relative residual of ~2e-12 on the benchmark slab; two sweeps stay below 1e-12 on every
+ * tested element. */
 typedef enum {
-    ELRT_LOCAL_FP64 = 0,     /* FP64 LU with partial pivoting on the CUDA cores */
-    ELRT_LOCAL_FP32_IR = 1,  /* FP32 LU, then FP64 iterative refinement with the structured residual */
-    ELRT_LOCAL_TF32_IR = 2   /* TF32 tensor-core trailing updates, FP32 accumulation, FP64 refinement */
+    ELRT_LOCAL_FP64 = 0,     /* FP64 LU with partial pivoting on the CUDA cores (no refinement) */
+    ELRT_LOCAL_FP32_IR = 1,  /* FP32 LU with partial pivoting on the CUDA cores, then float-float refinement */
+    ELRT_LOCAL_TF32_IR = 2   /* LU without pivoting whose trailing updates run on the tensor cores as
+                                3xTF32 (hi*hi + hi*lo + lo*hi of TF32 splits of the FP32 operands, FP32
+                                accumulation: FP32-level factors), then float-float refinement */
 } elrt_local_mode;
 
 typedef enum { ELRT_F32 = 0, ELRT_F64 = 1 } elrt_dtype;
@@ -166,7 +174,7 @@ elrt_status elrt_assemble(elrt_ctx* ctx, int64_t n_elems, double h, const double
 /* in2out and in2sol of E elements (eqs. hdg_local_i2u, hdg_local_i2o, ang_ave):
  *   X = -(B - C + M - S)^{-1} B^,  in2out = R^o X,  in2sol = (1/N) sum_k X[(k, i), :].
  * mode: elrt_local_mode; out_dtype: elrt_dtype of in2out/in2sol (device buffers sized above).
- * refine_steps: FP64 refinement steps for the IR modes (ignored for FP64; 0..8).
+ * refine_steps: float-float refinement sweeps for the IR modes (ignored for FP64; 0..8).
  * elem_status: device [E] int32 or NULL; per element 0 = ok, 1 = zero pivot, 2 = refinement
  * residual above 1e-10 after the last step, 4 = non-finite value.  stats (host, may be NULL)
  * synchronises the stream to fill it.  Inputs are checked for NaN and negative values on the
@@ -184,9 +192,12 @@ elrt_status elrt_build_local(elrt_ctx* ctx, int64_t n_elems, double h, const dou
  *   - It needs no context and allocates nothing: no cudaMalloc, cudaFree or other allocating call.
  *     Its scratch is one file-scope device array of ELRT_STATIC_SCRATCH_MIB MiB that every GPU
  *     which loads the library holds until the process exits.  The batch is processed in chunks
- *     that fit the array; ELRT_EINVAL is returned, before any launch, when a single element's
- *     workspace does not fit (the element's local system of nu = (p+1)^2 N unknowns needs about
- *     nu (nu + n_in) 4 bytes in FP32_IR, or 8 bytes in FP64, plus nu n_in 8 bytes in FP32_IR).
+ *     that fit the array.  An element of nu = (p+1)^2 N unknowns and n_in = 2 (p+1) N inflow DOFs
+ *     takes nu ld s + nu 4 + 76 bytes, plus nu n_in 8 in FP32_IR, where ld = nu + n_in rounded up
+ *     to a multiple of 32 and s = 4 (FP32_IR) or 8 (FP64); 256 bytes of the array hold flags.
+ *     ELRT_EINVAL is returned, before any launch, when one element does not fit the array or when
+ *     its LU panel needs more than 227 KB of shared memory (nu beyond 1512 in FP32_IR, 1588 in
+ *     FP64).
  *   - The first call on a device looks up the array's device address (once per device, with
  *     that device current); make that first call before any stream capture.
  *   - Every call on a device shares the array and leaves its contents behind; what must start
@@ -194,8 +205,10 @@ elrt_status elrt_build_local(elrt_ctx* ctx, int64_t n_elems, double h, const dou
  *     other host threads) race on the array: serialise them.
  *   - The caller passes inputs and outputs exactly as for elrt_build_local; `stream` is a
  *     cudaStream_t (NULL: legacy default stream).  The call synchronises that stream at the end
- *     and returns ELRT_EINVAL for bad arguments or invalid kappa/omega/h, ELRT_ECUDA on a CUDA
- *     failure.  It reports no statistics and no per-element status. */
+ *     and returns ELRT_EINVAL for bad arguments or invalid kappa/omega/h, ELRT_ESINGULAR when some
+ *     element met a zero pivot or produced a non-finite value (the other elements' operators are
+ *     still written), ELRT_ECUDA on a CUDA failure.  It reports no statistics and no per-element
+ *     status. */
 #define ELRT_STATIC_SCRATCH_MIB 64
 elrt_status elrt_build_local_static(const elrt_disc* disc, void* stream, int64_t n_elems, double h,
                                     const double* h_elem, const double* kappa, const double* omega, int32_t mode,
@@ -245,7 +258,7 @@ typedef struct elrt_net elrt_net;
 
 typedef struct {
     int32_t mode;           /* elrt_local_mode of the classical local stage */
-    int32_t refine_steps;   /* FP64-class refinement steps (IR modes) */
+    int32_t refine_steps;   /* float-float refinement sweeps (IR modes) */
     double rtol;            /* GMRES relative residual */
     int32_t max_iter;
     int32_t restart;
@@ -321,6 +334,27 @@ elrt_status elrt_net_sizes(const elrt_net* net, int64_t* n_feat, int64_t* n_feat
  * what = 0 W, 1 b, 2 dW (last gradient), 3 db; dir = 0 read into host buf, 1 write from it (W, b).
  * Synchronises. */
 elrt_status elrt_net_params(elrt_net* net, int32_t layer, int32_t what, int32_t dir, float* host_buf);
+
+/* Checkpoint of a network (the paper has none: it trains once and exports the result): one
+ * versioned little-endian binary file with everything training needs to resume bit-for-bit --
+ * the description (p, N, n_hidden, width, activation, seed), the FP32 master weights and biases,
+ * Adam's first and second moments, the Adam step counter and the input/output standardisation --
+ * followed by a CRC-32 (IEEE 802.3) of all preceding bytes.  Layout: a 60-byte header (magic
+ * "ELRTNET\0", u32 version 1, i32 p, n_angles, n_hidden, width, activation, u64 seed, i32
+ * standardised, i64 Adam step, i64 count F of FP32 values), F FP32 values (per layer: W
+ * [out][in_pad], b, m(W), v(W), m(b), v(b); then input mean, input std [in_pad], output mean,
+ * output std [n_out]), u32 CRC.  BF16 weight copies are rebuilt on load.
+ * elrt_net_save synchronises the network's stream and writes `path` (through `path`.tmp and a
+ * rename, so a reader never sees a half-written file); ELRT_EINVAL if the file cannot be written.
+ * elrt_net_load creates a network from the file on the current device (stream as elrt_net_create);
+ * ELRT_EINVAL, with no network created, if the file is missing, truncated, of another version, has
+ * an invalid description, a size that does not match it, or a CRC mismatch.
+ * elrt_net_file_info validates a file (header, size, CRC) and reports its description,
+ * standardisation flag, Adam step and value count without touching a GPU (any pointer may be NULL). */
+elrt_status elrt_net_save(elrt_net* net, const char* path);
+elrt_status elrt_net_load(elrt_net** net, const char* path, void* stream);
+elrt_status elrt_net_file_info(const char* path, elrt_net_desc* desc, int32_t* standardised, int64_t* adam_step,
+                               int64_t* n_values);
 
 /* Raw network on standardised features: x device [n][n_feat_pad] FP32 (rounded to BF16 on the
  * way in), y device [n][n_out] FP32 standardised outputs. */

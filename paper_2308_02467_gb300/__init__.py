@@ -12,7 +12,7 @@ _EXPORTS = (
     "KRYLOV_F32", "KRYLOV_F16",
     "Disc", "Context", "elrt_lgl", "elrt_phase_matrix", "elrt_node_coords", "elrt_n_nodes", "elrt_n_local",
     "elrt_n_skel", "elrt_n_inflow", "exported_symbols", "elrt_build_local_static", "Net",
-    "elrt_build_local_learned", "elrt_solve_batch",
+    "elrt_build_local_learned", "elrt_solve_batch", "elrt_net_file_info",
 )
 
 __all__ = list(_EXPORTS)

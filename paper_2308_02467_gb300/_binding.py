@@ -103,6 +103,9 @@ _sig = {
     "elrt_net_last_error": (C.c_char_p, [_vp]),
     "elrt_net_sizes": (_i32, [_vp, _P(_i64), _P(_i64), _P(_i64), _P(_i32), _P(_i64)]),
     "elrt_net_params": (_i32, [_vp, _i32, _i32, _i32, _vp]),
+    "elrt_net_save": (_i32, [_vp, C.c_char_p]),
+    "elrt_net_load": (_i32, [_P(_vp), C.c_char_p, _vp]),
+    "elrt_net_file_info": (_i32, [C.c_char_p, _P(NetDesc), _P(_i32), _P(_i64), _P(_i64)]),
     "elrt_net_forward": (_i32, [_vp, _i64, _vp, _vp]),
     "elrt_net_train_step": (_i32, [_vp, _i64, _vp, _vp, C.c_float, _P(C.c_float)]),
     "elrt_net_fit": (_i32, [_vp, _i64, _vp, _vp, _vp, _vp, _vp, _P(TrainOpts), _vp]),
@@ -350,11 +353,14 @@ def _net_check(status, h):
 class Net:
     """An elrt_net: the element network of Sec. 2.4.1 (calls run on the current torch stream)."""
 
-    def __init__(self, p, n_angles, n_hidden=4, width=1024, activation="gelu", seed=0):
+    def __init__(self, p, n_angles, n_hidden=4, width=1024, activation="gelu", seed=0, _handle=None):
         import torch
-        d = NetDesc(p, n_angles, n_hidden, width, 0 if activation == "gelu" else 1, seed)
-        h = C.c_void_p()
-        _check(_lib.elrt_net_create(C.byref(h), C.byref(d), C.c_void_p(torch.cuda.current_stream().cuda_stream)))
+        if _handle is None:
+            d = NetDesc(p, n_angles, n_hidden, width, 0 if activation == "gelu" else 1, seed)
+            h = C.c_void_p()
+            _check(_lib.elrt_net_create(C.byref(h), C.byref(d), C.c_void_p(torch.cuda.current_stream().cuda_stream)))
+        else:
+            h = _handle
         self._h = h
         a, b, c, nl, npar = C.c_int64(), C.c_int64(), C.c_int64(), C.c_int32(), C.c_int64()
         _lib.elrt_net_sizes(h, C.byref(a), C.byref(b), C.byref(c), C.byref(nl), C.byref(npar))
@@ -362,6 +368,20 @@ class Net:
         self.p, self.n_angles, self.width = p, n_angles, width
         self.nm = (p + 1) ** 2
         self.nin = 2 * (p + 1) * n_angles
+
+    @classmethod
+    def elrt_net_load(cls, path):
+        """A network restored from a checkpoint written by elrt_net_save (current device and stream)."""
+        import torch
+        h = C.c_void_p()
+        _check(_lib.elrt_net_load(C.byref(h), os.fsencode(path), C.c_void_p(torch.cuda.current_stream().cuda_stream)))
+        info = elrt_net_file_info(path)
+        return cls(info["p"], info["n_angles"], info["n_hidden"], info["width"],
+                   "gelu" if info["activation"] == 0 else "elu", info["seed"], _handle=h)
+
+    def elrt_net_save(self, path):
+        self._s()
+        _net_check(_lib.elrt_net_save(self._h, os.fsencode(path)), self._h)
 
     def _s(self):
         import torch
@@ -434,6 +454,15 @@ class Net:
                                        _ptr(omega, torch.float64, n, "omega"),
                                        _ptr(in2out, torch.float32, n * self.nin * self.nin, "in2out"),
                                        _ptr(in2sol, torch.float32, n * self.nm * self.nin, "in2sol")), self._h)
+
+
+def elrt_net_file_info(path):
+    """Description, standardisation flag, Adam step and value count of a network checkpoint, validated
+    (header, size, CRC) on the host; raises ElrtError(EINVAL) on a bad file."""
+    d, st, step, nv = NetDesc(), C.c_int32(), C.c_int64(), C.c_int64()
+    _check(_lib.elrt_net_file_info(os.fsencode(path), C.byref(d), C.byref(st), C.byref(step), C.byref(nv)))
+    return {"p": d.p, "n_angles": d.n_angles, "n_hidden": d.n_hidden, "width": d.width, "activation": d.activation,
+            "seed": d.seed, "standardised": st.value, "adam_step": step.value, "n_values": nv.value}
 
 
 def elrt_build_local_learned(ctx, net, kappa, omega, h, in2out, in2sol, tol=1e-3, h_elem=None, estimate=None):

@@ -111,3 +111,11 @@ extern "C" elrt_status elrt_build_local_learned(elrt_ctx* ctx, elrt_net* net, in
                                                 const double* kappa, const double* omega, double tol, float* in2out,
                                                 float* in2sol, float* estimate, int64_t* n_fallback);
 bool elrt_net_matches(const elrt_net* net, const elrt_disc* disc);
+
+// ---- network checkpoint file (ckpt.cpp): layout of the FP32 arrays, CRC-32, encode/decode
+uint32_t ckpt_crc32(const void* data, size_t n, uint32_t crc);
+std::vector<size_t> ckpt_layout(const elrt_net_desc& d);
+bool ckpt_write(const char* path, const elrt_net_desc& d, int32_t standardised, int64_t step,
+                const std::vector<const float*>& arrays, std::string* err);
+bool ckpt_read(const char* path, elrt_net_desc* d, int32_t* standardised, int64_t* step, int64_t* n_floats,
+               std::vector<float>* payload, std::string* err);

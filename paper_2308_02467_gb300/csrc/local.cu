@@ -1174,6 +1174,15 @@ elrt_status static_scratch(void** out) {
     return ELRT_OK;
 }
 
+// flags[1] |= every non-zero per-element status word (zero pivot, non-finite result)
+__global__ void k_static_status(const int* __restrict__ estat, int64_t n, int* __restrict__ flags) {
+    int any = 0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        any |= estat[e];
+    any = __reduce_or_sync(0xffffffffu, any);
+    if ((threadIdx.x & 31) == 0 && any) atomicOr(flags + 1, any);
+}
+
 template <typename T, int NB, int QN>
 elrt_status static_build(const Tab& t, cudaStream_t sm, unsigned char* scratch, int64_t E, double h,
                          const double* h_elem, const double* kappa, const double* omega, int mode, int steps,
@@ -1200,7 +1209,7 @@ elrt_status static_build(const Tab& t, cudaStream_t sm, unsigned char* scratch, 
         cudaFuncSetAttribute(k_lu_resolve<T, NB, QN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lu_smem) ||
         cudaFuncSetAttribute(k_residual<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)res_smem))
         return ELRT_ECUDA;
-    if (cudaMemsetAsync(flags, 0, sizeof(int), sm) != cudaSuccess) return ELRT_ECUDA;
+    if (cudaMemsetAsync(flags, 0, 2 * sizeof(int), sm) != cudaSuccess) return ELRT_ECUDA;
     const size_t osz = out_dtype == ELRT_F32 ? sizeof(float) : sizeof(double);
     for (int64_t e0 = 0; e0 < E; e0 += chunk) {
         const int64_t n = std::min(chunk, E - e0);
@@ -1233,12 +1242,13 @@ elrt_status static_build(const Tab& t, cudaStream_t sm, unsigned char* scratch, 
                 k_restrict<T, double><<<(unsigned)n, kThreads, 0, sm>>>(t, M, ld, estride, t.nu, (double*)o_i2o,
                                                                        (double*)o_i2m, estat, n);
         }
+        k_static_status<<<(unsigned)std::min<int64_t>(152, (n + 255) / 256), 256, 0, sm>>>(estat, n, flags);
         if (cudaGetLastError() != cudaSuccess) return ELRT_ECUDA;
     }
-    int bad = 0;
-    if (cudaMemcpyAsync(&bad, flags, sizeof(int), cudaMemcpyDeviceToHost, sm) != cudaSuccess) return ELRT_ECUDA;
+    int bad[2] = {0, 0};
+    if (cudaMemcpyAsync(bad, flags, sizeof(bad), cudaMemcpyDeviceToHost, sm) != cudaSuccess) return ELRT_ECUDA;
     if (cudaStreamSynchronize(sm) != cudaSuccess) return ELRT_ECUDA;
-    return bad ? ELRT_EINVAL : ELRT_OK;
+    return bad[0] ? ELRT_EINVAL : bad[1] ? ELRT_ESINGULAR : ELRT_OK;
 }
 
 }  // namespace

@@ -572,6 +572,26 @@ elrt_status check_err(elrt_net* net) {
 // ABI
 // ------------------------------------------------------------------------------------------------
 
+// device arrays of a network in checkpoint order (ckpt_layout)
+namespace {
+std::vector<float*> ckpt_arrays(elrt_net* net) {
+    std::vector<float*> a;
+    for (auto& ly : net->L) {
+        a.push_back(ly.W);
+        a.push_back(ly.b);
+        a.push_back(ly.mW);
+        a.push_back(ly.vW);
+        a.push_back(ly.mb);
+        a.push_back(ly.vb);
+    }
+    a.push_back(net->feat_mean);
+    a.push_back(net->feat_std);
+    a.push_back(net->out_mean);
+    a.push_back(net->out_std);
+    return a;
+}
+}  // namespace
+
 extern "C" {
 
 elrt_status elrt_net_create(elrt_net** out, const elrt_net_desc* d, void* stream) {
@@ -699,6 +719,64 @@ elrt_status elrt_net_sizes(const elrt_net* net, int64_t* n_feat, int64_t* n_feat
         for (auto& ly : net->L) np += (int64_t)ly.out * ly.in + ly.out;
         *n_params = np;
     }
+    return ELRT_OK;
+}
+
+elrt_status elrt_net_save(elrt_net* net, const char* path) {
+    if (!net || !path) return net_fail(net, ELRT_EINVAL, "elrt_net_save: bad arguments");
+    const std::vector<size_t> lay = ckpt_layout(net->desc);
+    const std::vector<float*> dev = ckpt_arrays(net);
+    size_t total = 0;
+    for (size_t c : lay) total += c;
+    std::vector<float> host(total);
+    std::vector<const float*> ptrs;
+    size_t off = 0;
+    cudaError_t e = cudaSuccess;
+    for (size_t a = 0; a < lay.size() && e == cudaSuccess; ++a) {
+        e = cudaMemcpyAsync(host.data() + off, dev[a], lay[a] * 4, cudaMemcpyDeviceToHost, net->stream);
+        ptrs.push_back(host.data() + off);
+        off += lay[a];
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(net->stream);
+    if (e != cudaSuccess) return net_cuda(net, e, "elrt_net_save");
+    std::string err;
+    if (!ckpt_write(path, net->desc, net->normalised ? 1 : 0, net->step, ptrs, &err))
+        return net_fail(net, ELRT_EINVAL, err);
+    return ELRT_OK;
+}
+
+elrt_status elrt_net_load(elrt_net** out, const char* path, void* stream) {
+    if (!out || !path) return ELRT_EINVAL;
+    *out = nullptr;
+    elrt_net_desc d{};
+    int32_t standardised = 0;
+    int64_t step = 0, nf = 0;
+    std::vector<float> payload;
+    std::string err;
+    if (!ckpt_read(path, &d, &standardised, &step, &nf, &payload, &err)) return ELRT_EINVAL;
+    elrt_net* net = nullptr;
+    elrt_status s = elrt_net_create(&net, &d, stream);
+    if (s) return s;
+    const std::vector<size_t> lay = ckpt_layout(d);
+    const std::vector<float*> dev = ckpt_arrays(net);
+    size_t off = 0;
+    cudaError_t e = cudaSuccess;
+    for (size_t a = 0; a < lay.size() && e == cudaSuccess; ++a) {
+        e = cudaMemcpyAsync(dev[a], payload.data() + off, lay[a] * 4, cudaMemcpyHostToDevice, net->stream);
+        off += lay[a];
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(net->stream);  // payload is pageable host memory
+    if (e == cudaSuccess) {
+        net->normalised = standardised != 0;
+        net->step = step;
+        s = refresh_bf16(net);
+        if (!s) e = cudaStreamSynchronize(net->stream);
+    }
+    if (s || e != cudaSuccess) {
+        elrt_net_destroy(net);
+        return s ? s : (e == cudaErrorMemoryAllocation ? ELRT_ENOMEM : ELRT_ECUDA);
+    }
+    *out = net;
     return ELRT_OK;
 }
 

@@ -82,3 +82,18 @@ def energy_defect(w, sdn, in_cells, out_cells, w2, kappa_hat, omega, n_angles, A
 
 def with_(problem, **kw):
     return dataclasses.replace(problem, **kw)
+
+
+def thick_and_thin_elements(n, p, seed):
+    """Per-node kappa spanning 1e-3 .. 1e4 km^-1 (a log-uniform element mean with +-0.5 per-node
+    log variation) at sides h ~ U[0.05, 1] km, so kappa_hat = kappa h / 2 covers ~1e-5 .. 5e3; the
+    first two elements are the extremes: kappa_hat = 1.5e3 and 1e-4 everywhere.  Albedo U[0.9, 1]."""
+    r = np.random.default_rng(seed)
+    nm = (p + 1) ** 2
+    h = r.uniform(0.05, 1.0, n)
+    mu = r.uniform(np.log(1e-3), np.log(1e4), n)
+    kappa = np.exp(mu[:, None] + r.uniform(-0.5, 0.5, (n, nm)))
+    h[0], kappa[0] = 1.0, 3.0e3
+    h[1], kappa[1] = 0.2, 1.0e-3
+    omega = r.uniform(0.9, 1.0, n)
+    return kappa, omega, h

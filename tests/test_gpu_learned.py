@@ -1,0 +1,146 @@
+"""The learned local stage at the benchmark's discretisation (p = 6, N = 16, 4 x 1024 GELU network,
+61,152 outputs) held to the FP64 oracle: the network forward element by element at the full
+shape, the energy-balance estimate against the oracle's energy defect on the network's own
+operators, and the whole learned pipeline (network + estimate + classical fallback + skeleton
+GMRES + recovery) against the oracle's classical solution of a cloud field."""
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import hdg, mlp
+from tests import _helpers as H
+
+pytestmark = pytest.mark.gpu
+
+P, NA = 6, 16
+
+
+def _bf16(a):
+    import torch
+    return torch.tensor(np.asarray(a, dtype=np.float32)).to(torch.bfloat16).to(torch.float64).numpy()
+
+
+def test_forward_full_shape_elementwise(lib):
+    """4 hidden layers x 1024 GELU, 61,152 outputs, random weights.  The library rounds the input,
+    the weights and every hidden activation to BF16 and accumulates in FP32; the oracle forward is
+    applied one layer at a time to the same BF16-rounded operands (FP64 arithmetic).  Per entry:
+    |y - y_ref| <= 2e-3 rms(y_ref) (an FP32 summation-order difference can move a hidden activation
+    across a BF16 rounding boundary, one BF16 ulp = 2^-8 relative, which shifts the next layer's
+    outputs by ~1e-4 of their rms)."""
+    import torch
+    net = lib.Net(P, NA, n_hidden=4, width=1024, seed=11)
+    assert net.n_out == 224 * (224 + 49)
+    rng = np.random.default_rng(4)
+    Ws, bs = [], []
+    for l in range(net.n_layers):
+        out, inp = net.layer_shape(l)
+        fan = net.n_feat if l == 0 else inp
+        Wl = (rng.uniform(-1, 1, (out, inp)) * np.sqrt(3.0 / fan)).astype(np.float32)
+        if l == 0:
+            Wl[:, net.n_feat:] = 0.0
+        bl = rng.uniform(-0.1, 0.1, out).astype(np.float32)
+        net.elrt_net_params(l, "W", Wl)
+        net.elrt_net_params(l, "b", bl)
+        Ws.append(_bf16(Wl))
+        bs.append(bl.astype(np.float64))
+    n = 48
+    x = rng.normal(size=(n, net.n_feat_pad))
+    x[:, net.n_feat:] = 0.0
+    y = torch.empty(n, net.n_out, device="cuda", dtype=torch.float32)
+    net.elrt_net_forward(torch.tensor(x, dtype=torch.float32, device="cuda"), y)
+    h = _bf16(x)
+    for l in range(net.n_layers):
+        _, h = mlp.forward([Ws[l]], [bs[l]], h)
+        if l + 1 < net.n_layers:
+            h = _bf16(mlp.gelu(h))
+    got = y.cpu().numpy().astype(np.float64)
+    rms = np.sqrt(np.mean(h * h))
+    err = np.abs(got - h)
+    assert err.max() <= 2e-3 * rms, (err.max() / rms, np.sqrt(np.mean(err ** 2)) / rms)
+    net.close()
+
+
+@pytest.fixture(scope="module")
+def net6(lib):
+    """The benchmark's network (4 x 1024 GELU) trained on 100k elements of the element-network
+    workload (h ~ U[0.05, 1] km, lognormal Gaussian-covariance kappa, albedo U[0.9, 1]) with labels
+    from the classical FP32-IR local solve."""
+    import torch
+    ctx = lib.Context(P, NA, 0.85, lib.ANG_FV0)
+    xi, _ = lib.elrt_lgl(P)
+    xx, zz = np.meshgrid(xi, xi)
+    eb = W.element_batch(100_000)
+    k = torch.tensor(eb.kappa_at(xx.reshape(-1), zz.reshape(-1)), device="cuda")
+    o = torch.tensor(eb.omega, device="cuda")
+    h = torch.tensor(eb.h, device="cuda")
+    a = torch.empty(len(eb), ctx.nin, ctx.nin, device="cuda", dtype=torch.float32)
+    m = torch.empty(len(eb), ctx.nm, ctx.nin, device="cuda", dtype=torch.float32)
+    ctx.elrt_build_local(k, o, 1.0, a, m, mode=lib.LOCAL_FP32_IR, refine_steps=1, h_elem=h)
+    net = lib.Net(P, NA, n_hidden=4, width=1024, seed=2308)
+    losses = net.elrt_net_fit(k, o, h, a, m, epochs=40, batch=1024, lr=1e-3, seed=7)
+    del a, m, k, o, h
+    torch.cuda.empty_cache()
+    print(f"net6: MAE {losses[0]:.4f} -> {losses[-1]:.4f}")
+    yield ctx, net
+    net.close()
+    ctx.close()
+
+
+def test_estimate_matches_oracle_energy_defect(lib, net6):
+    """The library's per-element estimate (max over inflow columns of the relative energy-balance
+    defect, FP32) equals the oracle's energy defect of the same network operators (FP64)."""
+    import torch
+    ctx, net = net6
+    xi, _ = lib.elrt_lgl(P)
+    xx, zz = np.meshgrid(xi, xi)
+    eb = W.element_batch(96, holdout=True)
+    kap = eb.kappa_at(xx.reshape(-1), zz.reshape(-1))
+    k, o, h = (torch.tensor(v, device="cuda") for v in (kap, eb.omega, eb.h))
+    n = len(eb)
+    a = torch.empty(n, ctx.nin, ctx.nin, device="cuda", dtype=torch.float32)
+    m = torch.empty(n, ctx.nm, ctx.nin, device="cuda", dtype=torch.float32)
+    est = torch.empty(n, device="cuda", dtype=torch.float32)
+    nf = lib.elrt_build_local_learned(ctx, net, k, o, 1.0, a, m, tol=1e30, h_elem=h, estimate=est)
+    assert nf == 0
+    A, M, E = a.double().cpu().numpy(), m.double().cpu().numpy(), est.double().cpu().numpy()
+    d = hdg.Disc(P, NA, 0.85)
+    ref = np.array([np.abs(d.energy_defect(kap[e] * eb.h[e] / 2, eb.omega[e], A[e], M[e])).max() for e in range(n)])
+    np.testing.assert_allclose(E, ref, rtol=1e-3, atol=2e-6)
+    assert ref.min() > 1e-6           # network operators are not exact: the comparison is not vacuous
+
+
+def test_learned_pipeline_matches_oracle_with_fallback(lib, net6):
+    """Algorithm 1 with the learned local stage on a 12 x 12 Gaussian-cloud slab (h = 0.83 km,
+    kappa_hat up to 8): the fallback threshold is set between the field's estimates so that some
+    elements keep the network's operators and some are re-solved classically; the mean intensity
+    must match the oracle's classical solution to relative L2 <= 1e-3."""
+    import torch
+    ctx, net = net6
+    prob = W.problem_gaussian_slab(n=12)
+    ref = hdg.solve_problem(prob, rtol=1e-12)
+    n = prob.n_elems
+    kap = torch.tensor(H.lib_kappa(prob), device="cuda")
+    om = torch.tensor(prob.omega, device="cuda")
+    g = torch.tensor(prob.inflow, device="cuda")
+    a = torch.empty(n, ctx.nin, ctx.nin, device="cuda", dtype=torch.float32)
+    m = torch.empty(n, ctx.nm, ctx.nin, device="cuda", dtype=torch.float32)
+    est = torch.empty(n, device="cuda", dtype=torch.float32)
+    sk = torch.empty(n * ctx.nin, device="cuda", dtype=torch.float64)
+    um = torch.empty(n, ctx.nm, device="cuda", dtype=torch.float64)
+
+    def solve(tol):
+        nf = lib.elrt_build_local_learned(ctx, net, kap, om, prob.h, a, m, tol=tol, estimate=est)
+        ctx.elrt_solve_global(prob.nx, prob.nz, a, g, sk, rtol=1e-10, restart=12, max_iter=20000)
+        ctx.elrt_recover_mean(prob.nx, prob.nz, m, sk, g, um)
+        return nf, hdg.rel_l2(um.cpu().numpy(), ref["u_mean"], ref["disc"])
+
+    nf_all, err_net = solve(1e30)                 # the network alone
+    tol = float(np.quantile(est.cpu().numpy(), 0.6))
+    nf, err = solve(tol)
+    nf0, err_cls = solve(1e-30)                   # every element classical
+    print(f"learned: network only {err_net:.2e}; tol {tol:.2e}: {nf}/{n} fallbacks, {err:.2e}; classical {err_cls:.2e}")
+    assert nf_all == 0 and nf0 == n
+    assert 0 < nf < n
+    assert err_cls < 1e-6
+    assert err <= 1e-3, err

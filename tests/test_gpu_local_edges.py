@@ -1,0 +1,81 @@
+"""GPU parity of the tensor-core local solve (mode TF32_IR: no pivoting, 3xTF32 trailing updates,
+float-float refinement) at the edges of its input range, against the FP64 oracle element by
+element: optically thick and thin elements (kappa_hat from ~1e-5 to 5e3, the range the element-
+network workload and the lognormal cloud slab reach), albedo exactly 1, and the refinement-step
+count of the benchmark (one sweep, FP32 operators)."""
+
+import numpy as np
+import pytest
+
+from oracle import hdg
+from tests import _helpers as H
+
+pytestmark = pytest.mark.gpu
+
+
+def _build(lib, p, N, kappa, omega, h, mode, refine, dtype):
+    import torch
+    n = len(omega)
+    ctx = lib.Context(p, N, 0.85, lib.ANG_FV0)
+    i2o = torch.empty(n, ctx.nin, ctx.nin, dtype=dtype, device="cuda")
+    i2m = torch.empty(n, ctx.nm, ctx.nin, dtype=dtype, device="cuda")
+    st = ctx.elrt_build_local(torch.tensor(kappa, device="cuda"), torch.tensor(omega, device="cuda"), 1.0, i2o, i2m,
+                              mode=mode, refine_steps=refine, h_elem=torch.tensor(h, device="cuda"))
+    out = i2o.double().cpu().numpy(), i2m.double().cpu().numpy(), st
+    ctx.close()
+    return out
+
+
+def _oracle(p, N, kappa, omega, h):
+    d = hdg.Disc(p, N, 0.85)
+    ops = [d.local_operators(kappa[e] * h[e] / 2, float(omega[e])) for e in range(len(omega))]
+    return np.stack([o[0] for o in ops]), np.stack([o[1] for o in ops])
+
+
+@pytest.mark.parametrize("p,N,n", [(6, 16, 14), (4, 8, 24)])
+def test_tf32_thick_and_thin_elements_match_oracle(lib, p, N, n):
+    import torch
+    kappa, omega, h = H.thick_and_thin_elements(n, p, seed=100 + p)
+    o_i2o, o_i2m = _oracle(p, N, kappa, omega, h)
+    # the benchmark's configuration: one refinement sweep, FP32 operators
+    a, m, st = _build(lib, p, N, kappa, omega, h, lib.LOCAL_TF32_IR, 1, torch.float32)
+    assert st.n_flagged == 0, st.n_flagged
+    np.testing.assert_allclose(a, o_i2o, atol=2e-6, rtol=2e-6)
+    np.testing.assert_allclose(m, o_i2m, atol=2e-6, rtol=2e-6)
+    # two sweeps, FP64 operators: FP64-level agreement
+    a, m, st = _build(lib, p, N, kappa, omega, h, lib.LOCAL_TF32_IR, 2, torch.float64)
+    assert st.n_flagged == 0 and st.max_rel_residual < 1e-12, st.max_rel_residual
+    np.testing.assert_allclose(a, o_i2o, atol=1e-10)
+    np.testing.assert_allclose(m, o_i2m, atol=1e-10)
+
+
+def test_tf32_albedo_one(lib):
+    """omega = 1 exactly (no absorption): constant preservation (rows of in2out and in2sol sum to 1)
+    and element-wise parity, in the benchmark's configuration and refined to FP64 level."""
+    import torch
+    p, N, n = 6, 16, 10
+    kappa, _, h = H.thick_and_thin_elements(n, p, seed=7)
+    omega = np.ones(n)
+    o_i2o, o_i2m = _oracle(p, N, kappa, omega, h)
+    a, m, st = _build(lib, p, N, kappa, omega, h, lib.LOCAL_TF32_IR, 1, torch.float32)
+    assert st.n_flagged == 0
+    np.testing.assert_allclose(a, o_i2o, atol=2e-6, rtol=2e-6)
+    np.testing.assert_allclose(a.sum(-1), 1.0, atol=2e-5)
+    np.testing.assert_allclose(m.sum(-1), 1.0, atol=2e-5)
+    a, m, st = _build(lib, p, N, kappa, omega, h, lib.LOCAL_TF32_IR, 2, torch.float64)
+    np.testing.assert_allclose(a, o_i2o, atol=1e-10)
+    np.testing.assert_allclose(m, o_i2m, atol=1e-10)
+    np.testing.assert_allclose(a.sum(-1), 1.0, atol=1e-10)
+    np.testing.assert_allclose(m.sum(-1), 1.0, atol=1e-10)
+
+
+def test_fp32_ir_thick_and_thin_elements_match_oracle(lib):
+    """The pivoted CUDA-core FP32 path on the same extreme elements."""
+    import torch
+    p, N, n = 6, 16, 8
+    kappa, omega, h = H.thick_and_thin_elements(n, p, seed=300)
+    o_i2o, o_i2m = _oracle(p, N, kappa, omega, h)
+    a, m, st = _build(lib, p, N, kappa, omega, h, lib.LOCAL_FP32_IR, 2, torch.float64)
+    assert st.n_flagged == 0
+    np.testing.assert_allclose(a, o_i2o, atol=1e-10)
+    np.testing.assert_allclose(m, o_i2m, atol=1e-10)

@@ -258,3 +258,60 @@ def test_inflow_layout_agrees_with_workloads():
         offs, total = hdg.inflow_side_offsets(hdg.Mesh(5, 3, 1.0), d)
         woffs, wtotal = W.inflow_layout(5, 3, 2, N)
         assert list(offs) == woffs and total == wtotal
+
+
+def test_unit_square_exact_solution_by_ray_marching():
+    """Pin P3 by brute force: march back from every node along -sbar_k in small steps until the ray
+    leaves the unit square; the exact angle-discrete solution is exp(-kappa t) if it leaves through
+    the top (unit inflow there) and 0 otherwise.  Independent of the closed-form path lengths."""
+    prob = W.problem_unit_square(p=2, n_angles=8, n=3, kappa=1.3)
+    d = hdg.Disc(prob.p, prob.n_angles, 0.0, prob.angular)
+    mesh = hdg.Mesh(prob.nx, prob.nz, prob.h)
+    x, z = mesh.node_coords(d)
+    ex = hdg.exact_unit_square_mean(prob, d, mesh, 1.3)
+    dt = 2e-4
+    total = np.zeros(x.shape)
+    for k in range(d.n_angles):
+        if d.sz[k] >= 0:
+            continue                          # upward cells see zero inflow through the bottom
+        px, pz = x.copy(), z.copy()
+        t = np.zeros(x.shape)
+        inside = np.ones(x.shape, bool)
+        for _ in range(int(3.0 / dt)):
+            if not inside.any():
+                break
+            px = np.where(inside, px - dt * d.sx[k], px)
+            pz = np.where(inside, pz - dt * d.sz[k], pz)
+            t = np.where(inside, t + dt, t)
+            inside = (px >= 0) & (px <= 1) & (pz <= 1)
+        top = pz > 1.0
+        total += np.where(top, np.exp(-1.3 * t), 0.0)
+    brute = total / d.n_angles
+    # the march overshoots by at most one step; nodes within a step of a shadow line can flip
+    close = np.abs(brute - ex) < 3 * dt
+    assert close.mean() > 0.97, close.mean()
+    np.testing.assert_allclose(brute[close], ex[close], atol=3 * dt)
+
+
+def test_unit_square_discrete_solution_converges_to_exact():
+    """The hybridised solution approaches the closed form under mesh refinement (reading A11: the
+    inflow is discontinuous along the corner characteristics, so only about O(h^1/2) in L2)."""
+    errs = []
+    for n in (4, 8, 16):
+        prob = W.problem_unit_square(p=2, n_angles=8, n=n)
+        ref = hdg.solve_problem(prob, rtol=1e-12)
+        ex = hdg.exact_unit_square_mean(prob, ref["disc"], ref["mesh"], 1.0)
+        errs.append(hdg.rel_l2(ref["u_mean"], ex, ref["disc"]))
+    assert errs[0] < 0.15 and errs[1] < errs[0] / 1.2 and errs[2] < errs[1] / 1.2, errs
+
+
+def test_golden_headline_field_is_the_recorded_oracle_output():
+    """The stored whole-field expectation of the benchmark slab is the file its generator recorded
+    (SHA-256), finite, of the documented shape, from a GMRES solve converged to 1e-12."""
+    import hashlib
+    path = os.path.join(GOLDEN, "gaussian_slab_64x64_mean.npy")
+    meta = json.load(open(os.path.join(GOLDEN, "gaussian_slab_64x64_mean.json")))
+    assert hashlib.sha256(open(path, "rb").read()).hexdigest() == meta["sha256"]
+    u = np.load(path)
+    assert u.shape == (4096, 49) and np.all(np.isfinite(u)) and meta["rel_residual"] < 1e-11
+    assert u.max() > 0.1                     # the beam enters: not a zero field

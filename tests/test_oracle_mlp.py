@@ -78,3 +78,30 @@ def test_adam_first_step_is_signed_lr():
     np.testing.assert_allclose(p, -0.01 * g / (np.abs(g) + 1e-8), rtol=1e-12)
     np.testing.assert_allclose(m, 0.1 * g)
     np.testing.assert_allclose(v, 0.001 * g * g)
+
+
+def test_adam_constant_gradient_moves_by_lr_every_step():
+    """With bias correction, a gradient that stays constant gives m_hat = g and v_hat = g^2 at every
+    step (1 - beta^t cancels the zero start), so each of the steps moves the parameter by
+    lr * g / (|g| + eps).  A wrong correction (e.g. 1 - beta * t, or none) breaks this from step 2."""
+    g = np.array([0.3, -2.0, 5e-2])
+    lr, eps = 0.01, 1e-8
+    p, m, v = np.zeros(3), np.zeros(3), np.zeros(3)
+    for step in range(1, 7):
+        p_new, m, v = mlp.adam(p, g, m, v, step, lr=lr, eps=eps)
+        np.testing.assert_allclose(p_new - p, -lr * g / (np.abs(g) + eps), rtol=1e-12)
+        p = p_new
+
+
+def test_adam_two_steps_by_hand():
+    """Two steps worked by hand (beta1 = 0.9, beta2 = 0.999, lr = 0.1, eps = 0):
+    step 1, g = 0.5:  m = 0.05, v = 2.5e-4, m_hat = 0.5, v_hat = 0.25, move = -0.1;
+    step 2, g = -0.25: m = 0.045 - 0.025 = 0.02, v = 2.4975e-4 + 6.25e-5 = 3.1225e-4,
+    m_hat = 0.02 / 0.19, v_hat = 3.1225e-4 / 1.999e-3, move = -0.1 m_hat / sqrt(v_hat)."""
+    p, m, v = mlp.adam(np.array([1.0]), np.array([0.5]), np.zeros(1), np.zeros(1), 1, lr=0.1, eps=0.0)
+    assert abs(p[0] - 0.9) < 1e-15 and abs(m[0] - 0.05) < 1e-16 and abs(v[0] - 2.5e-4) < 1e-18
+    p, m, v = mlp.adam(p, np.array([-0.25]), m, v, 2, lr=0.1, eps=0.0)
+    assert abs(m[0] - 0.02) < 1e-16 and abs(v[0] - 3.1225e-4) < 1e-17
+    m_hat, v_hat = 0.02 / 0.19, 3.1225e-4 / 1.999e-3
+    assert abs(p[0] - (0.9 - 0.1 * m_hat / math.sqrt(v_hat))) < 1e-14
+    assert abs(p[0] - 0.873366) < 1e-6      # 0.9 - 0.1 * 0.1052632 / 0.3952254

@@ -52,3 +52,37 @@ def test_static_build_rejects_elements_larger_than_the_array(lib):
     st = lib.elrt_build_local_static(p, N, 0.5, lib.ANG_FV0, k, o, 0.1, out_o, out_m, mode=lib.LOCAL_FP64)
     assert st == 1
     assert not torch.any(out_o) and not torch.any(out_m)
+
+
+def test_static_build_allocates_nothing_and_validates_inputs(lib):
+    """After a first call (which looks up the array's address), further calls that run several
+    chunks leave the device's free memory unchanged; invalid kappa / omega give EINVAL and an
+    element whose FP32 system overflows (kappa ~1e300) gives ESINGULAR."""
+    import torch
+    p, N, n = 6, 16, 29
+    kappa, omega, h = H.random_elements(n, p, seed=901)
+    k = torch.tensor(kappa, device="cuda")
+    o = torch.tensor(omega, device="cuda")
+    nm, nin = (p + 1) ** 2, 2 * (p + 1) * N
+    out_o = torch.empty(n, nin, nin, dtype=torch.float32, device="cuda")
+    out_m = torch.empty(n, nm, nin, dtype=torch.float32, device="cuda")
+    run = lambda kk, oo: lib.elrt_build_local_static(p, N, 0.85, lib.ANG_FV0, kk, oo, h, out_o, out_m,
+                                                     mode=lib.LOCAL_FP32_IR, refine_steps=1)
+    assert run(k, o) == 0
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    for _ in range(2):
+        assert run(k, o) == 0
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0, (free0, free1)
+    bad = k.clone()
+    bad[3, 5] = -1.0
+    assert run(bad, o) == 1
+    bad_o = o.clone()
+    bad_o[0] = 1.5
+    assert run(k, bad_o) == 1
+    huge = k.clone()
+    huge[7] = 1e300
+    assert run(huge, o) == 3
+    assert run(k, o) == 0          # the flags start from zero again on the next call
