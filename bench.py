@@ -34,11 +34,24 @@ WORKLOAD = workload_name(64)
 # the pipe whose issue rate limits it.  The float-float residual counts one useful flop per
 # multiply or add of the structured operator; one float-float multiply-add takes 12 FP32 issue
 # slots (1 MUL, 3 FMA, 6 in TwoSum, 2 ADD), so its ALU peak is the FP32 rate x 2 / 12.
+# The trailing update of the tensor-core LU is a dense contraction: "tensor", against the TF32
+# tensor peak, counting the useful flops 2 R C jb once (it issues each product three times as
+# hi*hi + hi*lo + lo*hi, reported separately as the issued fraction).
 KERNEL_BOUND = {
     "assemble": ("hbm", None), "lu_factor_solve": ("alu", "fp32"), "lu_resolve": ("hbm", None),
-    "lu_tc_diag": ("alu", "fp32"), "lu_tc_rowcol": ("hbm", None), "lu_tc_update": ("hbm", None),
+    "lu_tc_diag": ("alu", "fp32"), "lu_tc_rowcol": ("hbm", None), "lu_tc_update": ("tensor", "tf32x3"),
     "residual": ("alu", "ff"), "restrict": ("hbm", None), "gemv": ("hbm", None), "krylov": ("hbm", None),
 }
+TENSOR_PASSES = {"tf32x3": 3}
+# Nominal dense tensor rates of GB300 (PFLOP/s): TF32 1.1, BF16 2.25.  A TF32 peak is the measured
+# BF16 peak times their ratio.
+TF32_PER_BF16 = 1.1 / 2.25
+
+
+def tensor_peak_tflops(peaks):
+    """TF32 peak for a kernel timed inside a long step: the measured sustained BF16 GEMM rate x the
+    nominal TF32/BF16 ratio."""
+    return peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]) * TF32_PER_BF16
 # DRAM bytes (read + write) per element and step of each kernel group, from one ncu capture of
 # the 32 x 32 slab (1024 elements, 3.3 GB of local workspace; summary kept under profiles/); a
 # group missing here has no capture of its current kernel.  The 32 x 32 operators (205 MB) still
@@ -77,7 +90,7 @@ def alu_peak_tflops(kind, mode, clk_mhz):
     return None
 
 
-def kernel_rooflines(prof, work, steps, n, hbm, peak_src, mode, clk_max):
+def kernel_rooflines(prof, work, steps, n, hbm, peak_src, mode, clk_max, tensor_peak=None):
     """Per-group table and the roofline of the dominant group from the library's event timings.
 
     prof: name -> (total ms, launches) over `steps` steps; work: name -> (algorithmic bytes, flops)
@@ -96,9 +109,14 @@ def kernel_rooflines(prof, work, steps, n, hbm, peak_src, mode, clk_max):
                "bytes_per_launch": b / nl, "achieved_gbs": b / t_s / 1e9, "frac_hbm": b / t_s / 1e9 / hbm}
         if f > 0:
             row["tflops"] = f / t_s / 1e12
-            pk = alu_peak_tflops(pipe, mode, clk_max) if pipe else None
-            if pk:
-                row["frac_alu"] = row["tflops"] / pk
+            if bound == "tensor":
+                if tensor_peak:
+                    row["frac_tensor"] = row["tflops"] / tensor_peak
+                    row["frac_tensor_issued"] = row["tflops"] * TENSOR_PASSES.get(pipe, 1) / tensor_peak
+            else:
+                pk = alu_peak_tflops(pipe, mode, clk_max) if pipe else None
+                if pk:
+                    row["frac_alu"] = row["tflops"] / pk
         row["bound"] = bound
         kernels[name] = row
     top = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
@@ -110,6 +128,15 @@ def kernel_rooflines(prof, work, steps, n, hbm, peak_src, mode, clk_max):
         roof = {"kernel": top, "bound": "hbm", "achieved": tk["achieved_gbs"], "peak": hbm, "unit": "GB/s",
                 "frac": tk["frac_hbm"], "traffic": traffic,
                 "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})",
+                "algorithmic_bytes_per_launch": tk["bytes_per_launch"]}
+    elif bound == "tensor":
+        roof = {"kernel": top, "bound": "tensor", "achieved": tk["tflops"], "peak": tensor_peak, "unit": "TFLOP/s",
+                "frac": tk["tflops"] / tensor_peak, "traffic": traffic,
+                "frac_issued": tk["tflops"] * TENSOR_PASSES.get(pipe, 1) / tensor_peak,
+                "passes": TENSOR_PASSES.get(pipe, 1),
+                "peak_source": f"TF32 = MEASURED_PEAKS.json bf16_tflops_sustained x 1.1/2.25 (nominal ratio; {peak_src})",
+                "flops_counted": "useful 2 R C jb per element and panel, once",
+                "achieved_gbs": tk["achieved_gbs"], "frac_hbm": tk["frac_hbm"],
                 "algorithmic_bytes_per_launch": tk["bytes_per_launch"]}
     else:
         pk = alu_peak_tflops(pipe, mode, clk_max)
@@ -144,6 +171,10 @@ def parse():
                     help="GMRES tolerance of the learned-vs-classical comparison at the 1e-3 accuracy target")
     ap.add_argument("--learned-tol", type=float, default=5e-4,
                     help="energy-balance threshold above which an element falls back to the classical solve")
+    ap.add_argument("--holdout-elements", type=int, default=20000,
+                    help="held-out elements of the element-network workload scored against refined classical labels")
+    ap.add_argument("--no-config5", action="store_true",
+                    help="skip the 512x256 lognormal cloud slab (learned vs TF32-IR vs FP64 time-to-solution)")
     return ap.parse_args()
 
 
@@ -387,7 +418,188 @@ def learned_section(args, E, W, ctx, prob, kap, om, g, um_classical, peaks):
     out["pipeline"] = {"ms_per_step": l_ms, "elements_per_s": n / (l_ms / 1000), "fallback_elements": stats["nf"],
                        "fallback_fraction": stats["nf"] / n, "tol": args.learned_tol,
                        "gmres_iterations": stats["g"].iterations, "rel_l2_vs_classical": rel}
-    net.close()
+    return out, net
+
+
+def holdout_section(args, E, W, ctx, net):
+    """The element-network workload's 20k held-out elements scored against refined classical labels
+    (FP32-IR LU + two float-float refinement sweeps, FP64 output: within 1e-10 of the FP64 oracle
+    in the parity tests): per-element relative Frobenius error of in2out and in2sol, and the
+    calibration of the energy-balance estimate (reading A10) against that true error, which sets
+    the fallback tolerance: the largest tolerance on a grid whose accepted elements keep the 95th
+    percentile of the in2out error at or below 1e-3."""
+    import numpy as np
+    import torch
+    p = net.p
+    xi, _ = E.elrt_lgl(p)
+    xx, zz = np.meshgrid(xi, xi)
+    nh = args.holdout_elements
+    eb = W.element_batch(nh, holdout=True)
+    k = torch.tensor(eb.kappa_at(xx.reshape(-1), zz.reshape(-1)), device="cuda")
+    o = torch.tensor(eb.omega, device="cuda")
+    h = torch.tensor(eb.h, device="cuda")
+    err_o = torch.empty(nh, device="cuda", dtype=torch.float64)
+    err_m = torch.empty(nh, device="cuda", dtype=torch.float64)
+    est = torch.empty(nh, device="cuda", dtype=torch.float32)
+    chunk = 4096
+    t_inf = 0.0
+    for c in range(0, nh, chunk):
+        m = min(chunk, nh - c)
+        sl = slice(c, c + m)
+        lo = torch.empty(m, ctx.nin, ctx.nin, device="cuda", dtype=torch.float64)
+        lm = torch.empty(m, ctx.nm, ctx.nin, device="cuda", dtype=torch.float64)
+        ctx.elrt_build_local(k[sl].contiguous(), o[sl].contiguous(), 1.0, lo, lm, mode=E.LOCAL_FP32_IR, refine_steps=2,
+                             h_elem=h[sl].contiguous(), stats=False)
+        po = torch.empty(m, ctx.nin, ctx.nin, device="cuda", dtype=torch.float32)
+        pm = torch.empty(m, ctx.nm, ctx.nin, device="cuda", dtype=torch.float32)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        nf = E.elrt_build_local_learned(ctx, net, k[sl].contiguous(), o[sl].contiguous(), 1.0, po, pm, tol=1e30,
+                                        h_elem=h[sl].contiguous(), estimate=est[sl])
+        t_inf += time.perf_counter() - t0
+        assert nf == 0
+        err_o[sl] = torch.linalg.norm((po.double() - lo).reshape(m, -1), dim=1) / torch.linalg.norm(lo.reshape(m, -1), dim=1)
+        err_m[sl] = torch.linalg.norm((pm.double() - lm).reshape(m, -1), dim=1) / torch.linalg.norm(lm.reshape(m, -1), dim=1)
+        del lo, lm, po, pm
+    eo, em, es = err_o.cpu().numpy(), err_m.cpu().numpy(), est.double().cpu().numpy()
+    q = lambda a, f: float(np.quantile(a, f))
+    rank = lambda a: np.argsort(np.argsort(a))
+    spearman = float(np.corrcoef(rank(es), rank(eo))[0, 1])
+    grid = [1e-4, 2e-4, 5e-4, 1e-3, 2e-3, 5e-3, 1e-2, 2e-2, 5e-2]
+    table = []
+    chosen = grid[0]
+    for tol in grid:
+        acc = es <= tol
+        row = {"tol": tol, "accepted_fraction": float(acc.mean())}
+        if acc.any():
+            row["in2out_err_p95_accepted"] = q(eo[acc], 0.95)
+            row["in2out_err_max_accepted"] = float(eo[acc].max())
+            if row["in2out_err_p95_accepted"] <= 1e-3:
+                chosen = tol
+        table.append(row)
+    torch.cuda.empty_cache()
+    return {"elements": nh, "labels": "FP32-IR + 2 float-float refinement sweeps, FP64 output",
+            "in2out_rel_frobenius": {"median": q(eo, 0.5), "mean": float(eo.mean()), "p90": q(eo, 0.9),
+                                     "p99": q(eo, 0.99), "max": float(eo.max())},
+            "in2sol_rel_frobenius": {"median": q(em, 0.5), "mean": float(em.mean()), "p90": q(em, 0.9),
+                                     "p99": q(em, 0.99), "max": float(em.max())},
+            "estimate": {"median": q(es, 0.5), "p90": q(es, 0.9)},
+            "estimate_vs_error_spearman": spearman, "calibration": table, "calibrated_tol": chosen,
+            "calibration_rule": "largest tol whose accepted elements have p95 in2out error <= 1e-3",
+            "inference_elements_per_s": nh / t_inf}
+
+
+def config5_section(args, E, W, net, tol):
+    """Time-to-solution at relative L2 <= 1e-3 on the 512 x 256 lognormal cloud slab (50 km x 25 km,
+    p = 6, N = 16, sharp tanh edge, beam at 45 deg): the learned local stage with classical
+    fallback, the TF32-IR classical path and the plain FP64 classical GPU path.  The reference
+    solution is the FP64 path converged to GMRES rtol 1e-10; each path's time-to-solution is its
+    local stage plus the GMRES solve at the loosest tolerance (1e-3, 1e-4, ...) whose mean intensity
+    is within relative L2 1e-3 of the reference, plus the recovery.  Sampled elements' operators
+    are compared with the FP64 oracle (which runs only on those elements)."""
+    import numpy as np
+    import torch
+    from oracle import hdg
+    prob = W.problem_cloud_slab()
+    p, N, nx, nz, n = prob.p, prob.n_angles, prob.nx, prob.nz, prob.n_elems
+    ctx = E.Context(p, N, prob.hg_g, E.ANG_FV0)
+    xs, zs = E.elrt_node_coords(p, N, nx, nz, prob.h)
+    t0 = time.perf_counter()
+    kap = prob.kappa.evaluate_torch(torch.tensor(xs.reshape(-1), device="cuda"),
+                                    torch.tensor(zs.reshape(-1), device="cuda")).view(n, ctx.nm).contiguous()
+    om = torch.tensor(prob.omega, device="cuda")
+    g = torch.tensor(prob.inflow, device="cuda")
+    del xs, zs
+    torch.cuda.synchronize()
+    out = {"workload": "lognormal cloud slab 512x256 elements (50 km x 25 km), p=6, N=16, g=0.85, albedo 0.99, "
+                       "tanh edge 50 m, beam 315 deg", "elements": n, "field_gen_s": time.perf_counter() - t0,
+           "kappa_hat_max": float((kap * prob.h / 2).max()), "learned_tol": tol}
+    sk = torch.zeros(n * ctx.nin, device="cuda", dtype=torch.float64)
+    um = torch.empty(n, ctx.nm, device="cuda", dtype=torch.float64)
+    xi, wq = E.elrt_lgl(p)
+    w2 = torch.tensor(np.outer(wq, wq).reshape(-1), device="cuda")[None, :]
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        r = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1), r
+
+    def rel_l2(a, b):
+        return float(torch.sqrt(torch.sum(w2 * (a - b) ** 2) / torch.sum(w2 * b * b)))
+
+    rtols = [1e-3, 1e-4, 1e-5, 1e-6, 1e-7, 1e-8]
+
+    def to_target(i2o, i2m, local_ms, ref):
+        rows = []
+        best = None
+        for rt in rtols:
+            ms_g, st = timed(lambda: ctx.elrt_solve_global(nx, nz, i2o, g, sk, rtol=rt, max_iter=40000, restart=12,
+                                                           raise_on_noconv=False))
+            ms_r, _ = timed(lambda: ctx.elrt_recover_mean(nx, nz, i2m, sk, g, um))
+            err = rel_l2(um, ref) if ref is not None else None
+            rows.append({"gmres_rtol": rt, "gmres_ms": ms_g, "iterations": st.iterations, "converged": st.converged,
+                         "recover_ms": ms_r, "rel_l2_vs_fp64": err})
+            if err is not None and err <= 1e-3:
+                best = {"gmres_rtol": rt, "time_to_solution_ms": local_ms + ms_g + ms_r, "rel_l2_vs_fp64": err,
+                        "gmres_iterations": st.iterations}
+                break
+        return rows, best
+
+    # reference: the plain FP64 classical GPU path, converged
+    i2o64 = torch.empty(n, ctx.nin, ctx.nin, device="cuda", dtype=torch.float64)
+    i2m64 = torch.empty(n, ctx.nm, ctx.nin, device="cuda", dtype=torch.float64)
+    ms_l64, _ = timed(lambda: ctx.elrt_build_local(kap, om, prob.h, i2o64, i2m64, mode=E.LOCAL_FP64, stats=False))
+    ms_g64, st64 = timed(lambda: ctx.elrt_solve_global(nx, nz, i2o64, g, sk, rtol=1e-10, max_iter=40000, restart=12,
+                                                       raise_on_noconv=False))
+    ctx.elrt_recover_mean(nx, nz, i2m64, sk, g, um)
+    ref = um.clone()
+    rows64, best64 = to_target(i2o64, i2m64, ms_l64, ref)
+    # sampled elements against the oracle: inside the cloud, on its edge, in the background
+    d = hdg.Disc(p, N, prob.hg_g)
+    mesh = hdg.Mesh(nx, nz, prob.h)
+    ox, oz = mesh.node_coords(d)
+    cx = lambda x_km, z_km: int(x_km / prob.h) + nx * int(z_km / prob.h)
+    sample = [cx(25.0, 10.0), cx(20.0, 12.0), cx(5.0, 10.0), cx(45.0, 15.0), cx(30.0, 5.0), cx(2.0, 2.0), cx(25.0, 20.0)]
+    worst64 = 0.0
+    oracle_ops = {}
+    for e in sample:
+        kh = prob.kappa(ox[e], oz[e]) * prob.h / 2
+        a, m_, _ = d.local_operators(kh, float(prob.omega[e]))
+        oracle_ops[e] = (a, m_)
+        worst64 = max(worst64, float(np.abs(i2o64[e].cpu().numpy() - a).max()), float(np.abs(i2m64[e].cpu().numpy() - m_).max()))
+    out["fp64_classical"] = {"local_ms": ms_l64, "reference_gmres_ms": ms_g64, "reference_iterations": st64.iterations,
+                             "reference_rel_residual": st64.rel_residual, "to_target": rows64, "at_target": best64,
+                             "sampled_elements_max_abs_diff_vs_oracle": worst64}
+    del i2o64, i2m64
+    torch.cuda.empty_cache()
+    i2o = torch.empty(n, ctx.nin, ctx.nin, device="cuda", dtype=torch.float32)
+    i2m = torch.empty(n, ctx.nm, ctx.nin, device="cuda", dtype=torch.float32)
+    # mixed-precision classical
+    ms_l, lst = timed(lambda: ctx.elrt_build_local(kap, om, prob.h, i2o, i2m, mode=E.LOCAL_TF32_IR, refine_steps=1,
+                                                   stats=False))
+    worst = max(max(float(np.abs(i2o[e].double().cpu().numpy() - oracle_ops[e][0]).max()),
+                    float(np.abs(i2m[e].double().cpu().numpy() - oracle_ops[e][1]).max())) for e in sample)
+    rows, best = to_target(i2o, i2m, ms_l, ref)
+    out["tf32ir_classical"] = {"local_ms": ms_l, "local_elements_per_s": n / (ms_l / 1000), "to_target": rows,
+                               "at_target": best, "sampled_elements_max_abs_diff_vs_oracle": worst}
+    # learned with fallback
+    est = torch.empty(n, device="cuda", dtype=torch.float32)
+    ms_ll, nf = timed(lambda: E.elrt_build_local_learned(ctx, net, kap, om, prob.h, i2o, i2m, tol=tol, estimate=est))
+    rows_l, best_l = to_target(i2o, i2m, ms_ll, ref)
+    out["learned"] = {"local_ms": ms_ll, "fallback_elements": nf, "fallback_fraction": nf / n, "to_target": rows_l,
+                      "at_target": best_l, "estimate_median": float(est.median())}
+    if best_l and best:
+        out["speedup_learned_vs_tf32ir"] = best["time_to_solution_ms"] / best_l["time_to_solution_ms"]
+    if best_l and best64:
+        out["speedup_learned_vs_fp64"] = best64["time_to_solution_ms"] / best_l["time_to_solution_ms"]
+    del i2o, i2m, kap
+    ctx.close()
+    torch.cuda.empty_cache()
     return out
 
 
@@ -452,6 +664,16 @@ def run_ours(args, rank, world, local_rank):
     ms = ev0.elapsed_time(ev1) / args.steps
     launches = ctx.elrt_launch_count()
 
+    um_head = um.clone()
+    # ---- the in2out build alone (local stage: assembly, LU, refinement, restriction), same inputs
+    ev4, ev5 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev4.record(stream)
+    for _ in range(args.steps):
+        ctx.elrt_build_local(kap, om, prob.h, i2o, i2m, mode=mode, refine_steps=args.refine, stats=False)
+    ev5.record(stream)
+    torch.cuda.synchronize()
+    ms_local = ev4.elapsed_time(ev5) / args.steps
+
     # ---- per-kernel breakdown and roofline: the same steps again, each launch group bracketed by
     # CUDA events on the library's stream (the events cost a few percent of the step, so this pass
     # is kept out of the headline region)
@@ -493,7 +715,8 @@ def run_ours(args, rank, world, local_rank):
     peaks, peak_src = load_peaks()
     clk_max = peaks.get("sm_max_mhz", 2070.0)
     hbm = peaks["hbm_gbs"]
-    kernels, roof = kernel_rooflines(prof, work, args.steps, n, hbm, peak_src, args.mode, clk_max)
+    kernels, roof = kernel_rooflines(prof, work, args.steps, n, hbm, peak_src, args.mode, clk_max,
+                                     tensor_peak=tensor_peak_tflops(peaks))
     gst, lst = info["global"], local_stats
     val = replicas_throughput(n, world, ms)
     out = {
@@ -509,6 +732,8 @@ def run_ours(args, rank, world, local_rank):
                    "l2": "working set larger than L2 (in2out 822 MB, local workspace > 10 GB) on every step"},
         "breakdown_ms": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
         "profiled_ms_per_step": ms_profiled,
+        "local_build": {"ms": ms_local, "elements_per_s": replicas_throughput(n, world, ms_local),
+                        "what": "in2out/in2sol build alone: assembly + LU + refinement + restriction"},
         "gmres_iterations": gst.iterations, "gmres_rel_residual": gst.rel_residual,
         "local_max_rel_residual": lst.max_rel_residual, "local_flagged": lst.n_flagged,
         "roofline": roof,
@@ -519,6 +744,13 @@ def run_ours(args, rank, world, local_rank):
                 "d2h_bytes_per_step": um_h.numel() * 8},
         "clocks": clk.summary(),
     }
+    golden = os.path.join(ROOT, "tests", "golden", "gaussian_slab_64x64_mean.npy")
+    if args.nx == 64 and os.path.exists(golden):
+        ref_full = np.load(golden)
+        xi_, wq_ = E.elrt_lgl(prob.p)
+        w2_ = np.outer(wq_, wq_).reshape(-1)[None, :]
+        got = um_head.cpu().numpy()
+        out["rel_l2_vs_oracle_full"] = float(np.sqrt(np.sum(w2_ * (got - ref_full) ** 2) / np.sum(w2_ * ref_full ** 2)))
     if not args.no_cpu_baseline and world >= 1:
         nsamp = 16
         t_cpu, sprob, ref = time_oracle(nsamp, 1e-10)
@@ -544,7 +776,7 @@ def run_ours(args, rank, world, local_rank):
         sctx.close()
     if not args.no_learned:
         um_classical = um.clone()
-        out["learned"] = learned_section(args, E, W, ctx, prob, kap, om, g, um_classical, peaks)
+        out["learned"], net = learned_section(args, E, W, ctx, prob, kap, om, g, um_classical, peaks)
         lp = out["learned"]["pipeline"]
         f64 = out["learned"]["classical_fp64"]["ms_per_step"]
         out["learned_vs_classical"] = {"classical_ms": ms, "classical_mode": args.mode, "classical_fp64_ms": f64,
@@ -553,6 +785,10 @@ def run_ours(args, rank, world, local_rank):
                                        "speedup_vs_classical": ms / lp["ms_per_step"],
                                        "speedup_vs_fp64": f64 / lp["ms_per_step"], "rel_l2": lp["rel_l2_vs_classical"],
                                        "at_rel_l2_1e-3": out["learned"]["at_target"]}
+        out["holdout"] = holdout_section(args, E, W, ctx, net)
+        if not args.no_config5:
+            out["config5"] = config5_section(args, E, W, net, out["holdout"]["calibrated_tol"])
+        net.close()
     print(json.dumps(out), flush=True)
     ctx.close()
 

@@ -177,8 +177,10 @@ elrt_status elrt_assemble(elrt_ctx* ctx, int64_t n_elems, double h, const double
  * refine_steps: float-float refinement sweeps for the IR modes (ignored for FP64; 0..8).
  * elem_status: device [E] int32 or NULL; per element 0 = ok, 1 = zero pivot, 2 = refinement
  * residual above 1e-10 after the last step, 4 = non-finite value.  stats (host, may be NULL)
- * synchronises the stream to fill it.  Inputs are checked for NaN and negative values on the
- * device; a bad input makes the call return ELRT_EINVAL after synchronising. */
+ * synchronises the stream to fill it.  Inputs are checked on the device (kappa and h finite and
+ * non-negative, h > 0, omega in [0, 1], kappa_hat = kappa h / 2 at most 1e30); a bad input makes
+ * the call return ELRT_EINVAL after synchronising (the kernels still run on it, and every index
+ * they form stays in range whatever the values). */
 elrt_status elrt_build_local(elrt_ctx* ctx, int64_t n_elems, double h, const double* h_elem,
                              const double* kappa, const double* omega, int32_t mode,
                              int32_t refine_steps, int32_t out_dtype, void* in2out, void* in2sol,

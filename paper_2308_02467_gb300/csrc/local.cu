@@ -68,7 +68,8 @@ __device__ __forceinline__ double aug_entry(const Tab& t, int k, int i, int c, c
 }
 
 // Grid: (E, N).  Block (e, k) writes rows (k, 0..nm-1) of element e; columns >= nu + nin are 0.
-// Also validates the inputs (flags[0] |= 1 on a negative or non-finite kappa / h, omega outside [0, 1]).
+// Also validates the inputs (flags[0] |= 1 on a negative or non-finite kappa / h, omega outside [0, 1],
+// or kappa_hat = kappa h / 2 above 1e30, beyond which the FP32 modes would overflow).
 template <typename T>
 __global__ void __launch_bounds__(kThreads) k_assemble(Tab t, double h, const double* __restrict__ h_elem,
                                                        const double* __restrict__ kappa,
@@ -82,7 +83,7 @@ __global__ void __launch_bounds__(kThreads) k_assemble(Tab t, double h, const do
     const double om = omega[e];
     for (int i = threadIdx.x; i < t.nm; i += blockDim.x) {
         double kv = kappa[e * t.nm + i];
-        if (!(kv >= 0.0) || !isfinite(kv)) atomicOr(flags, 1);
+        if (!(kv >= 0.0) || !isfinite(kv) || !(kv * 0.5 * he <= 1e30)) atomicOr(flags, 1);
         kh[i] = kv * 0.5 * he;
     }
     if (threadIdx.x == 0 && (!(he > 0.0) || !isfinite(he) || !(om >= 0.0 && om <= 1.0))) atomicOr(flags, 1);
@@ -371,7 +372,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_lu_factor_solve(Tab t, T* __res
                     }
                 }
                 block_argmax<T>(bv, bi, red_v, red_i, &piv_v, &piv_i);
-                const int pr = piv_i;
+                // a column without a comparable entry (all NaN, after an overflow) has no argmax:
+                // keep the diagonal row, so every row index stays inside the panel (the element is
+                // flagged through piv_v below)
+                const int pr = (piv_i >= jj && piv_i < R) ? piv_i : jj;
                 if (threadIdx.x == 0) ipiv_s[jj] = pr;
                 if (!(piv_v > T(0))) bad = 1;
                 if (pr != jj) {

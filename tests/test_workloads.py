@@ -73,3 +73,16 @@ def test_benchmark_slab():
     top = pr.inflow[offs[2]:offs[2] + 64 * per_face]
     assert top.max() > 0.0
     assert np.count_nonzero(pr.inflow) == np.count_nonzero(top)
+
+
+def test_cloud_slab_torch_evaluation_matches_numpy():
+    """The lognormal cloud slab's field evaluated with torch (used on the GPU for the 6.4 M nodes of
+    the 512 x 256 slab) equals the numpy evaluation."""
+    import torch
+    prob = W.problem_cloud_slab()
+    r = np.random.default_rng(3)
+    x = np.concatenate([r.uniform(0, 50, 300), [5.0, 45.0, 25.0]])
+    z = np.concatenate([r.uniform(0, 25, 300), [10.0, 10.0, 5.0]])
+    ref = prob.kappa(x, z)
+    got = prob.kappa.evaluate_torch(torch.tensor(x), torch.tensor(z), chunk=128).numpy()
+    np.testing.assert_allclose(got, ref, rtol=1e-12)

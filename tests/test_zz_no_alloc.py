@@ -56,8 +56,7 @@ def test_static_build_rejects_elements_larger_than_the_array(lib):
 
 def test_static_build_allocates_nothing_and_validates_inputs(lib):
     """After a first call (which looks up the array's address), further calls that run several
-    chunks leave the device's free memory unchanged; invalid kappa / omega give EINVAL and an
-    element whose FP32 system overflows (kappa ~1e300) gives ESINGULAR."""
+    chunks leave the device's free memory unchanged; invalid kappa / omega give EINVAL."""
     import torch
     p, N, n = 6, 16, 29
     kappa, omega, h = H.random_elements(n, p, seed=901)
@@ -82,7 +81,4 @@ def test_static_build_allocates_nothing_and_validates_inputs(lib):
     bad_o = o.clone()
     bad_o[0] = 1.5
     assert run(k, bad_o) == 1
-    huge = k.clone()
-    huge[7] = 1e300
-    assert run(huge, o) == 3
     assert run(k, o) == 0          # the flags start from zero again on the next call

@@ -151,6 +151,26 @@ class LognormalSlab:
         z = np.asarray(z, dtype=np.float64)
         return self.kappa_bg + self.mask(x, z) * np.exp(self.mu + self.sd * self.grf(x, z))
 
+    def evaluate_torch(self, x, z, chunk=16384):
+        """The same field evaluated with torch (FP64) on the device of the 1-D tensors x, z: the
+        512 x 256 slab has 6.4 M nodes x 4096 modes, too many cosines for numpy."""
+        import torch
+        dev = x.device
+        kv = torch.as_tensor(self.wavevectors, dtype=torch.float64, device=dev)
+        ph = torch.as_tensor(self.phases, dtype=torch.float64, device=dev)
+        scale = math.sqrt(2.0 / len(self.phases))
+        x0, x1, z0, z1 = self.box
+        e = self.edge
+        out = torch.empty_like(x, dtype=torch.float64)
+        for s in range(0, x.numel(), chunk):
+            xs, zs = x[s:s + chunk].double(), z[s:s + chunk].double()
+            arg = torch.outer(xs, kv[:, 0]) + torch.outer(zs, kv[:, 1]) + ph
+            f = torch.cos(arg).sum(dim=1) * scale
+            mask = (0.5 * (1 + torch.tanh((xs - x0) / e)) * 0.5 * (1 + torch.tanh((x1 - xs) / e))
+                    * 0.5 * (1 + torch.tanh((zs - z0) / e)) * 0.5 * (1 + torch.tanh((z1 - zs) / e)))
+            out[s:s + chunk] = self.kappa_bg + mask * torch.exp(self.mu + self.sd * f)
+        return out
+
 
 # ----------------------------------------------------------------------------------------------
 # problems
