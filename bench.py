@@ -174,7 +174,10 @@ def parse():
     ap.add_argument("--holdout-elements", type=int, default=20000,
                     help="held-out elements of the element-network workload scored against refined classical labels")
     ap.add_argument("--no-config5", action="store_true",
-                    help="skip the 512x256 lognormal cloud slab (learned vs TF32-IR vs FP64 time-to-solution)")
+                    help="skip the 512x256 lognormal cloud slab (learned vs TF32-IR time-to-solution)")
+    ap.add_argument("--config5-fp64", action="store_true",
+                    help="also time the plain FP64 classical GPU path on the 512x256 slab and use it as the reference "
+                         "(about 4 more minutes: its local stage alone is 7.8e13 FP64 flops)")
     return ap.parse_args()
 
 
@@ -492,11 +495,13 @@ def holdout_section(args, E, W, ctx, net):
 def config5_section(args, E, W, net, tol):
     """Time-to-solution at relative L2 <= 1e-3 on the 512 x 256 lognormal cloud slab (50 km x 25 km,
     p = 6, N = 16, sharp tanh edge, beam at 45 deg): the learned local stage with classical
-    fallback, the TF32-IR classical path and the plain FP64 classical GPU path.  The reference
-    solution is the FP64 path converged to GMRES rtol 1e-10; each path's time-to-solution is its
-    local stage plus the GMRES solve at the loosest tolerance (1e-3, 1e-4, ...) whose mean intensity
-    is within relative L2 1e-3 of the reference, plus the recovery.  Sampled elements' operators
-    are compared with the FP64 oracle (which runs only on those elements)."""
+    fallback and the TF32-IR classical path (with --config5-fp64 also the plain FP64 classical GPU
+    path).  The reference solution is the FP64 path converged to GMRES rtol 1e-10 when it runs,
+    else the TF32-IR path converged to 1e-10 (its operators are within ~6e-8 of the FP64 oracle on
+    sampled elements, reported below).  Each path's time-to-solution is its local stage plus the
+    GMRES solve at the loosest tolerance (1e-3, 1e-4, ...) whose mean intensity is within relative
+    L2 1e-3 of the reference, plus the recovery.  Sampled elements' operators are compared with the
+    FP64 oracle (which runs only on those elements)."""
     import numpy as np
     import torch
     from oracle import hdg
@@ -513,7 +518,7 @@ def config5_section(args, E, W, net, tol):
     torch.cuda.synchronize()
     out = {"workload": "lognormal cloud slab 512x256 elements (50 km x 25 km), p=6, N=16, g=0.85, albedo 0.99, "
                        "tanh edge 50 m, beam 315 deg", "elements": n, "field_gen_s": time.perf_counter() - t0,
-           "kappa_hat_max": float((kap * prob.h / 2).max()), "learned_tol": tol}
+           "kappa_hat_max": float((kap * prob.h / 2).max()), "learned_tol": tol, "gmres_restart": args.restart}
     sk = torch.zeros(n * ctx.nin, device="cuda", dtype=torch.float64)
     um = torch.empty(n, ctx.nm, device="cuda", dtype=torch.float64)
     xi, wq = E.elrt_lgl(p)
@@ -538,55 +543,62 @@ def config5_section(args, E, W, net, tol):
         rows = []
         best = None
         for rt in rtols:
-            ms_g, st = timed(lambda: ctx.elrt_solve_global(nx, nz, i2o, g, sk, rtol=rt, max_iter=40000, restart=12,
-                                                           raise_on_noconv=False))
+            ms_g, st = timed(lambda: ctx.elrt_solve_global(nx, nz, i2o, g, sk, rtol=rt, max_iter=40000,
+                                                           restart=args.restart, raise_on_noconv=False))
             ms_r, _ = timed(lambda: ctx.elrt_recover_mean(nx, nz, i2m, sk, g, um))
-            err = rel_l2(um, ref) if ref is not None else None
+            err = rel_l2(um, ref)
             rows.append({"gmres_rtol": rt, "gmres_ms": ms_g, "iterations": st.iterations, "converged": st.converged,
-                         "recover_ms": ms_r, "rel_l2_vs_fp64": err})
-            if err is not None and err <= 1e-3:
-                best = {"gmres_rtol": rt, "time_to_solution_ms": local_ms + ms_g + ms_r, "rel_l2_vs_fp64": err,
+                         "recover_ms": ms_r, "rel_l2_vs_reference": err})
+            if err <= 1e-3:
+                best = {"gmres_rtol": rt, "time_to_solution_ms": local_ms + ms_g + ms_r, "rel_l2_vs_reference": err,
                         "gmres_iterations": st.iterations}
                 break
         return rows, best
 
-    # reference: the plain FP64 classical GPU path, converged
-    i2o64 = torch.empty(n, ctx.nin, ctx.nin, device="cuda", dtype=torch.float64)
-    i2m64 = torch.empty(n, ctx.nm, ctx.nin, device="cuda", dtype=torch.float64)
-    ms_l64, _ = timed(lambda: ctx.elrt_build_local(kap, om, prob.h, i2o64, i2m64, mode=E.LOCAL_FP64, stats=False))
-    ms_g64, st64 = timed(lambda: ctx.elrt_solve_global(nx, nz, i2o64, g, sk, rtol=1e-10, max_iter=40000, restart=12,
-                                                       raise_on_noconv=False))
-    ctx.elrt_recover_mean(nx, nz, i2m64, sk, g, um)
-    ref = um.clone()
-    rows64, best64 = to_target(i2o64, i2m64, ms_l64, ref)
+    def reference(i2o, i2m):
+        ms, st = timed(lambda: ctx.elrt_solve_global(nx, nz, i2o, g, sk, rtol=1e-10, max_iter=40000,
+                                                     restart=args.restart, raise_on_noconv=False))
+        ctx.elrt_recover_mean(nx, nz, i2m, sk, g, um)
+        return um.clone(), {"gmres_ms": ms, "iterations": st.iterations, "rel_residual": st.rel_residual}
+
     # sampled elements against the oracle: inside the cloud, on its edge, in the background
     d = hdg.Disc(p, N, prob.hg_g)
     mesh = hdg.Mesh(nx, nz, prob.h)
     ox, oz = mesh.node_coords(d)
     cx = lambda x_km, z_km: int(x_km / prob.h) + nx * int(z_km / prob.h)
     sample = [cx(25.0, 10.0), cx(20.0, 12.0), cx(5.0, 10.0), cx(45.0, 15.0), cx(30.0, 5.0), cx(2.0, 2.0), cx(25.0, 20.0)]
-    worst64 = 0.0
     oracle_ops = {}
     for e in sample:
-        kh = prob.kappa(ox[e], oz[e]) * prob.h / 2
-        a, m_, _ = d.local_operators(kh, float(prob.omega[e]))
+        a, m_, _ = d.local_operators(prob.kappa(ox[e], oz[e]) * prob.h / 2, float(prob.omega[e]))
         oracle_ops[e] = (a, m_)
-        worst64 = max(worst64, float(np.abs(i2o64[e].cpu().numpy() - a).max()), float(np.abs(i2m64[e].cpu().numpy() - m_).max()))
-    out["fp64_classical"] = {"local_ms": ms_l64, "reference_gmres_ms": ms_g64, "reference_iterations": st64.iterations,
-                             "reference_rel_residual": st64.rel_residual, "to_target": rows64, "at_target": best64,
-                             "sampled_elements_max_abs_diff_vs_oracle": worst64}
-    del i2o64, i2m64
-    torch.cuda.empty_cache()
+
+    def sampled_diff(i2o, i2m):
+        return max(max(float(np.abs(i2o[e].double().cpu().numpy() - oracle_ops[e][0]).max()),
+                       float(np.abs(i2m[e].double().cpu().numpy() - oracle_ops[e][1]).max())) for e in sample)
+
+    ref = None
+    if args.config5_fp64:
+        i2o64 = torch.empty(n, ctx.nin, ctx.nin, device="cuda", dtype=torch.float64)
+        i2m64 = torch.empty(n, ctx.nm, ctx.nin, device="cuda", dtype=torch.float64)
+        ms_l64, _ = timed(lambda: ctx.elrt_build_local(kap, om, prob.h, i2o64, i2m64, mode=E.LOCAL_FP64, stats=False))
+        ref, ref_info = reference(i2o64, i2m64)
+        rows64, best64 = to_target(i2o64, i2m64, ms_l64, ref)
+        out["reference"] = dict(path="fp64 classical, GMRES rtol 1e-10", **ref_info)
+        out["fp64_classical"] = {"local_ms": ms_l64, "to_target": rows64, "at_target": best64,
+                                 "sampled_elements_max_abs_diff_vs_oracle": sampled_diff(i2o64, i2m64)}
+        del i2o64, i2m64
+        torch.cuda.empty_cache()
     i2o = torch.empty(n, ctx.nin, ctx.nin, device="cuda", dtype=torch.float32)
     i2m = torch.empty(n, ctx.nm, ctx.nin, device="cuda", dtype=torch.float32)
     # mixed-precision classical
-    ms_l, lst = timed(lambda: ctx.elrt_build_local(kap, om, prob.h, i2o, i2m, mode=E.LOCAL_TF32_IR, refine_steps=1,
-                                                   stats=False))
-    worst = max(max(float(np.abs(i2o[e].double().cpu().numpy() - oracle_ops[e][0]).max()),
-                    float(np.abs(i2m[e].double().cpu().numpy() - oracle_ops[e][1]).max())) for e in sample)
+    ms_l, _ = timed(lambda: ctx.elrt_build_local(kap, om, prob.h, i2o, i2m, mode=E.LOCAL_TF32_IR, refine_steps=1,
+                                                 stats=False))
+    if ref is None:
+        ref, ref_info = reference(i2o, i2m)
+        out["reference"] = dict(path="tf32ir classical, GMRES rtol 1e-10", **ref_info)
     rows, best = to_target(i2o, i2m, ms_l, ref)
     out["tf32ir_classical"] = {"local_ms": ms_l, "local_elements_per_s": n / (ms_l / 1000), "to_target": rows,
-                               "at_target": best, "sampled_elements_max_abs_diff_vs_oracle": worst}
+                               "at_target": best, "sampled_elements_max_abs_diff_vs_oracle": sampled_diff(i2o, i2m)}
     # learned with fallback
     est = torch.empty(n, device="cuda", dtype=torch.float32)
     ms_ll, nf = timed(lambda: E.elrt_build_local_learned(ctx, net, kap, om, prob.h, i2o, i2m, tol=tol, estimate=est))
@@ -595,8 +607,8 @@ def config5_section(args, E, W, net, tol):
                       "at_target": best_l, "estimate_median": float(est.median())}
     if best_l and best:
         out["speedup_learned_vs_tf32ir"] = best["time_to_solution_ms"] / best_l["time_to_solution_ms"]
-    if best_l and best64:
-        out["speedup_learned_vs_fp64"] = best64["time_to_solution_ms"] / best_l["time_to_solution_ms"]
+    if best_l and out.get("fp64_classical", {}).get("at_target"):
+        out["speedup_learned_vs_fp64"] = out["fp64_classical"]["at_target"]["time_to_solution_ms"] / best_l["time_to_solution_ms"]
     del i2o, i2m, kap
     ctx.close()
     torch.cuda.empty_cache()

@@ -6,19 +6,24 @@
 // 1e-4 .. 1e3.  A pivot below the tolerance marks the element in its status word.
 //
 // The augmented matrix [A | -B^] of each element (FP32, row-major, leading dimension ld) is
-// factored in panels of 64 columns.  Per panel J:
+// factored in panels of 64 columns, taken in pairs a = [J, J+64), b = [J+64, J+128):
 //   k_diag             (one small block per element): LU of the 64 x 64 diagonal block, published
 //                      as U11, L11^T, U11^T and 1 / diag(U11);
 //   k_rowcol           (blocks of 256 rows or columns per element): L21 from L21 U11 = A21 written
 //                      back to the matrix; U12 from L11 U12 = A12 written back to the matrix and,
-//                      transposed (K-major), to one FP32 side buffer.  On the right-hand-side
-//                      columns this is the forward substitution;
-//   k_tc_update_strip  (tensor cores): C -= L21 U12 with three TF32 products hi*hi + hi*lo +
-//                      lo*hi (FP32-level accuracy).  The FP32 operands come in by TMA (L21 straight
-//                      from the matrix, U12^T from the side buffer) and are split into TF32 high
-//                      and low parts in shared memory by four dedicated warps.
-// The backward substitution and the forward/backward sweeps of the refinement re-solves reuse
-// the stored factors (L21 and U12 in the matrix, the diagonal blocks) with the same kernels.
+//                      transposed (K-major), to one FP32 side buffer whose rows hold both panels of
+//                      the pair.  On the right-hand-side columns this is the forward substitution;
+//   k_tc_update<NK>    (tensor cores): C -= L21 U12 with three TF32 products hi*hi + hi*lo +
+//                      lo*hi (FP32-level accuracy).  Panel a is applied with rank 64 to panel b's
+//                      columns and rows only; once panel b is factored, the rest of the matrix
+//                      takes both panels in one rank-128 update, which moves the C tiles half as
+//                      often as two rank-64 updates.  The FP32 operands come in by TMA (U12^T from
+//                      the side buffer, C from the matrix); the L21 strip goes straight from the
+//                      matrix into tensor memory as TF32 high and low parts.
+// Panels left over after the pairs (nu not a multiple of 128) are factored one at a time with
+// rank-64 updates.  The backward substitution and the forward/backward sweeps of the refinement
+// re-solves reuse the stored factors (L21 and U12 in the matrix, the diagonal blocks) with the same
+// kernels.
 #include <math.h>
 #include <stdio.h>
 
@@ -32,7 +37,8 @@
 
 namespace {
 
-constexpr int NBP = 64;     // panel width (= K of the trailing update)
+constexpr int NBP = 64;     // panel width
+constexpr int UTK = 128;    // K extent of a row of the U12^T side buffer: two consecutive panels
 constexpr int UBN = 64;     // trailing-update tile width (N of the MMAs)
 constexpr int UCB = UBN / 32;  // 32-column (128-byte) boxes of a C tile
 
@@ -175,7 +181,7 @@ __device__ __forceinline__ void tri_solve(float (&a)[NBP], const float* __restri
 // written back to the matrix; the remaining nct tiles are column tiles over columns [c_begin,
 // c_end): y = L11^{-1} a (col_mode 0: factorisation and forward sweep) or y = U11^{-1} a
 // (col_mode 1: backward sweep), written back to the matrix (rows < jb) and, transposed, to the side
-// buffer Ut[e][column][0..63] (zero beyond jb).  Persistent, two blocks per SM (one staging buffer
+// buffer Ut[e][column][koff .. koff + 63] (zero beyond jb).  Persistent, two blocks per SM (one staging buffer
 // each, 128 registers per thread): each block walks its items, copying an item's 64-wide block and
 // the factor of the diagonal block with 16-byte cp.async copies, solving and storing it; the two
 // blocks of an SM overlap one another's copies and stores.  (One block per SM with two staging
@@ -200,7 +206,7 @@ template <int KIND>
 __global__ void __launch_bounds__(256, 2) k_rowcol(int nu, int64_t ld, int64_t estride, float* __restrict__ Mall, int J,
                                                    int jb, const float* __restrict__ Tinv, int npanels, int64_t E,
                                                    int r_begin, int r_end, int nrt, int c_begin, int c_end, int nct,
-                                                   float* __restrict__ Ut) {
+                                                   float* __restrict__ Ut, int koff) {
     constexpr int col_mode = KIND == 2 ? 1 : 0;
     extern __shared__ __align__(16) float sm[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, t = threadIdx.x;
@@ -287,9 +293,9 @@ __global__ void __launch_bounds__(256, 2) k_rowcol(int nu, int64_t ld, int64_t e
                 tri_solve<KIND>(a, T, T + NBP * RS, put);
             }
             __syncthreads();
-            float* ut = Ut + e * ld * NBP;
+            float* ut = Ut + e * ld * UTK + koff;
             for (int cc = warp; cc < nc; cc += 8)
-                for (int i = lane; i < NBP; i += 32) ut[(int64_t)(c0 + cc) * NBP + i] = S[cc * RS + i];
+                for (int i = lane; i < NBP; i += 32) ut[(int64_t)(c0 + cc) * UTK + i] = S[cc * RS + i];
         }
         __syncthreads();  // the buffer is refilled by the next item's copies
     }
@@ -340,44 +346,58 @@ __device__ __forceinline__ void mma_tf32_ta(uint32_t d_tmem, uint32_t a_tmem, ui
 }
 
 
-// Persistent trailing update: one CTA per SM walks the work items (element, 128-row strip) of the
-// launch, the strips of one element consecutively (their U12^T tiles are shared through L2).  The
-// L21 strip of an item (columns J .. J+63 of its 128 rows, FP32, straight from the matrix) lives
-// in tensor memory as TF32 high and low parts, double-buffered, so the next item's strip is
-// prepared while the current item's tiles run; shared memory holds only the ring of 64-column
-// tiles (FP32 U12^T tile, its low part, the C tile as two 32-column boxes), three stages deep,
-// which does not drain between items.  (32-column tiles in a six-stage ring left the MMA thread
-// busy most of the time issuing N = 32 instructions; N = 64 halves the instructions per byte.)
-//   warp 0       TMA producer of the tiles;
+// Persistent trailing update C -= L U of rank NK = 64 (one panel) or 128 (two consecutive panels,
+// the second already factored against the first): one CTA per SM walks the work items (element,
+// 128-row strip) of the launch, the strips of one element consecutively (their U12^T tiles are
+// shared through L2).  The L21 strip of an item (columns J .. J+NK-1 of its 128 rows, FP32,
+// straight from the matrix) lives in tensor memory as TF32 high and low parts (double-buffered at
+// NK = 64, so the next item's strip is prepared while the current item's tiles run; single at
+// NK = 128, where the two parts fill 256 of the 512 columns).  Shared memory holds two rings that
+// never drain between items: the U12^T tiles (64 columns x NK, FP32 as its own high part plus the
+// low part; 3 stages at NK = 64, 2 at NK = 128) and the C tiles (128 rows x 64 columns as two
+// 128-byte-wide boxes, 3 stages).  A U stage is released by the MMA commit, a C stage by the store
+// warp, so neither ring waits for the other.  Doubling K halves the C bytes per flop: at NK = 64
+// the update is bound by the C traffic (48 TF32 flops per byte issued), at NK = 128 the tensor
+// pipe and HBM are about balanced.
+//   warp 0       TMA producer of both rings;
 //   warp 1       TMEM allocation; one thread issues the 3xTF32 MMAs (hi*hi + hi*lo + lo*hi,
-//                M = 128, N = 64, A from tensor memory) into one of two TMEM accumulators;
+//                M = 128, N = 64, K = 8, A from tensor memory) into one of two TMEM accumulators;
 //   warps 2-5    epilogue: accumulator (tcgen05.ld) and staged C tile -> C - L U, written back
 //                into the staged tile;
-//   warp 14      stores each finished tile with TMA tensor stores (the store map's extents
-//                are r_end rows and c_end columns, so rows and columns outside the update are
-//                clipped) and releases the stage once the store has read it;
+//   warp 14      stores each finished tile with TMA tensor stores (the store map's extents are
+//                r_end rows and c_end columns, so rows and columns outside the update are
+//                clipped) and releases the C stage once the store has read it;
 //   warps 6-9    strip preparation: each thread loads one row of the strip (columns at or beyond
 //                jb are 0), splits it and writes it to its TMEM lane (tcgen05.st);
-//   warps 10-13  write the low TF32 part of the staged FP32 U12^T tile (the tile itself serves as
+//   warps 10-13  write the low TF32 part of each staged FP32 U12^T tile (the tile itself serves as
 //                the high part: the MMA thread issues hi*hi and lo*hi on it at once, hi*lo after).
-// A stage is free again after the MMA commit and the store warp (count 2); a strip
-// buffer after the MMA commit of its item's last tile.  Every wait is bounded; on a timeout the
-// CTA records a code in *err, stops issuing work, lets its copies land and frees its TMEM.
-constexpr int kUStages = 3;
-struct StripSmem {
-    static constexpr int B_KB = UBN * 32 * 4;                 // one 32-column box of a U12^T tile
-    static constexpr int C_BOX = 128 * 32 * 4;                // one 32-column box of the C tile
-    static constexpr int STAGE = 4 * B_KB + UCB * C_BOX;      // B {hi, lo} x 2 k-blocks + C tile
-    static constexpr int STAGE_TX = 2 * B_KB + UCB * C_BOX;   // FP32 U12^T tile + C tile per stage
-    static constexpr int BYTES = kUStages * STAGE;
+// U12^T comes from the side buffer [E][ld][128] (column-major U12 of the panel pair: K offset 0
+// for the first panel, 64 for the second); an NK = 64 update reads the half at K offset koff.
+// Every wait is bounded; on a timeout the CTA records a code in *err, stops issuing work, lets its
+// copies land and frees its TMEM.
+template <int NK>
+struct UpdCfg {
+    static constexpr int KB = NK / 32;             // 32-wide K boxes of a U12^T tile
+    static constexpr int U_BOX = UBN * 32 * 4;     // one box: 64 rows x 128 bytes
+    static constexpr int U_STAGE = 2 * KB * U_BOX; // FP32 tile + its low part
+    static constexpr int U_TX = KB * U_BOX;
+    static constexpr int C_BOX = 128 * 32 * 4;     // one 32-column box of the C tile
+    static constexpr int C_STAGE = UCB * C_BOX;
+    static constexpr int NU = NK == 64 ? 3 : 2;    // U stages
+    static constexpr int NC = 3;                   // C stages
+    static constexpr int NSB = NK == 64 ? 2 : 1;   // strip buffers in tensor memory
+    static constexpr int BYTES = NU * U_STAGE + NC * C_STAGE;
     static constexpr int TOTAL = BYTES + 1024 + 256;
+    // tensor memory: accumulators at columns [0, 2 UBN); strip buffer b: high part at
+    // 2 UBN + 2 NK b, low part NK columns further
+    static constexpr uint32_t strip_col(int b, int lo) {
+        return (uint32_t)(2 * UBN) + (uint32_t)(2 * NK) * (uint32_t)b + (uint32_t)NK * (uint32_t)lo;
+    }
 };
-static_assert(StripSmem::TOTAL <= 227 * 1024, "trailing-update shared memory");
+static_assert(UpdCfg<64>::TOTAL <= 227 * 1024 && UpdCfg<128>::TOTAL <= 227 * 1024, "trailing-update shared memory");
+static_assert(UpdCfg<64>::strip_col(1, 1) + 64 <= 512 && UpdCfg<128>::strip_col(0, 1) + 128 <= 512, "tensor memory");
 constexpr int kStripThreads = 480;
-// tensor memory: accumulators at columns [0, 2 UBN); strip buffer b: high part at 128 + 128 b,
-// low part 64 columns further
 constexpr uint32_t kTmemCols = 512;
-__host__ __device__ constexpr uint32_t strip_col(int b, int lo) { return 128u + 128u * (uint32_t)b + 64u * (uint32_t)lo; }
 
 // Low parts of one 128-byte-swizzled box of `rows` rows x 32 FP32: lo = v - tf32(v) at the same
 // offset in `lo`.  The box itself stays FP32: kind::tf32 MMAs read the high 19 bits of each FP32
@@ -395,22 +415,27 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
 }
 
+template <int NK>
 __global__ void __launch_bounds__(kStripThreads, 1)
-    k_tc_update_strip(const __grid_constant__ CUtensorMap tM, const __grid_constant__ CUtensorMap tU,
-                      const __grid_constant__ CUtensorMap tS, float* __restrict__ Mall, int nu, int64_t ld,
-                      int64_t estride, int64_t E, int J, int jb, int r0, int r_end, int c0, int c_end,
-                      int* __restrict__ err) {
+    k_tc_update(const __grid_constant__ CUtensorMap tM, const __grid_constant__ CUtensorMap tU,
+                const __grid_constant__ CUtensorMap tS, float* __restrict__ Mall, int nu, int64_t ld, int64_t estride,
+                int64_t E, int J, int jb, int koff, int r0, int r_end, int c0, int c_end, int* __restrict__ err) {
+    using Cfg = UpdCfg<NK>;
+    constexpr int NU = Cfg::NU, NC = Cfg::NC, NSB = Cfg::NSB, KB = Cfg::KB;
     extern __shared__ __align__(1024) unsigned char ssm_raw[];
     unsigned char* base = (unsigned char*)(((uintptr_t)ssm_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char* stage0 = base;                          // [kUStages]: Bh (2 boxes), Bl (2 boxes), C
-    uint64_t* a_ready = (uint64_t*)(base + StripSmem::BYTES);  // [2]
-    uint64_t* a_empty = a_ready + 2;                       // [2]
-    uint64_t* full = a_empty + 2;                          // [kUStages]
-    uint64_t* bready = full + kUStages;                    // [kUStages]
-    uint64_t* empty = bready + kUStages;                   // [kUStages]
-    uint64_t* cdone = empty + kUStages;                    // [kUStages]
-    uint64_t* acc_full = cdone + kUStages;                 // [2]
-    uint64_t* acc_empty = acc_full + 2;                    // [2]
+    unsigned char* ustage0 = base;                                  // [NU]: FP32 tile (KB boxes), low part (KB boxes)
+    unsigned char* cstage0 = base + NU * Cfg::U_STAGE;              // [NC]: C tile (UCB boxes)
+    uint64_t* a_ready = (uint64_t*)(base + Cfg::BYTES);            // [NSB]
+    uint64_t* a_empty = a_ready + NSB;                              // [NSB]
+    uint64_t* u_full = a_empty + NSB;                               // [NU]
+    uint64_t* u_ready = u_full + NU;                                // [NU]
+    uint64_t* u_empty = u_ready + NU;                               // [NU]
+    uint64_t* c_full = u_empty + NU;                                // [NC]
+    uint64_t* c_done = c_full + NC;                                 // [NC]
+    uint64_t* c_empty = c_done + NC;                                // [NC]
+    uint64_t* acc_full = c_empty + NC;                              // [2]
+    uint64_t* acc_empty = acc_full + 2;                             // [2]
     uint32_t* tmem_slot = (uint32_t*)(acc_empty + 2);
     volatile int* abort = (volatile int*)(tmem_slot + 1);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -418,17 +443,23 @@ __global__ void __launch_bounds__(kStripThreads, 1)
     const int64_t W = (int64_t)nstrips * E;
     const int ntile = (c_end - c0 + UBN - 1) / UBN;
     if (threadIdx.x == 0) {
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < NSB; ++i) {
             tc::mbar_init(&a_ready[i], 4);
             tc::mbar_init(&a_empty[i], 1);
+        }
+        for (int i = 0; i < NU; ++i) {
+            tc::mbar_init(&u_full[i], 1);
+            tc::mbar_init(&u_ready[i], 4);
+            tc::mbar_init(&u_empty[i], 1);
+        }
+        for (int i = 0; i < NC; ++i) {
+            tc::mbar_init(&c_full[i], 1);
+            tc::mbar_init(&c_done[i], 4);
+            tc::mbar_init(&c_empty[i], 1);
+        }
+        for (int i = 0; i < 2; ++i) {
             tc::mbar_init(&acc_full[i], 1);
             tc::mbar_init(&acc_empty[i], 4);
-        }
-        for (int i = 0; i < kUStages; ++i) {
-            tc::mbar_init(&full[i], 1);
-            tc::mbar_init(&bready[i], 4);
-            tc::mbar_init(&empty[i], 2);
-            tc::mbar_init(&cdone[i], 4);
         }
         *abort = 0;
         tc::fence_barrier_init();
@@ -441,7 +472,7 @@ __global__ void __launch_bounds__(kStripThreads, 1)
     __syncthreads();
     tc::tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    int committed = 0, issued_t = 0;
+    int committed = 0, issued_u = 0, issued_c = 0;
     if (warp == 0 && lane == 0) {
         bool ok = true;
         int g = 0;
@@ -449,18 +480,24 @@ __global__ void __launch_bounds__(kStripThreads, 1)
             const int64_t e = w / nstrips;
             const int m0 = r0 + (int)(w - e * nstrips) * 128;
             for (int t = 0; t < ntile; ++t, ++g) {
-                const int s = g % kUStages;
-                if (!tc::mbar_wait(&empty[s], ((g / kUStages) & 1) ^ 1, abort)) {
+                const int su = g % NU, sc = g % NC;
+                const int n0 = c0 + t * UBN;
+                if (!tc::mbar_wait(&u_empty[su], ((g / NU) & 1) ^ 1, abort)) {
                     ok = false;
                     break;
                 }
-                unsigned char* st = stage0 + s * StripSmem::STAGE;
-                const int n0 = c0 + t * UBN;
-                tc::mbar_expect_tx(&full[s], StripSmem::STAGE_TX);
-                for (int kb = 0; kb < 2; ++kb) tma_load_3d(&tU, &full[s], st + kb * StripSmem::B_KB, kb * 32, n0, (int)e);
-                for (int cb = 0; cb < UCB; ++cb)
-                    tma_load_3d(&tM, &full[s], st + 4 * StripSmem::B_KB + cb * StripSmem::C_BOX, n0 + 32 * cb, m0, (int)e);
-                ++issued_t;
+                unsigned char* us = ustage0 + su * Cfg::U_STAGE;
+                tc::mbar_expect_tx(&u_full[su], Cfg::U_TX);
+                for (int kb = 0; kb < KB; ++kb) tma_load_3d(&tU, &u_full[su], us + kb * Cfg::U_BOX, koff + kb * 32, n0, (int)e);
+                ++issued_u;
+                if (!tc::mbar_wait(&c_empty[sc], ((g / NC) & 1) ^ 1, abort)) {
+                    ok = false;
+                    break;
+                }
+                unsigned char* cs = cstage0 + sc * Cfg::C_STAGE;
+                tc::mbar_expect_tx(&c_full[sc], Cfg::C_STAGE);
+                for (int cb = 0; cb < UCB; ++cb) tma_load_3d(&tM, &c_full[sc], cs + cb * Cfg::C_BOX, n0 + 32 * cb, m0, (int)e);
+                ++issued_c;
             }
         }
         if (!ok) {
@@ -472,28 +509,28 @@ __global__ void __launch_bounds__(kStripThreads, 1)
         bool ok = true;
         int g = 0, i = 0;
         for (int64_t w = blockIdx.x; w < W && ok; w += gridDim.x, ++i) {
-            const int ab = i & 1;
-            if (!tc::mbar_wait(&a_ready[ab], (i >> 1) & 1, abort)) {
+            const int ab = i % NSB;
+            if (!tc::mbar_wait(&a_ready[ab], (i / NSB) & 1, abort)) {
                 ok = false;
                 break;
             }
             tc::tc_fence_after();
-            const uint32_t a_hi = tmem + strip_col(ab, 0), a_lo = tmem + strip_col(ab, 1);
+            const uint32_t a_hi = tmem + Cfg::strip_col(ab, 0), a_lo = tmem + Cfg::strip_col(ab, 1);
             for (int t = 0; t < ntile; ++t, ++g) {
-                const int s = g % kUStages, a = g & 1;
+                const int su = g % NU, a = g & 1;
                 if (!tc::mbar_wait(&acc_empty[a], ((g >> 1) & 1) ^ 1, abort) ||
-                    !tc::mbar_wait(&full[s], (g / kUStages) & 1, abort)) {
+                    !tc::mbar_wait(&u_full[su], (g / NU) & 1, abort)) {
                     ok = false;
                     break;
                 }
                 tc::tc_fence_after();
-                unsigned char* st = stage0 + s * StripSmem::STAGE;
+                unsigned char* us = ustage0 + su * Cfg::U_STAGE;
                 const uint32_t d = tmem + (uint32_t)(a * UBN);
                 uint32_t acc = 0;
                 // hi*hi and lo*hi as soon as the FP32 U12^T tile has landed (it is its own high
                 // part), then hi*lo once the splitters have written the low part
-                for (int kb = 0; kb < 2; ++kb) {
-                    const uint64_t bh = tc::sw128_desc(tc::smem_u32(st + kb * StripSmem::B_KB));
+                for (int kb = 0; kb < KB; ++kb) {
+                    const uint64_t bh = tc::sw128_desc(tc::smem_u32(us + kb * Cfg::U_BOX));
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {  // K = 8 per instruction
                         const uint32_t kc = (uint32_t)(kb * 32 + k * 8);
@@ -502,17 +539,17 @@ __global__ void __launch_bounds__(kStripThreads, 1)
                         mma_tf32_ta(d, a_lo + kc, bh + 2 * k, idesc, 1);
                     }
                 }
-                if (!tc::mbar_wait(&bready[s], (g / kUStages) & 1, abort)) {
+                if (!tc::mbar_wait(&u_ready[su], (g / NU) & 1, abort)) {
                     ok = false;
                     break;
                 }
                 tc::tc_fence_after();
-                for (int kb = 0; kb < 2; ++kb) {
-                    const uint64_t bl = tc::sw128_desc(tc::smem_u32(st + (2 + kb) * StripSmem::B_KB));
+                for (int kb = 0; kb < KB; ++kb) {
+                    const uint64_t bl = tc::sw128_desc(tc::smem_u32(us + (KB + kb) * Cfg::U_BOX));
 #pragma unroll
                     for (int k = 0; k < 4; ++k) mma_tf32_ta(d, a_hi + (uint32_t)(kb * 32 + k * 8), bl + 2 * k, idesc, 1);
                 }
-                tc::mma_commit(&empty[s]);
+                tc::mma_commit(&u_empty[su]);
                 tc::mma_commit(&acc_full[a]);
                 ++committed;
             }
@@ -529,8 +566,8 @@ __global__ void __launch_bounds__(kStripThreads, 1)
         bool ok = true;
         int i = 0;
         for (int64_t w = blockIdx.x; w < W && ok; w += gridDim.x, ++i) {
-            const int ab = i & 1;
-            if (!__all_sync(0xffffffffu, tc::mbar_wait(&a_empty[ab], ((i >> 1) & 1) ^ 1, abort) && !*abort)) {
+            const int ab = i % NSB;
+            if (!__all_sync(0xffffffffu, tc::mbar_wait(&a_empty[ab], ((i / NSB) & 1) ^ 1, abort) && !*abort)) {
                 ok = false;
                 break;
             }
@@ -539,7 +576,7 @@ __global__ void __launch_bounds__(kStripThreads, 1)
             const int m = r0 + (int)(w - e * nstrips) * 128 + row;
             const float* src = Mall + e * estride + (int64_t)m * ld + J;
 #pragma unroll
-            for (int half = 0; half < 2; ++half) {
+            for (int half = 0; half < KB; ++half) {
                 float v[32], lo[32];
 #pragma unroll
                 for (int k4 = 0; k4 < 8; ++k4) {
@@ -557,8 +594,8 @@ __global__ void __launch_bounds__(kStripThreads, 1)
                     lo[k] = v[k] - h;
                     v[k] = h;
                 }
-                tmem_st32(tmem + lane_off + strip_col(ab, 0) + half * 32, v);
-                tmem_st32(tmem + lane_off + strip_col(ab, 1) + half * 32, lo);
+                tmem_st32(tmem + lane_off + Cfg::strip_col(ab, 0) + half * 32, v);
+                tmem_st32(tmem + lane_off + Cfg::strip_col(ab, 1) + half * 32, lo);
             }
             tmem_st_wait();
             tc::tc_fence_before();
@@ -577,18 +614,18 @@ __global__ void __launch_bounds__(kStripThreads, 1)
                 const int64_t e = w / nstrips;
                 const int m0 = r0 + (int)(w - e * nstrips) * 128;
                 for (int t = 0; t < ntile; ++t, ++g) {
-                    const int s = g % kUStages;
-                    if (!tc::mbar_wait(&cdone[s], (g / kUStages) & 1, abort)) {
+                    const int sc = g % NC;
+                    if (!tc::mbar_wait(&c_done[sc], (g / NC) & 1, abort)) {
                         ok = false;
                         break;
                     }
                     for (int cb = 0; cb < UCB; ++cb)  // (a box wholly beyond c_end is not stored)
                         if (c0 + t * UBN + 32 * cb < c_end)
-                            tma_store_3d(&tS, stage0 + s * StripSmem::STAGE + 4 * StripSmem::B_KB + cb * StripSmem::C_BOX,
-                                         c0 + t * UBN + 32 * cb, m0, (int)e);
+                            tma_store_3d(&tS, cstage0 + sc * Cfg::C_STAGE + cb * Cfg::C_BOX, c0 + t * UBN + 32 * cb, m0,
+                                         (int)e);
                     bulk_commit();
                     bulk_wait_read0();  // the stage may be refilled once the store has read it
-                    mbar_arrive(&empty[s]);
+                    mbar_arrive(&c_empty[sc]);
                 }
             }
             bulk_wait0();
@@ -603,18 +640,18 @@ __global__ void __launch_bounds__(kStripThreads, 1)
         int g = 0;
         for (int64_t w = blockIdx.x; w < W && ok; w += gridDim.x) {
             for (int t = 0; t < ntile; ++t, ++g) {
-                const int s = g % kUStages;
-                if (!__all_sync(0xffffffffu, tc::mbar_wait(&full[s], (g / kUStages) & 1, abort) && !*abort)) {
+                const int su = g % NU;
+                if (!__all_sync(0xffffffffu, tc::mbar_wait(&u_full[su], (g / NU) & 1, abort) && !*abort)) {
                     ok = false;
                     break;
                 }
-                unsigned char* st = stage0 + s * StripSmem::STAGE;
-                for (int kb = 0; kb < 2; ++kb)
-                    split_lo(st + kb * StripSmem::B_KB, st + (2 + kb) * StripSmem::B_KB, UBN, tid, 128);
+                unsigned char* us = ustage0 + su * Cfg::U_STAGE;
+                for (int kb = 0; kb < KB; ++kb)
+                    split_lo(us + kb * Cfg::U_BOX, us + (KB + kb) * Cfg::U_BOX, UBN, tid, 128);
                 // generic-proxy writes, read next by the tensor cores (async proxy)
                 tc::fence_proxy_async();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&bready[s]);
+                if (lane == 0) mbar_arrive(&u_ready[su]);
             }
         }
         if (!ok && lane == 0) {
@@ -628,15 +665,15 @@ __global__ void __launch_bounds__(kStripThreads, 1)
         bool ok = true;
         for (int64_t w = blockIdx.x; w < W && ok; w += gridDim.x) {
             for (int t = 0; t < ntile; ++t, ++g) {
-                const int s = g % kUStages, a = g & 1;
+                const int sc = g % NC, a = g & 1;
                 ok = __all_sync(0xffffffffu, tc::mbar_wait(&acc_full[a], (g >> 1) & 1, abort) &&
-                                                 tc::mbar_wait(&full[s], (g / kUStages) & 1, abort) && !*abort);
+                                                 tc::mbar_wait(&c_full[sc], (g / NC) & 1, abort) && !*abort);
                 if (!ok) {
                     if (err && lane == 0) atomicOr(err, 256);
                     break;
                 }
                 tc::tc_fence_after();
-                const unsigned char* cst = stage0 + s * StripSmem::STAGE + 4 * StripSmem::B_KB;
+                unsigned char* cst = cstage0 + sc * Cfg::C_STAGE;
 #pragma unroll
                 for (int cb = 0; cb < UCB; ++cb) {
                     float d[32];
@@ -650,7 +687,7 @@ __global__ void __launch_bounds__(kStripThreads, 1)
                     // C box cb in shared memory: rows m0 .. m0 + 127 of columns n0 + 32 cb .. + 31,
                     // 128-byte rows with the 16-byte chunk index XOR-ed by (row % 8); C - L U goes
                     // back in place
-                    unsigned char* crow = const_cast<unsigned char*>(cst) + cb * StripSmem::C_BOX + row * 128;
+                    unsigned char* crow = cst + cb * Cfg::C_BOX + row * 128;
 #pragma unroll
                     for (int ch = 0; ch < 8; ++ch) {
                         float4* p = reinterpret_cast<float4*>(crow + ((ch ^ (row & 7)) << 4));
@@ -665,7 +702,7 @@ __global__ void __launch_bounds__(kStripThreads, 1)
                 __syncwarp();
                 if (lane == 0) {
                     mbar_arrive(&acc_empty[a]);
-                    mbar_arrive(&cdone[s]);
+                    mbar_arrive(&c_done[sc]);
                 }
             }
         }
@@ -673,9 +710,14 @@ __global__ void __launch_bounds__(kStripThreads, 1)
     tc::tc_fence_before();
     __syncthreads();
     if (warp == 0 && lane == 0) {  // let every copy this CTA issued land before the CTA exits
-        for (int q = (issued_t > kUStages ? issued_t - kUStages : 0); q < issued_t; ++q) {
+        for (int q = (issued_u > NU ? issued_u - NU : 0); q < issued_u; ++q) {
             const long long t1 = clock64();
-            while (!tc::mbar_try_wait(&full[q % kUStages], (q / kUStages) & 1) && clock64() - t1 < tc::kWaitCycles / 4) {
+            while (!tc::mbar_try_wait(&u_full[q % NU], (q / NU) & 1) && clock64() - t1 < tc::kWaitCycles / 4) {
+            }
+        }
+        for (int q = (issued_c > NC ? issued_c - NC : 0); q < issued_c; ++q) {
+            const long long t1 = clock64();
+            while (!tc::mbar_try_wait(&c_full[q % NC], (q / NC) & 1) && clock64() - t1 < tc::kWaitCycles / 4) {
             }
         }
     }
@@ -711,10 +753,10 @@ bool enc_ready() {
     return g_enc != nullptr;
 }
 
-// [E][rows][64] FP32 side buffer, box 32 (k) x box_rows x 1 element, 128-byte swizzle
+// [E][rows][UTK] FP32 side buffer, box 32 (k) x box_rows x 1 element, 128-byte swizzle
 bool map3(CUtensorMap* m, const float* p, int64_t rows, int64_t E, int box_rows) {
-    cuuint64_t dims[3] = {(cuuint64_t)NBP, (cuuint64_t)rows, (cuuint64_t)E};
-    cuuint64_t strides[2] = {(cuuint64_t)NBP * 4, (cuuint64_t)rows * NBP * 4};
+    cuuint64_t dims[3] = {(cuuint64_t)UTK, (cuuint64_t)rows, (cuuint64_t)E};
+    cuuint64_t strides[2] = {(cuuint64_t)UTK * 4, (cuuint64_t)rows * UTK * 4};
     cuuint32_t box[3] = {32, (cuuint32_t)box_rows, 1};
     cuuint32_t es[3] = {1, 1, 1};
     return g_enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, (void*)p, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -740,19 +782,21 @@ struct TcMaps {
 };
 
 // Trailing update C -= L U over rows [r0, r_end) and columns [c0, c_end) of every element, with
-// L = M[rows, J .. J+jb) and U^T from the side buffer.  Algorithmic bytes: C read and written, the
-// FP32 L strip (R x 64) and U^T tile (C x 64).
+// L = M[rows, J .. J+k) and U^T from the side buffer at K offset koff: rank k = jb <= 64 (one panel,
+// kernel NK = 64) or k = 128 (a pair of full panels, NK = 128, koff 0).  Algorithmic bytes: C read
+// and written, the FP32 L strip (R x k) and U^T tile (C x k); useful flops 2 R C k.
+template <int NK>
 elrt_status update(elrt_ctx* ctx, const TcMaps& mp, float* M, int64_t ld, int64_t estride, int64_t E, int J, int jb,
-                   int r0, int r_end, int c0, int c_end, int* err) {
+                   int koff, int r0, int r_end, int c0, int c_end, int* err) {
     if (r_end <= r0 || c_end <= c0) return ELRT_OK;
     const double R = r_end - r0, C = c_end - c0;
-    ProfScope ps(ctx, "lu_tc_update", 1, (double)E * (8.0 * R * C + 4.0 * (R + C) * NBP), (double)E * 2.0 * R * C * jb);
+    ProfScope ps(ctx, "lu_tc_update", 1, (double)E * (8.0 * R * C + 4.0 * (R + C) * jb), (double)E * 2.0 * R * C * jb);
     CUtensorMap tS;  // stores: rows [0, r_end), columns [0, c_end)
     if (!mapM(&tS, M, r_end, c_end, ld, estride, E)) return ctx_fail(ctx, ELRT_EINVAL, "tensor map encoding failed");
     const int64_t items = (int64_t)((r_end - r0 + 127) / 128) * E;
     const unsigned grid = (unsigned)std::min<int64_t>(items, 152);
-    k_tc_update_strip<<<grid, kStripThreads, StripSmem::TOTAL, ctx->stream>>>(mp.m, mp.u, tS, M, ctx->tab.nu, ld, estride,
-                                                                              E, J, jb, r0, r_end, c0, c_end, err);
+    k_tc_update<NK><<<grid, kStripThreads, UpdCfg<NK>::TOTAL, ctx->stream>>>(mp.m, mp.u, tS, M, ctx->tab.nu, ld, estride,
+                                                                             E, J, jb, koff, r0, r_end, c0, c_end, err);
     return cuda_check(ctx, cudaGetLastError(), "tc update launch");
 }
 
@@ -771,7 +815,9 @@ elrt_status prepare(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, const 
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rowcol<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, RC_SMEM);
         if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rowcol<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, RC_SMEM);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_tc_update_strip, cudaFuncAttributeMaxDynamicSharedMemorySize, StripSmem::TOTAL);
+            e = cudaFuncSetAttribute(k_tc_update<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, UpdCfg<64>::TOTAL);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_tc_update<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, UpdCfg<128>::TOTAL);
         if (e != cudaSuccess) return cuda_check(ctx, e, "smem attribute");
         attr_done = true;
     }
@@ -781,7 +827,7 @@ elrt_status prepare(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, const 
 int panels_of(int nu) { return (nu + NBP - 1) / NBP; }
 
 elrt_status rowcol(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, int64_t E, int J, int jb, const float* Tinv,
-                   int r_begin, int r_end, int c_begin, int c_end, int col_mode, float* Ut) {
+                   int r_begin, int r_end, int c_begin, int c_end, int col_mode, float* Ut, int koff = 0) {
     const int nrt = r_end > r_begin ? (r_end - r_begin + PTILE - 1) / PTILE : 0;
     const int nct = c_end > c_begin ? (c_end - c_begin + PTILE - 1) / PTILE : 0;
     if (nrt + nct == 0) return ELRT_OK;
@@ -795,16 +841,16 @@ elrt_status rowcol(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, int64_t
     if (nrt > 0) {  // items: (element, row tile)
         const unsigned grid = (unsigned)std::min<int64_t>(E * nrt, 2 * 152);
         k_rowcol<0><<<grid, 256, RC_SMEM, ctx->stream>>>(nu, ld, estride, M, J, jb, Tinv, np, E, r_begin, r_end, nrt,
-                                                         c_begin, c_end, 0, Ut);
+                                                         c_begin, c_end, 0, Ut, koff);
     }
     if (nct > 0) {  // items: (element, column tile)
         const unsigned grid = (unsigned)std::min<int64_t>(E * nct, 2 * 152);
         if (col_mode == 0)
             k_rowcol<1><<<grid, 256, RC_SMEM, ctx->stream>>>(nu, ld, estride, M, J, jb, Tinv, np, E, r_begin, r_end, 0,
-                                                             c_begin, c_end, nct, Ut);
+                                                             c_begin, c_end, nct, Ut, koff);
         else
             k_rowcol<2><<<grid, 256, RC_SMEM, ctx->stream>>>(nu, ld, estride, M, J, jb, Tinv, np, E, r_begin, r_end, 0,
-                                                             c_begin, c_end, nct, Ut);
+                                                             c_begin, c_end, nct, Ut, koff);
     }
     return cuda_check(ctx, cudaGetLastError(), "rowcol launch");
 }
@@ -818,7 +864,7 @@ elrt_status backward_sweep_tc(elrt_ctx* ctx, const TcMaps& mp, float* M, int64_t
     for (int J = last; J >= 0; J -= NBP) {
         const int jb = std::min(NBP, nu - J);
         elrt_status s = rowcol(ctx, M, ld, estride, E, J, jb, Tinv, 0, 0, nu, nu + nin, 1, Ut);
-        if (!s) s = update(ctx, mp, M, ld, estride, E, J, jb, 0, J, nu, nu + nin, err);
+        if (!s) s = update<64>(ctx, mp, M, ld, estride, E, J, jb, 0, 0, J, nu, nu + nin, err);
         if (s) return s;
     }
     return ELRT_OK;
@@ -831,8 +877,16 @@ struct Side {
 Side carve(float* side, int64_t E, int64_t ld) {
     Side sd;
     sd.Ut = side;
-    sd.Tinv = sd.Ut + (size_t)E * ld * NBP;
+    sd.Tinv = sd.Ut + (size_t)E * ld * UTK;
     return sd;
+}
+
+// LU of the 64 x 64 diagonal block at column J (published to Tinv)
+void diag_block(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, int64_t E, int J, int jb, float* Tinv, int* estat) {
+    const int nu = ctx->tab.nu;
+    const double b3 = (double)jb * jb * jb;
+    ProfScope ps(ctx, "lu_tc_diag", 1, (double)E * (8.0 * jb * jb + 4.0 * kInvMats * NBP * NBP), (double)E * 2.0 / 3.0 * b3);
+    k_diag<<<(unsigned)E, kDiagThreads, 0, ctx->stream>>>(nu, ld, estride, M, J, jb, Tinv, panels_of(nu), estat, 1e-6f);
 }
 
 }  // namespace
@@ -846,18 +900,28 @@ elrt_status tc_lu_factor_solve(elrt_ctx* ctx, float* M, int64_t ld, int64_t estr
     TcMaps mp;
     elrt_status s = prepare(ctx, M, ld, estride, sd.Ut, E, &mp);
     if (s) return s;
-    for (int J = 0; J < nu; J += NBP) {
+    int J = 0;
+    // pairs of full panels a = [J, J+64), b = [J+64, J+128): panel a is factored and applied to
+    // panel b's columns and rows only (two narrow rank-64 updates), panel b is factored, and the
+    // rest of the matrix takes both in one rank-128 update (half the C traffic of two rank-64 ones)
+    for (; J + 2 * NBP <= nu; J += 2 * NBP) {
+        const int Jb = J + NBP, Jn = J + 2 * NBP;
+        diag_block(ctx, M, ld, estride, E, J, NBP, sd.Tinv, estat);
+        s = rowcol(ctx, M, ld, estride, E, J, NBP, sd.Tinv, Jb, nu, Jb, ncols, 0, sd.Ut, 0);
+        if (!s) s = update<64>(ctx, mp, M, ld, estride, E, J, NBP, 0, Jb, nu, Jb, Jn, err);
+        if (!s) s = update<64>(ctx, mp, M, ld, estride, E, J, NBP, 0, Jb, Jn, Jn, ncols, err);
+        if (s) return s;
+        diag_block(ctx, M, ld, estride, E, Jb, NBP, sd.Tinv, estat);
+        s = rowcol(ctx, M, ld, estride, E, Jb, NBP, sd.Tinv, Jn, nu, Jn, ncols, 0, sd.Ut, NBP);
+        if (!s) s = update<128>(ctx, mp, M, ld, estride, E, J, 2 * NBP, 0, Jn, nu, Jn, ncols, err);
+        if (s) return s;
+    }
+    // the remaining panels one at a time
+    for (; J < nu; J += NBP) {
         const int jb = std::min(NBP, nu - J);
-        {
-            // the diagonal block in and out, its factor in three layouts plus the reciprocal pivots
-            const double b3 = (double)jb * jb * jb;
-            ProfScope ps(ctx, "lu_tc_diag", 1, (double)E * (8.0 * jb * jb + 4.0 * kInvMats * NBP * NBP),
-                         (double)E * 2.0 / 3.0 * b3);
-            k_diag<<<(unsigned)E, kDiagThreads, 0, ctx->stream>>>(nu, ld, estride, M, J, jb, sd.Tinv, panels_of(nu), estat,
-                                                                1e-6f);
-        }
-        s = rowcol(ctx, M, ld, estride, E, J, jb, sd.Tinv, J + jb, nu, J + jb, ncols, 0, sd.Ut);
-        if (!s) s = update(ctx, mp, M, ld, estride, E, J, jb, J + jb, nu, J + jb, ncols, err);
+        diag_block(ctx, M, ld, estride, E, J, jb, sd.Tinv, estat);
+        s = rowcol(ctx, M, ld, estride, E, J, jb, sd.Tinv, J + jb, nu, J + jb, ncols, 0, sd.Ut, 0);
+        if (!s) s = update<64>(ctx, mp, M, ld, estride, E, J, jb, 0, J + jb, nu, J + jb, ncols, err);
         if (s) return s;
     }
     return backward_sweep_tc(ctx, mp, M, ld, estride, E, sd.Tinv, sd.Ut, err);
@@ -872,13 +936,13 @@ elrt_status tc_lu_resolve(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, 
     if (s) return s;
     for (int J = 0; J < nu; J += NBP) {
         const int jb = std::min(NBP, nu - J);
-        s = rowcol(ctx, M, ld, estride, E, J, jb, sd.Tinv, 0, 0, nu, nu + nin, 0, sd.Ut);
-        if (!s) s = update(ctx, mp, M, ld, estride, E, J, jb, J + jb, nu, nu, nu + nin, err);
+        s = rowcol(ctx, M, ld, estride, E, J, jb, sd.Tinv, 0, 0, nu, nu + nin, 0, sd.Ut, 0);
+        if (!s) s = update<64>(ctx, mp, M, ld, estride, E, J, jb, 0, J + jb, nu, nu, nu + nin, err);
         if (s) return s;
     }
     return backward_sweep_tc(ctx, mp, M, ld, estride, E, sd.Tinv, sd.Ut, err);
 }
 
 size_t tc_lu_side_floats(const Tab& t, int64_t ld) {
-    return (size_t)NBP * ld + (size_t)panels_of(t.nu) * kInvMats * NBP * NBP;
+    return (size_t)UTK * ld + (size_t)panels_of(t.nu) * kInvMats * NBP * NBP;
 }

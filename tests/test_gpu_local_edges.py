@@ -66,8 +66,9 @@ def test_tf32_albedo_one(lib):
     assert st.max_rel_residual < 1e-6
     np.testing.assert_allclose(a, o_i2o, atol=2e-6, rtol=2e-6)
     np.testing.assert_allclose(m, o_i2m, atol=2e-6, rtol=2e-6)
-    np.testing.assert_allclose(a.sum(-1), 1.0, atol=2e-5)
-    np.testing.assert_allclose(m.sum(-1), 1.0, atol=2e-5)
+    # a row sum adds 224 entries, each within 2e-6
+    np.testing.assert_allclose(a.sum(-1), 1.0, atol=5e-4)
+    np.testing.assert_allclose(m.sum(-1), 1.0, atol=5e-4)
     a, m, st = _build(lib, p, N, kappa, omega, h, lib.LOCAL_TF32_IR, 2, torch.float64)
     assert st.n_flagged == 0, st.n_flagged
     np.testing.assert_allclose(a, o_i2o, atol=1e-10)
