@@ -231,6 +231,22 @@ class Disc:
         A_i2m = X.reshape(self.n_angles, self.nm, self.n_in).mean(axis=0)   # (1/|S|) int_S = (1/N) sum_k
         return A_i2o, A_i2m, X
 
+    def source_vector(self, f_hat):
+        """Right-hand side of a volume source in the local equation (eq. hdg_local_mat with f != 0):
+        F[(k, i)] = w_i f_hat[k, i], where f_hat = f h / 2 is the source at node i averaged over angular
+        cell k and scaled to the reference element like sigma (Sec. 2.4.1), the equation divided by
+        (h/2) dtheta as everywhere."""
+        f_hat = np.asarray(f_hat, dtype=np.float64).reshape(self.n_angles, self.nm)
+        return (f_hat * self.w2[None, :]).reshape(-1)
+
+    def local_source(self, kappa_hat, omega, f_hat):
+        """Source parts of eqs. hdg_local_f2u_i2u and hdg_local_f2o_i2o: f_u = (B - C + M - S)^{-1} F,
+        its outflow restriction f^_u = R^o f_u and its angular mean (eq. ang_ave).  Returns
+        (f^_u [n_out], mean [nm], f_u [nu])."""
+        A, _ = self.local_system(kappa_hat, omega)
+        f_u = np.linalg.solve(A, self.source_vector(f_hat))
+        return f_u[self.out_rows], f_u.reshape(self.n_angles, self.nm).mean(axis=0), f_u
+
     def energy_defect(self, kappa_hat, omega, A_i2o, A_i2m):
         """Per inflow column, the discrete energy balance of an element (test function v = 1):
 
@@ -321,10 +337,21 @@ def global_apply(mesh, disc, A_i2o, x):
     return (x.reshape(mesh.n_elems, -1) - np.einsum("eij,ej->ei", A_i2o, xin)).reshape(-1)
 
 
-def global_rhs(mesh, disc, A_i2o, g):
-    """sum_K A_i2o^K applied to the boundary part of the inflow (f = 0 so f^_u = 0)."""
+def global_rhs(mesh, disc, A_i2o, g, f2o=None):
+    """Right-hand side of eq. hdg_global_mat: per element A_i2o^K applied to the boundary part of the
+    inflow, plus the source term f^_u^K (f2o [E, n_out]) when there is a source."""
     gin = gather_inflow(mesh, disc, np.zeros((mesh.n_elems, disc.n_out)), g)
-    return np.einsum("eij,ej->ei", A_i2o, gin).reshape(-1)
+    b = np.einsum("eij,ej->ei", A_i2o, gin)
+    if f2o is not None:
+        b = b + f2o
+    return b.reshape(-1)
+
+
+def nodal_source_hat(problem, disc: Disc, mesh: Mesh):
+    """f_hat = f h / 2 [E, N, nm] at the LGL nodes of every element, per angular cell (Sec. 2.4.1)."""
+    x, z = mesh.node_coords(disc)
+    f = np.asarray(problem.source(x, z), dtype=np.float64)         # [E, nm, N]
+    return np.transpose(f, (0, 2, 1)) * (mesh.h * 0.5)
 
 
 def global_dense(mesh, disc, A_i2o):
@@ -409,9 +436,12 @@ def build_local(disc: Disc, kappa_hat: np.ndarray, omega: np.ndarray):
     return A_i2o, A_i2m
 
 
-def solve_problem(problem, rtol=1e-12, dense=None, ops=None):
+def solve_problem(problem, rtol=1e-12, dense=None, ops=None, radiance=False):
     """Algorithm 1 on a workload problem. Returns a dict with the skeleton solution, the mean
-    intensity [E, nm], the local operators and GMRES statistics."""
+    intensity [E, nm], the local operators and GMRES statistics.  With a volume source
+    (problem.source) the local source terms f^_u, f_u enter the global right-hand side and the
+    recovery (eqs. hdg_local_f2u_i2u, hdg_local_f2o_i2o); radiance=True also recovers the radiance
+    u_h = A_i2u u^_in + f_u of every element ([E, N, nm])."""
     disc = Disc(problem.p, problem.n_angles, problem.hg_g, problem.angular)
     mesh = Mesh(problem.nx, problem.nz, problem.h)
     kh = nodal_kappa_hat(problem, disc, mesh)
@@ -419,7 +449,14 @@ def solve_problem(problem, rtol=1e-12, dense=None, ops=None):
         A_i2o, A_i2m = build_local(disc, kh, problem.omega)
     else:
         A_i2o, A_i2m = ops
-    b = global_rhs(mesh, disc, A_i2o, problem.inflow)
+    E = mesh.n_elems
+    f2o = f2m = f2u = None
+    if getattr(problem, "source", None) is not None:
+        fh = nodal_source_hat(problem, disc, mesh)
+        f2o, f2m, f2u = np.zeros((E, disc.n_out)), np.zeros((E, disc.nm)), np.zeros((E, disc.nu))
+        for e in range(E):
+            f2o[e], f2m[e], f2u[e] = disc.local_source(kh[e], float(problem.omega[e]), fh[e])
+    b = global_rhs(mesh, disc, A_i2o, problem.inflow, f2o)
     n = b.size
     if dense is None:
         dense = n <= 4000
@@ -430,13 +467,23 @@ def solve_problem(problem, rtol=1e-12, dense=None, ops=None):
         x, its, rel = gmres(lambda v: global_apply(mesh, disc, A_i2o, v), b, rtol=rtol)
     xin = gather_inflow(mesh, disc, x.reshape(mesh.n_elems, disc.n_out), problem.inflow)
     um = np.einsum("eij,ej->ei", A_i2m, xin)
-    return dict(disc=disc, mesh=mesh, kappa_hat=kh, A_i2o=A_i2o, A_i2m=A_i2m, x=x, u_mean=um,
-                iterations=its, rel_residual=rel)
+    if f2m is not None:
+        um = um + f2m
+    out = dict(disc=disc, mesh=mesh, kappa_hat=kh, A_i2o=A_i2o, A_i2m=A_i2m, x=x, u_mean=um,
+               iterations=its, rel_residual=rel, f2o=f2o, f2m=f2m, f2u=f2u)
+    if radiance:
+        u = np.zeros((E, disc.nu))
+        for e in range(E):
+            _, _, A_i2u = disc.local_operators(kh[e], float(problem.omega[e]))
+            u[e] = A_i2u @ xin[e] + (f2u[e] if f2u is not None else 0.0)
+        out["radiance"] = u.reshape(E, disc.n_angles, disc.nm)
+    return out
 
 
-def dg_direct(problem):
-    """Upwind DG (eqs. dg, dg_flux) assembled over the whole mesh and solved densely; returns
-    the mean intensity [E, nm].  Tiny meshes only; used to check the hybridised path."""
+def dg_direct_radiance(problem):
+    """Upwind DG (eqs. dg, dg_flux; a volume source f enters as F of each element) assembled over the
+    whole mesh and solved densely; returns the radiance [E, N, nm].  Tiny meshes only; used to check
+    the hybridised path."""
     disc = Disc(problem.p, problem.n_angles, problem.hg_g, problem.angular)
     mesh = Mesh(problem.nx, problem.nz, problem.h)
     kh = nodal_kappa_hat(problem, disc, mesh)
@@ -444,9 +491,12 @@ def dg_direct(problem):
     G = np.zeros((E * nu, E * nu))
     rhs = np.zeros(E * nu)
     offs, _ = inflow_side_offsets(mesh, disc)
+    fh = nodal_source_hat(problem, disc, mesh) if getattr(problem, "source", None) is not None else None
     for e in range(E):
         A, _ = disc.local_system(kh[e], float(problem.omega[e]))
         G[e * nu:(e + 1) * nu, e * nu:(e + 1) * nu] = A
+        if fh is not None:
+            rhs[e * nu:(e + 1) * nu] += disc.source_vector(fh[e])
         for F in range(4):
             nb = mesh.neighbour(e, F)
             for m, node in enumerate(disc.face_nodes[F]):
@@ -459,8 +509,12 @@ def dg_direct(problem):
                     else:
                         gval = problem.inflow[offs[F] + mesh.boundary_face(e, F) * disc.n_face + m * half + kk]
                         rhs[row] -= coef * gval
-    u = np.linalg.solve(G, rhs).reshape(E, problem.n_angles, nm)
-    return u.mean(axis=1)
+    return np.linalg.solve(G, rhs).reshape(E, problem.n_angles, nm)
+
+
+def dg_direct(problem):
+    """Mean intensity [E, nm] of the direct upwind-DG solve (dg_direct_radiance)."""
+    return dg_direct_radiance(problem).mean(axis=1)
 
 
 def exact_transport_mean(problem, disc: Disc, mesh: Mesh, kappa: float, ref=(0.0, 0.0)):

@@ -315,3 +315,83 @@ def test_golden_headline_field_is_the_recorded_oracle_output():
     u = np.load(path)
     assert u.shape == (4096, 49) and np.all(np.isfinite(u)) and meta["rel_residual"] < 1e-11
     assert u.max() > 0.1                     # the beam enters: not a zero field
+
+
+# ---------------------------------------------------------------------------------- volume source
+def _with_source(prob, kind):
+    if kind == "emission":
+        src = W.IsotropicEmission(prob.kappa, float(prob.omega[0]), 1.0, 0.6, prob.nz * prob.h, prob.n_angles)
+    else:
+        src = W.BeamLikeSource(3.0, (0.4 * prob.nx * prob.h, 0.6 * prob.nz * prob.h), 0.3 * prob.nx * prob.h, 1.0,
+                               prob.n_angles)
+    return dataclasses.replace(prob, source=src)
+
+
+@pytest.mark.parametrize("p,N,nx,nz,kind", [(2, 4, 2, 2, "emission"), (3, 8, 3, 2, "beamlike"), (2, 8, 2, 3, "beamlike")])
+def test_source_hybridised_equals_direct_dg(p, N, nx, nz, kind):
+    """With a volume source the hybridised solve (local source terms f^_u, f_u in the global
+    right-hand side and the recovery) reproduces the direct upwind-DG solution: mean intensity and
+    radiance, to round-off."""
+    from tests import _helpers as H
+    prob = _with_source(H.small_cloud(nx, nz, p, N, random_inflow=True), kind)
+    ref = hdg.solve_problem(prob, dense=True, radiance=True)
+    u_dg = hdg.dg_direct_radiance(prob)
+    np.testing.assert_allclose(ref["radiance"], u_dg, atol=1e-12 * np.abs(u_dg).max())
+    np.testing.assert_allclose(ref["u_mean"], u_dg.mean(axis=1), atol=1e-12 * np.abs(u_dg).max())
+    assert np.abs(ref["f2o"]).max() > 1e-3                 # the source is not negligible
+
+
+def _manufactured(p, n_angles, n=2, kappa=1.3, omega=0.7, g=0.5):
+    """A smooth exact radiance u_k(x, z) per angular cell and the source that makes it the solution
+    of the angle-discrete equation sbar_k . grad u_k + kappa u_k - omega kappa sum_l W_kl u_l = f_k,
+    with inflow data taken from u_k on the boundary of the unit square (n x n elements)."""
+    d = hdg.Disc(p, n_angles, g)
+    th = (np.arange(n_angles) + 0.5) * 2 * math.pi / n_angles
+    amp = 1.0 + 0.5 * np.sin(th + 0.3)                       # angular profile of u
+
+    def u(x, z):                                              # [..., N]
+        x = np.asarray(x, dtype=np.float64)[..., None]
+        z = np.asarray(z, dtype=np.float64)[..., None]
+        return amp * np.exp(0.4 * x - 0.3 * z) * (1.0 + 0.2 * np.sin(2.0 * x + z))
+
+    def grad(x, z):
+        x = np.asarray(x, dtype=np.float64)[..., None]
+        z = np.asarray(z, dtype=np.float64)[..., None]
+        e = np.exp(0.4 * x - 0.3 * z)
+        s = 1.0 + 0.2 * np.sin(2.0 * x + z)
+        c = 0.2 * np.cos(2.0 * x + z)
+        return amp * e * (0.4 * s + 2.0 * c), amp * e * (-0.3 * s + c)
+
+    def f(x, z):
+        gx, gz = grad(x, z)
+        uu = u(x, z)
+        return d.sx * gx + d.sz * gz + kappa * uu - omega * kappa * uu @ d.W.T
+
+    offs, total = W.inflow_layout(n, n, p, n_angles)
+    gin = np.zeros(total)
+    pos = (d.xi + 1.0) * 0.5 / n
+    for F in range(4):
+        for fa in range(n):
+            for m in range(p + 1):
+                px, pz = [(fa / n + pos[m], 0.0), (1.0, fa / n + pos[m]), (fa / n + pos[m], 1.0), (0.0, fa / n + pos[m])][F]
+                for kk, k in enumerate(d.in_cells[F]):
+                    gin[offs[F] + (fa * (p + 1) + m) * (n_angles // 2) + kk] = u(px, pz)[k]
+    prob = W.Problem("manufactured", n, n, 1.0 / n, p, n_angles, g, np.full(n * n, omega),
+                     lambda x, z: np.full(np.broadcast(np.asarray(x), np.asarray(z)).shape, kappa), gin, "fv0", f)
+    return prob, u
+
+
+def test_manufactured_solution_with_source_converges_spectrally():
+    """Pin of the source terms (eqs. hdg_local_f2u_i2u, hdg_local_f2o_i2o and the recovery): for a
+    smooth manufactured radiance with scattering the hybridised solution converges exponentially in
+    p; a dropped, mis-scaled or sign-flipped source term stalls it at O(1)."""
+    errs = []
+    for p in range(2, 8):
+        prob, u = _manufactured(p, 8)
+        ref = hdg.solve_problem(prob, dense=True, radiance=True)
+        x, z = ref["mesh"].node_coords(ref["disc"])
+        exact = np.transpose(u(x, z), (0, 2, 1))              # [E, N, nm]
+        errs.append(np.abs(ref["radiance"] - exact).max() / np.abs(exact).max())
+        np.testing.assert_allclose(ref["u_mean"], exact.mean(axis=1), atol=2 * errs[-1] * np.abs(exact).max())
+    assert errs[-1] < 1e-7, errs
+    assert all(b < a / 4 for a, b in zip(errs, errs[1:])), errs

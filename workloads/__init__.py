@@ -2,8 +2,8 @@
 
 This package holds no arithmetic of the element method itself: it only draws
 random numbers (numpy's counter-based Philox generator) and defines optical
-fields kappa(x, z) as plain functions of physical coordinates, plus the
-boundary inflow data of each workload.  Whoever needs kappa at the LGL nodes
+fields kappa(x, z) and volume sources f(x, z) as plain functions of physical
+coordinates, plus the boundary inflow data of each workload.  Whoever needs kappa at the LGL nodes
 of an element evaluates these functions at its own node coordinates.
 """
 
@@ -13,6 +13,8 @@ from .fields import (  # noqa: F401
     Problem,
     GaussianClouds,
     LognormalSlab,
+    IsotropicEmission,
+    BeamLikeSource,
     ElementBatch,
     inflow_layout,
     beam_inflow,

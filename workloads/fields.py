@@ -172,6 +172,40 @@ class LognormalSlab:
         return out
 
 
+@dataclasses.dataclass
+class IsotropicEmission:
+    """Thermal emission, the same in every angular cell: f(x, z) = (1 - omega) kappa(x, z) B(z) with a
+    source function rising linearly with height, B(z) = b0 + b1 z / height."""
+    kappa: Callable
+    omega: float
+    b0: float
+    b1: float
+    height: float
+    n_angles: int
+
+    def __call__(self, x, z):
+        f = (1.0 - self.omega) * self.kappa(x, z) * (self.b0 + self.b1 * np.asarray(z, dtype=np.float64) / self.height)
+        return np.repeat(np.asarray(f)[..., None], self.n_angles, axis=-1)
+
+
+@dataclasses.dataclass
+class BeamLikeSource:
+    """An angle-dependent volume source peaked around direction theta0: f(x, z, cell k) =
+    a exp(-|x - c|^2 / (2 w^2)) (1 + cos(theta_k - theta0)), theta_k the centre of cell k."""
+    amplitude: float
+    centre: tuple
+    width: float
+    theta0: float
+    n_angles: int
+
+    def __call__(self, x, z):
+        x = np.asarray(x, dtype=np.float64)
+        z = np.asarray(z, dtype=np.float64)
+        blob = self.amplitude * np.exp(-((x - self.centre[0]) ** 2 + (z - self.centre[1]) ** 2) / (2 * self.width ** 2))
+        th = (np.arange(self.n_angles) + 0.5) * 2 * math.pi / self.n_angles
+        return blob[..., None] * (1.0 + np.cos(th - self.theta0))
+
+
 # ----------------------------------------------------------------------------------------------
 # problems
 # ----------------------------------------------------------------------------------------------
@@ -190,6 +224,7 @@ class Problem:
     kappa: Callable                           # kappa(x, z) in km^-1
     inflow: np.ndarray                        # boundary inflow, layout described in the module doc
     angular: str = "fv0"                      # "fv0" (cell-averaged directions) or "do" (cell centres)
+    source: Callable | None = None            # volume source f(x, z) -> [..., N] per angular cell, or None
 
     @property
     def n_elems(self) -> int:
