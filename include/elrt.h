@@ -186,6 +186,34 @@ elrt_status elrt_build_local(elrt_ctx* ctx, int64_t n_elems, double h, const dou
                              int32_t refine_steps, int32_t out_dtype, void* in2out, void* in2sol,
                              int32_t* elem_status, elrt_local_stats* stats);
 
+/* Optional extras of a local build with a volume source f (eq. RT_PDE with f != 0; eqs.
+ * hdg_local_f2u_i2u and hdg_local_f2o_i2o: u_h = A_i2u u^_in + f_u on each element, with
+ * f_u = (B - C + M - S)^{-1} [f] and its outflow trace f^_u = R^o f_u), and the full radiance
+ * operator A_i2u for radiance recovery:
+ *   source  device [E][N][(p+1)^2] FP64: f at node i averaged over angular cell k (row k, column i),
+ *           km^-1 x radiance; the library scales it to the reference element like sigma (f h / 2)
+ *           and weights it by the node's quadrature weight.  NULL: no source (f2o, f2m, f2u unused);
+ *   f2o     device [E][n_out] FP64: f^_u (required with a source);
+ *   f2m     device [E][(p+1)^2] FP64: the angular mean (1/N) sum_k f_u[(k, i)] (required with a source);
+ *   f2u     device [E][nu] FP64: f_u itself, rows k (p+1)^2 + i, or NULL;
+ *   in2rad  device [E][nu][n_in] in the build's out_dtype: A_i2u (rows k (p+1)^2 + i), or NULL.
+ * The source is one more right-hand-side column of the element's solve (the matrix is factored
+ * once) and is refined with the others. */
+typedef struct {
+    const double* source;
+    double* f2o;
+    double* f2m;
+    double* f2u;
+    void* in2rad;
+} elrt_local_extras;
+
+/* elrt_build_local with extras (NULL extras: identical to elrt_build_local).  ELRT_EINVAL if a
+ * source is given without f2o and f2m. */
+elrt_status elrt_build_local_ex(elrt_ctx* ctx, int64_t n_elems, double h, const double* h_elem,
+                                const double* kappa, const double* omega, int32_t mode, int32_t refine_steps,
+                                int32_t out_dtype, void* in2out, void* in2sol, const elrt_local_extras* extras,
+                                int32_t* elem_status, elrt_local_stats* stats);
+
 /* Same operators as elrt_build_local (modes ELRT_LOCAL_FP64 and ELRT_LOCAL_FP32_IR), for callers
  * that cannot allocate device memory: code running where cudaMalloc is not allowed or not wanted,
  * such as a host process whose device memory is owned and budgeted by another framework, a
@@ -243,6 +271,26 @@ elrt_status elrt_solve_global(elrt_ctx* ctx, int32_t nx, int32_t nz, const void*
  * mean: device [E][(p+1)^2] FP64. */
 elrt_status elrt_recover_mean(elrt_ctx* ctx, int32_t nx, int32_t nz, const void* in2sol, int32_t dtype,
                               const double* skeleton, const double* inflow, double* mean);
+
+/* The same with a volume source: elrt_solve_global_source solves eq. hdg_global_mat with the source
+ * term, sum_K (R^o_K - A_i2o^K) u^ = sum_K f^_u^K, i.e. right-hand side A_bnd g + f2o (f2o: device
+ * [E][n_out] FP64 from elrt_build_local_ex, NULL: no source); elrt_recover_mean_source adds the
+ * source part of the mean, u^m_K = in2sol_K x_in(K) + f2m_K (f2m: device [E][(p+1)^2] FP64 or NULL).
+ * Other arguments and behaviour as elrt_solve_global / elrt_recover_mean. */
+elrt_status elrt_solve_global_source(elrt_ctx* ctx, int32_t nx, int32_t nz, const void* in2out, int32_t dtype,
+                                     const double* inflow, const double* f2o, double rtol, int32_t max_iter,
+                                     int32_t restart, int32_t use_guess, double* skeleton, elrt_solve_stats* stats);
+elrt_status elrt_recover_mean_source(elrt_ctx* ctx, int32_t nx, int32_t nz, const void* in2sol, int32_t dtype,
+                                     const double* f2m, const double* skeleton, const double* inflow, double* mean);
+
+/* Radiance of every element (eq. hdg_local_f2u_i2u, Algorithm 1 step 4): u_K = A_i2u^K x_in(K) +
+ * f_u^K, the inflow x_in(K) gathered from the skeleton solution and the boundary data.
+ * in2rad: device [E][nu][n_in] (dtype) from elrt_build_local_ex; f2u: device [E][nu] FP64 or NULL
+ * (no source); skeleton: device [E][n_out] FP64; u: device [E][nu] FP64, rows k (p+1)^2 + i.  The
+ * learned local stage has no A_i2u (the network predicts in2out and in2sol only): radiance needs
+ * the classical build. */
+elrt_status elrt_recover_radiance(elrt_ctx* ctx, int32_t nx, int32_t nz, const void* in2rad, int32_t dtype,
+                                  const double* f2u, const double* skeleton, const double* inflow, double* u);
 
 /* ---------------------------------------------------------------- whole pipeline (Algorithm 1) */
 

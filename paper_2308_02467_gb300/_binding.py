@@ -31,6 +31,11 @@ class LocalStats(C.Structure):
     _fields_ = [("refine_steps", C.c_int32), ("n_flagged", C.c_int32), ("max_rel_residual", C.c_double)]
 
 
+class LocalExtras(C.Structure):
+    _fields_ = [("source", C.c_void_p), ("f2o", C.c_void_p), ("f2m", C.c_void_p), ("f2u", C.c_void_p),
+                ("in2rad", C.c_void_p)]
+
+
 class SolveStats(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("restarts", C.c_int32), ("converged", C.c_int32),
                 ("rel_residual", C.c_double)]
@@ -85,6 +90,12 @@ _sig = {
     "elrt_last_error": (C.c_char_p, [_vp]),
     "elrt_assemble": (_i32, [_vp, _i64, _d, _vp, _vp, _vp, _vp, _vp]),
     "elrt_build_local": (_i32, [_vp, _i64, _d, _vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp, _vp, _P(LocalStats)]),
+    "elrt_build_local_ex": (_i32, [_vp, _i64, _d, _vp, _vp, _vp, _i32, _i32, _i32, _vp, _vp, _P(LocalExtras), _vp,
+                                   _P(LocalStats)]),
+    "elrt_solve_global_source": (_i32, [_vp, _i32, _i32, _vp, _i32, _vp, _vp, _d, _i32, _i32, _i32, _vp,
+                                        _P(SolveStats)]),
+    "elrt_recover_mean_source": (_i32, [_vp, _i32, _i32, _vp, _i32, _vp, _vp, _vp, _vp]),
+    "elrt_recover_radiance": (_i32, [_vp, _i32, _i32, _vp, _i32, _vp, _vp, _vp, _vp]),
     "elrt_global_apply": (_i32, [_vp, _i32, _i32, _vp, _i32, _vp, _vp]),
     "elrt_solve_global": (_i32, [_vp, _i32, _i32, _vp, _i32, _vp, _d, _i32, _i32, _i32, _vp, _P(SolveStats)]),
     "elrt_recover_mean": (_i32, [_vp, _i32, _i32, _vp, _i32, _vp, _vp, _vp]),
@@ -295,6 +306,28 @@ class Context:
             _ptr(elem_status, torch.int32, E, "elem_status"), C.byref(st) if stats else None), self._h)
         return st if stats else None
 
+    def elrt_build_local_ex(self, kappa, omega, h, in2out, in2sol, mode=LOCAL_FP64, refine_steps=2, source=None,
+                            f2o=None, f2m=None, f2u=None, in2rad=None, elem_status=None, h_elem=None, stats=True):
+        """elrt_build_local with a volume source (source [E][N][nm] FP64 -> f2o [E][nin], f2m [E][nm],
+        f2u [E][nu], FP64) and/or the full radiance operator in2rad [E][nu][nin]."""
+        import torch
+        E = omega.numel()
+        self._sync_stream()
+        st = LocalStats()
+        dt = _dt(in2out)
+        if in2sol.dtype != in2out.dtype or (in2rad is not None and in2rad.dtype != in2out.dtype):
+            raise ValueError("in2out, in2sol and in2rad must share a dtype")
+        ex = LocalExtras(_ptr(source, torch.float64, E * self.nu, "source"), _ptr(f2o, torch.float64, E * self.nin, "f2o"),
+                         _ptr(f2m, torch.float64, E * self.nm, "f2m"), _ptr(f2u, torch.float64, E * self.nu, "f2u"),
+                         _ptr(in2rad, None, E * self.nu * self.nin, "in2rad"))
+        _check(_lib.elrt_build_local_ex(
+            self._h, E, float(h), _ptr(h_elem, torch.float64, E, "h_elem"),
+            _ptr(kappa, torch.float64, E * self.nm, "kappa"), _ptr(omega, torch.float64, E, "omega"),
+            int(mode), int(refine_steps), dt, _ptr(in2out, None, E * self.nin * self.nin, "in2out"),
+            _ptr(in2sol, None, E * self.nm * self.nin, "in2sol"), C.byref(ex),
+            _ptr(elem_status, torch.int32, E, "elem_status"), C.byref(st) if stats else None), self._h)
+        return st if stats else None
+
     # ---- global stage
     def elrt_global_apply(self, nx, nz, in2out, x, y):
         import torch
@@ -333,6 +366,44 @@ class Context:
         if not (s == 4 and not raise_on_noconv):
             _check(s, self._h)
         return st
+
+    def elrt_solve_global_source(self, nx, nz, in2out, inflow, f2o, skeleton, rtol=1e-10, max_iter=5000, restart=12,
+                                 use_guess=False, raise_on_noconv=True):
+        import torch
+        n = nx * nz * self.nin
+        self._sync_stream()
+        st = SolveStats()
+        s = _lib.elrt_solve_global_source(self._h, nx, nz, _ptr(in2out, None, n * self.nin, "in2out"), _dt(in2out),
+                                          _ptr(inflow, torch.float64, 2 * (nx + nz) * (self.p + 1) * (self.n_angles // 2),
+                                               "inflow"),
+                                          _ptr(f2o, torch.float64, n, "f2o"), float(rtol), int(max_iter), int(restart),
+                                          int(bool(use_guess)), _ptr(skeleton, torch.float64, n, "skeleton"),
+                                          C.byref(st))
+        if s == 4 and not raise_on_noconv:
+            return st
+        _check(s, self._h)
+        return st
+
+    def elrt_recover_mean_source(self, nx, nz, in2sol, f2m, skeleton, inflow, mean):
+        import torch
+        E = nx * nz
+        self._sync_stream()
+        _check(_lib.elrt_recover_mean_source(self._h, nx, nz, _ptr(in2sol, None, E * self.nm * self.nin, "in2sol"),
+                                             _dt(in2sol), _ptr(f2m, torch.float64, E * self.nm, "f2m"),
+                                             _ptr(skeleton, torch.float64, E * self.nin, "skeleton"),
+                                             _ptr(inflow, torch.float64, None, "inflow"),
+                                             _ptr(mean, torch.float64, E * self.nm, "mean")), self._h)
+
+    def elrt_recover_radiance(self, nx, nz, in2rad, f2u, skeleton, inflow, u):
+        """u [E][nu] FP64 (rows k nm + i) = in2rad_K x_in(K) + f2u_K (f2u may be None)."""
+        import torch
+        E = nx * nz
+        self._sync_stream()
+        _check(_lib.elrt_recover_radiance(self._h, nx, nz, _ptr(in2rad, None, E * self.nu * self.nin, "in2rad"),
+                                          _dt(in2rad), _ptr(f2u, torch.float64, E * self.nu, "f2u"),
+                                          _ptr(skeleton, torch.float64, E * self.nin, "skeleton"),
+                                          _ptr(inflow, torch.float64, None, "inflow"),
+                                          _ptr(u, torch.float64, E * self.nu, "u")), self._h)
 
     def elrt_recover_mean(self, nx, nz, in2sol, skeleton, inflow, mean):
         import torch

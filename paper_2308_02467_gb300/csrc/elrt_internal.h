@@ -17,6 +17,7 @@
 // (fits in the 4 KB classic kernel-parameter space).
 struct Tab {
     int p, n1, nm, N, half, nu, nin, nface;
+    int nrhs;                                   // right-hand-side columns the local LU solves: nin (+1 with a source)
     double w[ELRT_MAX_N1];                      // LGL weights
     double D[ELRT_MAX_N1 * ELRT_MAX_N1];        // D[m*n1+a] = l_a'(xi_m)
     double sx[ELRT_MAX_ANG], sz[ELRT_MAX_ANG];  // direction of cell k
@@ -90,21 +91,25 @@ elrt_status local_assemble_f64(elrt_ctx* ctx, int64_t E, double h, const double*
                                const double* omega, double* A, double* rhs);
 elrt_status local_build(elrt_ctx* ctx, int64_t E, double h, const double* h_elem, const double* kappa,
                         const double* omega, int mode, int refine_steps, int out_dtype, void* in2out,
-                        void* in2sol, int32_t* elem_status, elrt_local_stats* stats);
+                        void* in2sol, int32_t* elem_status, elrt_local_stats* stats,
+                        const elrt_local_extras* extras = nullptr);
 
 // ---- tensor-core LU (lu_tc.cu)
 elrt_status tc_lu_factor_solve(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, int64_t E, int* estat, float* side,
-                               int* err);
-elrt_status tc_lu_resolve(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, int64_t E, float* side, int* err);
+                               int* err, int nrhs);
+elrt_status tc_lu_resolve(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, int64_t E, float* side, int* err,
+                          int nrhs);
 size_t tc_lu_side_floats(const Tab& t, int64_t ld);
 
 // ---- launchers implemented in global.cu
 elrt_status global_apply(elrt_ctx* ctx, int nx, int nz, const void* A, int dtype, const double* x, double* y);
 elrt_status global_solve(elrt_ctx* ctx, int nx, int nz, const void* A, int dtype, const double* inflow,
                          double rtol, int max_iter, int restart, int use_guess, double* x,
-                         elrt_solve_stats* stats);
+                         elrt_solve_stats* stats, const double* f2o = nullptr);
 elrt_status global_recover(elrt_ctx* ctx, int nx, int nz, const void* A, int dtype, const double* x,
-                           const double* inflow, double* mean);
+                           const double* inflow, double* mean, const double* f2m = nullptr);
+elrt_status global_recover_rows(elrt_ctx* ctx, int nx, int nz, int rows, const void* A, int dtype, const double* x,
+                                const double* inflow, const double* self, double* out);
 
 // ---- learned local stage (mlp.cu)
 extern "C" elrt_status elrt_build_local_learned(elrt_ctx* ctx, elrt_net* net, int64_t n, double h, const double* h_elem,

@@ -1454,7 +1454,7 @@ unsigned grid_for(int64_t n) { return (unsigned)std::max<int64_t>(1, std::min<in
 // float-float level (all inner products and norms accumulate in float-float, reduced in FP64).
 template <typename A, typename V, typename X>
 elrt_status gmres(elrt_ctx* ctx, int nx, int nz, const void* Aop, const double* inflow, double rtol, int max_iter,
-                  int restart, int use_guess, double* xout, elrt_solve_stats* stats) {
+                  int restart, int use_guess, double* xout, elrt_solve_stats* stats, const double* f2o) {
     const Tab& t = ctx->tab;
     const int64_t n = (int64_t)nx * nz * t.nin;
     const int m = std::max(1, std::min(restart, kMaxRestart));
@@ -1513,8 +1513,18 @@ elrt_status gmres(elrt_ctx* ctx, int nx, int nz, const void* Aop, const double* 
             use16 = true;
         }
     }
-    // b = A g_bnd
-    s = launch_gemv<A, X>(ctx, nx, nz, rows, Aop, nullptr, inflow, nullptr, 0, 1, b, nullptr);
+    // b = A g_bnd (+ f^_u: the source term of eq. hdg_global_mat, converted to X first)
+    const X* fsrc = nullptr;
+    if (f2o) {
+        if constexpr (std::is_same<X, double>::value) {
+            fsrc = f2o;
+        } else {
+            ProfScope ps(ctx, "krylov", 1, 16.0 * n);
+            k_d2ff<<<gb, kThreads, 0, sm>>>(f2o, r, n);
+            fsrc = r;
+        }
+    }
+    s = launch_gemv<A, X>(ctx, nx, nz, rows, Aop, nullptr, inflow, fsrc, fsrc ? 1 : 0, 1, b, nullptr);
     if (s) return s;
     { ProfScope ps(ctx, "krylov", 1, kv(1, n, sizeof(X))); k_dots<X><<<dim3(nblk, 1), kThreads, 0, sm>>>(b, n, b, partial, nullptr); }
     { ProfScope ps(ctx, "krylov"); k_dots_finish<<<1, kThreads, 0, sm>>>(partial, nblk, scal, 2, nullptr); }
@@ -1670,17 +1680,40 @@ elrt_status global_apply(elrt_ctx* ctx, int nx, int nz, const void* A, int dtype
     return launch_gemv<double, double>(ctx, nx, nz, ctx->tab.nin, A, x, nullptr, x, 1, -1, y, nullptr);
 }
 
+__global__ void k_add_to(double* __restrict__ y, const double* __restrict__ a, int64_t n) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        y[i] += a[i];
+}
+
+// out_K = self_K + Aop_K x_in(K) for operators of `rows` rows per element (nm: the mean intensity
+// with the source part f2m; nu: the radiance with f_u).  The matvec prefetches a self term of at
+// most 4 (p+1) N/2 rows per element; longer ones (the radiance) are added by a separate pass.
+elrt_status global_recover_rows(elrt_ctx* ctx, int nx, int nz, int rows, const void* A, int dtype, const double* x,
+                                const double* inflow, const double* self, double* out) {
+    constexpr int kSelfRows = 4 * ELRT_MAX_N1 * (ELRT_MAX_ANG / 2);
+    const bool fused = self && rows <= kSelfRows;
+    elrt_status s = dtype == ELRT_F32
+                        ? launch_gemv<float, double>(ctx, nx, nz, rows, A, x, inflow, fused ? self : nullptr, fused ? 1 : 0,
+                                                     1, out, nullptr)
+                        : launch_gemv<double, double>(ctx, nx, nz, rows, A, x, inflow, fused ? self : nullptr,
+                                                      fused ? 1 : 0, 1, out, nullptr);
+    if (s || !self || fused) return s;
+    const int64_t n = (int64_t)nx * nz * rows;
+    ProfScope ps(ctx, "gemv", 1, 24.0 * n);
+    k_add_to<<<grid_for(n), kThreads, 0, ctx->stream>>>(out, self, n);
+    return cuda_check(ctx, cudaGetLastError(), "add launch");
+}
+
 elrt_status global_recover(elrt_ctx* ctx, int nx, int nz, const void* A, int dtype, const double* x,
-                           const double* inflow, double* mean) {
-    if (dtype == ELRT_F32)
-        return launch_gemv<float, double>(ctx, nx, nz, ctx->tab.nm, A, x, inflow, nullptr, 0, 1, mean, nullptr);
-    return launch_gemv<double, double>(ctx, nx, nz, ctx->tab.nm, A, x, inflow, nullptr, 0, 1, mean, nullptr);
+                           const double* inflow, double* mean, const double* f2m) {
+    return global_recover_rows(ctx, nx, nz, ctx->tab.nm, A, dtype, x, inflow, f2m, mean);
 }
 
 elrt_status global_solve(elrt_ctx* ctx, int nx, int nz, const void* A, int dtype, const double* inflow, double rtol,
-                         int max_iter, int restart, int use_guess, double* x, elrt_solve_stats* stats) {
+                         int max_iter, int restart, int use_guess, double* x, elrt_solve_stats* stats,
+                         const double* f2o) {
     if (restart > kMaxRestart) return ctx_fail(ctx, ELRT_EINVAL, "restart above 200");
     if (dtype == ELRT_F32)
-        return gmres<float, float, ff>(ctx, nx, nz, A, inflow, rtol, max_iter, restart, use_guess, x, stats);
-    return gmres<double, double, double>(ctx, nx, nz, A, inflow, rtol, max_iter, restart, use_guess, x, stats);
+        return gmres<float, float, ff>(ctx, nx, nz, A, inflow, rtol, max_iter, restart, use_guess, x, stats, f2o);
+    return gmres<double, double, double>(ctx, nx, nz, A, inflow, rtol, max_iter, restart, use_guess, x, stats, f2o);
 }

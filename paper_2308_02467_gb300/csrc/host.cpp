@@ -153,6 +153,7 @@ bool build_tab(const elrt_disc* d, Tab* t) {
     t->nu = t->nm * N;
     t->nface = (p + 1) * (N / 2);
     t->nin = 4 * t->nface;
+    t->nrhs = t->nin;
     double xi[ELRT_MAX_N1];
     lgl_rule(p, xi, t->w);
     barycentric_derivative(p + 1, xi, t->D);
@@ -439,6 +440,28 @@ elrt_status elrt_build_local(elrt_ctx* ctx, int64_t n_elems, double h, const dou
                        elem_status, stats);
 }
 
+elrt_status elrt_build_local_ex(elrt_ctx* ctx, int64_t n_elems, double h, const double* h_elem, const double* kappa,
+                                const double* omega, int32_t mode, int32_t refine_steps, int32_t out_dtype,
+                                void* in2out, void* in2sol, const elrt_local_extras* extras, int32_t* elem_status,
+                                elrt_local_stats* stats) {
+    if (!ctx) return ctx_fail(nullptr, ELRT_EINVAL, "elrt_build_local_ex: null context");
+    if (extras && extras->source && n_elems > 0 && (!extras->f2o || !extras->f2m))
+        return ctx_fail(ctx, ELRT_EINVAL, "elrt_build_local_ex: a source needs f2o and f2m");
+    if (n_elems < 0 || (n_elems > 0 && (!kappa || !omega || !in2out || !in2sol)) || (!h_elem && !(h > 0)))
+        return ctx_fail(ctx, ELRT_EINVAL, "elrt_build_local_ex: bad arguments");
+    if (mode < ELRT_LOCAL_FP64 || mode > ELRT_LOCAL_TF32_IR)
+        return ctx_fail(ctx, ELRT_EINVAL, "elrt_build_local_ex: unknown mode");
+    if (out_dtype != ELRT_F32 && out_dtype != ELRT_F64)
+        return ctx_fail(ctx, ELRT_EINVAL, "elrt_build_local_ex: unknown output dtype");
+    if (refine_steps < 0 || refine_steps > 8)
+        return ctx_fail(ctx, ELRT_EINVAL, "elrt_build_local_ex: refine_steps must be in 0..8");
+    ctx->last_error.clear();
+    if (stats) memset(stats, 0, sizeof(*stats));
+    if (n_elems == 0) return ELRT_OK;
+    return local_build(ctx, n_elems, h, h_elem, kappa, omega, mode, refine_steps, out_dtype, in2out, in2sol,
+                       elem_status, stats, extras);
+}
+
 elrt_status elrt_global_apply(elrt_ctx* ctx, int32_t nx, int32_t nz, const void* in2out, int32_t dtype,
                               const double* x, double* y) {
     if (!ctx) return ctx_fail(nullptr, ELRT_EINVAL, "elrt_global_apply: null context");
@@ -467,6 +490,36 @@ elrt_status elrt_recover_mean(elrt_ctx* ctx, int32_t nx, int32_t nz, const void*
         return ctx_fail(ctx, ELRT_EINVAL, "elrt_recover_mean: bad arguments");
     ctx->last_error.clear();
     return global_recover(ctx, nx, nz, in2sol, dtype, skeleton, inflow, mean);
+}
+
+elrt_status elrt_solve_global_source(elrt_ctx* ctx, int32_t nx, int32_t nz, const void* in2out, int32_t dtype,
+                                     const double* inflow, const double* f2o, double rtol, int32_t max_iter,
+                                     int32_t restart, int32_t use_guess, double* skeleton, elrt_solve_stats* stats) {
+    if (!ctx) return ctx_fail(nullptr, ELRT_EINVAL, "elrt_solve_global_source: null context");
+    if (nx < 1 || nz < 1 || !in2out || !inflow || !skeleton || (dtype != ELRT_F32 && dtype != ELRT_F64) ||
+        !(rtol > 0) || max_iter < 1 || restart < 1 || restart > 200)
+        return ctx_fail(ctx, ELRT_EINVAL, "elrt_solve_global_source: bad arguments (restart must be 1..200)");
+    ctx->last_error.clear();
+    if (stats) memset(stats, 0, sizeof(*stats));
+    return global_solve(ctx, nx, nz, in2out, dtype, inflow, rtol, max_iter, restart, use_guess, skeleton, stats, f2o);
+}
+
+elrt_status elrt_recover_mean_source(elrt_ctx* ctx, int32_t nx, int32_t nz, const void* in2sol, int32_t dtype,
+                                     const double* f2m, const double* skeleton, const double* inflow, double* mean) {
+    if (!ctx) return ctx_fail(nullptr, ELRT_EINVAL, "elrt_recover_mean_source: null context");
+    if (nx < 1 || nz < 1 || !in2sol || !skeleton || !inflow || !mean || (dtype != ELRT_F32 && dtype != ELRT_F64))
+        return ctx_fail(ctx, ELRT_EINVAL, "elrt_recover_mean_source: bad arguments");
+    ctx->last_error.clear();
+    return global_recover(ctx, nx, nz, in2sol, dtype, skeleton, inflow, mean, f2m);
+}
+
+elrt_status elrt_recover_radiance(elrt_ctx* ctx, int32_t nx, int32_t nz, const void* in2rad, int32_t dtype,
+                                  const double* f2u, const double* skeleton, const double* inflow, double* u) {
+    if (!ctx) return ctx_fail(nullptr, ELRT_EINVAL, "elrt_recover_radiance: null context");
+    if (nx < 1 || nz < 1 || !in2rad || !skeleton || !inflow || !u || (dtype != ELRT_F32 && dtype != ELRT_F64))
+        return ctx_fail(ctx, ELRT_EINVAL, "elrt_recover_radiance: bad arguments");
+    ctx->last_error.clear();
+    return global_recover_rows(ctx, nx, nz, ctx->tab.nu, in2rad, dtype, skeleton, inflow, f2u, u);
 }
 
 }  // extern "C"

@@ -332,7 +332,7 @@ constexpr size_t lu_smem_bytes(int nu) {
     return (size_t)nu * (NB + 1) * sizeof(T) + (size_t)NB * 32 * QN * sizeof(T);
 }
 
-// Factor A (columns [0, nu)) and solve for the right-hand sides (columns [nu, nu + nin)).
+// Factor A (columns [0, nu)) and solve for the right-hand sides (columns [nu, nu + nrhs)).
 // estatus[e] |= 1 on an exactly zero pivot (the element's result is then meaningless).
 template <typename T, int NB, int QN>
 __global__ void __launch_bounds__(kThreads, 1) k_lu_factor_solve(Tab t, T* __restrict__ Mall, int64_t ld,
@@ -347,7 +347,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_lu_factor_solve(Tab t, T* __res
     __shared__ T piv_v;
     __shared__ int piv_i;
     constexpr int lds = NB + 1;
-    const int nu = t.nu, ncols = t.nu + t.nin;
+    const int nu = t.nu, ncols = t.nu + t.nrhs;
     for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
         T* M = Mall + e * estride;
         int* ipiv = ipiv_all + e * (int64_t)nu;
@@ -409,7 +409,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_lu_factor_solve(Tab t, T* __res
     }
 }
 
-// Solve A D = R for the right-hand sides stored in columns [nu, nu + nin), with the factors and
+// Solve A D = R for the right-hand sides stored in columns [nu, nu + nrhs), with the factors and
 // pivots left by k_lu_factor_solve (forward sweep with the interleaved swaps, then backward).
 template <typename T, int NB, int QN>
 __global__ void __launch_bounds__(kThreads, 1) k_lu_resolve(Tab t, T* __restrict__ Mall, int64_t ld, int64_t estride,
@@ -419,7 +419,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_lu_resolve(Tab t, T* __restrict
     T* Us = Ps + (size_t)t.nu * (NB + 1);
     __shared__ int ipiv_s[NB];
     constexpr int lds = NB + 1;
-    const int nu = t.nu, ncols = t.nu + t.nin;
+    const int nu = t.nu, ncols = t.nu + t.nrhs;
     for (int64_t e = blockIdx.x; e < E; e += gridDim.x) {
         T* M = Mall + e * estride;
         const int* ipiv = ipiv_all + e * (int64_t)nu;
@@ -811,6 +811,152 @@ __global__ void __launch_bounds__(kThreads) k_restrict(Tab t, const S* __restric
     if (bad) atomicOr(&estatus[e], 4);
 }
 
+// ------------------------------------------------------------------------------------------------
+// volume source (eqs. hdg_local_f2u_i2u, hdg_local_f2o_i2o): one more right-hand-side column,
+// column nu + nin of the matrix, solved with the others
+// ------------------------------------------------------------------------------------------------
+
+// F[(k, i)] = w_i (h/2) f[e][k][i]: the source term of the element's equation scaled like every
+// other term (divided by (h/2) dth, f h/2 on the reference element)
+template <typename T>
+__global__ void k_source_column(Tab t, double h, const double* __restrict__ h_elem, const double* __restrict__ src,
+                                T* __restrict__ M, int64_t ld, int64_t estride, int64_t E) {
+    const int64_t e = blockIdx.x;
+    if (e >= E) return;
+    const double half_h = 0.5 * (h_elem ? h_elem[e] : h);
+    T* Mc = M + e * estride + t.nu + t.nin;
+    const double* fe = src + e * (int64_t)t.nu;
+    for (int r = threadIdx.x; r < t.nu; r += blockDim.x) {
+        const int i = r % t.nm;
+        Mc[(int64_t)r * ld] = (T)(t.w[i % t.n1] * t.w[i / t.n1] * half_h * fe[r]);
+    }
+}
+
+// Refinement of the source column in FP64 (one column per element, so FP64 costs nothing here):
+// mode 0: Xs = D; 1: Xs += D, then R = F - A Xs over D; 2: Xs += D only.  A from its structure,
+// as the residual kernels of the -B^ columns do.  maxres[e] = max(maxres[e], |R|).
+template <typename T>
+__global__ void __launch_bounds__(kThreads) k_residual_src(Tab t, double h, const double* __restrict__ h_elem,
+                                                           const double* __restrict__ kappa,
+                                                           const double* __restrict__ omega,
+                                                           const double* __restrict__ src, T* __restrict__ Mall,
+                                                           int64_t ld, int64_t estride, double* __restrict__ Xall,
+                                                           int mode, double* __restrict__ maxres, int64_t E) {
+    __shared__ double xs[ELRT_MAX_N1 * ELRT_MAX_N1 * ELRT_MAX_ANG];
+    __shared__ double red[kThreads / 32];
+    const int64_t e = blockIdx.x;
+    if (e >= E) return;
+    const int nu = t.nu, nm = t.nm, n1 = t.n1, N = t.N, p = t.p;
+    const double he = h_elem ? h_elem[e] : h;
+    const double om = omega[e];
+    T* Mc = Mall + e * estride + t.nu + t.nin;
+    double* X = Xall + e * (int64_t)nu;
+    for (int r = threadIdx.x; r < nu; r += kThreads) {
+        const double d = (double)Mc[(int64_t)r * ld];
+        const double x = mode == 0 ? d : X[r] + d;
+        X[r] = x;
+        xs[r] = x;
+    }
+    if (mode == 2) return;
+    __syncthreads();
+    double rmax = 0.0;
+    for (int r = threadIdx.x; r < nu; r += kThreads) {
+        const int k = r / nm, i = r - k * nm, a = i % n1, b = i / n1;
+        const double kh = kappa[e * nm + i] * 0.5 * he, wi = t.w[a] * t.w[b];
+        double bd = 0.0;
+        if (b == 0 && t.sdn[0][k] > 0) bd += t.w[a] * t.sdn[0][k];
+        if (a == p && t.sdn[1][k] > 0) bd += t.w[b] * t.sdn[1][k];
+        if (b == p && t.sdn[2][k] > 0) bd += t.w[a] * t.sdn[2][k];
+        if (a == 0 && t.sdn[3][k] > 0) bd += t.w[b] * t.sdn[3][k];
+        double tx = 0.0, tz = 0.0;
+        for (int q = 0; q < n1; ++q) {
+            tx += t.w[q] * t.D[q * n1 + a] * xs[k * nm + q + n1 * b];
+            tz += t.w[q] * t.D[q * n1 + b] * xs[k * nm + a + n1 * q];
+        }
+        double sc = 0.0;
+        for (int l = 0; l < N; ++l) {
+            int d = k - l;
+            if (d < 0) d += N;
+            sc += t.wc[d] * xs[l * nm + i];
+        }
+        const double ax = (bd + wi * kh) * xs[r] - t.sx[k] * t.w[b] * tx - t.sz[k] * t.w[a] * tz - wi * om * kh * sc;
+        const double res = wi * 0.5 * he * src[e * (int64_t)nu + r] - ax;
+        rmax = fmax(rmax, fabs(res));
+        Mc[(int64_t)r * ld] = (T)res;
+    }
+    for (int off = 16; off > 0; off >>= 1) rmax = fmax(rmax, __shfl_down_sync(0xffffffffu, rmax, off));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = rmax;
+    __syncthreads();
+    if (threadIdx.x == 0 && maxres) {
+        double m = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) m = fmax(m, red[w]);
+        maxres[e] = fmax(maxres[e], m);
+    }
+}
+
+// f^_u = R^o f_u (outflow rows in skeleton order), (1/N) sum_k f_u[(k, i)] and f_u itself, from
+// the solved source column: X + e xestride + r xld is f_u[r] (the FP64 refined copy, or the column
+// of the matrix when there was no refinement)
+template <typename S>
+__global__ void k_restrict_src(Tab t, const S* __restrict__ X, int64_t xld, int64_t xestride, double* __restrict__ f2o,
+                               double* __restrict__ f2m, double* __restrict__ f2u, int* __restrict__ estatus,
+                               int64_t E) {
+    const int64_t e = blockIdx.x;
+    if (e >= E) return;
+    const S* Xe = X + e * xestride;
+    const int nm = t.nm, half = t.half;
+    int bad = 0;
+    for (int r = threadIdx.x; r < t.nin; r += blockDim.x) {
+        const int F = r / t.nface, rem = r - F * t.nface;
+        const int m = rem / half, kk = rem - m * half;
+        const double v = (double)Xe[(int64_t)(t.outc[F][kk] * nm + face_node(F, m, t.p)) * xld];
+        if (!isfinite(v)) bad = 1;
+        f2o[e * (int64_t)t.nin + r] = v;
+    }
+    for (int i = threadIdx.x; i < nm; i += blockDim.x) {
+        double s = 0.0;
+        for (int k = 0; k < t.N; ++k) s += (double)Xe[(int64_t)(k * nm + i) * xld];
+        f2m[e * (int64_t)nm + i] = s / t.N;
+    }
+    if (f2u)
+        for (int r = threadIdx.x; r < t.nu; r += blockDim.x) f2u[e * (int64_t)t.nu + r] = (double)Xe[(int64_t)r * xld];
+    if (bad) atomicOr(&estatus[e], 4);
+}
+
+// A_i2u itself (rows [0, nu) of the solution of the -B^ columns) into in2rad [E][nu][nin]: from the
+// float-float X (plus the pending last correction D when it was not written back) ...
+template <typename O>
+__global__ void __launch_bounds__(kThreads) k_write_rad_ff(Tab t, const ff* __restrict__ X, const float* __restrict__ D,
+                                                           int64_t dld, int64_t destride, O* __restrict__ out, int64_t E) {
+    const int64_t e = blockIdx.x;
+    if (e >= E) return;
+    const int nin = t.nin;
+    const ff* Xe = X + e * (int64_t)t.nu * nin;
+    const float* De = D ? D + e * destride : nullptr;
+    O* oe = out + e * (int64_t)t.nu * nin;
+    for (int64_t q = threadIdx.x; q < (int64_t)t.nu * nin; q += kThreads) {
+        const int r = (int)(q / nin), c = (int)(q - (int64_t)r * nin);
+        ff v = Xe[q];
+        if (De) v = ff_add(v, ff{De[(int64_t)r * dld + c], 0.f});
+        ff_store(oe + q, v);
+    }
+}
+
+// ... or from a plain buffer (the FP64 solution in the matrix or its FP64 copy)
+template <typename S, typename O>
+__global__ void __launch_bounds__(kThreads) k_write_rad(Tab t, const S* __restrict__ X, int64_t xld, int64_t xestride,
+                                                        O* __restrict__ out, int64_t E) {
+    const int64_t e = blockIdx.x;
+    if (e >= E) return;
+    const int nin = t.nin;
+    const S* Xe = X + e * xestride;
+    O* oe = out + e * (int64_t)t.nu * nin;
+    for (int64_t q = threadIdx.x; q < (int64_t)t.nu * nin; q += kThreads) {
+        const int r = (int)(q / nin), c = (int)(q - (int64_t)r * nin);
+        oe[q] = (O)(double)Xe[(int64_t)r * xld + c];
+    }
+}
+
 __global__ void k_flag_residual(const double* __restrict__ maxres, int* __restrict__ estatus, double tol, int64_t E) {
     const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e < E && !(maxres[e] <= tol)) estatus[e] |= 2;
@@ -882,9 +1028,10 @@ double restrict_bytes(const Tab& t, size_t ss, size_t so, int64_t n) {
     return ((double)(t.nin + t.nu) * t.nin * ss + (double)(t.nin + t.nm) * t.nin * so) * (double)n;
 }
 
+// t: the context's table with nrhs set to the right-hand-side columns of this build
 template <typename T, int NB, int QN>
-elrt_status run_lu(elrt_ctx* ctx, T* M, int64_t ld, int64_t estride, int* ipiv, int* estatus, int64_t n, bool resolve) {
-    const Tab& t = ctx->tab;
+elrt_status run_lu(elrt_ctx* ctx, const Tab& t, T* M, int64_t ld, int64_t estride, int* ipiv, int* estatus, int64_t n,
+                   bool resolve) {
     const size_t smem = lu_smem_bytes<T, NB, QN>(t.nu);
     if (smem > 227 * 1024) return ctx_fail(ctx, ELRT_EINVAL, "local system too large for the shared-memory panel");
     cudaError_t e;
@@ -991,9 +1138,12 @@ elrt_status run_restrict(elrt_ctx* ctx, const S* X, int64_t xld, int64_t xestrid
 template <typename T, int NB, int QN>
 elrt_status build_chunked(elrt_ctx* ctx, int64_t E, double h, const double* h_elem, const double* kappa,
                           const double* omega, int mode, int steps, int out_dtype, void* in2out, void* in2sol,
-                          int32_t* elem_status, elrt_local_stats* stats) {
+                          int32_t* elem_status, elrt_local_stats* stats, const elrt_local_extras* ex) {
     const Tab& t = ctx->tab;
-    const int64_t ld = ((t.nu + t.nin + 31) / 32) * 32;
+    const bool has_src = ex && ex->source;
+    Tab tl = t;  // the LU's right-hand sides: the -B^ columns, then the source column
+    tl.nrhs = t.nin + (has_src ? 1 : 0);
+    const int64_t ld = ((t.nu + tl.nrhs + 31) / 32) * 32;
     const int64_t estride = (int64_t)t.nu * ld;
     const bool ir = (mode != ELRT_LOCAL_FP64);
     double bmax = 0.0;  // max |B^| entry, the scale of the residuals
@@ -1005,15 +1155,16 @@ elrt_status build_chunked(elrt_ctx* ctx, int64_t E, double h, const double* h_el
     const size_t side_per = tc ? tc_lu_side_floats(t, ld) * sizeof(float) : 0;
     // bytes per element: M, ipiv, status, maxres, the FP64 solution when refining / measuring,
     // and the split operand buffers of the tensor-core LU
+    const size_t src_per = (has_src && ir) ? (size_t)t.nu * sizeof(double) : 0;  // refined source column
     const size_t per = estride * sizeof(T) + t.nu * sizeof(int) + sizeof(int) + sizeof(double) +
-                       (want_res ? (size_t)t.nu * t.nin * sizeof(double) : 0) + side_per;
+                       (want_res ? (size_t)t.nu * t.nin * sizeof(double) : 0) + side_per + src_per;
     const size_t budget = (size_t)16 << 30;
     int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(E, (int64_t)(budget / per)));
     if (chunk < E) {  // balance the chunks
         const int64_t nch = (E + chunk - 1) / chunk;
         chunk = (E + nch - 1) / nch;
     }
-    elrt_status s = ensure_ws(ctx, &ctx->ws, &ctx->ws_bytes, per * chunk + 2048);
+    elrt_status s = ensure_ws(ctx, &ctx->ws, &ctx->ws_bytes, per * chunk + 4096);
     if (s) return s;
     unsigned char* base = (unsigned char*)ctx->ws;
     T* M = (T*)base;
@@ -1022,6 +1173,9 @@ elrt_status build_chunked(elrt_ctx* ctx, int64_t E, double h, const double* h_el
     int* ipiv = (int*)(maxres + chunk);
     int* estat = ipiv + (size_t)chunk * t.nu;
     float* side = tc ? (float*)(((uintptr_t)(estat + chunk) + 255) & ~(uintptr_t)255) : nullptr;
+    unsigned char* after_side = tc ? (unsigned char*)(side + (size_t)chunk * tc_lu_side_floats(t, ld))
+                                   : (unsigned char*)(estat + chunk);
+    double* Xs = src_per ? (double*)(((uintptr_t)after_side + 255) & ~(uintptr_t)255) : nullptr;
     s = cuda_check(ctx, cudaMemsetAsync(ctx->d_flags, 0, 4 * sizeof(int) + 2 * sizeof(unsigned long long), ctx->stream),
                    "memset flags");
     if (s) return s;
@@ -1040,15 +1194,24 @@ elrt_status build_chunked(elrt_ctx* ctx, int64_t E, double h, const double* h_el
             k_assemble<T><<<grid, kThreads, 0, ctx->stream>>>(t, h, he ? he + a0 : nullptr, ka + a0 * t.nm, om + a0,
                                                               M + a0 * estride, ld, estride, nullptr, 0, ctx->d_flags);
         }
+        if (has_src)
+            k_source_column<T><<<(unsigned)n, kThreads, 0, ctx->stream>>>(t, h, he, ex->source + e0 * t.nu, M, ld,
+                                                                        estride, n);
         s = cuda_check(ctx, cudaGetLastError(), "assemble launch");
         if (s) return s;
         if constexpr (sizeof(T) == 4) {
-            if (tc) s = tc_lu_factor_solve(ctx, M, ld, estride, n, estat, side, ctx->d_flags + 2);
-            else s = run_lu<T, NB, QN>(ctx, M, ld, estride, ipiv, estat, n, false);
+            if (tc) s = tc_lu_factor_solve(ctx, M, ld, estride, n, estat, side, ctx->d_flags + 2, tl.nrhs);
+            else s = run_lu<T, NB, QN>(ctx, tl, M, ld, estride, ipiv, estat, n, false);
         } else {
-            s = run_lu<T, NB, QN>(ctx, M, ld, estride, ipiv, estat, n, false);
+            s = run_lu<T, NB, QN>(ctx, tl, M, ld, estride, ipiv, estat, n, false);
         }
         if (s) return s;
+        // the source column of the refined modes: its own FP64 copy and residual
+        auto src_residual = [&](int rmode) {
+            ProfScope ps(ctx, "residual", 1, (double)n * t.nu * (rmode == 2 ? 20.0 : 36.0));
+            k_residual_src<T><<<(unsigned)n, kThreads, 0, ctx->stream>>>(t, h, he, ka, om, ex->source + e0 * t.nu, M, ld,
+                                                                       estride, Xs, rmode, nullptr, n);
+        };
         void* o_i2o = (unsigned char*)in2out + (size_t)e0 * t.nin * t.nin * osz;
         void* o_i2m = (unsigned char*)in2sol + (size_t)e0 * t.nm * t.nin * osz;
         if (want_res) {
@@ -1056,19 +1219,21 @@ elrt_status build_chunked(elrt_ctx* ctx, int64_t E, double h, const double* h_el
                 s = run_residual_ff(ctx, h, he, ka, om, M, ld, estride, (ff*)X64, 0, maxres, n);
             else
                 s = run_residual<T>(ctx, h, he, ka, om, M, ld, estride, X64, 0, maxres, n);
+            if (Xs) src_residual(0);
             // the last correction needs no residual unless statistics or status words are wanted;
             // on the FP32 path the restriction then adds it on the fly (no pass over X)
             const bool last_residual = stats || elem_status;
             bool pending_d = false;
             for (int it = 0; it < (ir ? steps : 0) && !s; ++it) {
                 if constexpr (sizeof(T) == 4) {
-                    if (tc) s = tc_lu_resolve(ctx, M, ld, estride, n, side, ctx->d_flags + 2);
-                    else s = run_lu<T, NB, QN>(ctx, M, ld, estride, ipiv, estat, n, true);
+                    if (tc) s = tc_lu_resolve(ctx, M, ld, estride, n, side, ctx->d_flags + 2, tl.nrhs);
+                    else s = run_lu<T, NB, QN>(ctx, tl, M, ld, estride, ipiv, estat, n, true);
                 } else {
-                    s = run_lu<T, NB, QN>(ctx, M, ld, estride, ipiv, estat, n, true);
+                    s = run_lu<T, NB, QN>(ctx, tl, M, ld, estride, ipiv, estat, n, true);
                 }
                 if (s) break;
                 const int rmode = (it + 1 == steps && !last_residual) ? 2 : 1;
+                if (Xs) src_residual(rmode);
                 if constexpr (sizeof(T) == 4) {
                     if (rmode == 2) pending_d = true;
                     else s = run_residual_ff(ctx, h, he, ka, om, M, ld, estride, (ff*)X64, rmode, maxres, n);
@@ -1084,6 +1249,15 @@ elrt_status build_chunked(elrt_ctx* ctx, int64_t E, double h, const double* h_el
             }
             if constexpr (sizeof(T) == 4) {
                 const float* D = pending_d ? (const float*)M + t.nu : nullptr;
+                if (ex && ex->in2rad) {
+                    void* rad = (unsigned char*)ex->in2rad + (size_t)e0 * t.nu * t.nin * osz;
+                    if (out_dtype == ELRT_F32)
+                        k_write_rad_ff<float><<<(unsigned)n, kThreads, 0, ctx->stream>>>(t, (const ff*)X64, D, ld, estride,
+                                                                                       (float*)rad, n);
+                    else
+                        k_write_rad_ff<double><<<(unsigned)n, kThreads, 0, ctx->stream>>>(t, (const ff*)X64, D, ld, estride,
+                                                                                        (double*)rad, n);
+                }
                 if (out_dtype == ELRT_F32)
                     s = run_restrict_ff<float>(ctx, (const ff*)X64, D, ld, estride, (float*)o_i2o, (float*)o_i2m, estat,
                                                n);
@@ -1091,6 +1265,15 @@ elrt_status build_chunked(elrt_ctx* ctx, int64_t E, double h, const double* h_el
                     s = run_restrict_ff<double>(ctx, (const ff*)X64, D, ld, estride, (double*)o_i2o, (double*)o_i2m,
                                                 estat, n);
             } else {
+                if (ex && ex->in2rad) {
+                    void* rad = (unsigned char*)ex->in2rad + (size_t)e0 * t.nu * t.nin * osz;
+                    if (out_dtype == ELRT_F32)
+                        k_write_rad<double, float><<<(unsigned)n, kThreads, 0, ctx->stream>>>(
+                            t, X64, t.nin, (int64_t)t.nu * t.nin, (float*)rad, n);
+                    else
+                        k_write_rad<double, double><<<(unsigned)n, kThreads, 0, ctx->stream>>>(
+                            t, X64, t.nin, (int64_t)t.nu * t.nin, (double*)rad, n);
+                }
                 if (out_dtype == ELRT_F32)
                     s = run_restrict<double, float>(ctx, X64, t.nin, (int64_t)t.nu * t.nin, 0, (float*)o_i2o,
                                                     (float*)o_i2m, estat, n);
@@ -1099,12 +1282,32 @@ elrt_status build_chunked(elrt_ctx* ctx, int64_t E, double h, const double* h_el
                                                      (double*)o_i2m, estat, n);
             }
         } else {
+            if (ex && ex->in2rad) {
+                void* rad = (unsigned char*)ex->in2rad + (size_t)e0 * t.nu * t.nin * osz;
+                if (out_dtype == ELRT_F32)
+                    k_write_rad<T, float><<<(unsigned)n, kThreads, 0, ctx->stream>>>(t, M + t.nu, ld, estride, (float*)rad, n);
+                else
+                    k_write_rad<T, double><<<(unsigned)n, kThreads, 0, ctx->stream>>>(t, M + t.nu, ld, estride, (double*)rad,
+                                                                                     n);
+            }
             if (out_dtype == ELRT_F32)
                 s = run_restrict<T, float>(ctx, M, ld, estride, t.nu, (float*)o_i2o, (float*)o_i2m, estat, n);
             else
                 s = run_restrict<T, double>(ctx, M, ld, estride, t.nu, (double*)o_i2o, (double*)o_i2m, estat, n);
         }
         if (s) return s;
+        if (has_src) {
+            double* fo = ex->f2o + e0 * t.nin;
+            double* fm = ex->f2m + e0 * t.nm;
+            double* fu = ex->f2u ? ex->f2u + e0 * t.nu : nullptr;
+            if (Xs)
+                k_restrict_src<double><<<(unsigned)n, kThreads, 0, ctx->stream>>>(t, Xs, 1, t.nu, fo, fm, fu, estat, n);
+            else
+                k_restrict_src<T><<<(unsigned)n, kThreads, 0, ctx->stream>>>(t, M + t.nu + t.nin, ld, estride, fo, fm, fu,
+                                                                           estat, n);
+            s = cuda_check(ctx, cudaGetLastError(), "source restriction launch");
+            if (s) return s;
+        }
         ProfScope ps(ctx, "status", elem_status ? 2 : 1);
         k_reduce_status<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(
             estat, want_res ? maxres : nullptr, n, ctx->d_flags + 1, (unsigned long long*)(ctx->d_flags + 4));
@@ -1138,13 +1341,13 @@ elrt_status build_chunked(elrt_ctx* ctx, int64_t E, double h, const double* h_el
 
 elrt_status local_build(elrt_ctx* ctx, int64_t E, double h, const double* h_elem, const double* kappa,
                         const double* omega, int mode, int refine_steps, int out_dtype, void* in2out, void* in2sol,
-                        int32_t* elem_status, elrt_local_stats* stats) {
+                        int32_t* elem_status, elrt_local_stats* stats, const elrt_local_extras* extras) {
     if (mode == ELRT_LOCAL_FP64)
         return build_chunked<double, 16, 4>(ctx, E, h, h_elem, kappa, omega, mode, refine_steps, out_dtype, in2out,
-                                            in2sol, elem_status, stats);
+                                            in2sol, elem_status, stats, extras);
     if (mode == ELRT_LOCAL_FP32_IR || mode == ELRT_LOCAL_TF32_IR)
         return build_chunked<float, 32, 8>(ctx, E, h, h_elem, kappa, omega, mode, refine_steps, out_dtype, in2out,
-                                           in2sol, elem_status, stats);
+                                           in2sol, elem_status, stats, extras);
     return ctx_fail(ctx, ELRT_EINVAL, "local mode not available in this build");
 }
 

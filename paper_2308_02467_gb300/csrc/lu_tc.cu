@@ -858,8 +858,8 @@ elrt_status rowcol(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, int64_t
 // backward substitution on the right-hand-side columns: X_J = U11^{-1} X_J, then the rows above
 // lose U[0..J, J..J+jb) X_J
 elrt_status backward_sweep_tc(elrt_ctx* ctx, const TcMaps& mp, float* M, int64_t ld, int64_t estride, int64_t E,
-                              const float* Tinv, float* Ut, int* err) {
-    const int nu = ctx->tab.nu, nin = ctx->tab.nin;
+                              const float* Tinv, float* Ut, int* err, int nin) {
+    const int nu = ctx->tab.nu;
     const int last = ((nu - 1) / NBP) * NBP;
     for (int J = last; J >= 0; J -= NBP) {
         const int jb = std::min(NBP, nu - J);
@@ -892,10 +892,10 @@ void diag_block(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, int64_t E,
 }  // namespace
 
 // Factor every element's matrix without pivoting and solve for its right-hand sides (columns
-// [nu, nu + nin)).  side: tc_lu_side_floats() floats per element.  estat[e] |= 1 on a tiny pivot.
+// [nu, nu + nrhs)).  side: tc_lu_side_floats() floats per element.  estat[e] |= 1 on a tiny pivot.
 elrt_status tc_lu_factor_solve(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, int64_t E, int* estat, float* side,
-                               int* err) {
-    const int nu = ctx->tab.nu, nin = ctx->tab.nin, ncols = nu + nin;
+                               int* err, int nrhs) {
+    const int nu = ctx->tab.nu, ncols = nu + nrhs;
     const Side sd = carve(side, E, ld);
     TcMaps mp;
     elrt_status s = prepare(ctx, M, ld, estride, sd.Ut, E, &mp);
@@ -924,12 +924,13 @@ elrt_status tc_lu_factor_solve(elrt_ctx* ctx, float* M, int64_t ld, int64_t estr
         if (!s) s = update<64>(ctx, mp, M, ld, estride, E, J, jb, 0, J + jb, nu, J + jb, ncols, err);
         if (s) return s;
     }
-    return backward_sweep_tc(ctx, mp, M, ld, estride, E, sd.Tinv, sd.Ut, err);
+    return backward_sweep_tc(ctx, mp, M, ld, estride, E, sd.Tinv, sd.Ut, err, nrhs);
 }
 
-// Re-solve A D = R for the right-hand sides in columns [nu, nu + nin) with the stored factors.
-elrt_status tc_lu_resolve(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, int64_t E, float* side, int* err) {
-    const int nu = ctx->tab.nu, nin = ctx->tab.nin;
+// Re-solve A D = R for the right-hand sides in columns [nu, nu + nrhs) with the stored factors.
+elrt_status tc_lu_resolve(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, int64_t E, float* side, int* err,
+                          int nrhs) {
+    const int nu = ctx->tab.nu, nin = nrhs;
     const Side sd = carve(side, E, ld);
     TcMaps mp;
     elrt_status s = prepare(ctx, M, ld, estride, sd.Ut, E, &mp);
@@ -940,7 +941,7 @@ elrt_status tc_lu_resolve(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, 
         if (!s) s = update<64>(ctx, mp, M, ld, estride, E, J, jb, 0, J + jb, nu, nu, nu + nin, err);
         if (s) return s;
     }
-    return backward_sweep_tc(ctx, mp, M, ld, estride, E, sd.Tinv, sd.Ut, err);
+    return backward_sweep_tc(ctx, mp, M, ld, estride, E, sd.Tinv, sd.Ut, err, nrhs);
 }
 
 size_t tc_lu_side_floats(const Tab& t, int64_t ld) {

@@ -97,3 +97,10 @@ def thick_and_thin_elements(n, p, seed):
     h[1], kappa[1] = 0.2, 1.0e-3
     omega = r.uniform(0.9, 1.0, n)
     return kappa, omega, h
+
+
+def lib_source(problem):
+    """The problem's volume source at the library's LGL nodes, [E][N][nm] (cell k, node i)."""
+    import paper_2308_02467_gb300 as E
+    x, z = E.elrt_node_coords(problem.p, problem.n_angles, problem.nx, problem.nz, problem.h)
+    return np.ascontiguousarray(np.transpose(problem.source(x, z), (0, 2, 1)))
