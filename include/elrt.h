@@ -139,6 +139,14 @@ elrt_status elrt_set_stream(elrt_ctx* ctx, void* stream);
  * it when a restart cycle lowers the true residual by less than 10%.  ELRT_KRYLOV_F32: the FP32
  * operator everywhere.  FP64 operators ignore the setting.  ELRT_EINVAL on another value. */
 elrt_status elrt_set_krylov_op(elrt_ctx* ctx, int32_t op);
+/* CUDA-graph replay of the skeleton GMRES (on by default): each restart cycle -- restart residual,
+ * convergence test on the device, restart-length Arnoldi steps, update -- is captured once per
+ * solve and Arnoldi operator and replayed, with one host synchronisation per cycle instead of two
+ * and no per-launch host cost.  The results are those of plain launches (the same kernels in the
+ * same order); the one difference is that a stalled FP16 cycle switches the Arnoldi operator to
+ * FP32 from the following cycle on, one cycle later.  Off (0) or while kernel timing is enabled:
+ * plain launches. */
+elrt_status elrt_set_graphs(elrt_ctx* ctx, int32_t on);
 const char* elrt_status_str(elrt_status s);
 const char* elrt_last_error(const elrt_ctx* ctx);   /* message of the last failing call (or "") */
 

@@ -86,6 +86,7 @@ _sig = {
     "elrt_destroy": (_i32, [_vp]),
     "elrt_set_stream": (_i32, [_vp, _vp]),
     "elrt_set_krylov_op": (_i32, [_vp, _i32]),
+    "elrt_set_graphs": (_i32, [_vp, _i32]),
     "elrt_status_str": (C.c_char_p, [_i32]),
     "elrt_last_error": (C.c_char_p, [_vp]),
     "elrt_assemble": (_i32, [_vp, _i64, _d, _vp, _vp, _vp, _vp, _vp]),
@@ -273,6 +274,10 @@ class Context:
 
     def elrt_launch_count(self):
         return _lib.elrt_launch_count(self._h)
+
+    def elrt_set_graphs(self, on=True):
+        """CUDA-graph replay of the GMRES restart cycles (default on)."""
+        _check(_lib.elrt_set_graphs(self._h, int(bool(on))), self._h)
 
     def elrt_set_krylov_op(self, op):
         """KRYLOV_F16 (default) or KRYLOV_F32: operator of the Arnoldi-step matvecs (FP32 in2out)."""

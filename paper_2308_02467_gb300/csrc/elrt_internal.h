@@ -52,6 +52,7 @@ struct elrt_ctx {
     void* gm16 = nullptr;   // FP16 copy of the skeleton operator (Arnoldi steps)
     size_t gm16_bytes = 0;
     int krylov_op = ELRT_KRYLOV_F16;
+    int graphs = 1;         // replay GMRES restart cycles from captured CUDA graphs
     void* ops = nullptr;    // in2out / in2sol of elrt_solve_field
     size_t ops_bytes = 0;
     void* vec = nullptr;    // skeleton of elrt_solve_field when the caller passes none

@@ -1040,13 +1040,16 @@ __global__ void __launch_bounds__(kThreads) k_update_x(const V* __restrict__ Vb,
     }
 }
 
+// Start of a restart cycle.  A restart residual at or below the tolerance (or not finite) ends the
+// solve on the device: the cycle's kernels see done and do nothing, and j_done stays 0.
 __global__ void k_cycle_start(GmState* st, double* gv, int m, const double* beta, double* sc0) {
     if (sc0) *sc0 = 1.0;
-    st->done = 0;
+    const double b = *beta;
+    st->done = (b > st->tol && isfinite(b)) ? 0 : 1;
     st->j_done = 0;
-    st->beta = *beta;
-    st->res = *beta;
-    gv[0] = *beta;
+    st->beta = b;
+    st->res = b;
+    gv[0] = b;
     for (int i = 1; i <= m; ++i) gv[i] = 0.0;
 }
 
@@ -1568,34 +1571,26 @@ elrt_status gmres(elrt_ctx* ctx, int nx, int nz, const void* Aop, const double* 
     int its = 0, cycles = 0;
     double rel = 1.0, beta_prev = 0.0;
     bool converged = false;
-    for (;;) {
-        // r = b - (I - A_int) x, beta = ||r||
-        s = launch_gemv<A, X>(ctx, nx, nz, rows, Aop, x, nullptr, x, 1, -1, r, nullptr);
-        if (s) return s;
+    int* hflag = (int*)((unsigned char*)ctx->h_pinned + 2048);
+    // restart residual r = b - (I - A_int) x and beta = ||r||
+    auto enqueue_residual = [&]() -> elrt_status {
+        elrt_status e = launch_gemv<A, X>(ctx, nx, nz, rows, Aop, x, nullptr, x, 1, -1, r, nullptr);
+        if (e) return e;
         { ProfScope ps(ctx, "krylov", 1, kv(3, n, sizeof(X))); k_bminus<X><<<gb, kThreads, 0, sm>>>(b, r, n); }
         { ProfScope ps(ctx, "krylov", 1, kv(1, n, sizeof(X))); k_dots<X><<<dim3(nblk, 1), kThreads, 0, sm>>>(r, n, r, partial, nullptr); }
         { ProfScope ps(ctx, "krylov"); k_dots_finish<<<1, kThreads, 0, sm>>>(partial, nblk, scal + 1, 2, nullptr); }
-        s = cuda_check(ctx, cudaMemcpyAsync(ctx->h_pinned, scal + 1, sizeof(double), cudaMemcpyDeviceToHost, sm), "read beta");
-        if (!s) s = cuda_check(ctx, cudaStreamSynchronize(sm), "sync beta");
-        if (s) return s;
-        prof_flush(ctx);
-        const double beta = *(double*)ctx->h_pinned;
-        rel = beta / bnorm;
-        if (!(beta > rtol * bnorm) || !isfinite(beta)) {
-            converged = isfinite(beta);
-            break;
-        }
-        if (its >= max_iter) break;
-        // a cycle on the FP16 copy that took the true residual down by less than 10%: the rounding
-        // of the copy limits the refinement, continue with the FP32 operator
-        if (use16 && cycles > 0 && beta > 0.9 * beta_prev) use16 = false;
-        beta_prev = beta;
+        return ELRT_OK;
+    };
+    // v_0 = r / beta, then mj Arnoldi steps with the FP16 (f16) or the given operator, the small
+    // least-squares solve and x += V y; ends with the state and the matvec's timeout flag copied to
+    // pinned host memory
+    auto enqueue_cycle = [&](bool f16, int mj) -> elrt_status {
+        elrt_status e = ELRT_OK;
         {
             ProfScope ps(ctx, "krylov", 1, kv(1, n, sizeof(X)) + kv(1, n, sizeof(V)));
             k_scale<X, V><<<gb, kThreads, 0, sm>>>(r, Vb, n, scal + 1, nullptr);
         }
         { ProfScope ps(ctx, "krylov"); k_cycle_start<<<1, 1, 0, sm>>>(st, gv, m, scal + 1, arn4 ? arn->sc : nullptr); }
-        const int mj = std::min(m, max_iter - its);
         for (int j = 0; j < mj; ++j) {
             V* vj = Vb + (size_t)j * n;
             V* w = Vb + (size_t)(j + 1) * n;
@@ -1603,10 +1598,10 @@ elrt_status gmres(elrt_ctx* ctx, int nx, int nz, const void* Aop, const double* 
             if constexpr (std::is_same<V, float>::value) {
                 if (arn4) {  // matvec with the first Gram-Schmidt pass, then two launches
                     const ArnFuse fz{arn, partial, Vb, n, j};
-                    if (use16 && tc16) s = launch_gemv_tc(ctx, map16, nx, nz, vj, w, st, fz);
-                    else if (use16) s = launch_gemv<__half, V>(ctx, nx, nz, rows, A16, vj, nullptr, vj, 1, -1, w, st, fz);
-                    else s = launch_gemv<A, V>(ctx, nx, nz, rows, Aop, vj, nullptr, vj, 1, -1, w, st, fz);
-                    if (s) return s;
+                    if (f16 && tc16) e = launch_gemv_tc(ctx, map16, nx, nz, vj, w, st, fz);
+                    else if (f16) e = launch_gemv<__half, V>(ctx, nx, nz, rows, A16, vj, nullptr, vj, 1, -1, w, st, fz);
+                    else e = launch_gemv<A, V>(ctx, nx, nz, rows, Aop, vj, nullptr, vj, 1, -1, w, st, fz);
+                    if (e) return e;
                     const double vb = 4.0 * n;
                     // (bytes counted as if the second pass ran: the bound on what these launches move)
                     { ProfScope ps(ctx, "krylov", 1, (2 * j + 5) * vb); k_arn_axdots<<<nblk, kArnThreads, 0, sm>>>(Vb, n, j, partial, arn, st); }
@@ -1616,12 +1611,12 @@ elrt_status gmres(elrt_ctx* ctx, int nx, int nz, const void* Aop, const double* 
                     }
                     continue;
                 }
-                if (use16) s = launch_gemv<__half, V>(ctx, nx, nz, rows, A16, vj, nullptr, vj, 1, -1, w, st);
-                else s = launch_gemv<A, V>(ctx, nx, nz, rows, Aop, vj, nullptr, vj, 1, -1, w, st);
+                if (f16) e = launch_gemv<__half, V>(ctx, nx, nz, rows, A16, vj, nullptr, vj, 1, -1, w, st);
+                else e = launch_gemv<A, V>(ctx, nx, nz, rows, Aop, vj, nullptr, vj, 1, -1, w, st);
             } else {
-                s = launch_gemv<A, V>(ctx, nx, nz, rows, Aop, vj, nullptr, vj, 1, -1, w, st);
+                e = launch_gemv<A, V>(ctx, nx, nz, rows, Aop, vj, nullptr, vj, 1, -1, w, st);
             }
-            if (s) return s;
+            if (e) return e;
             // classical Gram-Schmidt, twice
             const size_t sv = sizeof(V);
             { ProfScope ps(ctx, "krylov", 1, kv(j + 2, n, sv)); k_dots<V><<<dim3(nblk, j + 1), kThreads, 0, sm>>>(Vb, n, w, partial, st); }
@@ -1642,21 +1637,109 @@ elrt_status gmres(elrt_ctx* ctx, int nx, int nz, const void* Aop, const double* 
             ProfScope ps(ctx, "krylov", 1, kv(m, n, sizeof(V)) + kv(2, n, sizeof(X)));
             k_update_x<V, X><<<gb, kThreads, 0, sm>>>(Vb, n, yv, arn4 ? arn->sc : nullptr, x, st);
         }
-        s = cuda_check(ctx, cudaGetLastError(), "gmres launches");
-        if (s) return s;
-        int* hflag = (int*)((unsigned char*)ctx->h_pinned + 2048);
-        s = cuda_check(ctx, cudaMemcpyAsync(hst, st, sizeof(GmState), cudaMemcpyDeviceToHost, sm), "read state");
-        if (!s)
-            s = cuda_check(ctx, cudaMemcpyAsync(hflag, ctx->d_flags + kGemvFlag, sizeof(int), cudaMemcpyDeviceToHost, sm),
+        e = cuda_check(ctx, cudaGetLastError(), "gmres launches");
+        if (!e) e = cuda_check(ctx, cudaMemcpyAsync(hst, st, sizeof(GmState), cudaMemcpyDeviceToHost, sm), "read state");
+        if (!e)
+            e = cuda_check(ctx, cudaMemcpyAsync(hflag, ctx->d_flags + kGemvFlag, sizeof(int), cudaMemcpyDeviceToHost, sm),
                            "read flag");
-        if (!s) s = cuda_check(ctx, cudaStreamSynchronize(sm), "sync cycle");
-        if (s) return s;
+        return e;
+    };
+    // Graph path (ctx->graphs, no per-launch timing): a whole restart cycle -- restart residual,
+    // convergence test on the device, m Arnoldi steps, update -- is captured once per Arnoldi
+    // operator and replayed, one host synchronisation per cycle.  The FP16-to-FP32 switch then acts
+    // from the cycle after the one that stalled.  A last partial cycle (max_iter) and the final
+    // residual check run as plain launches.
+    cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+    int64_t gnodes[2] = {0, 0};
+    bool graphs = ctx->graphs && !ctx->profiling;
+    auto capture = [&](int v) -> bool {
+        cudaGraph_t g = nullptr;
+        const int64_t l0 = ctx->launches;
+        if (cudaStreamBeginCapture(sm, cudaStreamCaptureModeRelaxed) != cudaSuccess) return false;
+        elrt_status e = enqueue_residual();
+        if (!e) e = enqueue_cycle(v == 1, m);
+        const cudaError_t ce = cudaStreamEndCapture(sm, &g);
+        gnodes[v] = ctx->launches - l0;
+        ctx->launches = l0;  // counted again at every replay
+        bool ok = !e && ce == cudaSuccess && g && cudaGraphInstantiate(&gexec[v], g, 0) == cudaSuccess;
+        if (g) cudaGraphDestroy(g);
+        if (!ok) {
+            gexec[v] = nullptr;
+            cudaGetLastError();
+            ctx->last_error.clear();
+        }
+        return ok;
+    };
+    auto release = [&]() {
+        for (auto& ge : gexec)
+            if (ge) cudaGraphExecDestroy(ge);
+    };
+    for (;;) {
+        if (graphs && its + m <= max_iter) {
+            const int v = use16 ? 1 : 0;
+            if (!gexec[v] && !capture(v)) {
+                graphs = false;  // capture not possible here: plain launches from now on
+                continue;
+            }
+            s = cuda_check(ctx, cudaGraphLaunch(gexec[v], sm), "graph launch");
+            if (!s) s = cuda_check(ctx, cudaStreamSynchronize(sm), "sync cycle");
+            if (s) {
+                release();
+                return s;
+            }
+            ctx->launches += gnodes[v];
+            if (*hflag) {
+                release();
+                return ctx_fail(ctx, ELRT_ETIMEOUT, "a copy wait of the streaming matvec timed out");
+            }
+            const double beta = hst->beta;
+            rel = beta / bnorm;
+            if (!(beta > rtol * bnorm) || !isfinite(beta)) {
+                converged = isfinite(beta);
+                break;
+            }
+            if (use16 && cycles > 0 && beta > 0.9 * beta_prev) use16 = false;
+            beta_prev = beta;
+            its += hst->j_done;
+            ++cycles;
+            if (hst->j_done == 0) break;  // no progress possible
+            continue;
+        }
+        s = enqueue_residual();
+        if (!s) s = cuda_check(ctx, cudaMemcpyAsync(ctx->h_pinned, scal + 1, sizeof(double), cudaMemcpyDeviceToHost, sm), "read beta");
+        if (!s) s = cuda_check(ctx, cudaStreamSynchronize(sm), "sync beta");
+        if (s) {
+            release();
+            return s;
+        }
         prof_flush(ctx);
-        if (*hflag) return ctx_fail(ctx, ELRT_ETIMEOUT, "a copy wait of the streaming matvec timed out");
+        const double beta = *(double*)ctx->h_pinned;
+        rel = beta / bnorm;
+        if (!(beta > rtol * bnorm) || !isfinite(beta)) {
+            converged = isfinite(beta);
+            break;
+        }
+        if (its >= max_iter) break;
+        // a cycle on the FP16 copy that took the true residual down by less than 10%: the rounding
+        // of the copy limits the refinement, continue with the FP32 operator
+        if (use16 && cycles > 0 && beta > 0.9 * beta_prev) use16 = false;
+        beta_prev = beta;
+        s = enqueue_cycle(use16, std::min(m, max_iter - its));
+        if (!s) s = cuda_check(ctx, cudaStreamSynchronize(sm), "sync cycle");
+        if (s) {
+            release();
+            return s;
+        }
+        prof_flush(ctx);
+        if (*hflag) {
+            release();
+            return ctx_fail(ctx, ELRT_ETIMEOUT, "a copy wait of the streaming matvec timed out");
+        }
         its += hst->j_done;
         ++cycles;
         if (hst->j_done == 0) break;  // no progress possible
     }
+    release();
     if constexpr (own_x) {
         ProfScope ps(ctx, "krylov", 1, 16.0 * n);
         k_ff2d<<<gb, kThreads, 0, sm>>>(x, xout, n);

@@ -395,6 +395,12 @@ elrt_status elrt_set_krylov_op(elrt_ctx* ctx, int32_t op) {
     return ELRT_OK;
 }
 
+elrt_status elrt_set_graphs(elrt_ctx* ctx, int32_t on) {
+    if (!ctx) return ctx_fail(nullptr, ELRT_EINVAL, "elrt_set_graphs: null context");
+    ctx->graphs = on ? 1 : 0;
+    return ELRT_OK;
+}
+
 const char* elrt_status_str(elrt_status s) {
     switch (s) {
         case ELRT_OK: return "ok";

@@ -110,7 +110,10 @@ extern "C" elrt_status elrt_solve_batch(elrt_ctx* const* ctxs, int32_t n_ctx, co
             first = ctx_fail(nullptr, ELRT_ECUDA, "worker stream");
         for (int k = 0; k < n_ctx && !first; ++k) {
             first = elrt_create(&wctx[w][k], &ctxs[k]->disc, streams[w]);
-            if (!first) wctx[w][k]->krylov_op = ctxs[k]->krylov_op;
+            if (!first) {
+                wctx[w][k]->krylov_op = ctxs[k]->krylov_op;
+                wctx[w][k]->graphs = ctxs[k]->graphs;
+            }
         }
     }
     auto per_field_ops = [&](int f) {
