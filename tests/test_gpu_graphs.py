@@ -1,6 +1,7 @@
 """CUDA-graph replay of the GMRES restart cycles gives the results of plain launches: the same
-kernels in the same order, so the same iterations, residual and solution; the launch count still
-counts every kernel of every replayed cycle."""
+kernels in the same order, so the same iterations, residual and solution.  The launch count counts
+every kernel of every replayed cycle, including the last cycle's, which the convergence test on the
+device turns into no-ops (plain launches stop on the host before them)."""
 
 import numpy as np
 import pytest
@@ -40,7 +41,7 @@ def test_graph_replay_equals_plain_launches(lib, dtype, nx, p, N):
     assert g[0] == n[0] and g[1] == n[1] and g[2] == n[2] == 1, (g[:3], n[:3])
     assert g[3] == n[3]
     assert np.array_equal(g[4], n[4])
-    assert g[5] == n[5], (g[5], n[5])          # every replayed kernel counted
+    assert g[5] >= n[5], (g[5], n[5])          # every replayed kernel counted
 
 
 def test_graph_replay_iteration_limit(lib):
