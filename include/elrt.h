@@ -350,6 +350,42 @@ elrt_status elrt_solve_batch(elrt_ctx* const* ctxs, int32_t n_ctx, const elrt_fi
                              int32_t n_fields, const elrt_solve_opts* opts, size_t wave_bytes, int32_t workers,
                              double* const* means, elrt_field_stats* stats);
 
+/* ---------------------------------------------------------------- autotuning */
+
+/* Launch parameters the library picks per discretisation, and an autotuner that measures them (the
+ * paper has no counterpart: these are implementation choices of this library):
+ *   local_chunk  elements per local-build chunk (0: as many as 16 GB of workspace hold);
+ *   lu_pairs     tensor-core LU schedule: 1 = panels in pairs, the second factored after a rank-64
+ *                update of its rows and columns, the rest of the matrix updated by both with one
+ *                rank-128 tensor-core update; 0 = panels one at a time with rank-64 updates;
+ *   restart      GMRES restart length of solve calls that pass restart = 0 (default 12).
+ * elrt_autotune builds the local operators of `field` (device inputs as elrt_solve_field) with
+ * every candidate (local_chunk in {0, 512, 1024, ...} below the field's element count, lu_pairs in
+ * {1, 0} for ELRT_LOCAL_TF32_IR), timing each by CUDA events (one warm-up, mean of two), keeps the
+ * fastest, then solves the skeleton system to rtol with restart lengths {8, 12, 16, 20, 30} and
+ * keeps the fastest converged one.  It allocates its own temporary operators (the field's in2out
+ * and in2sol in FP32), synchronises, and leaves the context unchanged on failure.  With the
+ * environment variable ELRT_TUNE_CACHE naming a file, each result is appended there as one text
+ * line, and elrt_create applies the last line that matches the device and the discretisation. */
+typedef struct {
+    int64_t local_chunk;
+    int32_t lu_pairs;
+    int32_t restart;
+    int32_t n_candidates;      /* configurations timed */
+    double local_ms_default;   /* local build with the default parameters */
+    double local_ms_best;      /* ... with the chosen ones */
+    double solve_ms_default;   /* skeleton solve with restart 12 */
+    double solve_ms_best;      /* ... with the chosen restart */
+} elrt_tune_report;
+
+elrt_status elrt_autotune(elrt_ctx* ctx, const elrt_field* field, int32_t mode, int32_t refine_steps,
+                          double rtol, elrt_tune_report* report);
+elrt_status elrt_get_tuning(const elrt_ctx* ctx, int64_t* local_chunk, int32_t* lu_pairs, int32_t* restart,
+                            int32_t* tuned);
+/* Sets the three parameters by hand (ELRT_EINVAL: local_chunk < 0, lu_pairs not 0/1, restart
+ * outside 1..200). */
+elrt_status elrt_set_tuning(elrt_ctx* ctx, int64_t local_chunk, int32_t lu_pairs, int32_t restart);
+
 /* ---------------------------------------------------------------- element network (Sec. 2.4) */
 
 /* The learned local solver of eq. param2sol: a fully connected network (Sec. 2.4.1)

@@ -36,6 +36,12 @@ class LocalExtras(C.Structure):
                 ("in2rad", C.c_void_p)]
 
 
+class TuneReport(C.Structure):
+    _fields_ = [("local_chunk", C.c_int64), ("lu_pairs", C.c_int32), ("restart", C.c_int32),
+                ("n_candidates", C.c_int32), ("local_ms_default", C.c_double), ("local_ms_best", C.c_double),
+                ("solve_ms_default", C.c_double), ("solve_ms_best", C.c_double)]
+
+
 class SolveStats(C.Structure):
     _fields_ = [("iterations", C.c_int32), ("restarts", C.c_int32), ("converged", C.c_int32),
                 ("rel_residual", C.c_double)]
@@ -87,6 +93,9 @@ _sig = {
     "elrt_set_stream": (_i32, [_vp, _vp]),
     "elrt_set_krylov_op": (_i32, [_vp, _i32]),
     "elrt_set_graphs": (_i32, [_vp, _i32]),
+    "elrt_autotune": (_i32, [_vp, _P(Field), _i32, _i32, _d, _P(TuneReport)]),
+    "elrt_get_tuning": (_i32, [_vp, _P(_i64), _P(_i32), _P(_i32), _P(_i32)]),
+    "elrt_set_tuning": (_i32, [_vp, _i64, _i32, _i32]),
     "elrt_status_str": (C.c_char_p, [_i32]),
     "elrt_last_error": (C.c_char_p, [_vp]),
     "elrt_assemble": (_i32, [_vp, _i64, _d, _vp, _vp, _vp, _vp, _vp]),
@@ -274,6 +283,23 @@ class Context:
 
     def elrt_launch_count(self):
         return _lib.elrt_launch_count(self._h)
+
+    def elrt_autotune(self, nx, nz, h, kappa, omega, inflow, mode=LOCAL_TF32_IR, refine_steps=1, rtol=1e-8):
+        """Measures the context's launch parameters on this field and keeps the fastest; returns the
+        report as a dict."""
+        self._sync_stream()
+        f = _field(self, nx, nz, h, kappa, omega, inflow)
+        r = TuneReport()
+        _check(_lib.elrt_autotune(self._h, C.byref(f), int(mode), int(refine_steps), float(rtol), C.byref(r)), self._h)
+        return {k: getattr(r, k) for k, _ in TuneReport._fields_}
+
+    def elrt_get_tuning(self):
+        c, p_, r, t = C.c_int64(), C.c_int32(), C.c_int32(), C.c_int32()
+        _check(_lib.elrt_get_tuning(self._h, C.byref(c), C.byref(p_), C.byref(r), C.byref(t)), self._h)
+        return {"local_chunk": c.value, "lu_pairs": p_.value, "restart": r.value, "tuned": t.value}
+
+    def elrt_set_tuning(self, local_chunk=0, lu_pairs=1, restart=12):
+        _check(_lib.elrt_set_tuning(self._h, int(local_chunk), int(lu_pairs), int(restart)), self._h)
 
     def elrt_set_graphs(self, on=True):
         """CUDA-graph replay of the GMRES restart cycles (default on)."""

@@ -38,8 +38,17 @@ __host__ __device__ inline int face_node(int F, int m, int p) {
     }
 }
 
+// Launch parameters the autotuner (tune.cpp) measures and sets; the defaults are the hand-chosen ones.
+struct Tuning {
+    int64_t local_chunk = 0;  // elements per local-build chunk (0: as many as 16 GB of workspace hold)
+    int lu_pairs = 1;         // tensor-core LU: panels in pairs with rank-128 updates (1) or one at a time (0)
+    int restart = 12;         // GMRES restart length of calls that pass restart = 0
+    int tuned = 0;            // 1 once measured or loaded from the cache
+};
+
 struct elrt_ctx {
     elrt_disc disc;
+    Tuning tune;
     Tab tab;
     cudaStream_t stream;
     int device;
@@ -79,6 +88,9 @@ struct ProfScope {
     ~ProfScope();
 };
 void prof_flush(elrt_ctx* ctx);  // call after a stream synchronisation
+
+// ---- autotuning (tune.cpp): apply the cached parameters of this device and discretisation
+void tune_load(elrt_ctx* ctx);
 
 // ---- host helpers implemented in host.cpp
 bool elrt_disc_valid(const elrt_disc* d);

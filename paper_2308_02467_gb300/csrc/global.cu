@@ -1652,20 +1652,33 @@ elrt_status gmres(elrt_ctx* ctx, int nx, int nz, const void* Aop, const double* 
     cudaGraphExec_t gexec[2] = {nullptr, nullptr};
     int64_t gnodes[2] = {0, 0};
     bool graphs = ctx->graphs && !ctx->profiling;
+    // The capture runs on a stream of its own (the context's may be the legacy default stream,
+    // which cannot be captured); the graph is then launched on the context's stream.
     auto capture = [&](int v) -> bool {
+        cudaStream_t cs = nullptr;
+        if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
         cudaGraph_t g = nullptr;
         const int64_t l0 = ctx->launches;
-        if (cudaStreamBeginCapture(sm, cudaStreamCaptureModeRelaxed) != cudaSuccess) return false;
-        elrt_status e = enqueue_residual();
-        if (!e) e = enqueue_cycle(v == 1, m);
-        const cudaError_t ce = cudaStreamEndCapture(sm, &g);
+        const cudaStream_t own = ctx->stream;
+        bool ok = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed) == cudaSuccess;
+        if (ok) {
+            ctx->stream = sm = cs;
+            elrt_status e = enqueue_residual();
+            if (!e) e = enqueue_cycle(v == 1, m);
+            const cudaError_t ce = cudaStreamEndCapture(cs, &g);
+            ctx->stream = sm = own;
+            ok = !e && ce == cudaSuccess && g && cudaGraphInstantiate(&gexec[v], g, 0) == cudaSuccess;
+        }
         gnodes[v] = ctx->launches - l0;
         ctx->launches = l0;  // counted again at every replay
-        bool ok = !e && ce == cudaSuccess && g && cudaGraphInstantiate(&gexec[v], g, 0) == cudaSuccess;
         if (g) cudaGraphDestroy(g);
+        cudaStreamDestroy(cs);
         if (!ok) {
             gexec[v] = nullptr;
-            cudaGetLastError();
+            cudaGetLastError();  // a failed capture leaves no error behind: plain launches follow
             ctx->last_error.clear();
         }
         return ok;
@@ -1795,6 +1808,7 @@ elrt_status global_recover(elrt_ctx* ctx, int nx, int nz, const void* A, int dty
 elrt_status global_solve(elrt_ctx* ctx, int nx, int nz, const void* A, int dtype, const double* inflow, double rtol,
                          int max_iter, int restart, int use_guess, double* x, elrt_solve_stats* stats,
                          const double* f2o) {
+    if (restart == 0) restart = ctx->tune.restart;
     if (restart > kMaxRestart) return ctx_fail(ctx, ELRT_EINVAL, "restart above 200");
     if (dtype == ELRT_F32)
         return gmres<float, float, ff>(ctx, nx, nz, A, inflow, rtol, max_iter, restart, use_guess, x, stats, f2o);

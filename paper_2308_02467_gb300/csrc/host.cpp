@@ -362,6 +362,7 @@ elrt_status elrt_create(elrt_ctx** out, const elrt_disc* disc, void* stream) {
         delete c;
         return s;
     }
+    tune_load(c);
     *out = c;
     return ELRT_OK;
 }
@@ -482,8 +483,8 @@ elrt_status elrt_solve_global(elrt_ctx* ctx, int32_t nx, int32_t nz, const void*
                               double* skeleton, elrt_solve_stats* stats) {
     if (!ctx) return ctx_fail(nullptr, ELRT_EINVAL, "elrt_solve_global: null context");
     if (nx < 1 || nz < 1 || !in2out || !inflow || !skeleton || (dtype != ELRT_F32 && dtype != ELRT_F64) ||
-        !(rtol > 0) || max_iter < 1 || restart < 1 || restart > 200)
-        return ctx_fail(ctx, ELRT_EINVAL, "elrt_solve_global: bad arguments (restart must be 1..200)");
+        !(rtol > 0) || max_iter < 1 || restart < 0 || restart > 200)
+        return ctx_fail(ctx, ELRT_EINVAL, "elrt_solve_global: bad arguments (restart must be 0..200)");
     ctx->last_error.clear();
     if (stats) memset(stats, 0, sizeof(*stats));
     return global_solve(ctx, nx, nz, in2out, dtype, inflow, rtol, max_iter, restart, use_guess, skeleton, stats);
@@ -503,8 +504,8 @@ elrt_status elrt_solve_global_source(elrt_ctx* ctx, int32_t nx, int32_t nz, cons
                                      int32_t restart, int32_t use_guess, double* skeleton, elrt_solve_stats* stats) {
     if (!ctx) return ctx_fail(nullptr, ELRT_EINVAL, "elrt_solve_global_source: null context");
     if (nx < 1 || nz < 1 || !in2out || !inflow || !skeleton || (dtype != ELRT_F32 && dtype != ELRT_F64) ||
-        !(rtol > 0) || max_iter < 1 || restart < 1 || restart > 200)
-        return ctx_fail(ctx, ELRT_EINVAL, "elrt_solve_global_source: bad arguments (restart must be 1..200)");
+        !(rtol > 0) || max_iter < 1 || restart < 0 || restart > 200)
+        return ctx_fail(ctx, ELRT_EINVAL, "elrt_solve_global_source: bad arguments (restart must be 0..200)");
     ctx->last_error.clear();
     if (stats) memset(stats, 0, sizeof(*stats));
     return global_solve(ctx, nx, nz, in2out, dtype, inflow, rtol, max_iter, restart, use_guess, skeleton, stats, f2o);

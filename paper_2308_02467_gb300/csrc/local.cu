@@ -1160,6 +1160,7 @@ elrt_status build_chunked(elrt_ctx* ctx, int64_t E, double h, const double* h_el
                        (want_res ? (size_t)t.nu * t.nin * sizeof(double) : 0) + side_per + src_per;
     const size_t budget = (size_t)16 << 30;
     int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(E, (int64_t)(budget / per)));
+    if (ctx->tune.local_chunk > 0) chunk = std::min<int64_t>(chunk, ctx->tune.local_chunk);
     if (chunk < E) {  // balance the chunks
         const int64_t nch = (E + chunk - 1) / chunk;
         chunk = (E + nch - 1) / nch;

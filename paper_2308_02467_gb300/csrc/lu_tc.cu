@@ -904,7 +904,7 @@ elrt_status tc_lu_factor_solve(elrt_ctx* ctx, float* M, int64_t ld, int64_t estr
     // pairs of full panels a = [J, J+64), b = [J+64, J+128): panel a is factored and applied to
     // panel b's columns and rows only (two narrow rank-64 updates), panel b is factored, and the
     // rest of the matrix takes both in one rank-128 update (half the C traffic of two rank-64 ones)
-    for (; J + 2 * NBP <= nu; J += 2 * NBP) {
+    for (; ctx->tune.lu_pairs && J + 2 * NBP <= nu; J += 2 * NBP) {
         const int Jb = J + NBP, Jn = J + 2 * NBP;
         diag_block(ctx, M, ld, estride, E, J, NBP, sd.Tinv, estat);
         s = rowcol(ctx, M, ld, estride, E, J, NBP, sd.Tinv, Jb, nu, Jb, ncols, 0, sd.Ut, 0);

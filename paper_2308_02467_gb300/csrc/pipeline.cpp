@@ -17,7 +17,7 @@ double ms_since(std::chrono::steady_clock::time_point t0) {
 
 bool opts_ok(const elrt_solve_opts* o) {
     return o && o->mode >= ELRT_LOCAL_FP64 && o->mode <= ELRT_LOCAL_TF32_IR && o->refine_steps >= 0 &&
-           o->refine_steps <= 8 && o->rtol > 0 && o->max_iter >= 1 && o->restart >= 1 && o->restart <= 200 &&
+           o->refine_steps <= 8 && o->rtol > 0 && o->max_iter >= 1 && o->restart >= 0 && o->restart <= 200 &&
            (!o->net || o->learned_tol > 0);
 }
 
@@ -113,6 +113,7 @@ extern "C" elrt_status elrt_solve_batch(elrt_ctx* const* ctxs, int32_t n_ctx, co
             if (!first) {
                 wctx[w][k]->krylov_op = ctxs[k]->krylov_op;
                 wctx[w][k]->graphs = ctxs[k]->graphs;
+                wctx[w][k]->tune = ctxs[k]->tune;
             }
         }
     }
