@@ -175,6 +175,10 @@ def parse():
                     help="held-out elements of the element-network workload scored against refined classical labels")
     ap.add_argument("--no-config5", action="store_true",
                     help="skip the 512x256 lognormal cloud slab (learned vs TF32-IR time-to-solution)")
+    ap.add_argument("--config3-fields", type=int, default=32,
+                    help="fields of the 256-field uneven batch to run (0: skip; 256: the whole workload)")
+    ap.add_argument("--no-refinement", action="store_true",
+                    help="skip the discretisation-error study against over-refined solutions")
     ap.add_argument("--config5-fp64", action="store_true",
                     help="also time the plain FP64 classical GPU path on the 512x256 slab and use it as the reference "
                          "(about 4 more minutes: its local stage alone is 7.8e13 FP64 flops)")
@@ -615,6 +619,154 @@ def config5_section(args, E, W, net, tol):
     return out
 
 
+def config3_section(args, E, W):
+    """Many independent fields of uneven size and degree in one call (elrt_solve_batch): the first
+    `--config3-fields` of the 256 seeded fields (sizes U{16..128}^2, p in {4, 6, 8}, 16 angles,
+    1-5 Gaussian clouds, albedo U[0.9, 1]); TF32-IR local solves with one refinement sweep, GMRES
+    to 1e-8 with each discretisation's autotuned restart length (tuned untimed on a 24 x 24 slab of
+    that degree), CUDA-graph restart cycles, concurrent worker streams.  Sampled elements of
+    several fields are checked against the FP64 oracle's local operators."""
+    import numpy as np
+    import torch
+    from oracle import hdg
+    probs = W.problem_batch_fields(args.config3_fields)
+    degrees = sorted({pr.p for pr in probs})
+    ctxs = [E.Context(p, 16, 0.85, E.ANG_FV0) for p in degrees]
+    tuning = {}
+    for p, c in zip(degrees, ctxs):
+        tp = W.problem_gaussian_slab(n=24, p=p)
+        xs, zs = E.elrt_node_coords(p, 16, 24, 24, tp.h)
+        rep = c.elrt_autotune(24, 24, tp.h, torch.tensor(tp.kappa(xs, zs), device="cuda"),
+                              torch.tensor(tp.omega, device="cuda"), torch.tensor(tp.inflow, device="cuda"),
+                              mode=E.LOCAL_TF32_IR, refine_steps=1, rtol=1e-8)
+        tuning[f"p{p}"] = rep
+    fields, fctx, means = [], [], []
+    for pr in probs:
+        xs, zs = E.elrt_node_coords(pr.p, 16, pr.nx, pr.nz, pr.h)
+        fields.append((pr.nx, pr.nz, pr.h, torch.tensor(pr.kappa(xs, zs), device="cuda"),
+                       torch.tensor(pr.omega, device="cuda"), torch.tensor(pr.inflow, device="cuda")))
+        fctx.append(degrees.index(pr.p))
+        means.append(torch.empty(pr.n_elems, (pr.p + 1) ** 2, dtype=torch.float64, device="cuda"))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    stats = E.elrt_solve_batch(ctxs, fields, fctx, means, mode=E.LOCAL_TF32_IR, refine_steps=1, rtol=1e-8, restart=0)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    n_el = sum(pr.n_elems for pr in probs)
+    per_p = {}
+    for pr, st in zip(probs, stats):
+        d = per_p.setdefault(f"p{pr.p}", {"fields": 0, "elements": 0, "local_ms": 0.0, "global_ms": 0.0,
+                                         "gmres_iterations": 0, "converged": 0})
+        d["fields"] += 1
+        d["elements"] += pr.n_elems
+        d["local_ms"] += st.local_ms
+        d["global_ms"] += st.global_ms
+        d["gmres_iterations"] += st.glob.iterations
+        d["converged"] += int(st.glob.converged == 1)
+    for d in per_p.values():
+        d["local_elements_per_s"] = d["elements"] / (d["local_ms"] / 1000) if d["local_ms"] > 0 else None
+    # sampled elements of the first fields of each degree against the oracle's local operators
+    worst = 0.0
+    checked = 0
+    for p in degrees:
+        for idx in [i for i, pr in enumerate(probs) if pr.p == p][:2]:
+            pr = probs[idx]
+            ctx = ctxs[degrees.index(p)]
+            d = hdg.Disc(p, 16, 0.85)
+            mesh = hdg.Mesh(pr.nx, pr.nz, pr.h)
+            ox, oz = mesh.node_coords(d)
+            sel = [0, pr.n_elems // 2, pr.n_elems - 1]
+            k = fields[idx][3][sel].contiguous()
+            o = fields[idx][4][sel].contiguous()
+            a = torch.empty(len(sel), ctx.nin, ctx.nin, device="cuda", dtype=torch.float32)
+            m = torch.empty(len(sel), ctx.nm, ctx.nin, device="cuda", dtype=torch.float32)
+            ctx.elrt_build_local(k, o, pr.h, a, m, mode=E.LOCAL_TF32_IR, refine_steps=1, stats=False)
+            for q, e in enumerate(sel):
+                ao, mo, _ = d.local_operators(pr.kappa(ox[e], oz[e]) * pr.h / 2, float(pr.omega[e]))
+                worst = max(worst, float(np.abs(a[q].double().cpu().numpy() - ao).max()),
+                            float(np.abs(m[q].double().cpu().numpy() - mo).max()))
+                checked += 1
+    for c in ctxs:
+        c.close()
+    return {"workload": f"first {len(probs)} of the 256 seeded uneven fields (sizes U{{16..128}}^2, p in {{4,6,8}}, "
+                        f"N=16, 1-5 Gaussian clouds)", "fields": len(probs), "elements": n_el,
+            "wall_s": wall, "elements_per_s": n_el / wall, "per_degree": per_p, "tuning": tuning,
+            "all_converged": all(st.glob.converged == 1 for st in stats),
+            "sampled_elements_checked": checked, "sampled_elements_max_abs_diff_vs_oracle": worst,
+            "call": "elrt_solve_batch (waves of 64 GiB operators, 8 worker streams, graph-replayed GMRES cycles)"}
+
+
+def lagrange_matrix(nodes, points):
+    """L[q][a] = l_a(points[q]) for the Lagrange basis on `nodes` (measurement helper: interpolates a
+    nodal solution to other points for the refinement study)."""
+    import numpy as np
+    L = np.ones((len(points), len(nodes)))
+    for a, xa in enumerate(nodes):
+        for b, xb in enumerate(nodes):
+            if b != a:
+                L[:, a] *= (points - xb) / (xa - xb)
+    return L
+
+
+def refinement_section(args, E, W):
+    """Discretisation error against an over-refined solution (the paper's methodology, Sec. 3):
+    the benchmark field (Gaussian cloud slab, N = 16, TF32-IR local solves refined twice, GMRES to
+    1e-10) solved on meshes of 8..64 elements per side at p = 6 against 128 x 128 at p = 6 (h
+    refinement), and at p = 2..8 on 16 x 16 elements against p = 10 (p refinement).  Coarse mean
+    intensities are interpolated (Lagrange, per element) to the reference nodes; relative L2 with
+    the reference's LGL quadrature."""
+    import numpy as np
+    import torch
+
+    def solve(n, p):
+        prob = W.problem_gaussian_slab(n=n, p=p)
+        ctx = E.Context(p, 16, prob.hg_g, E.ANG_FV0)
+        um = torch.empty(prob.n_elems, (p + 1) ** 2, dtype=torch.float64, device="cuda")
+        xs, zs = E.elrt_node_coords(p, 16, n, n, prob.h)
+        st = ctx.elrt_solve_field(n, n, prob.h, torch.tensor(prob.kappa(xs, zs), device="cuda"),
+                                  torch.tensor(prob.omega, device="cuda"), torch.tensor(prob.inflow, device="cuda"), um,
+                                  mode=E.LOCAL_TF32_IR, refine_steps=2, rtol=1e-10, restart=20)
+        ctx.close()
+        return um.cpu().numpy().reshape(n, n, p + 1, p + 1), st  # [iz][ix][b][a]
+
+    def rel_err(coarse, n_c, p_c, ref, n_f, p_f):
+        xi_c, _ = E.elrt_lgl(p_c)
+        xi_f, w_f = E.elrt_lgl(p_f)
+        r = n_f // n_c
+        err = norm = 0.0
+        W2 = np.outer(w_f, w_f)
+        for si in range(r):
+            Lx = lagrange_matrix(xi_c, -1 + (2.0 / r) * (si + (xi_f + 1) / 2))
+            for sj in range(r):
+                Lz = lagrange_matrix(xi_c, -1 + (2.0 / r) * (sj + (xi_f + 1) / 2))
+                # coarse element (ix, iz) -> fine element (r ix + si, r iz + sj): u_f[b][a] = Lz u_c Lx^T
+                uc = np.einsum("qb,zxba,pa->zxqp", Lz, coarse, Lx)
+                uf = ref[sj::r, si::r]
+                err += np.sum(W2 * (uc - uf) ** 2)
+                norm += np.sum(W2 * uf ** 2)
+        return float(np.sqrt(err / norm))
+
+    t0 = time.perf_counter()
+    ref_h, st_ref = solve(128, 6)
+    h_rows = []
+    for n in (8, 16, 32, 64):
+        u, st = solve(n, 6)
+        h_rows.append({"elements_per_side": n, "h_km": 10.0 / n, "rel_l2": rel_err(u, n, 6, ref_h, 128, 6),
+                       "gmres_iterations": st.glob.iterations})
+    ref_p, _ = solve(16, 10)
+    p_rows = []
+    for p in (2, 4, 6, 8):
+        u, st = solve(16, p)
+        p_rows.append({"p": p, "rel_l2": rel_err(u, 16, p, ref_p, 16, 10)})
+    for rows, key in ((h_rows, "h_km"), ):
+        for a, b in zip(rows, rows[1:]):
+            b["observed_order"] = float(np.log(a["rel_l2"] / b["rel_l2"]) / np.log(a[key] / b[key]))
+    return {"field": "gaussian-cloud slab (10 km, g=0.85, albedo 0.99, beam 300 deg), N=16",
+            "h_refinement": {"p": 6, "reference": "128x128 elements, p=6", "levels": h_rows},
+            "p_refinement": {"elements_per_side": 16, "reference": "p=10", "levels": p_rows},
+            "local": "TF32-IR, 2 refinement sweeps; GMRES rtol 1e-10", "seconds": time.perf_counter() - t0}
+
+
 def run_ours(args, rank, world, local_rank):
     import numpy as np
     import torch
@@ -801,6 +953,10 @@ def run_ours(args, rank, world, local_rank):
         if not args.no_config5:
             out["config5"] = config5_section(args, E, W, net, out["holdout"]["calibrated_tol"])
         net.close()
+    if args.config3_fields > 0:
+        out["config3"] = config3_section(args, E, W)
+    if not args.no_refinement:
+        out["refinement"] = refinement_section(args, E, W)
     print(json.dumps(out), flush=True)
     ctx.close()
 

@@ -392,9 +392,9 @@ elrt_status elrt_set_tuning(elrt_ctx* ctx, int64_t local_chunk, int32_t lu_pairs
  *     x_0 -> x_i = f(A_i x_{i-1} + b_i), i = 1..n_hidden (width units, f = GELU or ELU),
  *     output = A_out x_{n_hidden} + b_out  (linear),
  * mapping an element's coefficients to its (in2out, in2sol) = (A_i2o, A_i2m).  Input x_0: the
- * standardised log kappa_hat at the (p+1)^2 nodes and the standardised albedo (Sec. 2.4.1 with
- * sigma_s = omega sigma_e: one coefficient field plus the albedo), zero-padded to a multiple of
- * 64.  Output: the 2(p+1)N x 2(p+1)N in2out entries then the (p+1)^2 x 2(p+1)N in2sol entries,
+ * standardised log kappa_hat (or kappa_hat, desc.features) at the (p+1)^2 nodes and the standardised
+ * albedo (Sec. 2.4.1 with sigma_s = omega sigma_e: one coefficient field plus the albedo),
+ * zero-padded to a multiple of 64.  Output: the 2(p+1)N x 2(p+1)N in2out entries then the (p+1)^2 x 2(p+1)N in2sol entries,
  * each standardised by its training-set mean and standard deviation.  Weights are FP32 masters
  * with BF16 copies; every GEMM runs on tcgen05 (BF16 in, FP32 accumulate); training minimises the
  * mean absolute error with Adam (Sec. 3.1).  All calls are asynchronous on the network's stream
@@ -406,6 +406,8 @@ typedef struct {
     int32_t width;        /* hidden width, a multiple of 64 */
     int32_t activation;   /* 0 GELU, 1 ELU */
     uint64_t seed;        /* initial weights: uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) from this seed */
+    int32_t features;     /* node inputs before standardisation: 0 log(kappa_hat + 1e-12) (suits lognormal
+                             coefficients), 1 kappa_hat itself (Sec. 2.4.1's nodal sigma) */
 } elrt_net_desc;
 
 typedef struct {
@@ -433,9 +435,9 @@ elrt_status elrt_net_params(elrt_net* net, int32_t layer, int32_t what, int32_t 
  * versioned little-endian binary file with everything training needs to resume bit-for-bit --
  * the description (p, N, n_hidden, width, activation, seed), the FP32 master weights and biases,
  * Adam's first and second moments, the Adam step counter and the input/output standardisation --
- * followed by a CRC-32 (IEEE 802.3) of all preceding bytes.  Layout: a 60-byte header (magic
- * "ELRTNET\0", u32 version 1, i32 p, n_angles, n_hidden, width, activation, u64 seed, i32
- * standardised, i64 Adam step, i64 count F of FP32 values), F FP32 values (per layer: W
+ * followed by a CRC-32 (IEEE 802.3) of all preceding bytes.  Layout: a 64-byte header (magic
+ * "ELRTNET\0", u32 version 2, i32 p, n_angles, n_hidden, width, activation, u64 seed, i32
+ * standardised, i64 Adam step, i64 count F of FP32 values, i32 features), F FP32 values (per layer: W
  * [out][in_pad], b, m(W), v(W), m(b), v(b); then input mean, input std [in_pad], output mean,
  * output std [n_out]), u32 CRC.  BF16 weight copies are rebuilt on load.
  * elrt_net_save synchronises the network's stream and writes `path` (through `path`.tmp and a

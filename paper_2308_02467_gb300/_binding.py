@@ -49,7 +49,7 @@ class SolveStats(C.Structure):
 
 class NetDesc(C.Structure):
     _fields_ = [("p", C.c_int32), ("n_angles", C.c_int32), ("n_hidden", C.c_int32), ("width", C.c_int32),
-                ("activation", C.c_int32), ("seed", C.c_uint64)]
+                ("activation", C.c_int32), ("seed", C.c_uint64), ("features", C.c_int32)]
 
 
 class TrainOpts(C.Structure):
@@ -455,10 +455,11 @@ def _net_check(status, h):
 class Net:
     """An elrt_net: the element network of Sec. 2.4.1 (calls run on the current torch stream)."""
 
-    def __init__(self, p, n_angles, n_hidden=4, width=1024, activation="gelu", seed=0, _handle=None):
+    def __init__(self, p, n_angles, n_hidden=4, width=1024, activation="gelu", seed=0, features="log", _handle=None):
         import torch
         if _handle is None:
-            d = NetDesc(p, n_angles, n_hidden, width, 0 if activation == "gelu" else 1, seed)
+            d = NetDesc(p, n_angles, n_hidden, width, 0 if activation == "gelu" else 1, seed,
+                        0 if features == "log" else 1)
             h = C.c_void_p()
             _check(_lib.elrt_net_create(C.byref(h), C.byref(d), C.c_void_p(torch.cuda.current_stream().cuda_stream)))
         else:
@@ -479,7 +480,8 @@ class Net:
         _check(_lib.elrt_net_load(C.byref(h), os.fsencode(path), C.c_void_p(torch.cuda.current_stream().cuda_stream)))
         info = elrt_net_file_info(path)
         return cls(info["p"], info["n_angles"], info["n_hidden"], info["width"],
-                   "gelu" if info["activation"] == 0 else "elu", info["seed"], _handle=h)
+                   "gelu" if info["activation"] == 0 else "elu", info["seed"],
+                   "log" if info["features"] == 0 else "linear", _handle=h)
 
     def elrt_net_save(self, path):
         self._s()
@@ -564,7 +566,8 @@ def elrt_net_file_info(path):
     d, st, step, nv = NetDesc(), C.c_int32(), C.c_int64(), C.c_int64()
     _check(_lib.elrt_net_file_info(os.fsencode(path), C.byref(d), C.byref(st), C.byref(step), C.byref(nv)))
     return {"p": d.p, "n_angles": d.n_angles, "n_hidden": d.n_hidden, "width": d.width, "activation": d.activation,
-            "seed": d.seed, "standardised": st.value, "adam_step": step.value, "n_values": nv.value}
+            "seed": d.seed, "features": d.features, "standardised": st.value, "adam_step": step.value,
+            "n_values": nv.value}
 
 
 def elrt_build_local_learned(ctx, net, kappa, omega, h, in2out, in2sol, tol=1e-3, h_elem=None, estimate=None):

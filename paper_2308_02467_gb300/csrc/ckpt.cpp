@@ -2,7 +2,7 @@
 //
 //   offset  size  field
 //   0       8     magic "ELRTNET\0"
-//   8       4     u32 version (1)
+//   8       4     u32 version (2)
 //   12      4     i32 p
 //   16      4     i32 n_angles
 //   20      4     i32 n_hidden
@@ -12,11 +12,12 @@
 //   40      4     i32 standardised (1 once elrt_net_fit has set the input/output standardisation)
 //   44      8     i64 Adam step counter
 //   52      8     i64 number F of FP32 values that follow
-//   60      4F    FP32 values (IEEE-754 bit patterns, little-endian), in this order:
+//   60      4     i32 input features (0 log kappa_hat, 1 kappa_hat)
+//   64      4F    FP32 values (IEEE-754 bit patterns, little-endian), in this order:
 //                 per layer l = 0 .. n_hidden: W [out][in_pad], b [out], Adam m and v of W, m and v of b;
 //                 then the input mean and standard deviation [in_pad], the output mean and standard
 //                 deviation [n_out]
-//   60+4F   4     u32 CRC-32 (IEEE 802.3, reflected polynomial 0xEDB88320, initial value and final
+//   64+4F   4     u32 CRC-32 (IEEE 802.3, reflected polynomial 0xEDB88320, initial value and final
 //                 XOR 0xFFFFFFFF) of every byte before it
 // The layout depends only on the description: in_pad = n_feat rounded up to 64 for layer 0 and
 // width otherwise; out = width for hidden layers and n_out for the output layer (sizes as in
@@ -33,8 +34,8 @@
 namespace {
 
 const unsigned char kMagic[8] = {'E', 'L', 'R', 'T', 'N', 'E', 'T', 0};
-constexpr uint32_t kVersion = 1;
-constexpr size_t kHeaderBytes = 60;
+constexpr uint32_t kVersion = 2;
+constexpr size_t kHeaderBytes = 64;
 
 uint32_t crc_table_entry(uint32_t c) {
     for (int k = 0; k < 8; ++k) c = (c & 1u) ? 0xEDB88320u ^ (c >> 1) : c >> 1;
@@ -130,7 +131,8 @@ std::vector<size_t> ckpt_layout(const elrt_net_desc& d) {
 
 static bool desc_ok(const elrt_net_desc& d) {
     return d.p >= 1 && d.p <= 10 && d.n_angles >= 4 && d.n_angles <= 32 && d.n_angles % 4 == 0 && d.n_hidden >= 0 &&
-           d.n_hidden <= 8 && d.width >= 64 && d.width % 64 == 0 && (d.activation == 0 || d.activation == 1);
+           d.n_hidden <= 8 && d.width >= 64 && d.width % 64 == 0 && (d.activation == 0 || d.activation == 1) &&
+           (d.features == 0 || d.features == 1);
 }
 
 bool ckpt_write(const char* path, const elrt_net_desc& d, int32_t standardised, int64_t step,
@@ -154,6 +156,7 @@ bool ckpt_write(const char* path, const elrt_net_desc& d, int32_t standardised, 
     put_u32(h + 40, (uint32_t)standardised);
     put_u64(h + 44, (uint64_t)step);
     put_u64(h + 52, (uint64_t)nf);
+    put_u32(h + 60, (uint32_t)d.features);
     const std::string tmp = std::string(path) + ".tmp";
     FILE* f = fopen(tmp.c_str(), "wb");
     if (!f) {
@@ -212,6 +215,7 @@ bool ckpt_read(const char* path, elrt_net_desc* d, int32_t* standardised, int64_
     const int32_t st = (int32_t)get_u32(h + 40);
     const int64_t sp = (int64_t)get_u64(h + 44);
     const uint64_t nf = get_u64(h + 52);
+    dd.features = (int32_t)get_u32(h + 60);
     if (!desc_ok(dd) || (st != 0 && st != 1) || sp < 0) {
         fclose(f);
         *err = "checkpoint: invalid header";

@@ -106,9 +106,11 @@ __global__ void k_bf16_copies(const float* __restrict__ W, int rows, int cols, b
     }
 }
 
-// raw features: log(kappa_hat + 1e-12) at the nodes, then omega; fp32 [n][fpad] (padding zero)
+// raw features: log(kappa_hat + 1e-12) (lin = 0) or kappa_hat itself (lin = 1) at the nodes, then
+// omega; fp32 [n][fpad] (padding zero)
 __global__ void k_features_raw(const double* __restrict__ kappa, const double* __restrict__ omega, double h,
-                               const double* __restrict__ h_elem, int64_t n, int nm, int fpad, float* __restrict__ F) {
+                               const double* __restrict__ h_elem, int64_t n, int nm, int fpad, int lin,
+                               float* __restrict__ F) {
     const int64_t total = n * fpad;
     for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
         const int64_t e = k / fpad;
@@ -116,7 +118,8 @@ __global__ void k_features_raw(const double* __restrict__ kappa, const double* _
         float v = 0.f;
         if (i < nm) {
             const double he = h_elem ? h_elem[e] : h;
-            v = (float)log(kappa[e * nm + i] * 0.5 * he + 1e-12);
+            const double kh = kappa[e * nm + i] * 0.5 * he;
+            v = (float)(lin ? kh : log(kh + 1e-12));
         } else if (i == nm) {
             v = (float)omega[e];
         }
@@ -599,7 +602,7 @@ elrt_status elrt_net_create(elrt_net** out, const elrt_net_desc* d, void* stream
     *out = nullptr;
     elrt_disc disc{d->p, d->n_angles, 0, 0.0};
     if (!elrt_disc_valid(&disc) || d->n_hidden < 0 || d->n_hidden > 8 || d->width < 64 || d->width % 64 ||
-        (d->activation != 0 && d->activation != 1))
+        (d->activation != 0 && d->activation != 1) || (d->features != 0 && d->features != 1))
         return ELRT_EINVAL;
     if (!load_encode()) return ELRT_ECUDA;
     elrt_net* net = new (std::nothrow) elrt_net();
@@ -855,7 +858,8 @@ elrt_status elrt_net_fit(elrt_net* net, int64_t n, const double* kappa, const do
     float* F = nullptr;
     cudaError_t e = cudaMallocAsync(&F, (size_t)n * net->fpad * 4, sm);
     if (e != cudaSuccess) return net_cuda(net, e, "feature buffer");
-    k_features_raw<<<grid_of(n * net->fpad), kT, 0, sm>>>(kappa, omega, 1.0, h_elem, n, net->nm, net->fpad, F);
+    k_features_raw<<<grid_of(n * net->fpad), kT, 0, sm>>>(kappa, omega, 1.0, h_elem, n, net->nm, net->fpad,
+                                                          net->desc.features, F);
     k_col_stats<<<(net->fpad + 127) / 128, 128, 0, sm>>>(F, net->fpad, nullptr, 0, n, net->feat_mean, net->feat_std,
                                                          1e-3f);
     const int64_t co = (int64_t)net->nin * net->nin, cm = (int64_t)net->nm * net->nin;
@@ -935,7 +939,8 @@ elrt_status elrt_net_infer(elrt_net* net, int64_t n, double h, const double* h_e
     for (int64_t e0 = 0; e0 < n; e0 += B) {
         const int m = (int)std::min<int64_t>(B, n - e0);
         k_features_raw<<<grid_of((int64_t)m * net->fpad), kT, 0, sm>>>(
-            kappa + e0 * net->nm, omega + e0, h, h_elem ? h_elem + e0 : nullptr, m, net->nm, net->fpad, F);
+            kappa + e0 * net->nm, omega + e0, h, h_elem ? h_elem + e0 : nullptr, m, net->nm, net->fpad,
+            net->desc.features, F);
         k_batch_features<<<grid_of((int64_t)m * net->fpad), kT, 0, sm>>>(F, net->fpad, net->nfeat, net->feat_mean,
                                                                          net->feat_std, m, 0, m, 1, 0, net->X0,
                                                                          nullptr);

@@ -23,10 +23,12 @@ def _layout(p, n_angles, n_hidden, width):
     return sizes + [fpad, fpad, nout, nout]
 
 
-def _write(path, p=2, n_angles=4, n_hidden=1, width=64, act=1, seed=99, standardised=1, step=17, count=None):
+def _write(path, p=2, n_angles=4, n_hidden=1, width=64, act=1, seed=99, standardised=1, step=17, count=None,
+           features=1):
     n = sum(_layout(p, n_angles, n_hidden, width)) if count is None else count
-    head = b"ELRTNET\0" + struct.pack("<IiiiiiQiqq", 1, p, n_angles, n_hidden, width, act, seed, standardised, step, n)
-    assert len(head) == 60
+    head = b"ELRTNET\0" + struct.pack("<IiiiiiQiqqi", 2, p, n_angles, n_hidden, width, act, seed, standardised, step, n,
+                                       features)
+    assert len(head) == 64
     vals = np.random.default_rng(0).normal(size=n).astype("<f4").tobytes()
     body = head + vals
     with open(path, "wb") as f:
@@ -44,17 +46,19 @@ def test_valid_file_is_read(E, tmp_path):
     path = str(tmp_path / "net.bin")
     n = _write(path)
     info = E.elrt_net_file_info(path)
-    assert info == {"p": 2, "n_angles": 4, "n_hidden": 1, "width": 64, "activation": 1, "seed": 99,
+    assert info == {"p": 2, "n_angles": 4, "n_hidden": 1, "width": 64, "activation": 1, "seed": 99, "features": 1,
                     "standardised": 1, "adam_step": 17, "n_values": n}
 
 
-@pytest.mark.parametrize("damage", ["flip", "truncate", "append", "count", "magic", "version", "desc"])
+@pytest.mark.parametrize("damage", ["flip", "truncate", "append", "count", "magic", "version", "desc", "features"])
 def test_damaged_file_is_rejected(E, tmp_path, damage):
     path = str(tmp_path / "net.bin")
     if damage == "count":
         _write(path, count=sum(_layout(2, 4, 1, 64)) - 1)
     elif damage == "desc":
         _write(path, n_angles=6)                       # N not a multiple of 4
+    elif damage == "features":
+        _write(path, features=2)
     else:
         _write(path)
         b = bytearray(open(path, "rb").read())
@@ -67,7 +71,7 @@ def test_damaged_file_is_rejected(E, tmp_path, damage):
         elif damage == "magic":
             b[0] = ord("X")
         elif damage == "version":
-            b[8] = 2
+            b[8] = 1
         open(path, "wb").write(bytes(b))
     with pytest.raises(E.ElrtError) as ei:
         E.elrt_net_file_info(path)
