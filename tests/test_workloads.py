@@ -86,3 +86,21 @@ def test_cloud_slab_torch_evaluation_matches_numpy():
     ref = prob.kappa(x, z)
     got = prob.kappa.evaluate_torch(torch.tensor(x), torch.tensor(z), chunk=128).numpy()
     np.testing.assert_allclose(got, ref, rtol=1e-12)
+
+
+def test_modal_samples_follow_algorithm_2():
+    """The paper's training distribution (Sec. 2.4.2): nodal values in [0, X_A] with the minimum 0 and
+    the maximum X_A exactly; X_A uniform on [0, A_sigma]; the low-frequency bias makes the highest
+    modes ~e^-4 of the lowest on average; reproducible; the held-out stream differs."""
+    from oracle import hdg
+    xi, _ = hdg.lgl(6)
+    b = W.modal_sample_batch(400)
+    s = b.sigma_at(xi)
+    assert s.shape == (400, 49)
+    np.testing.assert_allclose(s.min(axis=1), 0.0, atol=1e-15)
+    np.testing.assert_allclose(s.max(axis=1), b.amplitude, rtol=1e-14)
+    assert b.amplitude.min() >= 0 and b.amplitude.max() <= 10 and b.amplitude.mean() > 4
+    ratio = np.abs(b.modal[:, 6, 6]).mean() / np.abs(b.modal[:, 0, 0]).mean()
+    assert 0.5 * np.exp(-4) < ratio < 2 * np.exp(-4), ratio
+    np.testing.assert_array_equal(W.modal_sample_batch(400).modal, b.modal)
+    assert not np.allclose(W.modal_sample_batch(400, holdout=True).modal, b.modal)

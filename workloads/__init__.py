@@ -24,4 +24,6 @@ from .fields import (  # noqa: F401
     problem_batch_fields,
     problem_cloud_slab,
     element_batch,
+    ModalSampleBatch,
+    modal_sample_batch,
 )

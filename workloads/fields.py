@@ -312,6 +312,42 @@ class ElementBatch:
         return np.exp(self.mu[:, None] + self.sd[:, None] * f)
 
 
+@dataclasses.dataclass
+class ModalSampleBatch:
+    """Optical-coefficient samples on the reference element [-1, 1]^2 drawn by the paper's data
+    generation (Sec. 2.4.2, Algorithm 2): Legendre-modal coefficients with a low-frequency bias,
+    sigma~_mn = exp(-c_sm ((m/p)^2 + (n/p)^2)) (X_mn - 1/2) with X_mn ~ U[0, 1] (the '+' between the
+    two squares is the reading taken where the printed formula has '-', which would favour high
+    frequencies in y); their nodal values at the points a caller gives, shifted to a minimum of 0,
+    divided by their maximum and multiplied by X_A ~ U[0, A_sigma]."""
+    modal: np.ndarray       # [n, p+1 (m, along x), p+1 (n, along z)] biased modal coefficients
+    amplitude: np.ndarray   # [n] X_A
+
+    def __len__(self):
+        return len(self.amplitude)
+
+    def sigma_at(self, xi: np.ndarray) -> np.ndarray:
+        """Nodal sigma [n, (p+1)^2] at the tensor points (xi_a, xi_b), node a + (p+1) b."""
+        from numpy.polynomial import legendre
+        xi = np.asarray(xi, dtype=np.float64)
+        V = legendre.legvander(xi, self.modal.shape[1] - 1)              # V[a][m] = L_m(xi_a)
+        s = np.einsum("am,emn,bn->eba", V, self.modal, V)                 # [n][b][a]
+        s = s.reshape(len(self), -1)
+        s = s - s.min(axis=1, keepdims=True)
+        s = s / s.max(axis=1, keepdims=True)
+        return s * self.amplitude[:, None]
+
+
+def modal_sample_batch(n: int, p: int = 6, c_sm: float = 2.0, a_sigma: float = 10.0, holdout: bool = False):
+    """n samples of Algorithm 2 (the paper's training set: c_sm = 2, A_sigma = 10, Q_6); the held-out
+    set comes from an independent counter block."""
+    r = philox(6, stream=1 if holdout else 0)
+    m = np.arange(p + 1) / p
+    decay = np.exp(-c_sm * (m[:, None] ** 2 + m[None, :] ** 2))
+    X = r.uniform(0.0, 1.0, size=(n, p + 1, p + 1))
+    return ModalSampleBatch(decay[None] * (X - 0.5), r.uniform(0.0, a_sigma, n))
+
+
 def element_batch(n: int, holdout: bool = False, modes: int = 64, chunk: int = 4096) -> ElementBatch:
     """n training (or, with holdout=True, held-out) elements: h ~ U[0.05,1] km, ell = U[0.1,2] h,
     log-mean U[-2,3.5], log-sd U[0,1.5], albedo U[0.9,1]."""
