@@ -379,15 +379,15 @@ template <int NK>
 struct UpdCfg {
     static constexpr int KB = NK / 32;             // 32-wide K boxes of a U12^T tile
     static constexpr int U_BOX = UBN * 32 * 4;     // one box: 64 rows x 128 bytes
-    static constexpr int U_STAGE = 2 * KB * U_BOX; // FP32 tile + its low part
-    static constexpr int U_TX = KB * U_BOX;
+    static constexpr int U_STAGE = KB * U_BOX;     // the FP32 tile, later its low part in place
+    static constexpr int U_TX = U_STAGE;
     static constexpr int C_BOX = 128 * 32 * 4;     // one 32-column box of the C tile
     static constexpr int C_STAGE = UCB * C_BOX;
-    static constexpr int NU = NK == 64 ? 3 : 2;    // U stages
+    static constexpr int NU = NK == 64 ? 6 : 4;    // U stages
     static constexpr int NC = 3;                   // C stages
     static constexpr int NSB = NK == 64 ? 2 : 1;   // strip buffers in tensor memory
     static constexpr int BYTES = NU * U_STAGE + NC * C_STAGE;
-    static constexpr int TOTAL = BYTES + 1024 + 256;
+    static constexpr int TOTAL = BYTES + 1024 + 512;
     // tensor memory: accumulators at columns [0, 2 UBN); strip buffer b: high part at
     // 2 UBN + 2 NK b, low part NK columns further
     static constexpr uint32_t strip_col(int b, int lo) {
@@ -399,15 +399,15 @@ static_assert(UpdCfg<64>::strip_col(1, 1) + 64 <= 512 && UpdCfg<128>::strip_col(
 constexpr int kStripThreads = 480;
 constexpr uint32_t kTmemCols = 512;
 
-// Low parts of one 128-byte-swizzled box of `rows` rows x 32 FP32: lo = v - tf32(v) at the same
-// offset in `lo`.  The box itself stays FP32: kind::tf32 MMAs read the high 19 bits of each FP32
-// operand and ignore the rest (checked: FP32 and pre-truncated operands give bit-identical
-// factorisations), so it serves as the high part unchanged.  Threads tid .. of nthr, 16 bytes each.
-__device__ __forceinline__ void split_lo(const unsigned char* box, unsigned char* lo, int rows, int tid, int nthr) {
+// Low parts of one 128-byte-swizzled box of `rows` rows x 32 FP32, in place: v -> v - tf32(v).
+// Until then the box is FP32 and serves as the TF32 high part unchanged: kind::tf32 MMAs read the
+// high 19 bits of each FP32 operand and ignore the rest (checked: FP32 and pre-truncated operands
+// give bit-identical factorisations).  Threads tid .. of nthr, 16 bytes each.
+__device__ __forceinline__ void split_lo_inplace(unsigned char* box, int rows, int tid, int nthr) {
     for (int q = tid; q < rows * 8; q += nthr) {
-        const float4 v = *reinterpret_cast<const float4*>(box + q * 16);
-        *reinterpret_cast<float4*>(lo + q * 16) =
-            make_float4(v.x - tf32_hi(v.x), v.y - tf32_hi(v.y), v.z - tf32_hi(v.z), v.w - tf32_hi(v.w));
+        float4* p = reinterpret_cast<float4*>(box + q * 16);
+        const float4 v = *p;
+        *p = make_float4(v.x - tf32_hi(v.x), v.y - tf32_hi(v.y), v.z - tf32_hi(v.z), v.w - tf32_hi(v.w));
     }
 }
 
@@ -424,12 +424,13 @@ __global__ void __launch_bounds__(kStripThreads, 1)
     constexpr int NU = Cfg::NU, NC = Cfg::NC, NSB = Cfg::NSB, KB = Cfg::KB;
     extern __shared__ __align__(1024) unsigned char ssm_raw[];
     unsigned char* base = (unsigned char*)(((uintptr_t)ssm_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char* ustage0 = base;                                  // [NU]: FP32 tile (KB boxes), low part (KB boxes)
+    unsigned char* ustage0 = base;                                  // [NU]: FP32 tile (KB boxes), then its low part
     unsigned char* cstage0 = base + NU * Cfg::U_STAGE;              // [NC]: C tile (UCB boxes)
     uint64_t* a_ready = (uint64_t*)(base + Cfg::BYTES);            // [NSB]
     uint64_t* a_empty = a_ready + NSB;                              // [NSB]
     uint64_t* u_full = a_empty + NSB;                               // [NU]
-    uint64_t* u_ready = u_full + NU;                                // [NU]
+    uint64_t* u_hidone = u_full + NU;                               // [NU]
+    uint64_t* u_ready = u_hidone + NU;                              // [NU]
     uint64_t* u_empty = u_ready + NU;                               // [NU]
     uint64_t* c_full = u_empty + NU;                                // [NC]
     uint64_t* c_done = c_full + NC;                                 // [NC]
@@ -449,6 +450,7 @@ __global__ void __launch_bounds__(kStripThreads, 1)
         }
         for (int i = 0; i < NU; ++i) {
             tc::mbar_init(&u_full[i], 1);
+            tc::mbar_init(&u_hidone[i], 1);
             tc::mbar_init(&u_ready[i], 4);
             tc::mbar_init(&u_empty[i], 1);
         }
@@ -508,6 +510,25 @@ __global__ void __launch_bounds__(kStripThreads, 1)
         constexpr uint32_t idesc = idesc_tf32(128, UBN);
         bool ok = true;
         int g = 0, i = 0;
+        uint32_t a_hi = 0, a_lo = 0;
+        // hi*lo pass of tile p (its U12^T stage now holds the low part) and the commits that free the
+        // stage and hand the accumulator to the epilogue
+        auto finish = [&](int p) -> bool {
+            const int su = p % NU, a = p & 1;
+            if (!tc::mbar_wait(&u_ready[su], (p / NU) & 1, abort)) return false;
+            tc::tc_fence_after();
+            const uint32_t d = tmem + (uint32_t)(a * UBN);
+            unsigned char* us = ustage0 + su * Cfg::U_STAGE;
+            for (int kb = 0; kb < KB; ++kb) {
+                const uint64_t bl = tc::sw128_desc(tc::smem_u32(us + kb * Cfg::U_BOX));
+#pragma unroll
+                for (int k = 0; k < 4; ++k) mma_tf32_ta(d, a_hi + (uint32_t)(kb * 32 + k * 8), bl + 2 * k, idesc, 1);
+            }
+            tc::mma_commit(&u_empty[su]);
+            tc::mma_commit(&acc_full[a]);
+            ++committed;
+            return true;
+        };
         for (int64_t w = blockIdx.x; w < W && ok; w += gridDim.x, ++i) {
             const int ab = i % NSB;
             if (!tc::mbar_wait(&a_ready[ab], (i / NSB) & 1, abort)) {
@@ -515,7 +536,9 @@ __global__ void __launch_bounds__(kStripThreads, 1)
                 break;
             }
             tc::tc_fence_after();
-            const uint32_t a_hi = tmem + Cfg::strip_col(ab, 0), a_lo = tmem + Cfg::strip_col(ab, 1);
+            a_hi = tmem + Cfg::strip_col(ab, 0);
+            a_lo = tmem + Cfg::strip_col(ab, 1);
+            int pending = -1;
             for (int t = 0; t < ntile; ++t, ++g) {
                 const int su = g % NU, a = g & 1;
                 if (!tc::mbar_wait(&acc_empty[a], ((g >> 1) & 1) ^ 1, abort) ||
@@ -527,8 +550,9 @@ __global__ void __launch_bounds__(kStripThreads, 1)
                 unsigned char* us = ustage0 + su * Cfg::U_STAGE;
                 const uint32_t d = tmem + (uint32_t)(a * UBN);
                 uint32_t acc = 0;
-                // hi*hi and lo*hi as soon as the FP32 U12^T tile has landed (it is its own high
-                // part), then hi*lo once the splitters have written the low part
+                // hi*hi and lo*hi on the FP32 U12^T tile as it landed (its own high part); the
+                // splitters then overwrite it with its low part, and its hi*lo pass is issued after
+                // the next tile's first two passes
                 for (int kb = 0; kb < KB; ++kb) {
                     const uint64_t bh = tc::sw128_desc(tc::smem_u32(us + kb * Cfg::U_BOX));
 #pragma unroll
@@ -539,20 +563,14 @@ __global__ void __launch_bounds__(kStripThreads, 1)
                         mma_tf32_ta(d, a_lo + kc, bh + 2 * k, idesc, 1);
                     }
                 }
-                if (!tc::mbar_wait(&u_ready[su], (g / NU) & 1, abort)) {
+                tc::mma_commit(&u_hidone[su]);
+                if (pending >= 0 && !finish(pending)) {
                     ok = false;
                     break;
                 }
-                tc::tc_fence_after();
-                for (int kb = 0; kb < KB; ++kb) {
-                    const uint64_t bl = tc::sw128_desc(tc::smem_u32(us + (KB + kb) * Cfg::U_BOX));
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) mma_tf32_ta(d, a_hi + (uint32_t)(kb * 32 + k * 8), bl + 2 * k, idesc, 1);
-                }
-                tc::mma_commit(&u_empty[su]);
-                tc::mma_commit(&acc_full[a]);
-                ++committed;
+                pending = g;
             }
+            if (ok && pending >= 0) ok = finish(pending);  // the item's last tile: its strip is released next
             if (ok) tc::mma_commit(&a_empty[ab]);
         }
         if (!ok) {
@@ -641,13 +659,13 @@ __global__ void __launch_bounds__(kStripThreads, 1)
         for (int64_t w = blockIdx.x; w < W && ok; w += gridDim.x) {
             for (int t = 0; t < ntile; ++t, ++g) {
                 const int su = g % NU;
-                if (!__all_sync(0xffffffffu, tc::mbar_wait(&u_full[su], (g / NU) & 1, abort) && !*abort)) {
+                // the stage's hi*hi and lo*hi MMAs have completed: its FP32 tile may be overwritten
+                if (!__all_sync(0xffffffffu, tc::mbar_wait(&u_hidone[su], (g / NU) & 1, abort) && !*abort)) {
                     ok = false;
                     break;
                 }
                 unsigned char* us = ustage0 + su * Cfg::U_STAGE;
-                for (int kb = 0; kb < KB; ++kb)
-                    split_lo(us + kb * Cfg::U_BOX, us + (KB + kb) * Cfg::U_BOX, UBN, tid, 128);
+                for (int kb = 0; kb < KB; ++kb) split_lo_inplace(us + kb * Cfg::U_BOX, UBN, tid, 128);
                 // generic-proxy writes, read next by the tensor cores (async proxy)
                 tc::fence_proxy_async();
                 __syncwarp();
