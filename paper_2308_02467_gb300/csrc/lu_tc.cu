@@ -874,15 +874,27 @@ elrt_status rowcol(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, int64_t
 }
 
 // backward substitution on the right-hand-side columns: X_J = U11^{-1} X_J, then the rows above
-// lose U[0..J, J..J+jb) X_J
+// lose U[0..J, J..J+jb) X_J.  With the pair schedule, the panels beyond the last pair go first, one
+// at a time; then per pair (a, b), last pair first: X_b, the rank-64 update of panel a's rows,
+// X_a, and one rank-128 update of the rows above the pair (both panels' solutions, side buffer K
+// offsets 0 and 64).
 elrt_status backward_sweep_tc(elrt_ctx* ctx, const TcMaps& mp, float* M, int64_t ld, int64_t estride, int64_t E,
                               const float* Tinv, float* Ut, int* err, int nin) {
     const int nu = ctx->tab.nu;
+    const int npair = ctx->tune.lu_pairs ? nu / (2 * NBP) : 0;
     const int last = ((nu - 1) / NBP) * NBP;
-    for (int J = last; J >= 0; J -= NBP) {
+    for (int J = last; J >= 2 * NBP * npair; J -= NBP) {
         const int jb = std::min(NBP, nu - J);
-        elrt_status s = rowcol(ctx, M, ld, estride, E, J, jb, Tinv, 0, 0, nu, nu + nin, 1, Ut);
+        elrt_status s = rowcol(ctx, M, ld, estride, E, J, jb, Tinv, 0, 0, nu, nu + nin, 1, Ut, 0);
         if (!s) s = update<64>(ctx, mp, M, ld, estride, E, J, jb, 0, 0, J, nu, nu + nin, err);
+        if (s) return s;
+    }
+    for (int q = npair - 1; q >= 0; --q) {
+        const int J = 2 * NBP * q, Jb = J + NBP;
+        elrt_status s = rowcol(ctx, M, ld, estride, E, Jb, NBP, Tinv, 0, 0, nu, nu + nin, 1, Ut, NBP);
+        if (!s) s = update<64>(ctx, mp, M, ld, estride, E, Jb, NBP, NBP, J, Jb, nu, nu + nin, err);
+        if (!s) s = rowcol(ctx, M, ld, estride, E, J, NBP, Tinv, 0, 0, nu, nu + nin, 1, Ut, 0);
+        if (!s) s = update<128>(ctx, mp, M, ld, estride, E, J, 2 * NBP, 0, 0, J, nu, nu + nin, err);
         if (s) return s;
     }
     return ELRT_OK;
@@ -953,7 +965,18 @@ elrt_status tc_lu_resolve(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, 
     TcMaps mp;
     elrt_status s = prepare(ctx, M, ld, estride, sd.Ut, E, &mp);
     if (s) return s;
-    for (int J = 0; J < nu; J += NBP) {
+    int J = 0;
+    // forward substitution with the unit lower factor, in the factorisation's panel pairs: X_a, the
+    // rank-64 update of panel b's rows, X_b, one rank-128 update of the rows below the pair
+    for (; ctx->tune.lu_pairs && J + 2 * NBP <= nu; J += 2 * NBP) {
+        const int Jb = J + NBP, Jn = J + 2 * NBP;
+        s = rowcol(ctx, M, ld, estride, E, J, NBP, sd.Tinv, 0, 0, nu, nu + nin, 0, sd.Ut, 0);
+        if (!s) s = update<64>(ctx, mp, M, ld, estride, E, J, NBP, 0, Jb, Jn, nu, nu + nin, err);
+        if (!s) s = rowcol(ctx, M, ld, estride, E, Jb, NBP, sd.Tinv, 0, 0, nu, nu + nin, 0, sd.Ut, NBP);
+        if (!s) s = update<128>(ctx, mp, M, ld, estride, E, J, 2 * NBP, 0, Jn, nu, nu, nu + nin, err);
+        if (s) return s;
+    }
+    for (; J < nu; J += NBP) {
         const int jb = std::min(NBP, nu - J);
         s = rowcol(ctx, M, ld, estride, E, J, jb, sd.Tinv, 0, 0, nu, nu + nin, 0, sd.Ut, 0);
         if (!s) s = update<64>(ctx, mp, M, ld, estride, E, J, jb, 0, J + jb, nu, nu, nu + nin, err);
