@@ -352,11 +352,12 @@ __device__ __forceinline__ void mma_tf32_ta(uint32_t d_tmem, uint32_t a_tmem, ui
 // shared through L2).  The L21 strip of an item (columns J .. J+NK-1 of its 128 rows, FP32,
 // straight from the matrix) lives in tensor memory as TF32 high and low parts (double-buffered at
 // NK = 64, so the next item's strip is prepared while the current item's tiles run; single at
-// NK = 128, where the two parts fill 256 of the 512 columns).  Shared memory holds two rings that
-// never drain between items: the U12^T tiles (64 columns x NK, FP32 as its own high part plus the
-// low part; 3 stages at NK = 64, 2 at NK = 128) and the C tiles (128 rows x 64 columns as two
-// 128-byte-wide boxes, 3 stages).  A U stage is released by the MMA commit, a C stage by the store
-// warp, so neither ring waits for the other.  Doubling K halves the C bytes per flop: at NK = 64
+// NK = 128, where the two parts fill 256 of the 512 columns).  Shared memory holds rings that
+// never drain between items: the FP32 U12^T tiles (64 columns x NK, their own high part; 4 stages
+// at NK = 64, 3 at NK = 128), their low parts (2 and 1) and the C tiles (128 rows x 64 columns as
+// two 128-byte-wide boxes, 3 stages).  A U stage is released by the MMA commit of its first two
+// passes together with the splitters, a low part by the commit of the third pass, a C stage by the
+// store warp, so no ring waits for another.  Doubling K halves the C bytes per flop: at NK = 64
 // the update is bound by the C traffic (48 TF32 flops per byte issued), at NK = 128 the tensor
 // pipe and HBM are about balanced.
 //   warp 0       TMA producer of both rings;
@@ -369,8 +370,9 @@ __device__ __forceinline__ void mma_tf32_ta(uint32_t d_tmem, uint32_t a_tmem, ui
 //                clipped) and releases the C stage once the store has read it;
 //   warps 6-9    strip preparation: each thread loads one row of the strip (columns at or beyond
 //                jb are 0), splits it and writes it to its TMEM lane (tcgen05.st);
-//   warps 10-13  write the low TF32 part of each staged FP32 U12^T tile (the tile itself serves as
-//                the high part: the MMA thread issues hi*hi and lo*hi on it at once, hi*lo after).
+//   warps 10-13  write the low TF32 part of each staged FP32 U12^T tile into a separate buffer
+//                (the tile itself serves as the high part: the MMA thread issues hi*hi and lo*hi
+//                on it as soon as it lands, hi*lo once the low part is ready).
 // U12^T comes from the side buffer [E][ld][128] (column-major U12 of the panel pair: K offset 0
 // for the first panel, 64 for the second); an NK = 64 update reads the half at K offset koff.
 // Every wait is bounded; on a timeout the CTA records a code in *err, stops issuing work, lets its
@@ -379,14 +381,15 @@ template <int NK>
 struct UpdCfg {
     static constexpr int KB = NK / 32;             // 32-wide K boxes of a U12^T tile
     static constexpr int U_BOX = UBN * 32 * 4;     // one box: 64 rows x 128 bytes
-    static constexpr int U_STAGE = KB * U_BOX;     // the FP32 tile, later its low part in place
+    static constexpr int U_STAGE = KB * U_BOX;     // one FP32 U12^T tile, or its low part
     static constexpr int U_TX = U_STAGE;
     static constexpr int C_BOX = 128 * 32 * 4;     // one 32-column box of the C tile
     static constexpr int C_STAGE = UCB * C_BOX;
-    static constexpr int NU = NK == 64 ? 6 : 4;    // U stages
+    static constexpr int NU = NK == 64 ? 4 : 3;    // FP32 U12^T tiles (TMA targets)
+    static constexpr int NL = NK == 64 ? 2 : 1;    // low parts
     static constexpr int NC = 3;                   // C stages
     static constexpr int NSB = NK == 64 ? 2 : 1;   // strip buffers in tensor memory
-    static constexpr int BYTES = NU * U_STAGE + NC * C_STAGE;
+    static constexpr int BYTES = (NU + NL) * U_STAGE + NC * C_STAGE;
     static constexpr int TOTAL = BYTES + 1024 + 512;
     // tensor memory: accumulators at columns [0, 2 UBN); strip buffer b: high part at
     // 2 UBN + 2 NK b, low part NK columns further
@@ -399,15 +402,15 @@ static_assert(UpdCfg<64>::strip_col(1, 1) + 64 <= 512 && UpdCfg<128>::strip_col(
 constexpr int kStripThreads = 480;
 constexpr uint32_t kTmemCols = 512;
 
-// Low parts of one 128-byte-swizzled box of `rows` rows x 32 FP32, in place: v -> v - tf32(v).
-// Until then the box is FP32 and serves as the TF32 high part unchanged: kind::tf32 MMAs read the
-// high 19 bits of each FP32 operand and ignore the rest (checked: FP32 and pre-truncated operands
-// give bit-identical factorisations).  Threads tid .. of nthr, 16 bytes each.
-__device__ __forceinline__ void split_lo_inplace(unsigned char* box, int rows, int tid, int nthr) {
+// Low parts of one 128-byte-swizzled box of `rows` rows x 32 FP32: lo = v - tf32(v) at the same
+// offset in `lo`.  The box itself stays FP32: kind::tf32 MMAs read the high 19 bits of each FP32
+// operand and ignore the rest (checked: FP32 and pre-truncated operands give bit-identical
+// factorisations), so it serves as the high part unchanged.  Threads tid .. of nthr, 16 bytes each.
+__device__ __forceinline__ void split_lo(const unsigned char* box, unsigned char* lo, int rows, int tid, int nthr) {
     for (int q = tid; q < rows * 8; q += nthr) {
-        float4* p = reinterpret_cast<float4*>(box + q * 16);
-        const float4 v = *p;
-        *p = make_float4(v.x - tf32_hi(v.x), v.y - tf32_hi(v.y), v.z - tf32_hi(v.z), v.w - tf32_hi(v.w));
+        const float4 v = *reinterpret_cast<const float4*>(box + q * 16);
+        *reinterpret_cast<float4*>(lo + q * 16) =
+            make_float4(v.x - tf32_hi(v.x), v.y - tf32_hi(v.y), v.z - tf32_hi(v.z), v.w - tf32_hi(v.w));
     }
 }
 
@@ -421,18 +424,19 @@ __global__ void __launch_bounds__(kStripThreads, 1)
                 const __grid_constant__ CUtensorMap tS, float* __restrict__ Mall, int nu, int64_t ld, int64_t estride,
                 int64_t E, int J, int jb, int koff, int r0, int r_end, int c0, int c_end, int* __restrict__ err) {
     using Cfg = UpdCfg<NK>;
-    constexpr int NU = Cfg::NU, NC = Cfg::NC, NSB = Cfg::NSB, KB = Cfg::KB;
+    constexpr int NU = Cfg::NU, NL = Cfg::NL, NC = Cfg::NC, NSB = Cfg::NSB, KB = Cfg::KB;
     extern __shared__ __align__(1024) unsigned char ssm_raw[];
     unsigned char* base = (unsigned char*)(((uintptr_t)ssm_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char* ustage0 = base;                                  // [NU]: FP32 tile (KB boxes), then its low part
-    unsigned char* cstage0 = base + NU * Cfg::U_STAGE;              // [NC]: C tile (UCB boxes)
+    unsigned char* ustage0 = base;                                  // [NU]: FP32 U12^T tile (KB boxes)
+    unsigned char* lstage0 = base + NU * Cfg::U_STAGE;              // [NL]: its low part (KB boxes)
+    unsigned char* cstage0 = lstage0 + NL * Cfg::U_STAGE;           // [NC]: C tile (UCB boxes)
     uint64_t* a_ready = (uint64_t*)(base + Cfg::BYTES);            // [NSB]
     uint64_t* a_empty = a_ready + NSB;                              // [NSB]
     uint64_t* u_full = a_empty + NSB;                               // [NU]
-    uint64_t* u_hidone = u_full + NU;                               // [NU]
-    uint64_t* u_ready = u_hidone + NU;                              // [NU]
-    uint64_t* u_empty = u_ready + NU;                               // [NU]
-    uint64_t* c_full = u_empty + NU;                                // [NC]
+    uint64_t* u_empty = u_full + NU;                                // [NU]: MMA commit + the four splitter warps
+    uint64_t* l_ready = u_empty + NU;                               // [NL]
+    uint64_t* l_empty = l_ready + NL;                               // [NL]
+    uint64_t* c_full = l_empty + NL;                                // [NC]
     uint64_t* c_done = c_full + NC;                                 // [NC]
     uint64_t* c_empty = c_done + NC;                                // [NC]
     uint64_t* acc_full = c_empty + NC;                              // [2]
@@ -450,9 +454,11 @@ __global__ void __launch_bounds__(kStripThreads, 1)
         }
         for (int i = 0; i < NU; ++i) {
             tc::mbar_init(&u_full[i], 1);
-            tc::mbar_init(&u_hidone[i], 1);
-            tc::mbar_init(&u_ready[i], 4);
-            tc::mbar_init(&u_empty[i], 1);
+            tc::mbar_init(&u_empty[i], 5);
+        }
+        for (int i = 0; i < NL; ++i) {
+            tc::mbar_init(&l_ready[i], 4);
+            tc::mbar_init(&l_empty[i], 1);
         }
         for (int i = 0; i < NC; ++i) {
             tc::mbar_init(&c_full[i], 1);
@@ -510,25 +516,6 @@ __global__ void __launch_bounds__(kStripThreads, 1)
         constexpr uint32_t idesc = idesc_tf32(128, UBN);
         bool ok = true;
         int g = 0, i = 0;
-        uint32_t a_hi = 0, a_lo = 0;
-        // hi*lo pass of tile p (its U12^T stage now holds the low part) and the commits that free the
-        // stage and hand the accumulator to the epilogue
-        auto finish = [&](int p) -> bool {
-            const int su = p % NU, a = p & 1;
-            if (!tc::mbar_wait(&u_ready[su], (p / NU) & 1, abort)) return false;
-            tc::tc_fence_after();
-            const uint32_t d = tmem + (uint32_t)(a * UBN);
-            unsigned char* us = ustage0 + su * Cfg::U_STAGE;
-            for (int kb = 0; kb < KB; ++kb) {
-                const uint64_t bl = tc::sw128_desc(tc::smem_u32(us + kb * Cfg::U_BOX));
-#pragma unroll
-                for (int k = 0; k < 4; ++k) mma_tf32_ta(d, a_hi + (uint32_t)(kb * 32 + k * 8), bl + 2 * k, idesc, 1);
-            }
-            tc::mma_commit(&u_empty[su]);
-            tc::mma_commit(&acc_full[a]);
-            ++committed;
-            return true;
-        };
         for (int64_t w = blockIdx.x; w < W && ok; w += gridDim.x, ++i) {
             const int ab = i % NSB;
             if (!tc::mbar_wait(&a_ready[ab], (i / NSB) & 1, abort)) {
@@ -536,11 +523,9 @@ __global__ void __launch_bounds__(kStripThreads, 1)
                 break;
             }
             tc::tc_fence_after();
-            a_hi = tmem + Cfg::strip_col(ab, 0);
-            a_lo = tmem + Cfg::strip_col(ab, 1);
-            int pending = -1;
+            const uint32_t a_hi = tmem + Cfg::strip_col(ab, 0), a_lo = tmem + Cfg::strip_col(ab, 1);
             for (int t = 0; t < ntile; ++t, ++g) {
-                const int su = g % NU, a = g & 1;
+                const int su = g % NU, sl = g % NL, a = g & 1;
                 if (!tc::mbar_wait(&acc_empty[a], ((g >> 1) & 1) ^ 1, abort) ||
                     !tc::mbar_wait(&u_full[su], (g / NU) & 1, abort)) {
                     ok = false;
@@ -550,9 +535,8 @@ __global__ void __launch_bounds__(kStripThreads, 1)
                 unsigned char* us = ustage0 + su * Cfg::U_STAGE;
                 const uint32_t d = tmem + (uint32_t)(a * UBN);
                 uint32_t acc = 0;
-                // hi*hi and lo*hi on the FP32 U12^T tile as it landed (its own high part); the
-                // splitters then overwrite it with its low part, and its hi*lo pass is issued after
-                // the next tile's first two passes
+                // hi*hi and lo*hi as soon as the FP32 U12^T tile has landed (it is its own high
+                // part), then hi*lo once the splitters have written the low part
                 for (int kb = 0; kb < KB; ++kb) {
                     const uint64_t bh = tc::sw128_desc(tc::smem_u32(us + kb * Cfg::U_BOX));
 #pragma unroll
@@ -563,14 +547,22 @@ __global__ void __launch_bounds__(kStripThreads, 1)
                         mma_tf32_ta(d, a_lo + kc, bh + 2 * k, idesc, 1);
                     }
                 }
-                tc::mma_commit(&u_hidone[su]);
-                if (pending >= 0 && !finish(pending)) {
+                tc::mma_commit(&u_empty[su]);  // with the splitters' arrivals: the FP32 tile is free
+                if (!tc::mbar_wait(&l_ready[sl], (g / NL) & 1, abort)) {
                     ok = false;
                     break;
                 }
-                pending = g;
+                tc::tc_fence_after();
+                unsigned char* ls = lstage0 + sl * Cfg::U_STAGE;
+                for (int kb = 0; kb < KB; ++kb) {
+                    const uint64_t bl = tc::sw128_desc(tc::smem_u32(ls + kb * Cfg::U_BOX));
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) mma_tf32_ta(d, a_hi + (uint32_t)(kb * 32 + k * 8), bl + 2 * k, idesc, 1);
+                }
+                tc::mma_commit(&l_empty[sl]);
+                tc::mma_commit(&acc_full[a]);
+                ++committed;
             }
-            if (ok && pending >= 0) ok = finish(pending);  // the item's last tile: its strip is released next
             if (ok) tc::mma_commit(&a_empty[ab]);
         }
         if (!ok) {
@@ -658,18 +650,23 @@ __global__ void __launch_bounds__(kStripThreads, 1)
         int g = 0;
         for (int64_t w = blockIdx.x; w < W && ok; w += gridDim.x) {
             for (int t = 0; t < ntile; ++t, ++g) {
-                const int su = g % NU;
-                // the stage's hi*hi and lo*hi MMAs have completed: its FP32 tile may be overwritten
-                if (!__all_sync(0xffffffffu, tc::mbar_wait(&u_hidone[su], (g / NU) & 1, abort) && !*abort)) {
+                const int su = g % NU, sl = g % NL;
+                // the FP32 tile has landed and the low-part buffer's previous hi*lo pass is done
+                if (!__all_sync(0xffffffffu, tc::mbar_wait(&u_full[su], (g / NU) & 1, abort) &&
+                                                 tc::mbar_wait(&l_empty[sl], ((g / NL) & 1) ^ 1, abort) && !*abort)) {
                     ok = false;
                     break;
                 }
-                unsigned char* us = ustage0 + su * Cfg::U_STAGE;
-                for (int kb = 0; kb < KB; ++kb) split_lo_inplace(us + kb * Cfg::U_BOX, UBN, tid, 128);
+                const unsigned char* us = ustage0 + su * Cfg::U_STAGE;
+                unsigned char* ls = lstage0 + sl * Cfg::U_STAGE;
+                for (int kb = 0; kb < KB; ++kb) split_lo(us + kb * Cfg::U_BOX, ls + kb * Cfg::U_BOX, UBN, tid, 128);
                 // generic-proxy writes, read next by the tensor cores (async proxy)
                 tc::fence_proxy_async();
                 __syncwarp();
-                if (lane == 0) mbar_arrive(&u_ready[su]);
+                if (lane == 0) {
+                    mbar_arrive(&l_ready[sl]);
+                    mbar_arrive(&u_empty[su]);  // done reading the FP32 tile
+                }
             }
         }
         if (!ok && lane == 0) {
