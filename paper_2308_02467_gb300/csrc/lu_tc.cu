@@ -38,7 +38,9 @@
 namespace {
 
 constexpr int NBP = 64;     // panel width
-constexpr int UTK = 128;    // K extent of a row of the U12^T side buffer: two consecutive panels
+constexpr int UTK = 256;    // row of the U12^T side buffer: two consecutive panels (K 0 .. 127), then
+                            // the low TF32 parts of the same values (K 128 .. 255)
+constexpr int UTL = 128;    // K offset of the low parts
 constexpr int UBN = 64;     // trailing-update tile width (N of the MMAs)
 constexpr int UCB = UBN / 32;  // 32-column (128-byte) boxes of a C tile
 
@@ -181,7 +183,8 @@ __device__ __forceinline__ void tri_solve(float (&a)[NBP], const float* __restri
 // written back to the matrix; the remaining nct tiles are column tiles over columns [c_begin,
 // c_end): y = L11^{-1} a (col_mode 0: factorisation and forward sweep) or y = U11^{-1} a
 // (col_mode 1: backward sweep), written back to the matrix (rows < jb) and, transposed, to the side
-// buffer Ut[e][column][koff .. koff + 63] (zero beyond jb).  Persistent, two blocks per SM (one staging buffer
+// buffer Ut[e][column][koff .. koff + 63] (zero beyond jb), with its low TF32 parts at K offset
+// UTL + koff.  Persistent, two blocks per SM (one staging buffer
 // each, 128 registers per thread): each block walks its items, copying an item's 64-wide block and
 // the factor of the diagonal block with 16-byte cp.async copies, solving and storing it; the two
 // blocks of an SM overlap one another's copies and stores.  (One block per SM with two staging
@@ -295,7 +298,11 @@ __global__ void __launch_bounds__(256, 2) k_rowcol(int nu, int64_t ld, int64_t e
             __syncthreads();
             float* ut = Ut + e * ld * UTK + koff;
             for (int cc = warp; cc < nc; cc += 8)
-                for (int i = lane; i < NBP; i += 32) ut[(int64_t)(c0 + cc) * UTK + i] = S[cc * RS + i];
+                for (int i = lane; i < NBP; i += 32) {
+                    const float v = S[cc * RS + i];
+                    ut[(int64_t)(c0 + cc) * UTK + i] = v;
+                    ut[(int64_t)(c0 + cc) * UTK + UTL + i] = v - tf32_hi(v);  // the low TF32 part, split once
+                }
         }
         __syncthreads();  // the buffer is refilled by the next item's copies
     }
@@ -350,69 +357,59 @@ __device__ __forceinline__ void mma_tf32_ta(uint32_t d_tmem, uint32_t a_tmem, ui
 // the second already factored against the first): one CTA per SM walks the work items (element,
 // 128-row strip) of the launch, the strips of one element consecutively (their U12^T tiles are
 // shared through L2).  The L21 strip of an item (columns J .. J+NK-1 of its 128 rows, FP32,
-// straight from the matrix) lives in tensor memory as TF32 high and low parts (double-buffered at
-// NK = 64, so the next item's strip is prepared while the current item's tiles run; single at
-// NK = 128, where the two parts fill 256 of the 512 columns).  Shared memory holds rings that
-// never drain between items: the FP32 U12^T tiles (64 columns x NK, their own high part; 4 stages
-// at NK = 64, 3 at NK = 128), their low parts (2 and 1) and the C tiles (128 rows x 64 columns as
-// two 128-byte-wide boxes, 3 stages).  A U stage is released by the MMA commit of its first two
-// passes together with the splitters, a low part by the commit of the third pass, a C stage by the
-// store warp, so no ring waits for another.  Doubling K halves the C bytes per flop: at NK = 64
-// the update is bound by the C traffic (48 TF32 flops per byte issued), at NK = 128 the tensor
-// pipe and HBM are about balanced.
+// straight from the matrix) lives in tensor memory as TF32 high and low parts, in 64-column halves
+// that rotate through three slots of 128 columns (64 high + 64 low) beside the two accumulators:
+// while an item's tiles run, the next item's first half (at NK = 64 the next two strips) is
+// already in place and its second half is loaded into registers, ready for the slot the current
+// item frees; the first tile of an item issues the passes of its first half before it waits for
+// the second.  Shared memory holds two rings that never drain between items: the U12^T tiles
+// (64 columns x NK, the FP32 values, which serve as their own TF32 high part, and their low parts,
+// both split once by the panel solve; 4 stages at NK = 64, 2 at NK = 128) and the C tiles (128
+// rows x 64 columns as two 128-byte-wide boxes, 3 stages).  A U stage is released by the MMA
+// commit, a C stage by the store warp, so neither ring waits for the other.  Doubling K halves the
+// C bytes per flop: at NK = 64 the update is bound by the C traffic (48 TF32 flops per byte
+// issued), at NK = 128 the tensor pipe and HBM are about balanced.
 //   warp 0       TMA producer of both rings;
-//   warp 1       TMEM allocation; one thread issues the 3xTF32 MMAs (hi*hi + hi*lo + lo*hi,
+//   warp 1       TMEM allocation; one thread issues the 3xTF32 MMAs (hi*hi + lo*hi + hi*lo,
 //                M = 128, N = 64, K = 8, A from tensor memory) into one of two TMEM accumulators;
-//   warps 2-5    epilogue: accumulator (tcgen05.ld) and staged C tile -> C - L U, written back
-//                into the staged tile;
+//   warps 2-5,   epilogue: accumulator (tcgen05.ld) and staged C tile -> C - L U, written back
+//   10-13        into the staged tile (warps 2-5 the first 32-column box, 10-13 the second);
 //   warp 14      stores each finished tile with TMA tensor stores (the store map's extents are
 //                r_end rows and c_end columns, so rows and columns outside the update are
 //                clipped) and releases the C stage once the store has read it;
-//   warps 6-9    strip preparation: each thread loads one row of the strip (columns at or beyond
-//                jb are 0), splits it and writes it to its TMEM lane (tcgen05.st);
-//   warps 10-13  write the low TF32 part of each staged FP32 U12^T tile into a separate buffer
-//                (the tile itself serves as the high part: the MMA thread issues hi*hi and lo*hi
-//                on it as soon as it lands, hi*lo once the low part is ready).
-// U12^T comes from the side buffer [E][ld][128] (column-major U12 of the panel pair: K offset 0
-// for the first panel, 64 for the second); an NK = 64 update reads the half at K offset koff.
-// Every wait is bounded; on a timeout the CTA records a code in *err, stops issuing work, lets its
-// copies land and frees its TMEM.
+//   warps 6-9    strip preparation: each thread loads one row of a strip half (columns at or
+//                beyond jb are 0) into registers, waits for a free slot, splits the row and
+//                writes it to its TMEM lane (tcgen05.st).
+// U12^T comes from the side buffer [E][ld][UTK] (column-major U12 of the panel pair: K offset 0
+// for the first panel, 64 for the second, their low parts UTL further); an NK = 64 update reads
+// the half at K offset koff.  Every wait is bounded; on a timeout the CTA records a code in *err,
+// stops issuing work, lets its copies land and frees its TMEM.
 template <int NK>
 struct UpdCfg {
     static constexpr int KB = NK / 32;             // 32-wide K boxes of a U12^T tile
     static constexpr int U_BOX = UBN * 32 * 4;     // one box: 64 rows x 128 bytes
-    static constexpr int U_STAGE = KB * U_BOX;     // one FP32 U12^T tile, or its low part
+    static constexpr int U_STAGE = 2 * KB * U_BOX; // FP32 U12^T tile (KB boxes), then its low part
     static constexpr int U_TX = U_STAGE;
     static constexpr int C_BOX = 128 * 32 * 4;     // one 32-column box of the C tile
     static constexpr int C_STAGE = UCB * C_BOX;
-    static constexpr int NU = NK == 64 ? 4 : 3;    // FP32 U12^T tiles (TMA targets)
-    static constexpr int NL = NK == 64 ? 2 : 1;    // low parts
+    static constexpr int NU = NK == 64 ? 4 : 2;    // U stages
     static constexpr int NC = 3;                   // C stages
-    static constexpr int NSB = NK == 64 ? 2 : 1;   // strip buffers in tensor memory
-    static constexpr int BYTES = (NU + NL) * U_STAGE + NC * C_STAGE;
+    static constexpr int NH = NK / 64;             // 64-column strip halves per item
+    static constexpr int BYTES = NU * U_STAGE + NC * C_STAGE;
     static constexpr int TOTAL = BYTES + 1024 + 512;
-    // tensor memory: accumulators at columns [0, 2 UBN); strip buffer b: high part at
-    // 2 UBN + 2 NK b, low part NK columns further
-    static constexpr uint32_t strip_col(int b, int lo) {
-        return (uint32_t)(2 * UBN) + (uint32_t)(2 * NK) * (uint32_t)b + (uint32_t)NK * (uint32_t)lo;
-    }
 };
 static_assert(UpdCfg<64>::TOTAL <= 227 * 1024 && UpdCfg<128>::TOTAL <= 227 * 1024, "trailing-update shared memory");
-static_assert(UpdCfg<64>::strip_col(1, 1) + 64 <= 512 && UpdCfg<128>::strip_col(0, 1) + 128 <= 512, "tensor memory");
-constexpr int kStripThreads = 480;
-constexpr uint32_t kTmemCols = 512;
-
-// Low parts of one 128-byte-swizzled box of `rows` rows x 32 FP32: lo = v - tf32(v) at the same
-// offset in `lo`.  The box itself stays FP32: kind::tf32 MMAs read the high 19 bits of each FP32
-// operand and ignore the rest (checked: FP32 and pre-truncated operands give bit-identical
-// factorisations), so it serves as the high part unchanged.  Threads tid .. of nthr, 16 bytes each.
-__device__ __forceinline__ void split_lo(const unsigned char* box, unsigned char* lo, int rows, int tid, int nthr) {
-    for (int q = tid; q < rows * 8; q += nthr) {
-        const float4 v = *reinterpret_cast<const float4*>(box + q * 16);
-        *reinterpret_cast<float4*>(lo + q * 16) =
-            make_float4(v.x - tf32_hi(v.x), v.y - tf32_hi(v.y), v.z - tf32_hi(v.z), v.w - tf32_hi(v.w));
-    }
+// tensor memory: accumulators at columns [0, 2 UBN); strip slot s (of kSlots): the high part of a
+// 64-column half at 2 UBN + 128 s, its low part 64 columns further
+constexpr int kSlots = 3;
+__host__ __device__ constexpr uint32_t slot_col(int s, int lo) {
+    return (uint32_t)(2 * UBN) + 128u * (uint32_t)s + 64u * (uint32_t)lo;
 }
+static_assert(slot_col(kSlots - 1, 1) + 64 <= 512, "tensor memory");
+static_assert(UCB == 2, "two epilogue warp groups, one per 32-column box of a C tile");
+constexpr int kStripThreads = 480;
+constexpr int kEpiWarps = 8;
+constexpr uint32_t kTmemCols = 512;
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
@@ -424,19 +421,16 @@ __global__ void __launch_bounds__(kStripThreads, 1)
                 const __grid_constant__ CUtensorMap tS, float* __restrict__ Mall, int nu, int64_t ld, int64_t estride,
                 int64_t E, int J, int jb, int koff, int r0, int r_end, int c0, int c_end, int* __restrict__ err) {
     using Cfg = UpdCfg<NK>;
-    constexpr int NU = Cfg::NU, NL = Cfg::NL, NC = Cfg::NC, NSB = Cfg::NSB, KB = Cfg::KB;
+    constexpr int NU = Cfg::NU, NC = Cfg::NC, NH = Cfg::NH, KB = Cfg::KB;
     extern __shared__ __align__(1024) unsigned char ssm_raw[];
     unsigned char* base = (unsigned char*)(((uintptr_t)ssm_raw + 1023) & ~(uintptr_t)1023);
-    unsigned char* ustage0 = base;                                  // [NU]: FP32 U12^T tile (KB boxes)
-    unsigned char* lstage0 = base + NU * Cfg::U_STAGE;              // [NL]: its low part (KB boxes)
-    unsigned char* cstage0 = lstage0 + NL * Cfg::U_STAGE;           // [NC]: C tile (UCB boxes)
-    uint64_t* a_ready = (uint64_t*)(base + Cfg::BYTES);            // [NSB]
-    uint64_t* a_empty = a_ready + NSB;                              // [NSB]
-    uint64_t* u_full = a_empty + NSB;                               // [NU]
-    uint64_t* u_empty = u_full + NU;                                // [NU]: MMA commit + the four splitter warps
-    uint64_t* l_ready = u_empty + NU;                               // [NL]
-    uint64_t* l_empty = l_ready + NL;                               // [NL]
-    uint64_t* c_full = l_empty + NL;                                // [NC]
+    unsigned char* ustage0 = base;                                  // [NU]: U12^T tile and low part (2 KB boxes)
+    unsigned char* cstage0 = base + NU * Cfg::U_STAGE;              // [NC]: C tile (UCB boxes)
+    uint64_t* s_ready = (uint64_t*)(base + Cfg::BYTES);            // [kSlots]
+    uint64_t* s_empty = s_ready + kSlots;                           // [kSlots]
+    uint64_t* u_full = s_empty + kSlots;                            // [NU]
+    uint64_t* u_empty = u_full + NU;                                // [NU]
+    uint64_t* c_full = u_empty + NU;                                // [NC]
     uint64_t* c_done = c_full + NC;                                 // [NC]
     uint64_t* c_empty = c_done + NC;                                // [NC]
     uint64_t* acc_full = c_empty + NC;                              // [2]
@@ -448,26 +442,22 @@ __global__ void __launch_bounds__(kStripThreads, 1)
     const int64_t W = (int64_t)nstrips * E;
     const int ntile = (c_end - c0 + UBN - 1) / UBN;
     if (threadIdx.x == 0) {
-        for (int i = 0; i < NSB; ++i) {
-            tc::mbar_init(&a_ready[i], 4);
-            tc::mbar_init(&a_empty[i], 1);
+        for (int i = 0; i < kSlots; ++i) {
+            tc::mbar_init(&s_ready[i], 4);
+            tc::mbar_init(&s_empty[i], 1);
         }
         for (int i = 0; i < NU; ++i) {
             tc::mbar_init(&u_full[i], 1);
-            tc::mbar_init(&u_empty[i], 5);
-        }
-        for (int i = 0; i < NL; ++i) {
-            tc::mbar_init(&l_ready[i], 4);
-            tc::mbar_init(&l_empty[i], 1);
+            tc::mbar_init(&u_empty[i], 1);
         }
         for (int i = 0; i < NC; ++i) {
             tc::mbar_init(&c_full[i], 1);
-            tc::mbar_init(&c_done[i], 4);
+            tc::mbar_init(&c_done[i], kEpiWarps);
             tc::mbar_init(&c_empty[i], 1);
         }
         for (int i = 0; i < 2; ++i) {
             tc::mbar_init(&acc_full[i], 1);
-            tc::mbar_init(&acc_empty[i], 4);
+            tc::mbar_init(&acc_empty[i], kEpiWarps);
         }
         *abort = 0;
         tc::fence_barrier_init();
@@ -496,7 +486,10 @@ __global__ void __launch_bounds__(kStripThreads, 1)
                 }
                 unsigned char* us = ustage0 + su * Cfg::U_STAGE;
                 tc::mbar_expect_tx(&u_full[su], Cfg::U_TX);
-                for (int kb = 0; kb < KB; ++kb) tma_load_3d(&tU, &u_full[su], us + kb * Cfg::U_BOX, koff + kb * 32, n0, (int)e);
+                for (int kb = 0; kb < KB; ++kb) {
+                    tma_load_3d(&tU, &u_full[su], us + kb * Cfg::U_BOX, koff + kb * 32, n0, (int)e);
+                    tma_load_3d(&tU, &u_full[su], us + (KB + kb) * Cfg::U_BOX, UTL + koff + kb * 32, n0, (int)e);
+                }
                 ++issued_u;
                 if (!tc::mbar_wait(&c_empty[sc], ((g / NC) & 1) ^ 1, abort)) {
                     ok = false;
@@ -517,15 +510,8 @@ __global__ void __launch_bounds__(kStripThreads, 1)
         bool ok = true;
         int g = 0, i = 0;
         for (int64_t w = blockIdx.x; w < W && ok; w += gridDim.x, ++i) {
-            const int ab = i % NSB;
-            if (!tc::mbar_wait(&a_ready[ab], (i / NSB) & 1, abort)) {
-                ok = false;
-                break;
-            }
-            tc::tc_fence_after();
-            const uint32_t a_hi = tmem + Cfg::strip_col(ab, 0), a_lo = tmem + Cfg::strip_col(ab, 1);
             for (int t = 0; t < ntile; ++t, ++g) {
-                const int su = g % NU, sl = g % NL, a = g & 1;
+                const int su = g % NU, a = g & 1;
                 if (!tc::mbar_wait(&acc_empty[a], ((g >> 1) & 1) ^ 1, abort) ||
                     !tc::mbar_wait(&u_full[su], (g / NU) & 1, abort)) {
                     ok = false;
@@ -535,35 +521,39 @@ __global__ void __launch_bounds__(kStripThreads, 1)
                 unsigned char* us = ustage0 + su * Cfg::U_STAGE;
                 const uint32_t d = tmem + (uint32_t)(a * UBN);
                 uint32_t acc = 0;
-                // hi*hi and lo*hi as soon as the FP32 U12^T tile has landed (it is its own high
-                // part), then hi*lo once the splitters have written the low part
-                for (int kb = 0; kb < KB; ++kb) {
-                    const uint64_t bh = tc::sw128_desc(tc::smem_u32(us + kb * Cfg::U_BOX));
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {  // K = 8 per instruction
-                        const uint32_t kc = (uint32_t)(kb * 32 + k * 8);
-                        mma_tf32_ta(d, a_hi + kc, bh + 2 * k, idesc, acc);
-                        acc = 1;
-                        mma_tf32_ta(d, a_lo + kc, bh + 2 * k, idesc, 1);
+                for (int j = 0; j < NH; ++j) {  // strip halves: K columns 64 j .. 64 j + 63
+                    const int h = i * NH + j, sl = h % kSlots;
+                    // (a completed phase stays complete until the slot is refilled, which needs
+                    // this item's commit below: later tiles pass at once)
+                    if (!tc::mbar_wait(&s_ready[sl], (h / kSlots) & 1, abort)) {
+                        ok = false;
+                        break;
+                    }
+                    tc::tc_fence_after();
+                    const uint32_t a_hi = tmem + slot_col(sl, 0), a_lo = tmem + slot_col(sl, 1);
+#pragma unroll
+                    for (int kq = 0; kq < 2; ++kq) {
+                        const int kb = 2 * j + kq;
+                        const uint64_t bh = tc::sw128_desc(tc::smem_u32(us + kb * Cfg::U_BOX));
+                        const uint64_t bl = tc::sw128_desc(tc::smem_u32(us + (KB + kb) * Cfg::U_BOX));
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {  // K = 8 per instruction
+                            const uint32_t kc = (uint32_t)(kq * 32 + k * 8);
+                            mma_tf32_ta(d, a_hi + kc, bh + 2 * k, idesc, acc);
+                            acc = 1;
+                            mma_tf32_ta(d, a_lo + kc, bh + 2 * k, idesc, 1);
+                            mma_tf32_ta(d, a_hi + kc, bl + 2 * k, idesc, 1);
+                        }
                     }
                 }
-                tc::mma_commit(&u_empty[su]);  // with the splitters' arrivals: the FP32 tile is free
-                if (!tc::mbar_wait(&l_ready[sl], (g / NL) & 1, abort)) {
-                    ok = false;
-                    break;
-                }
-                tc::tc_fence_after();
-                unsigned char* ls = lstage0 + sl * Cfg::U_STAGE;
-                for (int kb = 0; kb < KB; ++kb) {
-                    const uint64_t bl = tc::sw128_desc(tc::smem_u32(ls + kb * Cfg::U_BOX));
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) mma_tf32_ta(d, a_hi + (uint32_t)(kb * 32 + k * 8), bl + 2 * k, idesc, 1);
-                }
-                tc::mma_commit(&l_empty[sl]);
+                if (!ok) break;
+                tc::mma_commit(&u_empty[su]);
                 tc::mma_commit(&acc_full[a]);
                 ++committed;
             }
-            if (ok) tc::mma_commit(&a_empty[ab]);
+            if (ok)
+                for (int j = 0; j < NH; ++j) tc::mma_commit(&s_empty[(i * NH + j) % kSlots]);
         }
         if (!ok) {
             if (err) atomicOr(err, 128);
@@ -576,21 +566,16 @@ __global__ void __launch_bounds__(kStripThreads, 1)
         bool ok = true;
         int i = 0;
         for (int64_t w = blockIdx.x; w < W && ok; w += gridDim.x, ++i) {
-            const int ab = i % NSB;
-            if (!__all_sync(0xffffffffu, tc::mbar_wait(&a_empty[ab], ((i / NSB) & 1) ^ 1, abort) && !*abort)) {
-                ok = false;
-                break;
-            }
-            tc::tc_fence_after();
             const int64_t e = w / nstrips;
             const int m = r0 + (int)(w - e * nstrips) * 128 + row;
             const float* src = Mall + e * estride + (int64_t)m * ld + J;
+            for (int j = 0; j < NH && ok; ++j) {
+                const int h = i * NH + j, sl = h % kSlots;
+                // the half's row into registers first: its loads are in flight while the slot drains
+                float v[64];
 #pragma unroll
-            for (int half = 0; half < KB; ++half) {
-                float v[32], lo[32];
-#pragma unroll
-                for (int k4 = 0; k4 < 8; ++k4) {
-                    const int k = half * 32 + 4 * k4;
+                for (int k4 = 0; k4 < 16; ++k4) {
+                    const int k = 64 * j + 4 * k4;
                     float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
                     if (m < nu && k < jb) x = *reinterpret_cast<const float4*>(src + k);  // jb is a multiple of 4
                     v[4 * k4] = x.x;
@@ -598,19 +583,27 @@ __global__ void __launch_bounds__(kStripThreads, 1)
                     v[4 * k4 + 2] = x.z;
                     v[4 * k4 + 3] = x.w;
                 }
-#pragma unroll
-                for (int k = 0; k < 32; ++k) {
-                    const float h = tf32_hi(v[k]);
-                    lo[k] = v[k] - h;
-                    v[k] = h;
+                if (!__all_sync(0xffffffffu, tc::mbar_wait(&s_empty[sl], ((h / kSlots) & 1) ^ 1, abort) && !*abort)) {
+                    ok = false;
+                    break;
                 }
-                tmem_st32(tmem + lane_off + Cfg::strip_col(ab, 0) + half * 32, v);
-                tmem_st32(tmem + lane_off + Cfg::strip_col(ab, 1) + half * 32, lo);
+                tc::tc_fence_after();
+#pragma unroll
+                for (int hh = 0; hh < 2; ++hh) {
+                    float hi[32], lo[32];
+#pragma unroll
+                    for (int k = 0; k < 32; ++k) {
+                        hi[k] = tf32_hi(v[hh * 32 + k]);
+                        lo[k] = v[hh * 32 + k] - hi[k];
+                    }
+                    tmem_st32(tmem + lane_off + slot_col(sl, 0) + hh * 32, hi);
+                    tmem_st32(tmem + lane_off + slot_col(sl, 1) + hh * 32, lo);
+                }
+                tmem_st_wait();
+                tc::tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&s_ready[sl]);
             }
-            tmem_st_wait();
-            tc::tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&a_ready[ab]);
         }
         if (!ok && lane == 0) {
             if (err) atomicOr(err, 1024);
@@ -644,37 +637,9 @@ __global__ void __launch_bounds__(kStripThreads, 1)
                 *abort = 1;
             }
         }
-    } else if (warp >= 10) {  // U12^T tile splitters
-        const int tid = threadIdx.x - 10 * 32;
-        bool ok = true;
-        int g = 0;
-        for (int64_t w = blockIdx.x; w < W && ok; w += gridDim.x) {
-            for (int t = 0; t < ntile; ++t, ++g) {
-                const int su = g % NU, sl = g % NL;
-                // the FP32 tile has landed and the low-part buffer's previous hi*lo pass is done
-                if (!__all_sync(0xffffffffu, tc::mbar_wait(&u_full[su], (g / NU) & 1, abort) &&
-                                                 tc::mbar_wait(&l_empty[sl], ((g / NL) & 1) ^ 1, abort) && !*abort)) {
-                    ok = false;
-                    break;
-                }
-                const unsigned char* us = ustage0 + su * Cfg::U_STAGE;
-                unsigned char* ls = lstage0 + sl * Cfg::U_STAGE;
-                for (int kb = 0; kb < KB; ++kb) split_lo(us + kb * Cfg::U_BOX, ls + kb * Cfg::U_BOX, UBN, tid, 128);
-                // generic-proxy writes, read next by the tensor cores (async proxy)
-                tc::fence_proxy_async();
-                __syncwarp();
-                if (lane == 0) {
-                    mbar_arrive(&l_ready[sl]);
-                    mbar_arrive(&u_empty[su]);  // done reading the FP32 tile
-                }
-            }
-        }
-        if (!ok && lane == 0) {
-            if (err) atomicOr(err, 512);
-            *abort = 1;
-        }
-    } else if (warp >= 2) {
+    } else if (warp >= 2) {  // epilogue: warps 2-5 (box 0) and 10-13 (box 1)
         const int q = warp & 3;
+        const int cb = warp >= 10 ? 1 : 0;
         const int row = q * 32 + lane;
         int g = 0;
         bool ok = true;
@@ -688,29 +653,26 @@ __global__ void __launch_bounds__(kStripThreads, 1)
                     break;
                 }
                 tc::tc_fence_after();
-                unsigned char* cst = cstage0 + sc * Cfg::C_STAGE;
+                float d[32];
 #pragma unroll
-                for (int cb = 0; cb < UCB; ++cb) {
-                    float d[32];
+                for (int c = 0; c < 32; c += 16) {
+                    float v[16];
+                    tc::tmem_ld16(tmem + (uint32_t)(a * UBN + 32 * cb) + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
 #pragma unroll
-                    for (int c = 0; c < 32; c += 16) {
-                        float v[16];
-                        tc::tmem_ld16(tmem + (uint32_t)(a * UBN + 32 * cb) + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
-#pragma unroll
-                        for (int j = 0; j < 16; ++j) d[c + j] = v[j];
-                    }
-                    // C box cb in shared memory: rows m0 .. m0 + 127 of columns n0 + 32 cb .. + 31,
-                    // 128-byte rows with the 16-byte chunk index XOR-ed by (row % 8); C - L U goes
-                    // back in place
-                    unsigned char* crow = cst + cb * Cfg::C_BOX + row * 128;
-#pragma unroll
-                    for (int ch = 0; ch < 8; ++ch) {
-                        float4* p = reinterpret_cast<float4*>(crow + ((ch ^ (row & 7)) << 4));
-                        const float4 cv = *p;
-                        *p = make_float4(cv.x - d[4 * ch], cv.y - d[4 * ch + 1], cv.z - d[4 * ch + 2],
-                                         cv.w - d[4 * ch + 3]);
-                    }
+                    for (int j = 0; j < 16; ++j) d[c + j] = v[j];
                 }
+                // C box cb in shared memory: rows m0 .. m0 + 127 of columns n0 + 32 cb .. + 31,
+                // 128-byte rows with the 16-byte chunk index XOR-ed by (row % 8); C - L U goes back
+                // in place
+                unsigned char* crow = cstage0 + sc * Cfg::C_STAGE + cb * Cfg::C_BOX + row * 128;
+                float4 cv[8];
+#pragma unroll
+                for (int ch = 0; ch < 8; ++ch) cv[ch] = *reinterpret_cast<const float4*>(crow + ((ch ^ (row & 7)) << 4));
+#pragma unroll
+                for (int ch = 0; ch < 8; ++ch)
+                    *reinterpret_cast<float4*>(crow + ((ch ^ (row & 7)) << 4)) =
+                        make_float4(cv[ch].x - d[4 * ch], cv[ch].y - d[4 * ch + 1], cv[ch].z - d[4 * ch + 2],
+                                    cv[ch].w - d[4 * ch + 3]);
                 // written through the generic proxy, read next by the TMA store (async proxy)
                 tc::tc_fence_before();
                 tc::fence_proxy_async();
