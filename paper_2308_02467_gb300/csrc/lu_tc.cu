@@ -524,13 +524,15 @@ __global__ void __launch_bounds__(kStripThreads, 1)
 #pragma unroll
                 for (int j = 0; j < NH; ++j) {  // strip halves: K columns 64 j .. 64 j + 63
                     const int h = i * NH + j, sl = h % kSlots;
-                    // (a completed phase stays complete until the slot is refilled, which needs
-                    // this item's commit below: later tiles pass at once)
-                    if (!tc::mbar_wait(&s_ready[sl], (h / kSlots) & 1, abort)) {
-                        ok = false;
-                        break;
+                    // the item's first tile waits for each half (each wait the issuing thread makes
+                    // costs MMA issue slots; the slot stays filled until this item's commit below)
+                    if (t == 0) {
+                        if (!tc::mbar_wait(&s_ready[sl], (h / kSlots) & 1, abort)) {
+                            ok = false;
+                            break;
+                        }
+                        tc::tc_fence_after();
                     }
-                    tc::tc_fence_after();
                     const uint32_t a_hi = tmem + slot_col(sl, 0), a_lo = tmem + slot_col(sl, 1);
 #pragma unroll
                     for (int kq = 0; kq < 2; ++kq) {
@@ -703,6 +705,13 @@ __global__ void __launch_bounds__(kStripThreads, 1)
             const int last = committed - 1;
             const long long t0 = clock64();
             while (!tc::mbar_try_wait(&acc_full[last & 1], (last >> 1) & 1) && clock64() - t0 < tc::kWaitCycles) {
+            }
+            // and let the strip-slot commits issued after it arrive before the CTA's shared memory goes
+            const int items = (int)((W - 1 - blockIdx.x) / gridDim.x) + 1;
+            for (int h = (items - 1) * NH; committed == items * ntile && h < items * NH; ++h) {
+                const long long t1 = clock64();
+                while (!tc::mbar_try_wait(&s_empty[h % kSlots], (h / kSlots) & 1) && clock64() - t1 < tc::kWaitCycles / 4) {
+                }
             }
         }
         __syncwarp();
