@@ -34,12 +34,13 @@ WORKLOAD = workload_name(64)
 # the pipe whose issue rate limits it.  The float-float residual counts one useful flop per
 # multiply or add of the structured operator; one float-float multiply-add takes 12 FP32 issue
 # slots (1 MUL, 3 FMA, 6 in TwoSum, 2 ADD), so its ALU peak is the FP32 rate x 2 / 12.
-# The trailing update of the tensor-core LU is a dense contraction: "tensor", against the TF32
-# tensor peak, counting the useful flops 2 R C jb once (it issues each product three times as
-# hi*hi + hi*lo + lo*hi, reported separately as the issued fraction).
+# The trailing update of the tensor-core LU is a dense contraction that also streams its trailing
+# tiles through HBM: "roof" takes whichever floor binds, the bytes at the copy bandwidth or the
+# issued flops (each product three times, hi*hi + lo*hi + hi*lo) at the TF32 tensor peak, and
+# reports the achieved fraction of that roof (the other fraction beside it).
 KERNEL_BOUND = {
     "assemble": ("hbm", None), "lu_factor_solve": ("alu", "fp32"), "lu_resolve": ("hbm", None),
-    "lu_tc_diag": ("alu", "fp32"), "lu_tc_rowcol": ("hbm", None), "lu_tc_update": ("tensor", "tf32x3"),
+    "lu_tc_diag": ("alu", "fp32"), "lu_tc_rowcol": ("hbm", None), "lu_tc_update": ("roof", "tf32x3"),
     "residual": ("alu", "ff"), "restrict": ("hbm", None), "gemv": ("hbm", None), "krylov": ("hbm", None),
 }
 TENSOR_PASSES = {"tf32x3": 3}
@@ -53,13 +54,12 @@ def tensor_peak_tflops(peaks):
     nominal TF32/BF16 ratio."""
     return peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]) * TF32_PER_BF16
 # DRAM bytes (read + write) per element and step of each kernel group, from one ncu capture of
-# the 32 x 32 slab (1024 elements, 3.3 GB of local workspace; summary kept under profiles/); a
-# group missing here has no capture of its current kernel.  The 32 x 32 operators (205 MB) still
-# partly fit in the 126 MB L2, so the matvec figure is a lower bound at 64 x 64.  Scaled to a
-# launch of the benchmark by elements / launches.
+# the 32 x 32 slab (1024 elements, one local-build chunk; summary kept under profiles/); a group
+# missing here has no capture of its current kernel.  Scaled to a launch of the benchmark by
+# elements / launches.
 DRAM_BYTES_PER_ELEMENT_STEP = {
-    "lu_tc_update": 6.109e7, "lu_tc_rowcol": 1.225e7, "lu_tc_diag": 3.264e5, "residual": 3.236e6,
-    "assemble": 3.277e6, "restrict": 2.817e6,
+    "lu_tc_update": 4.916e7, "lu_tc_rowcol": 1.666e7, "lu_tc_diag": 3.261e5, "residual": 2.967e6,
+    "assemble": 3.273e6, "restrict": 2.905e6,
 }
 
 
@@ -109,10 +109,12 @@ def kernel_rooflines(prof, work, steps, n, hbm, peak_src, mode, clk_max, tensor_
                "bytes_per_launch": b / nl, "achieved_gbs": b / t_s / 1e9, "frac_hbm": b / t_s / 1e9 / hbm}
         if f > 0:
             row["tflops"] = f / t_s / 1e12
-            if bound == "tensor":
+            if bound in ("tensor", "roof"):
                 if tensor_peak:
                     row["frac_tensor"] = row["tflops"] / tensor_peak
                     row["frac_tensor_issued"] = row["tflops"] * TENSOR_PASSES.get(pipe, 1) / tensor_peak
+                if bound == "roof":  # the binding floor: bytes at the copy bandwidth or issued flops at the peak
+                    bound = "hbm" if not tensor_peak or row["frac_hbm"] >= row["frac_tensor_issued"] else "tensor"
             else:
                 pk = alu_peak_tflops(pipe, mode, clk_max) if pipe else None
                 if pk:
@@ -121,7 +123,7 @@ def kernel_rooflines(prof, work, steps, n, hbm, peak_src, mode, clk_max, tensor_
         kernels[name] = row
     top = max(kernels, key=lambda k: kernels[k]["ms_per_step"])
     tk = kernels[top]
-    bound, pipe = KERNEL_BOUND[top]
+    bound, pipe = tk["bound"], KERNEL_BOUND[top][1]
     dram = DRAM_BYTES_PER_ELEMENT_STEP.get(top)
     traffic = dram * n / tk["launches_per_step"] if dram else None
     if bound == "hbm":
@@ -129,6 +131,10 @@ def kernel_rooflines(prof, work, steps, n, hbm, peak_src, mode, clk_max, tensor_
                 "frac": tk["frac_hbm"], "traffic": traffic,
                 "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({peak_src})",
                 "algorithmic_bytes_per_launch": tk["bytes_per_launch"]}
+        if "frac_tensor_issued" in tk:  # a contraction whose bytes bind: its tensor-pipe figures beside
+            roof.update({"tflops": tk["tflops"], "tensor_peak": tensor_peak, "frac_tensor": tk["frac_tensor"],
+                         "frac_tensor_issued": tk["frac_tensor_issued"], "passes": TENSOR_PASSES.get(pipe, 1),
+                         "flops_counted": "useful 2 R C jb per element and panel, once"})
     elif bound == "tensor":
         roof = {"kernel": top, "bound": "tensor", "achieved": tk["tflops"], "peak": tensor_peak, "unit": "TFLOP/s",
                 "frac": tk["tflops"] / tensor_peak, "traffic": traffic,

@@ -24,20 +24,37 @@ def _tables(prof, work, mode="tf32ir", clk=2070.0):
     return bench.kernel_rooflines(prof, work, STEPS, N, HBM, "measured", mode, clk, tensor_peak=TF32)
 
 
-def test_tensor_bound_dominant_group():
-    """The trailing update: useful flops / event time against the TF32 peak derived from the
-    measured sustained BF16 rate; the issued fraction counts its three TF32 passes."""
+def test_contraction_takes_the_binding_roof():
+    """The trailing update moves its trailing tiles through HBM and issues each product three times
+    on the TF32 pipe: whichever floor binds is its roof.  Here the bytes bind (5.5 TB/s against 66
+    TFLOP/s issued): HBM-bound, with the tensor fractions reported beside it."""
     prof = {"lu_tc_update": (96 * 0.456, 96), "gemv": (20.0, 1385)}
     work = {"lu_tc_update": (96 * 2.5e9, 96 * 1.0e10), "gemv": (1385 * 4.8e8, 0.0)}
     kernels, roof = _tables(prof, work)
     assert bench.tensor_peak_tflops({"bf16_tflops": 1893.4, "bf16_tflops_sustained": 1697.3}) == pytest.approx(TF32)
-    assert roof["kernel"] == "lu_tc_update" and roof["bound"] == "tensor" and roof["unit"] == "TFLOP/s"
+    gbs = 2.5e9 / 0.456e-3 / 1e9
     tflops = 1.0e10 / 0.456e-3 / 1e12
+    assert roof["kernel"] == "lu_tc_update" and roof["bound"] == "hbm" and roof["unit"] == "GB/s"
+    assert roof["achieved"] == pytest.approx(gbs) and roof["peak"] == HBM
+    assert roof["frac"] == pytest.approx(gbs / HBM)
+    assert roof["frac_tensor"] == pytest.approx(tflops / TF32)
+    assert roof["frac_tensor_issued"] == pytest.approx(3 * tflops / TF32)
+    assert kernels["lu_tc_update"]["bound"] == "hbm"
+
+
+def test_contraction_bound_by_the_tensor_pipe():
+    """Ten times fewer bytes, ten times more flops: the issued flops bind (tensor roof), useful
+    flops over the TF32 peak derived from the measured sustained BF16 rate."""
+    prof = {"lu_tc_update": (96 * 0.456, 96), "gemv": (20.0, 1385)}
+    work = {"lu_tc_update": (96 * 2.5e8, 96 * 1.0e11), "gemv": (1385 * 4.8e8, 0.0)}
+    kernels, roof = _tables(prof, work)
+    tflops = 1.0e11 / 0.456e-3 / 1e12
+    assert roof["kernel"] == "lu_tc_update" and roof["bound"] == "tensor" and roof["unit"] == "TFLOP/s"
     assert roof["achieved"] == pytest.approx(tflops) and roof["peak"] == pytest.approx(TF32)
     assert roof["frac"] == pytest.approx(tflops / TF32)
     assert roof["frac_issued"] == pytest.approx(3 * tflops / TF32)
     assert kernels["lu_tc_update"]["frac_tensor"] == pytest.approx(tflops / TF32)
-    assert roof["frac_hbm"] == pytest.approx(2.5e9 / 0.456e-3 / 1e9 / HBM)
+    assert roof["frac_hbm"] == pytest.approx(2.5e8 / 0.456e-3 / 1e9 / HBM)
 
 
 def test_hbm_bound_dominant_group():
