@@ -13,6 +13,9 @@ Plain, slow, dense numpy code that follows the paper's formulation:
 * eq. hdg_global_mat: sum_K (R^o_K - A_i2o^K) u^ = 0 (f = 0), solved by GMRES
   (Sec. 2.3) or densely on tiny meshes.
 * Algorithm 1, step 4: mean-intensity recovery u^m = A_i2m u^_in.
+* Sec. 2.3 names transport sweeps among the solvers of radiative transfer: sweep_precond applies
+  upwind block Gauss-Seidel sweeps of eq. hdg_global_mat (the elements taken in the wavefront
+  order of one mesh corner, then of the others), the preconditioner of the library's GMRES.
 
 Readings where the paper is silent:
 * every integral uses the (p+1)-point LGL rule per direction (diagonal mass);
@@ -365,6 +368,56 @@ def global_dense(mesh, disc, A_i2o):
                 Fo = OPPOSITE[F]
                 G[e * no:(e + 1) * no, nb * no + Fo * nf: nb * no + (Fo + 1) * nf] -= A_i2o[e][:, F * nf:(F + 1) * nf]
     return G
+
+
+SWEEP_CORNERS = ("BL", "TR", "BR", "TL")
+
+
+def sweep_order(mesh: Mesh, corner: str):
+    """Elements in wavefront order from one corner of the mesh (bottom-left, top-right,
+    bottom-right, top-left): by the sum of the two distances from that corner, element number
+    breaking ties.  Neighbours differ by one in that sum, so the elements of one wavefront do not
+    touch and every neighbour is either one wavefront earlier (upwind) or one later."""
+    E = mesh.n_elems
+    ix, iz = np.arange(E) % mesh.nx, np.arange(E) // mesh.nx
+    dx = ix if corner in ("BL", "TL") else mesh.nx - 1 - ix
+    dz = iz if corner in ("BL", "BR") else mesh.nz - 1 - iz
+    return np.argsort(dx + dz, kind="stable")
+
+
+def sweep_precond(mesh: Mesh, disc: Disc, A_i2o, r, corners=SWEEP_CORNERS):
+    """z = M r: block Gauss-Seidel sweeps of eq. hdg_global_mat, (I - A_int) z = r, from z = 0,
+    one sweep per corner in turn.  A sweep visits the elements in wavefront order and replaces
+    each element's outflow by z_K = r_K + A_i2o^K z_in(K), the inflow gathered from the current
+    z (already swept neighbours: this sweep's values; the others: the previous sweep's, zero in the
+    first).  A linear operator: the preconditioner of the library's GMRES."""
+    E, no = mesh.n_elems, disc.n_out
+    r = np.asarray(r, dtype=np.float64).reshape(E, no)
+    z = np.zeros((E, no))
+    for corner in corners:
+        for e in sweep_order(mesh, corner):
+            zin = gather_inflow_one(mesh, disc, z, e)
+            z[e] = r[e] + A_i2o[e] @ zin
+    return z.reshape(-1)
+
+
+def gather_inflow_one(mesh: Mesh, disc: Disc, x: np.ndarray, e: int):
+    """Interior inflow [n_in] of element e from the outflow x [E, n_out] (zero on the boundary)."""
+    nf = disc.n_face
+    out = np.zeros(disc.n_in)
+    for F in range(4):
+        nb = mesh.neighbour(e, F)
+        if nb >= 0:
+            G = OPPOSITE[F]
+            out[F * nf:(F + 1) * nf] = x[nb, G * nf:(G + 1) * nf]
+    return out
+
+
+def gmres_right(apply, precond, b, rtol=1e-12, restart=50, max_iter=20000):
+    """GMRES on A M y = b, x = M y (right preconditioning: the residual it minimises is the true
+    one, b - A x).  Returns (x, iterations, relative residual)."""
+    y, it, rel = gmres(lambda v: apply(precond(v)), b, rtol=rtol, restart=restart, max_iter=max_iter)
+    return precond(y), it, rel
 
 
 def gmres(apply, b, rtol=1e-12, restart=50, max_iter=20000, x0=None):
