@@ -42,6 +42,7 @@ KERNEL_BOUND = {
     "assemble": ("hbm", None), "lu_factor_solve": ("alu", "fp32"), "lu_resolve": ("hbm", None),
     "lu_tc_diag": ("alu", "fp32"), "lu_tc_rowcol": ("hbm", None), "lu_tc_update": ("roof", "tf32x3"),
     "residual": ("alu", "ff"), "restrict": ("hbm", None), "gemv": ("hbm", None), "krylov": ("hbm", None),
+    "sweep": ("hbm", None),
 }
 TENSOR_PASSES = {"tf32x3": 3}
 # Nominal dense tensor rates of GB300 (PFLOP/s): TF32 1.1, BF16 2.25.  A TF32 peak is the measured
@@ -911,7 +912,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     ms_profiled = ev2.elapsed_time(ev3) / args.steps
     names = ("assemble", "lu_factor_solve", "lu_resolve", "lu_tc_diag", "lu_tc_rowcol", "lu_tc_update", "residual",
-             "restrict", "status", "gemv", "krylov")
+             "restrict", "status", "gemv", "krylov", "sweep")
     prof = {k: ctx.elrt_profile_get(k) for k in names}
     work = {k: ctx.elrt_profile_work(k) for k in names}
     ctx.elrt_profile_enable(False)

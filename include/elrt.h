@@ -147,6 +147,26 @@ elrt_status elrt_set_krylov_op(elrt_ctx* ctx, int32_t op);
  * FP32 from the following cycle on, one cycle later.  Off (0) or while kernel timing is enabled:
  * plain launches. */
 elrt_status elrt_set_graphs(elrt_ctx* ctx, int32_t on);
+
+/* Preconditioner of the skeleton GMRES for FP32 in2out (elrt_set_precond).  ELRT_PRECOND_SWEEP (the
+ * default): right preconditioning by upwind block Gauss-Seidel sweeps of the skeleton system
+ * (I - A_int) z = r (eq. hdg_global_mat; Sec. 2.3 lists transport sweeps among the solvers of
+ * radiative transfer), from z = 0, one sweep from each mesh corner in turn (bottom-left,
+ * top-right, bottom-right, top-left): a sweep visits the elements in wavefront order from its
+ * corner and sets z_K = r_K + A_i2o^K z_in(K) with the inflow gathered from the current z.  With
+ * right preconditioning GMRES still minimises the true residual, so the solution and the
+ * stopping test are those of plain GMRES; the Arnoldi steps fall by an order of magnitude on the
+ * scattering workloads (each then costs four sweeps, on the Arnoldi operator elrt_set_krylov_op
+ * selects).  ELRT_PRECOND_NONE: plain GMRES.  FP64 operators ignore the setting.  ELRT_EINVAL on
+ * another value. */
+typedef enum { ELRT_PRECOND_NONE = 0, ELRT_PRECOND_SWEEP = 1 } elrt_precond;
+elrt_status elrt_set_precond(elrt_ctx* ctx, int32_t kind);
+/* z = M r, the sweep preconditioner above applied once on the context's stream; synchronises.
+ * in2out: device [E][n_out][n_in] FP32 (dtype ELRT_F32; ELRT_EINVAL otherwise); r, z: device
+ * [E][n_out] FP32, distinct.  ELRT_ETIMEOUT (after a synchronisation) if a wait between elements
+ * gave up. */
+elrt_status elrt_apply_precond(elrt_ctx* ctx, int32_t nx, int32_t nz, const void* in2out, int32_t dtype,
+                               const float* r, float* z);
 const char* elrt_status_str(elrt_status s);
 const char* elrt_last_error(const elrt_ctx* ctx);   /* message of the last failing call (or "") */
 

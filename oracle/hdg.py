@@ -370,7 +370,7 @@ def global_dense(mesh, disc, A_i2o):
     return G
 
 
-SWEEP_CORNERS = ("BL", "TR", "BR", "TL")
+SWEEP_CORNERS = ("BL", "BR", "TR", "TL")
 
 
 def sweep_order(mesh: Mesh, corner: str):

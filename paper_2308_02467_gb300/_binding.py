@@ -20,6 +20,7 @@ ANG_FV0, ANG_DO = 0, 1
 LOCAL_FP64, LOCAL_FP32_IR, LOCAL_TF32_IR = 0, 1, 2
 F32, F64 = 0, 1
 KRYLOV_F32, KRYLOV_F16 = 0, 1
+PRECOND_NONE, PRECOND_SWEEP = 0, 1
 STATUS = {0: "ok", 1: "EINVAL", 2: "ENOMEM", 3: "ESINGULAR", 4: "ENOCONV", 5: "ETIMEOUT", 6: "ECUDA", 7: "ENOTRAINED"}
 
 
@@ -93,6 +94,8 @@ _sig = {
     "elrt_set_stream": (_i32, [_vp, _vp]),
     "elrt_set_krylov_op": (_i32, [_vp, _i32]),
     "elrt_set_graphs": (_i32, [_vp, _i32]),
+    "elrt_set_precond": (_i32, [_vp, _i32]),
+    "elrt_apply_precond": (_i32, [_vp, _i32, _i32, _vp, _i32, _vp, _vp]),
     "elrt_autotune": (_i32, [_vp, _P(Field), _i32, _i32, _d, _P(TuneReport)]),
     "elrt_get_tuning": (_i32, [_vp, _P(_i64), _P(_i32), _P(_i32), _P(_i32)]),
     "elrt_set_tuning": (_i32, [_vp, _i64, _i32, _i32]),
@@ -304,6 +307,18 @@ class Context:
     def elrt_set_graphs(self, on=True):
         """CUDA-graph replay of the GMRES restart cycles (default on)."""
         _check(_lib.elrt_set_graphs(self._h, int(bool(on))), self._h)
+
+    def elrt_set_precond(self, kind):
+        """PRECOND_SWEEP (default) or PRECOND_NONE: preconditioner of the skeleton GMRES (FP32 in2out)."""
+        _check(_lib.elrt_set_precond(self._h, int(kind)), self._h)
+
+    def elrt_apply_precond(self, nx, nz, in2out, r, z):
+        """z = M r: the sweep preconditioner once (FP32 in2out, FP32 r and z [E][n_out])."""
+        import torch
+        n = nx * nz * self.nin
+        self._sync_stream()
+        _check(_lib.elrt_apply_precond(self._h, nx, nz, _ptr(in2out, torch.float32, n * self.nin, "in2out"), F32,
+                                       _ptr(r, torch.float32, n, "r"), _ptr(z, torch.float32, n, "z")), self._h)
 
     def elrt_set_krylov_op(self, op):
         """KRYLOV_F16 (default) or KRYLOV_F32: operator of the Arnoldi-step matvecs (FP32 in2out)."""

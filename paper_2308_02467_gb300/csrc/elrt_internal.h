@@ -62,6 +62,7 @@ struct elrt_ctx {
     size_t gm16_bytes = 0;
     int krylov_op = ELRT_KRYLOV_F16;
     int graphs = 1;         // replay GMRES restart cycles from captured CUDA graphs
+    int precond = ELRT_PRECOND_SWEEP;  // skeleton GMRES preconditioner (FP32 operators)
     void* ops = nullptr;    // in2out / in2sol of elrt_solve_field
     size_t ops_bytes = 0;
     void* vec = nullptr;    // skeleton of elrt_solve_field when the caller passes none
@@ -123,6 +124,11 @@ elrt_status global_recover(elrt_ctx* ctx, int nx, int nz, const void* A, int dty
                            const double* inflow, double* mean, const double* f2m = nullptr);
 elrt_status global_recover_rows(elrt_ctx* ctx, int nx, int nz, int rows, const void* A, int dtype, const double* x,
                                 const double* inflow, const double* self, double* out);
+
+// ---- sweep preconditioner of the skeleton GMRES (sweep.cu)
+void sweep_orders(int nx, int nz, int* out);
+elrt_status sweep_apply(elrt_ctx* ctx, int nx, int nz, const void* A, int a_bytes, const float* u, float* z,
+                        const int* order, void* zw, int* flags, const int* done, const int* nsteps);
 
 // ---- learned local stage (mlp.cu)
 extern "C" elrt_status elrt_build_local_learned(elrt_ctx* ctx, elrt_net* net, int64_t n, double h, const double* h_elem,

@@ -1040,6 +1040,16 @@ __global__ void __launch_bounds__(kThreads) k_update_x(const V* __restrict__ Vb,
     }
 }
 
+// x += t (the preconditioned correction of a cycle), in the iterate's arithmetic
+template <typename X>
+__global__ void __launch_bounds__(kThreads) k_add_f(X* __restrict__ x, const float* __restrict__ t, int64_t n) {
+    for (int64_t k = blockIdx.x * (int64_t)kThreads + threadIdx.x; k < n; k += (int64_t)gridDim.x * kThreads) {
+        typename KV<X>::acc s = KV<X>::load(x[k]);
+        KV<float>::fma_cv(s, KV<X>::coef(1.0), t[k]);
+        x[k] = KV<X>::store(s);
+    }
+}
+
 // Start of a restart cycle.  A restart residual at or below the tolerance (or not finite) ends the
 // solve on the device: the cycle's kernels see done and do nothing, and j_done stays 0.
 __global__ void k_cycle_start(GmState* st, double* gv, int m, const double* beta, double* sc0) {
@@ -1471,7 +1481,13 @@ elrt_status gmres(elrt_ctx* ctx, int nx, int nz, const void* Aop, const double* 
     // FP64 small arrays: H, cs, sn, gv, yv, the per-block partials, then the Arnoldi-step state
     const size_t small = ((size_t)(m + 1) * m + 4 * (size_t)(m + 1) + (size_t)(m + 1) * nblk + 128) * sizeof(double) +
                          sizeof(ArnState);
-    elrt_status s = ensure_ws(ctx, &ctx->gm, &ctx->gm_bytes, vb_bytes + xbytes + 256 + small + sizeof(GmState) + 512);
+    // sweep preconditioner (FP32 basis): M v_j and the cycle's correction [n] FP32 each, the
+    // sweeps' versioned outflow [n] (8 bytes each), the item order [4 E] and two flags
+    const int64_t E = (int64_t)nx * nz;
+    const bool pc = std::is_same<V, float>::value && ctx->precond == ELRT_PRECOND_SWEEP;
+    const size_t pc_bytes =
+        pc ? (((size_t)4 * n * sizeof(float) + (size_t)4 * E * sizeof(int) + 64 + 255) & ~(size_t)255) : 0;
+    elrt_status s = ensure_ws(ctx, &ctx->gm, &ctx->gm_bytes, vb_bytes + xbytes + 256 + small + sizeof(GmState) + 512 + pc_bytes);
     if (s) return s;
     V* Vb = (V*)ctx->gm;
     X* b = (X*)((unsigned char*)ctx->gm + vb_bytes);
@@ -1486,6 +1502,11 @@ elrt_status gmres(elrt_ctx* ctx, int nx, int nz, const void* Aop, const double* 
     ArnState* arn = (ArnState*)(partial + (size_t)(m + 1) * nblk);
     double* scal = (double*)(arn + 1) + 8;  // [0] ||b||, [1] beta
     GmState* st = (GmState*)(scal + 64);
+    float* pc_t = pc ? (float*)(((uintptr_t)(st + 1) + 255) & ~(uintptr_t)255) : nullptr;  // M v_j, M u
+    float* pc_u = pc ? pc_t + n : nullptr;                                                 // sum y_i s_i W_i
+    void* pc_zw = pc ? (void*)(pc_u + n) : nullptr;                                       // 8 n bytes
+    int* pc_order = pc ? (int*)(pc_u + 3 * n) : nullptr;
+    int* pc_flags = pc ? pc_order + 4 * E : nullptr;
     // three-launch Arnoldi step: FP32 basis, restarts up to kArnMaxV - 1 and the streaming matvec
     const bool arn4 = std::is_same<V, float>::value && m + 1 <= kArnMaxV && gemv_streams(t, Aop, (int)sizeof(A));
     cudaStream_t sm = ctx->stream;
@@ -1495,6 +1516,14 @@ elrt_status gmres(elrt_ctx* ctx, int nx, int nz, const void* Aop, const double* 
     GmState* hst = (GmState*)ctx->h_pinned;
     const int rows = t.nin;
 
+    if (pc) {
+        std::vector<int> ord((size_t)4 * E);
+        sweep_orders(nx, nz, ord.data());
+        s = cuda_check(ctx, cudaMemcpyAsync(pc_order, ord.data(), ord.size() * sizeof(int), cudaMemcpyHostToDevice, sm),
+                       "sweep orders");
+        if (!s) s = cuda_check(ctx, cudaStreamSynchronize(sm), "sweep orders");  // (pageable source)
+        if (s) return s;
+    }
     s = cuda_check(ctx, cudaMemsetAsync(ctx->d_flags + kGemvFlag, 0, 2 * sizeof(int), sm), "clear flags");
     if (!s) s = cuda_check(ctx, cudaMemsetAsync(arn, 0, sizeof(ArnState), sm), "clear Arnoldi state");
     if (s) return s;
@@ -1571,7 +1600,8 @@ elrt_status gmres(elrt_ctx* ctx, int nx, int nz, const void* Aop, const double* 
     int its = 0, cycles = 0;
     double rel = 1.0, beta_prev = 0.0;
     bool converged = false;
-    int* hflag = (int*)((unsigned char*)ctx->h_pinned + 2048);
+    int* hflag = (int*)((unsigned char*)ctx->h_pinned + 2048);  // [0] matvec copy wait, [1] sweep wait
+    hflag[0] = hflag[1] = 0;
     // restart residual r = b - (I - A_int) x and beta = ||r||
     auto enqueue_residual = [&]() -> elrt_status {
         elrt_status e = launch_gemv<A, X>(ctx, nx, nz, rows, Aop, x, nullptr, x, 1, -1, r, nullptr);
@@ -1596,6 +1626,12 @@ elrt_status gmres(elrt_ctx* ctx, int nx, int nz, const void* Aop, const double* 
             V* w = Vb + (size_t)(j + 1) * n;
             double* hc = H + (size_t)j * (m + 1);
             if constexpr (std::is_same<V, float>::value) {
+                if (pc) {  // right preconditioning: the matvec takes M W_j (its scale folded in as before)
+                    e = sweep_apply(ctx, nx, nz, f16 ? (const void*)A16 : Aop, f16 ? 2 : (int)sizeof(A), vj, pc_t,
+                                    pc_order, pc_zw, pc_flags, &st->done, nullptr);
+                    if (e) return e;
+                    vj = pc_t;
+                }
                 if (arn4) {  // matvec with the first Gram-Schmidt pass, then two launches
                     const ArnFuse fz{arn, partial, Vb, n, j};
                     if (f16 && tc16) e = launch_gemv_tc(ctx, map16, nx, nz, vj, w, st, fz);
@@ -1633,7 +1669,22 @@ elrt_status gmres(elrt_ctx* ctx, int nx, int nz, const void* Aop, const double* 
             { ProfScope ps(ctx, "krylov"); k_givens<<<1, 1, 0, sm>>>(H, m + 1, cs, sn, gv, j, st); }
         }
         { ProfScope ps(ctx, "krylov"); k_solve_upper<<<1, 1, 0, sm>>>(H, m + 1, gv, yv, st); }
-        {
+        if constexpr (std::is_same<V, float>::value) {
+            if (pc) {  // x += M (sum y_i s_i W_i)
+                e = cuda_check(ctx, cudaMemsetAsync(pc_u, 0, (size_t)n * sizeof(float), sm), "zero correction");
+                if (e) return e;
+                {
+                    ProfScope ps(ctx, "krylov", 1, kv(m, n, sizeof(V)) + kv(2, n, sizeof(float)));
+                    k_update_x<V, float><<<gb, kThreads, 0, sm>>>(Vb, n, yv, arn4 ? arn->sc : nullptr, pc_u, st);
+                }
+                e = sweep_apply(ctx, nx, nz, f16 ? (const void*)A16 : Aop, f16 ? 2 : (int)sizeof(A), pc_u, pc_t,
+                                pc_order, pc_zw, pc_flags, nullptr, &st->j_done);
+                if (e) return e;
+                ProfScope ps(ctx, "krylov", 1, kv(1, n, sizeof(float)) + kv(2, n, sizeof(X)));
+                k_add_f<X><<<gb, kThreads, 0, sm>>>(x, pc_t, n);
+            }
+        }
+        if (!pc) {
             ProfScope ps(ctx, "krylov", 1, kv(m, n, sizeof(V)) + kv(2, n, sizeof(X)));
             k_update_x<V, X><<<gb, kThreads, 0, sm>>>(Vb, n, yv, arn4 ? arn->sc : nullptr, x, st);
         }
@@ -1642,6 +1693,9 @@ elrt_status gmres(elrt_ctx* ctx, int nx, int nz, const void* Aop, const double* 
         if (!e)
             e = cuda_check(ctx, cudaMemcpyAsync(hflag, ctx->d_flags + kGemvFlag, sizeof(int), cudaMemcpyDeviceToHost, sm),
                            "read flag");
+        if (!e && pc)
+            e = cuda_check(ctx, cudaMemcpyAsync(hflag + 1, pc_flags, sizeof(int), cudaMemcpyDeviceToHost, sm),
+                           "read sweep flag");
         return e;
     };
     // Graph path (ctx->graphs, no per-launch timing): a whole restart cycle -- restart residual,
@@ -1701,9 +1755,10 @@ elrt_status gmres(elrt_ctx* ctx, int nx, int nz, const void* Aop, const double* 
                 return s;
             }
             ctx->launches += gnodes[v];
-            if (*hflag) {
+            if (hflag[0] || hflag[1]) {
                 release();
-                return ctx_fail(ctx, ELRT_ETIMEOUT, "a copy wait of the streaming matvec timed out");
+                return ctx_fail(ctx, ELRT_ETIMEOUT, hflag[0] ? "a copy wait of the streaming matvec timed out"
+                                                             : "a wait of the sweep preconditioner timed out");
             }
             const double beta = hst->beta;
             rel = beta / bnorm;
@@ -1744,9 +1799,10 @@ elrt_status gmres(elrt_ctx* ctx, int nx, int nz, const void* Aop, const double* 
             return s;
         }
         prof_flush(ctx);
-        if (*hflag) {
+        if (hflag[0] || hflag[1]) {
             release();
-            return ctx_fail(ctx, ELRT_ETIMEOUT, "a copy wait of the streaming matvec timed out");
+            return ctx_fail(ctx, ELRT_ETIMEOUT, hflag[0] ? "a copy wait of the streaming matvec timed out"
+                                                         : "a wait of the sweep preconditioner timed out");
         }
         its += hst->j_done;
         ++cycles;

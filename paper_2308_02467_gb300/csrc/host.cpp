@@ -402,6 +402,14 @@ elrt_status elrt_set_graphs(elrt_ctx* ctx, int32_t on) {
     return ELRT_OK;
 }
 
+elrt_status elrt_set_precond(elrt_ctx* ctx, int32_t kind) {
+    if (!ctx) return ctx_fail(nullptr, ELRT_EINVAL, "elrt_set_precond: null context");
+    if (kind != ELRT_PRECOND_NONE && kind != ELRT_PRECOND_SWEEP)
+        return ctx_fail(ctx, ELRT_EINVAL, "elrt_set_precond: ELRT_PRECOND_NONE or ELRT_PRECOND_SWEEP");
+    ctx->precond = kind;
+    return ELRT_OK;
+}
+
 const char* elrt_status_str(elrt_status s) {
     switch (s) {
         case ELRT_OK: return "ok";
