@@ -166,6 +166,8 @@ def parse():
     ap.add_argument("--refine", type=int, default=1)
     ap.add_argument("--rtol", type=float, default=1e-8)
     ap.add_argument("--restart", type=int, default=12, help="GMRES restart length")
+    ap.add_argument("--precond", default="sweep", choices=["sweep", "none"],
+                    help="skeleton GMRES preconditioner: upwind block Gauss-Seidel sweeps, or none")
     ap.add_argument("--krylov-op", default="f16", choices=["f16", "f32"],
                     help="operator of the Arnoldi-step matvecs (restart residuals always use the FP32 operator)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -844,6 +846,7 @@ def run_ours(args, rank, world, local_rank):
     mode = {"tf32ir": E.LOCAL_TF32_IR, "fp32ir": E.LOCAL_FP32_IR, "fp64": E.LOCAL_FP64}[args.mode]
     ctx = E.Context(prob.p, prob.n_angles, prob.hg_g, E.ANG_FV0)
     ctx.elrt_set_krylov_op(E.KRYLOV_F16 if args.krylov_op == "f16" else E.KRYLOV_F32)
+    ctx.elrt_set_precond(E.PRECOND_SWEEP if args.precond == "sweep" else E.PRECOND_NONE)
     nx, nz, n = prob.nx, prob.nz, prob.n_elems
     xs, zs = E.elrt_node_coords(prob.p, prob.n_angles, nx, nz, prob.h)
     kap_h = torch.tensor(prob.kappa(xs, zs), dtype=torch.float64).pin_memory()
@@ -918,6 +921,21 @@ def run_ours(args, rank, world, local_rank):
     ctx.elrt_profile_enable(False)
     ms = max_over_ranks(ms, "cuda")
 
+    # ---- the skeleton solve alone, with and without the sweep preconditioner (same operators)
+    skel = {}
+    for name, kind in (("sweep", E.PRECOND_SWEEP), ("none", E.PRECOND_NONE)):
+        ctx.elrt_set_precond(kind)
+        ctx.elrt_solve_global(nx, nz, i2o, g, sk, rtol=args.rtol, max_iter=20000, restart=args.restart)  # warm
+        torch.cuda.synchronize()
+        e6, e7 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e6.record(stream)
+        for _ in range(3):
+            gs_ = ctx.elrt_solve_global(nx, nz, i2o, g, sk, rtol=args.rtol, max_iter=20000, restart=args.restart)
+        e7.record(stream)
+        torch.cuda.synchronize()
+        skel[name] = {"ms": e6.elapsed_time(e7) / 3, "iterations": gs_.iterations, "rel_residual": gs_.rel_residual}
+    ctx.elrt_set_precond(E.PRECOND_SWEEP if args.precond == "sweep" else E.PRECOND_NONE)
+
     # ---- end to end through the public API with host buffers
     barrier()
     torch.cuda.synchronize()
@@ -952,7 +970,7 @@ def run_ours(args, rank, world, local_rank):
                  + ("+f16" if args.krylov_op == "f16" and args.mode != "fp64" else ""), "data": "synthetic",
         "config": {"workload": workload_name(args.nx), "elements": n, "p": prob.p, "n_angles": prob.n_angles,
                    "local_mode": args.mode, "refine_steps": args.refine, "gmres_rtol": args.rtol, "gmres_restart": args.restart,
-                   "arnoldi_operator": args.krylov_op,
+                   "arnoldi_operator": args.krylov_op, "preconditioner": args.precond,
                    "operator_dtype": "f32", "parallelism": f"replicas x{world}",
                    "l2": "working set larger than L2 (in2out 822 MB, local workspace > 10 GB) on every step"},
         "breakdown_ms": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
@@ -960,6 +978,8 @@ def run_ours(args, rank, world, local_rank):
         "local_build": {"ms": ms_local, "elements_per_s": replicas_throughput(n, world, ms_local),
                         "what": "in2out/in2sol build alone: assembly + LU + refinement + restriction"},
         "gmres_iterations": gst.iterations, "gmres_rel_residual": gst.rel_residual,
+        "skeleton_solve": dict(skel, what="elrt_solve_global alone on the step's operators: upwind block "
+                                          "Gauss-Seidel sweep preconditioner against plain GMRES"),
         "local_max_rel_residual": lst.max_rel_residual, "local_flagged": lst.n_flagged,
         "roofline": roof,
         "kernels": kernels,
