@@ -62,6 +62,20 @@ bool make_map(CUtensorMap* m, const bf16* ptr, int64_t rows, int64_t cols, int b
     return r == CUDA_SUCCESS;
 }
 
+// an FP32 output matrix [rows][cols] (row pitch ld floats) for the output layer's tensor stores: box
+// 16 columns x 32 rows, no swizzle
+bool make_out_map(CUtensorMap* m, const float* ptr, int64_t rows, int64_t cols, int64_t ld) {
+    if (!ptr || ((uintptr_t)ptr & 15) || (ld * 4) % 16 || cols < 1) return false;
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+    cuuint32_t box[2] = {16, 32};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = g_encode(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)ptr, dims, strides, box, es,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
 // ------------------------------------------------------------------------------------------------
 // small kernels
 // ------------------------------------------------------------------------------------------------
@@ -364,14 +378,28 @@ elrt_status gemm(elrt_net* net, const bf16* A, const bf16* Bm, int M, int N, int
         return net_fail(net, ELRT_EINVAL, "tensor map encoding failed (alignment or stride)");
     const int tiles = ((M + tc::BM - 1) / tc::BM) * (wide ? (N + 255) / 256 : (N + 127) / 128) * std::max(1, ep.ksplit);
     dim3 grid(std::min(tiles, 152));
-    if (wide) {
+    // the output layer writes its tiles with tensor stores when both destinations allow the maps
+    CUtensorMap to = ta, to2 = ta;
+    const bool otma = mode == tc::EPI_OUTPUT && ep.split % 16 == 0 &&
+                      make_out_map(&to, ep.out_f, M, std::min(ep.split, N), ep.ld_out) &&
+                      (ep.split >= N || make_out_map(&to2, ep.out_f2, M, N - ep.split, ep.ld_out2));
+    if (otma && ep.split >= N) to2 = to;
+    if (wide && otma) {
+        const int smem = tc::GemmSmem<256, true>::TOTAL;
+        cudaFuncSetAttribute(tc::k_gemm_bf16<256, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        tc::k_gemm_bf16<256, true><<<grid, tc::kGemmThreads, smem, net->stream>>>(ta, tb, M, N, K, mode, ep, to, to2);
+    } else if (otma) {
+        const int smem = tc::GemmSmem<128, true>::TOTAL;
+        cudaFuncSetAttribute(tc::k_gemm_bf16<128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        tc::k_gemm_bf16<128, true><<<grid, tc::kGemmThreads, smem, net->stream>>>(ta, tb, M, N, K, mode, ep, to, to2);
+    } else if (wide) {
         const int smem = tc::GemmSmem<256>::TOTAL;
         cudaFuncSetAttribute(tc::k_gemm_bf16<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        tc::k_gemm_bf16<256><<<grid, tc::kGemmThreads, smem, net->stream>>>(ta, tb, M, N, K, mode, ep);
+        tc::k_gemm_bf16<256><<<grid, tc::kGemmThreads, smem, net->stream>>>(ta, tb, M, N, K, mode, ep, to, to2);
     } else {
         const int smem = tc::GemmSmem<128>::TOTAL;
         cudaFuncSetAttribute(tc::k_gemm_bf16<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-        tc::k_gemm_bf16<128><<<grid, tc::kGemmThreads, smem, net->stream>>>(ta, tb, M, N, K, mode, ep);
+        tc::k_gemm_bf16<128><<<grid, tc::kGemmThreads, smem, net->stream>>>(ta, tb, M, N, K, mode, ep, to, to2);
     }
     return net_cuda(net, cudaGetLastError(), "gemm launch");
 }

@@ -193,16 +193,33 @@ __device__ __forceinline__ float act_df(float z, int act) {
     return z > 0.f ? 1.f : expf(z);
 }
 
-template <int BN>
+// OUT_TMA: EPI_OUTPUT written by TMA tensor stores from a 32 x 16 FP32 staging buffer per epilogue
+// warp (the rows of one tile are elements whose outputs lie far apart, so row-wise stores from
+// the epilogue threads touch 32 rows per instruction)
+template <int BN, bool OUT_TMA = false>
 struct GemmSmem {
     static constexpr int STAGES = BN == 256 ? 4 : 6;
     static constexpr int A_BYTES = BM * BK * 2;
     static constexpr int B_BYTES = BN * BK * 2;
     static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
     static constexpr int PARAM_BYTES = 2 * 2 * BN * 4;  // per-tile column parameters (scale and shift, or bias), two tiles
-    static constexpr int TOTAL = STAGES * STAGE_BYTES + 1024 /*alignment*/ + 256 /*barriers*/ + PARAM_BYTES;
+    static constexpr int OUT_BOX = 32 * 16 * 4;          // one staged 32-row x 16-column FP32 box
+    static constexpr int OUT_BYTES = OUT_TMA ? 8 * OUT_BOX : 0;
+    static constexpr int TOTAL = STAGES * STAGE_BYTES + 1024 /*alignment*/ + 256 /*barriers*/ + PARAM_BYTES + OUT_BYTES;
     static constexpr int TMEM_COLS = 2 * BN;  // two accumulators: epilogue of one tile overlaps the next
 };
+static_assert(GemmSmem<256, true>::TOTAL <= 227 * 1024 && GemmSmem<128, true>::TOTAL <= 227 * 1024, "GEMM shared memory");
+
+// shared -> global tensor copy of a 2-D box (bulk group); coordinates non-negative
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int x, int y) {
+    asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(smem_u32(src)), "r"(x), "r"(y)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit_group() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 __device__ __forceinline__ void st_f32x16(float* dst, const float (&v)[16]) {
     float4* d = reinterpret_cast<float4*>(dst);
@@ -327,10 +344,8 @@ ep.out_bf_t[(size_t)(n0c + j) * ep.ld_t + m] = __float2bfloat16_rn(v[j]);
     }
 }
 
-// EPI_OUTPUT of 16 consecutive columns n0c .. n0c+15 of row m: y = acc * scale + shift into out_f
-// (columns below split) or out_f2; the split, a multiple of 16, never falls inside the group
-__device__ __forceinline__ void output16(const EpiArgs& ep, int m, int n0c, int N, float (&v)[16], const float* sc,
-                                         const float* sh) {
+// y = acc * scale + shift for 16 consecutive columns
+__device__ __forceinline__ void scale16(float (&v)[16], const float* sc, const float* sh) {
 #pragma unroll
     for (int j = 0; j < 16; j += 4) {
         const float4 s4 = *reinterpret_cast<const float4*>(sc + j);
@@ -340,6 +355,13 @@ __device__ __forceinline__ void output16(const EpiArgs& ep, int m, int n0c, int 
         v[j + 2] = fmaf(v[j + 2], s4.z, h4.z);
         v[j + 3] = fmaf(v[j + 3], s4.w, h4.w);
     }
+}
+
+// EPI_OUTPUT of 16 consecutive columns n0c .. n0c+15 of row m: y = acc * scale + shift into out_f
+// (columns below split) or out_f2; the split, a multiple of 16, never falls inside the group
+__device__ __forceinline__ void output16(const EpiArgs& ep, int m, int n0c, int N, float (&v)[16], const float* sc,
+                                         const float* sh) {
+    scale16(v, sc, sh);
     float* dst = n0c < ep.split ? ep.out_f + (size_t)m * ep.ld_out + n0c
                                 : ep.out_f2 + (size_t)m * ep.ld_out2 + (n0c - ep.split);
     if (n0c + 16 <= N) {
@@ -355,11 +377,13 @@ __device__ __forceinline__ void output16(const EpiArgs& ep, int m, int n0c, int 
 // dimension fastest, so concurrently running CTAs share the long operand's tile in L2).  The TMA producer streams k-blocks of
 // consecutive tiles through the ring without a break; the MMA issuer alternates between two TMEM
 // accumulators so the epilogue of one tile overlaps the MMAs of the next.
-template <int BN>
+// tmO / tmO2 (OUT_TMA only): out_f and out_f2 as 2-D FP32 tensors [M][split] and [M][N - split],
+// box 16 columns x 32 rows, no swizzle
+template <int BN, bool OUT_TMA = false>
 __global__ void __launch_bounds__(kGemmThreads, 1)
     k_gemm_bf16(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N, int K,
-                int mode, EpiArgs ep) {
-    using S = GemmSmem<BN>;
+                int mode, EpiArgs ep, const __grid_constant__ CUtensorMap tmO, const __grid_constant__ CUtensorMap tmO2) {
+    using S = GemmSmem<BN, OUT_TMA>;
     extern __shared__ __align__(1024) unsigned char gsm_raw[];
     unsigned char* base = (unsigned char*)(((uintptr_t)gsm_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* As = base;
@@ -371,6 +395,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     uint32_t* tmem_slot = (uint32_t*)(acc_empty + 2);
     volatile int* abort = (volatile int*)(tmem_slot + 1);
     float* prm = (float*)(base + S::STAGES * S::STAGE_BYTES + 256);  // [2 tiles][scale BN | shift BN]
+    float* ostage = (float*)((unsigned char*)prm + S::PARAM_BYTES);    // OUT_TMA: [8 warps][32 x 16]
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nkb = (K + BK - 1) / BK;
@@ -542,6 +567,32 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                         if (i + D < NCH && n0 + c0 + 16 * D < N) load_targets16(ep, m, n0 + c0 + 16 * D, N, tg[i % D]);
                     }
                 }
+            } else if (OUT_TMA && mode == EPI_OUTPUT) {
+                // the warp's 32 rows x 16 columns into its staging box, then one tensor store (rows
+                // beyond M and columns beyond N are clipped by the copy engine)
+                float* box = ostage + (warp - 2) * 512;
+#pragma unroll 1
+                for (int i = 0; i < NCH; ++i) {
+                    const int c0 = h * HB + 16 * i;
+                    const int n0c = n0 + c0;
+                    if (n0c >= N) break;  // warp-uniform
+                    float v[16];
+                    tmem_ld16(tb + (uint32_t)c0, v);
+                    scale16(v, sp + c0, sp + BN + c0);
+                    if (lane == 0) bulk_wait_read_all();  // the previous store has read the box
+                    __syncwarp();
+                    float4* row = reinterpret_cast<float4*>(box + lane * 16);
+#pragma unroll
+                    for (int q4 = 0; q4 < 4; ++q4)
+                        row[q4] = make_float4(v[4 * q4], v[4 * q4 + 1], v[4 * q4 + 2], v[4 * q4 + 3]);
+                    fence_proxy_async();  // generic writes, read next by the tensor store (async proxy)
+                    __syncwarp();
+                    if (lane == 0 && m0 + q * 32 < M) {  // (a box wholly below the last row is not stored)
+                        if (n0c < ep.split) tma_store_2d(&tmO, box, n0c, m0 + q * 32);
+                        else tma_store_2d(&tmO2, box, n0c - ep.split, m0 + q * 32);
+                        bulk_commit_group();
+                    }
+                }
             } else {
 #pragma unroll 1
                 for (int i = 0; i < NCH; ++i) {
@@ -565,6 +616,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             for (int off = 16; off > 0; off >>= 1) lsum += __shfl_down_sync(0xffffffffu, lsum, off);
             if (lane == 0) atomicAdd(ep.loss_acc, lsum);
         }
+        if (OUT_TMA && lane == 0) bulk_wait_all();  // every store of this warp complete before exit
     }
     tc_fence_before();
     __syncthreads();
