@@ -115,7 +115,7 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_sweep(SweepArgs a, const AT* 
     __shared__ int stop, stop_copy;  // a dependency wait / the copy wait gave up
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t total = 4 * a.E;
-    const int rows_w = (nin + kSwWarps - 1) / kSwWarps;  // rows of a warp (at most 44)
+    const int rows_w = (nin + kSwWarps - 1) / kSwWarps;  // rows of a warp (at most 44: three batches of 16)
     if (threadIdx.x == 0) {
         for (int i = 0; i < NS; ++i) tc::mbar_init(&bar[i], 1);
         tc::fence_barrier_init();
@@ -144,6 +144,15 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_sweep(SweepArgs a, const AT* 
         const int e = element_of(it);
         const int ix = e % a.nx, iz = e / a.nx;
         const int st = NS ? k % NS : 0;
+        // this lane's right-hand-side values (it writes rows r0 + b + lane / 2 of each batch), loaded
+        // now so that their latency passes while the item waits for its dependencies
+        const int r0 = warp * rows_w;
+        float uv[3];
+#pragma unroll
+        for (int bb = 0; bb < 3; ++bb) {
+            const int r = r0 + 16 * bb + (lane >> 1);
+            uv[bb] = (16 * bb < rows_w && 16 * bb + (lane >> 1) < rows_w && r < nin) ? __ldg(a.u + (int64_t)e * nin + r) : 0.f;
+        }
         // the element's operator block has landed (bounded wait)
         if (NS && threadIdx.x == 0) {
             const long long t0 = clock64();
@@ -206,7 +215,7 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_sweep(SweepArgs a, const AT* 
             const int pc = lane + 32 * q;
             xv[q] = pc < npair ? *reinterpret_cast<const float2*>(xin + 2 * pc) : make_float2(0.f, 0.f);
         }
-        const int r0 = warp * rows_w;
+#pragma unroll 1
         for (int b = 0; b < rows_w; b += 16) {
             float v[16];
 #pragma unroll
@@ -229,7 +238,7 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_sweep(SweepArgs a, const AT* 
             const int r = r0 + b + (lane >> 1);
             if ((lane & 1) == 0 && b + (lane >> 1) < rows_w && r < nin) {
                 const int64_t i = (int64_t)e * nin + r;
-                const float val = __ldg(a.u + i) + sum;
+                const float val = (b == 0 ? uv[0] : b == 16 ? uv[1] : uv[2]) + sum;
                 st_verval(a.zw + i, val, c + 1);
                 if (c == 3) a.z[i] = val;
             }
@@ -314,7 +323,7 @@ elrt_status sweep_apply(elrt_ctx* ctx, int nx, int nz, const void* A, int a_byte
                         const int* order, void* zw, int* flags, const int* done, const int* nsteps) {
     const Tab& t = ctx->tab;
     const int64_t E = (int64_t)nx * nz;
-    if (t.nin % 4 != 0 || t.nin > kSwMaxIn || E > (1LL << 28) || (a_bytes != 2 && a_bytes != 4) ||
+    if (t.nin % 8 != 0 || t.nin > kSwMaxIn || E > (1LL << 28) || (a_bytes != 2 && a_bytes != 4) ||
         ((uintptr_t)A & 15) != 0)
         return ctx_fail(ctx, ELRT_EINVAL, "sweep preconditioner: unsupported element size or alignment");
     int nsm = 0;
