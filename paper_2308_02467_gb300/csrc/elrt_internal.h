@@ -126,7 +126,8 @@ elrt_status global_recover_rows(elrt_ctx* ctx, int nx, int nz, int rows, const v
                                 const double* inflow, const double* self, double* out);
 
 // ---- sweep preconditioner of the skeleton GMRES (sweep.cu)
-void sweep_orders(int nx, int nz, int* out);
+int sweep_parts(const Tab& t);
+void sweep_orders(int nx, int nz, int parts, int* out);
 elrt_status sweep_apply(elrt_ctx* ctx, int nx, int nz, const void* A, int a_bytes, const float* u, float* z,
                         const int* order, void* zw, int* flags, const int* done, const int* nsteps);
 

@@ -1485,8 +1485,9 @@ elrt_status gmres(elrt_ctx* ctx, int nx, int nz, const void* Aop, const double* 
     // sweeps' versioned outflow [n] (8 bytes each), the item order [4 E] and two flags
     const int64_t E = (int64_t)nx * nz;
     const bool pc = std::is_same<V, float>::value && ctx->precond == ELRT_PRECOND_SWEEP;
+    const int pc_parts = pc ? sweep_parts(t) : 1;
     const size_t pc_bytes =
-        pc ? (((size_t)4 * n * sizeof(float) + (size_t)4 * E * sizeof(int) + 64 + 255) & ~(size_t)255) : 0;
+        pc ? (((size_t)4 * n * sizeof(float) + (size_t)4 * E * pc_parts * sizeof(int) + 64 + 255) & ~(size_t)255) : 0;
     elrt_status s = ensure_ws(ctx, &ctx->gm, &ctx->gm_bytes, vb_bytes + xbytes + 256 + small + sizeof(GmState) + 512 + pc_bytes);
     if (s) return s;
     V* Vb = (V*)ctx->gm;
@@ -1506,7 +1507,7 @@ elrt_status gmres(elrt_ctx* ctx, int nx, int nz, const void* Aop, const double* 
     float* pc_u = pc ? pc_t + n : nullptr;                                                 // sum y_i s_i W_i
     void* pc_zw = pc ? (void*)(pc_u + n) : nullptr;                                       // 8 n bytes
     int* pc_order = pc ? (int*)(pc_u + 3 * n) : nullptr;
-    int* pc_flags = pc ? pc_order + 4 * E : nullptr;
+    int* pc_flags = pc ? pc_order + 4 * E * pc_parts : nullptr;
     // three-launch Arnoldi step: FP32 basis, restarts up to kArnMaxV - 1 and the streaming matvec
     const bool arn4 = std::is_same<V, float>::value && m + 1 <= kArnMaxV && gemv_streams(t, Aop, (int)sizeof(A));
     cudaStream_t sm = ctx->stream;
@@ -1517,8 +1518,8 @@ elrt_status gmres(elrt_ctx* ctx, int nx, int nz, const void* Aop, const double* 
     const int rows = t.nin;
 
     if (pc) {
-        std::vector<int> ord((size_t)4 * E);
-        sweep_orders(nx, nz, ord.data());
+        std::vector<int> ord((size_t)4 * E * pc_parts);
+        sweep_orders(nx, nz, pc_parts, ord.data());
         s = cuda_check(ctx, cudaMemcpyAsync(pc_order, ord.data(), ord.size() * sizeof(int), cudaMemcpyHostToDevice, sm),
                        "sweep orders");
         if (!s) s = cuda_check(ctx, cudaStreamSynchronize(sm), "sweep orders");  // (pageable source)

@@ -8,10 +8,12 @@
 // previous sweep's (zero in the first).
 //
 // One persistent cooperative launch (one CTA of 512 threads per SM) runs all four sweeps.  The
-// work items (sweep, element) are ordered by the step at which their dependencies allow them to
-// start (1 + the latest start among them; a topological order, built on the host), so the four
-// sweeps overlap wherever the dependencies allow, and are dealt to the CTAs round robin, so every
-// CTA takes its items in that order.  Instead of a grid barrier per wavefront, every outflow
+// work items (sweep, element, half of its rows) are ordered by the step at which their
+// dependencies allow them to start (1 + the latest start among them; a topological order, built on
+// the host), so the four sweeps overlap wherever the dependencies allow, and are dealt to the CTAs
+// round robin, so every CTA takes its items in that order.  (Dealing them from a counter to
+// whichever CTA had a free stage was slower: a CTA then held the next items of the order before
+// they were ready while ready ones waited behind them.)  Instead of a grid barrier per wavefront, every outflow
 // value is stored with the sweep that wrote it, one 64-bit word (value, sweep + 1; single-copy
 // atomic), and an item polls exactly the words it needs (bounded): the faces of its upwind
 // neighbours until this sweep wrote them, those of its downwind neighbours until the previous
@@ -42,6 +44,23 @@ constexpr long long kSwSpin = 1000000000LL;   // ~0.5 s of clock64 per wait
 
 // Sixteen per-lane partial sums (v[k]: row k) reduced across the warp in five butterfly rounds of
 // independent shuffles (16 in all): afterwards lanes 2r and 2r + 1 hold the sum of row r.
+// Eight per-lane partial sums (v[k]: row k) reduced across the warp in five butterfly rounds (9
+// shuffles): afterwards the lanes 4r .. 4r + 3 hold the sum of row r.
+__device__ __forceinline__ float warp_sum8(float (&v)[8], int lane) {
+#pragma unroll
+    for (int h = 4, m = 16; h >= 1; h >>= 1, m >>= 1) {
+        const bool up = (lane & m) != 0;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const float send = up ? v[i] : v[i + h];
+            const float keep = up ? v[i + h] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, m);
+        }
+    }
+    float t = v[0] + __shfl_xor_sync(0xffffffffu, v[0], 2);
+    return t + __shfl_xor_sync(0xffffffffu, t, 1);
+}
+
 __device__ __forceinline__ float warp_sum16(float (&v)[16], int lane) {
 #pragma unroll
     for (int h = 8, m = 16; h >= 1; h >>= 1, m >>= 1) {
@@ -91,7 +110,8 @@ struct SweepArgs {
     int nx, nz, nin, nface;
     int64_t E;
     int stages;            // operator blocks staged in shared memory: 2, 1 or 0 (read from global)
-    const int* order;      // [4 E]: the work items c E + e in their global order
+    int parts, prows;      // an element's rows in `parts` work items of prows rows (the last may be shorter)
+    const int* order;      // [4 E parts]: the work items (c E + e) parts + part in their global order
     const float* u;        // [E][nin]
     float* z;              // [E][nin] result (written by the last sweep)
     VerVal* zw;            // [E][nin] versioned outflow, zero on entry
@@ -107,51 +127,56 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_sweep(SweepArgs a, const AT* 
     if ((a.done && *a.done) || (a.nsteps && *a.nsteps == 0)) return;
     extern __shared__ __align__(128) unsigned char sw_smem[];
     const int nin = a.nin, nf = a.nface, npair = nin / 2;
-    const int blk_bytes = nin * nin * (int)sizeof(AT);
+    const int blk_bytes = a.prows * nin * (int)sizeof(AT);  // a stage: one item's rows
     const int NS = a.stages;
     AT* stage0 = reinterpret_cast<AT*>(sw_smem);
     float* xin = reinterpret_cast<float*>(sw_smem + (size_t)NS * blk_bytes);
     uint64_t* bar = reinterpret_cast<uint64_t*>(xin + ((nin + 3) & ~3));  // [2]
     __shared__ int stop, stop_copy;  // a dependency wait / the copy wait gave up
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t total = 4 * a.E;
-    const int rows_w = (nin + kSwWarps - 1) / kSwWarps;  // rows of a warp (at most 44: three batches of 16)
+    const int total = (int)(4 * a.E * a.parts);
+    const int rows_w = (a.prows + kSwWarps - 1) / kSwWarps;  // rows of a warp (at most 44)
     if (threadIdx.x == 0) {
         for (int i = 0; i < NS; ++i) tc::mbar_init(&bar[i], 1);
         tc::fence_barrier_init();
         stop = stop_copy = 0;
     }
     __syncthreads();
-    auto element_of = [&](int64_t it) { return (int)(a.order[it] % a.E); };
-    auto issue = [&](int64_t it, int st) {  // the operator block of item it into stage st
-        const int e = element_of(it);
-        const unsigned char* src = reinterpret_cast<const unsigned char*>(A + (int64_t)e * nin * nin);
+    auto rows_of = [&](int part) { return min(a.prows, nin - part * a.prows); };
+    auto issue = [&](int64_t it, int st) {  // the operator rows of item it into stage st
+        const int code = a.order[it], part = code % a.parts;
+        const int e = (int)((code / a.parts) % a.E);
+        const int bytes = rows_of(part) * nin * (int)sizeof(AT);
+        const unsigned char* src =
+            reinterpret_cast<const unsigned char*>(A + (int64_t)e * nin * nin + (int64_t)part * a.prows * nin);
         unsigned char* dst = reinterpret_cast<unsigned char*>(stage0) + (size_t)st * blk_bytes;
-        tc::mbar_expect_tx(&bar[st], (uint32_t)blk_bytes);
-        for (int off = 0; off < blk_bytes; off += kSwChunk)
-            tc::bulk_load(dst + off, src + off, (uint32_t)min(kSwChunk, blk_bytes - off), &bar[st]);
+        tc::mbar_expect_tx(&bar[st], (uint32_t)bytes);
+        for (int off = 0; off < bytes; off += kSwChunk)
+            tc::bulk_load(dst + off, src + off, (uint32_t)min(kSwChunk, bytes - off), &bar[st]);
     };
     if (threadIdx.x == 0)
         for (int s = 0; s < NS; ++s) {
-            const int64_t it = blockIdx.x + (int64_t)s * gridDim.x;
+            const int it = blockIdx.x + s * (int)gridDim.x;
             if (it < total) issue(it, s);
         }
     int k = 0;
     int issued = (int)std::min<int64_t>((int64_t)NS, (total - blockIdx.x + gridDim.x - 1) / gridDim.x);
     bool alive = true;
-    for (int64_t it = blockIdx.x; it < total && alive; it += gridDim.x, ++k) {
-        const int c = a.order[it] / (int)a.E;
-        const int e = element_of(it);
+    for (int it = blockIdx.x; it < total && alive; it += gridDim.x, ++k) {
+        const int code = a.order[it], part = code % a.parts;
+        const int c = code / (a.parts * (int)a.E);
+        const int e = (int)((code / a.parts) % a.E);
         const int ix = e % a.nx, iz = e / a.nx;
         const int st = NS ? k % NS : 0;
-        // this lane's right-hand-side values (it writes rows r0 + b + lane / 2 of each batch), loaded
-        // now so that their latency passes while the item waits for its dependencies
+        const int prow0 = part * a.prows, nrows = rows_of(part);  // this item's rows of the element
+        // this lane's right-hand-side values (it writes row r0 + b + lane / 4 of each batch of 8),
+        // loaded now so that their latency passes while the item waits for its dependencies
         const int r0 = warp * rows_w;
-        float uv[3];
+        float uv[6];
 #pragma unroll
-        for (int bb = 0; bb < 3; ++bb) {
-            const int r = r0 + 16 * bb + (lane >> 1);
-            uv[bb] = (16 * bb < rows_w && 16 * bb + (lane >> 1) < rows_w && r < nin) ? __ldg(a.u + (int64_t)e * nin + r) : 0.f;
+        for (int bb = 0; bb < 6; ++bb) {
+            const int rl = r0 + 8 * bb + (lane >> 2);
+            uv[bb] = (8 * bb + (lane >> 2) < rows_w && rl < nrows) ? __ldg(a.u + (int64_t)e * nin + prow0 + rl) : 0.f;
         }
         // the element's operator block has landed (bounded wait)
         if (NS && threadIdx.x == 0) {
@@ -168,7 +193,7 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_sweep(SweepArgs a, const AT* 
         // written it; own rows (the next nin threads): once the previous sweep has written them
         const int we = wave_of(c, ix, iz, a.nx, a.nz);
         bool ok = true;
-        for (int i = threadIdx.x; i < 2 * nin && ok; i += kSwThreads) {
+        for (int i = threadIdx.x; i < nin + nrows && ok; i += kSwThreads) {
             const VerVal* w = nullptr;
             int need = c;
             if (i < nin) {
@@ -181,7 +206,7 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_sweep(SweepArgs a, const AT* 
                 w = a.zw + (int64_t)(jx + a.nx * jz) * nin + ((F + 2) & 3) * nf + off;
                 if (wave_of(c, jx, jz, a.nx, a.nz) < we) need = c + 1;
             } else {
-                w = a.zw + (int64_t)e * nin + (i - nin);
+                w = a.zw + (int64_t)e * nin + prow0 + (i - nin);
             }
             VerVal x = ld_verval(w);
             if (x.ver < need) {
@@ -206,7 +231,7 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_sweep(SweepArgs a, const AT* 
             alive = false;
             break;
         }
-        const AT* Ab = NS ? stage0 + (size_t)st * nin * nin : A + (int64_t)e * nin * nin;
+        const AT* Ab = NS ? stage0 + (size_t)st * a.prows * nin : A + (int64_t)e * nin * nin + (int64_t)prow0 * nin;
         // this warp's rows in batches of 16: per-lane partial sums over the lane's column pairs,
         // then one transposed reduction per batch
         float2 xv[NP];
@@ -216,36 +241,40 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_sweep(SweepArgs a, const AT* 
             xv[q] = pc < npair ? *reinterpret_cast<const float2*>(xin + 2 * pc) : make_float2(0.f, 0.f);
         }
 #pragma unroll 1
-        for (int b = 0; b < rows_w; b += 16) {
-            float v[16];
+        for (int b = 0; b < rows_w; b += 8) {
+            float v[8];
 #pragma unroll
-            for (int k = 0; k < 16; ++k) {
-                v[k] = 0.f;
-                const int r = r0 + b + k;
-                if (b + k < rows_w && r < nin) {
+            for (int kk = 0; kk < 8; ++kk) {
+                v[kk] = 0.f;
+                const int rl = r0 + b + kk;  // row within the item
+                if (b + kk < rows_w && rl < nrows) {
 #pragma unroll
                     for (int q = 0; q < NP; ++q) {
                         const int pc = lane + 32 * q;
                         if (pc < npair) {
-                            const float2 av = ld_pair(Ab, r * nin + 2 * pc);
-                            v[k] = fmaf(av.x, xv[q].x, v[k]);
-                            v[k] = fmaf(av.y, xv[q].y, v[k]);
+                            const float2 av = ld_pair(Ab, rl * nin + 2 * pc);
+                            v[kk] = fmaf(av.x, xv[q].x, v[kk]);
+                            v[kk] = fmaf(av.y, xv[q].y, v[kk]);
                         }
                     }
                 }
             }
-            const float sum = warp_sum16(v, lane);
-            const int r = r0 + b + (lane >> 1);
-            if ((lane & 1) == 0 && b + (lane >> 1) < rows_w && r < nin) {
-                const int64_t i = (int64_t)e * nin + r;
-                const float val = (b == 0 ? uv[0] : b == 16 ? uv[1] : uv[2]) + sum;
+            const float sum = warp_sum8(v, lane);
+            const int rl = r0 + b + (lane >> 2);
+            if ((lane & 3) == 0 && b + (lane >> 2) < rows_w && rl < nrows) {
+                const int64_t i = (int64_t)e * nin + prow0 + rl;
+                float uu = uv[0];
+#pragma unroll
+                for (int bb = 1; bb < 6; ++bb)
+                    if (b == 8 * bb) uu = uv[bb];
+                const float val = uu + sum;
                 st_verval(a.zw + i, val, c + 1);
                 if (c == 3) a.z[i] = val;
             }
         }
         __syncthreads();  // the stage is free
         if (threadIdx.x == 0) {
-            const int64_t nxt = it + (int64_t)NS * gridDim.x;
+            const int nxt = it + NS * (int)gridDim.x;
             if (NS && nxt < total) {
                 issue(nxt, st);
                 ++issued;
@@ -264,7 +293,7 @@ __global__ void __launch_bounds__(kSwThreads, 1) k_sweep(SweepArgs a, const AT* 
 
 template <typename AT, int NP>
 cudaError_t launch_sweep(cudaLaunchConfig_t cfg, const SweepArgs& a, const void* A) {
-    const size_t smem = (size_t)a.stages * a.nin * a.nin * sizeof(AT) + (((a.nin + 3) & ~3) + 32) * sizeof(float);
+    const size_t smem = (size_t)a.stages * a.prows * a.nin * sizeof(AT) + (((a.nin + 3) & ~3) + 32) * sizeof(float);
     static size_t attr = 0;
     if (smem > attr) {
         cudaError_t e = cudaFuncSetAttribute(k_sweep<AT, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -277,11 +306,16 @@ cudaError_t launch_sweep(cudaLaunchConfig_t cfg, const SweepArgs& a, const void*
 
 }  // namespace
 
-// Global order of the work items c E + e (sweep c from the bottom-left, bottom-right, top-right,
-// top-left corner): by the step t at which an item can start, t = 1 + the largest t among the
-// items it waits for (its upwind neighbours in sweep c, its downwind neighbours and itself in
-// sweep c - 1), then by sweep and by element.  Every item comes after everything it waits for.
-void sweep_orders(int nx, int nz, int* out) {
+// Work items per element: its rows in two halves once an element has 128 outflow DOFs or more,
+// so that the latency of an element's step on the chain is that of half its rows.
+int sweep_parts(const Tab& t) { return t.nin >= 128 ? 2 : 1; }
+
+// Global order of the work items (c E + e) parts + part (sweep c from the bottom-left,
+// bottom-right, top-right, top-left corner): by the step t at which an element's sweep can start,
+// t = 1 + the largest t among the elements' sweeps it waits for (its upwind neighbours in sweep c,
+// its downwind neighbours and itself in sweep c - 1), then by sweep, element and part.  Every item
+// comes after everything it waits for.
+void sweep_orders(int nx, int nz, int parts, int* out) {
     const int E = nx * nz;
     auto wave = [&](int c, int ix, int iz) {
         const int dx = (c == 0 || c == 3) ? ix : nx - 1 - ix;
@@ -312,25 +346,27 @@ void sweep_orders(int nx, int nz, int* out) {
     std::vector<int> items((size_t)4 * E);
     for (int i = 0; i < 4 * E; ++i) items[i] = i;
     std::stable_sort(items.begin(), items.end(), [&](int p, int q) { return t[p] < t[q]; });
-    std::copy(items.begin(), items.end(), out);
+    for (size_t i = 0; i < items.size(); ++i)
+        for (int part = 0; part < parts; ++part) out[i * parts + part] = items[i] * parts + part;
 }
 
 // z = M u on the stream, with the operator A (FP16 or FP32, [E][nin][nin], 16-byte aligned);
-// order: device [4 E] from sweep_orders; zw: device scratch of 8 E n_in bytes; flags: device ints (err,
+// order: device [4 E parts] from sweep_orders with parts = sweep_parts(tab); zw: device scratch of 8 E n_in bytes; flags: device ints (err,
 // abort), cleared here (err stays set after a timed-out wait); z is zeroed first, so a skipped
 // application leaves 0.
 elrt_status sweep_apply(elrt_ctx* ctx, int nx, int nz, const void* A, int a_bytes, const float* u, float* z,
                         const int* order, void* zw, int* flags, const int* done, const int* nsteps) {
     const Tab& t = ctx->tab;
     const int64_t E = (int64_t)nx * nz;
-    if (t.nin % 8 != 0 || t.nin > kSwMaxIn || E > (1LL << 28) || (a_bytes != 2 && a_bytes != 4) ||
+    if (t.nin % 8 != 0 || t.nin > kSwMaxIn || E > (1LL << 27) || (a_bytes != 2 && a_bytes != 4) ||
         ((uintptr_t)A & 15) != 0)
         return ctx_fail(ctx, ELRT_EINVAL, "sweep preconditioner: unsupported element size or alignment");
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device);
-    const size_t blk = (size_t)t.nin * t.nin * a_bytes, extra = (size_t)(t.nin + 36) * sizeof(float);
+    const int parts = sweep_parts(t), prows = (t.nin + parts - 1) / parts;
+    const size_t blk = (size_t)prows * t.nin * a_bytes, extra = (size_t)(t.nin + 36) * sizeof(float);
     const int stages = 2 * blk + extra <= (size_t)kSwSmemMax ? 2 : (blk + extra <= (size_t)kSwSmemMax ? 1 : 0);
-    SweepArgs a{nx, nz, t.nin, t.nface, E, stages, order, u, z, (VerVal*)zw, flags, done, nsteps, flags + 1};
+    SweepArgs a{nx, nz, t.nin, t.nface, E, stages, parts, prows, order, u, z, (VerVal*)zw, flags, done, nsteps, flags + 1};
     const double nop = (double)E * t.nin * t.nin;
     ProfScope ps(ctx, "sweep", 1, 4.0 * (nop * a_bytes + 12.0 * E * t.nin), 4.0 * 2.0 * nop);
     elrt_status s = cuda_check(ctx, cudaMemsetAsync(z, 0, (size_t)E * t.nin * sizeof(float), ctx->stream), "sweep z");
@@ -338,7 +374,7 @@ elrt_status sweep_apply(elrt_ctx* ctx, int nx, int nz, const void* A, int a_byte
     if (!s) s = cuda_check(ctx, cudaMemsetAsync(flags, 0, 2 * sizeof(int), ctx->stream), "sweep flags");
     if (s) return s;
     cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3((unsigned)std::max<int64_t>(1, std::min<int64_t>(4 * E, nsm)));  // one CTA per SM
+    cfg.gridDim = dim3((unsigned)std::max<int64_t>(1, std::min<int64_t>(4 * E * parts, nsm)));  // one CTA per SM
     cfg.blockDim = dim3(kSwThreads);
     cfg.stream = ctx->stream;
     cudaLaunchAttribute attr{};
@@ -364,16 +400,17 @@ extern "C" elrt_status elrt_apply_precond(elrt_ctx* ctx, int32_t nx, int32_t nz,
         return ctx_fail(ctx, ELRT_EINVAL, "elrt_apply_precond: bad arguments (FP32 in2out, distinct r and z)");
     ctx->last_error.clear();
     const int64_t E = (int64_t)nx * nz;
-    // scratch: the versioned outflow [E][n_in], the item order [4 E] and two flags
+    // scratch: the versioned outflow [E][n_in], the item order [4 E parts] and two flags
+    const int parts = sweep_parts(ctx->tab);
     const size_t wbytes = (size_t)E * ctx->tab.nin * sizeof(VerVal);
-    const size_t need = wbytes + (size_t)4 * E * sizeof(int) + 64;
+    const size_t need = wbytes + (size_t)4 * E * parts * sizeof(int) + 64;
     elrt_status s = ensure_ws(ctx, &ctx->vec, &ctx->vec_bytes, need);
     if (s) return s;
     void* zw = ctx->vec;
     int* order = (int*)((unsigned char*)ctx->vec + wbytes);
-    int* flags = order + 4 * E;
-    std::vector<int> ord((size_t)4 * E);
-    sweep_orders(nx, nz, ord.data());
+    int* flags = order + 4 * E * parts;
+    std::vector<int> ord((size_t)4 * E * parts);
+    sweep_orders(nx, nz, parts, ord.data());
     s = cuda_check(ctx, cudaMemcpyAsync(order, ord.data(), ord.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream),
                    "sweep orders");
     if (!s) s = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "sweep orders");
