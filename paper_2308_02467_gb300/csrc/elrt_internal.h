@@ -52,6 +52,7 @@ struct elrt_ctx {
     Tab tab;
     cudaStream_t stream;
     int device;
+    int sms = 152;  // streaming multiprocessors of the device (persistent grids are sized on it)
     std::string last_error;
     // workspace (grown on demand)
     void* ws = nullptr;

@@ -1371,7 +1371,7 @@ elrt_status launch_gemv_tc(elrt_ctx* ctx, const CUtensorMap& map, int nx, int nz
     ProfScope ps(ctx, "gemv", 1, bytes, 2.0 * (double)E * t.nin * t.nin);
     cudaError_t ce = cudaFuncSetAttribute(k_gemv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
     if (ce != cudaSuccess) return cuda_check(ctx, ce, "smem attribute");
-    const unsigned grid = (unsigned)std::min<int64_t>(T, 152);
+    const unsigned grid = (unsigned)std::min<int64_t>(T, ctx->sms);
     k_gemv_tc<<<grid, kTcThreads, kTcSmem, ctx->stream>>>(map, nx, nz, t.nin, t.nface, x, y, st,
                                                          ctx->d_flags + kGemvFlag, fz);
     return cuda_check(ctx, cudaGetLastError(), "tensor-core matvec launch");
@@ -1417,7 +1417,7 @@ elrt_status launch_gemv(elrt_ctx* ctx, int nx, int nz, int rows, const void* Aop
         if (gemv_streams(t, Aop, es)) {
             const size_t smem = (size_t)kGvStages * kGvStageBytes + 2 * (size_t)t.nin * sizeof(ff) +
                                 2 * (size_t)rows * sizeof(V);
-            const unsigned grid = (unsigned)std::min<int64_t>(E, 2 * 152);
+            const unsigned grid = (unsigned)std::min<int64_t>(E, 2 * ctx->sms);
             const A* Ap = (const A*)Aop;
             cudaError_t ce;
             if constexpr (sizeof(A) == 2) {
@@ -1541,7 +1541,7 @@ elrt_status gmres(elrt_ctx* ctx, int nx, int nz, const void* Aop, const double* 
             if (s) return s;
             A16 = (const __half*)ctx->gm16;
             ProfScope ps(ctx, "gemv", 1, 6.0 * nop);
-            k_op_to_f16<<<4 * 152, kThreads, 0, sm>>>((const float4*)Aop, (uint2*)ctx->gm16, nop / 4,
+            k_op_to_f16<<<4 * ctx->sms, kThreads, 0, sm>>>((const float4*)Aop, (uint2*)ctx->gm16, nop / 4,
                                                       ctx->d_flags + kF16Flag);
             use16 = true;
         }

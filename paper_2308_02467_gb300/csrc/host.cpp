@@ -354,6 +354,7 @@ elrt_status elrt_create(elrt_ctx** out, const elrt_disc* disc, void* stream) {
     }
     c->stream = (cudaStream_t)stream;
     cudaError_t e = cudaGetDevice(&c->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
     if (e == cudaSuccess) e = cudaMalloc(&c->d_flags, 256 * sizeof(int));
     if (e == cudaSuccess) e = cudaMallocHost(&c->h_pinned, 4096);
     if (e != cudaSuccess) {

@@ -26,6 +26,7 @@
 // kernels.
 #include <math.h>
 #include <stdio.h>
+#include <stdlib.h>
 
 #include <algorithm>
 #include <mutex>
@@ -52,7 +53,6 @@ __device__ __forceinline__ float tf32_hi(float a) { return __uint_as_float(__flo
 
 constexpr int TS = NBP + 1;
 constexpr int TI = NBP + 4;                                        // factor row stride: 16-byte aligned rows
-constexpr int PTILE = 256;                                         // rows or columns per tile
 
 // Factor layout per element and panel (the side buffer Tinv): [panel][4][64][64]:
 //   [0] U11 (upper, row-major), [1] L11^T (the strictly lower part of the unit-lower L11, transposed),
@@ -191,9 +191,14 @@ __device__ __forceinline__ void tri_solve(float (&a)[NBP], const float* __restri
 // buffers, copies of the next item in flight, measured 23% slower: 8 warps per SM were too few to
 // hide the shared-memory latency of the substitutions.)
 constexpr int RS = NBP + 4;                        // staging row stride: 16-byte aligned rows
-constexpr int RC_BUF = PTILE * RS + (NBP + 1) * RS;  // floats per buffer: staging + factor + 1/diag
-constexpr int RC_SMEM = RC_BUF * (int)sizeof(float);  // one buffer: two CTAs per SM overlap each other's copies
-static_assert(PTILE * RS >= NBP * PTILE, "the staging area holds a 64 x PTILE column block");
+// one thread per row or column of a tile, PTILE of them; one staging buffer per block
+template <int PTILE>
+struct RcCfg {
+    static constexpr int BUF = PTILE * RS + (NBP + 1) * RS;  // floats: staging + factor + 1/diag
+    static constexpr int SMEM = BUF * (int)sizeof(float);
+    static constexpr int PER_SM = PTILE == 256 ? 2 : 4;      // resident blocks per SM
+    static_assert(PTILE * RS >= NBP * PTILE, "the staging area holds a 64 x PTILE column block");
+};
 
 __device__ __forceinline__ void cp_async16(float* smem, const float* gmem, bool valid) {
     // src-size 0 fills the 16 bytes with zeros and reads nothing
@@ -205,8 +210,8 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 
 // KIND: 0 = row tiles (factorisation), 1 = column tiles of the factorisation / forward sweep,
 // 2 = column tiles of the backward sweep; one unrolled solve per instantiation
-template <int KIND>
-__global__ void __launch_bounds__(256, 2) k_rowcol(int nu, int64_t ld, int64_t estride, float* __restrict__ Mall, int J,
+template <int KIND, int PTILE>
+__global__ void __launch_bounds__(PTILE, RcCfg<PTILE>::PER_SM) k_rowcol(int nu, int64_t ld, int64_t estride, float* __restrict__ Mall, int J,
                                                    int jb, const float* __restrict__ Tinv, int npanels, int64_t E,
                                                    int r_begin, int r_end, int nrt, int c_begin, int c_end, int nct,
                                                    float* __restrict__ Ut, int koff) {
@@ -217,7 +222,7 @@ __global__ void __launch_bounds__(256, 2) k_rowcol(int nu, int64_t ld, int64_t e
     const int64_t W = E * ntl;
     // issue the copies of item w into buffer b
     auto load = [&](int64_t w, int b) {
-        float* S = sm + b * RC_BUF;
+        float* S = sm + b * RcCfg<PTILE>::BUF;
         float* T = S + PTILE * RS;
         const int64_t e = w / ntl;
         const int tile = (int)(w - e * ntl);
@@ -225,7 +230,7 @@ __global__ void __launch_bounds__(256, 2) k_rowcol(int nu, int64_t ld, int64_t e
         const float* inv = Tinv + ((int64_t)e * npanels + J / NBP) * kInvMats * NBP * NBP;
         if (tile < nrt) {
             const int r0 = r_begin + tile * PTILE, nr = min(PTILE, r_end - r0);
-            for (int idx = t; idx < PTILE * (NBP / 4); idx += 256) {
+            for (int idx = t; idx < PTILE * (NBP / 4); idx += PTILE) {
                 const int rr = idx >> 4, j4 = idx & 15;
                 const bool ok = rr < nr && 4 * j4 < jb;
                 cp_async16(S + rr * RS + 4 * j4, ok ? M + (int64_t)(r0 + rr) * ld + J + 4 * j4 : M, ok);
@@ -233,14 +238,14 @@ __global__ void __launch_bounds__(256, 2) k_rowcol(int nu, int64_t ld, int64_t e
             // U11 (row i: U[i][j])
         } else {
             const int c0 = c_begin + (tile - nrt) * PTILE, nc = min(PTILE, c_end - c0);
-            for (int idx = t; idx < NBP * (PTILE / 4); idx += 256) {
+            for (int idx = t; idx < NBP * (PTILE / 4); idx += PTILE) {
                 const int k = idx / (PTILE / 4), c4 = idx % (PTILE / 4);
                 const bool ok = k < jb && 4 * c4 < nc;
                 cp_async16(S + k * PTILE + 4 * c4, ok ? M + (int64_t)(J + k) * ld + c0 + 4 * c4 : M, ok);
             }
             inv += (col_mode == 0 ? 1 : 2) * NBP * NBP;  // L11^T or U11^T
         }
-        for (int idx = t; idx < NBP * (NBP / 4); idx += 256) {
+        for (int idx = t; idx < NBP * (NBP / 4); idx += PTILE) {
             const int r = idx >> 4, c4 = idx & 15;
             cp_async16(T + r * RS + 4 * c4, inv + r * NBP + 4 * c4, true);
         }
@@ -255,7 +260,7 @@ __global__ void __launch_bounds__(256, 2) k_rowcol(int nu, int64_t ld, int64_t e
         cp_async_commit();
         asm volatile("cp.async.wait_all;" ::: "memory");
         __syncthreads();
-        float* S = sm + b * RC_BUF;
+        float* S = sm + b * RcCfg<PTILE>::BUF;
         const float* T = S + PTILE * RS;
         const int64_t e = w / ntl;
         const int tile = (int)(w - e * ntl);
@@ -270,7 +275,7 @@ __global__ void __launch_bounds__(256, 2) k_rowcol(int nu, int64_t ld, int64_t e
                 tri_solve<0>(a, T, T + NBP * RS, [&](int bb, float4 v) { *reinterpret_cast<float4*>(out + 4 * bb) = v; });
             }
             __syncthreads();
-            for (int rr = warp; rr < nr; rr += 8)
+            for (int rr = warp; rr < nr; rr += PTILE / 32)
                 for (int j = lane; j < jb; j += 32) M[(int64_t)(r0 + rr) * ld + J + j] = S[rr * RS + j];
         } else if constexpr (KIND != 0) {
             const int c0 = c_begin + (tile - nrt) * PTILE, nc = min(PTILE, c_end - c0);
@@ -297,7 +302,7 @@ __global__ void __launch_bounds__(256, 2) k_rowcol(int nu, int64_t ld, int64_t e
             }
             __syncthreads();
             float* ut = Ut + e * ld * UTK + koff;
-            for (int cc = warp; cc < nc; cc += 8)
+            for (int cc = warp; cc < nc; cc += PTILE / 32)
                 for (int i = lane; i < NBP; i += 32) {
                     const float v = S[cc * RS + i];
                     ut[(int64_t)(c0 + cc) * UTK + i] = v;
@@ -780,10 +785,19 @@ elrt_status update(elrt_ctx* ctx, const TcMaps& mp, float* M, int64_t ld, int64_
     CUtensorMap tS;  // stores: rows [0, r_end), columns [0, c_end)
     if (!mapM(&tS, M, r_end, c_end, ld, estride, E)) return ctx_fail(ctx, ELRT_EINVAL, "tensor map encoding failed");
     const int64_t items = (int64_t)((r_end - r0 + 127) / 128) * E;
-    const unsigned grid = (unsigned)std::min<int64_t>(items, 152);
+    const unsigned grid = (unsigned)std::min<int64_t>(items, ctx->sms);
     k_tc_update<NK><<<grid, kStripThreads, UpdCfg<NK>::TOTAL, ctx->stream>>>(mp.m, mp.u, tS, M, ctx->tab.nu, ld, estride,
                                                                              E, J, jb, koff, r0, r_end, c0, c_end, err);
     return cuda_check(ctx, cudaGetLastError(), "tc update launch");
+}
+
+
+template <int PT>
+cudaError_t rowcol_attrs() {
+    cudaError_t e = cudaFuncSetAttribute(k_rowcol<0, PT>, cudaFuncAttributeMaxDynamicSharedMemorySize, RcCfg<PT>::SMEM);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rowcol<1, PT>, cudaFuncAttributeMaxDynamicSharedMemorySize, RcCfg<PT>::SMEM);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rowcol<2, PT>, cudaFuncAttributeMaxDynamicSharedMemorySize, RcCfg<PT>::SMEM);
+    return e;
 }
 
 elrt_status prepare(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, const float* Ut, int64_t E, TcMaps* mp) {
@@ -797,9 +811,8 @@ elrt_status prepare(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, const 
         return ctx_fail(ctx, ELRT_EINVAL, "tensor map encoding failed");
     static bool attr_done = false;
     if (!attr_done) {
-        cudaError_t e = cudaFuncSetAttribute(k_rowcol<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, RC_SMEM);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rowcol<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, RC_SMEM);
-        if (e == cudaSuccess) e = cudaFuncSetAttribute(k_rowcol<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, RC_SMEM);
+        cudaError_t e = rowcol_attrs<256>();
+        if (e == cudaSuccess) e = rowcol_attrs<128>();
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_tc_update<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, UpdCfg<64>::TOTAL);
         if (e == cudaSuccess)
@@ -812,32 +825,41 @@ elrt_status prepare(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, const 
 
 int panels_of(int nu) { return (nu + NBP - 1) / NBP; }
 
-elrt_status rowcol(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, int64_t E, int J, int jb, const float* Tinv,
-                   int r_begin, int r_end, int c_begin, int c_end, int col_mode, float* Ut, int koff = 0) {
+template <int PTILE>
+void rowcol_launch(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, int64_t E, int J, int jb, const float* Tinv,
+                   int r_begin, int r_end, int c_begin, int c_end, int col_mode, float* Ut, int koff) {
+    using C = RcCfg<PTILE>;
     const int nrt = r_end > r_begin ? (r_end - r_begin + PTILE - 1) / PTILE : 0;
     const int nct = c_end > c_begin ? (c_end - c_begin + PTILE - 1) / PTILE : 0;
-    if (nrt + nct == 0) return ELRT_OK;
+    const int np = panels_of(ctx->tab.nu), nu = ctx->tab.nu;
+    if (nrt > 0) {  // items: (element, row tile)
+        const unsigned grid = (unsigned)std::min<int64_t>(E * nrt, (int64_t)C::PER_SM * ctx->sms);
+        k_rowcol<0, PTILE><<<grid, PTILE, C::SMEM, ctx->stream>>>(nu, ld, estride, M, J, jb, Tinv, np, E, r_begin, r_end,
+                                                                 nrt, c_begin, c_end, 0, Ut, koff);
+    }
+    if (nct > 0) {  // items: (element, column tile)
+        const unsigned grid = (unsigned)std::min<int64_t>(E * nct, (int64_t)C::PER_SM * ctx->sms);
+        if (col_mode == 0)
+            k_rowcol<1, PTILE><<<grid, PTILE, C::SMEM, ctx->stream>>>(nu, ld, estride, M, J, jb, Tinv, np, E, r_begin,
+                                                                     r_end, 0, c_begin, c_end, nct, Ut, koff);
+        else
+            k_rowcol<2, PTILE><<<grid, PTILE, C::SMEM, ctx->stream>>>(nu, ld, estride, M, J, jb, Tinv, np, E, r_begin,
+                                                                     r_end, 0, c_begin, c_end, nct, Ut, koff);
+    }
+}
+
+elrt_status rowcol(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, int64_t E, int J, int jb, const float* Tinv,
+                   int r_begin, int r_end, int c_begin, int c_end, int col_mode, float* Ut, int koff = 0) {
+    if (r_end <= r_begin && c_end <= c_begin) return ELRT_OK;
     // algorithmic work per element: row tiles read R x jb and write it back; column tiles read and
     // write jb x C and write U^T (C x 64); triangular solves with U11, L11 (unit lower) or U11
     const double R = std::max(0, r_end - r_begin), C = std::max(0, c_end - c_begin);
     const double bytes = 8.0 * R * jb + 8.0 * C * jb + 4.0 * C * NBP + 4.0 * NBP * NBP * ((R > 0) + (C > 0));
     const double flops = R * jb * (jb + 1.0) + (col_mode == 0 ? C * jb * (jb - 1.0) : C * jb * (jb + 1.0));
-    ProfScope ps(ctx, "lu_tc_rowcol", (nrt > 0) + (nct > 0), (double)E * bytes, (double)E * flops);
-    const int np = panels_of(ctx->tab.nu), nu = ctx->tab.nu;
-    if (nrt > 0) {  // items: (element, row tile)
-        const unsigned grid = (unsigned)std::min<int64_t>(E * nrt, 2 * 152);
-        k_rowcol<0><<<grid, 256, RC_SMEM, ctx->stream>>>(nu, ld, estride, M, J, jb, Tinv, np, E, r_begin, r_end, nrt,
-                                                         c_begin, c_end, 0, Ut, koff);
-    }
-    if (nct > 0) {  // items: (element, column tile)
-        const unsigned grid = (unsigned)std::min<int64_t>(E * nct, 2 * 152);
-        if (col_mode == 0)
-            k_rowcol<1><<<grid, 256, RC_SMEM, ctx->stream>>>(nu, ld, estride, M, J, jb, Tinv, np, E, r_begin, r_end, 0,
-                                                             c_begin, c_end, nct, Ut, koff);
-        else
-            k_rowcol<2><<<grid, 256, RC_SMEM, ctx->stream>>>(nu, ld, estride, M, J, jb, Tinv, np, E, r_begin, r_end, 0,
-                                                             c_begin, c_end, nct, Ut, koff);
-    }
+    ProfScope ps(ctx, "lu_tc_rowcol", (R > 0) + (C > 0), (double)E * bytes, (double)E * flops);
+    static const int pt = getenv("ELRT_RC_TILE") && atoi(getenv("ELRT_RC_TILE")) == 128 ? 128 : 256;
+    if (pt == 128) rowcol_launch<128>(ctx, M, ld, estride, E, J, jb, Tinv, r_begin, r_end, c_begin, c_end, col_mode, Ut, koff);
+    else rowcol_launch<256>(ctx, M, ld, estride, E, J, jb, Tinv, r_begin, r_end, c_begin, c_end, col_mode, Ut, koff);
     return cuda_check(ctx, cudaGetLastError(), "rowcol launch");
 }
 

@@ -361,8 +361,7 @@ elrt_status sweep_apply(elrt_ctx* ctx, int nx, int nz, const void* A, int a_byte
     if (t.nin % 8 != 0 || t.nin > kSwMaxIn || E > (1LL << 27) || (a_bytes != 2 && a_bytes != 4) ||
         ((uintptr_t)A & 15) != 0)
         return ctx_fail(ctx, ELRT_EINVAL, "sweep preconditioner: unsupported element size or alignment");
-    int nsm = 0;
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, ctx->device);
+    const int nsm = ctx->sms;
     const int parts = sweep_parts(t), prows = (t.nin + parts - 1) / parts;
     const size_t blk = (size_t)prows * t.nin * a_bytes, extra = (size_t)(t.nin + 36) * sizeof(float);
     const int stages = 2 * blk + extra <= (size_t)kSwSmemMax ? 2 : (blk + extra <= (size_t)kSwSmemMax ? 1 : 0);
