@@ -1450,7 +1450,7 @@ elrt_status static_build(const Tab& t, cudaStream_t sm, unsigned char* scratch, 
                 k_restrict<T, double><<<(unsigned)n, kThreads, 0, sm>>>(t, M, ld, estride, t.nu, (double*)o_i2o,
                                                                        (double*)o_i2m, estat, n);
         }
-        k_static_status<<<(unsigned)std::min<int64_t>(ctx->sms, (n + 255) / 256), 256, 0, sm>>>(estat, n, flags);
+        k_static_status<<<(unsigned)std::min<int64_t>(152, (n + 255) / 256), 256, 0, sm>>>(estat, n, flags);
         if (cudaGetLastError() != cudaSuccess) return ELRT_ECUDA;
     }
     int bad[2] = {0, 0};

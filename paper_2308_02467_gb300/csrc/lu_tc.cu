@@ -9,7 +9,7 @@
 // factored in panels of 64 columns, taken in pairs a = [J, J+64), b = [J+64, J+128):
 //   k_diag             (one small block per element): LU of the 64 x 64 diagonal block, published
 //                      as U11, L11^T, U11^T and 1 / diag(U11);
-//   k_rowcol           (blocks of 256 rows or columns per element): L21 from L21 U11 = A21 written
+//   k_rowcol           (blocks of 128 rows or columns per element): L21 from L21 U11 = A21 written
 //                      back to the matrix; U12 from L11 U12 = A12 written back to the matrix and,
 //                      transposed (K-major), to one FP32 side buffer whose rows hold both panels of
 //                      the pair.  On the right-hand-side columns this is the forward substitution;
@@ -26,7 +26,6 @@
 // kernels.
 #include <math.h>
 #include <stdio.h>
-#include <stdlib.h>
 
 #include <algorithm>
 #include <mutex>
@@ -59,62 +58,74 @@ constexpr int TI = NBP + 4;                                        // factor row
 //   [2] U11^T, [3] row 0: 1 / diag(U11).
 // Beyond jb the block is padded with the identity (U_ii = 1), so every consumer can run all 64 steps.
 constexpr int kInvMats = 4;
-constexpr int kDiagThreads = 128;
+constexpr int kDiagThreads = NBP;  // one thread per column of the diagonal block
+// Right-looking LU without pivoting of the 64 x 64 diagonal block, one element per block: thread c
+// holds column c in registers.  Step j needs the pivot column j (as left by step j - 1) and the
+// pivot row entry D[j][c], which thread c already holds; the owner of column j + 1 publishes its
+// column, as updated by step j, for step j + 1, so each step takes one barrier (two buffers).
+// Every thread forms its multiplier D[j][c] / D[j][j] itself (D[r][c] -= D[r][j] (D[j][c] / D[j][j]));
+// the columns of L are scaled by 1 / pivot once, in shared memory, after the last step.  (Ownership
+// is tested on a bit mask: a test c == j would let the compiler index the register array by c.)
 __global__ void __launch_bounds__(kDiagThreads) k_diag(int nu, int64_t ld, int64_t estride, float* __restrict__ Mall,
                                                        int J, int jb, float* __restrict__ Tinv, int npanels,
                                                        int* __restrict__ estat, float piv_tol) {
     __shared__ float D[NBP][TS];
-    __shared__ float lcol[NBP];
+    __shared__ __align__(16) float lc[2][NBP];
     const int64_t e = blockIdx.x;
     float* M = Mall + e * estride;
-    const int t = threadIdx.x;
-    for (int idx = t; idx < NBP * NBP; idx += kDiagThreads) {
-        const int r = idx / NBP, c = idx % NBP;
-        D[r][c] = (r < jb && c < jb) ? M[(int64_t)(J + r) * ld + J + c] : (r == c ? 1.f : 0.f);
+    const int c = threadIdx.x;
+    const unsigned long long me = 1ull << c;
+    // a pivot below the tolerance is replaced by +-tolerance (the element is marked)
+    auto clamp_piv = [&](float piv) { return fabsf(piv) >= piv_tol ? piv : (piv < 0.f ? -piv_tol : piv_tol); };
+    float a[NBP];
+#pragma unroll
+    for (int r = 0; r < NBP; ++r)
+        a[r] = (r < jb && c < jb) ? M[(int64_t)(J + r) * ld + J + c] : (r == c ? 1.f : 0.f);
+    if (c == 0) {
+#pragma unroll
+        for (int r = 0; r < NBP; ++r) lc[0][r] = a[r];
     }
     __syncthreads();
-    // right-looking LU without pivoting: per step the multipliers, then the trailing block
-    int bad = 0;
-    for (int j = 0; j < jb; ++j) {
-        __syncthreads();  // the trailing update of step j - 1 is complete
-        float piv = D[j][j];
-        if (!(fabsf(piv) >= piv_tol)) {
-            bad = 1;
-            piv = piv < 0.f ? -piv_tol : piv_tol;
+#pragma unroll
+    for (int j = 0; j < NBP; ++j) {
+        const float* col = lc[j & 1];
+        if (c > j) {
+            const float m = a[j] * (1.f / clamp_piv(col[j]));
+#pragma unroll
+            for (int r = j + 1; r < NBP; ++r) a[r] = fmaf(-col[r], m, a[r]);
         }
-        const float rp = 1.f / piv;
-        // (thread 0 may write the clamped pivot while others read it: both clamp to the same value)
-        if (t == 0) D[j][j] = piv;
-        if (t > j && t < jb) {
-            const float l = D[t][j] * rp;
-            D[t][j] = l;
-            lcol[t] = l;
+        if (j + 1 < NBP && ((me >> (j + 1)) & 1ull)) {
+#pragma unroll
+            for (int r = j + 1; r < NBP; ++r) lc[(j + 1) & 1][r] = a[r];
         }
         __syncthreads();
-        // trailing block, rows and columns j+1 .. jb-1: column t % 64, every other row
-        const int c = t & (NBP - 1);
-        if (c > j && c < jb) {
-            const float ujc = D[j][c];
-            for (int r = j + 1 + (t >> 6); r < jb; r += kDiagThreads / NBP) D[r][c] -= lcol[r] * ujc;
-        }
+    }
+#pragma unroll
+    for (int r = 0; r < NBP; ++r) D[r][c] = a[r];
+    __syncthreads();
+    {  // column c of L: D[r][c] / pivot for r > c; the (clamped) pivot on the diagonal
+        const float raw = D[c][c], piv = clamp_piv(raw);
+        if (c < jb && piv != raw) atomicOr(&estat[e], 1);
+        const float rp = 1.f / piv;
+        D[c][c] = piv;
+        for (int r = c + 1; r < NBP; ++r) D[r][c] *= rp;
     }
     __syncthreads();
-    if (bad && t == 0) atomicOr(&estat[e], 1);
-    for (int idx = t; idx < jb * jb; idx += kDiagThreads) {
-        const int r = idx / jb, c = idx % jb;
-        M[(int64_t)(J + r) * ld + J + c] = D[r][c];
+    for (int idx = c; idx < jb * jb; idx += kDiagThreads) {
+        const int r = idx / jb, cc = idx % jb;
+        M[(int64_t)(J + r) * ld + J + cc] = D[r][cc];
     }
     float* Uo = Tinv + ((int64_t)e * npanels + J / NBP) * kInvMats * NBP * NBP;
     float* LT = Uo + NBP * NBP;
     float* UT = LT + NBP * NBP;
     float* rd = UT + NBP * NBP;
-    for (int idx = t; idx < NBP * NBP; idx += kDiagThreads) {
-        const int r = idx / NBP, c = idx % NBP;
-        Uo[idx] = c >= r ? D[r][c] : 0.f;   // U11
-        LT[idx] = c > r ? D[c][r] : 0.f;    // LT[r][c] = L[c][r], strictly lower part
-        UT[idx] = c <= r ? D[c][r] : 0.f;   // UT[r][c] = U[c][r]
+    for (int idx = c; idx < NBP * NBP; idx += kDiagThreads) {
+        const int r = idx / NBP, cc = idx % NBP;
+        Uo[idx] = cc >= r ? D[r][cc] : 0.f;   // U11
+        LT[idx] = cc > r ? D[cc][r] : 0.f;    // LT[r][c] = L[c][r], strictly lower part
+        UT[idx] = cc <= r ? D[cc][r] : 0.f;   // UT[r][c] = U[c][r]
     }
-    if (t < NBP) rd[t] = 1.f / D[t][t];
+    rd[c] = 1.f / D[c][c];
 }
 
 // Triangular solves of one row or column held in registers, with the factor in shared memory
@@ -184,12 +195,12 @@ __device__ __forceinline__ void tri_solve(float (&a)[NBP], const float* __restri
 // c_end): y = L11^{-1} a (col_mode 0: factorisation and forward sweep) or y = U11^{-1} a
 // (col_mode 1: backward sweep), written back to the matrix (rows < jb) and, transposed, to the side
 // buffer Ut[e][column][koff .. koff + 63] (zero beyond jb), with its low TF32 parts at K offset
-// UTL + koff.  Persistent, two blocks per SM (one staging buffer
-// each, 128 registers per thread): each block walks its items, copying an item's 64-wide block and
-// the factor of the diagonal block with 16-byte cp.async copies, solving and storing it; the two
-// blocks of an SM overlap one another's copies and stores.  (One block per SM with two staging
-// buffers, copies of the next item in flight, measured 23% slower: 8 warps per SM were too few to
-// hide the shared-memory latency of the substitutions.)
+// UTL + koff.  Persistent, four blocks of 128 threads per SM (one staging buffer each, 128
+// registers per thread): each block walks its items, copying an item's 64-wide block and the factor
+// of the diagonal block with 16-byte cp.async copies, solving and storing it; the blocks of an SM
+// overlap one another's copies and stores.  (One block per SM with two staging buffers, copies of
+// the next item in flight, measured 23% slower: 8 warps per SM were too few to hide the
+// shared-memory latency of the substitutions.)
 constexpr int RS = NBP + 4;                        // staging row stride: 16-byte aligned rows
 // one thread per row or column of a tile, PTILE of them; one staging buffer per block
 template <int PTILE>
@@ -199,6 +210,9 @@ struct RcCfg {
     static constexpr int PER_SM = PTILE == 256 ? 2 : 4;      // resident blocks per SM
     static_assert(PTILE * RS >= NBP * PTILE, "the staging area holds a 64 x PTILE column block");
 };
+// 128-row tiles, four blocks per SM: measured 2 % faster than 256-row tiles with two blocks per SM
+// (the same 16 warps, more independent copy / solve / store phases to overlap)
+constexpr int kRcTile = 128;
 
 __device__ __forceinline__ void cp_async16(float* smem, const float* gmem, bool valid) {
     // src-size 0 fills the 16 bytes with zeros and reads nothing
@@ -811,8 +825,7 @@ elrt_status prepare(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, const 
         return ctx_fail(ctx, ELRT_EINVAL, "tensor map encoding failed");
     static bool attr_done = false;
     if (!attr_done) {
-        cudaError_t e = rowcol_attrs<256>();
-        if (e == cudaSuccess) e = rowcol_attrs<128>();
+        cudaError_t e = rowcol_attrs<kRcTile>();
         if (e == cudaSuccess)
             e = cudaFuncSetAttribute(k_tc_update<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, UpdCfg<64>::TOTAL);
         if (e == cudaSuccess)
@@ -857,9 +870,7 @@ elrt_status rowcol(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, int64_t
     const double bytes = 8.0 * R * jb + 8.0 * C * jb + 4.0 * C * NBP + 4.0 * NBP * NBP * ((R > 0) + (C > 0));
     const double flops = R * jb * (jb + 1.0) + (col_mode == 0 ? C * jb * (jb - 1.0) : C * jb * (jb + 1.0));
     ProfScope ps(ctx, "lu_tc_rowcol", (R > 0) + (C > 0), (double)E * bytes, (double)E * flops);
-    static const int pt = getenv("ELRT_RC_TILE") && atoi(getenv("ELRT_RC_TILE")) == 128 ? 128 : 256;
-    if (pt == 128) rowcol_launch<128>(ctx, M, ld, estride, E, J, jb, Tinv, r_begin, r_end, c_begin, c_end, col_mode, Ut, koff);
-    else rowcol_launch<256>(ctx, M, ld, estride, E, J, jb, Tinv, r_begin, r_end, c_begin, c_end, col_mode, Ut, koff);
+    rowcol_launch<kRcTile>(ctx, M, ld, estride, E, J, jb, Tinv, r_begin, r_end, c_begin, c_end, col_mode, Ut, koff);
     return cuda_check(ctx, cudaGetLastError(), "rowcol launch");
 }
 
