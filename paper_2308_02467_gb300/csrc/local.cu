@@ -572,6 +572,17 @@ __device__ __forceinline__ void fma_cx(ff& acc, ff c, float x) { ff_fma_f(acc, x
 __device__ __forceinline__ void fma_cx(ff& acc, ff c, ff x) { ff_fma(acc, c, x); }
 __device__ __forceinline__ ff as_ff(float x) { return ff{x, 0.f}; }
 __device__ __forceinline__ ff as_ff(ff x) { return x; }
+// two adjacent staged columns in one shared load (8 or 16 bytes, aligned: even column offsets)
+__device__ __forceinline__ void ld_pair(const float* p, float& a, float& b) {
+    const float2 v = *reinterpret_cast<const float2*>(p);
+    a = v.x;
+    b = v.y;
+}
+__device__ __forceinline__ void ld_pair(const ff* p, ff& a, ff& b) {
+    const float4 v = *reinterpret_cast<const float4*>(p);
+    a = ff{v.x, v.y};
+    b = ff{v.z, v.w};
+}
 
 // XS: type of the staged X chunk: float for mode 0 (half the shared memory, so twice the
 // columns per pass), float-float for modes 1 and 2
@@ -591,8 +602,8 @@ __global__ void __launch_bounds__(kResThreads, 2) k_residual_ff(Tab t, double h,
     ff* wd = dcoef + nu;                       // [n1][n1]: w_q D[q][a]
     ff* sxw = wd + nm;                         // [N][n1]: sx_k w_b
     ff* szw = sxw + N * n1;                    // [N][n1]: sz_k w_a
-    ff* wcf = szw + N * n1;                    // [N]: circulant phase
-    ff* scoef = wcf + N;                       // [nm]: w_i omega kappa_hat_i
+    ff* wrot = szw + N * n1;                   // [N][N]: circulant phase, row k rotated: wc[(k - l) mod N]
+    ff* scoef = wrot + N * N;                  // [nm]: w_i omega kappa_hat_i
     int* abv = reinterpret_cast<int*>(scoef + nm);  // [nm]: a | b << 8 of node i
     __shared__ float red[kResThreads / 32];
     const int64_t e = blockIdx.x;
@@ -609,7 +620,10 @@ __global__ void __launch_bounds__(kResThreads, 2) k_residual_ff(Tab t, double h,
         sxw[q] = ff_from_double(t.sx[k] * t.w[b]);
         szw[q] = ff_from_double(t.sz[k] * t.w[b]);
     }
-    for (int q = threadIdx.x; q < N; q += kResThreads) wcf[q] = ff_from_double(t.wc[q]);
+    for (int q = threadIdx.x; q < N * N; q += kResThreads) {
+        const int k = q / N, l = q - k * N;
+        wrot[q] = ff_from_double(t.wc[k >= l ? k - l : k - l + N]);
+    }
     for (int r = threadIdx.x; r < nu; r += kResThreads) {
         const int k = r / nm, i = r - k * nm;
         const int a = i % n1, b = i / n1;
@@ -625,6 +639,9 @@ __global__ void __launch_bounds__(kResThreads, 2) k_residual_ff(Tab t, double h,
     float rmax = 0.f;
     const int rpp = kResThreads / CWR;
     const int tcol = threadIdx.x % CWR, trow = threadIdx.x / CWR;
+    // compute mapping: CWR / 2 column pairs per row (CWR is even)
+    const int ppp = kResThreads / (CWR / 2);
+    const int tpair = threadIdx.x % (CWR / 2), prow = threadIdx.x / (CWR / 2);
     for (int cs = 0; cs < nin; cs += CWR) {
         const int col = cs + tcol;
         const bool colok = col < nin;
@@ -661,51 +678,75 @@ __global__ void __launch_bounds__(kResThreads, 2) k_residual_ff(Tab t, double h,
         }
         if (mode == 2) continue;
         __syncthreads();
-        // the one nonzero of this column of B^: row tr, value tv
-        int tr = -1;
-        ff tv{0.f, 0.f};
-        if (colok) {
-            const int F = col / t.nface, rem = col - F * t.nface;
-            const int m = rem / t.half, kk = rem - m * t.half;
-            const int kin = t.inc[F][kk];
-            tr = kin * nm + face_node(F, m, p);
-            tv = ff_from_double(-t.w[m] * t.sdn[F][kin]);
+        // compute: each thread takes two adjacent staged columns (c0, c0 + 1), so every coefficient
+        // load and every staged-value load serves two entries
+        const int c0 = cs + 2 * tpair;
+        bool ok[2];
+        int tr[2];  // the one nonzero of each column of B^: row tr, value tv
+        ff tv[2];
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int col = c0 + u;
+            ok[u] = col < nin;
+            tr[u] = -1;
+            tv[u] = ff{0.f, 0.f};
+            if (ok[u]) {
+                const int F = col / t.nface, rem = col - F * t.nface;
+                const int m = rem / t.half, kk = rem - m * t.half;
+                const int kin = t.inc[F][kk];
+                tr[u] = kin * nm + face_node(F, m, p);
+                tv[u] = ff_from_double(-t.w[m] * t.sdn[F][kin]);
+            }
         }
-        int k = trow / nm, i = trow - k * nm;
-        for (int r = trow; r < nu; r += rpp) {
-            if (colok) {
+        int k = prow / nm, i = prow - k * nm;
+        for (int r = prow; r < nu; r += ppp) {
+            if (ok[0]) {
                 const int ab = abv[i];
                 const int a = ab & 0xff, b = ab >> 8;
-                const XS* xk = Xs + (size_t)k * nm * CWR + tcol;  // angle block k, this column
-                ff acc = ff_mul(dcoef[r], as_ff(xk[i * CWR]));
-                ff tx{0.f, 0.f}, tz{0.f, 0.f};
+                const XS* xk = Xs + (size_t)k * nm * CWR + 2 * tpair;  // angle block k, this column pair
+                XS x0, x1;
+                ld_pair(xk + i * CWR, x0, x1);
+                ff acc[2] = {ff_mul(dcoef[r], as_ff(x0)), ff_mul(dcoef[r], as_ff(x1))};
+                ff tx[2] = {}, tz[2] = {};
                 const XS* xrow = xk + n1 * b * CWR;  // x-line through node i
                 const XS* xcol = xk + a * CWR;       // z-line through node i
 #pragma unroll
                 for (int q = 0; q < n1; ++q) {
-                    fma_cx(tx, wd[q * n1 + a], xrow[q * CWR]);
-                    fma_cx(tz, wd[q * n1 + b], xcol[q * n1 * CWR]);
+                    const ff wx = wd[q * n1 + a], wz = wd[q * n1 + b];
+                    ld_pair(xrow + q * CWR, x0, x1);
+                    fma_cx(tx[0], wx, x0);
+                    fma_cx(tx[1], wx, x1);
+                    ld_pair(xcol + q * n1 * CWR, x0, x1);
+                    fma_cx(tz[0], wz, x0);
+                    fma_cx(tz[1], wz, x1);
                 }
-                tx = ff_norm(tx.h, tx.l);
-                tz = ff_norm(tz.h, tz.l);
-                const ff cxz = ff_add(ff_mul(sxw[k * n1 + b], tx), ff_mul(szw[k * n1 + a], tz));
-                const XS* xi = Xs + (size_t)i * CWR + tcol;  // node i across angles
-                ff sc{0.f, 0.f};
+                const XS* xi = Xs + (size_t)i * CWR + 2 * tpair;  // node i across angles
+                const ff* wk = wrot + k * N;                      // phase row k (fixed offsets below)
+                ff sc[2] = {};
 #pragma unroll
                 for (int l = 0; l < N; ++l) {
-                    int d = k - l;
-                    d += d < 0 ? N : 0;
-                    fma_cx(sc, wcf[d], xi[(size_t)l * nm * CWR]);
+                    const ff w = wk[l];
+                    ld_pair(xi + (size_t)l * nm * CWR, x0, x1);
+                    fma_cx(sc[0], w, x0);
+                    fma_cx(sc[1], w, x1);
                 }
-                sc = ff_norm(sc.h, sc.l);
-                acc = ff_add(acc, ff_neg(cxz));
-                acc = ff_add(acc, ff_neg(ff_mul(scoef[i], sc)));
-                const ff res = (r == tr) ? ff_add(tv, ff_neg(acc)) : ff_neg(acc);
-                const float rf = __fadd_rn(res.h, res.l);
-                rmax = fmaxf(rmax, fabsf(rf));
-                M[(int64_t)r * ld + nu + col] = rf;
+                const ff cx = sxw[k * n1 + b], cz = szw[k * n1 + a], cs_ = scoef[i];
+#pragma unroll
+                for (int u = 0; u < 2; ++u) {
+                    const ff ttx = ff_norm(tx[u].h, tx[u].l), ttz = ff_norm(tz[u].h, tz[u].l);
+                    const ff cxz = ff_add(ff_mul(cx, ttx), ff_mul(cz, ttz));
+                    const ff tsc = ff_norm(sc[u].h, sc[u].l);
+                    ff v = ff_add(acc[u], ff_neg(cxz));
+                    v = ff_add(v, ff_neg(ff_mul(cs_, tsc)));
+                    const ff res = (r == tr[u]) ? ff_add(tv[u], ff_neg(v)) : ff_neg(v);
+                    const float rf = __fadd_rn(res.h, res.l);
+                    if (ok[u]) {
+                        rmax = fmaxf(rmax, fabsf(rf));
+                        M[(int64_t)r * ld + nu + c0 + u] = rf;
+                    }
+                }
             }
-            i += rpp;
+            i += ppp;
             while (i >= nm) {
                 i -= nm;
                 ++k;
@@ -1070,7 +1111,7 @@ elrt_status run_residual(elrt_ctx* ctx, double h, const double* h_elem, const do
 
 // shared memory of the float-float residual for cwr staged columns of xs-byte entries
 size_t residual_ff_smem(const Tab& t, int cwr, size_t xs) {
-    return (size_t)t.nu * cwr * xs + ((size_t)t.nu + t.nm + 2 * (size_t)t.N * t.n1 + t.N + t.nm) * sizeof(ff) +
+    return (size_t)t.nu * cwr * xs + ((size_t)t.nu + t.nm + 2 * (size_t)t.N * t.n1 + (size_t)t.N * t.N + t.nm) * sizeof(ff) +
            t.nm * sizeof(int);
 }
 // columns staged per pass: as many as leave room for two blocks per SM (one stages its next
@@ -1086,6 +1127,7 @@ elrt_status launch_residual_ff(elrt_ctx* ctx, double h, const double* h_elem, co
                                float* M, int64_t ld, int64_t estride, ff* X, int mode, double* maxres, int64_t n) {
     const Tab& t = ctx->tab;
     const int cwr = residual_ff_cwr(t, sizeof(XS));
+    if (cwr < 2) return ctx_fail(ctx, ELRT_EINVAL, "float-float residual: element too large for two staged columns");
     const size_t smem = residual_ff_smem(t, cwr, sizeof(XS));
     cudaError_t e =
         cudaFuncSetAttribute(k_residual_ff<N1T, NAT, XS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
