@@ -67,6 +67,51 @@ __device__ __forceinline__ double aug_entry(const Tab& t, int k, int i, int c, c
     return v;
 }
 
+// FP32 copies of the tables one block (element e, angular cell k) of the FP32 assembly reads
+struct AugF {
+    float w[ELRT_MAX_N1], D[ELRT_MAX_N1 * ELRT_MAX_N1], wc[ELRT_MAX_ANG], sdn[4], kh[ELRT_MAX_N1 * ELRT_MAX_N1];
+    float sx, sz, om;
+};
+
+// The same entries as aug_entry for the candidates of row (k, i), evaluated in FP32: on the FP32
+// paths the assembled matrix only feeds the factorisation (the float-float residual of the
+// refinement and the right-hand side -B^ it uses come from the FP64 tables), so an entry a few
+// FP32 ulps from the rounded FP64 value changes nothing but the factorisation's own rounding, and
+// the FP64 pipe (1/64 of the FP32 rate on this GPU) is kept out of the assembly.
+__device__ __forceinline__ float aug_entry_f(const Tab& t, const AugF& f, int k, int i, int c) {
+    const int nm = t.nm, n1 = t.n1, p = t.p;
+    const int a = i % n1, b = i / n1;
+    float v = 0.f;
+    if (c < t.nu) {
+        const int l = c / nm, j = c - l * nm;
+        if (l == k) {
+            const int jc = j % n1, jd = j / n1;
+            const float wj = f.w[jc] * f.w[jd];
+            if (jd == b) v -= wj * f.sx * f.D[jc * n1 + a];
+            if (jc == a) v -= wj * f.sz * f.D[jd * n1 + b];
+            if (j == i) {
+                float bd = 0.f;
+                if (b == 0 && f.sdn[0] > 0.f) bd += f.w[a] * f.sdn[0];
+                if (a == p && f.sdn[1] > 0.f) bd += f.w[b] * f.sdn[1];
+                if (b == p && f.sdn[2] > 0.f) bd += f.w[a] * f.sdn[2];
+                if (a == 0 && f.sdn[3] > 0.f) bd += f.w[b] * f.sdn[3];
+                v += bd + f.w[a] * f.w[b] * f.kh[i];
+            }
+        }
+        if (j == i) {
+            int d = k - l;
+            if (d < 0) d += t.N;
+            v -= f.w[a] * f.w[b] * f.om * f.kh[i] * f.wc[d];
+        }
+    } else if (c < t.nu + t.nin) {
+        const int col = c - t.nu;
+        const int F = col / t.nface, rem = col - F * t.nface;
+        const int m = rem / t.half, kk = rem - m * t.half;
+        if (t.inc[F][kk] == k && face_node(F, m, p) == i) v = -f.w[m] * f.sdn[F];
+    }
+    return v;
+}
+
 // Grid: (E, N).  Block (e, k) writes rows (k, 0..nm-1) of element e; columns >= nu + nin are 0.
 // Also validates the inputs (flags[0] |= 1 on a negative or non-finite kappa / h, omega outside [0, 1],
 // or kappa_hat = kappa h / 2 above 1e30, beyond which the FP32 modes would overflow).
@@ -87,7 +132,26 @@ __global__ void __launch_bounds__(kThreads) k_assemble(Tab t, double h, const do
         kh[i] = kv * 0.5 * he;
     }
     if (threadIdx.x == 0 && (!(he > 0.0) || !isfinite(he) || !(om >= 0.0 && om <= 1.0))) atomicOr(flags, 1);
+    __shared__ AugF fa;  // FP32 tables (FP32 candidate path only)
+    if constexpr (sizeof(T) == 4) {
+        if (!rhs_out) {
+            for (int q = threadIdx.x; q < t.n1 * t.n1; q += blockDim.x) fa.D[q] = (float)t.D[q];
+            for (int q = threadIdx.x; q < t.n1; q += blockDim.x) fa.w[q] = (float)t.w[q];
+            for (int q = threadIdx.x; q < t.N; q += blockDim.x) fa.wc[q] = (float)t.wc[q];
+            if (threadIdx.x < 4) fa.sdn[threadIdx.x] = (float)t.sdn[threadIdx.x][k];
+            if (threadIdx.x == 0) {
+                fa.sx = (float)t.sx[k];
+                fa.sz = (float)t.sz[k];
+                fa.om = (float)om;
+            }
+        }
+    }
     __syncthreads();
+    if constexpr (sizeof(T) == 4) {
+        if (!rhs_out)
+            for (int q = threadIdx.x; q < t.nm; q += blockDim.x) fa.kh[q] = (float)kh[q];
+        __syncthreads();
+    }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     T* Me = M + e * estride;
     for (int i = warp; i < t.nm; i += kThreads / 32) {
@@ -133,7 +197,10 @@ __global__ void __launch_bounds__(kThreads) k_assemble(Tab t, double h, const do
                         if (t.inc[F][x] == k) kk = x;
                     if (m >= 0 && kk >= 0) c = t.nu + F * t.nface + m * t.half + kk;
                 }
-                if (c >= 0) row[c] = (T)aug_entry(t, k, i, c, kh, om);
+                if (c >= 0) {
+                    if constexpr (sizeof(T) == 4) row[c] = aug_entry_f(t, fa, k, i, c);
+                    else row[c] = (T)aug_entry(t, k, i, c, kh, om);
+                }
             }
         }
     }
