@@ -152,12 +152,15 @@ elrt_status elrt_set_graphs(elrt_ctx* ctx, int32_t on);
  * default): right preconditioning by upwind block Gauss-Seidel sweeps of the skeleton system
  * (I - A_int) z = r (eq. hdg_global_mat; Sec. 2.3 lists transport sweeps among the solvers of
  * radiative transfer), from z = 0, one sweep from each mesh corner in turn (bottom-left,
- * top-right, bottom-right, top-left): a sweep visits the elements in wavefront order from its
- * corner and sets z_K = r_K + A_i2o^K z_in(K) with the inflow gathered from the current z.  With
- * right preconditioning GMRES still minimises the true residual, so the solution and the
- * stopping test are those of plain GMRES; the Arnoldi steps fall by an order of magnitude on the
- * scattering workloads (each then costs four sweeps, on the Arnoldi operator elrt_set_krylov_op
- * selects).  ELRT_PRECOND_NONE: plain GMRES.  FP64 operators ignore the setting.  ELRT_EINVAL on
+ * bottom-right, top-right, top-left): a sweep visits the elements in wavefront order from its
+ * corner and recomputes the outflow of each element's two downwind faces (right and top from the
+ * bottom-left corner, left and top from the bottom-right, left and bottom from the top-right,
+ * right and bottom from the top-left) as z_F = r_F + A_i2o^K[F] z_in(K), with the inflow gathered
+ * from the current z (the latest values written; zero before any).  With right preconditioning
+ * GMRES still minimises the true residual, so the solution and the stopping test are those of
+ * plain GMRES; the Arnoldi steps fall by an order of magnitude on the scattering workloads (each
+ * then costs one application: every operator row read twice, on the Arnoldi operator
+ * elrt_set_krylov_op selects).  ELRT_PRECOND_NONE: plain GMRES.  FP64 operators ignore the setting.  ELRT_EINVAL on
  * another value. */
 typedef enum { ELRT_PRECOND_NONE = 0, ELRT_PRECOND_SWEEP = 1 } elrt_precond;
 elrt_status elrt_set_precond(elrt_ctx* ctx, int32_t kind);

@@ -15,7 +15,8 @@ Plain, slow, dense numpy code that follows the paper's formulation:
 * Algorithm 1, step 4: mean-intensity recovery u^m = A_i2m u^_in.
 * Sec. 2.3 names transport sweeps among the solvers of radiative transfer: sweep_precond applies
   upwind block Gauss-Seidel sweeps of eq. hdg_global_mat (the elements taken in the wavefront
-  order of one mesh corner, then of the others), the preconditioner of the library's GMRES.
+  order of one mesh corner, then of the others; each sweep recomputes every outflow value, or only
+  those of the faces pointing away from its corner), the preconditioner of the library's GMRES.
 
 Readings where the paper is silent:
 * every integral uses the (p+1)-point LGL rule per direction (diagonal mass);
@@ -385,19 +386,37 @@ def sweep_order(mesh: Mesh, corner: str):
     return np.argsort(dx + dz, kind="stable")
 
 
-def sweep_precond(mesh: Mesh, disc: Disc, A_i2o, r, corners=SWEEP_CORNERS):
+# The faces (0 bottom, 1 right, 2 top, 3 left) whose outflow travels away from a sweep's corner:
+# the downwind faces of the sweep.
+SWEEP_DOWNWIND = {"BL": (1, 2), "BR": (3, 2), "TR": (3, 0), "TL": (1, 0)}
+
+
+def sweep_rows(disc: Disc, corner: str, rows: str):
+    """Outflow rows of an element that a sweep from `corner` recomputes: all of them, or those of
+    its two downwind faces."""
+    if rows == "all":
+        return np.arange(disc.n_out)
+    nf = disc.n_face
+    return np.concatenate([np.arange(F * nf, (F + 1) * nf) for F in SWEEP_DOWNWIND[corner]])
+
+
+def sweep_precond(mesh: Mesh, disc: Disc, A_i2o, r, corners=SWEEP_CORNERS, rows="downwind"):
     """z = M r: block Gauss-Seidel sweeps of eq. hdg_global_mat, (I - A_int) z = r, from z = 0,
     one sweep per corner in turn.  A sweep visits the elements in wavefront order and replaces
-    each element's outflow by z_K = r_K + A_i2o^K z_in(K), the inflow gathered from the current
-    z (already swept neighbours: this sweep's values; the others: the previous sweep's, zero in the
-    first).  A linear operator: the preconditioner of the library's GMRES."""
+    outflow values of each element by z_K = r_K + A_i2o^K z_in(K), the inflow gathered from the
+    current z (already swept neighbours: this sweep's values; the others: the latest earlier
+    sweep's, zero before any).  rows = "all": every outflow value of the element; rows = "downwind"
+    (the library's): only those of the two faces that point away from the corner, the values the
+    sweep's later elements read — each face is then recomputed by two of the four sweeps.  A
+    linear operator: the preconditioner of the library's GMRES."""
     E, no = mesh.n_elems, disc.n_out
     r = np.asarray(r, dtype=np.float64).reshape(E, no)
     z = np.zeros((E, no))
     for corner in corners:
+        sel = sweep_rows(disc, corner, rows)
         for e in sweep_order(mesh, corner):
             zin = gather_inflow_one(mesh, disc, z, e)
-            z[e] = r[e] + A_i2o[e] @ zin
+            z[e, sel] = r[e, sel] + A_i2o[e][sel] @ zin
     return z.reshape(-1)
 
 

@@ -127,8 +127,8 @@ elrt_status global_recover_rows(elrt_ctx* ctx, int nx, int nz, int rows, const v
                                 const double* inflow, const double* self, double* out);
 
 // ---- sweep preconditioner of the skeleton GMRES (sweep.cu)
-int sweep_parts(const Tab& t);
-void sweep_orders(int nx, int nz, int parts, int* out);
+void sweep_orders(int nx, int nz, int* out);                 // [4 E] work items in their global order
+size_t sweep_words_bytes(const Tab& t, int64_t E);          // scratch of one application's outflow words
 elrt_status sweep_apply(elrt_ctx* ctx, int nx, int nz, const void* A, int a_bytes, const float* u, float* z,
                         const int* order, void* zw, int* flags, const int* done, const int* nsteps);
 

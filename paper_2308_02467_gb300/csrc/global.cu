@@ -15,6 +15,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
 #include <mutex>
 #include <type_traits>
 #include <vector>
@@ -1485,9 +1486,9 @@ elrt_status gmres(elrt_ctx* ctx, int nx, int nz, const void* Aop, const double* 
     // sweeps' versioned outflow [n] (8 bytes each), the item order [4 E] and two flags
     const int64_t E = (int64_t)nx * nz;
     const bool pc = std::is_same<V, float>::value && ctx->precond == ELRT_PRECOND_SWEEP;
-    const int pc_parts = pc ? sweep_parts(t) : 1;
+    const size_t pc_words = pc ? ((sweep_words_bytes(t, E) + 255) & ~(size_t)255) : 0;
     const size_t pc_bytes =
-        pc ? (((size_t)4 * n * sizeof(float) + (size_t)4 * E * pc_parts * sizeof(int) + 64 + 255) & ~(size_t)255) : 0;
+        pc ? (((size_t)2 * n * sizeof(float) + 256 + pc_words + (size_t)4 * E * sizeof(int) + 64 + 255) & ~(size_t)255) : 0;
     elrt_status s = ensure_ws(ctx, &ctx->gm, &ctx->gm_bytes, vb_bytes + xbytes + 256 + small + sizeof(GmState) + 512 + pc_bytes);
     if (s) return s;
     V* Vb = (V*)ctx->gm;
@@ -1505,9 +1506,9 @@ elrt_status gmres(elrt_ctx* ctx, int nx, int nz, const void* Aop, const double* 
     GmState* st = (GmState*)(scal + 64);
     float* pc_t = pc ? (float*)(((uintptr_t)(st + 1) + 255) & ~(uintptr_t)255) : nullptr;  // M v_j, M u
     float* pc_u = pc ? pc_t + n : nullptr;                                                 // sum y_i s_i W_i
-    void* pc_zw = pc ? (void*)(pc_u + n) : nullptr;                                       // 8 n bytes
-    int* pc_order = pc ? (int*)(pc_u + 3 * n) : nullptr;
-    int* pc_flags = pc ? pc_order + 4 * E * pc_parts : nullptr;
+    void* pc_zw = pc ? (void*)(((uintptr_t)(pc_u + n) + 255) & ~(uintptr_t)255) : nullptr;  // sweep_words_bytes
+    int* pc_order = pc ? (int*)((unsigned char*)pc_zw + pc_words) : nullptr;
+    int* pc_flags = pc ? pc_order + 4 * E : nullptr;
     // three-launch Arnoldi step: FP32 basis, restarts up to kArnMaxV - 1 and the streaming matvec
     const bool arn4 = std::is_same<V, float>::value && m + 1 <= kArnMaxV && gemv_streams(t, Aop, (int)sizeof(A));
     cudaStream_t sm = ctx->stream;
@@ -1518,8 +1519,8 @@ elrt_status gmres(elrt_ctx* ctx, int nx, int nz, const void* Aop, const double* 
     const int rows = t.nin;
 
     if (pc) {
-        std::vector<int> ord((size_t)4 * E * pc_parts);
-        sweep_orders(nx, nz, pc_parts, ord.data());
+        std::vector<int> ord((size_t)4 * E);
+        sweep_orders(nx, nz, ord.data());
         s = cuda_check(ctx, cudaMemcpyAsync(pc_order, ord.data(), ord.size() * sizeof(int), cudaMemcpyHostToDevice, sm),
                        "sweep orders");
         if (!s) s = cuda_check(ctx, cudaStreamSynchronize(sm), "sweep orders");  // (pageable source)
@@ -1615,14 +1616,20 @@ elrt_status gmres(elrt_ctx* ctx, int nx, int nz, const void* Aop, const double* 
     // v_0 = r / beta, then mj Arnoldi steps with the FP16 (f16) or the given operator, the small
     // least-squares solve and x += V y; ends with the state and the matvec's timeout flag copied to
     // pinned host memory
+    // While profiling (plain launches only), the algorithmic work each Arnoldi step enqueues is
+    // recorded, so that the steps the device skips once converged (their kernels return at once)
+    // can be taken out of the work counts after the cycle.
+    std::vector<std::map<std::string, std::pair<double, double>>> wsnap;
     auto enqueue_cycle = [&](bool f16, int mj) -> elrt_status {
         elrt_status e = ELRT_OK;
+        wsnap.clear();
         {
             ProfScope ps(ctx, "krylov", 1, kv(1, n, sizeof(X)) + kv(1, n, sizeof(V)));
             k_scale<X, V><<<gb, kThreads, 0, sm>>>(r, Vb, n, scal + 1, nullptr);
         }
         { ProfScope ps(ctx, "krylov"); k_cycle_start<<<1, 1, 0, sm>>>(st, gv, m, scal + 1, arn4 ? arn->sc : nullptr); }
         for (int j = 0; j < mj; ++j) {
+            if (ctx->profiling) wsnap.push_back(ctx->work);
             V* vj = Vb + (size_t)j * n;
             V* w = Vb + (size_t)(j + 1) * n;
             double* hc = H + (size_t)j * (m + 1);
@@ -1669,6 +1676,7 @@ elrt_status gmres(elrt_ctx* ctx, int nx, int nz, const void* Aop, const double* 
             { ProfScope ps(ctx, "krylov", 1, kv(2, n, sv)); k_scale<V, V><<<gb, kThreads, 0, sm>>>(w, w, n, hc + j + 1, st); }
             { ProfScope ps(ctx, "krylov"); k_givens<<<1, 1, 0, sm>>>(H, m + 1, cs, sn, gv, j, st); }
         }
+        if (ctx->profiling) wsnap.push_back(ctx->work);
         { ProfScope ps(ctx, "krylov"); k_solve_upper<<<1, 1, 0, sm>>>(H, m + 1, gv, yv, st); }
         if constexpr (std::is_same<V, float>::value) {
             if (pc) {  // x += M (sum y_i s_i W_i)
@@ -1805,6 +1813,18 @@ elrt_status gmres(elrt_ctx* ctx, int nx, int nz, const void* Aop, const double* 
             return ctx_fail(ctx, ELRT_ETIMEOUT, hflag[0] ? "a copy wait of the streaming matvec timed out"
                                                          : "a wait of the sweep preconditioner timed out");
         }
+        if (wsnap.size() >= 2) {  // take the skipped steps j_done .. mj - 1 out of the work counts
+            const auto& at = wsnap[std::min<size_t>((size_t)std::max(0, hst->j_done), wsnap.size() - 1)];
+            const auto& end = wsnap.back();
+            for (const auto& kv : end) {
+                const auto it = at.find(kv.first);
+                const double b0 = it == at.end() ? 0.0 : it->second.first;
+                const double f0 = it == at.end() ? 0.0 : it->second.second;
+                ctx->work[kv.first].first -= kv.second.first - b0;
+                ctx->work[kv.first].second -= kv.second.second - f0;
+            }
+        }
+        wsnap.clear();
         its += hst->j_done;
         ++cycles;
         if (hst->j_done == 0) break;  // no progress possible

@@ -41,11 +41,12 @@ def test_apply_matches_oracle(lib, nx, nz, p, N):
     np.testing.assert_allclose(_apply(lib, disc, mesh, A32, r), ref, rtol=0, atol=2e-5 * np.abs(ref).max())
 
 
-@pytest.mark.parametrize("faces", [(0, 3), (1, 2)])
+@pytest.mark.parametrize("faces", [(0, 3), (0, 1)])
 def test_apply_inverts_a_one_sided_operator(lib, faces):
-    """Blocks that take interior inflow only through the bottom and left faces (or only the top and
-    right): (I - A_int) is block triangular in the first (second) sweep's order, so M is its exact
-    inverse: the GPU result against a dense solve, independent of the oracle's sweep."""
+    """Blocks that take interior inflow only through the bottom and left faces (or the bottom and
+    right): (I - A_int) is block triangular in the first (second) sweep's order, and one application
+    of the downwind-face sweeps is its exact inverse: the GPU result against a dense solve,
+    independent of the oracle's sweep."""
     disc, mesh = hdg.Disc(3, 8, 0.5, "fv0"), hdg.Mesh(7, 6, 1.0)
     A32 = _random_blocks(mesh, disc, faces, seed=5)
     G = hdg.global_dense(mesh, disc, A32.astype(np.float64))

@@ -3,9 +3,12 @@ of eq. hdg_global_mat; Sec. 2.3 names sweeps among the solvers of radiative tran
 
 Exactness where the mathematics fixes it: when every element takes its interior inflow only from
 the neighbours one wavefront closer to a corner, (I - A_int) is block triangular in that corner's
-order and one sweep from it is the exact inverse (checked against a dense solve, which shares no
-code with the sweep); a mesh without interior faces makes M the identity; and on the physical
-skeleton system right-preconditioned GMRES reaches the plain solution in far fewer steps."""
+order and one sweep from it that recomputes every outflow value is the exact inverse (checked
+against a dense solve, which shares no code with the sweep); a mesh without interior faces makes M
+the identity; and on the physical skeleton system right-preconditioned GMRES reaches the plain
+solution in far fewer steps.  The library's form recomputes only each sweep's downwind faces:
+it is pinned against the same sweeps written as a multiplicative Schwarz iteration with dense
+block solves (no sweep loop), and by the one-sided operators it inverts exactly."""
 
 import numpy as np
 import pytest
@@ -35,9 +38,10 @@ def test_one_sweep_inverts_a_one_sided_operator(corner, faces):
     G = hdg.global_dense(mesh, disc, A)
     r = np.random.default_rng(7).standard_normal(G.shape[0])
     exact = np.linalg.solve(G, r)
-    np.testing.assert_allclose(hdg.sweep_precond(mesh, disc, A, r, corners=(corner,)), exact, rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(hdg.sweep_precond(mesh, disc, A, r, corners=(corner,), rows="all"), exact,
+                               rtol=1e-12, atol=1e-12)
     # the further sweeps of the full preconditioner keep the exact solution (a fixed point)
-    np.testing.assert_allclose(hdg.sweep_precond(mesh, disc, A, r), exact, rtol=1e-11, atol=1e-11)
+    np.testing.assert_allclose(hdg.sweep_precond(mesh, disc, A, r, rows="all"), exact, rtol=1e-11, atol=1e-11)
 
 
 def test_opposite_corner_does_not_invert_it():
@@ -49,7 +53,7 @@ def test_opposite_corner_does_not_invert_it():
     G = hdg.global_dense(mesh, disc, A)
     r = np.random.default_rng(8).standard_normal(G.shape[0])
     exact = np.linalg.solve(G, r)
-    z = hdg.sweep_precond(mesh, disc, A, r, corners=("TR",))
+    z = hdg.sweep_precond(mesh, disc, A, r, corners=("TR",), rows="all")
     assert np.linalg.norm(z - exact) > 1e-3 * np.linalg.norm(exact)
 
 
@@ -58,6 +62,7 @@ def test_single_element_is_identity():
     mesh = hdg.Mesh(1, 1, 1.0)
     A = _random_blocks(mesh, disc, (0, 1, 2, 3), seed=1)
     r = np.random.default_rng(2).standard_normal(disc.n_out)
+    np.testing.assert_array_equal(hdg.sweep_precond(mesh, disc, A, r, rows="all"), r)
     np.testing.assert_array_equal(hdg.sweep_precond(mesh, disc, A, r), r)
 
 
@@ -88,8 +93,50 @@ def test_preconditioned_gmres_on_the_skeleton_system():
     b = hdg.global_rhs(mesh, disc, A, np.asarray(prob.inflow))
     apply = lambda x: hdg.global_apply(mesh, disc, A, x)
     x0, it0, rel0 = hdg.gmres(apply, b, rtol=1e-10, restart=12)
-    x1, it1, rel1 = hdg.gmres_right(apply, lambda v: hdg.sweep_precond(mesh, disc, A, v), b, rtol=1e-10, restart=12)
-    assert rel0 <= 1e-10 and rel1 <= 1e-10
-    assert np.linalg.norm(b - apply(x1)) <= 1e-10 * np.linalg.norm(b) * 1.01
-    np.testing.assert_allclose(x1, x0, rtol=0, atol=1e-8 * np.abs(x0).max())
-    assert 3 * it1 <= it0, (it0, it1)
+    for rows in ("all", "downwind"):
+        x1, it1, rel1 = hdg.gmres_right(apply, lambda v: hdg.sweep_precond(mesh, disc, A, v, rows=rows), b, rtol=1e-10,
+                                        restart=12)
+        assert rel0 <= 1e-10 and rel1 <= 1e-10
+        assert np.linalg.norm(b - apply(x1)) <= 1e-10 * np.linalg.norm(b) * 1.01
+        np.testing.assert_allclose(x1, x0, rtol=0, atol=1e-8 * np.abs(x0).max())
+        assert 3 * it1 <= it0, (rows, it0, it1)
+
+
+def _schwarz(mesh, disc, A, r):
+    """The downwind-face sweeps as a multiplicative Schwarz iteration on G = I - A_int from z = 0:
+    per corner, the rows S of every element's two downwind faces are solved for exactly, the
+    others held: z_S += G_SS^{-1} (r - G z)_S, by a dense solve (no sweep loop, no gather)."""
+    G = hdg.global_dense(mesh, disc, A)
+    E, no, nf = mesh.n_elems, disc.n_out, disc.n_face
+    z = np.zeros(G.shape[0])
+    for corner in hdg.SWEEP_CORNERS:
+        S = np.concatenate([e * no + F * nf + np.arange(nf) for e in range(E) for F in hdg.SWEEP_DOWNWIND[corner]])
+        res = r - G @ z
+        z[S] += np.linalg.solve(G[np.ix_(S, S)], res[S])
+    return z
+
+
+@pytest.mark.parametrize("nx,nz", [(4, 3), (1, 5), (3, 3)])
+def test_downwind_sweeps_are_multiplicative_schwarz(nx, nz):
+    disc = hdg.Disc(2, 8, 0.5, "fv0")
+    mesh = hdg.Mesh(nx, nz, 1.0)
+    A = _random_blocks(mesh, disc, (0, 1, 2, 3), seed=nx * 7 + nz)
+    r = np.random.default_rng(nx + 10 * nz).standard_normal(mesh.n_elems * disc.n_out)
+    np.testing.assert_allclose(hdg.sweep_precond(mesh, disc, A, r), _schwarz(mesh, disc, A, r), rtol=1e-11, atol=1e-11)
+
+
+@pytest.mark.parametrize("faces,exact", [((0, 3), True), ((0, 1), True), ((1, 2), False), ((2, 3), False)])
+def test_downwind_sweeps_on_one_sided_operators(faces, exact):
+    """Inflow only from below and from the left (or from below and the right): the bottom-left (the
+    bottom-right) sweep, first (second) in turn, makes every value it recomputes exact and the later
+    sweeps recompute the rest from exact inflow, so one application is the exact inverse.  Inflow
+    only from above: the sweeps that recompute the top faces come before the ones that bring the
+    inflow, so it is not."""
+    disc = hdg.Disc(2, 8, 0.5, "fv0")
+    mesh = hdg.Mesh(4, 3, 1.0)
+    A = _random_blocks(mesh, disc, faces, seed=3)
+    G = hdg.global_dense(mesh, disc, A)
+    r = np.random.default_rng(7).standard_normal(G.shape[0])
+    ref = np.linalg.solve(G, r)
+    err = np.abs(hdg.sweep_precond(mesh, disc, A, r) - ref).max() / np.abs(ref).max()
+    assert (err < 1e-12) == exact, (faces, err)
