@@ -168,7 +168,7 @@ def parse():
     ap.add_argument("--restart", type=int, default=12, help="GMRES restart length")
     ap.add_argument("--precond", default="sweep", choices=["sweep", "none"],
                     help="skeleton GMRES preconditioner: upwind block Gauss-Seidel sweeps, or none")
-    ap.add_argument("--krylov-op", default="f16", choices=["f16", "f32"],
+    ap.add_argument("--krylov-op", default="f32", choices=["f16", "f32"],
                     help="operator of the Arnoldi-step matvecs (restart residuals always use the FP32 operator)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--nx", type=int, default=64, help="elements per side of the slab (64: the benchmark workload)")

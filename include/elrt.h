@@ -129,15 +129,18 @@ elrt_status elrt_node_coords(const elrt_disc* disc, int32_t nx, int32_t nz, doub
 elrt_status elrt_create(elrt_ctx** ctx, const elrt_disc* disc, void* stream);
 elrt_status elrt_destroy(elrt_ctx* ctx);
 elrt_status elrt_set_stream(elrt_ctx* ctx, void* stream);
-/* Operator of the Arnoldi-step matvecs of elrt_solve_global / elrt_solve_field / elrt_solve_batch
- * with FP32 in2out.  ELRT_KRYLOV_F16 (the default): each solve first writes an FP16 copy of in2out
- * into the context's workspace (2 bytes per entry) and builds the Krylov basis with it, while the
+/* Operator of the Arnoldi-step matvecs (and of the sweep preconditioner) of elrt_solve_global /
+ * elrt_solve_field / elrt_solve_batch with FP32 in2out.  ELRT_KRYLOV_F32 (the default): the FP32
+ * operator everywhere.  ELRT_KRYLOV_F16: each solve first writes an FP16 copy of in2out into the
+ * context's workspace (2 bytes per entry) and builds the Krylov basis with it, while the
  * right-hand side and every restart residual use the FP32 operator, so the restarts still refine
  * the iterate to rtol in the FP32 system (restarted GMRES as the inner solver of a mixed-precision
  * iterative refinement; half the operator bytes per Arnoldi step).  A solve keeps the FP32
  * operator throughout when in2out holds an entry beyond +-6e4 or a non-finite one, and switches to
- * it when a restart cycle lowers the true residual by less than 10%.  ELRT_KRYLOV_F32: the FP32
- * operator everywhere.  FP64 operators ignore the setting.  ELRT_EINVAL on another value. */
+ * it when a restart cycle lowers the true residual by less than 10%.  The FP16 copy pays when the
+ * solve is bound by its matvecs (plain GMRES, hundreds of steps); with the sweep preconditioner the
+ * FP32 operator needs fewer restart cycles (benchmark slab: 12 steps in one cycle against 16 in
+ * two, 12.1 against 15.6 ms).  FP64 operators ignore the setting.  ELRT_EINVAL on another value. */
 elrt_status elrt_set_krylov_op(elrt_ctx* ctx, int32_t op);
 /* CUDA-graph replay of the skeleton GMRES (on by default): each restart cycle -- restart residual,
  * convergence test on the device, restart-length Arnoldi steps, update -- is captured once per

@@ -321,7 +321,7 @@ class Context:
                                        _ptr(r, torch.float32, n, "r"), _ptr(z, torch.float32, n, "z")), self._h)
 
     def elrt_set_krylov_op(self, op):
-        """KRYLOV_F16 (default) or KRYLOV_F32: operator of the Arnoldi-step matvecs (FP32 in2out)."""
+        """KRYLOV_F32 (default) or KRYLOV_F16: operator of the Arnoldi-step matvecs (FP32 in2out)."""
         _check(_lib.elrt_set_krylov_op(self._h, int(op)), self._h)
 
     # ---- local stage

@@ -61,7 +61,7 @@ struct elrt_ctx {
     size_t gm_bytes = 0;
     void* gm16 = nullptr;   // FP16 copy of the skeleton operator (Arnoldi steps)
     size_t gm16_bytes = 0;
-    int krylov_op = ELRT_KRYLOV_F16;
+    int krylov_op = ELRT_KRYLOV_F32;
     int graphs = 1;         // replay GMRES restart cycles from captured CUDA graphs
     int precond = ELRT_PRECOND_SWEEP;  // skeleton GMRES preconditioner (FP32 operators)
     void* ops = nullptr;    // in2out / in2sol of elrt_solve_field
