@@ -709,7 +709,8 @@ __global__ void __launch_bounds__(kResThreads, 2) k_residual_ff(Tab t, double h,
     // compute mapping: CWR / 2 column pairs per row (CWR is even)
     const int ppp = kResThreads / (CWR / 2);
     const int tpair = threadIdx.x % (CWR / 2), prow = threadIdx.x / (CWR / 2);
-    for (int cs = 0; cs < nin; cs += CWR) {
+    // column chunks: all of them in this block, or (small batches: gridDim.y > 1) every gridDim.y-th
+    for (int cs = blockIdx.y * CWR; cs < nin; cs += gridDim.y * CWR) {
         const int col = cs + tcol;
         const bool colok = col < nin;
         __syncthreads();
@@ -827,7 +828,9 @@ __global__ void __launch_bounds__(kResThreads, 2) k_residual_ff(Tab t, double h,
     if (threadIdx.x == 0) {
         float m = 0.f;
         for (int w = 0; w < kResThreads / 32; ++w) m = fmaxf(m, red[w]);
-        maxres[e] = (double)m;
+        if (gridDim.y == 1) maxres[e] = (double)m;
+        else  // several blocks per element: the maximum of non-negative doubles by their bit patterns (zeroed first)
+            atomicMax(reinterpret_cast<unsigned long long*>(maxres + e), (unsigned long long)__double_as_longlong((double)m));
     }
 }
 
@@ -1199,9 +1202,16 @@ elrt_status launch_residual_ff(elrt_ctx* ctx, double h, const double* h_elem, co
     cudaError_t e =
         cudaFuncSetAttribute(k_residual_ff<N1T, NAT, XS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_check(ctx, e, "smem attribute");
+    // a batch too small to fill the GPU spreads each element's column chunks over several blocks
+    const int nchunk = (t.nin + cwr - 1) / cwr;
+    const int gy = (int)std::max<int64_t>(1, std::min<int64_t>(nchunk, (2 * (int64_t)ctx->sms) / std::max<int64_t>(n, 1)));
+    if (gy > 1 && mode != 2) {
+        e = cudaMemsetAsync(maxres, 0, (size_t)n * sizeof(double), ctx->stream);
+        if (e != cudaSuccess) return cuda_check(ctx, e, "residual maxima");
+    }
     ProfScope ps(ctx, "residual", 1, residual_bytes(t, sizeof(float), mode, n), residual_flops(t, mode, n));
-    k_residual_ff<N1T, NAT, XS><<<(unsigned)n, kResThreads, smem, ctx->stream>>>(t, h, h_elem, kappa, omega, M, ld,
-                                                                                 estride, X, mode, cwr, maxres, n);
+    k_residual_ff<N1T, NAT, XS><<<dim3((unsigned)n, (unsigned)gy), kResThreads, smem, ctx->stream>>>(
+        t, h, h_elem, kappa, omega, M, ld, estride, X, mode, cwr, maxres, n);
     return cuda_check(ctx, cudaGetLastError(), "residual launch");
 }
 

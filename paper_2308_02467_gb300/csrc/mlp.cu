@@ -1014,11 +1014,24 @@ __global__ void __launch_bounds__(256) k_energy_estimate(Tab t, double h, const 
     for (int j = threadIdx.x; j < nin; j += blockDim.x) {
         const int F = j / t.nface, rem = j - F * t.nface, m = rem / half, kk = rem - m * half;
         const float lhs = (float)(t.w[m] * fabs(t.sdn[F][t.inc[F][kk]]));
-        float rhs = 0.f;
-        const float* A = i2o + e * (int64_t)nin * nin;
-        for (int r = 0; r < nin; ++r) rhs = fmaf(wout[r], A[(int64_t)r * nin + j], rhs);
-        const float* Mm = i2m + e * (int64_t)nm * nin;
-        for (int i = 0; i < nm; ++i) rhs = fmaf(absorb[i], Mm[(int64_t)i * nin + j], rhs);
+        // four independent chains (the loads of a column are independent; one chain would serialise
+        // the column's 273 multiply-adds behind their loads)
+        float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        const float* A = i2o + e * (int64_t)nin * nin + j;
+        int r = 0;
+        for (; r + 4 <= nin; r += 4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc[u] = fmaf(wout[r + u], A[(int64_t)(r + u) * nin], acc[u]);
+        }
+        for (; r < nin; ++r) acc[0] = fmaf(wout[r], A[(int64_t)r * nin], acc[0]);
+        const float* Mm = i2m + e * (int64_t)nm * nin + j;
+        int i = 0;
+        for (; i + 4 <= nm; i += 4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc[u] = fmaf(absorb[i + u], Mm[(int64_t)(i + u) * nin], acc[u]);
+        }
+        for (; i < nm; ++i) acc[0] = fmaf(absorb[i], Mm[(int64_t)i * nin], acc[0]);
+        const float rhs = (acc[0] + acc[1]) + (acc[2] + acc[3]);
         const float d = fabsf(lhs - rhs) / lhs;
         worst = fmaxf(worst, d != d ? 1e30f : d);
     }
