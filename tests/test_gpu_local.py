@@ -203,3 +203,32 @@ def test_local_tensor_core_lu_matches_oracle(lib, p, N, ang, n):
     assert err2 < 1e-10 and st.max_rel_residual < 1e-12, (err0, err2, st.max_rel_residual)
     np.testing.assert_allclose(i2m.cpu().numpy(), o_i2m, atol=1e-10)
 
+
+
+@pytest.mark.parametrize("mode", ["tf32ir", "fp32ir"])
+def test_small_batch_matches_large_batch(lib, mode):
+    """A batch smaller than the GPU spreads each element's residual over several blocks (column
+    chunks per block); a large batch runs one block per element.  The arithmetic per entry is the
+    same, so nine elements built alone and the same nine inside a batch of 640 give bit-identical
+    operators and the same residual statistics."""
+    import torch
+    p, N = 6, 16
+    kappa, omega, h = H.random_elements(640, p, seed=91)
+    ctx = _ctx(lib, p, N, 0.85, "fv0")
+    m = {"tf32ir": lib.LOCAL_TF32_IR, "fp32ir": lib.LOCAL_FP32_IR}[mode]
+
+    def build(k, o, refine):
+        n = o.size
+        a = torch.empty(n, ctx.nin, ctx.nin, dtype=torch.float64, device="cuda")
+        b = torch.empty(n, ctx.nm, ctx.nin, dtype=torch.float64, device="cuda")
+        st = ctx.elrt_build_local(torch.tensor(k, device="cuda"), torch.tensor(o, device="cuda"), h, a, b, mode=m,
+                                  refine_steps=refine, stats=True)
+        return a.cpu().numpy(), b.cpu().numpy(), st
+
+    pick = np.array([0, 5, 77, 150, 300, 301, 450, 600, 639])
+    for refine in (1, 2):
+        a_all, b_all, st_all = build(kappa, omega, refine)
+        a_few, b_few, st_few = build(kappa[pick], omega[pick], refine)
+        assert np.array_equal(a_few, a_all[pick]) and np.array_equal(b_few, b_all[pick]), refine
+        assert st_few.n_flagged == 0 and st_all.n_flagged == 0
+        assert st_few.max_rel_residual <= st_all.max_rel_residual
