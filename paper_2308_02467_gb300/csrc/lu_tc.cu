@@ -289,8 +289,18 @@ __global__ void __launch_bounds__(PTILE, RcCfg<PTILE>::PER_SM) k_rowcol(int nu, 
                 tri_solve<0>(a, T, T + NBP * RS, [&](int bb, float4 v) { *reinterpret_cast<float4*>(out + 4 * bb) = v; });
             }
             __syncthreads();
-            for (int rr = warp; rr < nr; rr += PTILE / 32)
-                for (int j = lane; j < jb; j += 32) M[(int64_t)(r0 + rr) * ld + J + j] = S[rr * RS + j];
+            // two rows per warp pass, 16-byte stores (a half warp per row; jb % 4 == 0 except in a
+            // last panel narrower than 4, which takes the scalar path)
+            if ((jb & 3) == 0 && (J & 3) == 0 && (ld & 3) == 0) {
+                const int hrow = lane >> 4, q = lane & 15;
+                for (int rr = 2 * warp + hrow; rr < nr; rr += 2 * (PTILE / 32))
+                    if (4 * q < jb)
+                        *reinterpret_cast<float4*>(M + (int64_t)(r0 + rr) * ld + J + 4 * q) =
+                            *reinterpret_cast<const float4*>(S + rr * RS + 4 * q);
+            } else {
+                for (int rr = warp; rr < nr; rr += PTILE / 32)
+                    for (int j = lane; j < jb; j += 32) M[(int64_t)(r0 + rr) * ld + J + j] = S[rr * RS + j];
+            }
         } else if constexpr (KIND != 0) {
             const int c0 = c_begin + (tile - nrt) * PTILE, nc = min(PTILE, c_end - c0);
             float a[NBP];
@@ -315,13 +325,19 @@ __global__ void __launch_bounds__(PTILE, RcCfg<PTILE>::PER_SM) k_rowcol(int nu, 
                 tri_solve<KIND>(a, T, T + NBP * RS, put);
             }
             __syncthreads();
+            // two columns per warp pass (a half warp per column), 16-byte stores of the value and of
+            // its low TF32 part, split once (UTK, UTL and koff are multiples of 4)
             float* ut = Ut + e * ld * UTK + koff;
-            for (int cc = warp; cc < nc; cc += PTILE / 32)
-                for (int i = lane; i < NBP; i += 32) {
-                    const float v = S[cc * RS + i];
-                    ut[(int64_t)(c0 + cc) * UTK + i] = v;
-                    ut[(int64_t)(c0 + cc) * UTK + UTL + i] = v - tf32_hi(v);  // the low TF32 part, split once
+            {
+                const int hcol = lane >> 4, q = lane & 15;
+                for (int cc = 2 * warp + hcol; cc < nc; cc += 2 * (PTILE / 32)) {
+                    const float4 v = *reinterpret_cast<const float4*>(S + cc * RS + 4 * q);
+                    const float4 lo = make_float4(v.x - tf32_hi(v.x), v.y - tf32_hi(v.y), v.z - tf32_hi(v.z),
+                                                  v.w - tf32_hi(v.w));
+                    *reinterpret_cast<float4*>(ut + (int64_t)(c0 + cc) * UTK + 4 * q) = v;
+                    *reinterpret_cast<float4*>(ut + (int64_t)(c0 + cc) * UTK + UTL + 4 * q) = lo;
                 }
+            }
         }
         __syncthreads();  // the buffer is refilled by the next item's copies
     }
