@@ -167,6 +167,16 @@ elrt_status elrt_set_graphs(elrt_ctx* ctx, int32_t on);
  * another value. */
 typedef enum { ELRT_PRECOND_NONE = 0, ELRT_PRECOND_SWEEP = 1 } elrt_precond;
 elrt_status elrt_set_precond(elrt_ctx* ctx, int32_t kind);
+/* Products of the trailing updates of the TF32_IR local factorisation (elrt_set_lu_products).
+ * ELRT_LU_PRODUCTS_AUTO (the default): 3xFP16 -- each operand as its FP16 rounding plus the FP16
+ * rounding of the remainder, hi*hi + hi*lo + lo*hi accumulated in FP32, ~22-bit products like
+ * 3xTF32 at half the tensor-core instructions -- for a batch chunk whose assembled entries all lie
+ * in [0.25, 1024] and that has no source column, and 3xTF32 otherwise; the refinement re-solves
+ * always use 3xTF32 (their right-hand sides are residuals far below FP16's normal range).
+ * ELRT_LU_PRODUCTS_TF32: 3xTF32 everywhere.  The refined operators meet the same accuracy either way.
+ * ELRT_EINVAL on another value. */
+typedef enum { ELRT_LU_PRODUCTS_AUTO = 0, ELRT_LU_PRODUCTS_TF32 = 1 } elrt_lu_products;
+elrt_status elrt_set_lu_products(elrt_ctx* ctx, int32_t mode);
 /* z = M r, the sweep preconditioner above applied once on the context's stream; synchronises.
  * in2out: device [E][n_out][n_in] FP32 (dtype ELRT_F32; ELRT_EINVAL otherwise); r, z: device
  * [E][n_out] FP32, distinct.  ELRT_ETIMEOUT (after a synchronisation) if a wait between elements

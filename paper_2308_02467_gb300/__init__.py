@@ -9,7 +9,7 @@ ImportError.  The binding is loaded on first use, so `build` can run before the 
 
 _EXPORTS = (
     "LIB_PATH", "ElrtError", "ANG_FV0", "ANG_DO", "LOCAL_FP64", "LOCAL_FP32_IR", "LOCAL_TF32_IR", "F32", "F64",
-    "KRYLOV_F32", "KRYLOV_F16", "PRECOND_NONE", "PRECOND_SWEEP",
+    "KRYLOV_F32", "KRYLOV_F16", "PRECOND_NONE", "PRECOND_SWEEP", "LU_PRODUCTS_AUTO", "LU_PRODUCTS_TF32",
     "Disc", "Context", "elrt_lgl", "elrt_phase_matrix", "elrt_node_coords", "elrt_n_nodes", "elrt_n_local",
     "elrt_n_skel", "elrt_n_inflow", "exported_symbols", "elrt_build_local_static", "Net",
     "elrt_build_local_learned", "elrt_solve_batch", "elrt_net_file_info",

@@ -21,6 +21,7 @@ LOCAL_FP64, LOCAL_FP32_IR, LOCAL_TF32_IR = 0, 1, 2
 F32, F64 = 0, 1
 KRYLOV_F32, KRYLOV_F16 = 0, 1
 PRECOND_NONE, PRECOND_SWEEP = 0, 1
+LU_PRODUCTS_AUTO, LU_PRODUCTS_TF32 = 0, 1
 STATUS = {0: "ok", 1: "EINVAL", 2: "ENOMEM", 3: "ESINGULAR", 4: "ENOCONV", 5: "ETIMEOUT", 6: "ECUDA", 7: "ENOTRAINED"}
 
 
@@ -95,6 +96,7 @@ _sig = {
     "elrt_set_krylov_op": (_i32, [_vp, _i32]),
     "elrt_set_graphs": (_i32, [_vp, _i32]),
     "elrt_set_precond": (_i32, [_vp, _i32]),
+    "elrt_set_lu_products": (_i32, [_vp, _i32]),
     "elrt_apply_precond": (_i32, [_vp, _i32, _i32, _vp, _i32, _vp, _vp]),
     "elrt_autotune": (_i32, [_vp, _P(Field), _i32, _i32, _d, _P(TuneReport)]),
     "elrt_get_tuning": (_i32, [_vp, _P(_i64), _P(_i32), _P(_i32), _P(_i32)]),
@@ -307,6 +309,11 @@ class Context:
     def elrt_set_graphs(self, on=True):
         """CUDA-graph replay of the GMRES restart cycles (default on)."""
         _check(_lib.elrt_set_graphs(self._h, int(bool(on))), self._h)
+
+    def elrt_set_lu_products(self, mode):
+        """LU_PRODUCTS_AUTO (default: 3xFP16 trailing updates when the assembled entries allow) or
+        LU_PRODUCTS_TF32 (3xTF32 everywhere)."""
+        _check(_lib.elrt_set_lu_products(self._h, int(mode)), self._h)
 
     def elrt_set_precond(self, kind):
         """PRECOND_SWEEP (default) or PRECOND_NONE: preconditioner of the skeleton GMRES (FP32 in2out)."""

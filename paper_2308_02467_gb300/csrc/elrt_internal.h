@@ -63,7 +63,8 @@ struct elrt_ctx {
     size_t gm16_bytes = 0;
     int krylov_op = ELRT_KRYLOV_F32;
     int graphs = 1;         // replay GMRES restart cycles from captured CUDA graphs
-    int precond = ELRT_PRECOND_SWEEP;  // skeleton GMRES preconditioner (FP32 operators)
+    int precond = ELRT_PRECOND_SWEEP;
+    int lu_products = ELRT_LU_PRODUCTS_AUTO;  // products of the tensor-core LU's trailing updates  // skeleton GMRES preconditioner (FP32 operators)
     void* ops = nullptr;    // in2out / in2sol of elrt_solve_field
     size_t ops_bytes = 0;
     void* vec = nullptr;    // skeleton of elrt_solve_field when the caller passes none
@@ -109,11 +110,15 @@ elrt_status local_build(elrt_ctx* ctx, int64_t E, double h, const double* h_elem
                         void* in2sol, int32_t* elem_status, elrt_local_stats* stats,
                         const elrt_local_extras* extras = nullptr);
 
-// ---- tensor-core LU (lu_tc.cu)
+// ---- tensor-core LU (lu_tc.cu).  f16: the trailing updates form their products as 3xFP16 (FP16
+// high parts and remainders, half the MMA instructions of 3xTF32), allowed when every entry of the
+// assembled matrices lies within kLuF16Max; a re-solve must use the factorisation's setting.
+constexpr float kLuF16Max = 1024.f;
+constexpr int kAsmMaxFlag = 24;  // d_flags slot: largest |entry| of the assembled FP32 matrices (float bits)
 elrt_status tc_lu_factor_solve(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, int64_t E, int* estat, float* side,
-                               int* err, int nrhs);
+                               int* err, int nrhs, bool f16);
 elrt_status tc_lu_resolve(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, int64_t E, float* side, int* err,
-                          int nrhs);
+                          int nrhs, bool f16);
 size_t tc_lu_side_floats(const Tab& t, int64_t ld);
 
 // ---- launchers implemented in global.cu

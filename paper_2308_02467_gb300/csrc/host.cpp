@@ -411,6 +411,14 @@ elrt_status elrt_set_precond(elrt_ctx* ctx, int32_t kind) {
     return ELRT_OK;
 }
 
+elrt_status elrt_set_lu_products(elrt_ctx* ctx, int32_t mode) {
+    if (!ctx) return ctx_fail(nullptr, ELRT_EINVAL, "elrt_set_lu_products: null context");
+    if (mode != ELRT_LU_PRODUCTS_AUTO && mode != ELRT_LU_PRODUCTS_TF32)
+        return ctx_fail(ctx, ELRT_EINVAL, "elrt_set_lu_products: ELRT_LU_PRODUCTS_AUTO or ELRT_LU_PRODUCTS_TF32");
+    ctx->lu_products = mode;
+    return ELRT_OK;
+}
+
 const char* elrt_status_str(elrt_status s) {
     switch (s) {
         case ELRT_OK: return "ok";

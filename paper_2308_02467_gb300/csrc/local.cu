@@ -14,6 +14,8 @@
 #include <math.h>
 #include <stdio.h>
 
+#include <string.h>
+
 #include <algorithm>
 #include <type_traits>
 #include <string>
@@ -154,6 +156,7 @@ __global__ void __launch_bounds__(kThreads) k_assemble(Tab t, double h, const do
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     T* Me = M + e * estride;
+    float amax = 0.f;  // largest |entry| this thread wrote (FP32 candidate path)
     for (int i = warp; i < t.nm; i += kThreads / 32) {
         const int r = k * t.nm + i;
         if (rhs_out) {
@@ -198,10 +201,25 @@ __global__ void __launch_bounds__(kThreads) k_assemble(Tab t, double h, const do
                     if (m >= 0 && kk >= 0) c = t.nu + F * t.nface + m * t.half + kk;
                 }
                 if (c >= 0) {
-                    if constexpr (sizeof(T) == 4) row[c] = aug_entry_f(t, fa, k, i, c);
-                    else row[c] = (T)aug_entry(t, k, i, c, kh, om);
+                    if constexpr (sizeof(T) == 4) {
+                        const float v = aug_entry_f(t, fa, k, i, c);
+                        row[c] = v;
+                        amax = fmaxf(amax, fabsf(v));
+                    } else {
+                        row[c] = (T)aug_entry(t, k, i, c, kh, om);
+                    }
                 }
             }
+        }
+    }
+    if constexpr (sizeof(T) == 4) {
+        // the chunk's largest |entry| (float bits of a non-negative value order as unsigned ints);
+        // the common case, a block below the current maximum, reads instead of contending
+        for (int off = 16; off > 0; off >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, off));
+        if (lane == 0 && !rhs_out) {
+            unsigned* slot = reinterpret_cast<unsigned*>(flags + kAsmMaxFlag);
+            const unsigned bits = __float_as_uint(amax);
+            if (*(volatile unsigned*)slot < bits) atomicMax(slot, bits);
         }
     }
 }
@@ -1306,6 +1324,7 @@ elrt_status build_chunked(elrt_ctx* ctx, int64_t E, double h, const double* h_el
         const double* ka = kappa + e0 * t.nm;
         const double* om = omega + e0;
         s = cuda_check(ctx, cudaMemsetAsync(estat, 0, n * sizeof(int), ctx->stream), "memset status");
+        if (!s && tc) s = cuda_check(ctx, cudaMemsetAsync(ctx->d_flags + kAsmMaxFlag, 0, sizeof(int), ctx->stream), "memset max");
         if (s) return s;
         for (int64_t a0 = 0; a0 < n; a0 += 65535) {
             const int64_t m = std::min<int64_t>(65535, n - a0);
@@ -1319,8 +1338,24 @@ elrt_status build_chunked(elrt_ctx* ctx, int64_t E, double h, const double* h_el
                                                                         estride, n);
         s = cuda_check(ctx, cudaGetLastError(), "assemble launch");
         if (s) return s;
+        // 3xFP16 trailing updates when every entry of the chunk's matrices lies in [kLuF16Max / 4096,
+        // kLuF16Max] (the entries are O(1): transport 0.5 at the boundary nodes, absorption w^2 kappa_hat)
+        // and no source column rides along (its scale is the caller's); the refinement re-solves, whose
+        // right-hand sides are residuals far below O(1), keep 3xTF32
+        bool f16 = false;
+        if (tc && ctx->lu_products == ELRT_LU_PRODUCTS_AUTO && !has_src) {
+            unsigned bits = 0;
+            s = cuda_check(ctx, cudaMemcpyAsync(ctx->h_pinned, ctx->d_flags + kAsmMaxFlag, sizeof(unsigned),
+                                                cudaMemcpyDeviceToHost, ctx->stream), "read max");
+            if (!s) s = cuda_check(ctx, cudaStreamSynchronize(ctx->stream), "read max");
+            if (s) return s;
+            memcpy(&bits, ctx->h_pinned, sizeof(bits));
+            float amax;
+            memcpy(&amax, &bits, sizeof(amax));
+            f16 = amax >= kLuF16Max / 4096.f && amax <= kLuF16Max;
+        }
         if constexpr (sizeof(T) == 4) {
-            if (tc) s = tc_lu_factor_solve(ctx, M, ld, estride, n, estat, side, ctx->d_flags + 2, tl.nrhs);
+            if (tc) s = tc_lu_factor_solve(ctx, M, ld, estride, n, estat, side, ctx->d_flags + 2, tl.nrhs, f16);
             else s = run_lu<T, NB, QN>(ctx, tl, M, ld, estride, ipiv, estat, n, false);
         } else {
             s = run_lu<T, NB, QN>(ctx, tl, M, ld, estride, ipiv, estat, n, false);
@@ -1346,7 +1381,7 @@ elrt_status build_chunked(elrt_ctx* ctx, int64_t E, double h, const double* h_el
             bool pending_d = false;
             for (int it = 0; it < (ir ? steps : 0) && !s; ++it) {
                 if constexpr (sizeof(T) == 4) {
-                    if (tc) s = tc_lu_resolve(ctx, M, ld, estride, n, side, ctx->d_flags + 2, tl.nrhs);
+                    if (tc) s = tc_lu_resolve(ctx, M, ld, estride, n, side, ctx->d_flags + 2, tl.nrhs, false);
                     else s = run_lu<T, NB, QN>(ctx, tl, M, ld, estride, ipiv, estat, n, true);
                 } else {
                     s = run_lu<T, NB, QN>(ctx, tl, M, ld, estride, ipiv, estat, n, true);

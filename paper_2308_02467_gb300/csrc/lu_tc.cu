@@ -30,6 +30,7 @@
 #include <algorithm>
 #include <mutex>
 
+#include <cuda_fp16.h>
 #include <cudaTypedefs.h>
 
 #include "elrt_internal.h"
@@ -41,10 +42,18 @@ constexpr int NBP = 64;     // panel width
 constexpr int UTK = 256;    // row of the U12^T side buffer: two consecutive panels (K 0 .. 127), then
                             // the low TF32 parts of the same values (K 128 .. 255)
 constexpr int UTL = 128;    // K offset of the low parts
+// FP16 side buffer (updates with 3xFP16 products): a row holds the FP16 high parts of both panels
+// (K 0 .. 127), then the FP16 rounding of the remainders (K 128 .. 255), 512 bytes
+constexpr int UTK16 = 256;
+constexpr int UTL16 = 128;
 constexpr int UBN = 64;     // trailing-update tile width (N of the MMAs)
 constexpr int UCB = UBN / 32;  // 32-column (128-byte) boxes of a C tile
 
 __device__ __forceinline__ float tf32_hi(float a) { return __uint_as_float(__float_as_uint(a) & 0xFFFFE000u); }
+// two FP16 values in one 32-bit word, the first in the low half (the order of consecutive K)
+__device__ __forceinline__ uint32_t pack_h2(__half a, __half b) {
+    return (uint32_t)__half_as_ushort(a) | ((uint32_t)__half_as_ushort(b) << 16);
+}
 
 // ------------------------------------------------------------------------------------------------
 // panel kernels (CUDA cores)
@@ -228,7 +237,7 @@ template <int KIND, int PTILE>
 __global__ void __launch_bounds__(PTILE, RcCfg<PTILE>::PER_SM) k_rowcol(int nu, int64_t ld, int64_t estride, float* __restrict__ Mall, int J,
                                                    int jb, const float* __restrict__ Tinv, int npanels, int64_t E,
                                                    int r_begin, int r_end, int nrt, int c_begin, int c_end, int nct,
-                                                   float* __restrict__ Ut, int koff) {
+                                                   float* __restrict__ Ut, int koff, int ut16) {
     constexpr int col_mode = KIND == 2 ? 1 : 0;
     extern __shared__ __align__(16) float sm[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, t = threadIdx.x;
@@ -326,9 +335,22 @@ __global__ void __launch_bounds__(PTILE, RcCfg<PTILE>::PER_SM) k_rowcol(int nu, 
             }
             __syncthreads();
             // two columns per warp pass (a half warp per column), 16-byte stores of the value and of
-            // its low TF32 part, split once (UTK, UTL and koff are multiples of 4)
+            // its low TF32 part, split once (UTK, UTL and koff are multiples of 4); or, for the
+            // 3xFP16 updates, 8-byte stores of the FP16 high parts and of the FP16 remainders
             float* ut = Ut + e * ld * UTK + koff;
-            {
+            if (ut16) {
+                __half* uh = reinterpret_cast<__half*>(Ut) + e * ld * UTK16 + koff;
+                const int hcol = lane >> 4, q = lane & 15;
+                for (int cc = 2 * warp + hcol; cc < nc; cc += 2 * (PTILE / 32)) {
+                    const float4 v = *reinterpret_cast<const float4*>(S + cc * RS + 4 * q);
+                    const __half h0 = __float2half_rn(v.x), h1 = __float2half_rn(v.y), h2 = __float2half_rn(v.z),
+                                 h3 = __float2half_rn(v.w);
+                    const __half l0 = __float2half_rn(v.x - __half2float(h0)), l1 = __float2half_rn(v.y - __half2float(h1)),
+                                 l2 = __float2half_rn(v.z - __half2float(h2)), l3 = __float2half_rn(v.w - __half2float(h3));
+                    *reinterpret_cast<uint2*>(uh + (int64_t)(c0 + cc) * UTK16 + 4 * q) = make_uint2(pack_h2(h0, h1), pack_h2(h2, h3));
+                    *reinterpret_cast<uint2*>(uh + (int64_t)(c0 + cc) * UTK16 + UTL16 + 4 * q) = make_uint2(pack_h2(l0, l1), pack_h2(l2, l3));
+                }
+            } else {
                 const int hcol = lane >> 4, q = lane & 15;
                 for (int cc = 2 * warp + hcol; cc < nc; cc += 2 * (PTILE / 32)) {
                     const float4 v = *reinterpret_cast<const float4*>(S + cc * RS + 4 * q);
@@ -370,6 +392,10 @@ __device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_
 __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
+// kind::f16 with FP16 A and B (format code 0), FP32 D, K-major operands
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+    return (1u << 4) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
 
 // 32 consecutive 32-bit TMEM columns of this thread's lane (shape 32x32b: the warp covers the 32
 // lanes of its quarter) from registers; visible to later tcgen05 operations after tmem_st_wait
@@ -377,6 +403,16 @@ __device__ __forceinline__ void tmem_st32(uint32_t taddr, const float (&v)[32]) 
     asm volatile("tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};" ::"r"(taddr), "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])), "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])), "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])), "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])), "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])), "r"(__float_as_uint(v[15])), "r"(__float_as_uint(v[16])), "r"(__float_as_uint(v[17])), "r"(__float_as_uint(v[18])), "r"(__float_as_uint(v[19])), "r"(__float_as_uint(v[20])), "r"(__float_as_uint(v[21])), "r"(__float_as_uint(v[22])), "r"(__float_as_uint(v[23])), "r"(__float_as_uint(v[24])), "r"(__float_as_uint(v[25])), "r"(__float_as_uint(v[26])), "r"(__float_as_uint(v[27])), "r"(__float_as_uint(v[28])), "r"(__float_as_uint(v[29])), "r"(__float_as_uint(v[30])), "r"(__float_as_uint(v[31])) : "memory");
 }
 __device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// D (TMEM) (+)= A (TMEM, M x K, one row per lane, two FP16 elements of consecutive K per 32-bit
+// column, the first in the low half) x B (shared memory, FP16, K-major): K = 16 per instruction
+__device__ __forceinline__ void mma_f16_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
+                                           uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n}\n" ::"r"(
+            d_tmem),
+        "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate));
+}
 
 // D (TMEM) (+)= A (TMEM, M x K, one row per lane, one 32-bit element per column) x B (shared memory)
 __device__ __forceinline__ void mma_tf32_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
@@ -419,10 +455,11 @@ __device__ __forceinline__ void mma_tf32_ta(uint32_t d_tmem, uint32_t a_tmem, ui
 // for the first panel, 64 for the second, their low parts UTL further); an NK = 64 update reads
 // the half at K offset koff.  Every wait is bounded; on a timeout the CTA records a code in *err,
 // stops issuing work, lets its copies land and frees its TMEM.
-template <int NK>
+template <int NK, bool H = false>
 struct UpdCfg {
-    static constexpr int KB = NK / 32;             // 32-wide K boxes of a U12^T tile
-    static constexpr int U_BOX = UBN * 32 * 4;     // one box: 64 rows x 128 bytes
+    static constexpr int KW = H ? 64 : 32;         // K per 128-byte box row (FP16 or FP32)
+    static constexpr int KB = NK / KW;             // K boxes of a U12^T tile
+    static constexpr int U_BOX = UBN * 128;        // one box: 64 rows x 128 bytes
     static constexpr int U_STAGE = 2 * KB * U_BOX; // FP32 U12^T tile (KB boxes), then its low part
     static constexpr int U_TX = U_STAGE;
     static constexpr int C_BOX = 128 * 32 * 4;     // one 32-column box of the C tile
@@ -433,7 +470,9 @@ struct UpdCfg {
     static constexpr int BYTES = NU * U_STAGE + NC * C_STAGE;
     static constexpr int TOTAL = BYTES + 1024 + 512;
 };
-static_assert(UpdCfg<64>::TOTAL <= 227 * 1024 && UpdCfg<128>::TOTAL <= 227 * 1024, "trailing-update shared memory");
+static_assert(UpdCfg<64>::TOTAL <= 227 * 1024 && UpdCfg<128>::TOTAL <= 227 * 1024 &&
+                  UpdCfg<64, true>::TOTAL <= 227 * 1024 && UpdCfg<128, true>::TOTAL <= 227 * 1024,
+              "trailing-update shared memory");
 // tensor memory: accumulators at columns [0, 2 UBN); strip slot s (of kSlots): the high part of a
 // 64-column half at 2 UBN + 128 s, its low part 64 columns further
 constexpr int kSlots = 3;
@@ -450,13 +489,14 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tc::smem_u32(bar)) : "memory");
 }
 
-template <int NK>
+template <int NK, bool H>
 __global__ void __launch_bounds__(kStripThreads, 1)
     k_tc_update(const __grid_constant__ CUtensorMap tM, const __grid_constant__ CUtensorMap tU,
                 const __grid_constant__ CUtensorMap tS, float* __restrict__ Mall, int nu, int64_t ld, int64_t estride,
                 int64_t E, int J, int jb, int koff, int r0, int r_end, int c0, int c_end, int* __restrict__ err) {
-    using Cfg = UpdCfg<NK>;
-    constexpr int NU = Cfg::NU, NC = Cfg::NC, NH = Cfg::NH, KB = Cfg::KB;
+    using Cfg = UpdCfg<NK, H>;
+    constexpr int NU = Cfg::NU, NC = Cfg::NC, NH = Cfg::NH, KB = Cfg::KB, KW = Cfg::KW;
+    constexpr int ULO = H ? UTL16 : UTL;  // K offset of the low parts in the side buffer
     extern __shared__ __align__(1024) unsigned char ssm_raw[];
     unsigned char* base = (unsigned char*)(((uintptr_t)ssm_raw + 1023) & ~(uintptr_t)1023);
     unsigned char* ustage0 = base;                                  // [NU]: U12^T tile and low part (2 KB boxes)
@@ -522,8 +562,8 @@ __global__ void __launch_bounds__(kStripThreads, 1)
                 unsigned char* us = ustage0 + su * Cfg::U_STAGE;
                 tc::mbar_expect_tx(&u_full[su], Cfg::U_TX);
                 for (int kb = 0; kb < KB; ++kb) {
-                    tma_load_3d(&tU, &u_full[su], us + kb * Cfg::U_BOX, koff + kb * 32, n0, (int)e);
-                    tma_load_3d(&tU, &u_full[su], us + (KB + kb) * Cfg::U_BOX, UTL + koff + kb * 32, n0, (int)e);
+                    tma_load_3d(&tU, &u_full[su], us + kb * Cfg::U_BOX, koff + kb * KW, n0, (int)e);
+                    tma_load_3d(&tU, &u_full[su], us + (KB + kb) * Cfg::U_BOX, ULO + koff + kb * KW, n0, (int)e);
                 }
                 ++issued_u;
                 if (!tc::mbar_wait(&c_empty[sc], ((g / NC) & 1) ^ 1, abort)) {
@@ -541,7 +581,7 @@ __global__ void __launch_bounds__(kStripThreads, 1)
             *abort = 1;
         }
     } else if (warp == 1 && lane == 0) {
-        constexpr uint32_t idesc = idesc_tf32(128, UBN);
+        constexpr uint32_t idesc = H ? idesc_f16(128, UBN) : idesc_tf32(128, UBN);
         bool ok = true;
         int g = 0, i = 0;
         for (int64_t w = blockIdx.x; w < W && ok; w += gridDim.x, ++i) {
@@ -569,18 +609,31 @@ __global__ void __launch_bounds__(kStripThreads, 1)
                         tc::tc_fence_after();
                     }
                     const uint32_t a_hi = tmem + slot_col(sl, 0), a_lo = tmem + slot_col(sl, 1);
+                    if constexpr (H) {  // one 64-wide K box per half; K = 16 per instruction (8 TMEM columns, 32 bytes)
+                        const uint64_t bh = tc::sw128_desc(tc::smem_u32(us + j * Cfg::U_BOX));
+                        const uint64_t bl = tc::sw128_desc(tc::smem_u32(us + (KB + j) * Cfg::U_BOX));
 #pragma unroll
-                    for (int kq = 0; kq < 2; ++kq) {
-                        const int kb = 2 * j + kq;
-                        const uint64_t bh = tc::sw128_desc(tc::smem_u32(us + kb * Cfg::U_BOX));
-                        const uint64_t bl = tc::sw128_desc(tc::smem_u32(us + (KB + kb) * Cfg::U_BOX));
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) {  // K = 8 per instruction
-                            const uint32_t kc = (uint32_t)(kq * 32 + k * 8);
-                            mma_tf32_ta(d, a_hi + kc, bh + 2 * k, idesc, acc);
+                        for (int k = 0; k < 4; ++k) {
+                            const uint32_t kc = (uint32_t)(k * 8);
+                            mma_f16_ta(d, a_hi + kc, bh + 2 * k, idesc, acc);
                             acc = 1;
-                            mma_tf32_ta(d, a_lo + kc, bh + 2 * k, idesc, 1);
-                            mma_tf32_ta(d, a_hi + kc, bl + 2 * k, idesc, 1);
+                            mma_f16_ta(d, a_lo + kc, bh + 2 * k, idesc, 1);
+                            mma_f16_ta(d, a_hi + kc, bl + 2 * k, idesc, 1);
+                        }
+                    } else {
+#pragma unroll
+                        for (int kq = 0; kq < 2; ++kq) {
+                            const int kb = 2 * j + kq;
+                            const uint64_t bh = tc::sw128_desc(tc::smem_u32(us + kb * Cfg::U_BOX));
+                            const uint64_t bl = tc::sw128_desc(tc::smem_u32(us + (KB + kb) * Cfg::U_BOX));
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) {  // K = 8 per instruction
+                                const uint32_t kc = (uint32_t)(kq * 32 + k * 8);
+                                mma_tf32_ta(d, a_hi + kc, bh + 2 * k, idesc, acc);
+                                acc = 1;
+                                mma_tf32_ta(d, a_lo + kc, bh + 2 * k, idesc, 1);
+                                mma_tf32_ta(d, a_hi + kc, bl + 2 * k, idesc, 1);
+                            }
                         }
                     }
                 }
@@ -625,16 +678,30 @@ __global__ void __launch_bounds__(kStripThreads, 1)
                     break;
                 }
                 tc::tc_fence_after();
-#pragma unroll
-                for (int hh = 0; hh < 2; ++hh) {
+                if constexpr (H) {  // FP16 high parts and FP16 remainders, two per 32-bit column
                     float hi[32], lo[32];
 #pragma unroll
                     for (int k = 0; k < 32; ++k) {
-                        hi[k] = tf32_hi(v[hh * 32 + k]);
-                        lo[k] = v[hh * 32 + k] - hi[k];
+                        const __half h0 = __float2half_rn(v[2 * k]), h1 = __float2half_rn(v[2 * k + 1]);
+                        const __half l0 = __float2half_rn(v[2 * k] - __half2float(h0));
+                        const __half l1 = __float2half_rn(v[2 * k + 1] - __half2float(h1));
+                        hi[k] = __uint_as_float(pack_h2(h0, h1));
+                        lo[k] = __uint_as_float(pack_h2(l0, l1));
                     }
-                    tmem_st32(tmem + lane_off + slot_col(sl, 0) + hh * 32, hi);
-                    tmem_st32(tmem + lane_off + slot_col(sl, 1) + hh * 32, lo);
+                    tmem_st32(tmem + lane_off + slot_col(sl, 0), hi);
+                    tmem_st32(tmem + lane_off + slot_col(sl, 1), lo);
+                } else {
+#pragma unroll
+                    for (int hh = 0; hh < 2; ++hh) {
+                        float hi[32], lo[32];
+#pragma unroll
+                        for (int k = 0; k < 32; ++k) {
+                            hi[k] = tf32_hi(v[hh * 32 + k]);
+                            lo[k] = v[hh * 32 + k] - hi[k];
+                        }
+                        tmem_st32(tmem + lane_off + slot_col(sl, 0) + hh * 32, hi);
+                        tmem_st32(tmem + lane_off + slot_col(sl, 1) + hh * 32, lo);
+                    }
                 }
                 tmem_st_wait();
                 tc::tc_fence_before();
@@ -785,6 +852,18 @@ bool map3(CUtensorMap* m, const float* p, int64_t rows, int64_t E, int box_rows)
                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// [E][rows][UTK16] FP16 side buffer (within the same allocation), box 64 (k) x box_rows x 1 element,
+// 128-byte swizzle
+bool map3_16(CUtensorMap* m, const float* p, int64_t rows, int64_t E, int box_rows) {
+    cuuint64_t dims[3] = {(cuuint64_t)UTK16, (cuuint64_t)rows, (cuuint64_t)E};
+    cuuint64_t strides[2] = {(cuuint64_t)UTK16 * 2, (cuuint64_t)rows * UTK16 * 2};
+    cuuint32_t box[3] = {64, (cuuint32_t)box_rows, 1};
+    cuuint32_t es[3] = {1, 1, 1};
+    return g_enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 3, (void*)p, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                 CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // the matrix of every element seen as [E][rows][cols] (row pitch ld), box 32 columns x 128 rows x 1
 // element, 128-byte swizzle: with rows = nu, cols = ld the C tiles of the loads; with rows = r_end,
 // cols = c_end the stores of an update (whatever lies outside is clipped)
@@ -800,6 +879,7 @@ bool mapM(CUtensorMap* m, const float* M, int64_t rows, int64_t cols, int64_t ld
 
 struct TcMaps {
     CUtensorMap m, u;
+    bool f16;  // trailing updates with 3xFP16 products (FP16 side buffer), else 3xTF32
 };
 
 // Trailing update C -= L U over rows [r0, r_end) and columns [c0, c_end) of every element, with
@@ -816,8 +896,12 @@ elrt_status update(elrt_ctx* ctx, const TcMaps& mp, float* M, int64_t ld, int64_
     if (!mapM(&tS, M, r_end, c_end, ld, estride, E)) return ctx_fail(ctx, ELRT_EINVAL, "tensor map encoding failed");
     const int64_t items = (int64_t)((r_end - r0 + 127) / 128) * E;
     const unsigned grid = (unsigned)std::min<int64_t>(items, ctx->sms);
-    k_tc_update<NK><<<grid, kStripThreads, UpdCfg<NK>::TOTAL, ctx->stream>>>(mp.m, mp.u, tS, M, ctx->tab.nu, ld, estride,
-                                                                             E, J, jb, koff, r0, r_end, c0, c_end, err);
+    if (mp.f16)
+        k_tc_update<NK, true><<<grid, kStripThreads, UpdCfg<NK, true>::TOTAL, ctx->stream>>>(
+            mp.m, mp.u, tS, M, ctx->tab.nu, ld, estride, E, J, jb, koff, r0, r_end, c0, c_end, err);
+    else
+        k_tc_update<NK, false><<<grid, kStripThreads, UpdCfg<NK, false>::TOTAL, ctx->stream>>>(
+            mp.m, mp.u, tS, M, ctx->tab.nu, ld, estride, E, J, jb, koff, r0, r_end, c0, c_end, err);
     return cuda_check(ctx, cudaGetLastError(), "tc update launch");
 }
 
@@ -830,22 +914,30 @@ cudaError_t rowcol_attrs() {
     return e;
 }
 
-elrt_status prepare(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, const float* Ut, int64_t E, TcMaps* mp) {
+elrt_status prepare(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, const float* Ut, int64_t E, TcMaps* mp,
+                    bool f16) {
+    mp->f16 = f16;
     if (!enc_ready()) return ctx_fail(ctx, ELRT_ECUDA, "cuTensorMapEncodeTiled unavailable");
     if (E > 65535) return ctx_fail(ctx, ELRT_EINVAL, "tensor-core LU chunk above 65535 elements");
     const int nu = ctx->tab.nu;
     // every column block starts at a multiple of 64 or at nu, and the vector accesses and TMA copies
     // need each to start on a 16-byte boundary (n_angles % 4 == 0 already makes nu a multiple of 4)
     if (nu % 4 != 0 || ld % 4 != 0) return ctx_fail(ctx, ELRT_EINVAL, "tensor-core LU needs nu and ld multiples of 4");
-    if (!mapM(&mp->m, M, nu, ld, ld, estride, E) || !map3(&mp->u, Ut, ld, E, UBN))
+    if (!mapM(&mp->m, M, nu, ld, ld, estride, E) || !(f16 ? map3_16(&mp->u, Ut, ld, E, UBN) : map3(&mp->u, Ut, ld, E, UBN)))
         return ctx_fail(ctx, ELRT_EINVAL, "tensor map encoding failed");
     static bool attr_done = false;
     if (!attr_done) {
         cudaError_t e = rowcol_attrs<kRcTile>();
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_tc_update<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, UpdCfg<64>::TOTAL);
+            e = cudaFuncSetAttribute(k_tc_update<64, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, UpdCfg<64>::TOTAL);
         if (e == cudaSuccess)
-            e = cudaFuncSetAttribute(k_tc_update<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, UpdCfg<128>::TOTAL);
+            e = cudaFuncSetAttribute(k_tc_update<128, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, UpdCfg<128>::TOTAL);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_tc_update<64, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     UpdCfg<64, true>::TOTAL);
+        if (e == cudaSuccess)
+            e = cudaFuncSetAttribute(k_tc_update<128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     UpdCfg<128, true>::TOTAL);
         if (e != cudaSuccess) return cuda_check(ctx, e, "smem attribute");
         attr_done = true;
     }
@@ -856,7 +948,7 @@ int panels_of(int nu) { return (nu + NBP - 1) / NBP; }
 
 template <int PTILE>
 void rowcol_launch(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, int64_t E, int J, int jb, const float* Tinv,
-                   int r_begin, int r_end, int c_begin, int c_end, int col_mode, float* Ut, int koff) {
+                   int r_begin, int r_end, int c_begin, int c_end, int col_mode, float* Ut, int koff, int ut16) {
     using C = RcCfg<PTILE>;
     const int nrt = r_end > r_begin ? (r_end - r_begin + PTILE - 1) / PTILE : 0;
     const int nct = c_end > c_begin ? (c_end - c_begin + PTILE - 1) / PTILE : 0;
@@ -864,21 +956,22 @@ void rowcol_launch(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, int64_t
     if (nrt > 0) {  // items: (element, row tile)
         const unsigned grid = (unsigned)std::min<int64_t>(E * nrt, (int64_t)C::PER_SM * ctx->sms);
         k_rowcol<0, PTILE><<<grid, PTILE, C::SMEM, ctx->stream>>>(nu, ld, estride, M, J, jb, Tinv, np, E, r_begin, r_end,
-                                                                 nrt, c_begin, c_end, 0, Ut, koff);
+                                                                 nrt, c_begin, c_end, 0, Ut, koff, ut16);
     }
     if (nct > 0) {  // items: (element, column tile)
         const unsigned grid = (unsigned)std::min<int64_t>(E * nct, (int64_t)C::PER_SM * ctx->sms);
         if (col_mode == 0)
             k_rowcol<1, PTILE><<<grid, PTILE, C::SMEM, ctx->stream>>>(nu, ld, estride, M, J, jb, Tinv, np, E, r_begin,
-                                                                     r_end, 0, c_begin, c_end, nct, Ut, koff);
+                                                                     r_end, 0, c_begin, c_end, nct, Ut, koff, ut16);
         else
             k_rowcol<2, PTILE><<<grid, PTILE, C::SMEM, ctx->stream>>>(nu, ld, estride, M, J, jb, Tinv, np, E, r_begin,
-                                                                     r_end, 0, c_begin, c_end, nct, Ut, koff);
+                                                                     r_end, 0, c_begin, c_end, nct, Ut, koff, ut16);
     }
 }
 
-elrt_status rowcol(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, int64_t E, int J, int jb, const float* Tinv,
-                   int r_begin, int r_end, int c_begin, int c_end, int col_mode, float* Ut, int koff = 0) {
+elrt_status rowcol(elrt_ctx* ctx, const TcMaps& mp, float* M, int64_t ld, int64_t estride, int64_t E, int J, int jb,
+                   const float* Tinv, int r_begin, int r_end, int c_begin, int c_end, int col_mode, float* Ut,
+                   int koff = 0) {
     if (r_end <= r_begin && c_end <= c_begin) return ELRT_OK;
     // algorithmic work per element: row tiles read R x jb and write it back; column tiles read and
     // write jb x C and write U^T (C x 64); triangular solves with U11, L11 (unit lower) or U11
@@ -886,7 +979,8 @@ elrt_status rowcol(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, int64_t
     const double bytes = 8.0 * R * jb + 8.0 * C * jb + 4.0 * C * NBP + 4.0 * NBP * NBP * ((R > 0) + (C > 0));
     const double flops = R * jb * (jb + 1.0) + (col_mode == 0 ? C * jb * (jb - 1.0) : C * jb * (jb + 1.0));
     ProfScope ps(ctx, "lu_tc_rowcol", (R > 0) + (C > 0), (double)E * bytes, (double)E * flops);
-    rowcol_launch<kRcTile>(ctx, M, ld, estride, E, J, jb, Tinv, r_begin, r_end, c_begin, c_end, col_mode, Ut, koff);
+    rowcol_launch<kRcTile>(ctx, M, ld, estride, E, J, jb, Tinv, r_begin, r_end, c_begin, c_end, col_mode, Ut, koff,
+                           mp.f16 ? 1 : 0);
     return cuda_check(ctx, cudaGetLastError(), "rowcol launch");
 }
 
@@ -902,15 +996,15 @@ elrt_status backward_sweep_tc(elrt_ctx* ctx, const TcMaps& mp, float* M, int64_t
     const int last = ((nu - 1) / NBP) * NBP;
     for (int J = last; J >= 2 * NBP * npair; J -= NBP) {
         const int jb = std::min(NBP, nu - J);
-        elrt_status s = rowcol(ctx, M, ld, estride, E, J, jb, Tinv, 0, 0, nu, nu + nin, 1, Ut, 0);
+        elrt_status s = rowcol(ctx, mp, M, ld, estride, E, J, jb, Tinv, 0, 0, nu, nu + nin, 1, Ut, 0);
         if (!s) s = update<64>(ctx, mp, M, ld, estride, E, J, jb, 0, 0, J, nu, nu + nin, err);
         if (s) return s;
     }
     for (int q = npair - 1; q >= 0; --q) {
         const int J = 2 * NBP * q, Jb = J + NBP;
-        elrt_status s = rowcol(ctx, M, ld, estride, E, Jb, NBP, Tinv, 0, 0, nu, nu + nin, 1, Ut, NBP);
+        elrt_status s = rowcol(ctx, mp, M, ld, estride, E, Jb, NBP, Tinv, 0, 0, nu, nu + nin, 1, Ut, NBP);
         if (!s) s = update<64>(ctx, mp, M, ld, estride, E, Jb, NBP, NBP, J, Jb, nu, nu + nin, err);
-        if (!s) s = rowcol(ctx, M, ld, estride, E, J, NBP, Tinv, 0, 0, nu, nu + nin, 1, Ut, 0);
+        if (!s) s = rowcol(ctx, mp, M, ld, estride, E, J, NBP, Tinv, 0, 0, nu, nu + nin, 1, Ut, 0);
         if (!s) s = update<128>(ctx, mp, M, ld, estride, E, J, 2 * NBP, 0, 0, J, nu, nu + nin, err);
         if (s) return s;
     }
@@ -941,11 +1035,11 @@ void diag_block(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, int64_t E,
 // Factor every element's matrix without pivoting and solve for its right-hand sides (columns
 // [nu, nu + nrhs)).  side: tc_lu_side_floats() floats per element.  estat[e] |= 1 on a tiny pivot.
 elrt_status tc_lu_factor_solve(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, int64_t E, int* estat, float* side,
-                               int* err, int nrhs) {
+                               int* err, int nrhs, bool f16) {
     const int nu = ctx->tab.nu, ncols = nu + nrhs;
     const Side sd = carve(side, E, ld);
     TcMaps mp;
-    elrt_status s = prepare(ctx, M, ld, estride, sd.Ut, E, &mp);
+    elrt_status s = prepare(ctx, M, ld, estride, sd.Ut, E, &mp, f16);
     if (s) return s;
     int J = 0;
     // pairs of full panels a = [J, J+64), b = [J+64, J+128): panel a is factored and applied to
@@ -954,12 +1048,12 @@ elrt_status tc_lu_factor_solve(elrt_ctx* ctx, float* M, int64_t ld, int64_t estr
     for (; ctx->tune.lu_pairs && J + 2 * NBP <= nu; J += 2 * NBP) {
         const int Jb = J + NBP, Jn = J + 2 * NBP;
         diag_block(ctx, M, ld, estride, E, J, NBP, sd.Tinv, estat);
-        s = rowcol(ctx, M, ld, estride, E, J, NBP, sd.Tinv, Jb, nu, Jb, ncols, 0, sd.Ut, 0);
+        s = rowcol(ctx, mp, M, ld, estride, E, J, NBP, sd.Tinv, Jb, nu, Jb, ncols, 0, sd.Ut, 0);
         if (!s) s = update<64>(ctx, mp, M, ld, estride, E, J, NBP, 0, Jb, nu, Jb, Jn, err);
         if (!s) s = update<64>(ctx, mp, M, ld, estride, E, J, NBP, 0, Jb, Jn, Jn, ncols, err);
         if (s) return s;
         diag_block(ctx, M, ld, estride, E, Jb, NBP, sd.Tinv, estat);
-        s = rowcol(ctx, M, ld, estride, E, Jb, NBP, sd.Tinv, Jn, nu, Jn, ncols, 0, sd.Ut, NBP);
+        s = rowcol(ctx, mp, M, ld, estride, E, Jb, NBP, sd.Tinv, Jn, nu, Jn, ncols, 0, sd.Ut, NBP);
         if (!s) s = update<128>(ctx, mp, M, ld, estride, E, J, 2 * NBP, 0, Jn, nu, Jn, ncols, err);
         if (s) return s;
     }
@@ -967,7 +1061,7 @@ elrt_status tc_lu_factor_solve(elrt_ctx* ctx, float* M, int64_t ld, int64_t estr
     for (; J < nu; J += NBP) {
         const int jb = std::min(NBP, nu - J);
         diag_block(ctx, M, ld, estride, E, J, jb, sd.Tinv, estat);
-        s = rowcol(ctx, M, ld, estride, E, J, jb, sd.Tinv, J + jb, nu, J + jb, ncols, 0, sd.Ut, 0);
+        s = rowcol(ctx, mp, M, ld, estride, E, J, jb, sd.Tinv, J + jb, nu, J + jb, ncols, 0, sd.Ut, 0);
         if (!s) s = update<64>(ctx, mp, M, ld, estride, E, J, jb, 0, J + jb, nu, J + jb, ncols, err);
         if (s) return s;
     }
@@ -976,26 +1070,26 @@ elrt_status tc_lu_factor_solve(elrt_ctx* ctx, float* M, int64_t ld, int64_t estr
 
 // Re-solve A D = R for the right-hand sides in columns [nu, nu + nrhs) with the stored factors.
 elrt_status tc_lu_resolve(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, int64_t E, float* side, int* err,
-                          int nrhs) {
+                          int nrhs, bool f16) {
     const int nu = ctx->tab.nu, nin = nrhs;
     const Side sd = carve(side, E, ld);
     TcMaps mp;
-    elrt_status s = prepare(ctx, M, ld, estride, sd.Ut, E, &mp);
+    elrt_status s = prepare(ctx, M, ld, estride, sd.Ut, E, &mp, f16);
     if (s) return s;
     int J = 0;
     // forward substitution with the unit lower factor, in the factorisation's panel pairs: X_a, the
     // rank-64 update of panel b's rows, X_b, one rank-128 update of the rows below the pair
     for (; ctx->tune.lu_pairs && J + 2 * NBP <= nu; J += 2 * NBP) {
         const int Jb = J + NBP, Jn = J + 2 * NBP;
-        s = rowcol(ctx, M, ld, estride, E, J, NBP, sd.Tinv, 0, 0, nu, nu + nin, 0, sd.Ut, 0);
+        s = rowcol(ctx, mp, M, ld, estride, E, J, NBP, sd.Tinv, 0, 0, nu, nu + nin, 0, sd.Ut, 0);
         if (!s) s = update<64>(ctx, mp, M, ld, estride, E, J, NBP, 0, Jb, Jn, nu, nu + nin, err);
-        if (!s) s = rowcol(ctx, M, ld, estride, E, Jb, NBP, sd.Tinv, 0, 0, nu, nu + nin, 0, sd.Ut, NBP);
+        if (!s) s = rowcol(ctx, mp, M, ld, estride, E, Jb, NBP, sd.Tinv, 0, 0, nu, nu + nin, 0, sd.Ut, NBP);
         if (!s) s = update<128>(ctx, mp, M, ld, estride, E, J, 2 * NBP, 0, Jn, nu, nu, nu + nin, err);
         if (s) return s;
     }
     for (; J < nu; J += NBP) {
         const int jb = std::min(NBP, nu - J);
-        s = rowcol(ctx, M, ld, estride, E, J, jb, sd.Tinv, 0, 0, nu, nu + nin, 0, sd.Ut, 0);
+        s = rowcol(ctx, mp, M, ld, estride, E, J, jb, sd.Tinv, 0, 0, nu, nu + nin, 0, sd.Ut, 0);
         if (!s) s = update<64>(ctx, mp, M, ld, estride, E, J, jb, 0, J + jb, nu, nu, nu + nin, err);
         if (s) return s;
     }

@@ -112,6 +112,8 @@ extern "C" elrt_status elrt_solve_batch(elrt_ctx* const* ctxs, int32_t n_ctx, co
             first = elrt_create(&wctx[w][k], &ctxs[k]->disc, streams[w]);
             if (!first) {
                 wctx[w][k]->krylov_op = ctxs[k]->krylov_op;
+                wctx[w][k]->precond = ctxs[k]->precond;
+                wctx[w][k]->lu_products = ctxs[k]->lu_products;
                 wctx[w][k]->graphs = ctxs[k]->graphs;
                 wctx[w][k]->tune = ctxs[k]->tune;
             }

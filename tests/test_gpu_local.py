@@ -232,3 +232,32 @@ def test_small_batch_matches_large_batch(lib, mode):
         assert np.array_equal(a_few, a_all[pick]) and np.array_equal(b_few, b_all[pick]), refine
         assert st_few.n_flagged == 0 and st_all.n_flagged == 0
         assert st_few.max_rel_residual <= st_all.max_rel_residual
+
+
+@pytest.mark.parametrize("p,N,ang,n", [CASES[1], CASES[3], CASES[4]])
+def test_local_lu_products_fp16_and_tf32(lib, p, N, ang, n):
+    """The trailing updates of the factorisation with 3xFP16 products (the default when the
+    assembled entries lie in FP16's range) and with 3xTF32: before refinement both at FP32-level
+    accuracy and different from each other (so the FP16 path ran), after two refinement sweeps both
+    at the FP64 oracle to 1e-10."""
+    import torch
+    kappa, omega, h = H.random_elements(n, p, seed=p * 10 + N + 5)
+    ctx = _ctx(lib, p, N, 0.85, ang)
+    k, o = torch.tensor(kappa, device="cuda"), torch.tensor(omega, device="cuda")
+    _, (o_i2o, o_i2m) = _oracle_ops(p, N, 0.85, ang, kappa, omega, h)
+    out = {}
+    for prod in (lib.LU_PRODUCTS_TF32, lib.LU_PRODUCTS_AUTO):
+        ctx.elrt_set_lu_products(prod)
+        i2o = torch.empty(n, ctx.nin, ctx.nin, dtype=torch.float64, device="cuda")
+        i2m = torch.empty(n, ctx.nm, ctx.nin, dtype=torch.float64, device="cuda")
+        ctx.elrt_build_local(k, o, h, i2o, i2m, mode=lib.LOCAL_TF32_IR, refine_steps=0)
+        a0 = i2o.cpu().numpy()
+        st = ctx.elrt_build_local(k, o, h, i2o, i2m, mode=lib.LOCAL_TF32_IR, refine_steps=2)
+        out[prod] = (a0, np.abs(a0 - o_i2o).max(), np.abs(i2o.cpu().numpy() - o_i2o).max(), st,
+                     np.abs(i2m.cpu().numpy() - o_i2m).max())
+    a_t, e0_t, e2_t, st_t, m_t = out[lib.LU_PRODUCTS_TF32]
+    a_h, e0_h, e2_h, st_h, m_h = out[lib.LU_PRODUCTS_AUTO]
+    assert not np.array_equal(a_t, a_h)                      # the two product forms differ before refinement
+    assert e0_t < 1e-4 and e0_h < 1e-4 and e0_h < 10 * e0_t + 1e-7, (e0_t, e0_h)
+    assert e2_t < 1e-10 and e2_h < 1e-10 and m_t < 1e-10 and m_h < 1e-10, (e2_t, e2_h, m_t, m_h)
+    assert st_t.n_flagged == 0 and st_h.n_flagged == 0 and st_h.max_rel_residual < 1e-12
