@@ -111,8 +111,9 @@ elrt_status local_build(elrt_ctx* ctx, int64_t E, double h, const double* h_elem
                         const elrt_local_extras* extras = nullptr);
 
 // ---- tensor-core LU (lu_tc.cu).  f16: the trailing updates form their products as 3xFP16 (FP16
-// high parts and remainders, half the MMA instructions of 3xTF32), allowed when every entry of the
-// assembled matrices lies within kLuF16Max; a re-solve must use the factorisation's setting.
+// high parts and remainders, half the MMA instructions of 3xTF32), allowed for a factorisation when
+// every entry of the assembled matrices lies in [kLuF16Max / 4096, kLuF16Max]; the refinement
+// re-solves pass false (their right-hand sides are residuals far below FP16's normal range).
 constexpr float kLuF16Max = 1024.f;
 constexpr int kAsmMaxFlag = 24;  // d_flags slot: largest |entry| of the assembled FP32 matrices (float bits)
 elrt_status tc_lu_factor_solve(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, int64_t E, int* estat, float* side,
