@@ -59,8 +59,8 @@ def tensor_peak_tflops(peaks):
 # missing here has no capture of its current kernel.  Scaled to a launch of the benchmark by
 # elements / launches.
 DRAM_BYTES_PER_ELEMENT_STEP = {
-    "lu_tc_update": 4.916e7, "lu_tc_rowcol": 1.666e7, "lu_tc_diag": 3.261e5, "residual": 2.967e6,
-    "assemble": 3.273e6, "restrict": 2.905e6,
+    "lu_tc_update": 4.595e7, "lu_tc_rowcol": 1.382e7, "lu_tc_diag": 3.275e5, "residual": 3.704e6,
+    "assemble": 3.174e6, "restrict": 2.905e6,
 }
 
 
