@@ -97,3 +97,38 @@ def test_fp32_ir_thick_and_thin_elements_match_oracle(lib):
     assert st.n_flagged == 0
     np.testing.assert_allclose(a, o_i2o, atol=1e-10)
     np.testing.assert_allclose(m, o_i2m, atol=1e-10)
+
+
+def test_fp16_products_on_thick_and_thin_elements(lib):
+    """The 3xFP16 factorisation updates (ELRT_LU_PRODUCTS_AUTO) on thick and thin elements whose
+    assembled entries stay within its range (kappa_hat from ~1e-5 to 1.5e3): the same bars as the
+    3xTF32 path above, and a result before refinement that differs from the 3xTF32 one (so the FP16
+    path ran)."""
+    import torch
+    p, N, n = 6, 16, 14
+    kappa, omega, h = H.thick_and_thin_elements(n, p, seed=211)
+    kappa = np.minimum(kappa, 3.0e3 / h[:, None])  # kappa_hat = kappa h / 2 <= 1.5e3
+    o_i2o, o_i2m = _oracle(p, N, kappa, omega, h)
+
+    def build(prod, refine, dtype):
+        ctx = lib.Context(p, N, 0.85, lib.ANG_FV0)
+        ctx.elrt_set_lu_products(prod)
+        i2o = torch.empty(n, ctx.nin, ctx.nin, dtype=dtype, device="cuda")
+        i2m = torch.empty(n, ctx.nm, ctx.nin, dtype=dtype, device="cuda")
+        st = ctx.elrt_build_local(torch.tensor(kappa, device="cuda"), torch.tensor(omega, device="cuda"), 1.0, i2o,
+                                  i2m, mode=lib.LOCAL_TF32_IR, refine_steps=refine, h_elem=torch.tensor(h, device="cuda"))
+        out = i2o.double().cpu().numpy(), i2m.double().cpu().numpy(), st
+        ctx.close()
+        return out
+
+    a16, _, _ = build(lib.LU_PRODUCTS_AUTO, 0, torch.float64)
+    a32, _, _ = build(lib.LU_PRODUCTS_TF32, 0, torch.float64)
+    assert not np.array_equal(a16, a32)
+    a, m, st = build(lib.LU_PRODUCTS_AUTO, 1, torch.float32)
+    assert st.n_flagged == 0, st.n_flagged
+    np.testing.assert_allclose(a, o_i2o, atol=2e-6, rtol=2e-6)
+    np.testing.assert_allclose(m, o_i2m, atol=2e-6, rtol=2e-6)
+    a, m, st = build(lib.LU_PRODUCTS_AUTO, 2, torch.float64)
+    assert st.n_flagged == 0 and st.max_rel_residual < 1e-12, st.max_rel_residual
+    np.testing.assert_allclose(a, o_i2o, atol=1e-10)
+    np.testing.assert_allclose(m, o_i2m, atol=1e-10)
