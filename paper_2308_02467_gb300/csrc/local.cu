@@ -1152,9 +1152,11 @@ double residual_bytes(const Tab& t, size_t st, int mode, int64_t n) {
 double residual_flops(const Tab& t, int mode, int64_t n) {
     return mode == 2 ? (double)t.nu * t.nin * n : 2.0 * (1 + 2 * t.n1 + t.N) * (double)t.nu * t.nin * n;
 }
-// restriction: reads the nin outgoing rows and all nu rows of X, writes in2out and in2sol
+// restriction, algorithmic bytes: every row of the solution read once (the kernels read the outgoing
+// rows a second time, for the angular means; a one-pass variant was slower), in2out and in2sol
+// written once
 double restrict_bytes(const Tab& t, size_t ss, size_t so, int64_t n) {
-    return ((double)(t.nin + t.nu) * t.nin * ss + (double)(t.nin + t.nm) * t.nin * so) * (double)n;
+    return ((double)t.nu * t.nin * ss + (double)(t.nin + t.nm) * t.nin * so) * (double)n;
 }
 
 // t: the context's table with nrhs set to the right-hand-side columns of this build
