@@ -13,8 +13,10 @@
 //                      back to the matrix; U12 from L11 U12 = A12 written back to the matrix and,
 //                      transposed (K-major), to one FP32 side buffer whose rows hold both panels of
 //                      the pair.  On the right-hand-side columns this is the forward substitution;
-//   k_tc_update<NK>    (tensor cores): C -= L21 U12 with three TF32 products hi*hi + hi*lo +
-//                      lo*hi (FP32-level accuracy).  Panel a is applied with rank 64 to panel b's
+//   k_tc_update<NK, H> (tensor cores): C -= L21 U12 with three products hi*hi + hi*lo + lo*hi of
+//                      TF32 parts or (H, the factorisation when the entries fit FP16's range) FP16
+//                      parts, both FP32-level accuracy; FP16 needs half the MMA instructions (K = 16
+//                      per instruction against 8).  Panel a is applied with rank 64 to panel b's
 //                      columns and rows only; once panel b is factored, the rest of the matrix
 //                      takes both panels in one rank-128 update, which moves the C tiles half as
 //                      often as two rank-64 updates.  The FP32 operands come in by TMA (U12^T from
@@ -425,7 +427,8 @@ __device__ __forceinline__ void mma_tf32_ta(uint32_t d_tmem, uint32_t a_tmem, ui
 
 
 // Persistent trailing update C -= L U of rank NK = 64 (one panel) or 128 (two consecutive panels,
-// the second already factored against the first): one CTA per SM walks the work items (element,
+// the second already factored against the first; H: FP16 operands, as the notes after the role
+// list say): one CTA per SM walks the work items (element,
 // 128-row strip) of the launch, the strips of one element consecutively (their U12^T tiles are
 // shared through L2).  The L21 strip of an item (columns J .. J+NK-1 of its 128 rows, FP32,
 // straight from the matrix) lives in tensor memory as TF32 high and low parts, in 64-column halves
@@ -453,7 +456,9 @@ __device__ __forceinline__ void mma_tf32_ta(uint32_t d_tmem, uint32_t a_tmem, ui
 //                writes it to its TMEM lane (tcgen05.st).
 // U12^T comes from the side buffer [E][ld][UTK] (column-major U12 of the panel pair: K offset 0
 // for the first panel, 64 for the second, their low parts UTL further); an NK = 64 update reads
-// the half at K offset koff.  Every wait is bounded; on a timeout the CTA records a code in *err,
+// the half at K offset koff.  With H the side buffer is FP16 ([E][ld][UTK16], the FP16 roundings
+// and those of the remainders), the strip preparation packs two FP16 values per TMEM column, and
+// an MMA covers K = 16 with the same TMEM-column and descriptor strides as a TF32 one of K = 8.  Every wait is bounded; on a timeout the CTA records a code in *err,
 // stops issuing work, lets its copies land and frees its TMEM.
 template <int NK, bool H = false>
 struct UpdCfg {
