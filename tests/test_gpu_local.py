@@ -261,3 +261,12 @@ def test_local_lu_products_fp16_and_tf32(lib, p, N, ang, n):
     assert e0_t < 1e-4 and e0_h < 1e-4 and e0_h < 10 * e0_t + 1e-7, (e0_t, e0_h)
     assert e2_t < 1e-10 and e2_h < 1e-10 and m_t < 1e-10 and m_h < 1e-10, (e2_t, e2_h, m_t, m_h)
     assert st_t.n_flagged == 0 and st_h.n_flagged == 0 and st_h.max_rel_residual < 1e-12
+
+
+def test_lu_products_setting_rejects_other_values(lib):
+    ctx = _ctx(lib, 4, 8, 0.85, "fv0")
+    ctx.elrt_set_lu_products(lib.LU_PRODUCTS_TF32)
+    ctx.elrt_set_lu_products(lib.LU_PRODUCTS_AUTO)
+    for bad in (-1, 2, 7):
+        with pytest.raises(lib.ElrtError):
+            ctx.elrt_set_lu_products(bad)
