@@ -390,7 +390,8 @@ elrt_status elrt_solve_batch(elrt_ctx* const* ctxs, int32_t n_ctx, const elrt_fi
 
 /* Launch parameters the library picks per discretisation, and an autotuner that measures them (the
  * paper has no counterpart: these are implementation choices of this library):
- *   local_chunk  elements per local-build chunk (0: as many as 16 GB of workspace hold);
+ *   local_chunk  elements per local-build chunk (0: as many as the workspace budget holds: an
+ *                eighth of the device memory, at most 32 GB);
  *   lu_pairs     tensor-core LU schedule: 1 = panels in pairs, the second factored after a rank-64
  *                update of its rows and columns, the rest of the matrix updated by both with one
  *                rank-128 tensor-core update; 0 = panels one at a time with rank-64 updates;

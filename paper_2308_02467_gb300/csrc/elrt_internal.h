@@ -40,7 +40,7 @@ __host__ __device__ inline int face_node(int F, int m, int p) {
 
 // Launch parameters the autotuner (tune.cpp) measures and sets; the defaults are the hand-chosen ones.
 struct Tuning {
-    int64_t local_chunk = 0;  // elements per local-build chunk (0: as many as 16 GB of workspace hold)
+    int64_t local_chunk = 0;  // elements per local-build chunk (0: as many as the workspace budget holds)
     int lu_pairs = 1;         // tensor-core LU: panels in pairs with rank-128 updates (1) or one at a time (0)
     int restart = 12;         // GMRES restart length of calls that pass restart = 0
     int tuned = 0;            // 1 once measured or loaded from the cache
@@ -53,6 +53,7 @@ struct elrt_ctx {
     cudaStream_t stream;
     int device;
     int sms = 152;  // streaming multiprocessors of the device (persistent grids are sized on it)
+    size_t dev_bytes = (size_t)128 << 30;  // device memory (the local build's workspace is sized on it)
     std::string last_error;
     // workspace (grown on demand)
     void* ws = nullptr;

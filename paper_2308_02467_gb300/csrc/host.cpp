@@ -355,6 +355,11 @@ elrt_status elrt_create(elrt_ctx** out, const elrt_disc* disc, void* stream) {
     c->stream = (cudaStream_t)stream;
     cudaError_t e = cudaGetDevice(&c->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
+    if (e == cudaSuccess) {
+        cudaDeviceProp prop;
+        e = cudaGetDeviceProperties(&prop, c->device);
+        if (e == cudaSuccess) c->dev_bytes = prop.totalGlobalMem;
+    }
     if (e == cudaSuccess) e = cudaMalloc(&c->d_flags, 256 * sizeof(int));
     if (e == cudaSuccess) e = cudaMallocHost(&c->h_pinned, 4096);
     if (e != cudaSuccess) {

@@ -1297,7 +1297,9 @@ elrt_status build_chunked(elrt_ctx* ctx, int64_t E, double h, const double* h_el
     const size_t src_per = (has_src && ir) ? (size_t)t.nu * sizeof(double) : 0;  // refined source column
     const size_t per = estride * sizeof(T) + t.nu * sizeof(int) + sizeof(int) + sizeof(double) +
                        (want_res ? (size_t)t.nu * t.nin * sizeof(double) : 0) + side_per + src_per;
-    const size_t budget = (size_t)16 << 30;
+    // workspace of one chunk: an eighth of the device memory, at most 32 GB (4096 elements at p = 6,
+    // N = 16 on a 288 GB device: one chunk for a 64 x 64 field, half the launches of 16 GB chunks)
+    const size_t budget = std::min<size_t>((size_t)32 << 30, ctx->dev_bytes / 8);
     int64_t chunk = std::max<int64_t>(1, std::min<int64_t>(E, (int64_t)(budget / per)));
     if (ctx->tune.local_chunk > 0) chunk = std::min<int64_t>(chunk, ctx->tune.local_chunk);
     if (chunk < E) {  // balance the chunks
