@@ -192,7 +192,7 @@ const char* elrt_last_error(const elrt_ctx* ctx);   /* message of the last faili
  * launch of its kernels and, at the next synchronisation inside a call, adds the elapsed times to
  * per-kernel totals.  elrt_profile_get returns the total milliseconds and the number of timed
  * launches of one kernel group ("assemble", "lu_factor_solve", "lu_resolve", "lu_tc_diag",
- * "lu_tc_rowcol", "lu_tc_update", "residual", "restrict", "status", "gemv", "krylov",
+ * "lu_tc_rowcol", "lu_tc_update", "residual", "restrict", "status", "gemv", "krylov", "sweep",
  * "estimate"); unknown names give 0.  elrt_profile_work returns, for the same timed launches, the
  * algorithmic bytes (every operand read once and every result written once, at the width the
  * kernel stores it) and the useful flops the library counts for them (0 where a group has no
