@@ -889,8 +889,9 @@ struct TcMaps {
 
 // Trailing update C -= L U over rows [r0, r_end) and columns [c0, c_end) of every element, with
 // L = M[rows, J .. J+k) and U^T from the side buffer at K offset koff: rank k = jb <= 64 (one panel,
-// kernel NK = 64) or k = 128 (a pair of full panels, NK = 128, koff 0).  Algorithmic bytes: C read
-// and written, the FP32 L strip (R x k) and U^T tile (C x k); useful flops 2 R C k.
+// kernel NK = 64) or 64 < k <= 128 (a pair of panels, the second possibly partial, NK = 128, koff 0;
+// the strip is zero beyond jb).  Algorithmic bytes: C read and written, the FP32 L strip (R x k) and
+// U^T tile (C x k); useful flops 2 R C k.
 template <int NK>
 elrt_status update(elrt_ctx* ctx, const TcMaps& mp, float* M, int64_t ld, int64_t estride, int64_t E, int J, int jb,
                    int koff, int r0, int r_end, int c0, int c_end, int* err) {
@@ -990,14 +991,39 @@ elrt_status rowcol(elrt_ctx* ctx, const TcMaps& mp, float* M, int64_t ld, int64_
 }
 
 // backward substitution on the right-hand-side columns: X_J = U11^{-1} X_J, then the rows above
-// lose U[0..J, J..J+jb) X_J.  With the pair schedule, the panels beyond the last pair go first, one
-// at a time; then per pair (a, b), last pair first: X_b, the rank-64 update of panel a's rows,
-// X_a, and one rank-128 update of the rows above the pair (both panels' solutions, side buffer K
-// offsets 0 and 64).
+// lose U[0..J, J..J+jb) X_J.  With the pair schedule, per pair (a, b), last pair first: X_b, the
+// rank-64 update of panel a's rows, X_a, and one rank-128 update of the rows above the pair (both
+// panels' solutions, side buffer K offsets 0 and 64).  A last panel narrower than a pair joins the
+// last pair's second panel (the grouped form below); otherwise the panels beyond the last pair go
+// first, one at a time.
 elrt_status backward_sweep_tc(elrt_ctx* ctx, const TcMaps& mp, float* M, int64_t ld, int64_t estride, int64_t E,
                               const float* Tinv, float* Ut, int* err, int nin) {
     const int nu = ctx->tab.nu;
     const int npair = ctx->tune.lu_pairs ? nu / (2 * NBP) : 0;
+    const int rem = nu - 2 * NBP * npair;  // columns beyond the last pair
+    if (npair > 0 && rem > 0 && rem <= NBP) {
+        // the last panel t (rem columns, e.g. 16 of nu = 784) joins the panel b before it: X_t, b's
+        // rows lose U[b, t] X_t, X_b, and the rows above b take both in one update of rank 64 + rem
+        // (the strip is masked beyond jb, and t's side-buffer slots beyond rem hold zeros: its
+        // diagonal block is padded with the identity).  The panels below b then pair up shifted by
+        // one, [J, J + 128) for J = 128 q - 64, and panel 0 is solved alone, with no rows above it.
+        // Against t on its own, one rank-rem update of all nu - rem rows above t becomes a narrow
+        // one of b's 64 rows; the shifted pairs' updates cover 64 rows more each.
+        const int Jt = 2 * NBP * npair, Jb = Jt - NBP;
+        elrt_status s = rowcol(ctx, mp, M, ld, estride, E, Jt, rem, Tinv, 0, 0, nu, nu + nin, 1, Ut, NBP);
+        if (!s) s = update<64>(ctx, mp, M, ld, estride, E, Jt, rem, NBP, Jb, Jt, nu, nu + nin, err);
+        if (!s) s = rowcol(ctx, mp, M, ld, estride, E, Jb, NBP, Tinv, 0, 0, nu, nu + nin, 1, Ut, 0);
+        if (!s) s = update<128>(ctx, mp, M, ld, estride, E, Jb, NBP + rem, 0, 0, Jb, nu, nu + nin, err);
+        for (int J = Jb - 2 * NBP; J >= 0 && !s; J -= 2 * NBP) {
+            const int Jh = J + NBP;
+            s = rowcol(ctx, mp, M, ld, estride, E, Jh, NBP, Tinv, 0, 0, nu, nu + nin, 1, Ut, NBP);
+            if (!s) s = update<64>(ctx, mp, M, ld, estride, E, Jh, NBP, NBP, J, Jh, nu, nu + nin, err);
+            if (!s) s = rowcol(ctx, mp, M, ld, estride, E, J, NBP, Tinv, 0, 0, nu, nu + nin, 1, Ut, 0);
+            if (!s) s = update<128>(ctx, mp, M, ld, estride, E, J, 2 * NBP, 0, 0, J, nu, nu + nin, err);
+        }
+        if (!s) s = rowcol(ctx, mp, M, ld, estride, E, 0, NBP, Tinv, 0, 0, nu, nu + nin, 1, Ut, 0);
+        return s;
+    }
     const int last = ((nu - 1) / NBP) * NBP;
     for (int J = last; J >= 2 * NBP * npair; J -= NBP) {
         const int jb = std::min(NBP, nu - J);
