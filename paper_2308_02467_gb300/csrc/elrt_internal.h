@@ -120,7 +120,7 @@ constexpr int kAsmMaxFlag = 24;  // d_flags slot: largest |entry| of the assembl
 elrt_status tc_lu_factor_solve(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, int64_t E, int* estat, float* side,
                                int* err, int nrhs, bool f16);
 elrt_status tc_lu_resolve(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, int64_t E, float* side, int* err,
-                          int nrhs, bool f16);
+                          int nrhs, bool f16, const double* res_max);
 size_t tc_lu_side_floats(const Tab& t, int64_t ld);
 
 // ---- launchers implemented in global.cu

@@ -1344,8 +1344,9 @@ elrt_status build_chunked(elrt_ctx* ctx, int64_t E, double h, const double* h_el
         if (s) return s;
         // 3xFP16 trailing updates when every entry of the chunk's matrices lies in [kLuF16Max / 4096,
         // kLuF16Max] (the entries are O(1): transport 0.5 at the boundary nodes, absorption w^2 kappa_hat)
-        // and no source column rides along (its scale is the caller's); the refinement re-solves, whose
-        // right-hand sides are residuals far below O(1), keep 3xTF32
+        // and no source column rides along (its scale is the caller's); the refinement re-solves then
+        // run their forward sweep in 3xFP16 too, each element's residual scaled by a power of two into
+        // [0.5, 1), and their backward sweep in 3xTF32
         bool f16 = false;
         if (tc && ctx->lu_products == ELRT_LU_PRODUCTS_AUTO && !has_src) {
             unsigned bits = 0;
@@ -1385,7 +1386,7 @@ elrt_status build_chunked(elrt_ctx* ctx, int64_t E, double h, const double* h_el
             bool pending_d = false;
             for (int it = 0; it < (ir ? steps : 0) && !s; ++it) {
                 if constexpr (sizeof(T) == 4) {
-                    if (tc) s = tc_lu_resolve(ctx, M, ld, estride, n, side, ctx->d_flags + 2, tl.nrhs, false);
+                    if (tc) s = tc_lu_resolve(ctx, M, ld, estride, n, side, ctx->d_flags + 2, tl.nrhs, f16, maxres);
                     else s = run_lu<T, NB, QN>(ctx, tl, M, ld, estride, ipiv, estat, n, true);
                 } else {
                     s = run_lu<T, NB, QN>(ctx, tl, M, ld, estride, ipiv, estat, n, true);

@@ -235,11 +235,25 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 
 // KIND: 0 = row tiles (factorisation), 1 = column tiles of the factorisation / forward sweep,
 // 2 = column tiles of the backward sweep; one unrolled solve per instantiation
+// Scale of an element's FP16 operands in a refinement re-solve: the power of two that brings its
+// largest residual entry into [0.5, 1), so that the residual and its forward substitution sit in
+// FP16's normal range (residuals are ~1e-7 of the O(1) right-hand sides); 1 without a residual
+// (the factorisation) or for a zero or non-finite one.  Powers of two scale and unscale exactly.
+__device__ __forceinline__ float res_scale(const double* __restrict__ res_max, int64_t e) {
+    if (!res_max) return 1.f;
+    const double v = res_max[e];
+    if (!(v > 0.0) || !isfinite(v)) return 1.f;
+    int ex;
+    frexp(v, &ex);  // v = f 2^ex, f in [0.5, 1)
+    return ldexpf(1.f, -max(-120, min(120, ex)));
+}
+
 template <int KIND, int PTILE>
 __global__ void __launch_bounds__(PTILE, RcCfg<PTILE>::PER_SM) k_rowcol(int nu, int64_t ld, int64_t estride, float* __restrict__ Mall, int J,
                                                    int jb, const float* __restrict__ Tinv, int npanels, int64_t E,
                                                    int r_begin, int r_end, int nrt, int c_begin, int c_end, int nct,
-                                                   float* __restrict__ Ut, int koff, int ut16) {
+                                                   float* __restrict__ Ut, int koff, int ut16,
+                                                   const double* __restrict__ res_max) {
     constexpr int col_mode = KIND == 2 ? 1 : 0;
     extern __shared__ __align__(16) float sm[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, t = threadIdx.x;
@@ -343,8 +357,11 @@ __global__ void __launch_bounds__(PTILE, RcCfg<PTILE>::PER_SM) k_rowcol(int nu, 
             if (ut16) {
                 __half* uh = reinterpret_cast<__half*>(Ut) + e * ld * UTK16 + koff;
                 const int hcol = lane >> 4, q = lane & 15;
+                // the forward sweep of a scaled re-solve (kind 1); 1 in the factorisation
+                const float sc = KIND == 1 ? res_scale(res_max, e) : 1.f;
                 for (int cc = 2 * warp + hcol; cc < nc; cc += 2 * (PTILE / 32)) {
-                    const float4 v = *reinterpret_cast<const float4*>(S + cc * RS + 4 * q);
+                    float4 v = *reinterpret_cast<const float4*>(S + cc * RS + 4 * q);
+                    v = make_float4(v.x * sc, v.y * sc, v.z * sc, v.w * sc);
                     const __half h0 = __float2half_rn(v.x), h1 = __float2half_rn(v.y), h2 = __float2half_rn(v.z),
                                  h3 = __float2half_rn(v.w);
                     const __half l0 = __float2half_rn(v.x - __half2float(h0)), l1 = __float2half_rn(v.y - __half2float(h1)),
@@ -498,7 +515,8 @@ template <int NK, bool H>
 __global__ void __launch_bounds__(kStripThreads, 1)
     k_tc_update(const __grid_constant__ CUtensorMap tM, const __grid_constant__ CUtensorMap tU,
                 const __grid_constant__ CUtensorMap tS, float* __restrict__ Mall, int nu, int64_t ld, int64_t estride,
-                int64_t E, int J, int jb, int koff, int r0, int r_end, int c0, int c_end, int* __restrict__ err) {
+                int64_t E, int J, int jb, int koff, int r0, int r_end, int c0, int c_end, int* __restrict__ err,
+                const double* __restrict__ res_max) {
     using Cfg = UpdCfg<NK, H>;
     constexpr int NU = Cfg::NU, NC = Cfg::NC, NH = Cfg::NH, KB = Cfg::KB, KW = Cfg::KW;
     constexpr int ULO = H ? UTL16 : UTL;  // K offset of the low parts in the side buffer
@@ -753,6 +771,8 @@ __global__ void __launch_bounds__(kStripThreads, 1)
         int g = 0;
         bool ok = true;
         for (int64_t w = blockIdx.x; w < W && ok; w += gridDim.x) {
+            // the U^T tiles of a scaled re-solve carry the element's residual scale: undo it here
+            const float unscale = 1.f / res_scale(res_max, w / nstrips);
             for (int t = 0; t < ntile; ++t, ++g) {
                 const int sc = g % NC, a = g & 1;
                 ok = __all_sync(0xffffffffu, tc::mbar_wait(&acc_full[a], (g >> 1) & 1, abort) &&
@@ -768,7 +788,7 @@ __global__ void __launch_bounds__(kStripThreads, 1)
                     float v[16];
                     tc::tmem_ld16(tmem + (uint32_t)(a * UBN + 32 * cb) + ((uint32_t)(q * 32) << 16) + (uint32_t)c, v);
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) d[c + j] = v[j];
+                    for (int j = 0; j < 16; ++j) d[c + j] = v[j] * unscale;
                 }
                 // C box cb in shared memory: rows m0 .. m0 + 127 of columns n0 + 32 cb .. + 31,
                 // 128-byte rows with the 16-byte chunk index XOR-ed by (row % 8); C - L U goes back
@@ -885,6 +905,7 @@ bool mapM(CUtensorMap* m, const float* M, int64_t rows, int64_t cols, int64_t ld
 struct TcMaps {
     CUtensorMap m, u;
     bool f16;  // trailing updates with 3xFP16 products (FP16 side buffer), else 3xTF32
+    const double* res_max = nullptr;  // per-element residual maxima of a scaled FP16 re-solve
 };
 
 // Trailing update C -= L U over rows [r0, r_end) and columns [c0, c_end) of every element, with
@@ -904,10 +925,10 @@ elrt_status update(elrt_ctx* ctx, const TcMaps& mp, float* M, int64_t ld, int64_
     const unsigned grid = (unsigned)std::min<int64_t>(items, ctx->sms);
     if (mp.f16)
         k_tc_update<NK, true><<<grid, kStripThreads, UpdCfg<NK, true>::TOTAL, ctx->stream>>>(
-            mp.m, mp.u, tS, M, ctx->tab.nu, ld, estride, E, J, jb, koff, r0, r_end, c0, c_end, err);
+            mp.m, mp.u, tS, M, ctx->tab.nu, ld, estride, E, J, jb, koff, r0, r_end, c0, c_end, err, mp.res_max);
     else
         k_tc_update<NK, false><<<grid, kStripThreads, UpdCfg<NK, false>::TOTAL, ctx->stream>>>(
-            mp.m, mp.u, tS, M, ctx->tab.nu, ld, estride, E, J, jb, koff, r0, r_end, c0, c_end, err);
+            mp.m, mp.u, tS, M, ctx->tab.nu, ld, estride, E, J, jb, koff, r0, r_end, c0, c_end, err, nullptr);
     return cuda_check(ctx, cudaGetLastError(), "tc update launch");
 }
 
@@ -954,7 +975,8 @@ int panels_of(int nu) { return (nu + NBP - 1) / NBP; }
 
 template <int PTILE>
 void rowcol_launch(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, int64_t E, int J, int jb, const float* Tinv,
-                   int r_begin, int r_end, int c_begin, int c_end, int col_mode, float* Ut, int koff, int ut16) {
+                   int r_begin, int r_end, int c_begin, int c_end, int col_mode, float* Ut, int koff, int ut16,
+                   const double* res_max) {
     using C = RcCfg<PTILE>;
     const int nrt = r_end > r_begin ? (r_end - r_begin + PTILE - 1) / PTILE : 0;
     const int nct = c_end > c_begin ? (c_end - c_begin + PTILE - 1) / PTILE : 0;
@@ -962,16 +984,16 @@ void rowcol_launch(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, int64_t
     if (nrt > 0) {  // items: (element, row tile)
         const unsigned grid = (unsigned)std::min<int64_t>(E * nrt, (int64_t)C::PER_SM * ctx->sms);
         k_rowcol<0, PTILE><<<grid, PTILE, C::SMEM, ctx->stream>>>(nu, ld, estride, M, J, jb, Tinv, np, E, r_begin, r_end,
-                                                                 nrt, c_begin, c_end, 0, Ut, koff, ut16);
+                                                                 nrt, c_begin, c_end, 0, Ut, koff, ut16, nullptr);
     }
     if (nct > 0) {  // items: (element, column tile)
         const unsigned grid = (unsigned)std::min<int64_t>(E * nct, (int64_t)C::PER_SM * ctx->sms);
         if (col_mode == 0)
             k_rowcol<1, PTILE><<<grid, PTILE, C::SMEM, ctx->stream>>>(nu, ld, estride, M, J, jb, Tinv, np, E, r_begin,
-                                                                     r_end, 0, c_begin, c_end, nct, Ut, koff, ut16);
+                                                                     r_end, 0, c_begin, c_end, nct, Ut, koff, ut16, res_max);
         else
             k_rowcol<2, PTILE><<<grid, PTILE, C::SMEM, ctx->stream>>>(nu, ld, estride, M, J, jb, Tinv, np, E, r_begin,
-                                                                     r_end, 0, c_begin, c_end, nct, Ut, koff, ut16);
+                                                                     r_end, 0, c_begin, c_end, nct, Ut, koff, ut16, nullptr);
     }
 }
 
@@ -986,7 +1008,7 @@ elrt_status rowcol(elrt_ctx* ctx, const TcMaps& mp, float* M, int64_t ld, int64_
     const double flops = R * jb * (jb + 1.0) + (col_mode == 0 ? C * jb * (jb - 1.0) : C * jb * (jb + 1.0));
     ProfScope ps(ctx, "lu_tc_rowcol", (R > 0) + (C > 0), (double)E * bytes, (double)E * flops);
     rowcol_launch<kRcTile>(ctx, M, ld, estride, E, J, jb, Tinv, r_begin, r_end, c_begin, c_end, col_mode, Ut, koff,
-                           mp.f16 ? 1 : 0);
+                           mp.f16 ? 1 : 0, mp.res_max);
     return cuda_check(ctx, cudaGetLastError(), "rowcol launch");
 }
 
@@ -1100,13 +1122,19 @@ elrt_status tc_lu_factor_solve(elrt_ctx* ctx, float* M, int64_t ld, int64_t estr
 }
 
 // Re-solve A D = R for the right-hand sides in columns [nu, nu + nrhs) with the stored factors.
+// With f16 (and res_max, the per-element maxima of the residuals in those columns), the forward
+// sweep forms its products in 3xFP16 with the residual scaled into FP16's range per element; the
+// backward sweep keeps 3xTF32, because U^{-1} shrinks the correction of a thick element far below
+// its residual, where FP16 parts would be subnormal.
 elrt_status tc_lu_resolve(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, int64_t E, float* side, int* err,
-                          int nrhs, bool f16) {
+                          int nrhs, bool f16, const double* res_max) {
     const int nu = ctx->tab.nu, nin = nrhs;
     const Side sd = carve(side, E, ld);
     TcMaps mp;
-    elrt_status s = prepare(ctx, M, ld, estride, sd.Ut, E, &mp, f16);
+    const bool f16_fwd = f16 && res_max;
+    elrt_status s = prepare(ctx, M, ld, estride, sd.Ut, E, &mp, f16_fwd);
     if (s) return s;
+    if (f16_fwd) mp.res_max = res_max;
     int J = 0;
     // forward substitution with the unit lower factor, in the factorisation's panel pairs: X_a, the
     // rank-64 update of panel b's rows, X_b, one rank-128 update of the rows below the pair
@@ -1123,6 +1151,11 @@ elrt_status tc_lu_resolve(elrt_ctx* ctx, float* M, int64_t ld, int64_t estride, 
         s = rowcol(ctx, mp, M, ld, estride, E, J, jb, sd.Tinv, 0, 0, nu, nu + nin, 0, sd.Ut, 0);
         if (!s) s = update<64>(ctx, mp, M, ld, estride, E, J, jb, 0, J + jb, nu, nu, nu + nin, err);
         if (s) return s;
+    }
+    if (f16_fwd) {  // the backward sweep in 3xTF32: the FP32 side-buffer layout, no scale
+        s = prepare(ctx, M, ld, estride, sd.Ut, E, &mp, false);
+        if (s) return s;
+        mp.res_max = nullptr;
     }
     return backward_sweep_tc(ctx, mp, M, ld, estride, E, sd.Tinv, sd.Ut, err, nrhs);
 }
