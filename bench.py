@@ -38,8 +38,9 @@ WORKLOAD = workload_name(64)
 # tiles through HBM: "roof" takes whichever floor binds, the bytes at the copy bandwidth or the
 # issued flops (each product three times, hi*hi + lo*hi + hi*lo) at the TF32 tensor peak, and
 # reports the achieved fraction of that roof (the other fraction beside it).  The factorisation's
-# updates form their products in 3xFP16, at twice the TF32 rate, so the tensor fraction counted at
-# the TF32 rate is an upper bound on the tensor pipe's share.
+# updates and the refinement re-solves' forward sweeps form their products in 3xFP16, at twice the
+# TF32 rate, so the tensor fraction counted at the TF32 rate is an upper bound on the tensor pipe's
+# share.
 KERNEL_BOUND = {
     "assemble": ("hbm", None), "lu_factor_solve": ("alu", "fp32"), "lu_resolve": ("hbm", None),
     "lu_tc_diag": ("alu", "fp32"), "lu_tc_rowcol": ("hbm", None), "lu_tc_update": ("roof", "tf32x3"),

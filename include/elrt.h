@@ -171,8 +171,9 @@ elrt_status elrt_set_precond(elrt_ctx* ctx, int32_t kind);
  * ELRT_LU_PRODUCTS_AUTO (the default): 3xFP16 -- each operand as its FP16 rounding plus the FP16
  * rounding of the remainder, hi*hi + hi*lo + lo*hi accumulated in FP32, ~22-bit products like
  * 3xTF32 at half the tensor-core instructions -- for a batch chunk whose assembled entries all lie
- * in [0.25, 1024] and that has no source column, and 3xTF32 otherwise; the refinement re-solves
- * always use 3xTF32 (their right-hand sides are residuals far below FP16's normal range).
+ * in [0.25, 1024] and that has no source column, and 3xTF32 otherwise; the refinement re-solves of
+ * such a chunk run their forward sweep in 3xFP16 too (each element's residual scaled by a power of
+ * two into [0.5, 1)) and their backward sweep in 3xTF32.
  * ELRT_LU_PRODUCTS_TF32: 3xTF32 everywhere.  The refined operators meet the same accuracy either way.
  * ELRT_EINVAL on another value. */
 typedef enum { ELRT_LU_PRODUCTS_AUTO = 0, ELRT_LU_PRODUCTS_TF32 = 1 } elrt_lu_products;
