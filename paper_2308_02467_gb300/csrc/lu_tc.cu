@@ -14,7 +14,8 @@
 //                      transposed (K-major), to one FP32 side buffer whose rows hold both panels of
 //                      the pair.  On the right-hand-side columns this is the forward substitution;
 //   k_tc_update<NK, H> (tensor cores): C -= L21 U12 with three products hi*hi + hi*lo + lo*hi of
-//                      TF32 parts or (H, the factorisation when the entries fit FP16's range) FP16
+//                      TF32 parts or (H, when the entries fit FP16's range: the factorisation and
+//                      the re-solves' forward sweeps, their residuals scaled per element) FP16
 //                      parts, both FP32-level accuracy; FP16 needs half the MMA instructions (K = 16
 //                      per instruction against 8).  Panel a is applied with rank 64 to panel b's
 //                      columns and rows only; once panel b is factored, the rest of the matrix
@@ -23,9 +24,9 @@
 //                      the side buffer, C from the matrix); the L21 strip goes straight from the
 //                      matrix into tensor memory as TF32 high and low parts.
 // Panels left over after the pairs (nu not a multiple of 128) are factored one at a time with
-// rank-64 updates.  The backward substitution and the forward/backward sweeps of the refinement
-// re-solves reuse the stored factors (L21 and U12 in the matrix, the diagonal blocks) with the same
-// kernels.
+// rank-64 updates; in the backward sweeps a last partial panel joins the panel before it.  The
+// backward substitution and the forward/backward sweeps of the refinement re-solves reuse the
+// stored factors (L21 and U12 in the matrix, the diagonal blocks) with the same kernels.
 #include <math.h>
 #include <stdio.h>
 
