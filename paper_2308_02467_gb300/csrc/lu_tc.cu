@@ -11,8 +11,9 @@
 //                      as U11, L11^T, U11^T and 1 / diag(U11);
 //   k_rowcol           (blocks of 128 rows or columns per element): L21 from L21 U11 = A21 written
 //                      back to the matrix; U12 from L11 U12 = A12 written back to the matrix and,
-//                      transposed (K-major), to one FP32 side buffer whose rows hold both panels of
-//                      the pair.  On the right-hand-side columns this is the forward substitution;
+//                      transposed (K-major), to one side buffer whose rows hold both panels of the
+//                      pair (FP32 values and their low TF32 parts, or FP16 high parts and FP16
+//                      remainders).  On the right-hand-side columns this is the forward substitution;
 //   k_tc_update<NK, H> (tensor cores): C -= L21 U12 with three products hi*hi + hi*lo + lo*hi of
 //                      TF32 parts or (H, when the entries fit FP16's range: the factorisation and
 //                      the re-solves' forward sweeps, their residuals scaled per element) FP16
@@ -22,7 +23,7 @@
 //                      takes both panels in one rank-128 update, which moves the C tiles half as
 //                      often as two rank-64 updates.  The FP32 operands come in by TMA (U12^T from
 //                      the side buffer, C from the matrix); the L21 strip goes straight from the
-//                      matrix into tensor memory as TF32 high and low parts.
+//                      matrix into tensor memory as TF32 (or FP16) high and low parts.
 // Panels left over after the pairs (nu not a multiple of 128) are factored one at a time with
 // rank-64 updates; in the backward sweeps a last partial panel joins the panel before it.  The
 // backward substitution and the forward/backward sweeps of the refinement re-solves reuse the
