@@ -59,11 +59,11 @@ def tensor_peak_tflops(peaks):
     return peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]) * TF32_PER_BF16
 # DRAM bytes (read + write) per element and step of each kernel group, from one ncu capture of
 # the 32 x 32 slab (1024 elements, one local-build chunk; summary kept under profiles/); a group
-# missing here has no capture of its current kernel.  Scaled to a launch of the benchmark by
-# elements / launches.
+# missing here has no capture of its current kernel (the trailing update and the panel solves
+# changed after it: FP16 forward re-solves, the grouped last panel of the backward sweeps).  Scaled
+# to a launch of the benchmark by elements / launches.
 DRAM_BYTES_PER_ELEMENT_STEP = {
-    "lu_tc_update": 4.595e7, "lu_tc_rowcol": 1.382e7, "lu_tc_diag": 3.275e5, "residual": 3.704e6,
-    "assemble": 3.174e6, "restrict": 2.905e6,
+    "lu_tc_diag": 3.275e5, "residual": 3.704e6, "assemble": 3.174e6, "restrict": 2.905e6,
 }
 
 
